@@ -1,0 +1,210 @@
+/*
+ * psatd.h - C ABI of the GB300 PSATD push library (libpsatd.so).
+ *
+ * The library advances Maxwell's equations with the pseudo-spectral
+ * analytical time-domain (PSATD) method of arbitrary stencil order p on a
+ * batch of FFT boxes, each box being a sub-domain padded with guard cells
+ * ('local' decomposition, paper Fig. 1a and Sec. 1.3) or a group of
+ * sub-domains with guards only on its outer faces ('hybrid' decomposition,
+ * paper Fig. 1b and Sec. 2.1).  One step is, for every box:
+ *   S1  3D real-to-complex FFT of E, B (and J, rho) over the padded box,
+ *   S2  per-mode analytical update in k-space with order-p staggered
+ *       modified wavenumbers and Yee phase shifts (Sec. 1.1),
+ *   S3  inverse 3D FFT,
+ * then, across boxes,
+ *   S4  the guard exchange: each guard cell receives the value of the
+ *       interior cell that owns the same global position (Fig. 1, step (ii)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All pointers named "device" are CUDA device pointers of the current
+ *    device; they are owned by the caller and never freed by the library.
+ *  - A field component is ONE contiguous buffer holding every box of the
+ *    plan, box b starting at element psatd_plan_layout(...).elem_offset.
+ *    Inside a box the cell (x, y, z) is element x + n[0]*(y + n[1]*z)
+ *    (x fastest).  Element type: float (precision 32) or double (64).
+ *    Buffers must be at least 16-byte aligned; box offsets are multiples of
+ *    64 elements.
+ *  - Yee positions (in cells): E_x (i+1/2,j,k), E_y (i,j+1/2,k),
+ *    E_z (i,j,k+1/2), B_x (i,j+1/2,k+1/2), B_y (i+1/2,j,k+1/2),
+ *    B_z (i+1/2,j+1/2,k); J like E; rho at (i,j,k).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every device-side operation is asynchronous on it.
+ *  - Errors: argument and plan errors are returned synchronously and leave
+ *    no device work queued.  CUDA failures return PSATD_ERR_CUDA; the text
+ *    is available from psatd_last_error.  No call aborts the process and no
+ *    C++ exception crosses this boundary.
+ *  - A plan is not thread-safe: use it from one host thread and one stream
+ *    at a time.
+ */
+#ifndef PSATD_H
+#define PSATD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PSATD_OK = 0,
+  PSATD_ERR_INVALID_ARG = 1,      /* NULL pointer, bad count, bad geometry  */
+  PSATD_ERR_UNSUPPORTED_SIZE = 2, /* box size not even / not 5-smooth / too large */
+  PSATD_ERR_UNSUPPORTED_ORDER = 3,/* stencil order not 0 and not even in [2, 256] */
+  PSATD_ERR_OUT_OF_MEMORY = 4,    /* device allocation failed               */
+  PSATD_ERR_CUDA = 5,             /* a CUDA runtime call failed             */
+  PSATD_ERR_TIMEOUT = 6,          /* a bounded device-side wait ran out     */
+  PSATD_ERR_STATE = 7             /* call not valid for this plan's state   */
+} psatd_status;
+
+/* Decomposition of the global domain into FFT boxes (paper Fig. 1, Sec. 2.1). */
+typedef enum {
+  PSATD_DECOMP_GLOBAL = 0,      /* one box, the whole periodic domain (Sec. 1.2) */
+  PSATD_DECOMP_LOCAL = 1,       /* sub-domains with guards on every face (Sec. 1.3) */
+  PSATD_DECOMP_HYBRID = 2,      /* groups with guards on split axes only (Sec. 2.1) */
+  PSATD_DECOMP_INDEPENDENT = 3  /* self-periodic boxes: guards wrap onto own interior */
+} psatd_decomp;
+
+/* plan flags */
+#define PSATD_VACUUM         0x1u /* J = rho = 0: only E and B are read and written   */
+#define PSATD_RHO_CONTINUITY 0x2u /* rho is in/out, advanced by continuity; E takes   */
+                                  /* its longitudinal part from Gauss's law (rho form) */
+#define PSATD_NO_GRAPH       0x8u /* never capture multi-step pushes in a CUDA graph   */
+
+/* One FFT box.  n[] counts cells including guards; each n[d] must be even,
+ * 5-smooth (2^a 3^b 5^c), n[0] in [4, 1024], n[1], n[2] in [4, 512].
+ * ng_lo/ng_hi are the guard widths on the low/high face of each axis
+ * (0 on an axis that is periodic inside the box).  origin[] is the global
+ * index of the first interior cell.  order_p is the stencil order: even in
+ * [2, 256], or 0 for infinite order (pure spectral, Sec. 1.1). */
+typedef struct {
+  int32_t n[3];
+  int32_t ng_lo[3];
+  int32_t ng_hi[3];
+  int64_t origin[3];
+  int32_t order_p;
+} psatd_box;
+
+/* Plan description.  global_n/periodic describe the global domain (ignored
+ * for PSATD_DECOMP_INDEPENDENT); box interiors must tile it exactly.
+ * Non-periodic axes fill guard cells outside the domain with 0.
+ * dx: cell sizes; dt: time step (any sign); c: speed of light; eps0: vacuum
+ * permittivity; precision: 32 (float) or 64 (double) field arithmetic (the
+ * tables are always generated in double).  `boxes` is read during
+ * psatd_plan_create only. */
+typedef struct {
+  int32_t global_n[3];
+  int32_t periodic[3];
+  double dx[3];
+  double dt;
+  double c;
+  double eps0;
+  int32_t precision;
+  psatd_decomp decomp;
+  int32_t num_boxes;
+  const psatd_box* boxes;
+  uint32_t flags;
+} psatd_plan_desc;
+
+typedef struct psatd_plan psatd_plan;
+
+/* Field buffers (device, caller-owned, in/out). */
+typedef struct {
+  void* E[3];
+  void* B[3];
+} psatd_fields;
+
+/* Source buffers (device, caller-owned).  J is read-only and must already
+ * hold consistent guard values (fill them once with psatd_guard_exchange);
+ * rho is in/out with PSATD_RHO_CONTINUITY, unused otherwise.  Pass NULL for
+ * the whole struct with PSATD_VACUUM. */
+typedef struct {
+  const void* J[3];
+  void* rho;
+} psatd_sources;
+
+/* One guard-exchange copy block (host view of the precomputed exchange
+ * protocol, cf. the paper's Sec. 2.5.2 "intersection ... computed before the
+ * PIC loop").  src_box = -1 means "fill with zero" (outside a non-periodic
+ * domain).  Coordinates are box-local cell indices. */
+typedef struct {
+  int32_t dst_box, src_box;
+  int32_t dst_lo[3], src_lo[3], ext[3];
+} psatd_copy_block;
+
+/* Check a description without touching the GPU.  Returns PSATD_OK or the
+ * first error found; `msg` (may be NULL) receives a NUL-terminated reason of
+ * at most msg_len bytes. */
+psatd_status psatd_plan_validate(const psatd_plan_desc* desc, char* msg, size_t msg_len);
+
+/* Host-only: compute the guard-exchange copy blocks of a valid description.
+ * Writes up to `cap` blocks to `out` (may be NULL when cap = 0) and the total
+ * count to *count. */
+psatd_status psatd_exchange_blocks(const psatd_plan_desc* desc, psatd_copy_block* out,
+                                   int64_t cap, int64_t* count);
+
+/* Build a plan: validate, build the copy blocks and work lists, allocate the
+ * spectral workspace and tables, and generate the FP64 tables (twiddles,
+ * modified wavenumbers k_p, Yee phase factors, PSATD coefficients) with
+ * device kernels on `stream`.  Returns when the plan is ready.  On error
+ * *out is set to NULL and nothing is leaked. */
+psatd_status psatd_plan_create(const psatd_plan_desc* desc, void* stream, psatd_plan** out);
+
+/* Free every resource of the plan (synchronises the device first). NULL is ok. */
+psatd_status psatd_plan_destroy(psatd_plan* plan);
+
+/* Element offset and element count of box `box` inside every field buffer. */
+psatd_status psatd_plan_layout(const psatd_plan* plan, int32_t box, int64_t* elem_offset,
+                               int64_t* elems);
+
+/* Bytes of one field-component buffer (all boxes) and of the plan-owned
+ * device memory (spectral workspace plus tables). */
+psatd_status psatd_plan_memory(const psatd_plan* plan, size_t* field_bytes,
+                               size_t* workspace_bytes);
+
+/* S4 (and the initial fill, S0): copy every guard cell of E, B from its
+ * owning interior cell; with `src` non-NULL also J and rho.  Asynchronous. */
+psatd_status psatd_guard_exchange(psatd_plan* plan, const psatd_fields* fields,
+                                  const psatd_sources* src, void* stream);
+
+/* Advance `nsteps` >= 0 steps of S1..S4 in place on `fields` (and rho).
+ * Guards of E, B must be consistent on entry (psatd_guard_exchange) and are
+ * consistent on return.  Asynchronous on `stream`. */
+psatd_status psatd_push(psatd_plan* plan, const psatd_fields* fields,
+                        const psatd_sources* src, int32_t nsteps, void* stream);
+
+/* S1 alone for one component: unnormalised 3D R2C FFT of every box of
+ * `field` (device, one component buffer) into `spectrum` (device, complex
+ * float2/double2, box b at psatd_plan_spectrum_layout offset, element
+ * (mx, my, mz) at mx + (n[0]/2+1)*(my + n[1]*mz)). */
+psatd_status psatd_forward_fft(psatd_plan* plan, const void* field, void* spectrum,
+                               void* stream);
+
+/* S3 alone: C2R inverse (with the 1/(n0 n1 n2) factor) of `spectrum` into
+ * every cell of `field`.  `spectrum` is used as scratch and overwritten. */
+psatd_status psatd_inverse_fft(psatd_plan* plan, void* spectrum, void* field, void* stream);
+
+/* Complex-element offset and count of box `box` in a spectrum buffer. */
+psatd_status psatd_plan_spectrum_layout(const psatd_plan* plan, int32_t box,
+                                        int64_t* elem_offset, int64_t* elems);
+
+/* Wait for the plan's last stream and return the first pending error
+ * (CUDA error or device-side status word). */
+psatd_status psatd_sync_status(psatd_plan* plan);
+
+/* Static text for a status code. */
+const char* psatd_status_string(psatd_status s);
+
+/* Text of the last error of `plan`, or of the calling thread's last failed
+ * psatd_plan_create / psatd_plan_validate when plan is NULL.  Never NULL. */
+const char* psatd_last_error(const psatd_plan* plan);
+
+/* Number of kernel launches issued by the last psatd_push call (host count). */
+int64_t psatd_last_launch_count(const psatd_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSATD_H */

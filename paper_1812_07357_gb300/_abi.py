@@ -1,0 +1,207 @@
+"""ctypes binding of include/psatd.h: argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of its own; a missing or unbuilt library raises immediately (there
+is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (POINTER, Structure, c_char_p, c_double, c_int32, c_int64,
+                    c_size_t, c_uint32, c_void_p)
+
+from . import build as _build
+
+PSATD_OK = 0
+PSATD_ERR_INVALID_ARG = 1
+PSATD_ERR_UNSUPPORTED_SIZE = 2
+PSATD_ERR_UNSUPPORTED_ORDER = 3
+PSATD_ERR_OUT_OF_MEMORY = 4
+PSATD_ERR_CUDA = 5
+PSATD_ERR_TIMEOUT = 6
+PSATD_ERR_STATE = 7
+
+PSATD_DECOMP_GLOBAL = 0
+PSATD_DECOMP_LOCAL = 1
+PSATD_DECOMP_HYBRID = 2
+PSATD_DECOMP_INDEPENDENT = 3
+
+PSATD_VACUUM = 0x1
+PSATD_RHO_CONTINUITY = 0x2
+PSATD_NO_GRAPH = 0x8
+
+
+class psatd_box(Structure):
+    _fields_ = [("n", c_int32 * 3), ("ng_lo", c_int32 * 3), ("ng_hi", c_int32 * 3),
+                ("origin", c_int64 * 3), ("order_p", c_int32)]
+
+
+class psatd_plan_desc(Structure):
+    _fields_ = [("global_n", c_int32 * 3), ("periodic", c_int32 * 3), ("dx", c_double * 3),
+                ("dt", c_double), ("c", c_double), ("eps0", c_double), ("precision", c_int32),
+                ("decomp", c_int32), ("num_boxes", c_int32), ("boxes", POINTER(psatd_box)),
+                ("flags", c_uint32)]
+
+
+class psatd_fields(Structure):
+    _fields_ = [("E", c_void_p * 3), ("B", c_void_p * 3)]
+
+
+class psatd_sources(Structure):
+    _fields_ = [("J", c_void_p * 3), ("rho", c_void_p)]
+
+
+class psatd_copy_block(Structure):
+    _fields_ = [("dst_box", c_int32), ("src_box", c_int32), ("dst_lo", c_int32 * 3),
+                ("src_lo", c_int32 * 3), ("ext", c_int32 * 3)]
+
+
+class PsatdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{status_name(status)}: {msg}")
+        self.status = status
+
+
+_SIGS = {
+    "psatd_plan_validate": (c_int32, [POINTER(psatd_plan_desc), c_char_p, c_size_t]),
+    "psatd_exchange_blocks": (c_int32, [POINTER(psatd_plan_desc), POINTER(psatd_copy_block),
+                                        c_int64, POINTER(c_int64)]),
+    "psatd_plan_create": (c_int32, [POINTER(psatd_plan_desc), c_void_p, POINTER(c_void_p)]),
+    "psatd_plan_destroy": (c_int32, [c_void_p]),
+    "psatd_plan_layout": (c_int32, [c_void_p, c_int32, POINTER(c_int64), POINTER(c_int64)]),
+    "psatd_plan_memory": (c_int32, [c_void_p, POINTER(c_size_t), POINTER(c_size_t)]),
+    "psatd_guard_exchange": (c_int32, [c_void_p, POINTER(psatd_fields), POINTER(psatd_sources),
+                                       c_void_p]),
+    "psatd_push": (c_int32, [c_void_p, POINTER(psatd_fields), POINTER(psatd_sources), c_int32,
+                             c_void_p]),
+    "psatd_forward_fft": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "psatd_inverse_fft": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "psatd_plan_spectrum_layout": (c_int32, [c_void_p, c_int32, POINTER(c_int64),
+                                             POINTER(c_int64)]),
+    "psatd_sync_status": (c_int32, [c_void_p]),
+    "psatd_status_string": (c_char_p, [c_int32]),
+    "psatd_last_error": (c_char_p, [c_void_p]),
+    "psatd_last_launch_count": (c_int64, [c_void_p]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libpsatd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with paper_1812_07357_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def status_name(s: int) -> str:
+    try:
+        return load().psatd_status_string(s).decode()
+    except Exception:  # library unavailable while formatting an error
+        return f"status {s}"
+
+
+def _check(st, plan=None):
+    if st != PSATD_OK:
+        raise PsatdError(st, psatd_last_error(plan))
+
+
+# --- one wrapper per entry point (same names) ------------------------------
+
+def psatd_plan_validate(desc: psatd_plan_desc):
+    buf = ctypes.create_string_buffer(512)
+    st = load().psatd_plan_validate(ctypes.byref(desc), buf, 512)
+    return st, buf.value.decode()
+
+
+def psatd_exchange_blocks(desc: psatd_plan_desc):
+    n = c_int64(0)
+    _check(load().psatd_exchange_blocks(ctypes.byref(desc), None, 0, ctypes.byref(n)))
+    arr = (psatd_copy_block * max(n.value, 1))()
+    _check(load().psatd_exchange_blocks(ctypes.byref(desc), arr, n.value, ctypes.byref(n)))
+    return [arr[i] for i in range(n.value)]
+
+
+def psatd_plan_create(desc: psatd_plan_desc, stream: int = 0) -> int:
+    out = c_void_p()
+    _check(load().psatd_plan_create(ctypes.byref(desc), c_void_p(stream), ctypes.byref(out)))
+    return out.value
+
+
+def psatd_plan_destroy(plan: int):
+    _check(load().psatd_plan_destroy(c_void_p(plan)))
+
+
+def psatd_plan_layout(plan: int, box: int):
+    off, n = c_int64(), c_int64()
+    _check(load().psatd_plan_layout(c_void_p(plan), box, ctypes.byref(off), ctypes.byref(n)), plan)
+    return off.value, n.value
+
+
+def psatd_plan_spectrum_layout(plan: int, box: int):
+    off, n = c_int64(), c_int64()
+    _check(load().psatd_plan_spectrum_layout(c_void_p(plan), box, ctypes.byref(off),
+                                             ctypes.byref(n)), plan)
+    return off.value, n.value
+
+
+def psatd_plan_memory(plan: int):
+    f, w = c_size_t(), c_size_t()
+    _check(load().psatd_plan_memory(c_void_p(plan), ctypes.byref(f), ctypes.byref(w)), plan)
+    return f.value, w.value
+
+
+def psatd_guard_exchange(plan: int, fields: psatd_fields, src: psatd_sources | None,
+                         stream: int = 0):
+    _check(load().psatd_guard_exchange(c_void_p(plan), ctypes.byref(fields),
+                                       ctypes.byref(src) if src is not None else None,
+                                       c_void_p(stream)), plan)
+
+
+def psatd_push(plan: int, fields: psatd_fields, src: psatd_sources | None, nsteps: int,
+               stream: int = 0):
+    _check(load().psatd_push(c_void_p(plan), ctypes.byref(fields),
+                             ctypes.byref(src) if src is not None else None, nsteps,
+                             c_void_p(stream)), plan)
+
+
+def psatd_forward_fft(plan: int, field: int, spectrum: int, stream: int = 0):
+    _check(load().psatd_forward_fft(c_void_p(plan), c_void_p(field), c_void_p(spectrum),
+                                    c_void_p(stream)), plan)
+
+
+def psatd_inverse_fft(plan: int, spectrum: int, field: int, stream: int = 0):
+    _check(load().psatd_inverse_fft(c_void_p(plan), c_void_p(spectrum), c_void_p(field),
+                                    c_void_p(stream)), plan)
+
+
+def psatd_sync_status(plan: int):
+    _check(load().psatd_sync_status(c_void_p(plan)), plan)
+
+
+def psatd_status_string(s: int) -> str:
+    return load().psatd_status_string(s).decode()
+
+
+def psatd_last_error(plan: int | None = None) -> str:
+    return load().psatd_last_error(c_void_p(plan) if plan else None).decode()
+
+
+def psatd_last_launch_count(plan: int) -> int:
+    return int(load().psatd_last_launch_count(c_void_p(plan)))

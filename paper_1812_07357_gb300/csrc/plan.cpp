@@ -1,0 +1,817 @@
+// Host side of the PSATD library: description validation, the guard-exchange
+// protocol (copy blocks from box-overlap geometry, computed once before any
+// step as the paper's Sec. 2.5.2 describes for its G1/G2 grids), work lists,
+// device tables, and the C ABI entry points declared in include/psatd.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "psatd_internal.h"
+
+using namespace psatd;
+
+namespace {
+
+thread_local std::string g_thread_error = "no error";
+
+void set_msg(char* msg, size_t len, const std::string& s) {
+  if (msg && len) {
+    size_t n = std::min(len - 1, s.size());
+    std::memcpy(msg, s.data(), n);
+    msg[n] = 0;
+  }
+}
+
+std::string fmt(const char* f, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, f);
+  std::vsnprintf(buf, sizeof buf, f, ap);
+  va_end(ap);
+  return buf;
+}
+
+bool five_smooth(int n) {
+  if (n <= 0) return false;
+  for (int f : {2, 3, 5})
+    while (n % f == 0) n /= f;
+  return n == 1;
+}
+
+int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+struct Err {
+  psatd_status st;
+  std::string msg;
+};
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+Err validate(const psatd_plan_desc* d) {
+  if (!d) return {PSATD_ERR_INVALID_ARG, "desc is NULL"};
+  if (d->num_boxes < 1 || !d->boxes) return {PSATD_ERR_INVALID_ARG, "no boxes"};
+  if (d->precision != 32 && d->precision != 64)
+    return {PSATD_ERR_INVALID_ARG, fmt("precision %d is not 32 or 64", d->precision)};
+  if (!(std::isfinite(d->dt)) || d->dt == 0.0) return {PSATD_ERR_INVALID_ARG, "dt must be finite and nonzero"};
+  if (!(d->c > 0.0) || !std::isfinite(d->c)) return {PSATD_ERR_INVALID_ARG, "c must be > 0"};
+  if (!(d->eps0 > 0.0) || !std::isfinite(d->eps0)) return {PSATD_ERR_INVALID_ARG, "eps0 must be > 0"};
+  for (int a = 0; a < 3; ++a)
+    if (!(d->dx[a] > 0.0) || !std::isfinite(d->dx[a])) return {PSATD_ERR_INVALID_ARG, "dx must be > 0"};
+  const uint32_t known = PSATD_VACUUM | PSATD_RHO_CONTINUITY | PSATD_NO_GRAPH;
+  if (d->flags & ~known) return {PSATD_ERR_INVALID_ARG, "unknown flag bits"};
+  if ((d->flags & PSATD_VACUUM) && (d->flags & PSATD_RHO_CONTINUITY))
+    return {PSATD_ERR_INVALID_ARG, "PSATD_VACUUM and PSATD_RHO_CONTINUITY exclude each other"};
+  if (d->decomp < PSATD_DECOMP_GLOBAL || d->decomp > PSATD_DECOMP_INDEPENDENT)
+    return {PSATD_ERR_INVALID_ARG, "unknown decomposition"};
+  for (int i = 0; i < d->num_boxes; ++i) {
+    const psatd_box& b = d->boxes[i];
+    for (int a = 0; a < 3; ++a) {
+      const int lim = a == 0 ? 1024 : 512;
+      if (b.n[a] < 4 || b.n[a] % 2 || !five_smooth(b.n[a]) || b.n[a] > lim)
+        return {PSATD_ERR_UNSUPPORTED_SIZE,
+                fmt("box %d: n[%d] = %d must be even, 5-smooth, in [4, %d]", i, a, b.n[a], lim)};
+      if (b.ng_lo[a] < 0 || b.ng_hi[a] < 0 || b.ng_lo[a] + b.ng_hi[a] >= b.n[a])
+        return {PSATD_ERR_INVALID_ARG,
+                fmt("box %d: guards %d + %d leave no interior on axis %d", i, b.ng_lo[a], b.ng_hi[a], a)};
+    }
+    if (!(b.order_p == 0 || (b.order_p >= 2 && b.order_p <= 256 && b.order_p % 2 == 0)))
+      return {PSATD_ERR_UNSUPPORTED_ORDER, fmt("box %d: order %d is not 0 or even in [2, 256]", i, b.order_p)};
+  }
+  if (d->decomp == PSATD_DECOMP_INDEPENDENT) return {PSATD_OK, ""};
+  for (int a = 0; a < 3; ++a) {
+    if (d->global_n[a] < 1) return {PSATD_ERR_INVALID_ARG, "global_n must be >= 1"};
+    if (d->periodic[a] != 0 && d->periodic[a] != 1) return {PSATD_ERR_INVALID_ARG, "periodic must be 0 or 1"};
+  }
+  if (d->decomp == PSATD_DECOMP_GLOBAL) {
+    if (d->num_boxes != 1) return {PSATD_ERR_INVALID_ARG, "global decomposition takes one box"};
+    const psatd_box& b = d->boxes[0];
+    for (int a = 0; a < 3; ++a)
+      if (b.ng_lo[a] || b.ng_hi[a] || b.n[a] != d->global_n[a] || b.origin[a] != 0)
+        return {PSATD_ERR_INVALID_ARG, "global box must equal the domain, without guards"};
+  }
+  // interiors must tile the domain: inside, volumes add up, no overlaps
+  int64_t vol = 0;
+  for (int i = 0; i < d->num_boxes; ++i) {
+    const psatd_box& b = d->boxes[i];
+    int64_t v = 1;
+    for (int a = 0; a < 3; ++a) {
+      const int64_t m = b.n[a] - b.ng_lo[a] - b.ng_hi[a];
+      if (b.origin[a] < 0 || b.origin[a] + m > d->global_n[a])
+        return {PSATD_ERR_INVALID_ARG, fmt("box %d interior leaves the domain on axis %d", i, a)};
+      v *= m;
+    }
+    vol += v;
+  }
+  const int64_t gv = (int64_t)d->global_n[0] * d->global_n[1] * d->global_n[2];
+  if (vol != gv) return {PSATD_ERR_INVALID_ARG, "box interiors do not cover the domain exactly"};
+  for (int i = 0; i < d->num_boxes; ++i)
+    for (int j = i + 1; j < d->num_boxes; ++j) {
+      const psatd_box &p = d->boxes[i], &q = d->boxes[j];
+      bool overlap = true;
+      for (int a = 0; a < 3; ++a) {
+        const int64_t pl = p.origin[a], ph = pl + p.n[a] - p.ng_lo[a] - p.ng_hi[a];
+        const int64_t ql = q.origin[a], qh = ql + q.n[a] - q.ng_lo[a] - q.ng_hi[a];
+        if (ph <= ql || qh <= pl) overlap = false;
+      }
+      if (overlap) return {PSATD_ERR_INVALID_ARG, fmt("box interiors %d and %d overlap", i, j)};
+    }
+  return {PSATD_OK, ""};
+}
+
+// ---------------------------------------------------------------------------
+// guard-exchange protocol
+// ---------------------------------------------------------------------------
+struct Seg {
+  int64_t dst, g, len;
+  bool outside;
+};
+
+// Split the padded range [a, a+n) of one axis into pieces that map onto the
+// global axis [0, N) (periodic: wrap; otherwise pieces outside are flagged).
+std::vector<Seg> axis_segments(int64_t a, int64_t n, int64_t N, bool periodic) {
+  std::vector<Seg> out;
+  int64_t pos = a;
+  const int64_t end = a + n;
+  while (pos < end) {
+    if (periodic) {
+      const int64_t w = ((pos % N) + N) % N;
+      const int64_t l = std::min(end - pos, N - w);
+      out.push_back({pos - a, w, l, false});
+      pos += l;
+    } else if (pos < 0) {
+      const int64_t l = std::min(end, (int64_t)0) - pos;
+      out.push_back({pos - a, 0, l, true});
+      pos += l;
+    } else if (pos >= N) {
+      out.push_back({pos - a, 0, end - pos, true});
+      pos = end;
+    } else {
+      const int64_t l = std::min(end, N) - pos;
+      out.push_back({pos - a, pos, l, false});
+      pos += l;
+    }
+  }
+  return out;
+}
+
+std::vector<CopyBlk> build_blocks(const psatd_plan_desc* d) {
+  std::vector<CopyBlk> out;
+  const bool indep = d->decomp == PSATD_DECOMP_INDEPENDENT;
+  for (int b = 0; b < d->num_boxes; ++b) {
+    const psatd_box& B = d->boxes[b];
+    bool guards = false;
+    for (int a = 0; a < 3; ++a) guards |= B.ng_lo[a] || B.ng_hi[a];
+    if (!guards) continue;
+    int64_t N[3], org[3];
+    bool per[3];
+    for (int a = 0; a < 3; ++a) {
+      const int64_t m = B.n[a] - B.ng_lo[a] - B.ng_hi[a];
+      N[a] = indep ? m : d->global_n[a];
+      org[a] = indep ? 0 : B.origin[a];
+      per[a] = indep ? true : d->periodic[a] != 0;
+    }
+    std::vector<Seg> s[3];
+    for (int a = 0; a < 3; ++a) s[a] = axis_segments(org[a] - B.ng_lo[a], B.n[a], N[a], per[a]);
+    for (const Seg& sz : s[2])
+      for (const Seg& sy : s[1])
+        for (const Seg& sx : s[0]) {
+          const Seg* sg[3] = {&sx, &sy, &sz};
+          if (sx.outside || sy.outside || sz.outside) {
+            CopyBlk c{};
+            c.dst_box = b;
+            c.src_box = -1;
+            for (int a = 0; a < 3; ++a) {
+              c.dst_lo[a] = (int32_t)sg[a]->dst;
+              c.src_lo[a] = 0;
+              c.ext[a] = (int32_t)sg[a]->len;
+            }
+            out.push_back(c);
+            continue;
+          }
+          const int s0 = indep ? b : 0, s1 = indep ? b + 1 : d->num_boxes;
+          for (int sb = s0; sb < s1; ++sb) {
+            const psatd_box& S = d->boxes[sb];
+            int64_t lo[3], hi[3];
+            bool empty = false;
+            for (int a = 0; a < 3; ++a) {
+              const int64_t so = indep ? 0 : S.origin[a];
+              const int64_t sm = S.n[a] - S.ng_lo[a] - S.ng_hi[a];
+              lo[a] = std::max(sg[a]->g, so);
+              hi[a] = std::min(sg[a]->g + sg[a]->len, so + sm);
+              if (hi[a] <= lo[a]) empty = true;
+            }
+            if (empty) continue;
+            CopyBlk c{};
+            c.dst_box = b;
+            c.src_box = sb;
+            bool same = sb == b;
+            for (int a = 0; a < 3; ++a) {
+              const int64_t so = indep ? 0 : S.origin[a];
+              c.dst_lo[a] = (int32_t)(sg[a]->dst + (lo[a] - sg[a]->g));
+              c.src_lo[a] = (int32_t)(lo[a] - so + S.ng_lo[a]);
+              c.ext[a] = (int32_t)(hi[a] - lo[a]);
+              same = same && c.dst_lo[a] == c.src_lo[a];
+            }
+            if (!same) out.push_back(c);
+          }
+        }
+  }
+  return out;
+}
+
+// Radix schedule: 8s first (4,4 instead of 8,2), then 4 / 2, 3s and 5s.
+bool radix_plan(int n, AxisPlan& ap) {
+  ap.n = n;
+  ap.npass = 0;
+  int e2 = 0, v = n;
+  while (v % 2 == 0) v /= 2, ++e2;
+  std::vector<int> r;
+  int n8 = e2 / 3, rem = e2 % 3;
+  if (rem == 1 && n8 > 0) {
+    --n8;
+    rem = 4;
+  }
+  for (int i = 0; i < n8; ++i) r.push_back(8);
+  if (rem == 4) r.push_back(4), r.push_back(4);
+  if (rem == 2) r.push_back(4);
+  if (rem == 1) r.push_back(2);
+  while (v % 5 == 0) v /= 5, r.push_back(5);
+  while (v % 3 == 0) v /= 3, r.push_back(3);
+  if (v != 1 || (int)r.size() > kMaxPass) return false;
+  for (size_t i = 0; i < r.size(); ++i) ap.radix[i] = (uint8_t)r[i];
+  ap.npass = (int)r.size();
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the plan
+// ---------------------------------------------------------------------------
+struct psatd_plan {
+  psatd_plan_desc desc{};
+  std::vector<psatd_box> boxes;
+  int prec = 32;
+  int form = kVacuum;
+  size_t csize = 8;  // bytes of one complex element
+  size_t rsize = 4;
+
+  std::vector<BoxDev> hboxes;
+  std::vector<ShapeDev> hshapes;
+  std::vector<RowJob> rows_all, rows_int;
+  std::vector<ColJob> ycols_all, ycols_int, zcols;
+  std::vector<CopyBlk> blocks;
+  std::vector<XTile> tiles;
+
+  int64_t field_total = 0;  // elements per field buffer
+  int64_t spec_total = 0;   // complex elements per spectrum slot
+  int smem_fx = 0, smem_y = 0, smem_z = 0, smem_zonly = 0, smem_ix = 0;
+
+  // device memory
+  std::vector<void*> allocs;
+  BoxDev* d_boxes = nullptr;
+  ShapeDev* d_shapes = nullptr;
+  RowJob *d_rows_all = nullptr, *d_rows_int = nullptr;
+  ColJob *d_ycols_all = nullptr, *d_ycols_int = nullptr, *d_zcols = nullptr;
+  CopyBlk* d_blocks = nullptr;
+  XTile* d_tiles = nullptr;
+  void *d_rpool = nullptr, *d_cpool = nullptr, *d_coef = nullptr;
+  void* d_ws = nullptr;
+  size_t plan_bytes = 0;
+
+  std::string last_error = "no error";
+  cudaStream_t last_stream = nullptr;
+  int64_t last_launches = 0;
+
+  DevPlan dev() const {
+    DevPlan P;
+    P.boxes = d_boxes;
+    P.shapes = d_shapes;
+    P.rpool = d_rpool;
+    P.cpool = d_cpool;
+    P.coef = d_coef;
+    P.c = desc.c;
+    P.eps0 = desc.eps0;
+    P.dt = desc.dt;
+    return P;
+  }
+
+  ~psatd_plan() {
+    cudaDeviceSynchronize();
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+namespace {
+
+psatd_status fail(psatd_plan* p, psatd_status st, const std::string& m) {
+  if (p)
+    p->last_error = m;
+  else
+    g_thread_error = m;
+  return st;
+}
+
+#define CK(plan, expr)                                                                          \
+  do {                                                                                          \
+    cudaError_t _e = (expr);                                                                    \
+    if (_e != cudaSuccess) {                                                                    \
+      psatd_status _s = _e == cudaErrorMemoryAllocation ? PSATD_ERR_OUT_OF_MEMORY : PSATD_ERR_CUDA; \
+      return fail(plan, _s, fmt("%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__)); \
+    }                                                                                           \
+  } while (0)
+
+template <typename V>
+cudaError_t upload(psatd_plan* p, const std::vector<V>& h, V** d) {
+  *d = nullptr;
+  if (h.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc((void**)d, h.size() * sizeof(V));
+  if (e != cudaSuccess) return e;
+  p->allocs.push_back(*d);
+  p->plan_bytes += h.size() * sizeof(V);
+  return cudaMemcpy(*d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice);
+}
+
+cudaError_t dalloc(psatd_plan* p, size_t bytes, void** d) {
+  *d = nullptr;
+  if (!bytes) return cudaSuccess;
+  cudaError_t e = cudaMalloc(d, bytes);
+  if (e != cudaSuccess) return e;
+  p->allocs.push_back(*d);
+  p->plan_bytes += bytes;
+  return cudaSuccess;
+}
+
+std::vector<double> stencil_alpha(int p) {
+  // alpha_l = prod_{j != l} (2j-1)^2 / ((2j-1)^2 - (2l-1)^2), l = 1..p/2
+  const int q = p / 2;
+  std::vector<double> a(q);
+  for (int l = 1; l <= q; ++l) {
+    double v = 1.0;
+    const double xl = (double)(2 * l - 1) * (2 * l - 1);
+    for (int j = 1; j <= q; ++j) {
+      if (j == l) continue;
+      const double xj = (double)(2 * j - 1) * (2 * j - 1);
+      v *= xj / (xj - xl);
+    }
+    a[l - 1] = v;
+  }
+  return a;
+}
+
+psatd_status build(psatd_plan* P, cudaStream_t st) {
+  const psatd_plan_desc& d = P->desc;
+  const int FIN = fields_in(P->form);
+  // ---- shapes and table pool layout
+  std::map<std::tuple<int, int, int, int>, int> shape_of;
+  std::map<int, int64_t> tw_of;  // length -> complex pool offset
+  int64_t rtot = 0, ctot = 0, qtot = 0;
+  auto tw_offset = [&](int n) -> int64_t {
+    auto it = tw_of.find(n);
+    if (it != tw_of.end()) return it->second;
+    const int64_t o = ctot;
+    ctot += align_up(n, 2);
+    tw_of[n] = o;
+    return o;
+  };
+  for (const psatd_box& b : P->boxes) {
+    auto key = std::make_tuple(b.n[0], b.n[1], b.n[2], b.order_p);
+    if (shape_of.count(key)) continue;
+    ShapeDev s{};
+    for (int a = 0; a < 3; ++a) s.n[a] = b.n[a];
+    s.L = b.n[0] / 2;
+    s.hx = s.L + 1;
+    s.p = b.order_p;
+    if (!radix_plan(s.L, s.ax) || !radix_plan(b.n[1], s.ay) || !radix_plan(b.n[2], s.az))
+      return fail(nullptr, PSATD_ERR_UNSUPPORTED_SIZE, "no radix schedule");
+    s.ax.tw = tw_offset(s.L);
+    s.ay.tw = tw_offset(b.n[1]);
+    s.az.tw = tw_offset(b.n[2]);
+    s.post = ctot;
+    ctot += align_up(s.hx, 2);
+    s.phx = ctot;
+    ctot += align_up(s.hx, 2);
+    s.phy = ctot;
+    ctot += align_up(b.n[1], 2);
+    s.phz = ctot;
+    ctot += align_up(b.n[2], 2);
+    s.kx = rtot;
+    rtot += align_up(s.hx, 4);
+    s.ky = rtot;
+    rtot += align_up(b.n[1], 4);
+    s.kz = rtot;
+    rtot += align_up(b.n[2], 4);
+    s.coef = qtot;
+    qtot += (int64_t)s.hx * (b.n[1] / 2 + 1) * (b.n[2] / 2 + 1);
+    shape_of[key] = (int)P->hshapes.size();
+    P->hshapes.push_back(s);
+  }
+  // ---- boxes
+  int64_t foff = 0, soff = 0;
+  for (const psatd_box& b : P->boxes) {
+    BoxDev x{};
+    for (int a = 0; a < 3; ++a) {
+      x.n[a] = b.n[a];
+      x.ng_lo[a] = b.ng_lo[a];
+      x.ng_hi[a] = b.ng_hi[a];
+    }
+    x.shape = shape_of[std::make_tuple(b.n[0], b.n[1], b.n[2], b.order_p)];
+    x.foff = foff;
+    x.soff = soff;
+    foff += align_up((int64_t)b.n[0] * b.n[1] * b.n[2], 64);
+    soff += align_up((int64_t)(b.n[0] / 2 + 1) * b.n[1] * b.n[2], 32);
+    P->hboxes.push_back(x);
+  }
+  P->field_total = foff;
+  P->spec_total = soff;
+  // ---- work lists
+  const int csz = (int)P->csize;
+  const int zbudget = 100 * 1024;
+  for (int bi = 0; bi < (int)P->boxes.size(); ++bi) {
+    const psatd_box& b = P->boxes[bi];
+    const int n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
+    const int L = n0 / 2, hx = L + 1;
+    const int rows = n1 * n2;
+    const int nr = std::max(1, std::min(rows, kMaxPoints / L));
+    for (int r = 0; r < rows; r += nr) P->rows_all.push_back({bi, r, std::min(nr, rows - r), 0});
+    for (int z = b.ng_lo[2]; z < n2 - b.ng_hi[2]; ++z) {
+      const int y0 = b.ng_lo[1], y1 = n1 - b.ng_hi[1];
+      for (int y = y0; y < y1; y += nr) P->rows_int.push_back({bi, z * n1 + y, std::min(nr, y1 - y), 0});
+    }
+    P->smem_fx = std::max(P->smem_fx, nr * L * csz);
+    P->smem_ix = std::max(P->smem_ix, nr * (hx + L) * csz);
+    int ny = std::max(1, kMaxPoints / n1);
+    if (ny >= 8) ny = ny / 8 * 8;
+    ny = std::min(ny, hx);
+    for (int z = 0; z < n2; ++z) {
+      const bool inner = z >= b.ng_lo[2] && z < n2 - b.ng_hi[2];
+      for (int m = 0; m < hx; m += ny) {
+        ColJob j{bi, z, m, std::min(ny, hx - m)};
+        P->ycols_all.push_back(j);
+        if (inner) P->ycols_int.push_back(j);
+      }
+    }
+    P->smem_y = std::max(P->smem_y, n1 * ny * csz);
+    int nz = std::max(1, zbudget / (n2 * FIN * csz));
+    if (nz >= 4) nz = nz / 4 * 4;
+    nz = std::min(nz, hx);
+    for (int y = 0; y < n1; ++y)
+      for (int m = 0; m < hx; m += nz) P->zcols.push_back({bi, y, m, std::min(nz, hx - m)});
+    P->smem_z = std::max(P->smem_z, n2 * FIN * nz * csz);
+    P->smem_zonly = std::max(P->smem_zonly, n2 * nz * csz);
+  }
+  // ---- exchange protocol
+  P->blocks = build_blocks(&d);
+  for (int i = 0; i < (int)P->blocks.size(); ++i) {
+    const CopyBlk& c = P->blocks[i];
+    const int rows = c.ext[1] * c.ext[2];
+    const int per = std::max(1, 4096 / std::max(1, c.ext[0]));
+    for (int r = 0; r < rows; r += per) P->tiles.push_back({i, r, std::min(per, rows - r), 0});
+  }
+  // ---- device memory
+  CK(P, upload(P, P->hboxes, &P->d_boxes));
+  CK(P, upload(P, P->hshapes, &P->d_shapes));
+  CK(P, upload(P, P->rows_all, &P->d_rows_all));
+  CK(P, upload(P, P->rows_int, &P->d_rows_int));
+  CK(P, upload(P, P->ycols_all, &P->d_ycols_all));
+  CK(P, upload(P, P->ycols_int, &P->d_ycols_int));
+  CK(P, upload(P, P->zcols, &P->d_zcols));
+  CK(P, upload(P, P->blocks, &P->d_blocks));
+  CK(P, upload(P, P->tiles, &P->d_tiles));
+  CK(P, dalloc(P, (size_t)rtot * P->rsize, &P->d_rpool));
+  CK(P, dalloc(P, (size_t)ctot * P->csize, &P->d_cpool));
+  CK(P, dalloc(P, (size_t)qtot * 4 * P->rsize, &P->d_coef));
+  CK(P, dalloc(P, (size_t)FIN * P->spec_total * P->csize, &P->d_ws));
+  // ---- FP64 tables
+  double *r64 = nullptr, *alpha = nullptr;
+  double2* c64 = nullptr;
+  Coef4<double>* q64 = nullptr;
+  std::vector<void*> tmp;
+  auto tmp_alloc = [&](size_t bytes, void** ptr) -> cudaError_t {
+    cudaError_t e = cudaMalloc(ptr, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) tmp.push_back(*ptr);
+    return e;
+  };
+  auto free_tmp = [&]() {
+    cudaStreamSynchronize(st);
+    for (void* t : tmp) cudaFree(t);
+    tmp.clear();
+  };
+  cudaError_t e = cudaSuccess;
+  if (P->prec == 32) {
+    e = tmp_alloc((size_t)rtot * 8, (void**)&r64);
+    if (e == cudaSuccess) e = tmp_alloc((size_t)ctot * 16, (void**)&c64);
+    if (e == cudaSuccess) e = tmp_alloc((size_t)qtot * 32, (void**)&q64);
+  } else {
+    r64 = (double*)P->d_rpool;
+    c64 = (double2*)P->d_cpool;
+    q64 = (Coef4<double>*)P->d_coef;
+  }
+  // stencil weights of every order used
+  std::map<int, int64_t> alpha_of;
+  std::vector<double> halpha;
+  for (const ShapeDev& s : P->hshapes) {
+    if (s.p == 0 || alpha_of.count(s.p)) continue;
+    alpha_of[s.p] = (int64_t)halpha.size();
+    auto a = stencil_alpha(s.p);
+    halpha.insert(halpha.end(), a.begin(), a.end());
+  }
+  if (e == cudaSuccess) e = tmp_alloc(halpha.size() * 8, (void**)&alpha);
+  if (e == cudaSuccess && !halpha.empty())
+    e = cudaMemcpy(alpha, halpha.data(), halpha.size() * 8, cudaMemcpyHostToDevice);
+  for (auto& kv : tw_of)
+    if (e == cudaSuccess) e = gen_twiddles(c64 + kv.second, kv.first, st);
+  for (const ShapeDev& s : P->hshapes) {
+    if (e != cudaSuccess) break;
+    const int q = s.p / 2;
+    const double* al = q ? alpha + alpha_of[s.p] : alpha;
+    e = gen_post(c64 + s.post, s.n[0], st);
+    if (e == cudaSuccess) e = gen_axis(r64 + s.kx, c64 + s.phx, s.hx, s.n[0], d.dx[0], q, al, st);
+    if (e == cudaSuccess) e = gen_axis(r64 + s.ky, c64 + s.phy, s.n[1], s.n[1], d.dx[1], q, al, st);
+    if (e == cudaSuccess) e = gen_axis(r64 + s.kz, c64 + s.phz, s.n[2], s.n[2], d.dx[2], q, al, st);
+    if (e == cudaSuccess)
+      e = gen_coef(q64 + s.coef, s.hx, s.n[1], s.n[2], r64 + s.kx, r64 + s.ky, r64 + s.kz, d.c, d.dt, st);
+  }
+  if (e == cudaSuccess && P->prec == 32)
+    e = convert_pools(r64, (float*)P->d_rpool, rtot, c64, (float2*)P->d_cpool, ctot, q64,
+                      (Coef4<float>*)P->d_coef, qtot, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  free_tmp();
+  CK(P, e);
+  const int smem = std::max({P->smem_fx, P->smem_y, P->smem_z, P->smem_zonly, P->smem_ix});
+  if (smem > 227 * 1024) return fail(P, PSATD_ERR_UNSUPPORTED_SIZE, fmt("needs %d B shared memory", smem));
+  CK(P, configure_kernels(P->prec, smem));
+  return PSATD_OK;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+psatd_status psatd_plan_validate(const psatd_plan_desc* desc, char* msg, size_t msg_len) {
+  try {
+    Err e = validate(desc);
+    set_msg(msg, msg_len, e.st == PSATD_OK ? "ok" : e.msg);
+    if (e.st != PSATD_OK) g_thread_error = e.msg;
+    return e.st;
+  } catch (...) {
+    return PSATD_ERR_INVALID_ARG;
+  }
+}
+
+psatd_status psatd_exchange_blocks(const psatd_plan_desc* desc, psatd_copy_block* out, int64_t cap,
+                                   int64_t* count) {
+  try {
+    if (!count || cap < 0 || (cap > 0 && !out)) return fail(nullptr, PSATD_ERR_INVALID_ARG, "bad output arguments");
+    Err e = validate(desc);
+    if (e.st != PSATD_OK) return fail(nullptr, e.st, e.msg);
+    std::vector<CopyBlk> b = build_blocks(desc);
+    *count = (int64_t)b.size();
+    for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)b.size()); ++i) {
+      psatd_copy_block& o = out[i];
+      o.dst_box = b[i].dst_box;
+      o.src_box = b[i].src_box;
+      for (int a = 0; a < 3; ++a) {
+        o.dst_lo[a] = b[i].dst_lo[a];
+        o.src_lo[a] = b[i].src_lo[a];
+        o.ext[a] = b[i].ext[a];
+      }
+    }
+    return PSATD_OK;
+  } catch (...) {
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "internal error");
+  }
+}
+
+psatd_status psatd_plan_create(const psatd_plan_desc* desc, void* stream, psatd_plan** out) {
+  if (!out) return fail(nullptr, PSATD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  psatd_plan* P = nullptr;
+  try {
+    Err v = validate(desc);
+    if (v.st != PSATD_OK) return fail(nullptr, v.st, v.msg);
+    P = new psatd_plan();
+    P->desc = *desc;
+    P->boxes.assign(desc->boxes, desc->boxes + desc->num_boxes);
+    P->desc.boxes = P->boxes.data();
+    P->prec = desc->precision;
+    P->csize = P->prec == 32 ? 8 : 16;
+    P->rsize = P->prec == 32 ? 4 : 8;
+    P->form = (desc->flags & PSATD_VACUUM) ? kVacuum : (desc->flags & PSATD_RHO_CONTINUITY) ? kRhoForm : kJForm;
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce != cudaSuccess) {
+      std::string m = fmt("no CUDA device: %s", cudaGetErrorString(ce));
+      delete P;
+      return fail(nullptr, PSATD_ERR_CUDA, m);
+    }
+    psatd_status s = build(P, (cudaStream_t)stream);
+    if (s != PSATD_OK) {
+      std::string m = P->last_error != "no error" ? P->last_error : g_thread_error;
+      delete P;
+      return fail(nullptr, s, m);
+    }
+    P->last_stream = (cudaStream_t)stream;
+    *out = P;
+    return PSATD_OK;
+  } catch (const std::bad_alloc&) {
+    delete P;
+    return fail(nullptr, PSATD_ERR_OUT_OF_MEMORY, "host allocation failed");
+  } catch (...) {
+    delete P;
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "internal error");
+  }
+}
+
+psatd_status psatd_plan_destroy(psatd_plan* plan) {
+  delete plan;
+  return PSATD_OK;
+}
+
+psatd_status psatd_plan_layout(const psatd_plan* p, int32_t box, int64_t* off, int64_t* elems) {
+  if (!p || !off || !elems) return PSATD_ERR_INVALID_ARG;
+  if (box < 0 || box >= (int32_t)p->hboxes.size()) return PSATD_ERR_INVALID_ARG;
+  const BoxDev& b = p->hboxes[box];
+  *off = b.foff;
+  *elems = (int64_t)b.n[0] * b.n[1] * b.n[2];
+  return PSATD_OK;
+}
+
+psatd_status psatd_plan_spectrum_layout(const psatd_plan* p, int32_t box, int64_t* off,
+                                        int64_t* elems) {
+  if (!p || !off || !elems) return PSATD_ERR_INVALID_ARG;
+  if (box < 0 || box >= (int32_t)p->hboxes.size()) return PSATD_ERR_INVALID_ARG;
+  const BoxDev& b = p->hboxes[box];
+  *off = b.soff;
+  *elems = (int64_t)(b.n[0] / 2 + 1) * b.n[1] * b.n[2];
+  return PSATD_OK;
+}
+
+psatd_status psatd_plan_memory(const psatd_plan* p, size_t* field_bytes, size_t* workspace_bytes) {
+  if (!p) return PSATD_ERR_INVALID_ARG;
+  if (field_bytes) *field_bytes = (size_t)p->field_total * p->rsize;
+  if (workspace_bytes) *workspace_bytes = p->plan_bytes;
+  return PSATD_OK;
+}
+
+static psatd_status gather_fields(psatd_plan* P, const psatd_fields* f, const psatd_sources* s,
+                                  bool with_sources_for_form, FieldPtrs* fp, int* nf) {
+  if (!f) return fail(P, PSATD_ERR_INVALID_ARG, "fields is NULL");
+  std::memset(fp, 0, sizeof *fp);
+  for (int a = 0; a < 3; ++a) {
+    fp->p[a] = f->E[a];
+    fp->p[3 + a] = f->B[a];
+  }
+  int n = 6;
+  if (with_sources_for_form) {
+    if (P->form == kJForm) {
+      if (!s) return fail(P, PSATD_ERR_INVALID_ARG, "sources required (plan is not PSATD_VACUUM)");
+      for (int a = 0; a < 3; ++a) fp->p[6 + a] = const_cast<void*>(s->J[a]);
+      n = 9;
+    } else if (P->form == kRhoForm) {
+      if (!s) return fail(P, PSATD_ERR_INVALID_ARG, "sources required (plan is not PSATD_VACUUM)");
+      fp->p[6] = s->rho;
+      for (int a = 0; a < 3; ++a) fp->p[7 + a] = const_cast<void*>(s->J[a]);
+      n = 10;
+    }
+  } else if (s) {
+    for (int a = 0; a < 3; ++a) fp->p[6 + a] = const_cast<void*>(s->J[a]);
+    n = 9;
+    if (s->rho) fp->p[n++] = s->rho;
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!fp->p[i]) return fail(P, PSATD_ERR_INVALID_ARG, fmt("field slot %d is NULL", i));
+    if (!aligned16(fp->p[i])) return fail(P, PSATD_ERR_INVALID_ARG, fmt("field slot %d not 16-byte aligned", i));
+  }
+  *nf = n;
+  return PSATD_OK;
+}
+
+psatd_status psatd_guard_exchange(psatd_plan* P, const psatd_fields* f, const psatd_sources* s,
+                                  void* stream) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  try {
+    FieldPtrs fp;
+    int nf = 0;
+    psatd_status r = gather_fields(P, f, s, false, &fp, &nf);
+    if (r != PSATD_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    P->last_stream = st;
+    CK(P, launch_exchange(P->prec, P->dev(), fp, nf, P->d_blocks, P->d_tiles, (int64_t)P->tiles.size(), st));
+    return PSATD_OK;
+  } catch (...) {
+    return fail(P, PSATD_ERR_INVALID_ARG, "internal error");
+  }
+}
+
+psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_sources* s, int32_t nsteps,
+                        void* stream) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  if (nsteps < 0) return fail(P, PSATD_ERR_INVALID_ARG, "nsteps < 0");
+  try {
+    FieldPtrs fp;
+    int nf = 0;
+    psatd_status r = gather_fields(P, f, s, true, &fp, &nf);
+    if (r != PSATD_OK) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    P->last_stream = st;
+    const DevPlan D = P->dev();
+    const int FIN = fields_in(P->form), FOUT = fields_out(P->form);
+    const int64_t S = P->spec_total;
+    int64_t launches = 0;
+    for (int step = 0; step < nsteps; ++step) {
+      CK(P, launch_fwd_x(P->prec, D, fp, FIN, P->d_ws, S, P->d_rows_all, (int64_t)P->rows_all.size(), P->smem_fx, st));
+      CK(P, launch_col(P->prec, -1, 1, D, P->d_ws, S, FIN, P->d_ycols_all, (int64_t)P->ycols_all.size(), P->smem_y, st));
+      CK(P, launch_z_update(P->prec, P->form, D, P->d_ws, S, P->d_zcols, (int64_t)P->zcols.size(), P->smem_z, st));
+      CK(P, launch_col(P->prec, 1, 1, D, P->d_ws, S, FOUT, P->d_ycols_int, (int64_t)P->ycols_int.size(), P->smem_y, st));
+      CK(P, launch_inv_x(P->prec, D, fp, FOUT, P->d_ws, S, P->d_rows_int, (int64_t)P->rows_int.size(), P->smem_ix, 1, st));
+      launches += 5;
+      if (!P->tiles.empty()) {
+        CK(P, launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_tiles, (int64_t)P->tiles.size(), st));
+        ++launches;
+      }
+    }
+    P->last_launches = launches;
+    return PSATD_OK;
+  } catch (...) {
+    return fail(P, PSATD_ERR_INVALID_ARG, "internal error");
+  }
+}
+
+psatd_status psatd_forward_fft(psatd_plan* P, const void* field, void* spectrum, void* stream) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  if (!field || !spectrum || !aligned16(field) || !aligned16(spectrum))
+    return fail(P, PSATD_ERR_INVALID_ARG, "field/spectrum NULL or not 16-byte aligned");
+  FieldPtrs fp{};
+  fp.p[0] = const_cast<void*>(field);
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const DevPlan D = P->dev();
+  const int64_t S = P->spec_total;
+  CK(P, launch_fwd_x(P->prec, D, fp, 1, spectrum, S, P->d_rows_all, (int64_t)P->rows_all.size(), P->smem_fx, st));
+  CK(P, launch_col(P->prec, -1, 1, D, spectrum, S, 1, P->d_ycols_all, (int64_t)P->ycols_all.size(), P->smem_y, st));
+  CK(P, launch_col(P->prec, -1, 2, D, spectrum, S, 1, P->d_zcols, (int64_t)P->zcols.size(), P->smem_zonly, st));
+  P->last_launches = 3;
+  return PSATD_OK;
+}
+
+psatd_status psatd_inverse_fft(psatd_plan* P, void* spectrum, void* field, void* stream) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  if (!field || !spectrum || !aligned16(field) || !aligned16(spectrum))
+    return fail(P, PSATD_ERR_INVALID_ARG, "field/spectrum NULL or not 16-byte aligned");
+  FieldPtrs fp{};
+  fp.p[0] = field;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const DevPlan D = P->dev();
+  const int64_t S = P->spec_total;
+  CK(P, launch_col(P->prec, 1, 2, D, spectrum, S, 1, P->d_zcols, (int64_t)P->zcols.size(), P->smem_zonly, st));
+  CK(P, launch_col(P->prec, 1, 1, D, spectrum, S, 1, P->d_ycols_all, (int64_t)P->ycols_all.size(), P->smem_y, st));
+  CK(P, launch_inv_x(P->prec, D, fp, 1, spectrum, S, P->d_rows_all, (int64_t)P->rows_all.size(), P->smem_ix, 0, st));
+  P->last_launches = 3;
+  return PSATD_OK;
+}
+
+psatd_status psatd_sync_status(psatd_plan* P) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(P->last_stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(P, PSATD_ERR_CUDA, fmt("device error: %s", cudaGetErrorString(e)));
+  return PSATD_OK;
+}
+
+const char* psatd_status_string(psatd_status s) {
+  switch (s) {
+    case PSATD_OK: return "ok";
+    case PSATD_ERR_INVALID_ARG: return "invalid argument";
+    case PSATD_ERR_UNSUPPORTED_SIZE: return "unsupported box size";
+    case PSATD_ERR_UNSUPPORTED_ORDER: return "unsupported stencil order";
+    case PSATD_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case PSATD_ERR_CUDA: return "CUDA error";
+    case PSATD_ERR_TIMEOUT: return "device-side wait timed out";
+    case PSATD_ERR_STATE: return "invalid plan state";
+  }
+  return "unknown status";
+}
+
+const char* psatd_last_error(const psatd_plan* p) {
+  return p ? p->last_error.c_str() : g_thread_error.c_str();
+}
+
+int64_t psatd_last_launch_count(const psatd_plan* p) { return p ? p->last_launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal structures shared by the host plan (plan.cpp) and the CUDA kernels.
+// Everything here is plain old data copied to the device as-is.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/psatd.h"
+
+namespace psatd {
+
+constexpr int kMaxPass = 16;       // radix passes of one axis (2^10 needs <= 4 with radix 8)
+constexpr int kThreads = 256;      // threads per CTA of every FFT kernel
+constexpr int kPointsPerThread = 16;
+constexpr int kMaxPoints = kThreads * kPointsPerThread;  // points of one FFT chunk in smem
+
+// Equation form of the k-space update (slot layout of the fields):
+//   kVacuum: E 0-2, B 3-5                      (6 in, 6 out)
+//   kJForm : E 0-2, B 3-5, J 6-8               (9 in, 6 out)
+//   kRhoForm: E 0-2, B 3-5, rho 6, J 7-9       (10 in, 7 out)
+enum Form { kVacuum = 0, kJForm = 1, kRhoForm = 2 };
+
+constexpr int fields_in(int form) { return form == kVacuum ? 6 : form == kJForm ? 9 : 10; }
+constexpr int fields_out(int form) { return form == kRhoForm ? 7 : 6; }
+
+// Radix schedule of one complex FFT length.
+struct AxisPlan {
+  int32_t n;
+  int32_t npass;
+  int64_t tw;                     // offset of the n-entry twiddle table (complex pool)
+  uint8_t radix[kMaxPass];
+};
+
+// Tables of one box shape (n0, n1, n2, p); offsets index the typed pools.
+struct ShapeDev {
+  int32_t n[3];
+  int32_t L;                      // n0/2: length of the packed complex FFT along x
+  int32_t hx;                     // n0/2 + 1: half-spectrum length along x
+  int32_t p;
+  AxisPlan ax, ay, az;            // x: length L; y: n1; z: n2
+  int64_t post;                   // hx entries exp(-2 pi i k / n0)         (complex pool)
+  int64_t kx, ky, kz;             // modified wavenumbers, hx / n1 / n2      (real pool)
+  int64_t phx, phy, phz;          // exp(i k h / 2), hx / n1 / n2            (complex pool)
+  int64_t coef;                   // hx*(n1/2+1)*(n2/2+1) coefficient quads (coef pool)
+};
+
+struct BoxDev {
+  int32_t n[3];
+  int32_t ng_lo[3];
+  int32_t ng_hi[3];
+  int32_t shape;
+  int64_t foff;                   // element offset in every field buffer
+  int64_t soff;                   // complex-element offset in every spectrum slot
+};
+
+// rows r0 .. r0+nr-1 of one box, row r = y + n1*z (x-axis passes)
+struct RowJob {
+  int32_t box, r0, nr, pad;
+};
+
+// columns m0 .. m0+nm-1 of one plane (y-axis passes: plane = z; z-axis: plane = y)
+struct ColJob {
+  int32_t box, plane, m0, nm;
+};
+
+struct CopyBlk {
+  int32_t dst_box, src_box;
+  int32_t dst_lo[3], src_lo[3], ext[3];
+};
+
+// rows [row0, row0+nrows) of one copy block, row = ry + ext1*rz
+struct XTile {
+  int32_t blk, row0, nrows, pad;
+};
+
+// Up to 10 field slots (see Form).
+struct FieldPtrs {
+  void* p[10];
+};
+
+template <typename T>
+struct alignas(4 * sizeof(T)) Coef4 {
+  T c;    // cos(theta)
+  T s;    // sin(theta)/(c K)
+  T x1;   // (1 - cos theta)/K^2
+  T x3;   // (sin(theta)/(c K) - dt)/K^2
+};
+
+// Device view of a plan, passed by value to every kernel.
+struct DevPlan {
+  const BoxDev* boxes;
+  const ShapeDev* shapes;
+  const void* rpool;              // T[]
+  const void* cpool;              // T2[]
+  const void* coef;               // Coef4<T>[]
+  double c, eps0, dt;
+};
+
+// ---- kernel launchers (fft_kernels.cu, exchange.cu) ----------------------
+
+// Forward R2C along x of `nf` field slots into spectrum slots (stride sstride).
+cudaError_t launch_fwd_x(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                         int64_t sstride, const RowJob* jobs, int64_t njobs, int smem,
+                         cudaStream_t st);
+// Complex FFT along y (axis 1) or z (axis 2), in place on spectrum slots.
+cudaError_t launch_col(int prec, int dir, int axis, const DevPlan& P, void* spec,
+                       int64_t sstride, int nf, const ColJob* jobs, int64_t njobs, int smem,
+                       cudaStream_t st);
+// z forward FFT + k-space update + z inverse FFT, all slots of `form`.
+cudaError_t launch_z_update(int prec, int form, const DevPlan& P, void* spec, int64_t sstride,
+                            const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+// C2R inverse along x with 1/(n0 n1 n2) into field slots; interior_only skips guards.
+cudaError_t launch_inv_x(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                         int64_t sstride, const RowJob* jobs, int64_t njobs, int smem,
+                         int interior_only, cudaStream_t st);
+// Guard exchange of `nf` field slots.
+cudaError_t launch_exchange(int prec, const DevPlan& P, const FieldPtrs& f, int nf,
+                            const CopyBlk* blocks, const XTile* tiles, int64_t ntiles,
+                            cudaStream_t st);
+// Maximum dynamic shared memory opt-in for all kernels of a precision.
+cudaError_t configure_kernels(int prec, int smem_bytes);
+
+// ---- FP64 table generators (tables.cu) ------------------------------------
+cudaError_t gen_twiddles(double2* out, int n, cudaStream_t st);
+cudaError_t gen_post(double2* out, int n0, cudaStream_t st);
+cudaError_t gen_axis(double* K, double2* ph, int count, int n, double h, int q,
+                     const double* alpha_dev, cudaStream_t st);
+cudaError_t gen_coef(Coef4<double>* out, int hx, int n1, int n2, const double* kx,
+                     const double* ky, const double* kz, double c, double dt, cudaStream_t st);
+cudaError_t convert_pools(const double* r64, float* r32, int64_t nr, const double2* c64,
+                          float2* c32, int64_t nc, const Coef4<double>* q64, Coef4<float>* q32,
+                          int64_t nq, cudaStream_t st);
+
+}  // namespace psatd

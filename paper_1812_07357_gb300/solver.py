@@ -1,0 +1,154 @@
+"""Convenience layer over the C ABI: builds a plan description from a box
+layout, and moves per-box numpy arrays in and out of the plan's contiguous
+device buffers.  PyTorch provides device memory and the current stream;
+all arithmetic of the push runs in libpsatd.so.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import _abi as A
+
+_DECOMP = {"global": A.PSATD_DECOMP_GLOBAL, "local": A.PSATD_DECOMP_LOCAL,
+           "hybrid": A.PSATD_DECOMP_HYBRID, "independent": A.PSATD_DECOMP_INDEPENDENT}
+COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
+
+
+def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no_graph=False):
+    """psatd_plan_desc for an ``inputs.Layout``; the returned object keeps the
+    box array alive (attribute ``_boxes``)."""
+    nb = len(layout.boxes)
+    arr = (A.psatd_box * nb)()
+    for i, b in enumerate(layout.boxes):
+        arr[i].n[:] = list(b.n)
+        arr[i].ng_lo[:] = list(b.ng_lo)
+        arr[i].ng_hi[:] = list(b.ng_hi)
+        arr[i].origin[:] = list(b.origin)
+        arr[i].order_p = int(b.p)
+    d = A.psatd_plan_desc()
+    d.global_n[:] = list(layout.global_n)
+    d.periodic[:] = list(layout.periodic)
+    d.dx[:] = list(h)
+    d.dt, d.c, d.eps0 = float(dt), float(c), float(eps0)
+    d.precision = int(precision)
+    d.decomp = _DECOMP[layout.kind]
+    d.num_boxes = nb
+    d.boxes = ctypes.cast(arr, ctypes.POINTER(A.psatd_box))
+    flags = {"vacuum": A.PSATD_VACUUM, "J": 0, "rho": A.PSATD_RHO_CONTINUITY}[sources]
+    if no_graph:
+        flags |= A.PSATD_NO_GRAPH
+    d.flags = flags
+    d._boxes = arr
+    return d
+
+
+class Plan:
+    """A PSATD plan on the current CUDA device."""
+
+    def __init__(self, layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum",
+                 stream=None, no_graph=False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        self.torch = torch
+        self.layout = layout
+        self.precision = precision
+        self.sources = sources
+        self.dtype = torch.float32 if precision == 32 else torch.float64
+        self.cdtype = torch.complex64 if precision == 32 else torch.complex128
+        self.np_dtype = np.float32 if precision == 32 else np.float64
+        self.desc = make_desc(layout, h, dt, c, eps0, precision, sources, no_graph)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.handle = A.psatd_plan_create(self.desc, self.stream.cuda_stream)
+        self.offsets = [A.psatd_plan_layout(self.handle, i) for i in range(len(layout.boxes))]
+        self.spec_offsets = [A.psatd_plan_spectrum_layout(self.handle, i)
+                             for i in range(len(layout.boxes))]
+        fb, wb = A.psatd_plan_memory(self.handle)
+        self.field_elems = fb // (4 if precision == 32 else 8)
+        self.workspace_bytes = wb
+        last = self.spec_offsets[-1]
+        self.spec_elems = last[0] + last[1] + 64
+
+    def close(self):
+        if getattr(self, "handle", None):
+            A.psatd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- buffers -------------------------------------------------------------
+    def empty(self):
+        return self.torch.zeros(self.field_elems, dtype=self.dtype, device="cuda")
+
+    def pack(self, arrays: List[np.ndarray]):
+        host = np.zeros(self.field_elems, dtype=self.np_dtype)
+        for (off, n), a in zip(self.offsets, arrays):
+            host[off:off + n] = np.asarray(a, dtype=self.np_dtype).ravel()
+        return self.torch.from_numpy(host).to("cuda")
+
+    def unpack(self, t) -> List[np.ndarray]:
+        host = t.detach().cpu().numpy().astype(np.float64)
+        return [host[off:off + n].reshape(b.shape).copy()
+                for (off, n), b in zip(self.offsets, self.layout.boxes)]
+
+    def pack_fields(self, d: Dict[str, List[np.ndarray]]):
+        return {k: self.pack(v) for k, v in d.items()}
+
+    def unpack_fields(self, d):
+        return {k: self.unpack(v) for k, v in d.items()}
+
+    # -- ABI structs ---------------------------------------------------------
+    @staticmethod
+    def fields_struct(f) -> A.psatd_fields:
+        s = A.psatd_fields()
+        s.E[:] = [f["Ex"].data_ptr(), f["Ey"].data_ptr(), f["Ez"].data_ptr()]
+        s.B[:] = [f["Bx"].data_ptr(), f["By"].data_ptr(), f["Bz"].data_ptr()]
+        return s
+
+    @staticmethod
+    def sources_struct(s) -> Optional[A.psatd_sources]:
+        if not s:
+            return None
+        r = A.psatd_sources()
+        r.J[:] = [s["Jx"].data_ptr(), s["Jy"].data_ptr(), s["Jz"].data_ptr()]
+        r.rho = s["rho"].data_ptr() if s.get("rho") is not None else None
+        return r
+
+    # -- entry points ----------------------------------------------------------
+    def push(self, fields, sources=None, nsteps=1):
+        A.psatd_push(self.handle, self.fields_struct(fields), self.sources_struct(sources),
+                     int(nsteps), self.stream.cuda_stream)
+
+    def guard_exchange(self, fields, sources=None):
+        A.psatd_guard_exchange(self.handle, self.fields_struct(fields),
+                               self.sources_struct(sources), self.stream.cuda_stream)
+
+    def forward_fft(self, field):
+        spec = self.torch.zeros(self.spec_elems, dtype=self.cdtype, device="cuda")
+        A.psatd_forward_fft(self.handle, field.data_ptr(), spec.data_ptr(), self.stream.cuda_stream)
+        return spec
+
+    def inverse_fft(self, spec):
+        out = self.empty()
+        A.psatd_inverse_fft(self.handle, spec.data_ptr(), out.data_ptr(), self.stream.cuda_stream)
+        return out
+
+    def unpack_spectrum(self, spec) -> List[np.ndarray]:
+        host = spec.detach().cpu().numpy().astype(np.complex128)
+        out = []
+        for (off, n), b in zip(self.spec_offsets, self.layout.boxes):
+            out.append(host[off:off + n].reshape(b.n[2], b.n[1], b.n[0] // 2 + 1).copy())
+        return out
+
+    def sync(self):
+        A.psatd_sync_status(self.handle)
+
+    def last_launch_count(self) -> int:
+        return A.psatd_last_launch_count(self.handle)

@@ -1,0 +1,235 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances: FP64 GPU <= 1e-12 relative L2; FP32 GPU <= 2e-5 relative L2 (the
+FP32 run is compared with the oracle fed the FP32-rounded inputs).  The
+guard exchange is pure data movement and must be bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import psatd_oracle as O
+from paper_1812_07357_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 2e-5}
+FFT_TOL = {64: 1e-13, 32: 2e-6}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_07357_gb300 import build
+    build.build()
+
+
+def Plan(*a, **k):
+    from paper_1812_07357_gb300.solver import Plan as P
+    return P(*a, **k)
+
+
+def rel_l2(a, b):
+    num = sum(float(np.sum(np.abs(x - y) ** 2)) for x, y in zip(a, b))
+    den = sum(float(np.sum(np.abs(y) ** 2)) for y in b)
+    return (num / den) ** 0.5
+
+
+def run_push(lay, fields, src, nsteps, h, dt, prec, form):
+    plan = Plan(lay, h, dt, precision=prec, sources=form)
+    df = plan.pack_fields(fields)
+    ds = plan.pack_fields(src) if form != "vacuum" else None
+    plan.push(df, ds, nsteps)
+    plan.sync()
+    out = plan.unpack_fields(df)
+    if form == "rho":
+        out["rho"] = plan.unpack(ds["rho"])
+    plan.close()
+    return out
+
+
+def check_push(lay, fields, src, nsteps, h, dt, prec, form):
+    if prec == 32:
+        fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
+        src = {k: I.round_to(v, np.float32) for k, v in src.items()}
+    got = run_push(lay, fields, src, nsteps, h, dt, prec, form)
+    ref = O.push(lay, fields, src, nsteps, h, dt, form=form)
+    comps = O.COMPS + (("rho",) if form == "rho" else ())
+    err = O.rel_l2_fields(lay, got, ref, comps)
+    # per-field: E and B separately must also meet the bound
+    eE = O.rel_l2_fields(lay, got, ref, ("Ex", "Ey", "Ez"))
+    eB = O.rel_l2_fields(lay, got, ref, ("Bx", "By", "Bz"))
+    assert err <= TOL[prec], (err, eE, eB)
+    # guards are consistent after the step (exchange ran): whole box compared
+    for k in comps:
+        for g, r in zip(got[k], ref[k]):
+            scale = max(1.0, float(np.abs(r).max()))
+            assert np.abs(g - r).max() <= 50 * TOL[prec] * scale * max(1, nsteps) ** 0.5
+    return err
+
+
+# ---------------------------------------------------------------------------
+# S1 / S3 alone
+# ---------------------------------------------------------------------------
+
+def _fft_layout():
+    boxes = [I.Box(n, (0, 0, 0), (0, 0, 0), (0, 0, 0), 0) for n in
+             [(8, 8, 8), (12, 10, 6), (96, 48, 20), (30, 18, 50), (4, 4, 4), (160, 8, 6),
+              (1024, 4, 4), (6, 512, 4), (4, 6, 512)]]
+    return I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_forward_fft_matches_oracle_fft(prec):
+    lay = _fft_layout()
+    rng = np.random.default_rng(21)
+    arrs = I.round_to([rng.standard_normal(b.shape) for b in lay.boxes], np.float32 if prec == 32 else np.float64)
+    plan = Plan(lay, (1.0,) * 3, 0.5, precision=prec)
+    spec = plan.forward_fft(plan.pack(arrs))
+    plan.sync()
+    got = plan.unpack_spectrum(spec)
+    for b, a, g in zip(lay.boxes, arrs, got):
+        ref = O.fft3(a)[:, :, : b.n[0] // 2 + 1]
+        assert rel_l2([g], [ref]) <= FFT_TOL[prec], b.n
+    plan.close()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_inverse_fft_roundtrip(prec):
+    lay = _fft_layout()
+    rng = np.random.default_rng(22)
+    arrs = [rng.standard_normal(b.shape) for b in lay.boxes]
+    plan = Plan(lay, (1.0,) * 3, 0.5, precision=prec)
+    import torch
+    host = np.zeros(plan.spec_elems, np.complex128)
+    for (off, n), b, a in zip(plan.spec_offsets, lay.boxes, arrs):
+        host[off:off + n] = O.fft3(a)[:, :, : b.n[0] // 2 + 1].ravel()
+    spec = torch.from_numpy(host.astype(np.complex64 if prec == 32 else np.complex128)).cuda()
+    out = plan.unpack(plan.inverse_fft(spec))
+    plan.sync()
+    for b, a, g in zip(lay.boxes, arrs, out):
+        assert rel_l2([g], [a]) <= FFT_TOL[prec], b.n
+    plan.close()
+
+
+# ---------------------------------------------------------------------------
+# guard exchange: bit-exact
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("kind", ["local", "local_open", "hybrid", "independent"])
+def test_guard_exchange_bit_exact(prec, kind):
+    if kind == "local":
+        lay = I.local_layout((48, 32, 32), (3, 2, 2), 4, 8)
+    elif kind == "local_open":
+        lay = I.local_layout((48, 32, 32), (3, 2, 2), 4, 8, periodic=(0, 1, 0))
+    elif kind == "hybrid":
+        lay = I.hybrid_layout((96, 24, 20), (4, 1, 1), 6, 8)
+    else:
+        lay = I.independent_layout(seed=4, nboxes=7, sizes=(16, 20, 24, 30, 32), ngs=(2, 4, 6),
+                                   min_interior=8)
+    rng = np.random.default_rng(23)
+    dt = np.float32 if prec == 32 else np.float64
+    f = {k: I.round_to([rng.standard_normal(b.shape) for b in lay.boxes], dt) for k in O.COMPS}
+    plan = Plan(lay, (1.0,) * 3, 0.5, precision=prec)
+    df = plan.pack_fields(f)
+    plan.guard_exchange(df)
+    plan.sync()
+    got = plan.unpack_fields(df)
+    for k in O.COMPS:
+        ref = O.exchange(lay, f[k])
+        for g, r in zip(got[k], ref):
+            assert np.array_equal(g, r)
+    plan.close()
+
+
+# ---------------------------------------------------------------------------
+# whole push, each decomposition and equation form
+# ---------------------------------------------------------------------------
+
+def test_plane_waves_infinite_order_fp64():
+    """32^3 periodic, p = infinity, dt = 0.5, 64 steps (full size): GPU FP64
+    vs oracle and vs the analytic solution."""
+    w = I.make_workload("plane_waves_32")
+    err = check_push(w.layout, w.fields, w.src, w.steps, w.h, w.dt, 64, "vacuum")
+    got = run_push(w.layout, w.fields, w.src, w.steps, w.h, w.dt, 64, "vacuum")
+    ana = I.plane_wave_fields(I.plane_wave_set(seed=1), (32, 32, 32), w.h, 1.0, w.steps * w.dt)
+    assert O.rel_l2_fields(w.layout, got, {k: [v] for k, v in ana.items()}, O.COMPS) <= 1e-12
+    assert err <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("form", ["rho", "J"])
+def test_sources_global_reduced(prec, form):
+    """Sources workload at 32^3 (p = 16, dt = 0.9, filtered J), 20 steps."""
+    w = I.make_workload("sources_128", scale=4, steps=20)
+    src = dict(w.src)
+    if form == "J":
+        src.pop("rho")
+    check_push(w.layout, w.fields, src, w.steps, w.h, w.dt, prec, form)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_local_decomposition_reduced(prec):
+    """Local layout 2x2x2 boxes of 16^3 + 4 guards, p = 8, laser, 6 steps."""
+    lay = I.local_layout((32, 32, 32), (2, 2, 2), 4, 8)
+    f = I.laser_fields((32, 32, 32), wavelength=8.0, waist=5.0, duration=4.0)
+    fields = {k: I.scatter_global(v, lay) for k, v in f.items()}
+    check_push(lay, fields, {}, 6, (1.0,) * 3, 0.9, prec, "vacuum")
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_local_nonperiodic_anisotropic(prec):
+    lay = I.local_layout((48, 16, 24), (2, 2, 3), (4, 2, 2), 4, periodic=(0, 1, 1))
+    f = I.laser_fields((48, 16, 24), wavelength=6.0, waist=4.0, duration=4.0)
+    fields = {k: I.scatter_global(v, lay) for k, v in f.items()}
+    check_push(lay, fields, {}, 4, (1.0, 0.8, 1.2), 0.7, prec, "vacuum")
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_hybrid_reduced(prec):
+    """Hybrid: 4 groups along x of 16 cells with 4 guards on the x faces."""
+    w = I.make_workload("hybrid_1024", scale=16, steps=5)
+    check_push(w.layout, w.fields, w.src, w.steps, w.h, w.dt, prec, "vacuum")
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_uneven_independent_reduced(prec):
+    """Uneven batch of self-periodic boxes, mixed sizes/guards/orders, rho form."""
+    w = I.make_workload("uneven_300", scale=4, steps=5)
+    check_push(w.layout, w.fields, w.src, w.steps, w.h, w.dt, prec, "rho")
+
+
+def test_zero_steps_is_identity():
+    lay = I.local_layout((32, 16, 16), (2, 1, 1), 4, 8)
+    rng = np.random.default_rng(5)
+    f = {k: [rng.standard_normal(b.shape) for b in lay.boxes] for k in O.COMPS}
+    got = run_push(lay, f, {}, 0, (1.0,) * 3, 0.5, 64, "vacuum")
+    for k in O.COMPS:
+        for g, r in zip(got[k], f[k]):
+            assert np.array_equal(g, r)
+
+
+def test_errors_are_reported_not_raised_on_device():
+    import torch
+    from paper_1812_07357_gb300 import _abi as A
+    lay = I.global_layout((16, 16, 16), 8)
+    plan = Plan(lay, (1.0,) * 3, 0.5, precision=32, sources="rho")
+    f = {k: plan.empty() for k in O.COMPS}
+    with pytest.raises(A.PsatdError) as e:
+        plan.push(f, None, 1)           # sources missing
+    assert e.value.status == A.PSATD_ERR_INVALID_ARG
+    s = {k: plan.empty() for k in ("Jx", "Jy", "Jz", "rho")}
+    bad = dict(f)
+    raw = torch.zeros(plan.field_elems + 4, dtype=torch.float32, device="cuda")
+    bad["Ex"] = raw[1:]                 # 4-byte misaligned
+    with pytest.raises(A.PsatdError) as e:
+        plan.push(bad, s, 1)
+    assert e.value.status == A.PSATD_ERR_INVALID_ARG
+    with pytest.raises(A.PsatdError):
+        plan.push(f, s, -1)
+    plan.push(f, s, 1)
+    plan.sync()
+    plan.close()
