@@ -1,0 +1,468 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched PSATD push on one GB300.
+
+Workload (default): the 'local' decomposition of a 512^3 periodic domain into
+8x8x8 sub-domains of 64^3 cells, each padded with 16 guard cells per face
+(512 FFT boxes of 96^3), stencil order p = 32, FP32 fields with FP64-generated
+tables, vacuum, Gaussian laser pulse (lambda = 16, waist 32, duration 20
+cells) travelling along +x, dt = 0.9.  One step = S1 forward FFT of E, B on
+every box, S2 k-space update, S3 inverse FFT, S4 guard exchange.
+
+Metric: interior cell-steps per second (512^3 interior cells per step).
+Inputs (10.9 GB of fields) are far larger than L2, so no flush is needed.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores instead.
+
+Multi-GPU: the push shards into independent replicas (one plan per GPU, no
+data-path collective); ``value`` is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PSATD cell-steps/s, FP32-batched vs FP64-plain at stated L2 err; % HBM roofline"
+UNIT = "cell-steps/s"
+FALLBACK_HBM = 6800.0
+
+WORKLOADS = {
+    # name: (layout builder args, dt, p)
+    "local_512": dict(kind="local", global_n=(512, 512, 512), nsub=(8, 8, 8), ng=16, p=32, dt=0.9),
+    # small case of the same kernels (8 boxes of 96^3) for detailed profiles
+    "local_128": dict(kind="local", global_n=(128, 128, 128), nsub=(2, 2, 2), ng=16, p=32, dt=0.9),
+    "hybrid_1024": dict(kind="hybrid", global_n=(1024, 256, 256), nsub=(4, 1, 1), ng=64, p=64, dt=0.9),
+    "local_1024": dict(kind="local", global_n=(1024, 256, 256), nsub=(16, 4, 4), ng=64, p=64, dt=0.9),
+}
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--workload", default="local_512", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ----------------------------------------------------------------------------
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    rank, local, world = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ.setdefault("MASTER_PORT", "29511")
+        dist.init_process_group(backend, rank=rank, world_size=world)
+    return rank, local, world
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def reduce_max(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def total_units(per_rank: float, world: int) -> float:
+    """Weak scaling: every rank processes the same workload."""
+    return per_rank * world
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return FALLBACK_HBM, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        top = max(sm) if sm else 0
+        under = [s for s in sm if s >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(under) if under else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if _isnum(r[3])), default=None)}
+
+
+def _isnum(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+def build_layout(name):
+    from paper_1812_07357_gb300 import inputs as I
+    w = WORKLOADS[name]
+    if w["kind"] == "local":
+        return I.local_layout(w["global_n"], w["nsub"], w["ng"], w["p"])
+    return I.hybrid_layout(w["global_n"], w["nsub"], w["ng"], w["p"])
+
+
+def kernel_bytes(layout, s=4, fin=6, fout=6):
+    """Compulsory bytes of one launch of every kernel kind (each kernel reads
+    its inputs once and writes its outputs once)."""
+    C = sum(b.cells for b in layout.boxes)
+    M = sum((b.n[0] // 2 + 1) * b.n[1] * b.n[2] for b in layout.boxes)
+    Mz = sum((b.n[0] // 2 + 1) * b.n[1] * b.interior[2] for b in layout.boxes)
+    Mr = sum((b.n[0] // 2 + 1) * b.interior[1] * b.interior[2] for b in layout.boxes)
+    I_ = layout.interior_cells
+    G = layout.guard_cells
+    c = 2 * s
+    return [fin * (C * s + M * c),          # k_fwd_x: real in, half spectrum out
+            fin * 2 * M * c,                # k_col forward along y (in place)
+            (fin + fout) * M * c,           # k_z_update
+            fout * 2 * Mz * c,              # k_col inverse along y (interior z planes)
+            fout * (Mr * c + I_ * s),       # k_inv_x (interior rows, interior cells)
+            fout * 2 * G * s]               # k_exchange: read interior, write guard
+
+
+def step_algorithmic_bytes(layout, s=4, fin=6, fout=6):
+    """Minimal bytes of one step: every padded cell of every field read once
+    and written once, plus one write per guard cell and output field."""
+    return fin * layout.cells * s + fout * layout.cells * s + fout * layout.guard_cells * s
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    rank, local, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1812_07357_gb300 import _abi as A
+    from paper_1812_07357_gb300 import build as B
+    from paper_1812_07357_gb300 import inputs as I
+    from paper_1812_07357_gb300.solver import Plan
+
+    if rank == 0 or world == 1:
+        B.build()
+    barrier()
+    A.load()
+    lay = build_layout(args.workload)
+    w = WORKLOADS[args.workload]
+    h = (1.0, 1.0, 1.0)
+    plan = Plan(lay, h, w["dt"], precision=32, sources="vacuum")
+    fac = I.laser_box_factors(lay, h)
+    fields = {k: plan.pack_separable(fac[k]) for k in I.COMPONENTS}
+    plan.guard_exchange(fields)
+    plan.sync()
+    stream = plan.stream
+
+    for _ in range(args.warmup):
+        plan.push(fields, None, 1)
+    plan.sync()
+    A.psatd_plan_set_timing(plan.handle, True)
+    A.psatd_plan_kernel_times(plan.handle)   # discard warm-up records
+
+    clocks = ClockSampler(local).start() if rank == 0 else None
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.push(fields, None, 1)
+            launches += plan.last_launch_count()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop() if clocks else None
+    kms, kn = A.psatd_plan_kernel_times(plan.handle)
+    A.psatd_plan_set_timing(plan.handle, False)
+    ms_max = reduce_max(ms, dev if world > 1 else None)
+
+    interior = lay.interior_cells
+    value = total_units(interior * args.steps, world) / (ms_max / 1e3)
+    peak, peak_src = measured_peaks()
+    kb = kernel_bytes(lay)
+    avg = [kms[i] / kn[i] if kn[i] else 0.0 for i in range(len(kms))]
+    dom = max(range(len(avg)), key=lambda i: avg[i])
+    ach = kb[dom] / (avg[dom] / 1e3) / 1e9
+    step_ms = ms_max / args.steps
+    sab = step_algorithmic_bytes(lay)
+    traffic = _ncu_traffic(A.KERNEL_NAMES[dom], args.workload)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "decomposition": lay.kind,
+                   "global_n": list(lay.global_n), "boxes": len(lay.boxes),
+                   "box_n": list(lay.boxes[0].n), "ng": lay.boxes[0].ng_lo[0],
+                   "order_p": lay.boxes[0].p, "dt": w["dt"], "tables": "f64-generated",
+                   "interior_cells": interior, "padded_cells": lay.cells,
+                   "l2": "inputs larger than L2 (%.1f GB of fields)" % (6 * lay.cells * 4 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "hbm", "kernel": A.KERNEL_NAMES[dom], "achieved": ach,
+                     "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": kb[dom], "avg_launch_ms": avg[dom],
+                     "peak_source": peak_src},
+        "step_roofline": {"algorithmic_bytes_per_step": sab,
+                          "achieved": sab / (step_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                          "frac": sab / (step_ms / 1e3) / 1e9 / peak},
+        "kernels": {A.KERNEL_NAMES[i]: {"launches": kn[i], "total_ms": kms[i], "avg_ms": avg[i],
+                                        "bytes_per_launch": kb[i],
+                                        "gbps": (kb[i] / (avg[i] / 1e3) / 1e9) if avg[i] else None}
+                    for i in range(len(kms))},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if not args.no_e2e:
+        out["e2e"] = run_e2e(plan, fields, args, lay, world)
+    if rank == 0 and world == 1 and not args.no_fp64:
+        out["fp64_plain"] = run_fp64_plain(lay, w, fac)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_sample(lay, w, fac, target_s=12.0)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def run_e2e(plan, fields, args, lay, world):
+    """Same metric through the C ABI with host buffers: every step copies the
+    fields from pinned host memory to the device, pushes one step and copies
+    them back."""
+    import torch
+    from paper_1812_07357_gb300 import inputs as I
+    host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in fields.items()}
+    for k in host:
+        host[k].copy_(fields[k])
+    stream = plan.stream
+    torch.cuda.synchronize()
+    nb = sum(v.numel() * v.element_size() for v in host.values())
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            for k in I.COMPONENTS:
+                fields[k].copy_(host[k], non_blocking=True)
+            plan.push(fields, None, 1)
+            for k in I.COMPONENTS:
+                host[k].copy_(fields[k], non_blocking=True)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = reduce_max(e0.elapsed_time(e1), torch.device("cuda", torch.cuda.current_device())
+                    if world > 1 else None)
+    v = total_units(lay.interior_cells * args.e2e_steps, world) / (ms / 1e3)
+    return {"value": v, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
+            "steps": args.e2e_steps, "ms_per_step": ms / args.e2e_steps}
+
+
+def run_fp64_plain(lay, w, fac, nbox=2, nsteps=3):
+    """Plain FP64 GPU push: same kernels in double, one box per plan (no
+    batching), on a sample of boxes of the same workload."""
+    import torch
+    from paper_1812_07357_gb300 import inputs as I
+    from paper_1812_07357_gb300.solver import Plan
+    tot_ms = 0.0
+    cells = 0
+    for b in range(nbox):
+        box = lay.boxes[b]
+        sub = I.Layout("independent", (0, 0, 0), (1, 1, 1), [box])
+        plan = Plan(sub, (1.0,) * 3, w["dt"], precision=64, sources="vacuum")
+        f = {k: plan.pack_separable([fac[k][b]] if fac[k] is not None else None)
+             for k in I.COMPONENTS}
+        plan.push(f, None, 1)
+        plan.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(plan.stream):
+            e0.record(plan.stream)
+            plan.push(f, None, nsteps)
+            e1.record(plan.stream)
+        torch.cuda.synchronize()
+        tot_ms += e0.elapsed_time(e1)
+        cells += box.interior_cells * nsteps
+        plan.close()
+    return {"value": cells / (tot_ms / 1e3), "unit": UNIT,
+            "sample": f"{nbox} boxes x {nsteps} steps, FP64, one box per plan (unbatched); "
+                      "guard exchange of a self-periodic box"}
+
+
+def oracle_sample(lay, w, fac, target_s=12.0, max_boxes=64):
+    """The FP64 oracle (as it stands) on a bounded sample: S1-S3 of whole
+    boxes for one step, on the host cores."""
+    import numpy as np
+    from oracle import psatd_oracle as O
+    from paper_1812_07357_gb300 import inputs as I
+    boxes = []
+    t0 = time.perf_counter()
+    done = 0
+    cells = 0
+    while done < max_boxes and (done == 0 or (time.perf_counter() - t0) < target_s):
+        b = done
+        box = lay.boxes[b]
+        f = {}
+        for k in I.COMPONENTS:
+            if fac[k] is None:
+                f[k] = np.zeros(box.shape)
+            else:
+                fz, fy, fx, d = fac[k][b]
+                f[k] = (fz[:, None, None] * fy[None, :, None] * fx[None, None, :]) / d
+        f = I.round_to(f, np.float32)
+        O.push_box(f, None, (1.0,) * 3, box.p, w["dt"], form="vacuum")
+        done += 1
+        cells += box.interior_cells
+    dt = time.perf_counter() - t0
+    return {"value": cells / dt, "unit": UNIT, "cores": O._WORKERS, "kind": "oracle",
+            "sample": f"{done} of {len(lay.boxes)} boxes x 1 step (S1-S3 per box, FP64 numpy/"
+                      f"scipy.fft oracle), {dt:.1f} s"}
+
+
+def _ncu_traffic(kernel_name, workload):
+    """Per-launch DRAM bytes of the dominant kernel from a committed ncu
+    summary (profiles/<kernel>_<workload>.json), if one exists for the
+    current kernel source; else None."""
+    base = kernel_name.split("(")[0]
+    p = os.path.join(ROOT, "profiles", f"{base}_{workload}.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return d.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ----------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    from paper_1812_07357_gb300 import inputs as I
+    lay = build_layout(args.workload)
+    w = WORKLOADS[args.workload]
+    fac = I.laser_box_factors(lay, (1.0,) * 3)
+    for _ in range(args.warmup):
+        oracle_sample(lay, w, fac, target_s=0.0, max_boxes=1)
+    t0 = time.perf_counter()
+    vals = []
+    for _ in range(args.steps):
+        r = oracle_sample(lay, w, fac, target_s=0.0, max_boxes=1)
+        vals.append(r)
+    dt = time.perf_counter() - t0
+    cells = lay.boxes[0].interior_cells * args.steps
+    value = cells / dt
+    cb = {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+          "sample": f"1 of {len(lay.boxes)} boxes per step (S1-S3 of one box, FP64 oracle)"}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": args.workload, "decomposition": lay.kind,
+                      "boxes": len(lay.boxes), "box_n": list(lay.boxes[0].n),
+                      "order_p": lay.boxes[0].p, "dt": w["dt"]},
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    args = parse(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -203,6 +203,19 @@ const char* psatd_last_error(const psatd_plan* plan);
 /* Number of kernel launches issued by the last psatd_push call (host count). */
 int64_t psatd_last_launch_count(const psatd_plan* plan);
 
+/* Kernel kinds reported by psatd_plan_kernel_times. */
+#define PSATD_KERNEL_KINDS 6 /* 0 fwd_x, 1 col forward, 2 z_update, 3 col inverse, 4 inv_x, 5 exchange */
+
+/* Diagnostics: with enable != 0, psatd_push brackets every kernel launch with
+ * CUDA events recorded on its stream (no extra synchronisation). */
+psatd_status psatd_plan_set_timing(psatd_plan* plan, int32_t enable);
+
+/* Synchronise the plan's last stream, then add the device time (ms) and the
+ * number of launches of every kernel kind recorded since the previous call
+ * into ms[0..n) and launches[0..n) (n <= PSATD_KERNEL_KINDS; either array may
+ * be NULL), and forget the records. */
+psatd_status psatd_plan_kernel_times(psatd_plan* plan, double* ms, int64_t* launches, int32_t n);
+
 #ifdef __cplusplus
 }
 #endif

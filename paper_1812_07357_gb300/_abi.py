@@ -83,7 +83,12 @@ _SIGS = {
     "psatd_status_string": (c_char_p, [c_int32]),
     "psatd_last_error": (c_char_p, [c_void_p]),
     "psatd_last_launch_count": (c_int64, [c_void_p]),
+    "psatd_plan_set_timing": (c_int32, [c_void_p, c_int32]),
+    "psatd_plan_kernel_times": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32]),
 }
+
+PSATD_KERNEL_KINDS = 6
+KERNEL_NAMES = ("k_fwd_x", "k_col(fwd)", "k_z_update", "k_col(inv)", "k_inv_x", "k_exchange")
 
 _lib = None
 
@@ -205,3 +210,14 @@ def psatd_last_error(plan: int | None = None) -> str:
 
 def psatd_last_launch_count(plan: int) -> int:
     return int(load().psatd_last_launch_count(c_void_p(plan)))
+
+
+def psatd_plan_set_timing(plan: int, enable: bool):
+    _check(load().psatd_plan_set_timing(c_void_p(plan), 1 if enable else 0), plan)
+
+
+def psatd_plan_kernel_times(plan: int):
+    ms = (c_double * PSATD_KERNEL_KINDS)()
+    n = (c_int64 * PSATD_KERNEL_KINDS)()
+    _check(load().psatd_plan_kernel_times(c_void_p(plan), ms, n, PSATD_KERNEL_KINDS), plan)
+    return list(ms), list(n)

@@ -292,6 +292,15 @@ struct psatd_plan {
   cudaStream_t last_stream = nullptr;
   int64_t last_launches = 0;
 
+  // per-kernel timing (diagnostics)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  struct Rec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+
   DevPlan dev() const {
     DevPlan P;
     P.boxes = d_boxes;
@@ -308,6 +317,22 @@ struct psatd_plan {
   ~psatd_plan() {
     cudaDeviceSynchronize();
     for (void* p : allocs) cudaFree(p);
+    for (auto& r : recs) {
+      ev_pool.push_back(r.a);
+      ev_pool.push_back(r.b);
+    }
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  }
+
+  cudaEvent_t take_event() {
+    if (!ev_pool.empty()) {
+      cudaEvent_t e = ev_pool.back();
+      ev_pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
   }
 };
 
@@ -555,6 +580,19 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Run one launch, bracketed by events when the plan records kernel times.
+template <typename F>
+cudaError_t timed(psatd_plan* P, int kind, cudaStream_t st, F&& launch) {
+  if (!P->timing) return launch();
+  cudaEvent_t a = P->take_event(), b = P->take_event();
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaEventRecord(a, st);
+  if (e == cudaSuccess) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecord(b, st);
+  P->recs.push_back({kind, a, b});
+  return e;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -734,14 +772,26 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
     const int64_t S = P->spec_total;
     int64_t launches = 0;
     for (int step = 0; step < nsteps; ++step) {
-      CK(P, launch_fwd_x(P->prec, D, fp, FIN, P->d_ws, S, P->d_rows_all, (int64_t)P->rows_all.size(), P->smem_fx, st));
-      CK(P, launch_col(P->prec, -1, 1, D, P->d_ws, S, FIN, P->d_ycols_all, (int64_t)P->ycols_all.size(), P->smem_y, st));
-      CK(P, launch_z_update(P->prec, P->form, D, P->d_ws, S, P->d_zcols, (int64_t)P->zcols.size(), P->smem_z, st));
-      CK(P, launch_col(P->prec, 1, 1, D, P->d_ws, S, FOUT, P->d_ycols_int, (int64_t)P->ycols_int.size(), P->smem_y, st));
-      CK(P, launch_inv_x(P->prec, D, fp, FOUT, P->d_ws, S, P->d_rows_int, (int64_t)P->rows_int.size(), P->smem_ix, 1, st));
+      CK(P, timed(P, 0, st, [&] {
+           return launch_fwd_x(P->prec, D, fp, FIN, P->d_ws, S, P->d_rows_all, (int64_t)P->rows_all.size(), P->smem_fx, st);
+         }));
+      CK(P, timed(P, 1, st, [&] {
+           return launch_col(P->prec, -1, 1, D, P->d_ws, S, FIN, P->d_ycols_all, (int64_t)P->ycols_all.size(), P->smem_y, st);
+         }));
+      CK(P, timed(P, 2, st, [&] {
+           return launch_z_update(P->prec, P->form, D, P->d_ws, S, P->d_zcols, (int64_t)P->zcols.size(), P->smem_z, st);
+         }));
+      CK(P, timed(P, 3, st, [&] {
+           return launch_col(P->prec, 1, 1, D, P->d_ws, S, FOUT, P->d_ycols_int, (int64_t)P->ycols_int.size(), P->smem_y, st);
+         }));
+      CK(P, timed(P, 4, st, [&] {
+           return launch_inv_x(P->prec, D, fp, FOUT, P->d_ws, S, P->d_rows_int, (int64_t)P->rows_int.size(), P->smem_ix, 1, st);
+         }));
       launches += 5;
       if (!P->tiles.empty()) {
-        CK(P, launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_tiles, (int64_t)P->tiles.size(), st));
+        CK(P, timed(P, 5, st, [&] {
+             return launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_tiles, (int64_t)P->tiles.size(), st);
+           }));
         ++launches;
       }
     }
@@ -813,5 +863,30 @@ const char* psatd_last_error(const psatd_plan* p) {
 }
 
 int64_t psatd_last_launch_count(const psatd_plan* p) { return p ? p->last_launches : 0; }
+
+psatd_status psatd_plan_set_timing(psatd_plan* P, int32_t enable) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  P->timing = enable != 0;
+  return PSATD_OK;
+}
+
+psatd_status psatd_plan_kernel_times(psatd_plan* P, double* ms, int64_t* launches, int32_t n) {
+  if (!P || n < 0) return PSATD_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(P->last_stream);
+  if (e != cudaSuccess) return fail(P, PSATD_ERR_CUDA, fmt("device error: %s", cudaGetErrorString(e)));
+  for (auto& r : P->recs) {
+    float t = 0.f;
+    if (r.kind < n) {
+      e = cudaEventElapsedTime(&t, r.a, r.b);
+      if (e != cudaSuccess) return fail(P, PSATD_ERR_CUDA, fmt("event timing: %s", cudaGetErrorString(e)));
+      if (ms) ms[r.kind] += t;
+      if (launches) launches[r.kind] += 1;
+    }
+    P->ev_pool.push_back(r.a);
+    P->ev_pool.push_back(r.b);
+  }
+  P->recs.clear();
+  return PSATD_OK;
+}
 
 }  // extern "C"

@@ -276,6 +276,34 @@ def laser_fields(global_n, h=(1.0, 1.0, 1.0), c=1.0, wavelength=16.0,
     return out
 
 
+def laser_box_factors(layout: Layout, h=(1.0, 1.0, 1.0), c=1.0, wavelength=16.0,
+                      waist=32.0, duration=20.0):
+    """The laser of ``laser_fields`` is separable: per box and component return
+    the 1D factors (fz, fy, fx) and the divisor d such that
+    (fz[:,None,None] * fy[None,:,None] * fx[None,None,:]) / d equals
+    ``scatter_global(laser_fields(...), layout)`` for that box, bit for bit.
+    Components other than E_y and B_z are zero (returned as None)."""
+    n = layout.global_n
+    x0, y0, z0 = (n[0] * h[0] / 2, n[1] * h[1] / 2, n[2] * h[2] / 2)
+    k0 = 2 * np.pi / (wavelength * h[0])
+    w0, tau = waist * h[1], duration * h[0]
+    out = {c_: None for c_ in COMPONENTS}
+    for comp in ("Ey", "Bz"):
+        s = _SAMPLE_AT[comp]
+        x = (np.arange(n[0]) + s[0]) * h[0] - x0
+        y = (np.arange(n[1]) + s[1]) * h[1] - y0
+        z = (np.arange(n[2]) + s[2]) * h[2] - z0
+        g = [np.append(np.exp(-x ** 2 / tau ** 2) * np.cos(k0 * x), 0.0),
+             np.append(np.exp(-y ** 2 / w0 ** 2), 0.0),
+             np.append(np.exp(-z ** 2 / w0 ** 2), 0.0)]
+        per = []
+        for b in layout.boxes:
+            idx = [_box_index(b, layout, d) for d in range(3)]   # -1 -> appended 0
+            per.append((g[2][idx[2]], g[1][idx[1]], g[0][idx[0]], 1.0 if comp == "Ey" else c))
+        out[comp] = per
+    return out
+
+
 def _true_k2(n, h):
     ks = [2 * np.pi * np.fft.fftfreq(n[d], d=h[d]) for d in range(3)]
     KZ, KY, KX = np.meshgrid(ks[2], ks[1], ks[0], indexing="ij")

@@ -98,6 +98,21 @@ class Plan:
         return [host[off:off + n].reshape(b.shape).copy()
                 for (off, n), b in zip(self.offsets, self.layout.boxes)]
 
+    def pack_separable(self, factors):
+        """Device buffer from per-box separable factors (see
+        ``inputs.laser_box_factors``); None gives zeros."""
+        t = self.empty()
+        if factors is None:
+            return t
+        torch = self.torch
+        for (off, n), (fz, fy, fx, d) in zip(self.offsets, factors):
+            z = torch.from_numpy(np.ascontiguousarray(fz)).cuda()
+            y = torch.from_numpy(np.ascontiguousarray(fy)).cuda()
+            x = torch.from_numpy(np.ascontiguousarray(fx)).cuda()
+            v = (z.view(-1, 1, 1) * y.view(1, -1, 1) * x.view(1, 1, -1)) / d
+            t[off:off + n] = v.reshape(-1).to(self.dtype)
+        return t
+
     def pack_fields(self, d: Dict[str, List[np.ndarray]]):
         return {k: self.pack(v) for k, v in d.items()}
 
