@@ -228,6 +228,13 @@ std::vector<CopyBlk> build_blocks(const psatd_plan_desc* d) {
   return out;
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// helpers shared with the no-allocation single-box variant (static_push.cu)
+// ---------------------------------------------------------------------------
+namespace psatd {
+
 // Radix schedule: 8s first (4,4 instead of 8,2), then 4 / 2, 3s and 5s.
 bool radix_plan(int n, AxisPlan& ap) {
   ap.n = n;
@@ -252,7 +259,28 @@ bool radix_plan(int n, AxisPlan& ap) {
   return true;
 }
 
-}  // namespace
+
+// Order-p staggered stencil weights (see tables.cu for their use):
+std::vector<double> stencil_alpha(int p) {
+  // alpha_l = prod_{j != l} (2j-1)^2 / ((2j-1)^2 - (2l-1)^2), l = 1..p/2
+  const int q = p / 2;
+  std::vector<double> a(q);
+  for (int l = 1; l <= q; ++l) {
+    double v = 1.0;
+    const double xl = (double)(2 * l - 1) * (2 * l - 1);
+    for (int j = 1; j <= q; ++j) {
+      if (j == l) continue;
+      const double xj = (double)(2 * j - 1) * (2 * j - 1);
+      v *= xj / (xj - xl);
+    }
+    a[l - 1] = v;
+  }
+  return a;
+}
+
+void set_thread_error(const char* msg) { g_thread_error = msg; }
+
+}  // namespace psatd
 
 // ---------------------------------------------------------------------------
 // the plan
@@ -376,22 +404,6 @@ cudaError_t dalloc(psatd_plan* p, size_t bytes, void** d) {
   return cudaSuccess;
 }
 
-std::vector<double> stencil_alpha(int p) {
-  // alpha_l = prod_{j != l} (2j-1)^2 / ((2j-1)^2 - (2l-1)^2), l = 1..p/2
-  const int q = p / 2;
-  std::vector<double> a(q);
-  for (int l = 1; l <= q; ++l) {
-    double v = 1.0;
-    const double xl = (double)(2 * l - 1) * (2 * l - 1);
-    for (int j = 1; j <= q; ++j) {
-      if (j == l) continue;
-      const double xj = (double)(2 * j - 1) * (2 * j - 1);
-      v *= xj / (xj - xl);
-    }
-    a[l - 1] = v;
-  }
-  return a;
-}
 
 psatd_status build(psatd_plan* P, cudaStream_t st) {
   const psatd_plan_desc& d = P->desc;
@@ -573,8 +585,13 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   free_tmp();
   CK(P, e);
   const int smem = std::max({P->smem_fx, P->smem_y, P->smem_z, P->smem_zonly, P->smem_ix});
-  if (smem > 227 * 1024) return fail(P, PSATD_ERR_UNSUPPORTED_SIZE, fmt("needs %d B shared memory", smem));
-  CK(P, configure_kernels(P->prec, smem));
+  int dev = 0, optin = 0;
+  CK(P, cudaGetDevice(&dev));
+  CK(P, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > optin) return fail(P, PSATD_ERR_UNSUPPORTED_SIZE, fmt("needs %d B shared memory", smem));
+  // The attribute is a per-kernel cap shared by every plan: raise it to the
+  // device maximum so that no plan lowers it below another plan's need.
+  CK(P, configure_kernels(P->prec, optin));
   return PSATD_OK;
 }
 

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/psatd.h"
@@ -119,6 +121,14 @@ cudaError_t launch_exchange(int prec, const DevPlan& P, const FieldPtrs& f, int 
                             cudaStream_t st);
 // Maximum dynamic shared memory opt-in for all kernels of a precision.
 cudaError_t configure_kernels(int prec, int smem_bytes);
+
+// ---- host helpers (plan.cpp) ------------------------------------------------
+// Radix schedule of a complex FFT length (false if it is not 5-smooth).
+bool radix_plan(int n, AxisPlan& ap);
+// Weights alpha_l, l = 1..p/2, of the order-p staggered difference.
+std::vector<double> stencil_alpha(int p);
+// Text returned by psatd_last_error(NULL) on this thread.
+void set_thread_error(const char* msg);
 
 // ---- FP64 table generators (tables.cu) ------------------------------------
 cudaError_t gen_twiddles(double2* out, int n, cudaStream_t st);
