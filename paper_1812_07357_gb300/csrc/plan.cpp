@@ -1,6 +1,6 @@
 // Host side of the PSATD library: description validation, the guard-exchange
 // protocol (copy blocks from box-overlap geometry, computed once before any
-// step as the paper's Sec. 2.5.2 describes for its G1/G2 grids), work lists,
+// step, as the paper's Sec. 2.6 does for its two grids), work lists,
 // device tables, and the C ABI entry points declared in include/psatd.h.
 #include <cuda_runtime.h>
 
