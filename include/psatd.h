@@ -125,9 +125,10 @@ typedef struct {
 } psatd_sources;
 
 /* One guard-exchange copy block (host view of the precomputed exchange
- * protocol, cf. the paper's Sec. 2.5.2 "intersection ... computed before the
- * PIC loop").  src_box = -1 means "fill with zero" (outside a non-periodic
- * domain).  Coordinates are box-local cell indices. */
+ * protocol; the paper's Sec. 2.6 computes the overlaps of its two
+ * decompositions once, before the time loop, in the same way).  src_box = -1
+ * means "fill with zero" (outside a non-periodic domain).  Coordinates are
+ * box-local cell indices. */
 typedef struct {
   int32_t dst_box, src_box;
   int32_t dst_lo[3], src_lo[3], ext[3];
