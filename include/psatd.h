@@ -217,6 +217,35 @@ psatd_status psatd_plan_set_timing(psatd_plan* plan, int32_t enable);
  * be NULL), and forget the records. */
 psatd_status psatd_plan_kernel_times(psatd_plan* plan, double* ms, int64_t* launches, int32_t n);
 
+/* ---------------------------------------------------------------------------
+ * Push without device allocation (the paper has no counterpart: this is a
+ * service for callers that may not allocate device memory, e.g. code running
+ * under a host framework that owns every device allocation, or a fixed-memory
+ * real-time loop).
+ *
+ * Advances one periodic box of n[0] x n[1] x n[2] cells (no guards, the
+ * 'global' decomposition), FP32, vacuum, by `nsteps` steps of S1..S3, in place
+ * on the caller's six FP32 device buffers (x fastest, 16-byte aligned, each
+ * n[0]*n[1]*n[2] floats).  order_p, dx, dt, c as in psatd_plan_desc
+ * (eps0 is irrelevant in vacuum).  The result equals psatd_push on a
+ * one-box PSATD_DECOMP_GLOBAL FP32 vacuum plan.
+ *
+ * Nothing is allocated: the spectral workspace, tables and work lists live in
+ * one static device array of PSATD_STATIC_SCRATCH_BYTES (64 MiB), reserved on
+ * every GPU that loads the library until the process exits.  A box whose
+ * needs exceed it (a 128^3 box fits, 144^3 does not) is rejected with
+ * PSATD_ERR_UNSUPPORTED_SIZE and a message giving both byte counts.  All calls
+ * on a device share the array; calls that overlap on the GPU race and give
+ * wrong results.  The first call on each device looks up the array's address
+ * and sets kernel attributes: make it before any stream capture.  Errors are
+ * reported through psatd_last_error(NULL).
+ * ------------------------------------------------------------------------- */
+#define PSATD_STATIC_SCRATCH_BYTES (64ull << 20)
+
+psatd_status psatd_push_box_static(const int32_t n[3], int32_t order_p, const double dx[3],
+                                   double dt, double c, const psatd_fields* fields,
+                                   int32_t nsteps, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

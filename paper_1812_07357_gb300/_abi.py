@@ -85,7 +85,11 @@ _SIGS = {
     "psatd_last_launch_count": (c_int64, [c_void_p]),
     "psatd_plan_set_timing": (c_int32, [c_void_p, c_int32]),
     "psatd_plan_kernel_times": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32]),
+    "psatd_push_box_static": (c_int32, [POINTER(c_int32), c_int32, POINTER(c_double), c_double,
+                                        c_double, POINTER(psatd_fields), c_int32, c_void_p]),
 }
+
+PSATD_STATIC_SCRATCH_BYTES = 64 << 20
 
 PSATD_KERNEL_KINDS = 6
 KERNEL_NAMES = ("k_fwd_x", "k_col(fwd)", "k_z_update", "k_col(inv)", "k_inv_x", "k_exchange")
@@ -221,3 +225,13 @@ def psatd_plan_kernel_times(plan: int):
     n = (c_int64 * PSATD_KERNEL_KINDS)()
     _check(load().psatd_plan_kernel_times(c_void_p(plan), ms, n, PSATD_KERNEL_KINDS), plan)
     return list(ms), list(n)
+
+
+def psatd_push_box_static(n, order_p: int, dx, dt: float, c: float, fields: psatd_fields,
+                          nsteps: int, stream: int = 0):
+    """One periodic FP32 vacuum box, pushed without any device allocation
+    (scratch lives in the library's static device array)."""
+    nn = (c_int32 * 3)(*[int(v) for v in n])
+    dd = (c_double * 3)(*[float(v) for v in dx])
+    _check(load().psatd_push_box_static(nn, int(order_p), dd, float(dt), float(c),
+                                        ctypes.byref(fields), int(nsteps), c_void_p(stream)))
