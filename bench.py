@@ -188,7 +188,10 @@ def build_layout(name):
 
 def kernel_bytes(layout, s=4, fin=6, fout=6):
     """Compulsory bytes of one launch of every kernel kind (each kernel reads
-    its inputs once and writes its outputs once)."""
+    its inputs once and writes its outputs once).  Kinds: forward x(+y),
+    generic y forward, z + update, generic y inverse, inverse (y+)x, exchange.
+    On the fast path the y passes are fused into the x kernels, so kinds 0 and
+    4 carry the plane kernels' bytes and kinds 1 and 3 do not launch."""
     C = sum(b.cells for b in layout.boxes)
     M = sum((b.n[0] // 2 + 1) * b.n[1] * b.n[2] for b in layout.boxes)
     Mz = sum((b.n[0] // 2 + 1) * b.n[1] * b.interior[2] for b in layout.boxes)
@@ -196,12 +199,18 @@ def kernel_bytes(layout, s=4, fin=6, fout=6):
     I_ = layout.interior_cells
     G = layout.guard_cells
     c = 2 * s
-    return [fin * (C * s + M * c),          # k_fwd_x: real in, half spectrum out
-            fin * 2 * M * c,                # k_col forward along y (in place)
-            (fin + fout) * M * c,           # k_z_update
-            fout * 2 * Mz * c,              # k_col inverse along y (interior z planes)
-            fout * (Mr * c + I_ * s),       # k_inv_x (interior rows, interior cells)
-            fout * 2 * G * s]               # k_exchange: read interior, write guard
+    return {"generic": [fin * (C * s + M * c),          # k_fwd_x: real in, half spectrum out
+                        fin * 2 * M * c,                # k_col forward along y (in place)
+                        (fin + fout) * M * c,           # k_z_update
+                        fout * 2 * Mz * c,              # k_col inverse along y (interior z)
+                        fout * (Mr * c + I_ * s),       # k_inv_x (interior rows, cells)
+                        fout * 2 * G * s],              # k_exchange: read interior, write guard
+            "fast": [fin * (C * s + M * c),             # k_plane_fwd: real plane in, spectrum out
+                     0,
+                     (fin + fout) * M * c,              # k_z_fast
+                     0,
+                     fout * (Mz * c + I_ * s),          # k_plane_inv: interior planes in, cells out
+                     fout * 2 * G * s]}
 
 
 def step_algorithmic_bytes(layout, s=4, fin=6, fout=6):
@@ -267,7 +276,7 @@ def run_gpu(args):
     interior = lay.interior_cells
     value = total_units(interior * args.steps, world) / (ms_max / 1e3)
     peak, peak_src = measured_peaks()
-    kb = kernel_bytes(lay)
+    kb = kernel_bytes(lay)["fast" if plan.fast_boxes == len(lay.boxes) else "generic"]
     avg = [kms[i] / kn[i] if kn[i] else 0.0 for i in range(len(kms))]
     dom = max(range(len(avg)), key=lambda i: avg[i])
     ach = kb[dom] / (avg[dom] / 1e3) / 1e9
@@ -286,7 +295,8 @@ def run_gpu(args):
                    "order_p": lay.boxes[0].p, "dt": w["dt"], "tables": "f64-generated",
                    "interior_cells": interior, "padded_cells": lay.cells,
                    "l2": "inputs larger than L2 (%.1f GB of fields)" % (6 * lay.cells * 4 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "fast_boxes": plan.fast_boxes},
         "roofline": {"bound": "hbm", "kernel": A.KERNEL_NAMES[dom], "achieved": ach,
                      "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": kb[dom], "avg_launch_ms": avg[dom],

@@ -71,6 +71,9 @@ typedef enum {
 #define PSATD_RHO_CONTINUITY 0x2u /* rho is in/out, advanced by continuity; E takes   */
                                   /* its longitudinal part from Gauss's law (rho form) */
 #define PSATD_NO_GRAPH       0x8u /* never capture multi-step pushes in a CUDA graph   */
+#define PSATD_GENERIC_KERNELS 0x10u /* diagnostics: run every box through the generic */
+                                  /* kernels even where a fast path exists (the two  */
+                                  /* agree to rounding)                              */
 
 /* One FFT box.  n[] counts cells including guards; each n[d] must be even,
  * 5-smooth (2^a 3^b 5^c), n[0] in [4, 1024], n[1], n[2] in [4, 512].
@@ -203,6 +206,11 @@ const char* psatd_last_error(const psatd_plan* plan);
 
 /* Number of kernel launches issued by the last psatd_push call (host count). */
 int64_t psatd_last_launch_count(const psatd_plan* plan);
+
+/* Number of boxes that run on the fast kernels (all three FFT lengths have a
+ * two-pass register schedule and the planes fit in shared memory); the other
+ * boxes run on the generic multi-pass kernels.  -1 for a NULL plan. */
+int32_t psatd_plan_fast_boxes(const psatd_plan* plan);
 
 /* Kernel kinds reported by psatd_plan_kernel_times. */
 #define PSATD_KERNEL_KINDS 6 /* 0 fwd_x, 1 col forward, 2 z_update, 3 col inverse, 4 inv_x, 5 exchange */

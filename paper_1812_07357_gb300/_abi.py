@@ -30,6 +30,7 @@ PSATD_DECOMP_INDEPENDENT = 3
 PSATD_VACUUM = 0x1
 PSATD_RHO_CONTINUITY = 0x2
 PSATD_NO_GRAPH = 0x8
+PSATD_GENERIC_KERNELS = 0x10
 
 
 class psatd_box(Structure):
@@ -85,6 +86,7 @@ _SIGS = {
     "psatd_last_launch_count": (c_int64, [c_void_p]),
     "psatd_plan_set_timing": (c_int32, [c_void_p, c_int32]),
     "psatd_plan_kernel_times": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32]),
+    "psatd_plan_fast_boxes": (c_int32, [c_void_p]),
     "psatd_push_box_static": (c_int32, [POINTER(c_int32), c_int32, POINTER(c_double), c_double,
                                         c_double, POINTER(psatd_fields), c_int32, c_void_p]),
 }
@@ -92,7 +94,7 @@ _SIGS = {
 PSATD_STATIC_SCRATCH_BYTES = 64 << 20
 
 PSATD_KERNEL_KINDS = 6
-KERNEL_NAMES = ("k_fwd_x", "k_col(fwd)", "k_z_update", "k_col(inv)", "k_inv_x", "k_exchange")
+KERNEL_NAMES = ("fwd_xy", "col_fwd", "z_update", "col_inv", "inv_yx", "exchange")
 
 _lib = None
 
@@ -235,3 +237,7 @@ def psatd_push_box_static(n, order_p: int, dx, dt: float, c: float, fields: psat
     dd = (c_double * 3)(*[float(v) for v in dx])
     _check(load().psatd_push_box_static(nn, int(order_p), dd, float(dt), float(c),
                                         ctypes.byref(fields), int(nsteps), c_void_p(stream)))
+
+
+def psatd_plan_fast_boxes(plan: int) -> int:
+    return int(load().psatd_plan_fast_boxes(c_void_p(plan)))

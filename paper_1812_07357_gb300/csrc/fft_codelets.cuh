@@ -1,0 +1,259 @@
+// Complex helpers and small-DFT codelets held entirely in registers.
+//
+// Dft<T, R, DIR>::run(v) replaces v[0..R) by y_k = sum_t v_t exp(DIR 2 pi i t k / R)
+// (DIR = -1 forward, +1 inverse, unnormalised).  R in {2,3,4,5,8} are written
+// out; R in {6,10,12,16} are composed from two of them (decimation in time,
+// R = A*B) with the internal twiddles exp(DIR 2 pi i m / R) taken from their
+// closed forms (cos(pi/8) = sqrt(2 + sqrt 2)/2, cos(pi/5) = (1 + sqrt 5)/4, ...).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+namespace psatd {
+
+template <typename T>
+using cx = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+
+template <typename T>
+__device__ __forceinline__ cx<T> mk(T a, T b) {
+  cx<T> r;
+  r.x = a;
+  r.y = b;
+  return r;
+}
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+template <typename C>
+__device__ __forceinline__ C cmul(C a, C b) {
+  C r;
+  r.x = a.x * b.x - a.y * b.y;
+  r.y = a.x * b.y + a.y * b.x;
+  return r;
+}
+template <typename C>
+__device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
+  C r;
+  r.x = a.x * b.x + a.y * b.y;
+  r.y = a.y * b.x - a.x * b.y;
+  return r;
+}
+template <typename C, typename T>
+__device__ __forceinline__ C rmul(T s, C a) {
+  C r;
+  r.x = s * a.x;
+  r.y = s * a.y;
+  return r;
+}
+template <typename C>
+__device__ __forceinline__ C conjg(C a) {
+  a.y = -a.y;
+  return a;
+}
+template <typename C>
+__device__ __forceinline__ C times_i(C a) {  // i * a
+  C r;
+  r.x = -a.y;
+  r.y = a.x;
+  return r;
+}
+// multiply by exp(DIR * i pi/2): DIR = -1 -> -i (forward), +1 -> +i (inverse)
+template <int DIR, typename C>
+__device__ __forceinline__ C rot(C a) {
+  C r;
+  if (DIR < 0) {
+    r.x = a.y;
+    r.y = -a.x;
+  } else {
+    r.x = -a.y;
+    r.y = a.x;
+  }
+  return r;
+}
+// a * w (forward, w = exp(-i phi) from the table) or a * conj(w) (inverse)
+template <int DIR, typename C>
+__device__ __forceinline__ C twmul(C a, C w) {
+  return DIR < 0 ? cmul(a, w) : cmulc(a, w);
+}
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I in [B, E).
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// cos(2 pi m / R) and sin(2 pi m / R) for the composite codelets, from their
+// closed forms; evaluated at compile time only.
+constexpr double root_cos(int R, int m) {
+  const double r2 = 0.70710678118654752440;   // sqrt(2)/2
+  const double c8 = 0.92387953251128675613;   // cos(pi/8) = sqrt(2 + sqrt 2)/2
+  const double s8 = 0.38268343236508977173;   // sin(pi/8) = sqrt(2 - sqrt 2)/2
+  const double h3 = 0.86602540378443864676;   // sqrt(3)/2
+  const double c5 = 0.80901699437494742410;   // cos(pi/5) = (1 + sqrt 5)/4
+  const double c25 = 0.30901699437494742410;  // cos(2 pi/5) = (sqrt 5 - 1)/4
+  const double t16[16] = {1, c8, r2, s8, 0, -s8, -r2, -c8, -1, -c8, -r2, -s8, 0, s8, r2, c8};
+  const double t12[12] = {1, h3, 0.5, 0, -0.5, -h3, -1, -h3, -0.5, 0, 0.5, h3};
+  const double t10[10] = {1, c5, c25, -c25, -c5, -1, -c5, -c25, c25, c5};
+  const double t6[6] = {1, 0.5, -0.5, -1, -0.5, 0.5};
+  m %= R;
+  return R == 16 ? t16[m] : R == 12 ? t12[m] : R == 10 ? t10[m] : R == 6 ? t6[m] : 1.0;
+}
+constexpr double root_sin(int R, int m) {
+  const double r2 = 0.70710678118654752440;
+  const double c8 = 0.92387953251128675613;
+  const double s8 = 0.38268343236508977173;
+  const double h3 = 0.86602540378443864676;
+  const double s5 = 0.58778525229247312917;   // sin(pi/5)
+  const double s25 = 0.95105651629515357212;  // sin(2 pi/5)
+  const double t16[16] = {0, s8, r2, c8, 1, c8, r2, s8, 0, -s8, -r2, -c8, -1, -c8, -r2, -s8};
+  const double t12[12] = {0, 0.5, h3, 1, h3, 0.5, 0, -0.5, -h3, -1, -h3, -0.5};
+  const double t10[10] = {0, s5, s25, s25, s5, 0, -s5, -s25, -s25, -s5};
+  const double t6[6] = {0, h3, h3, 0, -h3, -h3};
+  m %= R;
+  return R == 16 ? t16[m] : R == 12 ? t12[m] : R == 10 ? t10[m] : R == 6 ? t6[m] : 0.0;
+}
+
+template <typename T, int R, int DIR>
+struct Dft;
+
+template <typename T, int DIR>
+struct Dft<T, 1, DIR> {
+  static __device__ __forceinline__ void run(cx<T>*) {}
+};
+
+template <typename T, int DIR>
+struct Dft<T, 2, DIR> {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    cx<T> a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+  }
+};
+
+template <typename T, int DIR>
+struct Dft<T, 3, DIR> {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    const T h = T(0.86602540378443864676);  // sin(2 pi / 3)
+    cx<T> s = v[1] + v[2], d = v[1] - v[2];
+    cx<T> m = mk<T>(v[0].x - T(0.5) * s.x, v[0].y - T(0.5) * s.y);
+    cx<T> r = rmul(h, rot<DIR>(d));
+    v[0] = v[0] + s;
+    v[1] = m + r;
+    v[2] = m - r;
+  }
+};
+
+template <typename T, int DIR>
+struct Dft<T, 4, DIR> {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    cx<T> t0 = v[0] + v[2], t1 = v[0] - v[2];
+    cx<T> t2 = v[1] + v[3], t3 = rot<DIR>(v[1] - v[3]);
+    v[0] = t0 + t2;
+    v[2] = t0 - t2;
+    v[1] = t1 + t3;
+    v[3] = t1 - t3;
+  }
+};
+
+template <typename T, int DIR>
+struct Dft<T, 5, DIR> {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    const T c1 = T(0.30901699437494742410);   // cos(2 pi/5)
+    const T c2 = T(-0.80901699437494742410);  // cos(4 pi/5)
+    const T s1 = T(0.95105651629515357212);   // sin(2 pi/5)
+    const T s2 = T(0.58778525229247312917);   // sin(4 pi/5)
+    cx<T> a0 = v[0];
+    cx<T> p1 = v[1] + v[4], d1 = v[1] - v[4];
+    cx<T> p2 = v[2] + v[3], d2 = v[2] - v[3];
+    cx<T> m1 = mk<T>(a0.x + c1 * p1.x + c2 * p2.x, a0.y + c1 * p1.y + c2 * p2.y);
+    cx<T> m2 = mk<T>(a0.x + c2 * p1.x + c1 * p2.x, a0.y + c2 * p1.y + c1 * p2.y);
+    cx<T> n1 = mk<T>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
+    cx<T> n2 = mk<T>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+    cx<T> r1 = rot<DIR>(n1), r2 = rot<DIR>(n2);
+    v[0] = a0 + p1 + p2;
+    v[1] = m1 + r1;
+    v[4] = m1 - r1;
+    v[2] = m2 + r2;
+    v[3] = m2 - r2;
+  }
+};
+
+template <typename T, int DIR>
+struct Dft<T, 8, DIR> {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    const T r2 = T(0.70710678118654752440);
+    cx<T> e[4] = {v[0], v[2], v[4], v[6]};
+    cx<T> o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<T, 4, DIR>::run(e);
+    Dft<T, 4, DIR>::run(o);
+    // o[k] *= exp(DIR i pi k / 4)
+    cx<T> w1, w3;
+    if (DIR < 0) {
+      w1 = mk<T>(r2 * (o[1].x + o[1].y), r2 * (o[1].y - o[1].x));
+      w3 = mk<T>(r2 * (o[3].y - o[3].x), -r2 * (o[3].x + o[3].y));
+    } else {
+      w1 = mk<T>(r2 * (o[1].x - o[1].y), r2 * (o[1].x + o[1].y));
+      w3 = mk<T>(-r2 * (o[3].x + o[3].y), r2 * (o[3].x - o[3].y));
+    }
+    cx<T> w2 = rot<DIR>(o[2]);
+    v[0] = e[0] + o[0];
+    v[4] = e[0] - o[0];
+    v[1] = e[1] + w1;
+    v[5] = e[1] - w1;
+    v[2] = e[2] + w2;
+    v[6] = e[2] - w2;
+    v[3] = e[3] + w3;
+    v[7] = e[3] - w3;
+  }
+};
+
+// R = A * B by decimation in time: n = B n1 + n2, k = k1 + A k2,
+// X[k1 + A k2] = sum_n2 w_B^{n2 k2} w_R^{n2 k1} sum_n1 x[B n1 + n2] w_A^{n1 k1}.
+template <typename T, int A, int B, int DIR>
+struct DftComposite {
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    constexpr int R = A * B;
+    cx<T> u[B][A];
+    static_for<0, B>([&](auto n2c) {
+      constexpr int n2 = decltype(n2c)::value;
+#pragma unroll
+      for (int n1 = 0; n1 < A; ++n1) u[n2][n1] = v[B * n1 + n2];
+      Dft<T, A, DIR>::run(u[n2]);
+      static_for<1, A>([&](auto k1c) {
+        constexpr int k1 = decltype(k1c)::value;
+        if constexpr (n2 > 0) {
+          constexpr double c = root_cos(R, n2 * k1);
+          constexpr double s = root_sin(R, n2 * k1);
+          u[n2][k1] = cmul(u[n2][k1], mk<T>(T(c), DIR < 0 ? T(-s) : T(s)));
+        }
+      });
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      cx<T> w[B];
+#pragma unroll
+      for (int n2 = 0; n2 < B; ++n2) w[n2] = u[n2][k1];
+      Dft<T, B, DIR>::run(w);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) v[k1 + A * k2] = w[k2];
+    }
+  }
+};
+
+template <typename T, int DIR>
+struct Dft<T, 6, DIR> : DftComposite<T, 3, 2, DIR> {};
+template <typename T, int DIR>
+struct Dft<T, 10, DIR> : DftComposite<T, 5, 2, DIR> {};
+template <typename T, int DIR>
+struct Dft<T, 12, DIR> : DftComposite<T, 4, 3, DIR> {};
+template <typename T, int DIR>
+struct Dft<T, 16, DIR> : DftComposite<T, 4, 4, DIR> {};
+
+}  // namespace psatd

@@ -17,165 +17,12 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <type_traits>
 
+#include "fft_codelets.cuh"
 #include "psatd_internal.h"
+#include "psatd_update.cuh"
 
 namespace psatd {
-
-template <typename T>
-using cx = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-
-template <typename T>
-__device__ __forceinline__ cx<T> mk(T a, T b) {
-  cx<T> r;
-  r.x = a;
-  r.y = b;
-  return r;
-}
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-
-template <typename C>
-__device__ __forceinline__ C cmul(C a, C b) {
-  C r;
-  r.x = a.x * b.x - a.y * b.y;
-  r.y = a.x * b.y + a.y * b.x;
-  return r;
-}
-template <typename C>
-__device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
-  C r;
-  r.x = a.x * b.x + a.y * b.y;
-  r.y = a.y * b.x - a.x * b.y;
-  return r;
-}
-template <typename C, typename T>
-__device__ __forceinline__ C rmul(T s, C a) {
-  C r;
-  r.x = s * a.x;
-  r.y = s * a.y;
-  return r;
-}
-template <typename C>
-__device__ __forceinline__ C conjg(C a) {
-  a.y = -a.y;
-  return a;
-}
-template <typename C>
-__device__ __forceinline__ C times_i(C a) {  // i * a
-  C r;
-  r.x = -a.y;
-  r.y = a.x;
-  return r;
-}
-// multiply by exp(DIR * i pi/2): DIR = -1 -> -i (forward), +1 -> +i (inverse)
-template <int DIR, typename C>
-__device__ __forceinline__ C rot(C a) {
-  C r;
-  if (DIR < 0) {
-    r.x = a.y;
-    r.y = -a.x;
-  } else {
-    r.x = -a.y;
-    r.y = a.x;
-  }
-  return r;
-}
-
-// ---------------------------------------------------------------------------
-// DFT butterflies of size R, y_k = sum_t a_t exp(DIR 2 pi i t k / R)
-// ---------------------------------------------------------------------------
-template <typename T, int R, int DIR>
-struct Dft;
-
-template <typename T, int DIR>
-struct Dft<T, 2, DIR> {
-  static __device__ __forceinline__ void run(cx<T>* v) {
-    cx<T> a = v[0], b = v[1];
-    v[0] = a + b;
-    v[1] = a - b;
-  }
-};
-
-template <typename T, int DIR>
-struct Dft<T, 3, DIR> {
-  static __device__ __forceinline__ void run(cx<T>* v) {
-    const T h = T(0.86602540378443864676);  // sin(2 pi / 3)
-    cx<T> s = v[1] + v[2], d = v[1] - v[2];
-    cx<T> m = mk<T>(v[0].x - T(0.5) * s.x, v[0].y - T(0.5) * s.y);
-    cx<T> r = rmul(h, rot<DIR>(d));
-    v[0] = v[0] + s;
-    v[1] = m + r;
-    v[2] = m - r;
-  }
-};
-
-template <typename T, int DIR>
-struct Dft<T, 4, DIR> {
-  static __device__ __forceinline__ void run(cx<T>* v) {
-    cx<T> t0 = v[0] + v[2], t1 = v[0] - v[2];
-    cx<T> t2 = v[1] + v[3], t3 = rot<DIR>(v[1] - v[3]);
-    v[0] = t0 + t2;
-    v[2] = t0 - t2;
-    v[1] = t1 + t3;
-    v[3] = t1 - t3;
-  }
-};
-
-template <typename T, int DIR>
-struct Dft<T, 5, DIR> {
-  static __device__ __forceinline__ void run(cx<T>* v) {
-    const T c1 = T(0.30901699437494742410);   // cos(2 pi/5)
-    const T c2 = T(-0.80901699437494742410);  // cos(4 pi/5)
-    const T s1 = T(0.95105651629515357212);   // sin(2 pi/5)
-    const T s2 = T(0.58778525229247312917);   // sin(4 pi/5)
-    cx<T> a0 = v[0];
-    cx<T> p1 = v[1] + v[4], d1 = v[1] - v[4];
-    cx<T> p2 = v[2] + v[3], d2 = v[2] - v[3];
-    cx<T> m1 = mk<T>(a0.x + c1 * p1.x + c2 * p2.x, a0.y + c1 * p1.y + c2 * p2.y);
-    cx<T> m2 = mk<T>(a0.x + c2 * p1.x + c1 * p2.x, a0.y + c2 * p1.y + c1 * p2.y);
-    cx<T> n1 = mk<T>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
-    cx<T> n2 = mk<T>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
-    cx<T> r1 = rot<DIR>(n1), r2 = rot<DIR>(n2);
-    v[0] = a0 + p1 + p2;
-    v[1] = m1 + r1;
-    v[4] = m1 - r1;
-    v[2] = m2 + r2;
-    v[3] = m2 - r2;
-  }
-};
-
-template <typename T, int DIR>
-struct Dft<T, 8, DIR> {
-  static __device__ __forceinline__ void run(cx<T>* v) {
-    const T r2 = T(0.70710678118654752440);
-    cx<T> e[4] = {v[0], v[2], v[4], v[6]};
-    cx<T> o[4] = {v[1], v[3], v[5], v[7]};
-    Dft<T, 4, DIR>::run(e);
-    Dft<T, 4, DIR>::run(o);
-    // o[k] *= exp(DIR i pi k / 4)
-    cx<T> w1, w3;
-    if (DIR < 0) {
-      w1 = mk<T>(r2 * (o[1].x + o[1].y), r2 * (o[1].y - o[1].x));
-      w3 = mk<T>(r2 * (o[3].y - o[3].x), -r2 * (o[3].x + o[3].y));
-    } else {
-      w1 = mk<T>(r2 * (o[1].x - o[1].y), r2 * (o[1].x + o[1].y));
-      w3 = mk<T>(-r2 * (o[3].x + o[3].y), r2 * (o[3].x - o[3].y));
-    }
-    cx<T> w2 = rot<DIR>(o[2]);
-    v[0] = e[0] + o[0];
-    v[4] = e[0] - o[0];
-    v[1] = e[1] + w1;
-    v[5] = e[1] - w1;
-    v[2] = e[2] + w2;
-    v[6] = e[2] - w2;
-    v[3] = e[3] + w3;
-    v[7] = e[3] - w3;
-  }
-};
 
 // ---------------------------------------------------------------------------
 // One Stockham pass of radix R over `nseq` sequences of length N in smem.
@@ -259,14 +106,6 @@ __device__ void fft_smem(cx<T>* buf, int nseq, int sseq, int sidx, const AxisPla
   }
 }
 
-template <typename T>
-__device__ __forceinline__ const cx<T>* cpool(const DevPlan& P) {
-  return reinterpret_cast<const cx<T>*>(P.cpool);
-}
-template <typename T>
-__device__ __forceinline__ const T* rpool(const DevPlan& P) {
-  return reinterpret_cast<const T*>(P.rpool);
-}
 
 // ---------------------------------------------------------------------------
 // S1, x axis: real rows -> half spectrum (R2C via a packed complex FFT)
@@ -337,87 +176,6 @@ __global__ void __launch_bounds__(kThreads) k_col(DevPlan P, cx<T>* spec, int64_
     const int i = e / nm, t = e - i * nm;
     g[i * stride + t] = sm[e];
   }
-}
-
-// ---------------------------------------------------------------------------
-// S2: analytical update of one mode (centred spectra; see plan docs).
-// md[s * fs] is field slot s of this mode in smem.
-// ---------------------------------------------------------------------------
-template <typename T, int FORM>
-__device__ __forceinline__ void update_mode(cx<T>* md, int fs, int mx, int my, int mz,
-                                            const ShapeDev& sh, const DevPlan& P) {
-  using C = cx<T>;
-  const T* rp = rpool<T>(P);
-  const C* cp = cpool<T>(P);
-  const int n1 = sh.n[1], n2 = sh.n[2], hx = sh.hx;
-  const T Kx = rp[sh.kx + mx], Ky = rp[sh.ky + my], Kz = rp[sh.kz + mz];
-  const C px = cp[sh.phx + mx], py = cp[sh.phy + my], pz = cp[sh.phz + mz];
-  const int myr = my <= n1 - my ? my : n1 - my;
-  const int mzr = mz <= n2 - mz ? mz : n2 - mz;
-  const Coef4<T> q = reinterpret_cast<const Coef4<T>*>(P.coef)[sh.coef +
-                                                             ((int64_t)mzr * (n1 / 2 + 1) + myr) * hx + mx];
-  const C pyz = cmul(py, pz), pxz = cmul(px, pz), pxy = cmul(px, py);
-  // centred spectra: F~ = exp(-i k.s h) F^
-  const C ex = cmulc(md[0], px), ey = cmulc(md[fs], py), ez = cmulc(md[2 * fs], pz);
-  const C bx = cmulc(md[3 * fs], pyz), by = cmulc(md[4 * fs], pxz), bz = cmulc(md[5 * fs], pxy);
-  const T cc = T(P.c) * T(P.c);
-  const T ieps = T(1.0 / P.eps0);
-  // K x B, K x E, K.B
-  const C kbx = rmul(Ky, bz) - rmul(Kz, by);
-  const C kby = rmul(Kz, bx) - rmul(Kx, bz);
-  const C kbz = rmul(Kx, by) - rmul(Ky, bx);
-  const C kex = rmul(Ky, ez) - rmul(Kz, ey);
-  const C key = rmul(Kz, ex) - rmul(Kx, ez);
-  const C kez = rmul(Kx, ey) - rmul(Ky, ex);
-  const C kdb = rmul(Kx, bx) + rmul(Ky, by) + rmul(Kz, bz);
-  const T csw = cc * q.s;
-  // B' = C B + X1 K (K.B) - i Sw K x E (+ i X1/c^2 K x J / eps0)
-  C nbx = rmul(q.c, bx) + rmul(q.x1 * Kx, kdb) - rmul(q.s, times_i(kex));
-  C nby = rmul(q.c, by) + rmul(q.x1 * Ky, kdb) - rmul(q.s, times_i(key));
-  C nbz = rmul(q.c, bz) + rmul(q.x1 * Kz, kdb) - rmul(q.s, times_i(kez));
-  C nex, ney, nez;
-  if (FORM == kRhoForm) {
-    const C rho = md[6 * fs];
-    const C jx = cmulc(md[7 * fs], px), jy = cmulc(md[8 * fs], py), jz = cmulc(md[9 * fs], pz);
-    const C kdj = rmul(Kx, jx) + rmul(Ky, jy) + rmul(Kz, jz);
-    const T dt = T(P.dt);
-    const C rhon = rho - rmul(dt, times_i(kdj));
-    const T y1 = q.x3 / dt;
-    const T y2 = -q.x1 - q.x3 / dt;
-    const C g = times_i(rmul(y1, rhon) + rmul(y2, rho));  // i (Y1 rho' + Y2 rho)
-    nex = rmul(q.c, ex) + rmul(csw, times_i(kbx)) - rmul(q.s * ieps, jx) + rmul(Kx * ieps, g);
-    ney = rmul(q.c, ey) + rmul(csw, times_i(kby)) - rmul(q.s * ieps, jy) + rmul(Ky * ieps, g);
-    nez = rmul(q.c, ez) + rmul(csw, times_i(kbz)) - rmul(q.s * ieps, jz) + rmul(Kz * ieps, g);
-    const T x2 = q.x1 / cc * ieps;
-    nbx = nbx + rmul(x2, times_i(rmul(Ky, jz) - rmul(Kz, jy)));
-    nby = nby + rmul(x2, times_i(rmul(Kz, jx) - rmul(Kx, jz)));
-    nbz = nbz + rmul(x2, times_i(rmul(Kx, jy) - rmul(Ky, jx)));
-    md[6 * fs] = rhon;
-  } else {
-    const C kde = rmul(Kx, ex) + rmul(Ky, ey) + rmul(Kz, ez);
-    nex = rmul(q.c, ex) + rmul(q.x1 * Kx, kde) + rmul(csw, times_i(kbx));
-    ney = rmul(q.c, ey) + rmul(q.x1 * Ky, kde) + rmul(csw, times_i(kby));
-    nez = rmul(q.c, ez) + rmul(q.x1 * Kz, kde) + rmul(csw, times_i(kbz));
-    if (FORM == kJForm) {
-      const C jx = cmulc(md[6 * fs], px), jy = cmulc(md[7 * fs], py), jz = cmulc(md[8 * fs], pz);
-      const C kdj = rmul(Kx, jx) + rmul(Ky, jy) + rmul(Kz, jz);
-      const T a = q.s * ieps, b = q.x3 * ieps;
-      nex = nex - rmul(a, jx) + rmul(b * Kx, kdj);
-      ney = ney - rmul(a, jy) + rmul(b * Ky, kdj);
-      nez = nez - rmul(a, jz) + rmul(b * Kz, kdj);
-      const T x2 = q.x1 / cc * ieps;
-      nbx = nbx + rmul(x2, times_i(rmul(Ky, jz) - rmul(Kz, jy)));
-      nby = nby + rmul(x2, times_i(rmul(Kz, jx) - rmul(Kx, jz)));
-      nbz = nbz + rmul(x2, times_i(rmul(Kx, jy) - rmul(Ky, jx)));
-    }
-  }
-  // back to the staggered sample positions: F^ = exp(+i k.s h) F~
-  md[0] = cmul(nex, px);
-  md[fs] = cmul(ney, py);
-  md[2 * fs] = cmul(nez, pz);
-  md[3 * fs] = cmul(nbx, pyz);
-  md[4 * fs] = cmul(nby, pxz);
-  md[5 * fs] = cmul(nbz, pxy);
 }
 
 // z forward FFT of every slot, update, z inverse FFT of the output slots.

@@ -66,7 +66,7 @@ Err validate(const psatd_plan_desc* d) {
   if (!(d->eps0 > 0.0) || !std::isfinite(d->eps0)) return {PSATD_ERR_INVALID_ARG, "eps0 must be > 0"};
   for (int a = 0; a < 3; ++a)
     if (!(d->dx[a] > 0.0) || !std::isfinite(d->dx[a])) return {PSATD_ERR_INVALID_ARG, "dx must be > 0"};
-  const uint32_t known = PSATD_VACUUM | PSATD_RHO_CONTINUITY | PSATD_NO_GRAPH;
+  const uint32_t known = PSATD_VACUUM | PSATD_RHO_CONTINUITY | PSATD_NO_GRAPH | PSATD_GENERIC_KERNELS;
   if (d->flags & ~known) return {PSATD_ERR_INVALID_ARG, "unknown flag bits"};
   if ((d->flags & PSATD_VACUUM) && (d->flags & PSATD_RHO_CONTINUITY))
     return {PSATD_ERR_INVALID_ARG, "PSATD_VACUUM and PSATD_RHO_CONTINUITY exclude each other"};
@@ -296,13 +296,19 @@ struct psatd_plan {
   std::vector<BoxDev> hboxes;
   std::vector<ShapeDev> hshapes;
   std::vector<RowJob> rows_all, rows_int;
-  std::vector<ColJob> ycols_all, ycols_int, zcols;
+  std::vector<ColJob> ycols_all, ycols_int, zcols;           // every box (standalone FFTs)
+  std::vector<RowJob> g_rows, g_rows_int;                     // push, generic boxes
+  std::vector<ColJob> g_ycols, g_ycols_int, g_zcols;
+  std::vector<int2> plane_fwd, plane_inv;                     // push, fast boxes
+  std::vector<ColJob> zfast;
+  int fast_boxes = 0;
   std::vector<CopyBlk> blocks;
   std::vector<XTile> tiles;
 
   int64_t field_total = 0;  // elements per field buffer
   int64_t spec_total = 0;   // complex elements per spectrum slot
   int smem_fx = 0, smem_y = 0, smem_z = 0, smem_zonly = 0, smem_ix = 0;
+  int smem_pf = 0, smem_pi = 0, smem_zf = 0;
 
   // device memory
   std::vector<void*> allocs;
@@ -310,6 +316,9 @@ struct psatd_plan {
   ShapeDev* d_shapes = nullptr;
   RowJob *d_rows_all = nullptr, *d_rows_int = nullptr;
   ColJob *d_ycols_all = nullptr, *d_ycols_int = nullptr, *d_zcols = nullptr;
+  RowJob *d_g_rows = nullptr, *d_g_rows_int = nullptr;
+  ColJob *d_g_ycols = nullptr, *d_g_ycols_int = nullptr, *d_g_zcols = nullptr, *d_zfast = nullptr;
+  int2 *d_plane_fwd = nullptr, *d_plane_inv = nullptr;
   CopyBlk* d_blocks = nullptr;
   XTile* d_tiles = nullptr;
   void *d_rpool = nullptr, *d_cpool = nullptr, *d_coef = nullptr;
@@ -449,6 +458,17 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     rtot += align_up(b.n[2], 4);
     s.coef = qtot;
     qtot += (int64_t)s.hx * (b.n[1] / 2 + 1) * (b.n[2] / 2 + 1);
+    s.fx = fast_code(s.L);
+    s.fy = fast_code(b.n[1]);
+    s.fz = fast_code(b.n[2]);
+    // x-pass row pitch = R2 (mod 16) and work pitch = 1 (mod 16) keep the
+    // shared-memory accesses of the plane kernels free of most bank conflicts
+    int r2x = 1;
+#define PSATD_R2(code, N, R1, R2) if (s.fx == code) r2x = R2;
+    PSATD_FAST_LENGTHS(PSATD_R2)
+#undef PSATD_R2
+    s.lp = s.L + (int)((r2x - s.L % 16 + 32) % 16);
+    s.hp = s.hx + (int)((1 - s.hx % 16 + 32) % 16);
     shape_of[key] = (int)P->hshapes.size();
     P->hshapes.push_back(s);
   }
@@ -473,16 +493,44 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   // ---- work lists
   const int csz = (int)P->csize;
   const int zbudget = 100 * 1024;
+  int dev = 0, optin = 0;
+  CK(P, cudaGetDevice(&dev));
+  CK(P, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int tile = fast_tile(P->prec);
   for (int bi = 0; bi < (int)P->boxes.size(); ++bi) {
     const psatd_box& b = P->boxes[bi];
     const int n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
     const int L = n0 / 2, hx = L + 1;
+    const ShapeDev& sh = P->hshapes[P->hboxes[bi].shape];
+    const int ni = n1 - b.ng_lo[1] - b.ng_hi[1];
+    const int sm_pf = n1 * (sh.lp + sh.hp) * csz, sm_pi = (n1 + ni) * sh.hp * csz;
+    const int sm_zf = z_fast_smem(P->prec, P->form, n2);
+    const bool fast = !(d.flags & PSATD_GENERIC_KERNELS) && sh.fx >= 0 && sh.fy >= 0 && sh.fz >= 0 &&
+                      sm_pf <= optin && sm_pi <= optin && sm_zf <= optin;
     const int rows = n1 * n2;
     const int nr = std::max(1, std::min(rows, kMaxPoints / L));
     for (int r = 0; r < rows; r += nr) P->rows_all.push_back({bi, r, std::min(nr, rows - r), 0});
     for (int z = b.ng_lo[2]; z < n2 - b.ng_hi[2]; ++z) {
       const int y0 = b.ng_lo[1], y1 = n1 - b.ng_hi[1];
       for (int y = y0; y < y1; y += nr) P->rows_int.push_back({bi, z * n1 + y, std::min(nr, y1 - y), 0});
+    }
+    if (fast) {
+      ++P->fast_boxes;
+      for (int z = 0; z < n2; ++z) {
+        P->plane_fwd.push_back(make_int2(bi, z));
+        if (z >= b.ng_lo[2] && z < n2 - b.ng_hi[2]) P->plane_inv.push_back(make_int2(bi, z));
+      }
+      for (int y = 0; y < n1; ++y)
+        for (int m = 0; m < hx; m += tile) P->zfast.push_back({bi, y, m, std::min(tile, hx - m)});
+      P->smem_pf = std::max(P->smem_pf, sm_pf);
+      P->smem_pi = std::max(P->smem_pi, sm_pi);
+      P->smem_zf = std::max(P->smem_zf, sm_zf);
+    } else {
+      for (int r = 0; r < rows; r += nr) P->g_rows.push_back({bi, r, std::min(nr, rows - r), 0});
+      for (int z = b.ng_lo[2]; z < n2 - b.ng_hi[2]; ++z) {
+        const int y0 = b.ng_lo[1], y1 = n1 - b.ng_hi[1];
+        for (int y = y0; y < y1; y += nr) P->g_rows_int.push_back({bi, z * n1 + y, std::min(nr, y1 - y), 0});
+      }
     }
     P->smem_fx = std::max(P->smem_fx, nr * L * csz);
     P->smem_ix = std::max(P->smem_ix, nr * (hx + L) * csz);
@@ -495,6 +543,10 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
         ColJob j{bi, z, m, std::min(ny, hx - m)};
         P->ycols_all.push_back(j);
         if (inner) P->ycols_int.push_back(j);
+        if (!fast) {
+          P->g_ycols.push_back(j);
+          if (inner) P->g_ycols_int.push_back(j);
+        }
       }
     }
     P->smem_y = std::max(P->smem_y, n1 * ny * csz);
@@ -502,7 +554,10 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     if (nz >= 4) nz = nz / 4 * 4;
     nz = std::min(nz, hx);
     for (int y = 0; y < n1; ++y)
-      for (int m = 0; m < hx; m += nz) P->zcols.push_back({bi, y, m, std::min(nz, hx - m)});
+      for (int m = 0; m < hx; m += nz) {
+        P->zcols.push_back({bi, y, m, std::min(nz, hx - m)});
+        if (!fast) P->g_zcols.push_back({bi, y, m, std::min(nz, hx - m)});
+      }
     P->smem_z = std::max(P->smem_z, n2 * FIN * nz * csz);
     P->smem_zonly = std::max(P->smem_zonly, n2 * nz * csz);
   }
@@ -522,6 +577,14 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   CK(P, upload(P, P->ycols_all, &P->d_ycols_all));
   CK(P, upload(P, P->ycols_int, &P->d_ycols_int));
   CK(P, upload(P, P->zcols, &P->d_zcols));
+  CK(P, upload(P, P->g_rows, &P->d_g_rows));
+  CK(P, upload(P, P->g_rows_int, &P->d_g_rows_int));
+  CK(P, upload(P, P->g_ycols, &P->d_g_ycols));
+  CK(P, upload(P, P->g_ycols_int, &P->d_g_ycols_int));
+  CK(P, upload(P, P->g_zcols, &P->d_g_zcols));
+  CK(P, upload(P, P->zfast, &P->d_zfast));
+  CK(P, upload(P, P->plane_fwd, &P->d_plane_fwd));
+  CK(P, upload(P, P->plane_inv, &P->d_plane_inv));
   CK(P, upload(P, P->blocks, &P->d_blocks));
   CK(P, upload(P, P->tiles, &P->d_tiles));
   CK(P, dalloc(P, (size_t)rtot * P->rsize, &P->d_rpool));
@@ -584,14 +647,13 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   free_tmp();
   CK(P, e);
-  const int smem = std::max({P->smem_fx, P->smem_y, P->smem_z, P->smem_zonly, P->smem_ix});
-  int dev = 0, optin = 0;
-  CK(P, cudaGetDevice(&dev));
-  CK(P, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const int smem = std::max({P->smem_fx, P->smem_y, P->smem_z, P->smem_zonly, P->smem_ix, P->smem_pf,
+                             P->smem_pi, P->smem_zf});
   if (smem > optin) return fail(P, PSATD_ERR_UNSUPPORTED_SIZE, fmt("needs %d B shared memory", smem));
   // The attribute is a per-kernel cap shared by every plan: raise it to the
   // device maximum so that no plan lowers it below another plan's need.
   CK(P, configure_kernels(P->prec, optin));
+  CK(P, configure_fast_kernels(P->prec, optin));
   return PSATD_OK;
 }
 
@@ -789,22 +851,51 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
     const int64_t S = P->spec_total;
     int64_t launches = 0;
     for (int step = 0; step < nsteps; ++step) {
-      CK(P, timed(P, 0, st, [&] {
-           return launch_fwd_x(P->prec, D, fp, FIN, P->d_ws, S, P->d_rows_all, (int64_t)P->rows_all.size(), P->smem_fx, st);
-         }));
-      CK(P, timed(P, 1, st, [&] {
-           return launch_col(P->prec, -1, 1, D, P->d_ws, S, FIN, P->d_ycols_all, (int64_t)P->ycols_all.size(), P->smem_y, st);
-         }));
-      CK(P, timed(P, 2, st, [&] {
-           return launch_z_update(P->prec, P->form, D, P->d_ws, S, P->d_zcols, (int64_t)P->zcols.size(), P->smem_z, st);
-         }));
-      CK(P, timed(P, 3, st, [&] {
-           return launch_col(P->prec, 1, 1, D, P->d_ws, S, FOUT, P->d_ycols_int, (int64_t)P->ycols_int.size(), P->smem_y, st);
-         }));
-      CK(P, timed(P, 4, st, [&] {
-           return launch_inv_x(P->prec, D, fp, FOUT, P->d_ws, S, P->d_rows_int, (int64_t)P->rows_int.size(), P->smem_ix, 1, st);
-         }));
-      launches += 5;
+      // S1: forward x+y (fast boxes: one plane kernel; generic: x rows, y columns)
+      if (!P->plane_fwd.empty()) {
+        CK(P, timed(P, 0, st, [&] {
+             return launch_plane_fwd(P->prec, D, fp, FIN, P->d_ws, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(), P->smem_pf, st);
+           }));
+        ++launches;
+      }
+      if (!P->g_rows.empty()) {
+        CK(P, timed(P, 0, st, [&] {
+             return launch_fwd_x(P->prec, D, fp, FIN, P->d_ws, S, P->d_g_rows, (int64_t)P->g_rows.size(), P->smem_fx, st);
+           }));
+        CK(P, timed(P, 1, st, [&] {
+             return launch_col(P->prec, -1, 1, D, P->d_ws, S, FIN, P->d_g_ycols, (int64_t)P->g_ycols.size(), P->smem_y, st);
+           }));
+        launches += 2;
+      }
+      // S1 (z) + S2 + S3 (z)
+      if (!P->zfast.empty()) {
+        CK(P, timed(P, 2, st, [&] {
+             return launch_z_fast(P->prec, P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->smem_zf, st);
+           }));
+        ++launches;
+      }
+      if (!P->g_zcols.empty()) {
+        CK(P, timed(P, 2, st, [&] {
+             return launch_z_update(P->prec, P->form, D, P->d_ws, S, P->d_g_zcols, (int64_t)P->g_zcols.size(), P->smem_z, st);
+           }));
+        ++launches;
+      }
+      // S3: inverse y+x, interior cells only
+      if (!P->plane_inv.empty()) {
+        CK(P, timed(P, 4, st, [&] {
+             return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv, (int64_t)P->plane_inv.size(), P->smem_pi, st);
+           }));
+        ++launches;
+      }
+      if (!P->g_rows.empty()) {
+        CK(P, timed(P, 3, st, [&] {
+             return launch_col(P->prec, 1, 1, D, P->d_ws, S, FOUT, P->d_g_ycols_int, (int64_t)P->g_ycols_int.size(), P->smem_y, st);
+           }));
+        CK(P, timed(P, 4, st, [&] {
+             return launch_inv_x(P->prec, D, fp, FOUT, P->d_ws, S, P->d_g_rows_int, (int64_t)P->g_rows_int.size(), P->smem_ix, 1, st);
+           }));
+        launches += 2;
+      }
       if (!P->tiles.empty()) {
         CK(P, timed(P, 5, st, [&] {
              return launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_tiles, (int64_t)P->tiles.size(), st);
@@ -880,6 +971,8 @@ const char* psatd_last_error(const psatd_plan* p) {
 }
 
 int64_t psatd_last_launch_count(const psatd_plan* p) { return p ? p->last_launches : 0; }
+
+int32_t psatd_plan_fast_boxes(const psatd_plan* p) { return p ? p->fast_boxes : -1; }
 
 psatd_status psatd_plan_set_timing(psatd_plan* P, int32_t enable) {
   if (!P) return PSATD_ERR_INVALID_ARG;

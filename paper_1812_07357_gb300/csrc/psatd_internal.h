@@ -44,7 +44,23 @@ struct ShapeDev {
   int64_t kx, ky, kz;             // modified wavenumbers, hx / n1 / n2      (real pool)
   int64_t phx, phy, phz;          // exp(i k h / 2), hx / n1 / n2            (complex pool)
   int64_t coef;                   // hx*(n1/2+1)*(n2/2+1) coefficient quads (coef pool)
+  int32_t fx, fy, fz;             // fast-length codes of L, n1, n2 (-1: not a fast length)
+  int32_t lp, hp;                 // smem row pitches (complex) of the fast plane kernels
 };
+
+// Lengths with a two-pass register FFT, N = R1 * R2: X(code, N, R1, R2).
+#define PSATD_FAST_LENGTHS(X)                                                          \
+  X(0, 24, 8, 3) X(1, 30, 6, 5) X(2, 32, 8, 4) X(3, 40, 8, 5) X(4, 48, 8, 6)              \
+  X(5, 60, 12, 5) X(6, 64, 8, 8) X(7, 80, 10, 8) X(8, 96, 12, 8) X(9, 120, 12, 10)       \
+  X(10, 128, 16, 8)
+
+inline int fast_code(int n) {
+#define PSATD_CODE(code, N, R1, R2) \
+  if (n == N) return code;
+  PSATD_FAST_LENGTHS(PSATD_CODE)
+#undef PSATD_CODE
+  return -1;
+}
 
 struct BoxDev {
   int32_t n[3];
@@ -121,6 +137,18 @@ cudaError_t launch_exchange(int prec, const DevPlan& P, const FieldPtrs& f, int 
                             cudaStream_t st);
 // Maximum dynamic shared memory opt-in for all kernels of a precision.
 cudaError_t configure_kernels(int prec, int smem_bytes);
+
+// ---- fast path (fast_kernels.cu): boxes whose three FFT lengths are fast --
+// jobs: (box, z plane); forward writes every plane, inverse takes interior z.
+cudaError_t launch_plane_fwd(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                             int64_t sstride, const int2* jobs, int64_t njobs, int smem, cudaStream_t st);
+cudaError_t launch_plane_inv(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                             int64_t sstride, const int2* jobs, int64_t njobs, int smem, cudaStream_t st);
+cudaError_t launch_z_fast(int prec, int form, const DevPlan& P, void* spec, int64_t sstride,
+                          const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+int fast_tile(int prec);                        // mx columns per k_z_fast job
+int z_fast_smem(int prec, int form, int n2);    // bytes of shared memory of k_z_fast
+cudaError_t configure_fast_kernels(int prec, int smem_bytes);
 
 // ---- host helpers (plan.cpp) ------------------------------------------------
 // Radix schedule of a complex FFT length (false if it is not 5-smooth).

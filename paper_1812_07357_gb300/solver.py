@@ -17,7 +17,8 @@ _DECOMP = {"global": A.PSATD_DECOMP_GLOBAL, "local": A.PSATD_DECOMP_LOCAL,
 COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
-def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no_graph=False):
+def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no_graph=False,
+              generic=False):
     """psatd_plan_desc for an ``inputs.Layout``; the returned object keeps the
     box array alive (attribute ``_boxes``)."""
     nb = len(layout.boxes)
@@ -40,6 +41,8 @@ def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no
     flags = {"vacuum": A.PSATD_VACUUM, "J": 0, "rho": A.PSATD_RHO_CONTINUITY}[sources]
     if no_graph:
         flags |= A.PSATD_NO_GRAPH
+    if generic:
+        flags |= A.PSATD_GENERIC_KERNELS
     d.flags = flags
     d._boxes = arr
     return d
@@ -49,7 +52,7 @@ class Plan:
     """A PSATD plan on the current CUDA device."""
 
     def __init__(self, layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum",
-                 stream=None, no_graph=False):
+                 stream=None, no_graph=False, generic=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -60,7 +63,7 @@ class Plan:
         self.dtype = torch.float32 if precision == 32 else torch.float64
         self.cdtype = torch.complex64 if precision == 32 else torch.complex128
         self.np_dtype = np.float32 if precision == 32 else np.float64
-        self.desc = make_desc(layout, h, dt, c, eps0, precision, sources, no_graph)
+        self.desc = make_desc(layout, h, dt, c, eps0, precision, sources, no_graph, generic)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = A.psatd_plan_create(self.desc, self.stream.cuda_stream)
         self.offsets = [A.psatd_plan_layout(self.handle, i) for i in range(len(layout.boxes))]
@@ -69,6 +72,7 @@ class Plan:
         fb, wb = A.psatd_plan_memory(self.handle)
         self.field_elems = fb // (4 if precision == 32 else 8)
         self.workspace_bytes = wb
+        self.fast_boxes = A.psatd_plan_fast_boxes(self.handle)
         last = self.spec_offsets[-1]
         self.spec_elems = last[0] + last[1] + 64
 

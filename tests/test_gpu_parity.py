@@ -233,3 +233,66 @@ def test_errors_are_reported_not_raised_on_device():
     plan.push(f, s, 1)
     plan.sync()
     plan.close()
+
+
+# ---------------------------------------------------------------------------
+# fast path (two-pass register FFT kernels) on fast box sizes
+# ---------------------------------------------------------------------------
+
+def _fast_plan_check(lay, fields, src, nsteps, h, dt, prec, form, expect_fast):
+    plan = Plan(lay, h, dt, precision=prec, sources=form)
+    assert plan.fast_boxes == expect_fast, (plan.fast_boxes, expect_fast)
+    plan.close()
+    return check_push(lay, fields, src, nsteps, h, dt, prec, form)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_fast_local_48(prec):
+    """8 local boxes of 48^3 (32^3 + 8 guards), p = 16, laser, 4 steps."""
+    lay = I.local_layout((64, 64, 64), (2, 2, 2), 8, 16)
+    f = I.laser_fields((64, 64, 64), wavelength=8.0, waist=8.0, duration=5.0)
+    fields = {k: I.scatter_global(v, lay) for k, v in f.items()}
+    _fast_plan_check(lay, fields, {}, 4, (1.0,) * 3, 0.9, prec, "vacuum", 8)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_fast_uneven_rho(prec):
+    """Self-periodic boxes with fast sizes {48, 60, 80} per axis, rho form."""
+    lay = I.independent_layout(seed=11, nboxes=4, sizes=(48, 60, 80), ngs=(4, 8), min_interior=16)
+    rng = np.random.default_rng(12)
+    js = {k: [] for k in ("Jx", "Jy", "Jz")}
+    for b in lay.boxes:
+        j = I.band_limited_current(b.interior, rng)
+        for k in js:
+            js[k].append(j[k])
+    src = {k: I.scatter_self(v, lay) for k, v in js.items()}
+    src["rho"] = I.zeros(lay)
+    fields = {k: I.zeros(lay) for k in O.COMPS}
+    _fast_plan_check(lay, fields, src, 3, (1.0,) * 3, 0.9, prec, "rho", 4)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_fast_global_jform_anisotropic(prec):
+    """One 60 x 48 x 80 periodic box (all three lengths fast), J form."""
+    lay = I.global_layout((60, 48, 80), 8)
+    rng = np.random.default_rng(13)
+    src = {k: [rng.standard_normal(lay.boxes[0].shape)] for k in ("Jx", "Jy", "Jz")}
+    fields = {k: [rng.standard_normal(lay.boxes[0].shape)] for k in O.COMPS}
+    _fast_plan_check(lay, fields, src, 3, (1.0, 0.9, 1.1), 0.8, prec, "J", 1)
+
+
+def test_fast_equals_generic_fp32():
+    """The fast and the generic kernels give the same FP32 push."""
+    lay = I.local_layout((64, 128, 64), (2, 2, 1), (8, 16, 0), 32)
+    f = I.laser_fields((64, 128, 64), wavelength=8.0, waist=8.0, duration=5.0)
+    fields = {k: I.round_to(I.scatter_global(v, lay), np.float32) for k, v in f.items()}
+    outs = []
+    for generic in (False, True):
+        plan = Plan(lay, (1.0,) * 3, 0.9, precision=32, sources="vacuum", generic=generic)
+        assert plan.fast_boxes == (0 if generic else 4)
+        df = plan.pack_fields(fields)
+        plan.push(df, None, 5)
+        plan.sync()
+        outs.append(plan.unpack_fields(df))
+        plan.close()
+    assert O.rel_l2_fields(lay, outs[0], outs[1], O.COMPS) < 2e-6
