@@ -5,22 +5,62 @@
 // non-periodic domain: zero).  A tile is a run of rows of one block; a row is
 // ext[0] consecutive cells in both the source and the destination box.  Reads
 // touch interior cells only and writes guard cells only, so tiles never race.
+// Where both rows start on 16-byte boundaries and ext[0] fills whole 16-byte
+// units, a thread moves 16 bytes at a time (XTile::vec > 1).
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "psatd_internal.h"
 
 namespace psatd {
 
+namespace {
+
+// e / d for 0 <= e < 2^24, d > 0, with inv = 1.0f / d.
+__device__ __forceinline__ int div_small(int e, int d, float inv) {
+  int q = __float2int_rz((float)e * inv);
+  q += (q + 1) * d <= e;
+  q -= q * d > e;
+  return q;
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void copy_tile(T* base, const CopyBlk& b, const XTile& t, const BoxDev& db,
+                                          int64_t sfoff, int64_t sn0, int64_t sn1) {
+  using Vec = typename std::conditional<V == 1, T, float4>::type;
+  const int ex = b.ext[0], ey = b.ext[1];
+  const int upr = ex / V;
+  const float inv_upr = 1.0f / upr, inv_ey = 1.0f / ey;
+  const int64_t dn0 = db.n[0], dn1 = db.n[1];
+  const int units = t.nrows * upr;
+  for (int u = threadIdx.x; u < units; u += blockDim.x) {
+    const int rr = div_small(u, upr, inv_upr);
+    const int x = (u - rr * upr) * V;
+    const int r = t.row0 + rr;
+    const int rz = div_small(r, ey, inv_ey);
+    const int ry = r - rz * ey;
+    const int64_t d = db.foff + ((int64_t)(b.dst_lo[2] + rz) * dn1 + (b.dst_lo[1] + ry)) * dn0 +
+                      b.dst_lo[0] + x;
+    Vec v;
+    if (b.src_box >= 0) {
+      const int64_t s = sfoff + ((int64_t)(b.src_lo[2] + rz) * sn1 + (b.src_lo[1] + ry)) * sn0 +
+                        b.src_lo[0] + x;
+      v = *reinterpret_cast<const Vec*>(base + s);
+    } else {
+      v = Vec{};
+    }
+    *reinterpret_cast<Vec*>(base + d) = v;
+  }
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_exchange(DevPlan P, FieldPtrs F,
-                                                  const CopyBlk* __restrict__ blocks,
+__global__ void __launch_bounds__(256) k_exchange(DevPlan P, FieldPtrs F, const CopyBlk* __restrict__ blocks,
                                                   const XTile* __restrict__ tiles) {
   const XTile t = tiles[blockIdx.x];
   const CopyBlk b = blocks[t.blk];
   T* base = reinterpret_cast<T*>(F.p[blockIdx.y]);
   const BoxDev db = P.boxes[b.dst_box];
-  const int ex = b.ext[0], ey = b.ext[1];
-  const int64_t dn0 = db.n[0], dn1 = db.n[1];
   int64_t sfoff = 0, sn0 = 0, sn1 = 0;
   if (b.src_box >= 0) {
     const BoxDev sb = P.boxes[b.src_box];
@@ -28,23 +68,13 @@ __global__ void __launch_bounds__(256) k_exchange(DevPlan P, FieldPtrs F,
     sn0 = sb.n[0];
     sn1 = sb.n[1];
   }
-  const int count = t.nrows * ex;
-  for (int e = threadIdx.x; e < count; e += blockDim.x) {
-    const int rr = e / ex;
-    const int x = e - rr * ex;
-    const int r = t.row0 + rr;
-    const int ry = r % ey, rz = r / ey;
-    const int64_t d = db.foff + ((int64_t)(b.dst_lo[2] + rz) * dn1 + (b.dst_lo[1] + ry)) * dn0 +
-                      b.dst_lo[0] + x;
-    T v = T(0);
-    if (b.src_box >= 0) {
-      const int64_t s = sfoff + ((int64_t)(b.src_lo[2] + rz) * sn1 + (b.src_lo[1] + ry)) * sn0 +
-                        b.src_lo[0] + x;
-      v = base[s];
-    }
-    base[d] = v;
-  }
+  if (t.vec > 1)
+    copy_tile<T, 16 / sizeof(T)>(base, b, t, db, sfoff, sn0, sn1);
+  else
+    copy_tile<T, 1>(base, b, t, db, sfoff, sn0, sn1);
 }
+
+}  // namespace
 
 cudaError_t launch_exchange(int prec, const DevPlan& P, const FieldPtrs& f, int nf,
                             const CopyBlk* blocks, const XTile* tiles, int64_t ntiles,

@@ -2,19 +2,23 @@
 // N = R1 * R2 with both factors in the register codelet set (list in
 // psatd_internal.h, PSATD_FAST_LENGTHS).  Three kernels per step:
 //
-//   k_plane_fwd   one (box, field, z) plane: real rows -> R2C along x ->
-//                 complex FFT along y -> half spectrum plane in HBM.
-//   k_z_fast      one (box, y, mx tile): z FFT of every field slot, loaded
+//   k_plane_fwd   (box, field, z) planes: real rows -> R2C along x -> complex
+//                 FFT along y -> half-spectrum plane in HBM.
+//   k_z_fast      (box, y, mx tile): z FFT of every field slot, loaded
 //                 straight from HBM into registers; k-space update; inverse z
 //                 FFT of the output slots, stored straight to HBM.
-//   k_plane_inv   one (box, field, interior z) plane: inverse y FFT -> C2R
-//                 along x for interior rows -> interior cells to HBM.
+//   k_plane_inv   (box, field, interior z) planes: inverse y FFT -> C2R along
+//                 x for interior rows -> interior cells to HBM.
 //
 // Every 1D FFT is a two-pass ("four-step") transform: pass 1 takes R1
 // elements at stride R2, does DFT_R1 in registers and multiplies by
 // w_N^(n2 k1); pass 2 takes R2 consecutive pass-1 results and does DFT_R2,
 // giving X[k1 + R1 k2] in natural order.  Shared memory holds the data
-// between the passes; all index arithmetic inside a pass is compile-time.
+// between the passes.
+//
+// The plane kernels are persistent: each CTA walks the plane list with a
+// stride of gridDim.x and loads plane i+1 into its second shared-memory
+// buffer with cp.async while it transforms plane i.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -27,13 +31,19 @@ namespace psatd {
 
 namespace {
 
+constexpr int kPlaneThreads = 512;
+constexpr int kMaxPlaneRows = 128;   // largest n1 of a fast box
+
+// Longest x half-length L = n0/2 the plane kernels take (their in-place x
+// pass keeps L/4 complex values per thread in registers).
+template <typename T>
+constexpr int max_plane_x() {
+  return sizeof(T) == 4 ? 64 : 48;
+}
+
 template <typename T>
 __device__ __forceinline__ const cx<T>* ctab(const DevPlan& P) {
   return reinterpret_cast<const cx<T>*>(P.cpool);
-}
-template <typename T>
-__device__ __forceinline__ const T* rtab(const DevPlan& P) {
-  return reinterpret_cast<const T*>(P.rpool);
 }
 
 // e / d for 0 <= e < 2^24, d > 0, with inv = 1.0f / d.
@@ -43,6 +53,14 @@ __device__ __forceinline__ int div_small(int e, int d, float inv) {
   q -= q * d > e;
   return q;
 }
+
+// asynchronous 16-byte global -> shared copies (bypassing L1)
+__device__ __forceinline__ void cp16(void* s, const void* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // pass 1, in place: column c, positions n1*R2 + n2 (n1 < R1); DFT_R1 along
@@ -101,31 +119,67 @@ __device__ __forceinline__ void pass2(const cx<T>* buf, int ncol, int cs, int ns
   }
 }
 
-// ---------------------------------------------------------------------------
-// forward plane: x (R2C) then y
-// ---------------------------------------------------------------------------
-template <typename T, int R1, int R2>
-__device__ __forceinline__ void plane_x_fwd(cx<T>* in, cx<T>* work, const cx<T>* g, int n1, int lp,
-                                            int hp, const cx<T>* __restrict__ twx,
-                                            const cx<T>* __restrict__ post) {
-  constexpr int L = R1 * R2;
-  // load: n1 rows of L complex (pairs of reals), contiguous in HBM
-  for (int e = threadIdx.x; e < n1 * L; e += blockDim.x) {
-    const int y = e / L, x = e - y * L;
-    in[y * lp + x] = g[e];
+// pass 2 along rows (ns = 1), in place: every thread first loads and
+// transforms its items (at most MAXI), then all store in natural order.
+template <typename T, int R1, int R2, int DIR>
+__device__ __forceinline__ void pass2_rows_inplace(cx<T>* buf, int nrows, int pitch) {
+  constexpr int MAXI = (kMaxPlaneRows * R1 + kPlaneThreads - 1) / kPlaneThreads;
+  const int items = nrows * R1;
+  cx<T> u[MAXI][R2];
+#pragma unroll
+  for (int i = 0; i < MAXI; ++i) {
+    const int it = threadIdx.x + i * kPlaneThreads;
+    if (it < items) {
+      const int c = it / R1, k1 = it - c * R1;
+      const cx<T>* p = buf + c * pitch + k1 * R2;
+#pragma unroll
+      for (int j = 0; j < R2; ++j) u[i][j] = p[j];
+      Dft<T, R2, DIR>::run(u[i]);
+    }
   }
   __syncthreads();
-  pass1<T, R1, R2, -1, false>(in, n1, lp, 1, twx, 0.f);
+#pragma unroll
+  for (int i = 0; i < MAXI; ++i) {
+    const int it = threadIdx.x + i * kPlaneThreads;
+    if (it < items) {
+      const int c = it / R1, k1 = it - c * R1;
+      cx<T>* p = buf + c * pitch + k1;
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) p[R1 * k2] = u[i][k2];
+    }
+  }
+}
+
+// Issue the cp.async copies of `rows` rows of `row_bytes` (multiple of 16)
+// from contiguous global memory into shared rows of `pitch_bytes`.
+__device__ __forceinline__ void load_rows_async(void* dst, const void* src, int rows, int row_bytes,
+                                                int pitch_bytes) {
+  const int upr = row_bytes >> 4;
+  const int total = rows * upr;
+  const float inv = 1.0f / upr;
+  for (int u = threadIdx.x; u < total; u += blockDim.x) {
+    const int r = div_small(u, upr, inv), x = u - r * upr;
+    cp16(static_cast<char*>(dst) + r * pitch_bytes + x * 16, static_cast<const char*>(src) + (size_t)u * 16);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// forward plane: x (R2C) then y, in place in one buffer of pitch lp >= hx
+// ---------------------------------------------------------------------------
+template <typename T, int R1, int R2>
+__device__ __forceinline__ void plane_x_fwd(cx<T>* buf, int n1, int lp, const cx<T>* __restrict__ twx,
+                                            const cx<T>* __restrict__ post) {
+  constexpr int L = R1 * R2;
+  pass1<T, R1, R2, -1, false>(buf, n1, lp, 1, twx, 0.f);
   __syncthreads();
-  pass2<T, R1, R2, -1, false>(in, n1, lp, 1, 0.f,
-                              [&](int c, int k, cx<T> v) { work[c * hp + k] = v; });
+  pass2_rows_inplace<T, R1, R2, -1>(buf, n1, lp);
   __syncthreads();
   // R2C split in place, one thread per pair (k, L-k):
   // X[k] = (Z[k] + conj Z[L-k])/2 - i w^k (Z[k] - conj Z[L-k])/2
   constexpr int H = L / 2 + 1;
   for (int e = threadIdx.x; e < n1 * H; e += blockDim.x) {
     const int y = e / H, k = e - y * H;
-    cx<T>* row = work + y * hp;
+    cx<T>* row = buf + y * lp;
     const cx<T> a = row[k];
     const cx<T> b = row[k == 0 ? 0 : L - k];
     // A = (a + conj b)/2, Bv = (a - conj b)/(2i)
@@ -136,82 +190,103 @@ __device__ __forceinline__ void plane_x_fwd(cx<T>* in, cx<T>* work, const cx<T>*
       row[L] = mk<T>(A.x - Bv.x, A.y - Bv.y);
     } else {
       row[k] = A + cmul(post[k], Bv);
-      if (2 * k != L) {
-        // partner: A' = conj A, Bv' = conj Bv
-        row[L - k] = conjg(A) + cmul(post[L - k], conjg(Bv));
-      }
+      // partner: A' = conj A, Bv' = conj Bv
+      if (2 * k != L) row[L - k] = conjg(A) + cmul(post[L - k], conjg(Bv));
     }
   }
 }
 
 template <typename T, int R1, int R2>
-__device__ __forceinline__ void plane_y_fwd(cx<T>* work, int hx, int hp, cx<T>* out,
+__device__ __forceinline__ void plane_y_fwd(cx<T>* buf, int hx, int lp, cx<T>* out,
                                             const cx<T>* __restrict__ twy) {
   const float inv = 1.0f / hx;
-  pass1<T, R1, R2, -1, true>(work, hx, 1, hp, twy, inv);
+  pass1<T, R1, R2, -1, true>(buf, hx, 1, lp, twy, inv);
   __syncthreads();
-  pass2<T, R1, R2, -1, true>(work, hx, 1, hp, inv,
+  pass2<T, R1, R2, -1, true>(buf, hx, 1, lp, inv,
                              [&](int c, int k, cx<T> v) { out[k * hx + c] = v; });
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_plane_fwd(DevPlan P, FieldPtrs F, cx<T>* spec, int64_t sstride,
-                                                      const int2* __restrict__ jobs) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int2 J = jobs[blockIdx.x];
-  const int f = blockIdx.y;
+__device__ __forceinline__ void fwd_issue(const DevPlan& P, const FieldPtrs& F, const int2* jobs, int nplanes,
+                                          int j, cx<T>* buf) {
+  const int f = j / nplanes;
+  const int2 J = jobs[j - f * nplanes];
   const BoxDev bx = P.boxes[J.x];
   const ShapeDev& sh = P.shapes[bx.shape];
-  const int n1 = bx.n[1], hx = sh.hx, L = sh.L;
-  const int lp = sh.lp, hp = sh.hp;
-  cx<T>* in = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* work = in + n1 * lp;
-  const cx<T>* g = reinterpret_cast<const cx<T>*>(reinterpret_cast<const T*>(F.p[f]) + bx.foff) +
-                   (int64_t)J.y * n1 * L;
-  const cx<T>* twx = ctab<T>(P) + sh.ax.tw;
-  const cx<T>* post = ctab<T>(P) + sh.post;
-  switch (sh.fx) {
-#define PSATD_ARM(code, N, R1, R2) \
-  case code: plane_x_fwd<T, R1, R2>(in, work, g, n1, lp, hp, twx, post); break;
-    PSATD_FAST_LENGTHS(PSATD_ARM)
+  const int n0 = bx.n[0], n1 = bx.n[1];
+  const T* g = reinterpret_cast<const T*>(F.p[f]) + bx.foff + (int64_t)J.y * n1 * n0;
+  load_rows_async(buf, g, n1, n0 * (int)sizeof(T), sh.lp * (int)sizeof(cx<T>));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPlaneThreads, sizeof(T) == 4 ? 2 : 1)
+    k_plane_fwd(DevPlan P, FieldPtrs F, cx<T>* spec, int64_t sstride, const int2* __restrict__ jobs,
+                int nplanes, int nf, int bufsz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* bufs = reinterpret_cast<cx<T>*>(smem_raw);
+  const int total = nplanes * nf;
+  int j = blockIdx.x;
+  if (j >= total) return;
+  int cur = 0;
+  fwd_issue<T>(P, F, jobs, nplanes, j, bufs);
+  cp_commit();
+  for (; j < total; j += gridDim.x) {
+    const int jn = j + gridDim.x;
+    if (jn < total) fwd_issue<T>(P, F, jobs, nplanes, jn, bufs + (cur ^ 1) * bufsz);
+    cp_commit();
+    cp_wait_prev();
+    __syncthreads();
+    cx<T>* buf = bufs + cur * bufsz;
+    const int f = j / nplanes;
+    const int2 J = jobs[j - f * nplanes];
+    const BoxDev bx = P.boxes[J.x];
+    const ShapeDev& sh = P.shapes[bx.shape];
+    const int n1 = bx.n[1], hx = sh.hx, lp = sh.lp;
+    const cx<T>* twx = ctab<T>(P) + sh.ax.tw;
+    const cx<T>* post = ctab<T>(P) + sh.post;
+    switch (sh.fx) {
+#define PSATD_ARM(code, N, R1, R2)                                   \
+  case code:                                                         \
+    if constexpr (N <= max_plane_x<T>()) plane_x_fwd<T, R1, R2>(buf, n1, lp, twx, post); \
+    break;
+      PSATD_FAST_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
-    default: break;
-  }
-  __syncthreads();
-  cx<T>* out = spec + f * sstride + bx.soff + (int64_t)J.y * n1 * hx;
-  const cx<T>* twy = ctab<T>(P) + sh.ay.tw;
-  switch (sh.fy) {
+      default: break;
+    }
+    __syncthreads();
+    cx<T>* out = spec + f * sstride + bx.soff + (int64_t)J.y * n1 * hx;
+    const cx<T>* twy = ctab<T>(P) + sh.ay.tw;
+    switch (sh.fy) {
 #define PSATD_ARM(code, N, R1, R2) \
-  case code: plane_y_fwd<T, R1, R2>(work, hx, hp, out, twy); break;
-    PSATD_FAST_LENGTHS(PSATD_ARM)
+  case code: plane_y_fwd<T, R1, R2>(buf, hx, lp, out, twy); break;
+      PSATD_FAST_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
-    default: break;
+      default: break;
+    }
+    __syncthreads();
+    cur ^= 1;
   }
 }
 
 // ---------------------------------------------------------------------------
-// inverse plane: y then C2R along x, interior rows and cells only
+// inverse plane: y then C2R along x, interior rows and cells only.  The
+// spectrum plane is copied as is (pitch hx); interior rows go to a second
+// buffer of pitch hp.
 // ---------------------------------------------------------------------------
 template <typename T, int R1, int R2>
-__device__ __forceinline__ void plane_y_inv(cx<T>* work, const cx<T>* g, int hx, int hp, cx<T>* out,
-                                            int ylo, int yhi, const cx<T>* __restrict__ twy) {
-  constexpr int N = R1 * R2;
+__device__ __forceinline__ void plane_y_inv(cx<T>* buf, int hx, cx<T>* rows, int hp, int ylo, int yhi,
+                                            const cx<T>* __restrict__ twy) {
   const float inv = 1.0f / hx;
-  for (int e = threadIdx.x; e < N * hx; e += blockDim.x) {
-    const int y = div_small(e, hx, inv), x = e - y * hx;
-    work[y * hp + x] = g[e];
-  }
+  pass1<T, R1, R2, 1, true>(buf, hx, 1, hx, twy, inv);
   __syncthreads();
-  pass1<T, R1, R2, 1, true>(work, hx, 1, hp, twy, inv);
-  __syncthreads();
-  pass2<T, R1, R2, 1, true>(work, hx, 1, hp, inv, [&](int c, int k, cx<T> v) {
-    if (k >= ylo && k < yhi) out[(k - ylo) * hp + c] = v;
+  pass2<T, R1, R2, 1, true>(buf, hx, 1, hx, inv, [&](int c, int k, cx<T> v) {
+    if (k >= ylo && k < yhi) rows[(k - ylo) * hp + c] = v;
   });
 }
 
 template <typename T, int R1, int R2>
-__device__ __forceinline__ void plane_x_inv(cx<T>* rows, int nrows, int hp, T* gout, int n0,
-                                            int xlo, int xhi, T scale, const cx<T>* __restrict__ twx,
+__device__ __forceinline__ void plane_x_inv(cx<T>* rows, int nrows, int hp, T* gout, int n0, int xlo,
+                                            int xhi, T scale, const cx<T>* __restrict__ twx,
                                             const cx<T>* __restrict__ post) {
   constexpr int L = R1 * R2;
   constexpr int H = L / 2 + 1;
@@ -223,10 +298,7 @@ __device__ __forceinline__ void plane_x_inv(cx<T>* rows, int nrows, int hp, T* g
     const cx<T> a = row[k];
     const cx<T> b = row[L - k];
     const cx<T> za = (a + conjg(b)) + times_i(cmulc(a - conjg(b), post[k]));
-    if (k != 0 && 2 * k != L) {
-      const cx<T> zb = (b + conjg(a)) + times_i(cmulc(b - conjg(a), post[L - k]));
-      row[L - k] = zb;
-    }
+    if (k != 0 && 2 * k != L) row[L - k] = (b + conjg(a)) + times_i(cmulc(b - conjg(a), post[L - k]));
     row[k] = za;
   }
   __syncthreads();
@@ -234,46 +306,80 @@ __device__ __forceinline__ void plane_x_inv(cx<T>* rows, int nrows, int hp, T* g
   __syncthreads();
   pass2<T, R1, R2, 1, false>(rows, nrows, hp, 1, 0.f, [&](int r, int m, cx<T> v) {
     T* o = gout + (int64_t)r * n0 + 2 * m;
-    if (2 * m >= xlo && 2 * m < xhi) o[0] = scale * v.x;
-    if (2 * m + 1 >= xlo && 2 * m + 1 < xhi) o[1] = scale * v.y;
+    if (2 * m >= xlo && 2 * m + 1 < xhi) {
+      cx<T> w = mk<T>(scale * v.x, scale * v.y);
+      *reinterpret_cast<cx<T>*>(o) = w;
+    } else {
+      if (2 * m >= xlo && 2 * m < xhi) o[0] = scale * v.x;
+      if (2 * m + 1 >= xlo && 2 * m + 1 < xhi) o[1] = scale * v.y;
+    }
   });
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 4 ? 2 : 1) k_plane_inv(DevPlan P, FieldPtrs F, const cx<T>* spec,
-                                                      int64_t sstride, const int2* __restrict__ jobs) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int2 J = jobs[blockIdx.x];
-  const int f = blockIdx.y;
+__device__ __forceinline__ void inv_issue(const DevPlan& P, const cx<T>* spec, int64_t sstride,
+                                          const int2* jobs, int nplanes, int j, cx<T>* buf) {
+  const int f = j / nplanes;
+  const int2 J = jobs[j - f * nplanes];
   const BoxDev bx = P.boxes[J.x];
   const ShapeDev& sh = P.shapes[bx.shape];
-  const int n0 = bx.n[0], n1 = bx.n[1], hx = sh.hx, hp = sh.hp;
-  const int ylo = bx.ng_lo[1], yhi = n1 - bx.ng_hi[1];
-  cx<T>* work = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* rows = work + n1 * hp;
+  const int n1 = bx.n[1], hx = sh.hx;
   const cx<T>* g = spec + f * sstride + bx.soff + (int64_t)J.y * n1 * hx;
-  const cx<T>* twy = ctab<T>(P) + sh.ay.tw;
-  switch (sh.fy) {
+  const int bytes = n1 * hx * (int)sizeof(cx<T>);
+  load_rows_async(buf, g, 1, bytes, bytes);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPlaneThreads, sizeof(T) == 4 ? 2 : 1)
+    k_plane_inv(DevPlan P, FieldPtrs F, const cx<T>* spec, int64_t sstride, const int2* __restrict__ jobs,
+                int nplanes, int nf, int bufsz) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* bufs = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* rows = bufs + 2 * bufsz;
+  const int total = nplanes * nf;
+  int j = blockIdx.x;
+  if (j >= total) return;
+  int cur = 0;
+  inv_issue<T>(P, spec, sstride, jobs, nplanes, j, bufs);
+  cp_commit();
+  for (; j < total; j += gridDim.x) {
+    const int jn = j + gridDim.x;
+    if (jn < total) inv_issue<T>(P, spec, sstride, jobs, nplanes, jn, bufs + (cur ^ 1) * bufsz);
+    cp_commit();
+    cp_wait_prev();
+    __syncthreads();
+    cx<T>* buf = bufs + cur * bufsz;
+    const int f = j / nplanes;
+    const int2 J = jobs[j - f * nplanes];
+    const BoxDev bx = P.boxes[J.x];
+    const ShapeDev& sh = P.shapes[bx.shape];
+    const int n0 = bx.n[0], n1 = bx.n[1], hx = sh.hx, hp = sh.hp;
+    const int ylo = bx.ng_lo[1], yhi = n1 - bx.ng_hi[1];
+    const cx<T>* twy = ctab<T>(P) + sh.ay.tw;
+    switch (sh.fy) {
 #define PSATD_ARM(code, N, R1, R2) \
-  case code: plane_y_inv<T, R1, R2>(work, g, hx, hp, rows, ylo, yhi, twy); break;
-    PSATD_FAST_LENGTHS(PSATD_ARM)
+  case code: plane_y_inv<T, R1, R2>(buf, hx, rows, hp, ylo, yhi, twy); break;
+      PSATD_FAST_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
-    default: break;
-  }
-  __syncthreads();
-  const T scale = T(1.0 / ((double)n0 * n1 * bx.n[2]));
-  T* gout = reinterpret_cast<T*>(F.p[f]) + bx.foff + ((int64_t)J.y * n1 + ylo) * n0;
-  const cx<T>* twx = ctab<T>(P) + sh.ax.tw;
-  const cx<T>* post = ctab<T>(P) + sh.post;
-  switch (sh.fx) {
-#define PSATD_ARM(code, N, R1, R2)                                                          \
-  case code:                                                                                \
-    plane_x_inv<T, R1, R2>(rows, yhi - ylo, hp, gout, n0, bx.ng_lo[0], n0 - bx.ng_hi[0], scale, \
-                           twx, post);                                                      \
+      default: break;
+    }
+    __syncthreads();
+    const T scale = T(1.0 / ((double)n0 * n1 * bx.n[2]));
+    T* gout = reinterpret_cast<T*>(F.p[f]) + bx.foff + ((int64_t)J.y * n1 + ylo) * n0;
+    const cx<T>* twx = ctab<T>(P) + sh.ax.tw;
+    const cx<T>* post = ctab<T>(P) + sh.post;
+    switch (sh.fx) {
+#define PSATD_ARM(code, N, R1, R2)                                                                  \
+  case code:                                                                                        \
+    if constexpr (N <= max_plane_x<T>())                                                            \
+      plane_x_inv<T, R1, R2>(rows, yhi - ylo, hp, gout, n0, bx.ng_lo[0], n0 - bx.ng_hi[0], scale, twx, post); \
     break;
-    PSATD_FAST_LENGTHS(PSATD_ARM)
+      PSATD_FAST_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
-    default: break;
+      default: break;
+    }
+    __syncthreads();
+    cur ^= 1;
   }
 }
 
@@ -389,35 +495,55 @@ __global__ void __launch_bounds__(kThreads, 2) k_z_fast(DevPlan P, cx<T>* spec, 
   }
 }
 
+
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-constexpr int kPlaneThreads = 512;
-
 int fast_tile(int prec) { return prec == 32 ? 8 : 4; }
+int fast_max_x(int prec) { return prec == 32 ? max_plane_x<float>() : max_plane_x<double>(); }
+int plane_threads() { return kPlaneThreads; }
 
 cudaError_t launch_plane_fwd(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
-                             int64_t sstride, const int2* jobs, int64_t njobs, int smem, cudaStream_t st) {
-  if (njobs <= 0 || nf <= 0) return cudaSuccess;
-  dim3 grid((unsigned)njobs, nf);
+                             int64_t sstride, const int2* jobs, int64_t nplanes, int bufsz, int smem,
+                             int grid, cudaStream_t st) {
+  if (nplanes <= 0 || nf <= 0) return cudaSuccess;
   if (prec == 32)
-    k_plane_fwd<float><<<grid, kPlaneThreads, smem, st>>>(P, f, (float2*)spec, sstride, jobs);
+    k_plane_fwd<float><<<grid, kPlaneThreads, smem, st>>>(P, f, (float2*)spec, sstride, jobs, (int)nplanes, nf,
+                                                          bufsz);
   else
-    k_plane_fwd<double><<<grid, kPlaneThreads, smem, st>>>(P, f, (double2*)spec, sstride, jobs);
+    k_plane_fwd<double><<<grid, kPlaneThreads, smem, st>>>(P, f, (double2*)spec, sstride, jobs, (int)nplanes,
+                                                           nf, bufsz);
   return cudaGetLastError();
 }
 
 cudaError_t launch_plane_inv(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
-                             int64_t sstride, const int2* jobs, int64_t njobs, int smem, cudaStream_t st) {
-  if (njobs <= 0 || nf <= 0) return cudaSuccess;
-  dim3 grid((unsigned)njobs, nf);
+                             int64_t sstride, const int2* jobs, int64_t nplanes, int bufsz, int smem,
+                             int grid, cudaStream_t st) {
+  if (nplanes <= 0 || nf <= 0) return cudaSuccess;
   if (prec == 32)
-    k_plane_inv<float><<<grid, kPlaneThreads, smem, st>>>(P, f, (const float2*)spec, sstride, jobs);
+    k_plane_inv<float><<<grid, kPlaneThreads, smem, st>>>(P, f, (const float2*)spec, sstride, jobs,
+                                                          (int)nplanes, nf, bufsz);
   else
-    k_plane_inv<double><<<grid, kPlaneThreads, smem, st>>>(P, f, (const double2*)spec, sstride, jobs);
+    k_plane_inv<double><<<grid, kPlaneThreads, smem, st>>>(P, f, (const double2*)spec, sstride, jobs,
+                                                           (int)nplanes, nf, bufsz);
   return cudaGetLastError();
+}
+
+cudaError_t plane_occupancy(int prec, int smem_fwd, int smem_inv, int* fwd_per_sm, int* inv_per_sm) {
+  cudaError_t e;
+  if (prec == 32) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fwd_per_sm, k_plane_fwd<float>, kPlaneThreads, smem_fwd);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(inv_per_sm, k_plane_inv<float>, kPlaneThreads, smem_inv);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(fwd_per_sm, k_plane_fwd<double>, kPlaneThreads, smem_fwd);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(inv_per_sm, k_plane_inv<double>, kPlaneThreads, smem_inv);
+  }
+  return e;
 }
 
 cudaError_t launch_z_fast(int prec, int form, const DevPlan& P, void* spec, int64_t sstride,

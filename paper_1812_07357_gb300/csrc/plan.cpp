@@ -309,6 +309,8 @@ struct psatd_plan {
   int64_t spec_total = 0;   // complex elements per spectrum slot
   int smem_fx = 0, smem_y = 0, smem_z = 0, smem_zonly = 0, smem_ix = 0;
   int smem_pf = 0, smem_pi = 0, smem_zf = 0;
+  int buf_pf = 0, buf_pi = 0, rows_pi = 0;     // complex elements per plane buffer
+  int grid_pf = 0, grid_pi = 0;                // persistent grid sizes
 
   // device memory
   std::vector<void*> allocs;
@@ -467,7 +469,10 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
 #define PSATD_R2(code, N, R1, R2) if (s.fx == code) r2x = R2;
     PSATD_FAST_LENGTHS(PSATD_R2)
 #undef PSATD_R2
-    s.lp = s.L + (int)((r2x - s.L % 16 + 32) % 16);
+    // forward plane buffer: even pitch >= hx (16-byte rows for cp.async),
+    // close to R2 (mod 16); inverse row buffer: pitch >= hx, = 1 (mod 16)
+    s.lp = s.hx;
+    while (s.lp % 2 || (s.lp % 16 != r2x % 16 && s.lp % 16 != (r2x + 1) % 16)) ++s.lp;
     s.hp = s.hx + (int)((1 - s.hx % 16 + 32) % 16);
     shape_of[key] = (int)P->hshapes.size();
     P->hshapes.push_back(s);
@@ -503,9 +508,10 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     const int L = n0 / 2, hx = L + 1;
     const ShapeDev& sh = P->hshapes[P->hboxes[bi].shape];
     const int ni = n1 - b.ng_lo[1] - b.ng_hi[1];
-    const int sm_pf = n1 * (sh.lp + sh.hp) * csz, sm_pi = (n1 + ni) * sh.hp * csz;
+    const int sm_pf = 2 * n1 * sh.lp * csz, sm_pi = (2 * n1 * hx + ni * sh.hp) * csz;
     const int sm_zf = z_fast_smem(P->prec, P->form, n2);
     const bool fast = !(d.flags & PSATD_GENERIC_KERNELS) && sh.fx >= 0 && sh.fy >= 0 && sh.fz >= 0 &&
+                      L <= fast_max_x(P->prec) &&
                       sm_pf <= optin && sm_pi <= optin && sm_zf <= optin;
     const int rows = n1 * n2;
     const int nr = std::max(1, std::min(rows, kMaxPoints / L));
@@ -522,8 +528,9 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       }
       for (int y = 0; y < n1; ++y)
         for (int m = 0; m < hx; m += tile) P->zfast.push_back({bi, y, m, std::min(tile, hx - m)});
-      P->smem_pf = std::max(P->smem_pf, sm_pf);
-      P->smem_pi = std::max(P->smem_pi, sm_pi);
+      P->buf_pf = std::max(P->buf_pf, n1 * sh.lp);
+      P->buf_pi = std::max(P->buf_pi, n1 * hx);
+      P->rows_pi = std::max(P->rows_pi, ni * sh.hp);
       P->smem_zf = std::max(P->smem_zf, sm_zf);
     } else {
       for (int r = 0; r < rows; r += nr) P->g_rows.push_back({bi, r, std::min(nr, rows - r), 0});
@@ -561,13 +568,26 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     P->smem_z = std::max(P->smem_z, n2 * FIN * nz * csz);
     P->smem_zonly = std::max(P->smem_zonly, n2 * nz * csz);
   }
+  if (P->fast_boxes) {
+    P->smem_pf = 2 * P->buf_pf * csz;
+    P->smem_pi = (2 * P->buf_pi + P->rows_pi) * csz;
+    if (P->smem_pf > optin || P->smem_pi > optin)
+      return fail(P, PSATD_ERR_UNSUPPORTED_SIZE, "plane buffers exceed shared memory");
+  }
   // ---- exchange protocol
   P->blocks = build_blocks(&d);
   for (int i = 0; i < (int)P->blocks.size(); ++i) {
     const CopyBlk& c = P->blocks[i];
     const int rows = c.ext[1] * c.ext[2];
-    const int per = std::max(1, 4096 / std::max(1, c.ext[0]));
-    for (int r = 0; r < rows; r += per) P->tiles.push_back({i, r, std::min(per, rows - r), 0});
+    // 16-byte units when both rows start on 16-byte boundaries (box offsets
+    // are 64-element aligned, so the row pitch and x offsets decide)
+    const int v16 = 16 / (int)P->rsize;
+    const psatd_box& db = P->boxes[c.dst_box];
+    bool vec = c.ext[0] % v16 == 0 && c.dst_lo[0] % v16 == 0 && db.n[0] % v16 == 0;
+    if (c.src_box >= 0) vec = vec && c.src_lo[0] % v16 == 0 && P->boxes[c.src_box].n[0] % v16 == 0;
+    const int unit = vec ? v16 : 1;
+    const int per = std::max(1, 2048 * unit / std::max(1, c.ext[0]));
+    for (int r = 0; r < rows; r += per) P->tiles.push_back({i, r, std::min(per, rows - r), vec ? v16 : 1});
   }
   // ---- device memory
   CK(P, upload(P, P->hboxes, &P->d_boxes));
@@ -654,6 +674,15 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   // device maximum so that no plan lowers it below another plan's need.
   CK(P, configure_kernels(P->prec, optin));
   CK(P, configure_fast_kernels(P->prec, optin));
+  if (P->fast_boxes) {
+    int sms = 0, occ_f = 0, occ_i = 0;
+    CK(P, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(P, plane_occupancy(P->prec, P->smem_pf, P->smem_pi, &occ_f, &occ_i));
+    if (occ_f < 1 || occ_i < 1) return fail(P, PSATD_ERR_UNSUPPORTED_SIZE, "plane kernels do not fit an SM");
+    const int FINv = fields_in(P->form), FOUTv = fields_out(P->form);
+    P->grid_pf = (int)std::min<int64_t>((int64_t)occ_f * sms, (int64_t)P->plane_fwd.size() * FINv);
+    P->grid_pi = (int)std::min<int64_t>((int64_t)occ_i * sms, (int64_t)P->plane_inv.size() * FOUTv);
+  }
   return PSATD_OK;
 }
 
@@ -854,7 +883,8 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
       // S1: forward x+y (fast boxes: one plane kernel; generic: x rows, y columns)
       if (!P->plane_fwd.empty()) {
         CK(P, timed(P, 0, st, [&] {
-             return launch_plane_fwd(P->prec, D, fp, FIN, P->d_ws, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(), P->smem_pf, st);
+             return launch_plane_fwd(P->prec, D, fp, FIN, P->d_ws, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
+                                     P->buf_pf, P->smem_pf, P->grid_pf, st);
            }));
         ++launches;
       }
@@ -883,7 +913,8 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
       // S3: inverse y+x, interior cells only
       if (!P->plane_inv.empty()) {
         CK(P, timed(P, 4, st, [&] {
-             return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv, (int64_t)P->plane_inv.size(), P->smem_pi, st);
+             return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv, (int64_t)P->plane_inv.size(),
+                                     P->buf_pi, P->smem_pi, P->grid_pi, st);
            }));
         ++launches;
       }

@@ -86,9 +86,10 @@ struct CopyBlk {
   int32_t dst_lo[3], src_lo[3], ext[3];
 };
 
-// rows [row0, row0+nrows) of one copy block, row = ry + ext1*rz
+// rows [row0, row0+nrows) of one copy block, row = ry + ext1*rz; vec > 1:
+// rows are copied in 16-byte units of `vec` elements
 struct XTile {
-  int32_t blk, row0, nrows, pad;
+  int32_t blk, row0, nrows, vec;
 };
 
 // Up to 10 field slots (see Form).
@@ -140,13 +141,20 @@ cudaError_t configure_kernels(int prec, int smem_bytes);
 
 // ---- fast path (fast_kernels.cu): boxes whose three FFT lengths are fast --
 // jobs: (box, z plane); forward writes every plane, inverse takes interior z.
+// Persistent kernels: `grid` CTAs walk nplanes x nf planes; bufsz is the
+// complex-element size of one plane buffer (two per CTA).
 cudaError_t launch_plane_fwd(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
-                             int64_t sstride, const int2* jobs, int64_t njobs, int smem, cudaStream_t st);
+                             int64_t sstride, const int2* jobs, int64_t nplanes, int bufsz, int smem,
+                             int grid, cudaStream_t st);
 cudaError_t launch_plane_inv(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
-                             int64_t sstride, const int2* jobs, int64_t njobs, int smem, cudaStream_t st);
+                             int64_t sstride, const int2* jobs, int64_t nplanes, int bufsz, int smem,
+                             int grid, cudaStream_t st);
+// Resident CTAs per SM of the plane kernels at the given shared memory.
+cudaError_t plane_occupancy(int prec, int smem_fwd, int smem_inv, int* fwd_per_sm, int* inv_per_sm);
 cudaError_t launch_z_fast(int prec, int form, const DevPlan& P, void* spec, int64_t sstride,
                           const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
 int fast_tile(int prec);                        // mx columns per k_z_fast job
+int fast_max_x(int prec);                       // longest n0/2 of a fast-path box
 int z_fast_smem(int prec, int form, int n2);    // bytes of shared memory of k_z_fast
 cudaError_t configure_fast_kernels(int prec, int smem_bytes);
 
