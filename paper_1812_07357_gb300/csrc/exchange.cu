@@ -17,13 +17,11 @@ namespace psatd {
 
 namespace {
 
-// e / d for 0 <= e < 2^24, d > 0, with inv = 1.0f / d.
-__device__ __forceinline__ int div_small(int e, int d, float inv) {
-  int q = __float2int_rz((float)e * inv);
-  q += (q + 1) * d <= e;
-  q -= q * d > e;
-  return q;
-}
+// Exact e / d for 0 <= e, d < 2^16 with m = floor((2^32 - 1)/d) + 1; for
+// d = 1 that constant wraps to 0 and the quotient is e itself.
+__device__ __forceinline__ int fdiv(int e, unsigned m) { return m ? (int)__umulhi((unsigned)e, m) : e; }
+
+constexpr int kBatch = 4;   // units loaded before any is stored (bytes in flight)
 
 template <typename T, int V>
 __device__ __forceinline__ void copy_tile(T* base, const CopyBlk& b, const XTile& t, const BoxDev& db,
@@ -31,26 +29,36 @@ __device__ __forceinline__ void copy_tile(T* base, const CopyBlk& b, const XTile
   using Vec = typename std::conditional<V == 1, T, float4>::type;
   const int ex = b.ext[0], ey = b.ext[1];
   const int upr = ex / V;
-  const float inv_upr = 1.0f / upr, inv_ey = 1.0f / ey;
+  const unsigned m_upr = 0xFFFFFFFFu / (unsigned)upr + 1u, m_ey = 0xFFFFFFFFu / (unsigned)ey + 1u;
   const int64_t dn0 = db.n[0], dn1 = db.n[1];
   const int units = t.nrows * upr;
-  for (int u = threadIdx.x; u < units; u += blockDim.x) {
-    const int rr = div_small(u, upr, inv_upr);
-    const int x = (u - rr * upr) * V;
-    const int r = t.row0 + rr;
-    const int rz = div_small(r, ey, inv_ey);
-    const int ry = r - rz * ey;
-    const int64_t d = db.foff + ((int64_t)(b.dst_lo[2] + rz) * dn1 + (b.dst_lo[1] + ry)) * dn0 +
-                      b.dst_lo[0] + x;
-    Vec v;
-    if (b.src_box >= 0) {
-      const int64_t s = sfoff + ((int64_t)(b.src_lo[2] + rz) * sn1 + (b.src_lo[1] + ry)) * sn0 +
-                        b.src_lo[0] + x;
-      v = *reinterpret_cast<const Vec*>(base + s);
-    } else {
-      v = Vec{};
+  const bool zero = b.src_box < 0;
+  for (int u0 = threadIdx.x; u0 < units; u0 += kBatch * blockDim.x) {
+    Vec v[kBatch];
+    int64_t d[kBatch];
+#pragma unroll
+    for (int i = 0; i < kBatch; ++i) {
+      const int u = u0 + i * blockDim.x;
+      d[i] = -1;
+      if (u < units) {
+        const int rr = fdiv(u, m_upr);
+        const int x = (u - rr * upr) * V;
+        const int r = t.row0 + rr;
+        const int rz = fdiv(r, m_ey);
+        const int ry = r - rz * ey;
+        d[i] = db.foff + ((int64_t)(b.dst_lo[2] + rz) * dn1 + (b.dst_lo[1] + ry)) * dn0 + b.dst_lo[0] + x;
+        if (zero) {
+          v[i] = Vec{};
+        } else {
+          const int64_t s = sfoff + ((int64_t)(b.src_lo[2] + rz) * sn1 + (b.src_lo[1] + ry)) * sn0 +
+                            b.src_lo[0] + x;
+          v[i] = *reinterpret_cast<const Vec*>(base + s);
+        }
+      }
     }
-    *reinterpret_cast<Vec*>(base + d) = v;
+#pragma unroll
+    for (int i = 0; i < kBatch; ++i)
+      if (d[i] >= 0) *reinterpret_cast<Vec*>(base + d[i]) = v[i];
   }
 }
 

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "fft_codelets.cuh"
 #include "psatd_internal.h"
@@ -32,6 +33,8 @@ namespace psatd {
 namespace {
 
 constexpr int kPlaneThreads = 512;
+constexpr int kTileF32 = 8;          // mx columns per z tile (FP32 / FP64)
+constexpr int kTileF64 = 4;
 constexpr int kMaxPlaneRows = 128;   // largest n1 of a fast box
 
 // Longest x half-length L = n0/2 the plane kernels take (their in-place x
@@ -46,13 +49,11 @@ __device__ __forceinline__ const cx<T>* ctab(const DevPlan& P) {
   return reinterpret_cast<const cx<T>*>(P.cpool);
 }
 
-// e / d for 0 <= e < 2^24, d > 0, with inv = 1.0f / d.
-__device__ __forceinline__ int div_small(int e, int d, float inv) {
-  int q = __float2int_rz((float)e * inv);
-  q += (q + 1) * d <= e;
-  q -= q * d > e;
-  return q;
-}
+// Exact e / d for 0 <= e, d < 2^16 with m = magic(d) = floor((2^32 - 1) / d) + 1:
+// e*m / 2^32 = e/d + e*(m - 2^32/d)/2^32 and the error term stays below 1/d.
+__device__ __forceinline__ unsigned magic(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
+// (for d = 1 the constant wraps to 0 and the quotient is e itself)
+__device__ __forceinline__ int fdiv(int e, unsigned m) { return m ? (int)__umulhi((unsigned)e, m) : e; }
 
 // asynchronous 16-byte global -> shared copies (bypassing L1)
 __device__ __forceinline__ void cp16(void* s, const void* g) {
@@ -69,12 +70,12 @@ __device__ __forceinline__ void cp_wait_prev() { asm volatile("cp.async.wait_gro
 // ---------------------------------------------------------------------------
 template <typename T, int R1, int R2, int DIR, bool CFAST>
 __device__ __forceinline__ void pass1(cx<T>* buf, int ncol, int cs, int ns, const cx<T>* __restrict__ tw,
-                                      float inv_ncol) {
+                                      unsigned m_ncol) {
   const int items = ncol * R2;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     int c, n2;
     if (CFAST) {
-      n2 = div_small(it, ncol, inv_ncol);
+      n2 = fdiv(it, m_ncol);
       c = it - n2 * ncol;
     } else {
       c = it / R2;
@@ -97,13 +98,13 @@ __device__ __forceinline__ void pass1(cx<T>* buf, int ncol, int cs, int ns, cons
 // pass 2: column c, R2 consecutive pass-1 results at k1*R2 + n2; DFT_R2;
 // st(c, k1 + R1*k2, value) receives the natural-order outputs.
 template <typename T, int R1, int R2, int DIR, bool CFAST, typename Store>
-__device__ __forceinline__ void pass2(const cx<T>* buf, int ncol, int cs, int ns, float inv_ncol,
+__device__ __forceinline__ void pass2(const cx<T>* buf, int ncol, int cs, int ns, unsigned m_ncol,
                                       Store&& st) {
   const int items = ncol * R1;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     int c, k1;
     if (CFAST) {
-      k1 = div_small(it, ncol, inv_ncol);
+      k1 = fdiv(it, m_ncol);
       c = it - k1 * ncol;
     } else {
       c = it / R1;
@@ -156,9 +157,9 @@ __device__ __forceinline__ void load_rows_async(void* dst, const void* src, int 
                                                 int pitch_bytes) {
   const int upr = row_bytes >> 4;
   const int total = rows * upr;
-  const float inv = 1.0f / upr;
+  const unsigned m = magic(upr);
   for (int u = threadIdx.x; u < total; u += blockDim.x) {
-    const int r = div_small(u, upr, inv), x = u - r * upr;
+    const int r = rows == 1 ? 0 : fdiv(u, m), x = u - r * upr;
     cp16(static_cast<char*>(dst) + r * pitch_bytes + x * 16, static_cast<const char*>(src) + (size_t)u * 16);
   }
 }
@@ -170,7 +171,7 @@ template <typename T, int R1, int R2>
 __device__ __forceinline__ void plane_x_fwd(cx<T>* buf, int n1, int lp, const cx<T>* __restrict__ twx,
                                             const cx<T>* __restrict__ post) {
   constexpr int L = R1 * R2;
-  pass1<T, R1, R2, -1, false>(buf, n1, lp, 1, twx, 0.f);
+  pass1<T, R1, R2, -1, false>(buf, n1, lp, 1, twx, 0u);
   __syncthreads();
   pass2_rows_inplace<T, R1, R2, -1>(buf, n1, lp);
   __syncthreads();
@@ -199,7 +200,7 @@ __device__ __forceinline__ void plane_x_fwd(cx<T>* buf, int n1, int lp, const cx
 template <typename T, int R1, int R2>
 __device__ __forceinline__ void plane_y_fwd(cx<T>* buf, int hx, int lp, cx<T>* out,
                                             const cx<T>* __restrict__ twy) {
-  const float inv = 1.0f / hx;
+  const unsigned inv = magic(hx);
   pass1<T, R1, R2, -1, true>(buf, hx, 1, lp, twy, inv);
   __syncthreads();
   pass2<T, R1, R2, -1, true>(buf, hx, 1, lp, inv,
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kPlaneThreads, sizeof(T) == 4 ? 2 : 1)
 template <typename T, int R1, int R2>
 __device__ __forceinline__ void plane_y_inv(cx<T>* buf, int hx, cx<T>* rows, int hp, int ylo, int yhi,
                                             const cx<T>* __restrict__ twy) {
-  const float inv = 1.0f / hx;
+  const unsigned inv = magic(hx);
   pass1<T, R1, R2, 1, true>(buf, hx, 1, hx, twy, inv);
   __syncthreads();
   pass2<T, R1, R2, 1, true>(buf, hx, 1, hx, inv, [&](int c, int k, cx<T> v) {
@@ -285,8 +286,8 @@ __device__ __forceinline__ void plane_y_inv(cx<T>* buf, int hx, cx<T>* rows, int
 }
 
 template <typename T, int R1, int R2>
-__device__ __forceinline__ void plane_x_inv(cx<T>* rows, int nrows, int hp, T* gout, int n0, int xlo,
-                                            int xhi, T scale, const cx<T>* __restrict__ twx,
+__device__ __forceinline__ void plane_x_inv(cx<T>* rows, int nrows, int hp, T* ibuf, int nxi, int xlo,
+                                            T scale, const cx<T>* __restrict__ twx,
                                             const cx<T>* __restrict__ post) {
   constexpr int L = R1 * R2;
   constexpr int H = L / 2 + 1;
@@ -302,18 +303,29 @@ __device__ __forceinline__ void plane_x_inv(cx<T>* rows, int nrows, int hp, T* g
     row[k] = za;
   }
   __syncthreads();
-  pass1<T, R1, R2, 1, false>(rows, nrows, hp, 1, twx, 0.f);
+  pass1<T, R1, R2, 1, false>(rows, nrows, hp, 1, twx, 0u);
   __syncthreads();
-  pass2<T, R1, R2, 1, false>(rows, nrows, hp, 1, 0.f, [&](int r, int m, cx<T> v) {
-    T* o = gout + (int64_t)r * n0 + 2 * m;
-    if (2 * m >= xlo && 2 * m + 1 < xhi) {
-      cx<T> w = mk<T>(scale * v.x, scale * v.y);
-      *reinterpret_cast<cx<T>*>(o) = w;
-    } else {
-      if (2 * m >= xlo && 2 * m < xhi) o[0] = scale * v.x;
-      if (2 * m + 1 >= xlo && 2 * m + 1 < xhi) o[1] = scale * v.y;
-    }
+  // interior cells of the interior rows -> ibuf (row pitch nxi)
+  pass2<T, R1, R2, 1, false>(rows, nrows, hp, 1, 0u, [&](int r, int m, cx<T> v) {
+    T* o = ibuf + r * nxi - xlo + 2 * m;
+    if (2 * m >= xlo && 2 * m < xlo + nxi) o[0] = scale * v.x;
+    if (2 * m + 1 >= xlo && 2 * m + 1 < xlo + nxi) o[1] = scale * v.y;
   });
+}
+
+// Copy ny rows of nx elements from shared memory (pitch spitch) to global
+// memory (pitch dpitch), in units of V elements, by `nthreads` threads
+// numbered `tid`.
+template <typename T, int V>
+__device__ __forceinline__ void copy_rect(const T* src, int spitch, T* dst, int64_t dpitch, int ny, int nx,
+                                          int tid, int nthreads) {
+  using Vec = typename std::conditional<V == 1, T, float4>::type;
+  const int upr = nx / V;
+  const unsigned m = magic(upr);
+  for (int u = tid; u < ny * upr; u += nthreads) {
+    const int r = fdiv(u, m), c = (u - r * upr) * V;
+    *reinterpret_cast<Vec*>(dst + r * dpitch + c) = *reinterpret_cast<const Vec*>(src + r * spitch + c);
+  }
 }
 
 template <typename T>
@@ -332,7 +344,8 @@ __device__ __forceinline__ void inv_issue(const DevPlan& P, const cx<T>* spec, i
 template <typename T>
 __global__ void __launch_bounds__(kPlaneThreads, sizeof(T) == 4 ? 2 : 1)
     k_plane_inv(DevPlan P, FieldPtrs F, const cx<T>* spec, int64_t sstride, const int2* __restrict__ jobs,
-                int nplanes, int nf, int bufsz) {
+                int nplanes, int nf, int bufsz, const int* __restrict__ seg_start,
+                const GuardSeg* __restrict__ segs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* bufs = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* rows = bufs + 2 * bufsz;
@@ -365,18 +378,44 @@ __global__ void __launch_bounds__(kPlaneThreads, sizeof(T) == 4 ? 2 : 1)
     }
     __syncthreads();
     const T scale = T(1.0 / ((double)n0 * n1 * bx.n[2]));
-    T* gout = reinterpret_cast<T*>(F.p[f]) + bx.foff + ((int64_t)J.y * n1 + ylo) * n0;
+    const int xlo = bx.ng_lo[0], nxi = n0 - bx.ng_lo[0] - bx.ng_hi[0], ni = yhi - ylo;
+    T* ibuf = reinterpret_cast<T*>(buf);   // the spectrum plane is no longer needed
     const cx<T>* twx = ctab<T>(P) + sh.ax.tw;
     const cx<T>* post = ctab<T>(P) + sh.post;
     switch (sh.fx) {
-#define PSATD_ARM(code, N, R1, R2)                                                                  \
-  case code:                                                                                        \
-    if constexpr (N <= max_plane_x<T>())                                                            \
-      plane_x_inv<T, R1, R2>(rows, yhi - ylo, hp, gout, n0, bx.ng_lo[0], n0 - bx.ng_hi[0], scale, twx, post); \
+#define PSATD_ARM(code, N, R1, R2)                                                       \
+  case code:                                                                             \
+    if constexpr (N <= max_plane_x<T>())                                                 \
+      plane_x_inv<T, R1, R2>(rows, ni, hp, ibuf, nxi, xlo, scale, twx, post);            \
     break;
       PSATD_FAST_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
       default: break;
+    }
+    __syncthreads();
+    // interior cells to this box
+    T* fbase = reinterpret_cast<T*>(F.p[f]);
+    T* own = fbase + bx.foff + ((int64_t)J.y * n1 + ylo) * n0 + xlo;
+    constexpr int V16 = 16 / sizeof(T);
+    if (nxi % V16 == 0 && xlo % V16 == 0 && n0 % V16 == 0)
+      copy_rect<T, V16>(ibuf, nxi, own, n0, ni, nxi, threadIdx.x, blockDim.x);
+    else
+      copy_rect<T, 1>(ibuf, nxi, own, n0, ni, nxi, threadIdx.x, blockDim.x);
+    // guard cells fed by this plane (fused exchange), one rectangle per warp
+    if (seg_start) {
+      const int p = j - f * nplanes;
+      const int s1 = seg_start[p + 1];
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int si = seg_start[p] + warp; si < s1; si += nw) {
+        const GuardSeg g = segs[si];
+        const BoxDev db = P.boxes[g.dst_box];
+        T* dst = fbase + db.foff + ((int64_t)g.dst_z * db.n[1] + g.dy) * db.n[0] + g.dx;
+        const T* src = ibuf + (g.sy - ylo) * nxi + (g.sx - xlo);
+        if (g.vec > 1)
+          copy_rect<T, V16>(src, nxi, dst, db.n[0], g.ny, g.nx, lane, 32);
+        else
+          copy_rect<T, 1>(src, nxi, dst, db.n[0], g.ny, g.nx, lane, 32);
+      }
     }
     __syncthreads();
     cur ^= 1;
@@ -502,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_z_fast(DevPlan P, cx<T>* spec, 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-int fast_tile(int prec) { return prec == 32 ? 8 : 4; }
+int fast_tile(int prec) { return prec == 32 ? kTileF32 : kTileF64; }
 int fast_max_x(int prec) { return prec == 32 ? max_plane_x<float>() : max_plane_x<double>(); }
 int plane_threads() { return kPlaneThreads; }
 
@@ -521,14 +560,14 @@ cudaError_t launch_plane_fwd(int prec, const DevPlan& P, const FieldPtrs& f, int
 
 cudaError_t launch_plane_inv(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
                              int64_t sstride, const int2* jobs, int64_t nplanes, int bufsz, int smem,
-                             int grid, cudaStream_t st) {
+                             int grid, const int* seg_start, const GuardSeg* segs, cudaStream_t st) {
   if (nplanes <= 0 || nf <= 0) return cudaSuccess;
   if (prec == 32)
     k_plane_inv<float><<<grid, kPlaneThreads, smem, st>>>(P, f, (const float2*)spec, sstride, jobs,
-                                                          (int)nplanes, nf, bufsz);
+                                                          (int)nplanes, nf, bufsz, seg_start, segs);
   else
     k_plane_inv<double><<<grid, kPlaneThreads, smem, st>>>(P, f, (const double2*)spec, sstride, jobs,
-                                                           (int)nplanes, nf, bufsz);
+                                                           (int)nplanes, nf, bufsz, seg_start, segs);
   return cudaGetLastError();
 }
 
@@ -553,13 +592,13 @@ cudaError_t launch_z_fast(int prec, int form, const DevPlan& P, void* spec, int6
 #define PSATD_ZF(T, C2, FORMV, TXV) \
   k_z_fast<T, FORMV, TXV><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs)
   if (prec == 32) {
-    if (form == kVacuum) PSATD_ZF(float, float2, kVacuum, 8);
-    else if (form == kJForm) PSATD_ZF(float, float2, kJForm, 8);
-    else PSATD_ZF(float, float2, kRhoForm, 8);
+    if (form == kVacuum) PSATD_ZF(float, float2, kVacuum, kTileF32);
+    else if (form == kJForm) PSATD_ZF(float, float2, kJForm, kTileF32);
+    else PSATD_ZF(float, float2, kRhoForm, kTileF32);
   } else {
-    if (form == kVacuum) PSATD_ZF(double, double2, kVacuum, 4);
-    else if (form == kJForm) PSATD_ZF(double, double2, kJForm, 4);
-    else PSATD_ZF(double, double2, kRhoForm, 4);
+    if (form == kVacuum) PSATD_ZF(double, double2, kVacuum, kTileF64);
+    else if (form == kJForm) PSATD_ZF(double, double2, kJForm, kTileF64);
+    else PSATD_ZF(double, double2, kRhoForm, kTileF64);
   }
 #undef PSATD_ZF
   return cudaGetLastError();
@@ -582,15 +621,15 @@ cudaError_t configure_fast_kernels(int prec, int smem) {
   if (prec == 32) {
     PSATD_SET(k_plane_fwd<float>);
     PSATD_SET(k_plane_inv<float>);
-    PSATD_SET((k_z_fast<float, kVacuum, 8>));
-    PSATD_SET((k_z_fast<float, kJForm, 8>));
-    PSATD_SET((k_z_fast<float, kRhoForm, 8>));
+    PSATD_SET((k_z_fast<float, kVacuum, kTileF32>));
+    PSATD_SET((k_z_fast<float, kJForm, kTileF32>));
+    PSATD_SET((k_z_fast<float, kRhoForm, kTileF32>));
   } else {
     PSATD_SET(k_plane_fwd<double>);
     PSATD_SET(k_plane_inv<double>);
-    PSATD_SET((k_z_fast<double, kVacuum, 4>));
-    PSATD_SET((k_z_fast<double, kJForm, 4>));
-    PSATD_SET((k_z_fast<double, kRhoForm, 4>));
+    PSATD_SET((k_z_fast<double, kVacuum, kTileF64>));
+    PSATD_SET((k_z_fast<double, kJForm, kTileF64>));
+    PSATD_SET((k_z_fast<double, kRhoForm, kTileF64>));
   }
 #undef PSATD_SET
   return e;

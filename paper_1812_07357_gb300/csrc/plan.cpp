@@ -303,7 +303,10 @@ struct psatd_plan {
   std::vector<ColJob> zfast;
   int fast_boxes = 0;
   std::vector<CopyBlk> blocks;
-  std::vector<XTile> tiles;
+  std::vector<XTile> tiles;                                   // every block (psatd_guard_exchange)
+  std::vector<XTile> step_tiles;                              // blocks not fused into the inverse
+  std::vector<int> seg_start;                                 // fused exchange, CSR per plane_inv
+  std::vector<GuardSeg> segs;
 
   int64_t field_total = 0;  // elements per field buffer
   int64_t spec_total = 0;   // complex elements per spectrum slot
@@ -323,6 +326,9 @@ struct psatd_plan {
   int2 *d_plane_fwd = nullptr, *d_plane_inv = nullptr;
   CopyBlk* d_blocks = nullptr;
   XTile* d_tiles = nullptr;
+  XTile* d_step_tiles = nullptr;
+  int* d_seg_start = nullptr;
+  GuardSeg* d_segs = nullptr;
   void *d_rpool = nullptr, *d_cpool = nullptr, *d_coef = nullptr;
   void* d_ws = nullptr;
   size_t plan_bytes = 0;
@@ -576,18 +582,61 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   }
   // ---- exchange protocol
   P->blocks = build_blocks(&d);
+  // Guard rectangles fed by fast boxes are written by the inverse plane
+  // kernel itself (fused exchange); the step's exchange kernel keeps the
+  // blocks whose source box runs on the generic kernels.  Blocks outside a
+  // non-periodic domain (zero fill) keep the value written by the explicit
+  // psatd_guard_exchange: no step writes those cells.
+  std::vector<char> box_fast(P->boxes.size(), 0);
+  std::map<std::pair<int, int>, int> plane_index;  // (box, z) -> plane_inv index
+  for (int i = 0; i < (int)P->plane_inv.size(); ++i) {
+    box_fast[P->plane_inv[i].x] = 1;
+    plane_index[{P->plane_inv[i].x, P->plane_inv[i].y}] = i;
+  }
+  std::vector<std::vector<GuardSeg>> per_plane(P->plane_inv.size());
+  const int v16 = 16 / (int)P->rsize;
+  for (const CopyBlk& c : P->blocks) {
+    if (c.src_box < 0 || !box_fast[c.src_box]) continue;
+    const psatd_box& sb = P->boxes[c.src_box];
+    const psatd_box& db = P->boxes[c.dst_box];
+    const int nxi = sb.n[0] - sb.ng_lo[0] - sb.ng_hi[0];
+    const bool vec = c.ext[0] % v16 == 0 && (c.src_lo[0] - sb.ng_lo[0]) % v16 == 0 && nxi % v16 == 0 &&
+                     c.dst_lo[0] % v16 == 0 && db.n[0] % v16 == 0;
+    for (int k = 0; k < c.ext[2]; ++k) {
+      GuardSeg g{};
+      g.dst_box = c.dst_box;
+      g.dst_z = c.dst_lo[2] + k;
+      g.sy = c.src_lo[1];
+      g.sx = c.src_lo[0];
+      g.ny = c.ext[1];
+      g.nx = c.ext[0];
+      g.dy = c.dst_lo[1];
+      g.dx = c.dst_lo[0];
+      g.vec = vec ? v16 : 1;
+      per_plane[plane_index.at({c.src_box, c.src_lo[2] + k})].push_back(g);
+    }
+  }
+  P->seg_start.assign(P->plane_inv.size() + 1, 0);
+  for (size_t i = 0; i < per_plane.size(); ++i) {
+    P->seg_start[i + 1] = P->seg_start[i] + (int)per_plane[i].size();
+    P->segs.insert(P->segs.end(), per_plane[i].begin(), per_plane[i].end());
+  }
   for (int i = 0; i < (int)P->blocks.size(); ++i) {
     const CopyBlk& c = P->blocks[i];
+    const bool fused = c.src_box >= 0 && box_fast[c.src_box];
+    const bool stepwise = c.src_box >= 0 && !fused;
     const int rows = c.ext[1] * c.ext[2];
     // 16-byte units when both rows start on 16-byte boundaries (box offsets
     // are 64-element aligned, so the row pitch and x offsets decide)
-    const int v16 = 16 / (int)P->rsize;
     const psatd_box& db = P->boxes[c.dst_box];
     bool vec = c.ext[0] % v16 == 0 && c.dst_lo[0] % v16 == 0 && db.n[0] % v16 == 0;
     if (c.src_box >= 0) vec = vec && c.src_lo[0] % v16 == 0 && P->boxes[c.src_box].n[0] % v16 == 0;
     const int unit = vec ? v16 : 1;
     const int per = std::max(1, 2048 * unit / std::max(1, c.ext[0]));
-    for (int r = 0; r < rows; r += per) P->tiles.push_back({i, r, std::min(per, rows - r), vec ? v16 : 1});
+    for (int r = 0; r < rows; r += per) {
+      P->tiles.push_back({i, r, std::min(per, rows - r), vec ? v16 : 1});
+      if (stepwise) P->step_tiles.push_back({i, r, std::min(per, rows - r), vec ? v16 : 1});
+    }
   }
   // ---- device memory
   CK(P, upload(P, P->hboxes, &P->d_boxes));
@@ -607,6 +656,9 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   CK(P, upload(P, P->plane_inv, &P->d_plane_inv));
   CK(P, upload(P, P->blocks, &P->d_blocks));
   CK(P, upload(P, P->tiles, &P->d_tiles));
+  CK(P, upload(P, P->step_tiles, &P->d_step_tiles));
+  CK(P, upload(P, P->seg_start, &P->d_seg_start));
+  CK(P, upload(P, P->segs, &P->d_segs));
   CK(P, dalloc(P, (size_t)rtot * P->rsize, &P->d_rpool));
   CK(P, dalloc(P, (size_t)ctot * P->csize, &P->d_cpool));
   CK(P, dalloc(P, (size_t)qtot * 4 * P->rsize, &P->d_coef));
@@ -914,7 +966,8 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
       if (!P->plane_inv.empty()) {
         CK(P, timed(P, 4, st, [&] {
              return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv, (int64_t)P->plane_inv.size(),
-                                     P->buf_pi, P->smem_pi, P->grid_pi, st);
+                                     P->buf_pi, P->smem_pi, P->grid_pi, P->segs.empty() ? nullptr : P->d_seg_start,
+                                     P->d_segs, st);
            }));
         ++launches;
       }
@@ -927,9 +980,10 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
            }));
         launches += 2;
       }
-      if (!P->tiles.empty()) {
+      if (!P->step_tiles.empty()) {
         CK(P, timed(P, 5, st, [&] {
-             return launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_tiles, (int64_t)P->tiles.size(), st);
+             return launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_step_tiles, (int64_t)P->step_tiles.size(),
+                                    st);
            }));
         ++launches;
       }

@@ -92,6 +92,16 @@ struct XTile {
   int32_t blk, row0, nrows, vec;
 };
 
+// A rectangle of one interior source plane that feeds guard cells of a box:
+// source rows sy.., columns sx.. (box-local) -> destination (dst_box, dst_z,
+// dy.., dx..).  vec: rows can move in 16-byte units.
+struct GuardSeg {
+  int32_t dst_box, dst_z;
+  int32_t sy, sx, ny, nx;
+  int32_t dy, dx;
+  int32_t vec, pad;
+};
+
 // Up to 10 field slots (see Form).
 struct FieldPtrs {
   void* p[10];
@@ -146,9 +156,11 @@ cudaError_t configure_kernels(int prec, int smem_bytes);
 cudaError_t launch_plane_fwd(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
                              int64_t sstride, const int2* jobs, int64_t nplanes, int bufsz, int smem,
                              int grid, cudaStream_t st);
+// The inverse kernel also writes the guard cells its interior plane feeds
+// (segments seg_start[p] .. seg_start[p+1] of plane p; NULL: none).
 cudaError_t launch_plane_inv(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
                              int64_t sstride, const int2* jobs, int64_t nplanes, int bufsz, int smem,
-                             int grid, cudaStream_t st);
+                             int grid, const int* seg_start, const GuardSeg* segs, cudaStream_t st);
 // Resident CTAs per SM of the plane kernels at the given shared memory.
 cudaError_t plane_occupancy(int prec, int smem_fwd, int smem_inv, int* fwd_per_sm, int* inv_per_sm);
 cudaError_t launch_z_fast(int prec, int form, const DevPlan& P, void* spec, int64_t sstride,
