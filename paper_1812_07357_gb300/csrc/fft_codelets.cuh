@@ -2,14 +2,16 @@
 //
 // Dft<T, R, DIR>::run(v) replaces v[0..R) by y_k = sum_t v_t exp(DIR 2 pi i t k / R)
 // (DIR = -1 forward, +1 inverse, unnormalised).  R in {2,3,4,5,8} are written
-// out; R in {6,10,12,16} are composed from two of them (decimation in time,
-// R = A*B) with the internal twiddles exp(DIR 2 pi i m / R) taken from their
-// closed forms (cos(pi/8) = sqrt(2 + sqrt 2)/2, cos(pi/5) = (1 + sqrt 5)/4, ...).
+// out; the other sizes are composed from two smaller codelets (decimation in
+// time, R = A*B) whose internal twiddles exp(DIR 2 pi i m / R) are
+// compile-time constants (unit_roots.h).
 #pragma once
 
 #include <cuda_runtime.h>
 
 #include <type_traits>
+
+#include "unit_roots.h"
 
 namespace psatd {
 
@@ -87,37 +89,6 @@ __device__ __forceinline__ void static_for(F&& f) {
     f(std::integral_constant<int, B>{});
     static_for<B + 1, E>(f);
   }
-}
-
-// cos(2 pi m / R) and sin(2 pi m / R) for the composite codelets, from their
-// closed forms; evaluated at compile time only.
-constexpr double root_cos(int R, int m) {
-  const double r2 = 0.70710678118654752440;   // sqrt(2)/2
-  const double c8 = 0.92387953251128675613;   // cos(pi/8) = sqrt(2 + sqrt 2)/2
-  const double s8 = 0.38268343236508977173;   // sin(pi/8) = sqrt(2 - sqrt 2)/2
-  const double h3 = 0.86602540378443864676;   // sqrt(3)/2
-  const double c5 = 0.80901699437494742410;   // cos(pi/5) = (1 + sqrt 5)/4
-  const double c25 = 0.30901699437494742410;  // cos(2 pi/5) = (sqrt 5 - 1)/4
-  const double t16[16] = {1, c8, r2, s8, 0, -s8, -r2, -c8, -1, -c8, -r2, -s8, 0, s8, r2, c8};
-  const double t12[12] = {1, h3, 0.5, 0, -0.5, -h3, -1, -h3, -0.5, 0, 0.5, h3};
-  const double t10[10] = {1, c5, c25, -c25, -c5, -1, -c5, -c25, c25, c5};
-  const double t6[6] = {1, 0.5, -0.5, -1, -0.5, 0.5};
-  m %= R;
-  return R == 16 ? t16[m] : R == 12 ? t12[m] : R == 10 ? t10[m] : R == 6 ? t6[m] : 1.0;
-}
-constexpr double root_sin(int R, int m) {
-  const double r2 = 0.70710678118654752440;
-  const double c8 = 0.92387953251128675613;
-  const double s8 = 0.38268343236508977173;
-  const double h3 = 0.86602540378443864676;
-  const double s5 = 0.58778525229247312917;   // sin(pi/5)
-  const double s25 = 0.95105651629515357212;  // sin(2 pi/5)
-  const double t16[16] = {0, s8, r2, c8, 1, c8, r2, s8, 0, -s8, -r2, -c8, -1, -c8, -r2, -s8};
-  const double t12[12] = {0, 0.5, h3, 1, h3, 0.5, 0, -0.5, -h3, -1, -h3, -0.5};
-  const double t10[10] = {0, s5, s25, s25, s5, 0, -s5, -s25, -s25, -s5};
-  const double t6[6] = {0, h3, h3, 0, -h3, -h3};
-  m %= R;
-  return R == 16 ? t16[m] : R == 12 ? t12[m] : R == 10 ? t10[m] : R == 6 ? t6[m] : 0.0;
 }
 
 template <typename T, int R, int DIR>
@@ -228,6 +199,7 @@ struct DftComposite {
       Dft<T, A, DIR>::run(u[n2]);
       static_for<1, A>([&](auto k1c) {
         constexpr int k1 = decltype(k1c)::value;
+        (void)k1;
         if constexpr (n2 > 0) {
           constexpr double c = root_cos(R, n2 * k1);
           constexpr double s = root_sin(R, n2 * k1);
@@ -255,5 +227,16 @@ template <typename T, int DIR>
 struct Dft<T, 12, DIR> : DftComposite<T, 4, 3, DIR> {};
 template <typename T, int DIR>
 struct Dft<T, 16, DIR> : DftComposite<T, 4, 4, DIR> {};
+// register-resident lengths of the one-thread-per-line kernels
+template <typename T, int DIR>
+struct Dft<T, 24, DIR> : DftComposite<T, 8, 3, DIR> {};
+template <typename T, int DIR>
+struct Dft<T, 30, DIR> : DftComposite<T, 10, 3, DIR> {};
+template <typename T, int DIR>
+struct Dft<T, 32, DIR> : DftComposite<T, 8, 4, DIR> {};
+template <typename T, int DIR>
+struct Dft<T, 40, DIR> : DftComposite<T, 8, 5, DIR> {};
+template <typename T, int DIR>
+struct Dft<T, 48, DIR> : DftComposite<T, 16, 3, DIR> {};
 
 }  // namespace psatd

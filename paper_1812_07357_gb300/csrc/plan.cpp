@@ -314,6 +314,7 @@ struct psatd_plan {
   int smem_pf = 0, smem_pi = 0, smem_zf = 0;
   int buf_pf = 0, buf_pi = 0, rows_pi = 0;     // complex elements per plane buffer
   int grid_pf = 0, grid_pi = 0;                // persistent grid sizes
+  int reg_code = -1;                           // register plane kernels for every fast box
 
   // device memory
   std::vector<void*> allocs;
@@ -574,6 +575,20 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     P->smem_z = std::max(P->smem_z, n2 * FIN * nz * csz);
     P->smem_zonly = std::max(P->smem_zonly, n2 * nz * csz);
   }
+  if (P->fast_boxes && P->prec == 32) {
+    // one register-kernel shape for every fast box, or none
+    int code = -2;
+    for (size_t bi = 0; bi < P->boxes.size() && code != -1; ++bi) {
+      const psatd_box& b = P->boxes[bi];
+      const ShapeDev& sh = P->hshapes[P->hboxes[bi].shape];
+      const bool fastb = std::find_if(P->plane_fwd.begin(), P->plane_fwd.end(),
+                                      [&](const int2& j) { return j.x == (int)bi; }) != P->plane_fwd.end();
+      if (!fastb) continue;
+      const int c = reg_shape_code(sh.L, b.n[1]);
+      code = (code == -2 || code == c) ? c : -1;
+    }
+    if (code >= 0 && reg_fwd_smem(code) <= optin && reg_inv_smem(code) <= optin) P->reg_code = code;
+  }
   if (P->fast_boxes) {
     P->smem_pf = 2 * P->buf_pf * csz;
     P->smem_pi = (2 * P->buf_pi + P->rows_pi) * csz;
@@ -726,6 +741,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   // device maximum so that no plan lowers it below another plan's need.
   CK(P, configure_kernels(P->prec, optin));
   CK(P, configure_fast_kernels(P->prec, optin));
+  if (P->prec == 32) CK(P, configure_reg_kernels(optin));
   if (P->fast_boxes) {
     int sms = 0, occ_f = 0, occ_i = 0;
     CK(P, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -933,7 +949,13 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
     int64_t launches = 0;
     for (int step = 0; step < nsteps; ++step) {
       // S1: forward x+y (fast boxes: one plane kernel; generic: x rows, y columns)
-      if (!P->plane_fwd.empty()) {
+      if (!P->plane_fwd.empty() && P->reg_code >= 0) {
+        CK(P, timed(P, 0, st, [&] {
+             return launch_plane_fwd_reg(P->reg_code, D, fp, FIN, P->d_ws, S, P->d_plane_fwd,
+                                         (int64_t)P->plane_fwd.size(), st);
+           }));
+        ++launches;
+      } else if (!P->plane_fwd.empty()) {
         CK(P, timed(P, 0, st, [&] {
              return launch_plane_fwd(P->prec, D, fp, FIN, P->d_ws, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
                                      P->buf_pf, P->smem_pf, P->grid_pf, st);
@@ -963,7 +985,14 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
         ++launches;
       }
       // S3: inverse y+x, interior cells only
-      if (!P->plane_inv.empty()) {
+      if (!P->plane_inv.empty() && P->reg_code >= 0) {
+        CK(P, timed(P, 4, st, [&] {
+             return launch_plane_inv_reg(P->reg_code, D, fp, FOUT, P->d_ws, S, P->d_plane_inv,
+                                         (int64_t)P->plane_inv.size(), P->segs.empty() ? nullptr : P->d_seg_start,
+                                         P->d_segs, st);
+           }));
+        ++launches;
+      } else if (!P->plane_inv.empty()) {
         CK(P, timed(P, 4, st, [&] {
              return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv, (int64_t)P->plane_inv.size(),
                                      P->buf_pi, P->smem_pi, P->grid_pi, P->segs.empty() ? nullptr : P->d_seg_start,

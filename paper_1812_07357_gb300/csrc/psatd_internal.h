@@ -170,6 +170,18 @@ int fast_max_x(int prec);                       // longest n0/2 of a fast-path b
 int z_fast_smem(int prec, int form, int n2);    // bytes of shared memory of k_z_fast
 cudaError_t configure_fast_kernels(int prec, int smem_bytes);
 
+// ---- register-resident plane kernels (reg_kernels.cu), FP32 -----------------
+// code >= 0 when the plane shape (n0/2, n1) has register kernels
+int reg_shape_code(int L, int n1);
+int reg_fwd_smem(int code);
+int reg_inv_smem(int code);
+cudaError_t launch_plane_fwd_reg(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                                 int64_t sstride, const int2* jobs, int64_t nplanes, cudaStream_t st);
+cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                                 int64_t sstride, const int2* jobs, int64_t nplanes, const int* seg_start,
+                                 const GuardSeg* segs, cudaStream_t st);
+cudaError_t configure_reg_kernels(int smem_bytes);
+
 // ---- host helpers (plan.cpp) ------------------------------------------------
 // Radix schedule of a complex FFT length (false if it is not 5-smooth).
 bool radix_plan(int n, AxisPlan& ap);

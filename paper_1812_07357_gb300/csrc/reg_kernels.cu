@@ -1,0 +1,356 @@
+// Register-resident plane kernels (FP32) for boxes whose x half-length L and
+// y length NY have register codelets (L, NY/2 <= 48): every 1D FFT of a
+// plane is done inside registers, so a plane costs two block barriers.
+//
+//   k_plane_fwd_reg  x: one thread per row: the packed length-L complex FFT
+//                    (z[m] = x[2m] + i x[2m+1]) and the R2C split, both in
+//                    registers; y: two threads per column, each a length-NY/2
+//                    FFT of the even / odd rows, joined by one radix-2 step
+//                    whose operands cross between the pair with shuffles.
+//   k_plane_inv_reg  the mirror image, keeping interior rows and cells only,
+//                    and writing the guard cells the plane feeds (fused S4).
+//
+// Twiddle factors are compile-time constants (unit_roots.h).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <type_traits>
+
+#include "fft_codelets.cuh"
+#include "psatd_internal.h"
+
+namespace psatd {
+
+namespace {
+
+constexpr int kRegThreads = 128;
+
+__device__ __forceinline__ void cp16(void* s, const void* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned magic(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
+__device__ __forceinline__ int fdiv(int e, unsigned m) { return m ? (int)__umulhi((unsigned)e, m) : e; }
+
+// w^k for w = exp(DIR 2 pi i / R), a compile-time constant
+template <int R, int K, int DIR>
+__device__ __forceinline__ float2 root() {
+  constexpr float c = (float)root_cos(R, K);
+  constexpr float s = (float)root_sin(R, K);
+  return make_float2(c, DIR < 0 ? -s : s);
+}
+
+// float row pitch of a plane buffer holding rows of n0 reals or n0/2 + 1
+// complex values: >= n0 + 2, a multiple of 4 (16-byte rows) and = 4 (mod 8)
+// so that one-row-per-thread 16-byte accesses spread over all banks.
+constexpr int row_pitch(int n0) {
+  int p = n0 + 2;
+  while (p % 8 != 4) ++p;
+  return p;
+}
+
+// Thread pair (half = 0 even rows, 1 odd rows) -> one length-NY column FFT.
+// v: the pair member's length-NY/2 FFT (in place on entry).  Writes, through
+// st(y, value), the outputs y in [k0, k0 + NY/4) and [k0 + NY/2, ...), with
+// k0 = half * NY/4.
+template <int NY, int DIR, typename Store>
+__device__ __forceinline__ void pair_join(float2* v, int half, Store&& st) {
+  constexpr int H = NY / 2, Q = NY / 4;
+  static_for<0, Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    // half 0 keeps E[i], sends E[Q+i]; half 1 keeps O[Q+i], sends O[i]
+    const float2 send = half ? v[i] : v[Q + i];
+    const float2 keep = half ? v[Q + i] : v[i];
+    float2 recv;
+    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+    const float2 e = half ? recv : keep;
+    const float2 o = half ? keep : recv;
+    const float2 w0 = root<NY, i, DIR>(), w1 = root<NY, Q + i, DIR>();
+    const float2 w = half ? w1 : w0;
+    const float2 t = cmul(o, w);
+    const int k = i + half * Q;
+    st(k, e + t);
+    st(k + H, e - t);
+  });
+}
+
+// Same join, results left in v: v[i] is output row i + half*NY/4 and v[NY/4 + i]
+// output row i + half*NY/4 + NY/2.
+template <int NY, int DIR>
+__device__ __forceinline__ void pair_join_inplace(float2* v, int half) {
+  constexpr int Q = NY / 4;
+  static_for<0, Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const float2 send = half ? v[i] : v[Q + i];
+    const float2 keep = half ? v[Q + i] : v[i];
+    float2 recv;
+    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+    const float2 e = half ? recv : keep;
+    const float2 o = half ? keep : recv;
+    const float2 w0 = root<NY, i, DIR>(), w1 = root<NY, Q + i, DIR>();
+    const float2 t = cmul(o, half ? w1 : w0);
+    v[i] = e + t;
+    v[Q + i] = e - t;
+  });
+}
+
+// ---------------------------------------------------------------------------
+template <int L, int NY>
+__global__ void __launch_bounds__(kRegThreads, 4) k_plane_fwd_reg(DevPlan P, FieldPtrs F, float2* spec,
+                                                                  int64_t sstride, const int2* __restrict__ jobs) {
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0);
+  static_assert(NY <= kRegThreads && 2 * HX <= kRegThreads, "one thread per row / per half column");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* buf = reinterpret_cast<float*>(smem_raw);
+  const int2 J = jobs[blockIdx.x];
+  const int f = blockIdx.y;
+  const BoxDev bx = P.boxes[J.x];
+  const float* g = reinterpret_cast<const float*>(F.p[f]) + bx.foff + (int64_t)J.y * NY * N0;
+  constexpr int UPR = N0 / 4;
+  for (int u = threadIdx.x; u < NY * UPR; u += kRegThreads) {
+    const int r = u / UPR, x = u - r * UPR;
+    cp16(buf + r * PF + 4 * x, g + 4 * u);
+  }
+  cp_commit_wait_all();
+  __syncthreads();
+  // x: row r -> half spectrum X[0..L] written back into the same row
+  if (threadIdx.x < NY) {
+    float* row = buf + threadIdx.x * PF;
+    float2 z[L];
+#pragma unroll
+    for (int j = 0; j < L / 2; ++j) {
+      const float4 q = reinterpret_cast<const float4*>(row)[j];
+      z[2 * j] = make_float2(q.x, q.y);
+      z[2 * j + 1] = make_float2(q.z, q.w);
+    }
+    Dft<float, L, -1>::run(z);
+    float2* xr = reinterpret_cast<float2*>(row);
+    // X[k] = (Z[k] + conj Z[L-k])/2 - i w^k (Z[k] - conj Z[L-k])/2, w = exp(-2 pi i / N0)
+    static_for<0, L / 2 + 1>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const float2 a = z[k % L], b = z[(L - k) % L];
+      const float2 A = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+      const float2 Bv = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
+      if constexpr (k == 0) {
+        xr[0] = make_float2(A.x + Bv.x, A.y + Bv.y);
+        xr[L] = make_float2(A.x - Bv.x, A.y - Bv.y);
+      } else {
+        xr[k] = A + cmul(root<N0, k, -1>(), Bv);
+        if constexpr (2 * k != L) xr[L - k] = conjg(A) + cmul(root<N0, L - k, -1>(), conjg(Bv));
+      }
+    });
+  }
+  __syncthreads();
+  // y: thread pair per column c; threads past the last column repeat it
+  {
+    const int t = threadIdx.x;
+    const int half = t & 1;
+    const int c = min(t >> 1, HX - 1);
+    const bool live = (t >> 1) < HX;
+    const float2* xs = reinterpret_cast<const float2*>(buf);
+    float2 v[NY / 2];
+#pragma unroll
+    for (int m = 0; m < NY / 2; ++m) v[m] = xs[(2 * m + half) * (PF / 2) + c];
+    Dft<float, NY / 2, -1>::run(v);
+    float2* out = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX + c;
+    pair_join<NY, -1>(v, half, [&](int y, float2 val) {
+      if (live) out[y * HX] = val;
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename V>
+__device__ __forceinline__ void copy_rect_w(const float* src, int spitch, float* dst, int64_t dpitch, int ny,
+                                            int nx, int tid, int nthreads) {
+  constexpr int W = sizeof(V) / 4;
+  const int upr = nx / W;
+  const unsigned m = magic(upr);
+  for (int u = tid; u < ny * upr; u += nthreads) {
+    const int r = fdiv(u, m), c = (u - r * upr) * W;
+    *reinterpret_cast<V*>(dst + r * dpitch + c) = *reinterpret_cast<const V*>(src + r * spitch + c);
+  }
+}
+
+template <int L, int NY>
+__global__ void __launch_bounds__(kRegThreads, 4) k_plane_inv_reg(DevPlan P, FieldPtrs F, const float2* spec,
+                                                                  int64_t sstride, const int2* __restrict__ jobs,
+                                                                  const int* __restrict__ seg_start,
+                                                                  const GuardSeg* __restrict__ segs) {
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0), Q = NY / 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // one buffer: first the NY x HX spectrum plane (pitch HX), then, once it is
+  // consumed, the interior rows (pitch PF floats): X values, then real cells
+  float2* sp = reinterpret_cast<float2*>(smem_raw);
+  float* rows = reinterpret_cast<float*>(smem_raw);
+  const int2 J = jobs[blockIdx.x];
+  const int f = blockIdx.y;
+  const BoxDev bx = P.boxes[J.x];
+  const int ylo = bx.ng_lo[1], yhi = NY - bx.ng_hi[1], ni = yhi - ylo;
+  const int xlo = bx.ng_lo[0], nxi = N0 - bx.ng_lo[0] - bx.ng_hi[0];
+  const float2* g = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX;
+  constexpr int UNITS = NY * HX / 2;   // 16-byte units of the contiguous plane
+  for (int u = threadIdx.x; u < UNITS; u += kRegThreads) cp16(sp + 2 * u, g + 2 * u);
+  cp_commit_wait_all();
+  __syncthreads();
+  // y: thread pair per column, inverse; outputs kept in v until the plane is consumed
+  const int t = threadIdx.x;
+  const int half = t & 1;
+  const int c = min(t >> 1, HX - 1);
+  const bool live = (t >> 1) < HX;
+  float2 v[NY / 2];
+#pragma unroll
+  for (int m = 0; m < NY / 2; ++m) v[m] = sp[(2 * m + half) * HX + c];
+  Dft<float, NY / 2, 1>::run(v);
+  pair_join_inplace<NY, 1>(v, half);
+  __syncthreads();
+  if (live) {
+    float2* rs = reinterpret_cast<float2*>(rows);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int y1 = i + half * Q, y2 = y1 + NY / 2;
+      if (y1 >= ylo && y1 < yhi) rs[(y1 - ylo) * (PF / 2) + c] = v[i];
+      if (y2 >= ylo && y2 < yhi) rs[(y2 - ylo) * (PF / 2) + c] = v[Q + i];
+    }
+  }
+  __syncthreads();
+  // x: thread per interior row: C2R merge, inverse packed FFT, interior cells
+  // written back into the thread's own row
+  const float scale = (float)(1.0 / ((double)N0 * NY * bx.n[2]));
+  const bool vec_rows = (nxi % 4 == 0) && (xlo % 4 == 0);
+  if (threadIdx.x < ni) {
+    float* row = rows + threadIdx.x * PF;
+    const float2* xr = reinterpret_cast<const float2*>(row);
+    float2 z[L];
+    // Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), w = exp(-2 pi i / N0)
+    static_for<0, L / 2 + 1>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const float2 a = xr[k], b = xr[L - k];
+      z[k] = (a + conjg(b)) + times_i(cmul(a - conjg(b), root<N0, k, 1>()));
+      if constexpr (k != 0 && 2 * k != L)
+        z[L - k] = (b + conjg(a)) + times_i(cmul(b - conjg(a), root<N0, L - k, 1>()));
+    });
+    Dft<float, L, 1>::run(z);
+    float* o = row - xlo;
+    if (vec_rows) {
+#pragma unroll
+      for (int m = 0; m < L; m += 2) {
+        const int x = 2 * m;
+        if (x >= xlo && x < xlo + nxi)
+          *reinterpret_cast<float4*>(o + x) =
+              make_float4(scale * z[m].x, scale * z[m].y, scale * z[m + 1].x, scale * z[m + 1].y);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < L; ++m) {
+        const int x = 2 * m;
+        if (x >= xlo && x < xlo + nxi) o[x] = scale * z[m].x;
+        if (x + 1 >= xlo && x + 1 < xlo + nxi) o[x + 1] = scale * z[m].y;
+      }
+    }
+  }
+  __syncthreads();
+  // interior cells to this box, then the guard cells this plane feeds
+  float* fbase = reinterpret_cast<float*>(F.p[f]);
+  float* own = fbase + bx.foff + ((int64_t)J.y * NY + ylo) * N0 + xlo;
+  if (vec_rows)
+    copy_rect_w<float4>(rows, PF, own, N0, ni, nxi, threadIdx.x, kRegThreads);
+  else
+    copy_rect_w<float>(rows, PF, own, N0, ni, nxi, threadIdx.x, kRegThreads);
+  if (seg_start) {
+    const int p = blockIdx.x;
+    const int s1 = seg_start[p + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kRegThreads >> 5;
+    for (int si = seg_start[p] + warp; si < s1; si += nw) {
+      const GuardSeg gs = segs[si];
+      const BoxDev db = P.boxes[gs.dst_box];
+      float* dst = fbase + db.foff + ((int64_t)gs.dst_z * db.n[1] + gs.dy) * db.n[0] + gs.dx;
+      const float* src = rows + (gs.sy - ylo) * PF + (gs.sx - xlo);
+      if (gs.vec > 1 && vec_rows)
+        copy_rect_w<float4>(src, PF, dst, db.n[0], gs.ny, gs.nx, lane, 32);
+      else
+        copy_rect_w<float>(src, PF, dst, db.n[0], gs.ny, gs.nx, lane, 32);
+    }
+  }
+}
+
+}  // namespace
+
+// Register-resident plane shapes: X(code, L, NY)
+#define PSATD_REG_SHAPES(X) X(0, 48, 96)
+
+int reg_shape_code(int L, int n1) {
+#define PSATD_RC(code, LV, NYV) \
+  if (L == LV && n1 == NYV) return code;
+  PSATD_REG_SHAPES(PSATD_RC)
+#undef PSATD_RC
+  return -1;
+}
+
+int reg_fwd_smem(int code) {
+#define PSATD_RS(code_, LV, NYV) \
+  if (code == code_) return NYV * row_pitch(2 * LV) * 4;
+  PSATD_REG_SHAPES(PSATD_RS)
+#undef PSATD_RS
+  return 0;
+}
+
+// the spectrum plane, or at most NY interior rows of pitch row_pitch(n0)
+int reg_inv_smem(int code) {
+#define PSATD_RS(code_, LV, NYV) \
+  if (code == code_) return NYV * (LV + 1) * 8 > NYV * row_pitch(2 * LV) * 4 ? NYV * (LV + 1) * 8 \
+                                                                            : NYV * row_pitch(2 * LV) * 4;
+  PSATD_REG_SHAPES(PSATD_RS)
+#undef PSATD_RS
+  return 0;
+}
+
+cudaError_t launch_plane_fwd_reg(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                                 int64_t sstride, const int2* jobs, int64_t nplanes, cudaStream_t st) {
+  if (nplanes <= 0 || nf <= 0) return cudaSuccess;
+  dim3 grid((unsigned)nplanes, nf);
+#define PSATD_RL(code_, LV, NYV)                                                                        \
+  if (code == code_)                                                                                   \
+    k_plane_fwd_reg<LV, NYV><<<grid, kRegThreads, reg_fwd_smem(code_), st>>>(P, f, (float2*)spec, sstride, \
+                                                                           jobs);
+  PSATD_REG_SHAPES(PSATD_RL)
+#undef PSATD_RL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                                 int64_t sstride, const int2* jobs, int64_t nplanes, const int* seg_start,
+                                 const GuardSeg* segs, cudaStream_t st) {
+  if (nplanes <= 0 || nf <= 0) return cudaSuccess;
+  dim3 grid((unsigned)nplanes, nf);
+#define PSATD_RL(code_, LV, NYV)                                                                   \
+  if (code == code_)                                                                              \
+    k_plane_inv_reg<LV, NYV><<<grid, kRegThreads, reg_inv_smem(code_), st>>>(                         \
+        P, f, (const float2*)spec, sstride, jobs, seg_start, segs);
+  PSATD_REG_SHAPES(PSATD_RL)
+#undef PSATD_RL
+  return cudaGetLastError();
+}
+
+cudaError_t configure_reg_kernels(int smem) {
+  cudaError_t e = cudaSuccess;
+#define PSATD_RC(code, LV, NYV)                                                                          \
+  {                                                                                                      \
+    cudaError_t r = cudaFuncSetAttribute(k_plane_fwd_reg<LV, NYV>,                                        \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);            \
+    if (r != cudaSuccess) e = r;                                                                         \
+    r = cudaFuncSetAttribute(k_plane_inv_reg<LV, NYV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    if (r != cudaSuccess) e = r;                                                                         \
+  }
+  PSATD_REG_SHAPES(PSATD_RC)
+#undef PSATD_RC
+  return e;
+}
+
+}  // namespace psatd

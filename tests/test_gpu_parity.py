@@ -296,3 +296,27 @@ def test_fast_equals_generic_fp32():
         outs.append(plan.unpack_fields(df))
         plan.close()
     assert O.rel_l2_fields(lay, outs[0], outs[1], O.COMPS) < 2e-6
+
+
+@pytest.mark.parametrize("prec", [32])
+def test_register_planes_local_96(prec):
+    """Boxes 96 x 96 x 24 (the 96^2 planes of the benchmark boxes run on the
+    register-resident plane kernels), local layout, p = 16, laser, 3 steps;
+    against the oracle and against the generic kernels."""
+    lay = I.local_layout((128, 64, 32), (2, 1, 2), (16, 16, 4), 16)
+    assert all(b.n == (96, 96, 24) for b in lay.boxes)
+    f = I.laser_fields((128, 64, 32), wavelength=8.0, waist=10.0, duration=6.0)
+    fields = {k: I.round_to(I.scatter_global(v, lay), np.float32) for k, v in f.items()}
+    _fast_plan_check(lay, fields, {}, 3, (1.0,) * 3, 0.9, prec, "vacuum", 4)
+    outs = []
+    for generic in (False, True):
+        plan = Plan(lay, (1.0,) * 3, 0.9, precision=32, sources="vacuum", generic=generic)
+        df = plan.pack_fields(fields)
+        plan.push(df, None, 3)
+        plan.sync()
+        outs.append(plan.unpack_fields(df))
+        plan.close()
+    assert O.rel_l2_fields(lay, outs[0], outs[1], O.COMPS) < 2e-6
+    for k in O.COMPS:          # guards written by the fused exchange agree too
+        for a, b in zip(outs[0][k], outs[1][k]):
+            assert np.abs(a - b).max() <= 1e-5 * max(1.0, np.abs(b).max())
