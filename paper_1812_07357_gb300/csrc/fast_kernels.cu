@@ -427,7 +427,10 @@ __global__ void __launch_bounds__(kPlaneThreads, sizeof(T) == 4 ? 2 : 1)
 // ---------------------------------------------------------------------------
 template <typename T, int FORM, int TX, int R1, int R2>
 __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, int64_t zst, int nm, int m0,
-                                       int y, const ShapeDev& sh, const DevPlan& P) {
+                                       int y, int tstride, bool nyq, const ShapeDev& sh, const DevPlan& P) {
+  // column t of the tile is mode column (mx, my) = (m0 + t, y), or for a
+  // Nyquist tile (mx = n0/2 for TX consecutive y) (m0, y + t); its spectrum
+  // starts at g + t * tstride
   constexpr int FIN = fields_in(FORM), FOUT = fields_out(FORM);
   constexpr int NCOL = FIN * TX;
   constexpr int NP = NCOL + ((24 - NCOL % 16) % 16);   // row pitch, = 8 (mod 16)
@@ -438,7 +441,7 @@ __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, in
     const int n2 = it / NCOL, c = it - n2 * NCOL;
     const int s = c / TX, t = c - s * TX;
     if (t >= nm) continue;
-    const cx<T>* p = g + s * sstride + n2 * zst + t;
+    const cx<T>* p = g + s * sstride + n2 * zst + t * tstride;
     cx<T> v[R1];
 #pragma unroll
     for (int j = 0; j < R1; ++j) v[j] = p[j * R2 * zst];
@@ -480,7 +483,7 @@ __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, in
   __syncthreads();
   for (int e = threadIdx.x; e < N * TX; e += blockDim.x) {
     const int z = e / TX, t = e - z * TX;
-    if (t < nm) update_mode<T, FORM>(buf + z * NP + t, TX, m0 + t, y, z, sh, P);
+    if (t < nm) update_mode<T, FORM>(buf + z * NP + t, TX, nyq ? m0 : m0 + t, nyq ? y + t : y, z, sh, P);
   }
   __syncthreads();
   // inverse pass 1 in place on the output slots
@@ -508,7 +511,7 @@ __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, in
 #pragma unroll
     for (int j = 0; j < R2; ++j) u[j] = buf[(k1 * R2 + j) * NP + c];
     Dft<T, R2, 1>::run(u);
-    cx<T>* p = g + s * sstride + t;
+    cx<T>* p = g + s * sstride + t * tstride;
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) p[(k1 + R1 * k2) * zst] = u[k2];
   }
@@ -524,10 +527,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_z_fast(DevPlan P, cx<T>* spec, 
   const ShapeDev& sh = P.shapes[bx.shape];
   const int hx = sh.hx, n1 = bx.n[1];
   const int64_t zst = (int64_t)n1 * hx;
+  const bool nyq = J.nm < 0;
+  const int nm = nyq ? -J.nm : J.nm, ts = nyq ? hx : 1;
   cx<T>* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
   switch (sh.fz) {
 #define PSATD_ARM(code, N, R1, R2) \
-  case code: z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, J.nm, J.m0, J.plane, sh, P); break;
+  case code: z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, nm, J.m0, J.plane, ts, nyq, sh, P); break;
     PSATD_FAST_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
     default: break;

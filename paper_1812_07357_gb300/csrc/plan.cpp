@@ -315,6 +315,7 @@ struct psatd_plan {
   int buf_pf = 0, buf_pi = 0, rows_pi = 0;     // complex elements per plane buffer
   int grid_pf = 0, grid_pi = 0;                // persistent grid sizes
   int reg_code = -1;                           // register plane kernels for every fast box
+  int reg_z = 0;                               // register z kernel length (0: none)
 
   // device memory
   std::vector<void*> allocs;
@@ -534,7 +535,9 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
         if (z >= b.ng_lo[2] && z < n2 - b.ng_hi[2]) P->plane_inv.push_back(make_int2(bi, z));
       }
       for (int y = 0; y < n1; ++y)
-        for (int m = 0; m < hx; m += tile) P->zfast.push_back({bi, y, m, std::min(tile, hx - m)});
+        for (int m = 0; m < L; m += tile) P->zfast.push_back({bi, y, m, std::min(tile, L - m)});
+      // the Nyquist column mx = L in tiles of consecutive y (negative count)
+      for (int y = 0; y < n1; y += tile) P->zfast.push_back({bi, y, L, -std::min(tile, n1 - y)});
       P->buf_pf = std::max(P->buf_pf, n1 * sh.lp);
       P->buf_pi = std::max(P->buf_pi, n1 * hx);
       P->rows_pi = std::max(P->rows_pi, ni * sh.hp);
@@ -588,6 +591,14 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       code = (code == -2 || code == c) ? c : -1;
     }
     if (code >= 0 && reg_fwd_smem(code) <= optin && reg_inv_smem(code) <= optin) P->reg_code = code;
+    // one register z length for every fast box, or none
+    int nz = -2;
+    for (const ColJob& j : P->zfast) {
+      const int n2 = P->boxes[j.box].n[2];
+      nz = (nz == -2 || nz == n2) ? n2 : -1;
+      if (nz == -1) break;
+    }
+    if (nz > 0 && z_reg_ok(nz) && z_reg_smem(P->form, nz) <= optin) P->reg_z = nz;
   }
   if (P->fast_boxes) {
     P->smem_pf = 2 * P->buf_pf * csz;
@@ -972,7 +983,12 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
         launches += 2;
       }
       // S1 (z) + S2 + S3 (z)
-      if (!P->zfast.empty()) {
+      if (!P->zfast.empty() && P->reg_z) {
+        CK(P, timed(P, 2, st, [&] {
+             return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, st);
+           }));
+        ++launches;
+      } else if (!P->zfast.empty()) {
         CK(P, timed(P, 2, st, [&] {
              return launch_z_fast(P->prec, P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->smem_zf, st);
            }));

@@ -76,7 +76,9 @@ struct RowJob {
   int32_t box, r0, nr, pad;
 };
 
-// columns m0 .. m0+nm-1 of one plane (y-axis passes: plane = z; z-axis: plane = y)
+// columns m0 .. m0+nm-1 of one plane (y-axis passes: plane = z; z-axis: plane = y).
+// Fast z tiles with nm < 0 hold the Nyquist column mx = m0 = n0/2 of the -nm
+// planes y = plane .. plane-nm-1.
 struct ColJob {
   int32_t box, plane, m0, nm;
 };
@@ -181,6 +183,11 @@ cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f,
                                  int64_t sstride, const int2* jobs, int64_t nplanes, const int* seg_start,
                                  const GuardSeg* segs, cudaStream_t st);
 cudaError_t configure_reg_kernels(int smem_bytes);
+// register z kernel (FP32, tiles of fast_tile(32) columns) for z length n2
+int z_reg_ok(int n2);
+int z_reg_smem(int form, int n2);
+cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
+                         int64_t njobs, int n2, cudaStream_t st);
 
 // ---- host helpers (plan.cpp) ------------------------------------------------
 // Radix schedule of a complex FFT length (false if it is not 5-smooth).

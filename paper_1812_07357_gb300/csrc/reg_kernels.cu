@@ -9,6 +9,10 @@
 //                    whose operands cross between the pair with shuffles.
 //   k_plane_inv_reg  the mirror image, keeping interior rows and cells only,
 //                    and writing the guard cells the plane feeds (fused S4).
+//   k_z_reg          z FFT of every field slot of a tile of columns (a thread
+//                    pair per column, loads straight from HBM into registers),
+//                    the k-space update of every mode through shared memory,
+//                    and the inverse z FFT of the output slots back to HBM.
 //
 // Twiddle factors are compile-time constants (unit_roots.h).
 #include <cuda_runtime.h>
@@ -18,6 +22,7 @@
 
 #include "fft_codelets.cuh"
 #include "psatd_internal.h"
+#include "psatd_update.cuh"
 
 namespace psatd {
 
@@ -280,7 +285,114 @@ __global__ void __launch_bounds__(kRegThreads, 4) k_plane_inv_reg(DevPlan P, Fie
   }
 }
 
+// ---------------------------------------------------------------------------
+constexpr int kZTile = 8;   // mx columns (or Nyquist-column y rows) per z tile
+
+template <int FORM>
+constexpr int z_reg_threads() {
+  return 2 * fields_in(FORM) * kZTile;
+}
+template <int FORM>
+constexpr int z_reg_pitch() {
+  return fields_in(FORM) * kZTile + ((24 - (fields_in(FORM) * kZTile) % 16) % 16);
+}
+
+template <int NZ, int FORM>
+__global__ void __launch_bounds__(z_reg_threads<FORM>(), 3) k_z_reg(DevPlan P, float2* spec, int64_t sstride,
+                                                                    const ColJob* __restrict__ jobs) {
+  constexpr int TX = kZTile, FOUT = fields_out(FORM);
+  constexpr int NT = z_reg_threads<FORM>(), NP = z_reg_pitch<FORM>();
+  constexpr int H = NZ / 2, Q = NZ / 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* buf = reinterpret_cast<float2*>(smem_raw);    // [z][slot * TX + t], pitch NP
+  const ColJob J = jobs[blockIdx.x];
+  const BoxDev bx = P.boxes[J.box];
+  const ShapeDev& sh = P.shapes[bx.shape];
+  const int hx = sh.hx, n1 = bx.n[1];
+  const int64_t zst = (int64_t)n1 * hx;
+  // column t: mode column (m0 + t, y), or (m0 = n0/2, y + t) for a Nyquist tile
+  const bool nyq = J.nm < 0;
+  const int nm = nyq ? -J.nm : J.nm, ts = nyq ? hx : 1;
+  float2* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
+  const int tid = threadIdx.x, half = tid & 1, col = tid >> 1;
+  const int s = col / TX, t = col - s * TX;
+  const bool live = t < nm;
+  const int tc = live ? t : 0;
+  float2 v[H];
+  {
+    const float2* src = g + s * sstride + (int64_t)tc * ts + half * zst;
+#pragma unroll
+    for (int m = 0; m < H; ++m) v[m] = src[2 * m * zst];
+  }
+  Dft<float, H, -1>::run(v);
+  pair_join_inplace<NZ, -1>(v, half);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    buf[(i + half * Q) * NP + col] = v[i];
+    buf[(i + half * Q + H) * NP + col] = v[Q + i];
+  }
+  __syncthreads();
+  for (int e = tid; e < NZ * TX; e += NT) {
+    const int z = e / TX, tt = e - z * TX;
+    if (tt < nm)
+      update_mode<float, FORM>(buf + z * NP + tt, TX, nyq ? J.m0 : J.m0 + tt, nyq ? J.plane + tt : J.plane, z,
+                               sh, P);
+  }
+  __syncthreads();
+  // inverse of the output slots; threads of the remaining slots repeat the
+  // last output slot (the pair shuffles need both lanes) and store nothing
+  const int so = s < FOUT ? s : FOUT - 1;
+#pragma unroll
+  for (int m = 0; m < H; ++m) v[m] = buf[(2 * m + half) * NP + so * TX + t];
+  Dft<float, H, 1>::run(v);
+  pair_join_inplace<NZ, 1>(v, half);
+  if (live && s < FOUT) {
+    float2* dst = g + s * sstride + (int64_t)t * ts;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int z1 = i + half * Q;
+      dst[z1 * zst] = v[i];
+      dst[(z1 + H) * zst] = v[Q + i];
+    }
+  }
+}
+
 }  // namespace
+
+// z lengths with a register z kernel: X(NZ)
+#define PSATD_REG_Z(X) X(96) X(48)
+
+int z_reg_ok(int n2) {
+#define PSATD_ZC(NZV) \
+  if (n2 == NZV) return 1;
+  PSATD_REG_Z(PSATD_ZC)
+#undef PSATD_ZC
+  return 0;
+}
+
+int z_reg_smem(int form, int n2) {
+  const int ncol = fields_in(form) * kZTile;
+  return n2 * (ncol + ((24 - ncol % 16) % 16)) * 8;
+}
+
+cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
+                         int64_t njobs, int n2, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  dim3 grid((unsigned)njobs);
+  const int smem = z_reg_smem(form, n2);
+#define PSATD_ZL(NZV)                                                                                 \
+  if (n2 == NZV) {                                                                                   \
+    if (form == kVacuum)                                                                             \
+      k_z_reg<NZV, kVacuum><<<grid, z_reg_threads<kVacuum>(), smem, st>>>(P, (float2*)spec, sstride, jobs); \
+    else if (form == kJForm)                                                                         \
+      k_z_reg<NZV, kJForm><<<grid, z_reg_threads<kJForm>(), smem, st>>>(P, (float2*)spec, sstride, jobs);   \
+    else                                                                                             \
+      k_z_reg<NZV, kRhoForm><<<grid, z_reg_threads<kRhoForm>(), smem, st>>>(P, (float2*)spec, sstride, jobs); \
+  }
+  PSATD_REG_Z(PSATD_ZL)
+#undef PSATD_ZL
+  return cudaGetLastError();
+}
 
 // Register-resident plane shapes: X(code, L, NY)
 #define PSATD_REG_SHAPES(X) X(0, 48, 96)
@@ -350,6 +462,17 @@ cudaError_t configure_reg_kernels(int smem) {
   }
   PSATD_REG_SHAPES(PSATD_RC)
 #undef PSATD_RC
+#define PSATD_ZS(NZV)                                                                                      \
+  {                                                                                                        \
+    cudaError_t r = cudaFuncSetAttribute(k_z_reg<NZV, kVacuum>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    if (r != cudaSuccess) e = r;                                                                           \
+    r = cudaFuncSetAttribute(k_z_reg<NZV, kJForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);       \
+    if (r != cudaSuccess) e = r;                                                                           \
+    r = cudaFuncSetAttribute(k_z_reg<NZV, kRhoForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
+    if (r != cudaSuccess) e = r;                                                                           \
+  }
+  PSATD_REG_Z(PSATD_ZS)
+#undef PSATD_ZS
   return e;
 }
 

@@ -320,3 +320,18 @@ def test_register_planes_local_96(prec):
     for k in O.COMPS:          # guards written by the fused exchange agree too
         for a, b in zip(outs[0][k], outs[1][k]):
             assert np.abs(a - b).max() <= 1e-5 * max(1.0, np.abs(b).max())
+
+
+@pytest.mark.parametrize("form", ["rho", "J"])
+def test_register_z_kernel_sources(form):
+    """One 60 x 48 x 96 periodic box, FP32: z length 96 runs on the
+    register-resident z kernel (with sources), including the Nyquist tiles."""
+    lay = I.global_layout((60, 48, 96), 16)
+    rng = np.random.default_rng(41)
+    shp = lay.boxes[0].shape
+    src = {k: [rng.standard_normal(shp)] for k in ("Jx", "Jy", "Jz")}
+    fields = {k: [rng.standard_normal(shp)] for k in O.COMPS}
+    if form == "rho":
+        src["rho"] = [np.zeros(shp)]
+        fields = {k: [np.zeros(shp)] for k in O.COMPS}
+    _fast_plan_check(lay, fields, src, 3, (1.0, 1.0, 1.0), 0.9, 32, form, 1)
