@@ -186,12 +186,15 @@ def build_layout(name):
     return I.hybrid_layout(w["global_n"], w["nsub"], w["ng"], w["p"])
 
 
-def kernel_bytes(layout, s=4, fin=6, fout=6):
+def kernel_bytes(layout, s=4, fin=6, fout=6, fused=True):
     """Compulsory bytes of one launch of every kernel kind (each kernel reads
     its inputs once and writes its outputs once).  Kinds: forward x(+y),
     generic y forward, z + update, generic y inverse, inverse (y+)x, exchange.
     On the fast path the y passes are fused into the x kernels, so kinds 0 and
-    4 carry the plane kernels' bytes and kinds 1 and 3 do not launch."""
+    4 carry the plane kernels' bytes and kinds 1 and 3 do not launch; its z
+    kernel stores the interior z planes only, and with `fused` the inverse
+    plane kernel also writes the guard cells its plane feeds (the exchange
+    kind then does not launch)."""
     C = sum(b.cells for b in layout.boxes)
     M = sum((b.n[0] // 2 + 1) * b.n[1] * b.n[2] for b in layout.boxes)
     Mz = sum((b.n[0] // 2 + 1) * b.n[1] * b.interior[2] for b in layout.boxes)
@@ -205,11 +208,11 @@ def kernel_bytes(layout, s=4, fin=6, fout=6):
                         fout * 2 * Mz * c,              # k_col inverse along y (interior z)
                         fout * (Mr * c + I_ * s),       # k_inv_x (interior rows, cells)
                         fout * 2 * G * s],              # k_exchange: read interior, write guard
-            "fast": [fin * (C * s + M * c),             # k_plane_fwd: real plane in, spectrum out
+            "fast": [fin * (C * s + M * c),             # plane forward: real plane in, spectrum out
                      0,
-                     (fin + fout) * M * c,              # k_z_fast
+                     fin * M * c + fout * Mz * c,       # z kernel: all planes in, interior z out
                      0,
-                     fout * (Mz * c + I_ * s),          # k_plane_inv: interior planes in, cells out
+                     fout * (Mz * c + I_ * s + (G * s if fused else 0)),   # plane inverse
                      fout * 2 * G * s]}
 
 
@@ -276,7 +279,7 @@ def run_gpu(args):
     interior = lay.interior_cells
     value = total_units(interior * args.steps, world) / (ms_max / 1e3)
     peak, peak_src = measured_peaks()
-    kb = kernel_bytes(lay)["fast" if plan.fast_boxes == len(lay.boxes) else "generic"]
+    kb = kernel_bytes(lay, fused=kn[5] == 0)["fast" if plan.fast_boxes == len(lay.boxes) else "generic"]
     avg = [kms[i] / kn[i] if kn[i] else 0.0 for i in range(len(kms))]
     dom = max(range(len(avg)), key=lambda i: avg[i])
     ach = kb[dom] / (avg[dom] / 1e3) / 1e9

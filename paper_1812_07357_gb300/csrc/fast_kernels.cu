@@ -427,10 +427,12 @@ __global__ void __launch_bounds__(kPlaneThreads, sizeof(T) == 4 ? 2 : 1)
 // ---------------------------------------------------------------------------
 template <typename T, int FORM, int TX, int R1, int R2>
 __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, int64_t zst, int nm, int m0,
-                                       int y, int tstride, bool nyq, const ShapeDev& sh, const DevPlan& P) {
+                                       int y, int tstride, bool nyq, int zlo, int zhi, const ShapeDev& sh,
+                                       const DevPlan& P) {
   // column t of the tile is mode column (mx, my) = (m0 + t, y), or for a
   // Nyquist tile (mx = n0/2 for TX consecutive y) (m0, y + t); its spectrum
-  // starts at g + t * tstride
+  // starts at g + t * tstride.  Only the interior z planes [zlo, zhi) are
+  // stored back: the inverse plane pass reads no others.
   constexpr int FIN = fields_in(FORM), FOUT = fields_out(FORM);
   constexpr int NCOL = FIN * TX;
   constexpr int NP = NCOL + ((24 - NCOL % 16) % 16);   // row pitch, = 8 (mod 16)
@@ -481,9 +483,14 @@ __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, in
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < N * TX; e += blockDim.x) {
-    const int z = e / TX, t = e - z * TX;
-    if (t < nm) update_mode<T, FORM>(buf + z * NP + t, TX, nyq ? m0 : m0 + t, nyq ? y + t : y, z, sh, P);
+  static_assert(kThreads % TX == 0, "update threads keep one column");
+  {
+    const int t = threadIdx.x % TX;
+    if (t < nm) {
+      const ModeXY<T> xy = mode_xy<T>(nyq ? m0 : m0 + t, nyq ? y + t : y, sh, P);
+      for (int z = threadIdx.x / TX; z < N; z += kThreads / TX)
+        update_mode_z<T, FORM>(buf + z * NP + t, TX, xy, z, sh, P);
+    }
   }
   __syncthreads();
   // inverse pass 1 in place on the output slots
@@ -513,7 +520,10 @@ __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, in
     Dft<T, R2, 1>::run(u);
     cx<T>* p = g + s * sstride + t * tstride;
 #pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) p[(k1 + R1 * k2) * zst] = u[k2];
+    for (int k2 = 0; k2 < R2; ++k2) {
+      const int z = k1 + R1 * k2;
+      if (z >= zlo && z < zhi) p[z * zst] = u[k2];
+    }
   }
 }
 
@@ -532,7 +542,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_z_fast(DevPlan P, cx<T>* spec, 
   cx<T>* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
   switch (sh.fz) {
 #define PSATD_ARM(code, N, R1, R2) \
-  case code: z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, nm, J.m0, J.plane, ts, nyq, sh, P); break;
+  case code:                                                                                     \
+    z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, nm, J.m0, J.plane, ts, nyq, bx.ng_lo[2], N - bx.ng_hi[2], sh, P); \
+    break;
     PSATD_FAST_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
     default: break;

@@ -355,9 +355,7 @@ struct psatd_plan {
     P.rpool = d_rpool;
     P.cpool = d_cpool;
     P.coef = d_coef;
-    P.c = desc.c;
-    P.eps0 = desc.eps0;
-    P.dt = desc.dt;
+    set_constants(P, desc.c, desc.eps0, desc.dt);
     return P;
   }
 
@@ -599,6 +597,21 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       if (nz == -1) break;
     }
     if (nz > 0 && z_reg_ok(nz) && z_reg_smem(P->form, nz) <= optin) P->reg_z = nz;
+    // the register z kernel has its own tile width: re-tile (jobs are grouped by box)
+    const int rt = z_reg_tile_width(P->form);
+    if (P->reg_z && rt != tile) {
+      std::vector<ColJob> zt;
+      int last = -1;
+      for (const ColJob& j : P->zfast) {
+        if (j.box == last) continue;
+        last = j.box;
+        const int L = P->boxes[j.box].n[0] / 2, n1 = P->boxes[j.box].n[1];
+        for (int y = 0; y < n1; ++y)
+          for (int m = 0; m < L; m += rt) zt.push_back({j.box, y, m, std::min(rt, L - m)});
+        for (int y = 0; y < n1; y += rt) zt.push_back({j.box, y, L, -std::min(rt, n1 - y)});
+      }
+      P->zfast.swap(zt);
+    }
   }
   if (P->fast_boxes) {
     P->smem_pf = 2 * P->buf_pf * csz;

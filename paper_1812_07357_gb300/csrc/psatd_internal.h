@@ -125,7 +125,18 @@ struct DevPlan {
   const void* cpool;              // T2[]
   const void* coef;               // Coef4<T>[]
   double c, eps0, dt;
+  double cc, ieps, idt, icce;     // c^2, 1/eps0, 1/dt, 1/(c^2 eps0)
 };
+
+inline void set_constants(DevPlan& P, double c, double eps0, double dt) {
+  P.c = c;
+  P.eps0 = eps0;
+  P.dt = dt;
+  P.cc = c * c;
+  P.ieps = 1.0 / eps0;
+  P.idt = 1.0 / dt;
+  P.icce = 1.0 / (c * c * eps0);
+}
 
 // ---- kernel launchers (fft_kernels.cu, exchange.cu) ----------------------
 
@@ -183,9 +194,10 @@ cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f,
                                  int64_t sstride, const int2* jobs, int64_t nplanes, const int* seg_start,
                                  const GuardSeg* segs, cudaStream_t st);
 cudaError_t configure_reg_kernels(int smem_bytes);
-// register z kernel (FP32, tiles of fast_tile(32) columns) for z length n2
+// register z kernel (FP32, tiles of z_reg_tile_width(form) columns) for z length n2
 int z_reg_ok(int n2);
 int z_reg_smem(int form, int n2);
+int z_reg_tile_width(int form);
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
                          int64_t njobs, int n2, cudaStream_t st);
 

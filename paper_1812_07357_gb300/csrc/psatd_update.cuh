@@ -27,25 +27,49 @@ __device__ __forceinline__ const T* rpool(const DevPlan& P) {
   return reinterpret_cast<const T*>(P.rpool);
 }
 
+// Quantities of a mode that depend on (mx, my) only: a thread that updates
+// several z of one (mx, my) loads them once.
+template <typename T>
+struct ModeXY {
+  T Kx, Ky;
+  cx<T> px, py, pxy;
+  int64_t qbase;   // coefficient index of (mx, |my|, mz = 0)
+};
+
+template <typename T>
+__device__ __forceinline__ ModeXY<T> mode_xy(int mx, int my, const ShapeDev& sh, const DevPlan& P) {
+  const T* rp = rpool<T>(P);
+  const cx<T>* cp = cpool<T>(P);
+  const int n1 = sh.n[1];
+  const int myr = my <= n1 - my ? my : n1 - my;
+  ModeXY<T> r;
+  r.Kx = rp[sh.kx + mx];
+  r.Ky = rp[sh.ky + my];
+  r.px = cp[sh.phx + mx];
+  r.py = cp[sh.phy + my];
+  r.pxy = cmul(r.px, r.py);
+  r.qbase = sh.coef + (int64_t)myr * sh.hx + mx;
+  return r;
+}
+
 template <typename T, int FORM>
-__device__ __forceinline__ void update_mode(cx<T>* md, int fs, int mx, int my, int mz,
-                                            const ShapeDev& sh, const DevPlan& P) {
+__device__ __forceinline__ void update_mode_z(cx<T>* md, int fs, const ModeXY<T>& m, int mz, const ShapeDev& sh,
+                                              const DevPlan& P) {
   using C = cx<T>;
   const T* rp = rpool<T>(P);
   const C* cp = cpool<T>(P);
-  const int n1 = sh.n[1], n2 = sh.n[2], hx = sh.hx;
-  const T Kx = rp[sh.kx + mx], Ky = rp[sh.ky + my], Kz = rp[sh.kz + mz];
-  const C px = cp[sh.phx + mx], py = cp[sh.phy + my], pz = cp[sh.phz + mz];
-  const int myr = my <= n1 - my ? my : n1 - my;
+  const int n1 = sh.n[1], n2 = sh.n[2];
+  const T Kx = m.Kx, Ky = m.Ky, Kz = rp[sh.kz + mz];
+  const C px = m.px, py = m.py, pz = cp[sh.phz + mz], pxy = m.pxy;
   const int mzr = mz <= n2 - mz ? mz : n2 - mz;
-  const Coef4<T> q = reinterpret_cast<const Coef4<T>*>(P.coef)[sh.coef +
-                                                             ((int64_t)mzr * (n1 / 2 + 1) + myr) * hx + mx];
-  const C pyz = cmul(py, pz), pxz = cmul(px, pz), pxy = cmul(px, py);
+  const Coef4<T> q =
+      reinterpret_cast<const Coef4<T>*>(P.coef)[m.qbase + (int64_t)mzr * (n1 / 2 + 1) * sh.hx];
+  const C pyz = cmul(py, pz), pxz = cmul(px, pz);
   // centred spectra: F~ = exp(-i k.s h) F^
   const C ex = cmulc(md[0], px), ey = cmulc(md[fs], py), ez = cmulc(md[2 * fs], pz);
   const C bx = cmulc(md[3 * fs], pyz), by = cmulc(md[4 * fs], pxz), bz = cmulc(md[5 * fs], pxy);
-  const T cc = T(P.c) * T(P.c);
-  const T ieps = T(1.0 / P.eps0);
+  const T cc = T(P.cc);
+  const T ieps = T(P.ieps);
   // K x B, K x E, K.B
   const C kbx = rmul(Ky, bz) - rmul(Kz, by);
   const C kby = rmul(Kz, bx) - rmul(Kx, bz);
@@ -66,13 +90,13 @@ __device__ __forceinline__ void update_mode(cx<T>* md, int fs, int mx, int my, i
     const C kdj = rmul(Kx, jx) + rmul(Ky, jy) + rmul(Kz, jz);
     const T dt = T(P.dt);
     const C rhon = rho - rmul(dt, times_i(kdj));
-    const T y1 = q.x3 / dt;
-    const T y2 = -q.x1 - q.x3 / dt;
+    const T y1 = q.x3 * T(P.idt);
+    const T y2 = -q.x1 - y1;
     const C g = times_i(rmul(y1, rhon) + rmul(y2, rho));  // i (Y1 rho' + Y2 rho)
     nex = rmul(q.c, ex) + rmul(csw, times_i(kbx)) - rmul(q.s * ieps, jx) + rmul(Kx * ieps, g);
     ney = rmul(q.c, ey) + rmul(csw, times_i(kby)) - rmul(q.s * ieps, jy) + rmul(Ky * ieps, g);
     nez = rmul(q.c, ez) + rmul(csw, times_i(kbz)) - rmul(q.s * ieps, jz) + rmul(Kz * ieps, g);
-    const T x2 = q.x1 / cc * ieps;
+    const T x2 = q.x1 * T(P.icce);
     nbx = nbx + rmul(x2, times_i(rmul(Ky, jz) - rmul(Kz, jy)));
     nby = nby + rmul(x2, times_i(rmul(Kz, jx) - rmul(Kx, jz)));
     nbz = nbz + rmul(x2, times_i(rmul(Kx, jy) - rmul(Ky, jx)));
@@ -89,7 +113,7 @@ __device__ __forceinline__ void update_mode(cx<T>* md, int fs, int mx, int my, i
       nex = nex - rmul(a, jx) + rmul(b * Kx, kdj);
       ney = ney - rmul(a, jy) + rmul(b * Ky, kdj);
       nez = nez - rmul(a, jz) + rmul(b * Kz, kdj);
-      const T x2 = q.x1 / cc * ieps;
+      const T x2 = q.x1 * T(P.icce);
       nbx = nbx + rmul(x2, times_i(rmul(Ky, jz) - rmul(Kz, jy)));
       nby = nby + rmul(x2, times_i(rmul(Kz, jx) - rmul(Kx, jz)));
       nbz = nbz + rmul(x2, times_i(rmul(Kx, jy) - rmul(Ky, jx)));
@@ -102,6 +126,12 @@ __device__ __forceinline__ void update_mode(cx<T>* md, int fs, int mx, int my, i
   md[3 * fs] = cmul(nbx, pyz);
   md[4 * fs] = cmul(nby, pxz);
   md[5 * fs] = cmul(nbz, pxy);
+}
+
+template <typename T, int FORM>
+__device__ __forceinline__ void update_mode(cx<T>* md, int fs, int mx, int my, int mz,
+                                            const ShapeDev& sh, const DevPlan& P) {
+  update_mode_z<T, FORM>(md, fs, mode_xy<T>(mx, my, sh, P), mz, sh, P);
 }
 
 }  // namespace psatd

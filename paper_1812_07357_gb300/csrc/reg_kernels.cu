@@ -58,10 +58,16 @@ constexpr int row_pitch(int n0) {
   return p;
 }
 
-// Thread pair (half = 0 even rows, 1 odd rows) -> one length-NY column FFT.
-// v: the pair member's length-NY/2 FFT (in place on entry).  Writes, through
-// st(y, value), the outputs y in [k0, k0 + NY/4) and [k0 + NY/2, ...), with
-// k0 = half * NY/4.
+// Thread pairs: the two members of a pair are lanes l and l ^ 16 of a warp,
+// so that each half-warp touches one row of a shared-memory plane (no bank
+// conflicts between the members).  Thread t: half = (t >> 4) & 1 picks the
+// even / odd rows, the pair index is (t & 15) + 16 (t >> 5).
+__device__ __forceinline__ int pair_half(int t) { return (t >> 4) & 1; }
+__device__ __forceinline__ int pair_index(int t) { return (t & 15) + ((t >> 5) << 4); }
+
+// Thread pair -> one length-NY column FFT.  v: the pair member's
+// length-NY/2 FFT (in place on entry).  Writes, through st(y, value), the
+// outputs y in [k0, k0 + NY/4) and [k0 + NY/2, ...), with k0 = half * NY/4.
 template <int NY, int DIR, typename Store>
 __device__ __forceinline__ void pair_join(float2* v, int half, Store&& st) {
   constexpr int H = NY / 2, Q = NY / 4;
@@ -71,8 +77,8 @@ __device__ __forceinline__ void pair_join(float2* v, int half, Store&& st) {
     const float2 send = half ? v[i] : v[Q + i];
     const float2 keep = half ? v[Q + i] : v[i];
     float2 recv;
-    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
-    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
     const float2 e = half ? recv : keep;
     const float2 o = half ? keep : recv;
     const float2 w0 = root<NY, i, DIR>(), w1 = root<NY, Q + i, DIR>();
@@ -94,8 +100,8 @@ __device__ __forceinline__ void pair_join_inplace(float2* v, int half) {
     const float2 send = half ? v[i] : v[Q + i];
     const float2 keep = half ? v[Q + i] : v[i];
     float2 recv;
-    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
-    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
+    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
     const float2 e = half ? recv : keep;
     const float2 o = half ? keep : recv;
     const float2 w0 = root<NY, i, DIR>(), w1 = root<NY, Q + i, DIR>();
@@ -155,9 +161,9 @@ __global__ void __launch_bounds__(kRegThreads, 4) k_plane_fwd_reg(DevPlan P, Fie
   // y: thread pair per column c; threads past the last column repeat it
   {
     const int t = threadIdx.x;
-    const int half = t & 1;
-    const int c = min(t >> 1, HX - 1);
-    const bool live = (t >> 1) < HX;
+    const int half = pair_half(t);
+    const int c = min(pair_index(t), HX - 1);
+    const bool live = pair_index(t) < HX;
     const float2* xs = reinterpret_cast<const float2*>(buf);
     float2 v[NY / 2];
 #pragma unroll
@@ -206,9 +212,9 @@ __global__ void __launch_bounds__(kRegThreads, 4) k_plane_inv_reg(DevPlan P, Fie
   __syncthreads();
   // y: thread pair per column, inverse; outputs kept in v until the plane is consumed
   const int t = threadIdx.x;
-  const int half = t & 1;
-  const int c = min(t >> 1, HX - 1);
-  const bool live = (t >> 1) < HX;
+  const int half = pair_half(t);
+  const int c = min(pair_index(t), HX - 1);
+  const bool live = pair_index(t) < HX;
   float2 v[NY / 2];
 #pragma unroll
   for (int m = 0; m < NY / 2; ++m) v[m] = sp[(2 * m + half) * HX + c];
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(kRegThreads, 4) k_plane_inv_reg(DevPlan P, Fie
   __syncthreads();
   // x: thread per interior row: C2R merge, inverse packed FFT, interior cells
   // written back into the thread's own row
-  const float scale = (float)(1.0 / ((double)N0 * NY * bx.n[2]));
+  const float scale = __frcp_rn((float)(N0 * NY * bx.n[2]));   // exact integer < 2^24
   const bool vec_rows = (nxi % 4 == 0) && (xlo % 4 == 0);
   if (threadIdx.x < ni) {
     float* row = rows + threadIdx.x * PF;
@@ -286,23 +292,32 @@ __global__ void __launch_bounds__(kRegThreads, 4) k_plane_inv_reg(DevPlan P, Fie
 }
 
 // ---------------------------------------------------------------------------
-constexpr int kZTile = 8;   // mx columns (or Nyquist-column y rows) per z tile
+// mx columns (or Nyquist-column y rows) per z tile: 16 (128-byte rows of a
+// slot) for the 6-slot vacuum form, 8 for the forms with sources
+constexpr int z_reg_tile(int form) { return form == kVacuum ? 16 : 8; }
 
+// fields_in * tile (slot, column) FFTs per tile, a thread pair each, rounded
+// up to whole warps (the pairs past the last slot compute a copy and store nothing)
 template <int FORM>
 constexpr int z_reg_threads() {
-  return 2 * fields_in(FORM) * kZTile;
+  return (2 * fields_in(FORM) * z_reg_tile(FORM) + 31) / 32 * 32;
+}
+// shared-memory pitch (complex) of one z row: >= fields_in * tile, = 8 (mod 16)
+constexpr int z_reg_pitch(int form) {
+  return fields_in(form) * z_reg_tile(form) + ((24 - (fields_in(form) * z_reg_tile(form)) % 16) % 16);
 }
 template <int FORM>
-constexpr int z_reg_pitch() {
-  return fields_in(FORM) * kZTile + ((24 - (fields_in(FORM) * kZTile) % 16) % 16);
+constexpr int z_reg_min_blocks() {
+  return 2;
 }
 
 template <int NZ, int FORM>
-__global__ void __launch_bounds__(z_reg_threads<FORM>(), 3) k_z_reg(DevPlan P, float2* spec, int64_t sstride,
-                                                                    const ColJob* __restrict__ jobs) {
-  constexpr int TX = kZTile, FOUT = fields_out(FORM);
-  constexpr int NT = z_reg_threads<FORM>(), NP = z_reg_pitch<FORM>();
+__global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>())
+    k_z_reg(DevPlan P, float2* spec, int64_t sstride, const ColJob* __restrict__ jobs) {
+  constexpr int TX = z_reg_tile(FORM), FIN = fields_in(FORM), FOUT = fields_out(FORM);
+  constexpr int NT = z_reg_threads<FORM>(), NP = z_reg_pitch(FORM);
   constexpr int H = NZ / 2, Q = NZ / 4;
+  static_assert(NT % (2 * TX) == 0, "update threads keep one column");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* buf = reinterpret_cast<float2*>(smem_raw);    // [z][slot * TX + t], pitch NP
   const ColJob J = jobs[blockIdx.x];
@@ -314,45 +329,51 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), 3) k_z_reg(DevPlan P, f
   const bool nyq = J.nm < 0;
   const int nm = nyq ? -J.nm : J.nm, ts = nyq ? hx : 1;
   float2* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
-  const int tid = threadIdx.x, half = tid & 1, col = tid >> 1;
+  const int tid = threadIdx.x, half = pair_half(tid), col = pair_index(tid);
   const int s = col / TX, t = col - s * TX;
-  const bool live = t < nm;
-  const int tc = live ? t : 0;
+  const bool live = t < nm && s < FIN;
+  const int tc = t < nm ? t : 0, sc = s < FIN ? s : FIN - 1;
   float2 v[H];
   {
-    const float2* src = g + s * sstride + (int64_t)tc * ts + half * zst;
+    const float2* src = g + sc * sstride + (int64_t)tc * ts + half * zst;
 #pragma unroll
     for (int m = 0; m < H; ++m) v[m] = src[2 * m * zst];
   }
   Dft<float, H, -1>::run(v);
   pair_join_inplace<NZ, -1>(v, half);
+  if (s < FIN) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    buf[(i + half * Q) * NP + col] = v[i];
-    buf[(i + half * Q + H) * NP + col] = v[Q + i];
+    for (int i = 0; i < Q; ++i) {
+      buf[(i + half * Q) * NP + col] = v[i];
+      buf[(i + half * Q + H) * NP + col] = v[Q + i];
+    }
   }
   __syncthreads();
-  for (int e = tid; e < NZ * TX; e += NT) {
-    const int z = e / TX, tt = e - z * TX;
-    if (tt < nm)
-      update_mode<float, FORM>(buf + z * NP + tt, TX, nyq ? J.m0 : J.m0 + tt, nyq ? J.plane + tt : J.plane, z,
-                               sh, P);
+  // k-space update: thread tid keeps column tt = tid % TX and walks z
+  {
+    const int tt = tid % TX;
+    if (tt < nm) {
+      const ModeXY<float> xy = mode_xy<float>(nyq ? J.m0 : J.m0 + tt, nyq ? J.plane + tt : J.plane, sh, P);
+      for (int z = tid / TX; z < NZ; z += NT / TX) update_mode_z<float, FORM>(buf + z * NP + tt, TX, xy, z, sh, P);
+    }
   }
   __syncthreads();
   // inverse of the output slots; threads of the remaining slots repeat the
-  // last output slot (the pair shuffles need both lanes) and store nothing
+  // last output slot (the pair shuffles need both lanes) and store nothing.
+  // Only interior z planes are stored: the inverse plane pass reads no others.
   const int so = s < FOUT ? s : FOUT - 1;
 #pragma unroll
   for (int m = 0; m < H; ++m) v[m] = buf[(2 * m + half) * NP + so * TX + t];
   Dft<float, H, 1>::run(v);
   pair_join_inplace<NZ, 1>(v, half);
   if (live && s < FOUT) {
+    const int zlo = bx.ng_lo[2], zhi = NZ - bx.ng_hi[2];
     float2* dst = g + s * sstride + (int64_t)t * ts;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int z1 = i + half * Q;
-      dst[z1 * zst] = v[i];
-      dst[(z1 + H) * zst] = v[Q + i];
+      const int z1 = i + half * Q, z2 = z1 + H;
+      if (z1 >= zlo && z1 < zhi) dst[z1 * zst] = v[i];
+      if (z2 >= zlo && z2 < zhi) dst[z2 * zst] = v[Q + i];
     }
   }
 }
@@ -370,10 +391,9 @@ int z_reg_ok(int n2) {
   return 0;
 }
 
-int z_reg_smem(int form, int n2) {
-  const int ncol = fields_in(form) * kZTile;
-  return n2 * (ncol + ((24 - ncol % 16) % 16)) * 8;
-}
+int z_reg_smem(int form, int n2) { return n2 * z_reg_pitch(form) * 8; }
+
+int z_reg_tile_width(int form) { return z_reg_tile(form); }
 
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
                          int64_t njobs, int n2, cudaStream_t st) {

@@ -230,9 +230,7 @@ extern "C" psatd_status psatd_push_box_static(const int32_t n[3], int32_t order_
   P.rpool = A + o_r32;
   P.cpool = A + o_c32;
   P.coef = A + o_q32;
-  P.c = c;
-  P.eps0 = 1.0;
-  P.dt = dt;
+  set_constants(P, c, 1.0, dt);
   void* ws = A + o_ws;
   const RowJob* drows = reinterpret_cast<const RowJob*>(A + o_rows);
   const ColJob* dy = reinterpret_cast<const ColJob*>(A + o_ycols);
