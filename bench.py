@@ -417,15 +417,31 @@ def oracle_sample(lay, w, fac, target_s=12.0, max_boxes=64):
                       f"scipy.fft oracle), {dt:.1f} s"}
 
 
+def kernel_source_digest():
+    """SHA-256 over the CUDA/C++ sources of the library (sorted by name): a
+    committed ncu traffic figure counts only for the sources it was taken on."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1812_07357_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
 def _ncu_traffic(kernel_name, workload):
     """Per-launch DRAM bytes of the dominant kernel from a committed ncu
     summary (profiles/<kernel>_<workload>.json), if one exists for the
-    current kernel source; else None."""
+    current kernel sources; else None."""
     base = kernel_name.split("(")[0]
     p = os.path.join(ROOT, "profiles", f"{base}_{workload}.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
+        if d.get("source_sha256") != kernel_source_digest():
+            return None
         return d.get("dram_bytes_per_launch")
     except Exception:
         return None

@@ -349,12 +349,19 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
     }
   }
   __syncthreads();
-  // k-space update: thread tid keeps column tt = tid % TX and walks z
+  // k-space update: thread tid keeps column tt = tid % TX and walks z with a
+  // compile-time trip count (unrolled, so the table loads of all its modes
+  // are in flight together)
   {
-    const int tt = tid % TX;
+    constexpr int ZS = NT / TX, NIT = (NZ + ZS - 1) / ZS;
+    const int tt = tid % TX, z0 = tid / TX;
     if (tt < nm) {
       const ModeXY<float> xy = mode_xy<float>(nyq ? J.m0 : J.m0 + tt, nyq ? J.plane + tt : J.plane, sh, P);
-      for (int z = tid / TX; z < NZ; z += NT / TX) update_mode_z<float, FORM>(buf + z * NP + tt, TX, xy, z, sh, P);
+#pragma unroll
+      for (int j = 0; j < NIT; ++j) {
+        const int z = z0 + j * ZS;
+        if (NZ % ZS == 0 || z < NZ) update_mode_z<float, FORM>(buf + z * NP + tt, TX, xy, z, sh, P);
+      }
     }
   }
   __syncthreads();
