@@ -35,6 +35,10 @@ __device__ __forceinline__ float2 operator-(float2 a, float2 b) {
       : "l"(*reinterpret_cast<const unsigned long long*>(&a)), "l"(*reinterpret_cast<const unsigned long long*>(&b)));
   return *reinterpret_cast<const float2*>(&r);
 }
+// lane-wise product and negation of two-lane FP32 values (the packed update
+// keeps the same real quantity of two modes in one float2)
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 

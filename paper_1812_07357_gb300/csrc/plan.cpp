@@ -339,6 +339,13 @@ struct psatd_plan {
   cudaStream_t last_stream = nullptr;
   int64_t last_launches = 0;
 
+  // multi-step pushes replay one captured step (CUDA graph) per field set
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;   // capture only; never executes work
+  FieldPtrs graph_fp{};
+  int graph_nf = 0;
+  int64_t graph_launches = 0;
+
   // per-kernel timing (diagnostics)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -361,6 +368,8 @@ struct psatd_plan {
 
   ~psatd_plan() {
     cudaDeviceSynchronize();
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (void* p : allocs) cudaFree(p);
     for (auto& r : recs) {
       ev_pool.push_back(r.a);
@@ -956,94 +965,155 @@ psatd_status psatd_guard_exchange(psatd_plan* P, const psatd_fields* f, const ps
   }
 }
 
+// One step S1..S4 of every box on `st`; adds the launches to *launches.
+static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, cudaStream_t st,
+                              int64_t* launches_out) {
+  const int FIN = fields_in(P->form), FOUT = fields_out(P->form);
+  const int64_t S = P->spec_total;
+  int64_t launches = 0;
+  // S1: forward x+y (fast boxes: one plane kernel; generic: x rows, y columns)
+  if (!P->plane_fwd.empty() && P->reg_code >= 0) {
+    CK(P, timed(P, 0, st, [&] {
+         return launch_plane_fwd_reg(P->reg_code, D, fp, FIN, P->d_ws, S, P->d_plane_fwd,
+                                     (int64_t)P->plane_fwd.size(), st);
+       }));
+    ++launches;
+  } else if (!P->plane_fwd.empty()) {
+    CK(P, timed(P, 0, st, [&] {
+         return launch_plane_fwd(P->prec, D, fp, FIN, P->d_ws, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
+                                 P->buf_pf, P->smem_pf, P->grid_pf, st);
+       }));
+    ++launches;
+  }
+  if (!P->g_rows.empty()) {
+    CK(P, timed(P, 0, st, [&] {
+         return launch_fwd_x(P->prec, D, fp, FIN, P->d_ws, S, P->d_g_rows, (int64_t)P->g_rows.size(), P->smem_fx, st);
+       }));
+    CK(P, timed(P, 1, st, [&] {
+         return launch_col(P->prec, -1, 1, D, P->d_ws, S, FIN, P->d_g_ycols, (int64_t)P->g_ycols.size(), P->smem_y, st);
+       }));
+    launches += 2;
+  }
+  // S1 (z) + S2 + S3 (z)
+  if (!P->zfast.empty() && P->reg_z) {
+    CK(P, timed(P, 2, st, [&] {
+         return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, st);
+       }));
+    ++launches;
+  } else if (!P->zfast.empty()) {
+    CK(P, timed(P, 2, st, [&] {
+         return launch_z_fast(P->prec, P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->smem_zf, st);
+       }));
+    ++launches;
+  }
+  if (!P->g_zcols.empty()) {
+    CK(P, timed(P, 2, st, [&] {
+         return launch_z_update(P->prec, P->form, D, P->d_ws, S, P->d_g_zcols, (int64_t)P->g_zcols.size(), P->smem_z, st);
+       }));
+    ++launches;
+  }
+  // S3: inverse y+x, interior cells only
+  if (!P->plane_inv.empty() && P->reg_code >= 0) {
+    CK(P, timed(P, 4, st, [&] {
+         return launch_plane_inv_reg(P->reg_code, D, fp, FOUT, P->d_ws, S, P->d_plane_inv,
+                                     (int64_t)P->plane_inv.size(), P->segs.empty() ? nullptr : P->d_seg_start,
+                                     P->d_segs, st);
+       }));
+    ++launches;
+  } else if (!P->plane_inv.empty()) {
+    CK(P, timed(P, 4, st, [&] {
+         return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv, (int64_t)P->plane_inv.size(),
+                                 P->buf_pi, P->smem_pi, P->grid_pi, P->segs.empty() ? nullptr : P->d_seg_start,
+                                 P->d_segs, st);
+       }));
+    ++launches;
+  }
+  if (!P->g_rows.empty()) {
+    CK(P, timed(P, 3, st, [&] {
+         return launch_col(P->prec, 1, 1, D, P->d_ws, S, FOUT, P->d_g_ycols_int, (int64_t)P->g_ycols_int.size(), P->smem_y, st);
+       }));
+    CK(P, timed(P, 4, st, [&] {
+         return launch_inv_x(P->prec, D, fp, FOUT, P->d_ws, S, P->d_g_rows_int, (int64_t)P->g_rows_int.size(), P->smem_ix, 1, st);
+       }));
+    launches += 2;
+  }
+  if (!P->step_tiles.empty()) {
+    CK(P, timed(P, 5, st, [&] {
+         return launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_step_tiles, (int64_t)P->step_tiles.size(),
+                                st);
+       }));
+    ++launches;
+  }
+  *launches_out += launches;
+  return PSATD_OK;
+}
+
+// Capture one step into a CUDA graph for the field set fp (kept until the
+// field pointers change).  The capture runs on a plan-owned stream (nothing
+// executes during capture), so the graph can then be launched on any stream,
+// the legacy default stream included.  Returns false, with nothing captured,
+// when the caller's stream is itself being captured or capture fails; the
+// push then launches the kernels directly.
+static bool step_graph(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, int nf, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  if (P->graph_exec && nf == P->graph_nf && std::memcmp(&fp, &P->graph_fp, sizeof(FieldPtrs)) == 0) return true;
+  if (!P->cap_stream && cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    P->cap_stream = nullptr;
+    cudaGetLastError();
+    return false;
+  }
+  if (P->graph_exec) {
+    cudaGraphExecDestroy(P->graph_exec);
+    P->graph_exec = nullptr;
+  }
+  if (cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int64_t n = 0;
+  const psatd_status r = push_step(P, D, fp, P->cap_stream, &n);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(P->cap_stream, &g);
+  cudaGraphExec_t x = nullptr;
+  const bool ok = r == PSATD_OK && e == cudaSuccess && g && cudaGraphInstantiate(&x, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    cudaGetLastError();
+    if (x) cudaGraphExecDestroy(x);
+    return false;
+  }
+  P->graph_exec = x;
+  P->graph_fp = fp;
+  P->graph_nf = nf;
+  P->graph_launches = n;
+  return true;
+}
+
 psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_sources* s, int32_t nsteps,
                         void* stream) {
   if (!P) return PSATD_ERR_INVALID_ARG;
   if (nsteps < 0) return fail(P, PSATD_ERR_INVALID_ARG, "nsteps < 0");
   try {
-    FieldPtrs fp;
+    FieldPtrs fp{};
     int nf = 0;
     psatd_status r = gather_fields(P, f, s, true, &fp, &nf);
     if (r != PSATD_OK) return r;
     cudaStream_t st = (cudaStream_t)stream;
     P->last_stream = st;
     const DevPlan D = P->dev();
-    const int FIN = fields_in(P->form), FOUT = fields_out(P->form);
-    const int64_t S = P->spec_total;
     int64_t launches = 0;
-    for (int step = 0; step < nsteps; ++step) {
-      // S1: forward x+y (fast boxes: one plane kernel; generic: x rows, y columns)
-      if (!P->plane_fwd.empty() && P->reg_code >= 0) {
-        CK(P, timed(P, 0, st, [&] {
-             return launch_plane_fwd_reg(P->reg_code, D, fp, FIN, P->d_ws, S, P->d_plane_fwd,
-                                         (int64_t)P->plane_fwd.size(), st);
-           }));
-        ++launches;
-      } else if (!P->plane_fwd.empty()) {
-        CK(P, timed(P, 0, st, [&] {
-             return launch_plane_fwd(P->prec, D, fp, FIN, P->d_ws, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
-                                     P->buf_pf, P->smem_pf, P->grid_pf, st);
-           }));
-        ++launches;
-      }
-      if (!P->g_rows.empty()) {
-        CK(P, timed(P, 0, st, [&] {
-             return launch_fwd_x(P->prec, D, fp, FIN, P->d_ws, S, P->d_g_rows, (int64_t)P->g_rows.size(), P->smem_fx, st);
-           }));
-        CK(P, timed(P, 1, st, [&] {
-             return launch_col(P->prec, -1, 1, D, P->d_ws, S, FIN, P->d_g_ycols, (int64_t)P->g_ycols.size(), P->smem_y, st);
-           }));
-        launches += 2;
-      }
-      // S1 (z) + S2 + S3 (z)
-      if (!P->zfast.empty() && P->reg_z) {
-        CK(P, timed(P, 2, st, [&] {
-             return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, st);
-           }));
-        ++launches;
-      } else if (!P->zfast.empty()) {
-        CK(P, timed(P, 2, st, [&] {
-             return launch_z_fast(P->prec, P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->smem_zf, st);
-           }));
-        ++launches;
-      }
-      if (!P->g_zcols.empty()) {
-        CK(P, timed(P, 2, st, [&] {
-             return launch_z_update(P->prec, P->form, D, P->d_ws, S, P->d_g_zcols, (int64_t)P->g_zcols.size(), P->smem_z, st);
-           }));
-        ++launches;
-      }
-      // S3: inverse y+x, interior cells only
-      if (!P->plane_inv.empty() && P->reg_code >= 0) {
-        CK(P, timed(P, 4, st, [&] {
-             return launch_plane_inv_reg(P->reg_code, D, fp, FOUT, P->d_ws, S, P->d_plane_inv,
-                                         (int64_t)P->plane_inv.size(), P->segs.empty() ? nullptr : P->d_seg_start,
-                                         P->d_segs, st);
-           }));
-        ++launches;
-      } else if (!P->plane_inv.empty()) {
-        CK(P, timed(P, 4, st, [&] {
-             return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv, (int64_t)P->plane_inv.size(),
-                                     P->buf_pi, P->smem_pi, P->grid_pi, P->segs.empty() ? nullptr : P->d_seg_start,
-                                     P->d_segs, st);
-           }));
-        ++launches;
-      }
-      if (!P->g_rows.empty()) {
-        CK(P, timed(P, 3, st, [&] {
-             return launch_col(P->prec, 1, 1, D, P->d_ws, S, FOUT, P->d_g_ycols_int, (int64_t)P->g_ycols_int.size(), P->smem_y, st);
-           }));
-        CK(P, timed(P, 4, st, [&] {
-             return launch_inv_x(P->prec, D, fp, FOUT, P->d_ws, S, P->d_g_rows_int, (int64_t)P->g_rows_int.size(), P->smem_ix, 1, st);
-           }));
-        launches += 2;
-      }
-      if (!P->step_tiles.empty()) {
-        CK(P, timed(P, 5, st, [&] {
-             return launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_step_tiles, (int64_t)P->step_tiles.size(),
-                                    st);
-           }));
-        ++launches;
+    const bool graph = nsteps > 1 && !(P->desc.flags & PSATD_NO_GRAPH) && !P->timing && step_graph(P, D, fp, nf, st);
+    if (graph) {
+      for (int step = 0; step < nsteps; ++step) CK(P, cudaGraphLaunch(P->graph_exec, st));
+      launches = P->graph_launches * nsteps;
+    } else {
+      for (int step = 0; step < nsteps; ++step) {
+        r = push_step(P, D, fp, st, &launches);
+        if (r != PSATD_OK) return r;
       }
     }
     P->last_launches = launches;

@@ -13,6 +13,8 @@
 // constant over the step; paper Sec. 1.1 states the principle).
 #pragma once
 
+#include <type_traits>
+
 #include "fft_codelets.cuh"
 #include "psatd_internal.h"
 
@@ -52,24 +54,44 @@ __device__ __forceinline__ ModeXY<T> mode_xy(int mx, int my, const ShapeDev& sh,
   return r;
 }
 
-template <typename T, int FORM>
-__device__ __forceinline__ void update_mode_z(cx<T>* md, int fs, const ModeXY<T>& m, int mz, const ShapeDev& sh,
-                                              const DevPlan& P) {
-  using C = cx<T>;
-  const T* rp = rpool<T>(P);
-  const C* cp = cpool<T>(P);
-  const int n1 = sh.n[1], n2 = sh.n[2];
-  const T Kx = m.Kx, Ky = m.Ky, Kz = rp[sh.kz + mz];
-  const C px = m.px, py = m.py, pz = cp[sh.phz + mz], pxy = m.pxy;
-  const int mzr = mz <= n2 - mz ? mz : n2 - mz;
-  const Coef4<T> q =
-      reinterpret_cast<const Coef4<T>*>(P.coef)[m.qbase + (int64_t)mzr * (n1 / 2 + 1) * sh.hx];
+// ---- value types of the update ---------------------------------------------
+// The arithmetic below is written once for a real type T and a complex type C:
+// (float, float2) and (double, double2) update one mode; (float2, C2) update
+// two modes at once, lane 0 and lane 1 of every packed register holding the
+// same quantity of mode A and mode B (two-lane FP32 instructions of sm_100+,
+// each lane rounded like the scalar instruction).
+struct C2 {
+  float2 x, y;   // real parts (A, B), imaginary parts (A, B)
+};
+__device__ __forceinline__ C2 operator+(C2 a, C2 b) { return C2{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ C2 operator-(C2 a, C2 b) { return C2{a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ C2 cmul(C2 a, C2 b) {
+  return C2{__ffma2_rn(a.x, b.x, -(a.y * b.y)), __ffma2_rn(a.x, b.y, a.y * b.x)};
+}
+__device__ __forceinline__ C2 cmulc(C2 a, C2 b) {   // a * conj(b)
+  return C2{__ffma2_rn(a.x, b.x, a.y * b.y), __ffma2_rn(a.y, b.x, -(a.x * b.y))};
+}
+
+template <typename T>
+__device__ __forceinline__ T bcast(double v) {
+  if constexpr (std::is_same<T, float2>::value)
+    return make_float2((float)v, (float)v);
+  else
+    return T(v);
+}
+
+// The update of one mode (or of two, with the packed types) in centred form;
+// m[0..FIN) holds the field slots of the mode (see Form) in the sampled
+// (uncentred) representation and receives E', B' (and rho').
+template <typename T, typename C, int FORM>
+__device__ __forceinline__ void update_core(C* m, T Kx, T Ky, T Kz, C px, C py, C pz, C pxy, const Coef4<T>& q,
+                                            const DevPlan& P) {
   const C pyz = cmul(py, pz), pxz = cmul(px, pz);
   // centred spectra: F~ = exp(-i k.s h) F^
-  const C ex = cmulc(md[0], px), ey = cmulc(md[fs], py), ez = cmulc(md[2 * fs], pz);
-  const C bx = cmulc(md[3 * fs], pyz), by = cmulc(md[4 * fs], pxz), bz = cmulc(md[5 * fs], pxy);
-  const T cc = T(P.cc);
-  const T ieps = T(P.ieps);
+  const C ex = cmulc(m[0], px), ey = cmulc(m[1], py), ez = cmulc(m[2], pz);
+  const C bx = cmulc(m[3], pyz), by = cmulc(m[4], pxz), bz = cmulc(m[5], pxy);
+  const T cc = bcast<T>(P.cc);
+  const T ieps = bcast<T>(P.ieps);
   // K x B, K x E, K.B
   const C kbx = rmul(Ky, bz) - rmul(Kz, by);
   const C kby = rmul(Kz, bx) - rmul(Kx, bz);
@@ -85,47 +107,120 @@ __device__ __forceinline__ void update_mode_z(cx<T>* md, int fs, const ModeXY<T>
   C nbz = rmul(q.c, bz) + rmul(q.x1 * Kz, kdb) - rmul(q.s, times_i(kez));
   C nex, ney, nez;
   if (FORM == kRhoForm) {
-    const C rho = md[6 * fs];
-    const C jx = cmulc(md[7 * fs], px), jy = cmulc(md[8 * fs], py), jz = cmulc(md[9 * fs], pz);
+    const C rho = m[6];
+    const C jx = cmulc(m[7], px), jy = cmulc(m[8], py), jz = cmulc(m[9], pz);
     const C kdj = rmul(Kx, jx) + rmul(Ky, jy) + rmul(Kz, jz);
-    const T dt = T(P.dt);
+    const T dt = bcast<T>(P.dt);
     const C rhon = rho - rmul(dt, times_i(kdj));
-    const T y1 = q.x3 * T(P.idt);
+    const T y1 = q.x3 * bcast<T>(P.idt);
     const T y2 = -q.x1 - y1;
     const C g = times_i(rmul(y1, rhon) + rmul(y2, rho));  // i (Y1 rho' + Y2 rho)
     nex = rmul(q.c, ex) + rmul(csw, times_i(kbx)) - rmul(q.s * ieps, jx) + rmul(Kx * ieps, g);
     ney = rmul(q.c, ey) + rmul(csw, times_i(kby)) - rmul(q.s * ieps, jy) + rmul(Ky * ieps, g);
     nez = rmul(q.c, ez) + rmul(csw, times_i(kbz)) - rmul(q.s * ieps, jz) + rmul(Kz * ieps, g);
-    const T x2 = q.x1 * T(P.icce);
+    const T x2 = q.x1 * bcast<T>(P.icce);
     nbx = nbx + rmul(x2, times_i(rmul(Ky, jz) - rmul(Kz, jy)));
     nby = nby + rmul(x2, times_i(rmul(Kz, jx) - rmul(Kx, jz)));
     nbz = nbz + rmul(x2, times_i(rmul(Kx, jy) - rmul(Ky, jx)));
-    md[6 * fs] = rhon;
+    m[6] = rhon;
   } else {
     const C kde = rmul(Kx, ex) + rmul(Ky, ey) + rmul(Kz, ez);
     nex = rmul(q.c, ex) + rmul(q.x1 * Kx, kde) + rmul(csw, times_i(kbx));
     ney = rmul(q.c, ey) + rmul(q.x1 * Ky, kde) + rmul(csw, times_i(kby));
     nez = rmul(q.c, ez) + rmul(q.x1 * Kz, kde) + rmul(csw, times_i(kbz));
     if (FORM == kJForm) {
-      const C jx = cmulc(md[6 * fs], px), jy = cmulc(md[7 * fs], py), jz = cmulc(md[8 * fs], pz);
+      const C jx = cmulc(m[6], px), jy = cmulc(m[7], py), jz = cmulc(m[8], pz);
       const C kdj = rmul(Kx, jx) + rmul(Ky, jy) + rmul(Kz, jz);
       const T a = q.s * ieps, b = q.x3 * ieps;
       nex = nex - rmul(a, jx) + rmul(b * Kx, kdj);
       ney = ney - rmul(a, jy) + rmul(b * Ky, kdj);
       nez = nez - rmul(a, jz) + rmul(b * Kz, kdj);
-      const T x2 = q.x1 * T(P.icce);
+      const T x2 = q.x1 * bcast<T>(P.icce);
       nbx = nbx + rmul(x2, times_i(rmul(Ky, jz) - rmul(Kz, jy)));
       nby = nby + rmul(x2, times_i(rmul(Kz, jx) - rmul(Kx, jz)));
       nbz = nbz + rmul(x2, times_i(rmul(Kx, jy) - rmul(Ky, jx)));
     }
   }
   // back to the staggered sample positions: F^ = exp(+i k.s h) F~
-  md[0] = cmul(nex, px);
-  md[fs] = cmul(ney, py);
-  md[2 * fs] = cmul(nez, pz);
-  md[3 * fs] = cmul(nbx, pyz);
-  md[4 * fs] = cmul(nby, pxz);
-  md[5 * fs] = cmul(nbz, pxy);
+  m[0] = cmul(nex, px);
+  m[1] = cmul(ney, py);
+  m[2] = cmul(nez, pz);
+  m[3] = cmul(nbx, pyz);
+  m[4] = cmul(nby, pxz);
+  m[5] = cmul(nbz, pxy);
+}
+
+// One mode (mx, my, mz): md[f * fs] is field slot f.
+template <typename T, int FORM>
+__device__ __forceinline__ void update_mode_z(cx<T>* md, int fs, const ModeXY<T>& m, int mz, const ShapeDev& sh,
+                                              const DevPlan& P) {
+  using C = cx<T>;
+  const int n1 = sh.n[1], n2 = sh.n[2];
+  const T Kz = rpool<T>(P)[sh.kz + mz];
+  const C pz = cpool<T>(P)[sh.phz + mz];
+  const int mzr = mz <= n2 - mz ? mz : n2 - mz;
+  const Coef4<T> q =
+      reinterpret_cast<const Coef4<T>*>(P.coef)[m.qbase + (int64_t)mzr * (n1 / 2 + 1) * sh.hx];
+  C v[fields_in(FORM)];
+#pragma unroll
+  for (int f = 0; f < fields_in(FORM); ++f) v[f] = md[f * fs];
+  update_core<T, C, FORM>(v, m.Kx, m.Ky, Kz, m.px, m.py, pz, m.pxy, q, P);
+#pragma unroll
+  for (int f = 0; f < fields_out(FORM); ++f) md[f * fs] = v[f];
+}
+
+// ---- two modes per thread (FP32) --------------------------------------------
+// Modes A and B share mz and are adjacent in shared memory (columns t, t + 1
+// of a z tile): A = (mxA, myA), B = (mxB, myB).
+struct ModeXY2 {
+  float2 Kx, Ky;
+  C2 px, py, pxy;
+  int64_t qa, qb;   // coefficient indices of A and B at mz = 0
+};
+
+__device__ __forceinline__ C2 pack2(float2 a, float2 b) { return C2{make_float2(a.x, b.x), make_float2(a.y, b.y)}; }
+
+__device__ __forceinline__ ModeXY2 mode_xy2(int mxa, int mya, int mxb, int myb, const ShapeDev& sh,
+                                            const DevPlan& P) {
+  const ModeXY<float> a = mode_xy<float>(mxa, mya, sh, P), b = mode_xy<float>(mxb, myb, sh, P);
+  ModeXY2 r;
+  r.Kx = make_float2(a.Kx, b.Kx);
+  r.Ky = make_float2(a.Ky, b.Ky);
+  r.px = pack2(a.px, b.px);
+  r.py = pack2(a.py, b.py);
+  r.pxy = pack2(a.pxy, b.pxy);
+  r.qa = a.qbase;
+  r.qb = b.qbase;
+  return r;
+}
+
+// md: mode A of field slot 0 (16-byte aligned); slot f of A and B is the
+// float4 at md + f * fs (complex elements).
+template <int FORM>
+__device__ __forceinline__ void update_mode_z2(float2* md, int fs, const ModeXY2& m, int mz, const ShapeDev& sh,
+                                               const DevPlan& P) {
+  const int n1 = sh.n[1], n2 = sh.n[2];
+  const float kz = rpool<float>(P)[sh.kz + mz];
+  const float2 pz1 = cpool<float>(P)[sh.phz + mz];
+  const int mzr = mz <= n2 - mz ? mz : n2 - mz;
+  const int64_t zoff = (int64_t)mzr * (n1 / 2 + 1) * sh.hx;
+  const float4 qa = reinterpret_cast<const float4*>(P.coef)[m.qa + zoff];
+  const float4 qb = reinterpret_cast<const float4*>(P.coef)[m.qb + zoff];
+  Coef4<float2> q;
+  q.c = make_float2(qa.x, qb.x);
+  q.s = make_float2(qa.y, qb.y);
+  q.x1 = make_float2(qa.z, qb.z);
+  q.x3 = make_float2(qa.w, qb.w);
+  C2 v[fields_in(FORM)];
+#pragma unroll
+  for (int f = 0; f < fields_in(FORM); ++f) {
+    const float4 w = *reinterpret_cast<const float4*>(md + f * fs);
+    v[f] = C2{make_float2(w.x, w.z), make_float2(w.y, w.w)};
+  }
+  update_core<float2, C2, FORM>(v, m.Kx, m.Ky, make_float2(kz, kz), m.px, m.py, pack2(pz1, pz1), m.pxy, q, P);
+#pragma unroll
+  for (int f = 0; f < fields_out(FORM); ++f)
+    *reinterpret_cast<float4*>(md + f * fs) = make_float4(v[f].x.x, v[f].y.x, v[f].x.y, v[f].y.y);
 }
 
 template <typename T, int FORM>

@@ -349,18 +349,24 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
     }
   }
   __syncthreads();
-  // k-space update: thread tid keeps column tt = tid % TX and walks z with a
-  // compile-time trip count (unrolled, so the table loads of all its modes
-  // are in flight together)
+  // k-space update, two modes per thread: thread tid keeps the column pair
+  // (2 tp, 2 tp + 1), tp = tid % (TX/2), and walks z with a compile-time trip
+  // count (unrolled, so the table loads of all its modes are in flight
+  // together).  A pair whose second column is past the tile computes it on
+  // dead data (clamped table indices) and only writes dead shared memory.
   {
-    constexpr int ZS = NT / TX, NIT = (NZ + ZS - 1) / ZS;
-    const int tt = tid % TX, z0 = tid / TX;
-    if (tt < nm) {
-      const ModeXY<float> xy = mode_xy<float>(nyq ? J.m0 : J.m0 + tt, nyq ? J.plane + tt : J.plane, sh, P);
+    constexpr int TP = TX / 2, ZS = NT / TP, NIT = (NZ + ZS - 1) / ZS;
+    static_assert(TX % 2 == 0 && NT % TP == 0, "column pairs");
+    const int tp = tid % TP, z0 = tid / TP;
+    const int ta = 2 * tp;
+    if (ta < nm) {
+      const int mxa = nyq ? J.m0 : J.m0 + ta, mya = nyq ? J.plane + ta : J.plane;
+      const int mxb = nyq ? J.m0 : mxa + 1, myb = nyq ? min(mya + 1, n1 - 1) : J.plane;
+      const ModeXY2 xy = mode_xy2(mxa, mya, mxb, myb, sh, P);
 #pragma unroll
       for (int j = 0; j < NIT; ++j) {
         const int z = z0 + j * ZS;
-        if (NZ % ZS == 0 || z < NZ) update_mode_z<float, FORM>(buf + z * NP + tt, TX, xy, z, sh, P);
+        if (NZ % ZS == 0 || z < NZ) update_mode_z2<FORM>(buf + z * NP + ta, TX, xy, z, sh, P);
       }
     }
   }
