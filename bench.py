@@ -43,6 +43,11 @@ WORKLOADS = {
     "local_128": dict(kind="local", global_n=(128, 128, 128), nsub=(2, 2, 2), ng=16, p=32, dt=0.9),
     "hybrid_1024": dict(kind="hybrid", global_n=(1024, 256, 256), nsub=(4, 1, 1), ng=64, p=64, dt=0.9),
     "local_1024": dict(kind="local", global_n=(1024, 256, 256), nsub=(16, 4, 4), ng=64, p=64, dt=0.9),
+    # the other synthetic configurations (seeded inputs from inputs.make_workload);
+    # their lines add the error against the analytic solution or the oracle
+    "plane_waves_32": dict(kind="config", precision=64),
+    "sources_128": dict(kind="config", precision=32),
+    "uneven_300": dict(kind="config", precision=32),
 }
 
 
@@ -57,6 +62,10 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", type=int, choices=(32, 64), default=None,
+                    help="override the precision of a configuration workload")
+    ap.add_argument("--no-errors", action="store_true",
+                    help="configuration workloads: skip the error check against the reference")
     return ap.parse_args(argv)
 
 
@@ -226,6 +235,120 @@ def step_algorithmic_bytes(layout, s=4, fin=6, fout=6):
 # GPU arm
 # ----------------------------------------------------------------------------
 
+def run_config(args):
+    """One of the other synthetic configurations on one GPU: the config's own
+    step count is pushed once from the seeded initial state and compared with
+    its reference (32^3 plane waves: the analytic solution; with sources: the
+    FP64 oracle's single step of the whole interval, equal to the stepped
+    result for time-constant J); then K steps are timed as one multi-step
+    push (replayed CUDA graph) after W warm-up steps."""
+    import numpy as np
+    import torch
+    from oracle import psatd_oracle as O
+    from paper_1812_07357_gb300 import _abi as A
+    from paper_1812_07357_gb300 import build as B
+    from paper_1812_07357_gb300 import inputs as I
+    from paper_1812_07357_gb300.solver import Plan
+
+    B.build()
+    A.load()
+    w = I.make_workload(args.workload)
+    prec = args.precision or WORKLOADS[args.workload]["precision"]
+    lay = w.layout
+    fields = w.fields
+    src = w.src
+    if prec == 32:
+        fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
+        src = {k: I.round_to(v, np.float32) for k, v in src.items()}
+    plan = Plan(lay, w.h, w.dt, c=w.c, eps0=w.eps0, precision=prec, sources=w.sources)
+    errors = None
+    if not args.no_errors:
+        df = plan.pack_fields(fields)
+        ds = plan.pack_fields(src) if w.sources != "vacuum" else None
+        plan.push(df, ds, w.steps)
+        plan.sync()
+        got = plan.unpack_fields(df)
+        if w.sources == "rho":
+            got["rho"] = plan.unpack(ds["rho"])
+        ref64 = None
+        if args.workload == "uneven_300":
+            # guards refilled from each box's own interior every step: no
+            # one-step shortcut; the reference is the FP64 GPU push of the same
+            # (FP32-rounded) inputs, itself held to the oracle <= 1e-12 by the tests
+            p64 = Plan(lay, w.h, w.dt, c=w.c, eps0=w.eps0, precision=64, sources=w.sources)
+            d64 = p64.pack_fields(fields)
+            s64 = p64.pack_fields(src)
+            p64.push(d64, s64, w.steps)
+            p64.sync()
+            ref64 = p64.unpack_fields(d64)
+            ref64["rho"] = p64.unpack(s64["rho"])
+            p64.close()
+        errors = _config_errors(args.workload, w, lay, fields, src, got, O, I, ref64)
+    df = plan.pack_fields(fields)
+    ds = plan.pack_fields(src) if w.sources != "vacuum" else None
+    plan.push(df, ds, args.warmup)
+    plan.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(plan.stream):
+        e0.record(plan.stream)
+        plan.push(df, ds, args.steps)
+        e1.record(plan.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    launches = plan.last_launch_count()
+    plan.close()
+    fin, fout = {"vacuum": (6, 6), "J": (9, 6), "rho": (10, 7)}[w.sources]
+    s = prec // 8
+    sab = step_algorithmic_bytes(lay, s=s, fin=fin, fout=fout)
+    step_ms = ms / args.steps
+    peak, peak_src = measured_peaks()
+    out = {"metric": METRIC, "value": lay.interior_cells * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f%d" % prec, "data": "synthetic",
+           "config": {"workload": args.workload, "decomposition": lay.kind, "boxes": len(lay.boxes),
+                      "interior_cells": lay.interior_cells, "padded_cells": lay.cells, "form": w.sources,
+                      "config_steps": w.steps, "dt": w.dt, "launch": "one multi-step push (CUDA graph)"},
+           "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": sab,
+                             "achieved": sab / (step_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": sab / (step_ms / 1e3) / 1e9 / peak, "peak_source": peak_src},
+           "gpu_launches": launches, "errors": errors}
+    print(json.dumps(out), flush=True)
+
+
+def _config_errors(name, w, lay, fields, src, got, O, I, ref64=None):
+    """Relative L2 and max-norm errors per field vector over interior cells."""
+    import numpy as np
+    if ref64 is not None:
+        ref, ref_name, sub = ref64, "FP64 GPU push of the same inputs", lay
+    elif name == "plane_waves_32":
+        n = lay.global_n
+        waves = I.plane_wave_set(seed=1, mmax=min(6, n[0] // 2 - 2))
+        f = I.plane_wave_fields(waves, n, w.h, w.c, w.dt * w.steps)
+        ref = {k: I.scatter_global(v, lay) for k, v in f.items()}
+        ref_name = "analytic solution at t = %g" % (w.dt * w.steps)
+        sub = lay
+    else:
+        idx = list(range(len(lay.boxes)))
+        if len(idx) > 8:
+            idx = sorted(set(np.linspace(0, len(idx) - 1, 8).astype(int).tolist()))
+        sub = I.Layout(lay.kind, lay.global_n, lay.periodic, [lay.boxes[i] for i in idx])
+        pick = lambda d: {k: [v[i] for i in idx] for k, v in d.items()}
+        fields, src, got = pick(fields), pick(src), pick(got)
+        ref = O.push(sub, fields, src, 1, w.h, w.dt * w.steps, c=w.c, eps0=w.eps0, form=w.sources)
+        ref_name = ("FP64 oracle, one step of %d dt (%d of %d boxes)" % (w.steps, len(idx), len(lay.boxes)))
+    out = {"reference": ref_name}
+    groups = {"E": ("Ex", "Ey", "Ez"), "B": ("Bx", "By", "Bz")}
+    if "rho" in got:
+        groups["rho"] = ("rho",)
+    for g, comps in groups.items():
+        # every (component, box) array as one "box" of the error metric
+        rep = I.Layout(sub.kind, sub.global_n, sub.periodic, list(sub.boxes) * len(comps))
+        rel, mx = O.rel_errors(rep, sum((list(got[k]) for k in comps), []), sum((list(ref[k]) for k in comps), []))
+        out[g] = {"rel_l2": rel, "max_norm": mx}
+    return out
+
+
 def run_gpu(args):
     import torch
     rank, local, world = dist_init("nccl" if int(os.environ.get("WORLD_SIZE", "1")) > 1 else "gloo")
@@ -313,6 +436,7 @@ def run_gpu(args):
                     for i in range(len(kms))},
         "gpu_launches": launches,
         "clocks": clk,
+        "memory": dict(zip(("field_bytes", "workspace_bytes"), A.psatd_plan_memory(plan.handle))),
     }
     if not args.no_e2e:
         out["e2e"] = run_e2e(plan, fields, args, lay, world)
@@ -489,6 +613,8 @@ def main(argv=None):
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif WORKLOADS[args.workload]["kind"] == "config":
+        run_config(args)
     else:
         run_gpu(args)
 
