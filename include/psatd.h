@@ -207,10 +207,17 @@ const char* psatd_last_error(const psatd_plan* plan);
 /* Number of kernel launches issued by the last psatd_push call (host count). */
 int64_t psatd_last_launch_count(const psatd_plan* plan);
 
-/* Number of boxes that run on the fast kernels (all three FFT lengths have a
- * two-pass register schedule and the planes fit in shared memory); the other
- * boxes run on the generic multi-pass kernels.  -1 for a NULL plan. */
+/* Number of boxes that run on the fast plane kernels (all three FFT lengths
+ * have a two-pass register schedule and the planes fit in shared memory);
+ * -1 for a NULL plan. */
 int32_t psatd_plan_fast_boxes(const psatd_plan* plan);
+
+/* Number of boxes that run on the pencil kernels (two-pass lengths up to 512
+ * along x and y, up to 256 along z in FP32 / 128 in FP64, planes too large
+ * for the plane kernels); the remaining boxes run on the generic multi-pass
+ * kernels.  -1 for a NULL plan.  No counterpart in the paper (a property of
+ * this implementation's kernel selection). */
+int32_t psatd_plan_pencil_boxes(const psatd_plan* plan);
 
 /* Kernel kinds reported by psatd_plan_kernel_times. */
 #define PSATD_KERNEL_KINDS 6 /* 0 fwd_x, 1 col forward, 2 z_update, 3 col inverse, 4 inv_x, 5 exchange */

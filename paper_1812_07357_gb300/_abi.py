@@ -87,6 +87,7 @@ _SIGS = {
     "psatd_plan_set_timing": (c_int32, [c_void_p, c_int32]),
     "psatd_plan_kernel_times": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32]),
     "psatd_plan_fast_boxes": (c_int32, [c_void_p]),
+    "psatd_plan_pencil_boxes": (c_int32, [c_void_p]),
     "psatd_push_box_static": (c_int32, [POINTER(c_int32), c_int32, POINTER(c_double), c_double,
                                         c_double, POINTER(psatd_fields), c_int32, c_void_p]),
 }
@@ -241,3 +242,7 @@ def psatd_push_box_static(n, order_p: int, dx, dt: float, c: float, fields: psat
 
 def psatd_plan_fast_boxes(plan: int) -> int:
     return int(load().psatd_plan_fast_boxes(c_void_p(plan)))
+
+
+def psatd_plan_pencil_boxes(plan: int) -> int:
+    return int(load().psatd_plan_pencil_boxes(c_void_p(plan)))

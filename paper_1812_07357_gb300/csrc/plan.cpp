@@ -302,6 +302,9 @@ struct psatd_plan {
   std::vector<int2> plane_fwd, plane_inv;                     // push, fast boxes
   std::vector<ColJob> zfast;
   int fast_boxes = 0;
+  std::vector<RowJob> pen_rows, pen_rows_int;                 // push, pencil boxes
+  std::vector<ColJob> pen_ycols, pen_ycols_int, zpen;
+  int pen_boxes = 0;
   std::vector<CopyBlk> blocks;
   std::vector<XTile> tiles;                                   // every block (psatd_guard_exchange)
   std::vector<XTile> step_tiles;                              // blocks not fused into the inverse
@@ -312,6 +315,7 @@ struct psatd_plan {
   int64_t spec_total = 0;   // complex elements per spectrum slot
   int smem_fx = 0, smem_y = 0, smem_z = 0, smem_zonly = 0, smem_ix = 0;
   int smem_pf = 0, smem_pi = 0, smem_zf = 0;
+  int smem_penx = 0, smem_penxi = 0, smem_penc = 0, smem_penz = 0;
   int buf_pf = 0, buf_pi = 0, rows_pi = 0;     // complex elements per plane buffer
   int grid_pf = 0, grid_pi = 0;                // persistent grid sizes
   int reg_code = -1;                           // register plane kernels for every fast box
@@ -326,6 +330,8 @@ struct psatd_plan {
   RowJob *d_g_rows = nullptr, *d_g_rows_int = nullptr;
   ColJob *d_g_ycols = nullptr, *d_g_ycols_int = nullptr, *d_g_zcols = nullptr, *d_zfast = nullptr;
   int2 *d_plane_fwd = nullptr, *d_plane_inv = nullptr;
+  RowJob *d_pen_rows = nullptr, *d_pen_rows_int = nullptr;
+  ColJob *d_pen_ycols = nullptr, *d_pen_ycols_int = nullptr, *d_zpen = nullptr;
   CopyBlk* d_blocks = nullptr;
   XTile* d_tiles = nullptr;
   XTile* d_step_tiles = nullptr;
@@ -478,6 +484,9 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     s.fx = fast_code(s.L);
     s.fy = fast_code(b.n[1]);
     s.fz = fast_code(b.n[2]);
+    s.px = pencil_code(s.L);
+    s.py = pencil_code(b.n[1]);
+    s.pz = pencil_code(b.n[2]);
     // x-pass row pitch = R2 (mod 16) and work pitch = 1 (mod 16) keep the
     // shared-memory accesses of the plane kernels free of most bank conflicts
     int r2x = 1;
@@ -535,6 +544,9 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       const int y0 = b.ng_lo[1], y1 = n1 - b.ng_hi[1];
       for (int y = y0; y < y1; y += nr) P->rows_int.push_back({bi, z * n1 + y, std::min(nr, y1 - y), 0});
     }
+    const bool pencil = !fast && !(d.flags & PSATD_GENERIC_KERNELS) && sh.px >= 0 && sh.py >= 0 && sh.pz >= 0 &&
+                        n2 <= pen_z_max(P->prec) && sm_zf <= optin && pen_col_smem(P->prec, n1) <= optin;
+    const bool generic = !fast && !pencil;   // the generic Stockham kernels
     if (fast) {
       ++P->fast_boxes;
       for (int z = 0; z < n2; ++z) {
@@ -549,6 +561,29 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       P->buf_pi = std::max(P->buf_pi, n1 * hx);
       P->rows_pi = std::max(P->rows_pi, ni * sh.hp);
       P->smem_zf = std::max(P->smem_zf, sm_zf);
+    } else if (pencil) {
+      // pencil kernels: x rows, y tiles, z tiles (+ update), y tiles, x rows
+      ++P->pen_boxes;
+      const int pr = pen_rows(P->prec, L, rows, 64 * 1024);
+      for (int r = 0; r < rows; r += pr) P->pen_rows.push_back({bi, r, std::min(pr, rows - r), 0});
+      const int y0 = b.ng_lo[1], y1 = n1 - b.ng_hi[1];
+      const int pri = pen_rows(P->prec, L, y1 - y0, 64 * 1024);
+      for (int z = b.ng_lo[2]; z < n2 - b.ng_hi[2]; ++z)
+        for (int y = y0; y < y1; y += pri) P->pen_rows_int.push_back({bi, z * n1 + y, std::min(pri, y1 - y), 0});
+      const int ct = pen_col_tile(P->prec);
+      for (int z = 0; z < n2; ++z)
+        for (int m = 0; m < hx; m += ct) {
+          const ColJob j{bi, z, m, std::min(ct, hx - m)};
+          P->pen_ycols.push_back(j);
+          if (z >= b.ng_lo[2] && z < n2 - b.ng_hi[2]) P->pen_ycols_int.push_back(j);
+        }
+      for (int y = 0; y < n1; ++y)
+        for (int m = 0; m < L; m += tile) P->zpen.push_back({bi, y, m, std::min(tile, L - m)});
+      for (int y = 0; y < n1; y += tile) P->zpen.push_back({bi, y, L, -std::min(tile, n1 - y)});
+      P->smem_penx = std::max(P->smem_penx, pen_x_smem(P->prec, L, pr));
+      P->smem_penxi = std::max(P->smem_penxi, pen_x_smem(P->prec, L, pri));
+      P->smem_penc = std::max(P->smem_penc, pen_col_smem(P->prec, n1));
+      P->smem_penz = std::max(P->smem_penz, sm_zf);
     } else {
       for (int r = 0; r < rows; r += nr) P->g_rows.push_back({bi, r, std::min(nr, rows - r), 0});
       for (int z = b.ng_lo[2]; z < n2 - b.ng_hi[2]; ++z) {
@@ -567,7 +602,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
         ColJob j{bi, z, m, std::min(ny, hx - m)};
         P->ycols_all.push_back(j);
         if (inner) P->ycols_int.push_back(j);
-        if (!fast) {
+        if (generic) {
           P->g_ycols.push_back(j);
           if (inner) P->g_ycols_int.push_back(j);
         }
@@ -580,7 +615,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     for (int y = 0; y < n1; ++y)
       for (int m = 0; m < hx; m += nz) {
         P->zcols.push_back({bi, y, m, std::min(nz, hx - m)});
-        if (!fast) P->g_zcols.push_back({bi, y, m, std::min(nz, hx - m)});
+        if (generic) P->g_zcols.push_back({bi, y, m, std::min(nz, hx - m)});
       }
     P->smem_z = std::max(P->smem_z, n2 * FIN * nz * csz);
     P->smem_zonly = std::max(P->smem_zonly, n2 * nz * csz);
@@ -702,6 +737,11 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   CK(P, upload(P, P->zfast, &P->d_zfast));
   CK(P, upload(P, P->plane_fwd, &P->d_plane_fwd));
   CK(P, upload(P, P->plane_inv, &P->d_plane_inv));
+  CK(P, upload(P, P->pen_rows, &P->d_pen_rows));
+  CK(P, upload(P, P->pen_rows_int, &P->d_pen_rows_int));
+  CK(P, upload(P, P->pen_ycols, &P->d_pen_ycols));
+  CK(P, upload(P, P->pen_ycols_int, &P->d_pen_ycols_int));
+  CK(P, upload(P, P->zpen, &P->d_zpen));
   CK(P, upload(P, P->blocks, &P->d_blocks));
   CK(P, upload(P, P->tiles, &P->d_tiles));
   CK(P, upload(P, P->step_tiles, &P->d_step_tiles));
@@ -768,12 +808,13 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   free_tmp();
   CK(P, e);
   const int smem = std::max({P->smem_fx, P->smem_y, P->smem_z, P->smem_zonly, P->smem_ix, P->smem_pf,
-                             P->smem_pi, P->smem_zf});
+                             P->smem_pi, P->smem_zf, P->smem_penx, P->smem_penxi, P->smem_penc, P->smem_penz});
   if (smem > optin) return fail(P, PSATD_ERR_UNSUPPORTED_SIZE, fmt("needs %d B shared memory", smem));
   // The attribute is a per-kernel cap shared by every plan: raise it to the
   // device maximum so that no plan lowers it below another plan's need.
   CK(P, configure_kernels(P->prec, optin));
   CK(P, configure_fast_kernels(P->prec, optin));
+  CK(P, configure_pen_kernels(P->prec, optin));
   if (P->prec == 32) CK(P, configure_reg_kernels(optin));
   if (P->fast_boxes) {
     int sms = 0, occ_f = 0, occ_i = 0;
@@ -994,7 +1035,24 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
        }));
     launches += 2;
   }
+  if (!P->pen_rows.empty()) {
+    CK(P, timed(P, 0, st, [&] {
+         return launch_pen_xf(P->prec, D, fp, FIN, P->d_ws, S, P->d_pen_rows, (int64_t)P->pen_rows.size(),
+                              P->smem_penx, st);
+       }));
+    CK(P, timed(P, 1, st, [&] {
+         return launch_pen_col(P->prec, -1, D, P->d_ws, S, FIN, P->d_pen_ycols, (int64_t)P->pen_ycols.size(),
+                               P->smem_penc, st);
+       }));
+    launches += 2;
+  }
   // S1 (z) + S2 + S3 (z)
+  if (!P->zpen.empty()) {
+    CK(P, timed(P, 2, st, [&] {
+         return launch_z_pen(P->prec, P->form, D, P->d_ws, S, P->d_zpen, (int64_t)P->zpen.size(), P->smem_penz, st);
+       }));
+    ++launches;
+  }
   if (!P->zfast.empty() && P->reg_z) {
     CK(P, timed(P, 2, st, [&] {
          return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, st);
@@ -1034,6 +1092,17 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
        }));
     CK(P, timed(P, 4, st, [&] {
          return launch_inv_x(P->prec, D, fp, FOUT, P->d_ws, S, P->d_g_rows_int, (int64_t)P->g_rows_int.size(), P->smem_ix, 1, st);
+       }));
+    launches += 2;
+  }
+  if (!P->pen_rows_int.empty()) {
+    CK(P, timed(P, 3, st, [&] {
+         return launch_pen_col(P->prec, 1, D, P->d_ws, S, FOUT, P->d_pen_ycols_int,
+                               (int64_t)P->pen_ycols_int.size(), P->smem_penc, st);
+       }));
+    CK(P, timed(P, 4, st, [&] {
+         return launch_pen_xi(P->prec, D, fp, FOUT, P->d_ws, S, P->d_pen_rows_int, (int64_t)P->pen_rows_int.size(),
+                              P->smem_penxi, st);
        }));
     launches += 2;
   }
@@ -1186,6 +1255,8 @@ const char* psatd_last_error(const psatd_plan* p) {
 int64_t psatd_last_launch_count(const psatd_plan* p) { return p ? p->last_launches : 0; }
 
 int32_t psatd_plan_fast_boxes(const psatd_plan* p) { return p ? p->fast_boxes : -1; }
+
+int32_t psatd_plan_pencil_boxes(const psatd_plan* p) { return p ? p->pen_boxes : -1; }
 
 psatd_status psatd_plan_set_timing(psatd_plan* P, int32_t enable) {
   if (!P) return PSATD_ERR_INVALID_ARG;

@@ -45,6 +45,7 @@ struct ShapeDev {
   int64_t phx, phy, phz;          // exp(i k h / 2), hx / n1 / n2            (complex pool)
   int64_t coef;                   // hx*(n1/2+1)*(n2/2+1) coefficient quads (coef pool)
   int32_t fx, fy, fz;             // fast-length codes of L, n1, n2 (-1: not a fast length)
+  int32_t px, py, pz;             // pencil-length codes of L, n1, n2 (-1: none)
   int32_t lp, hp;                 // smem row pitches (complex) of the fast plane kernels
 };
 
@@ -53,6 +54,22 @@ struct ShapeDev {
   X(0, 24, 8, 3) X(1, 30, 6, 5) X(2, 32, 8, 4) X(3, 40, 8, 5) X(4, 48, 8, 6)              \
   X(5, 60, 12, 5) X(6, 64, 8, 8) X(7, 80, 10, 8) X(8, 96, 12, 8) X(9, 120, 12, 10)       \
   X(10, 128, 16, 8)
+
+// Lengths of the pencil kernels (boxes too large for the plane kernels):
+// the same two-pass factorizations, extended to 512.  Codes 0-10 coincide
+// with PSATD_FAST_LENGTHS.
+#define PSATD_PENCIL_LENGTHS(X)                                                         \
+  PSATD_FAST_LENGTHS(X)                                                                \
+  X(11, 144, 12, 12) X(12, 160, 16, 10) X(13, 192, 16, 12) X(14, 240, 24, 10)            \
+  X(15, 256, 16, 16) X(16, 320, 32, 10) X(17, 384, 24, 16) X(18, 512, 32, 16)
+
+inline int pencil_code(int n) {
+#define PSATD_CODE(code, N, R1, R2) \
+  if (n == N) return code;
+  PSATD_PENCIL_LENGTHS(PSATD_CODE)
+#undef PSATD_CODE
+  return -1;
+}
 
 inline int fast_code(int n) {
 #define PSATD_CODE(code, N, R1, R2) \
@@ -200,6 +217,23 @@ int z_reg_smem(int form, int n2);
 int z_reg_tile_width(int form);
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
                          int64_t njobs, int n2, cudaStream_t st);
+
+// ---- pencil kernels (pencil_kernels.cu): boxes of two-pass lengths too large
+// for the plane kernels; the z pass takes fast_tile(prec) mx columns per tile
+int pen_rows(int prec, int L, int rows, int smem_cap);   // x rows per CTA
+int pen_x_smem(int prec, int L, int nr);
+int pen_z_max(int prec);                                  // longest n2 of a pencil box
+int pen_col_tile(int prec);                               // mx columns of a y tile
+int pen_col_smem(int prec, int n1);
+cudaError_t launch_pen_xf(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,
+                          const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+cudaError_t launch_pen_col(int prec, int dir, const DevPlan& P, void* spec, int64_t sstride, int nf,
+                           const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+cudaError_t launch_z_pen(int prec, int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
+                         int64_t njobs, int smem, cudaStream_t st);
+cudaError_t launch_pen_xi(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,
+                          const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+cudaError_t configure_pen_kernels(int prec, int smem_bytes);
 
 // ---- host helpers (plan.cpp) ------------------------------------------------
 // Radix schedule of a complex FFT length (false if it is not 5-smooth).

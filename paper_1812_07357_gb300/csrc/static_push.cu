@@ -100,6 +100,7 @@ extern "C" psatd_status psatd_push_box_static(const int32_t n[3], int32_t order_
   const int n0 = n[0], n1 = n[1], n2 = n[2];
   const int L = n0 / 2, hx = L + 1, FIN = fields_in(kVacuum);
   ShapeDev s{};
+  s.fx = s.fy = s.fz = s.px = s.py = s.pz = -1;   // generic kernels only
   for (int a = 0; a < 3; ++a) s.n[a] = n[a];
   s.L = L;
   s.hx = hx;

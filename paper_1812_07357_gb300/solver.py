@@ -73,6 +73,7 @@ class Plan:
         self.field_elems = fb // (4 if precision == 32 else 8)
         self.workspace_bytes = wb
         self.fast_boxes = A.psatd_plan_fast_boxes(self.handle)
+        self.pencil_boxes = A.psatd_plan_pencil_boxes(self.handle)
         last = self.spec_offsets[-1]
         self.spec_elems = last[0] + last[1] + 64
 

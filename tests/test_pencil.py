@@ -1,0 +1,118 @@
+"""Pencil kernels (boxes with two-pass FFT lengths whose planes are too large
+for the plane kernels: n0/2 above 64 in FP32 / 48 in FP64, or n1 above 128)
+against the FP64 oracle, against the generic kernels, and mixed with plane and
+generic boxes in one plan (guard exchange across the three kernel families).
+Tolerances as in test_gpu_parity: FP64 <= 1e-12, FP32 <= 2e-5 relative L2."""
+import numpy as np
+import pytest
+
+from oracle import psatd_oracle as O
+from paper_1812_07357_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {64: 1e-12, 32: 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_07357_gb300 import build
+    build.build()
+
+
+def _run(lay, fields, src, nsteps, h, dt, prec, form, generic=False):
+    from paper_1812_07357_gb300.solver import Plan
+    plan = Plan(lay, h, dt, precision=prec, sources=form, generic=generic)
+    paths = (plan.fast_boxes, plan.pencil_boxes)
+    df = plan.pack_fields(fields)
+    ds = plan.pack_fields(src) if form != "vacuum" else None
+    plan.push(df, ds, nsteps)
+    plan.sync()
+    out = plan.unpack_fields(df)
+    if form == "rho":
+        out["rho"] = plan.unpack(ds["rho"])
+    plan.close()
+    return out, paths
+
+
+def _check(lay, fields, src, nsteps, h, dt, prec, form, paths):
+    if prec == 32:
+        fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
+        src = {k: I.round_to(v, np.float32) for k, v in src.items()}
+    got, p = _run(lay, fields, src, nsteps, h, dt, prec, form)
+    assert p == paths, p
+    ref = O.push(lay, fields, src, nsteps, h, dt, form=form)
+    comps = O.COMPS + (("rho",) if form == "rho" else ())
+    err = O.rel_l2_fields(lay, got, ref, comps)
+    assert err <= TOL[prec], err
+    for k in comps:   # guards too (exchange ran)
+        for g, r in zip(got[k], ref[k]):
+            assert np.abs(g - r).max() <= 50 * TOL[prec] * max(1.0, float(np.abs(r).max())) * nsteps ** 0.5
+    return got
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_pencil_independent_long_x_rho(prec):
+    """Self-periodic boxes with n0/2 in {80, 96, 128} (pencil in both
+    precisions) and short y, z; rho form."""
+    sizes = [(160, 24, 32), (192, 30, 40), (256, 32, 24)]
+    boxes = [I.Box(n, (4, 4, 4), (4, 4, 4), (0, 0, 0), p) for n, p in zip(sizes, (8, 16, 0))]
+    lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
+    rng = np.random.default_rng(21)
+    js = {k: [] for k in ("Jx", "Jy", "Jz")}
+    for b in lay.boxes:
+        j = I.band_limited_current(b.interior, rng)
+        for k in js:
+            js[k].append(j[k])
+    src = {k: I.scatter_self(v, lay) for k, v in js.items()}
+    src["rho"] = I.zeros(lay)
+    fields = {k: I.zeros(lay) for k in O.COMPS}
+    _check(lay, fields, src, 3, (1.0, 1.0, 1.0), 0.9, prec, "rho", (0, 3))
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_pencil_local_laser(prec):
+    """8 local boxes of 192 x 96 x 96 (128 x 32 x 32 interior + 32 guards),
+    p = 16, laser, 3 steps: pencil x, y and z passes with the batched exchange."""
+    lay = I.local_layout((256, 64, 64), (2, 2, 2), 32, 16)
+    assert all(b.n == (192, 96, 96) for b in lay.boxes)
+    f = I.laser_fields((256, 64, 64), wavelength=8.0, waist=10.0, duration=8.0)
+    fields = {k: I.scatter_global(v, lay) for k, v in f.items()}
+    _check(lay, fields, {}, 3, (1.0, 1.0, 1.0), 0.9, prec, "vacuum", (0, 8))
+
+
+def test_pencil_long_y_jform():
+    """n1 = 160 > 128 (pencil along y with a 48-point x), J form, FP32."""
+    lay = I.global_layout((48, 160, 24), 8)
+    rng = np.random.default_rng(23)
+    shp = lay.boxes[0].shape
+    src = {k: [rng.standard_normal(shp)] for k in ("Jx", "Jy", "Jz")}
+    fields = {k: [rng.standard_normal(shp)] for k in O.COMPS}
+    _check(lay, fields, src, 3, (1.0, 0.9, 1.1), 0.8, 32, "J", (0, 1))
+
+
+def test_pencil_equals_generic_fp32():
+    lay = I.local_layout((256, 64, 64), (2, 2, 2), 32, 16)
+    f = I.laser_fields((256, 64, 64), wavelength=8.0, waist=10.0, duration=8.0)
+    fields = {k: I.round_to(I.scatter_global(v, lay), np.float32) for k, v in f.items()}
+    a, pa = _run(lay, fields, {}, 3, (1.0,) * 3, 0.9, 32, "vacuum")
+    b, pb = _run(lay, fields, {}, 3, (1.0,) * 3, 0.9, 32, "vacuum", generic=True)
+    assert pa == (0, 8) and pb == (0, 0)
+    assert O.rel_l2_fields(lay, a, b, O.COMPS) < 2e-6
+
+
+def test_mixed_plane_pencil_generic_boxes():
+    """One plan with a plane box (48^3), a pencil box (160 x 48 x 48) and a
+    generic box (50 x 50 x 50: 25 is not a two-pass length), self-periodic,
+    FP64, vacuum."""
+    boxes = [I.Box((48, 48, 48), (4,) * 3, (4,) * 3, (0, 0, 0), 8),
+             I.Box((160, 48, 48), (8,) * 3, (8,) * 3, (0, 0, 0), 16),
+             I.Box((50, 50, 50), (5,) * 3, (5,) * 3, (0, 0, 0), 0)]
+    lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
+    rng = np.random.default_rng(25)
+    fields = {k: [rng.standard_normal(b.shape) for b in lay.boxes] for k in O.COMPS}
+    fields = {k: O.exchange(lay, v) for k, v in fields.items()}
+    _check(lay, fields, {}, 3, (1.0, 1.0, 1.0), 0.9, 64, "vacuum", (1, 1))
