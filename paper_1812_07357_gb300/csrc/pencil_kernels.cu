@@ -12,7 +12,10 @@
 //   k_pen_xi   (box, interior rows, field): C2R along x with 1/N, interior
 //              cells to HBM (S3, x).
 //
-// The guard exchange (S4) of these boxes is the batched copy kernel.
+// Every kernel is instantiated per FFT length (its registers and occupancy
+// follow that length); the plan groups the jobs of each length and issues
+// one launch per group.  The guard exchange (S4) of these boxes is the
+// batched copy kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -103,7 +106,7 @@ __device__ __forceinline__ void pen_xf_body(cx<T>* buf, int nr, const cx<T>* __r
   }
 }
 
-template <typename T>
+template <typename T, int R1, int R2>
 __global__ void __launch_bounds__(kPenThreads) k_pen_xf(DevPlan P, FieldPtrs F, cx<T>* spec, int64_t sstride,
                                                         const RowJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -118,15 +121,7 @@ __global__ void __launch_bounds__(kPenThreads) k_pen_xf(DevPlan P, FieldPtrs F, 
   load_rows_async(buf, g, J.nr, n0 * (int)sizeof(T), LP * (int)sizeof(cx<T>));
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
-  const cx<T>* twx = ctab<T>(P) + sh.ax.tw;
-  const cx<T>* post = ctab<T>(P) + sh.post;
-  switch (sh.px) {
-#define PSATD_ARM(code, N, R1, R2) \
-  case code: pen_xf_body<T, R1, R2>(buf, J.nr, twx, post); break;
-    PSATD_PENCIL_LENGTHS(PSATD_ARM)
-#undef PSATD_ARM
-    default: break;
-  }
+  pen_xf_body<T, R1, R2>(buf, J.nr, ctab<T>(P) + sh.ax.tw, ctab<T>(P) + sh.post);
   __syncthreads();
   // the nr half-spectrum rows are contiguous in the spectrum slot
   cx<T>* out = spec + f * sstride + bx.soff + (int64_t)J.r0 * hx;
@@ -138,7 +133,7 @@ __global__ void __launch_bounds__(kPenThreads) k_pen_xf(DevPlan P, FieldPtrs F, 
 
 // ---------------------------------------------------------------------------
 // y pass of a tile: columns m0 .. m0+nm-1 of z plane `plane`, all n1 rows.
-template <typename T, int DIR>
+template <typename T, int DIR, int R1, int R2>
 __global__ void __launch_bounds__(kPenThreads) k_pen_col(DevPlan P, cx<T>* spec, int64_t sstride,
                                                          const ColJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -155,22 +150,13 @@ __global__ void __launch_bounds__(kPenThreads) k_pen_col(DevPlan P, cx<T>* spec,
     buf[e] = g[(int64_t)y * hx + c];
   }
   __syncthreads();
-  const cx<T>* tw = ctab<T>(P) + sh.ay.tw;
-  switch (sh.py) {
-#define PSATD_ARM(code, N, R1, R2)                                                               \
-  case code:                                                                                     \
-    pass1<T, R1, R2, DIR, true>(buf, nm, 1, nm, tw, mnm);                                        \
-    __syncthreads();                                                                             \
-    pass2<T, R1, R2, DIR, true>(buf, nm, 1, nm, mnm, [&](int c, int k, cx<T> v) { g[(int64_t)k * hx + c] = v; }); \
-    break;
-    PSATD_PENCIL_LENGTHS(PSATD_ARM)
-#undef PSATD_ARM
-    default: break;
-  }
+  pass1<T, R1, R2, DIR, true>(buf, nm, 1, nm, ctab<T>(P) + sh.ay.tw, mnm);
+  __syncthreads();
+  pass2<T, R1, R2, DIR, true>(buf, nm, 1, nm, mnm, [&](int c, int k, cx<T> v) { g[(int64_t)k * hx + c] = v; });
 }
 
 // ---------------------------------------------------------------------------
-template <typename T, int FORM, int TX>
+template <typename T, int FORM, int TX, int R1, int R2>
 __global__ void __launch_bounds__(kThreads, 1) k_z_pen(DevPlan P, cx<T>* spec, int64_t sstride,
                                                        const ColJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -183,17 +169,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_z_pen(DevPlan P, cx<T>* spec, i
   const bool nyq = J.nm < 0;
   const int nm = nyq ? -J.nm : J.nm, ts = nyq ? hx : 1;
   cx<T>* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
-  switch (sh.pz) {
-#define PSATD_ARM(code, NV, R1, R2)                                                                  \
-  case code:                                                                                         \
-    if constexpr (NV <= pen_max_z<T>())                                                              \
-      z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, nm, J.m0, J.plane, ts, nyq, bx.ng_lo[2],     \
-                                  N - bx.ng_hi[2], sh, P);                                           \
-    break;
-    PSATD_PENCIL_LENGTHS(PSATD_ARM)
-#undef PSATD_ARM
-    default: break;
-  }
+  z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, nm, J.m0, J.plane, ts, nyq, bx.ng_lo[2], N - bx.ng_hi[2], sh, P);
 }
 
 // ---------------------------------------------------------------------------
@@ -225,7 +201,7 @@ __device__ __forceinline__ void pen_xi_body(cx<T>* buf, int nr, T* out, int n0, 
 }
 
 // rows r0 .. r0+nr-1 of one box (consecutive y of one z plane, all interior)
-template <typename T>
+template <typename T, int R1, int R2>
 __global__ void __launch_bounds__(kPenThreads) k_pen_xi(DevPlan P, FieldPtrs F, const cx<T>* spec,
                                                         int64_t sstride, const RowJob* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -243,17 +219,8 @@ __global__ void __launch_bounds__(kPenThreads) k_pen_xi(DevPlan P, FieldPtrs F, 
   __syncthreads();
   const T scale = T(1.0 / ((double)n0 * bx.n[1] * bx.n[2]));
   T* out = reinterpret_cast<T*>(F.p[f]) + bx.foff + (int64_t)J.r0 * n0;
-  const cx<T>* twx = ctab<T>(P) + sh.ax.tw;
-  const cx<T>* post = ctab<T>(P) + sh.post;
-  switch (sh.px) {
-#define PSATD_ARM(code, N, R1, R2)                                                                   \
-  case code:                                                                                         \
-    pen_xi_body<T, R1, R2>(buf, J.nr, out, n0, bx.ng_lo[0], n0 - bx.ng_lo[0] - bx.ng_hi[0], scale, twx, post); \
-    break;
-    PSATD_PENCIL_LENGTHS(PSATD_ARM)
-#undef PSATD_ARM
-    default: break;
-  }
+  pen_xi_body<T, R1, R2>(buf, J.nr, out, n0, bx.ng_lo[0], n0 - bx.ng_lo[0] - bx.ng_hi[0], scale,
+                         ctab<T>(P) + sh.ax.tw, ctab<T>(P) + sh.post);
 }
 
 }  // namespace
@@ -275,89 +242,131 @@ int pen_x_smem(int prec, int L, int nr) { return nr * pen_x_pitch(L) * (prec == 
 int pen_col_tile(int prec) { return prec == 32 ? pen_tile<float>() : pen_tile<double>(); }
 int pen_col_smem(int prec, int n1) { return n1 * pen_col_tile(prec) * (prec == 32 ? 8 : 16); }
 
-cudaError_t launch_pen_xf(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,
-                          const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
+// One launch per FFT-length group: `code` is the pencil-length code of the
+// axis the kernel transforms (x for the row kernels, y for the column
+// kernels, z for the z kernel); every job of the launch has that length.
+cudaError_t launch_pen_xf(int prec, int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
   if (njobs <= 0 || nf <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs, nf);
-  if (prec == 32)
-    k_pen_xf<float><<<grid, kPenThreads, smem, st>>>(P, f, (float2*)spec, sstride, jobs);
-  else
-    k_pen_xf<double><<<grid, kPenThreads, smem, st>>>(P, f, (double2*)spec, sstride, jobs);
+  switch (code) {
+#define PSATD_ARM(c, N, R1, R2)                                                                       \
+  case c:                                                                                             \
+    if (prec == 32)                                                                                   \
+      k_pen_xf<float, R1, R2><<<grid, kPenThreads, smem, st>>>(P, f, (float2*)spec, sstride, jobs);    \
+    else                                                                                              \
+      k_pen_xf<double, R1, R2><<<grid, kPenThreads, smem, st>>>(P, f, (double2*)spec, sstride, jobs);  \
+    break;
+    PSATD_PENCIL_LENGTHS(PSATD_ARM)
+#undef PSATD_ARM
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_pen_col(int prec, int dir, const DevPlan& P, void* spec, int64_t sstride, int nf,
+cudaError_t launch_pen_col(int prec, int dir, int code, const DevPlan& P, void* spec, int64_t sstride, int nf,
                            const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
   if (njobs <= 0 || nf <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs, nf);
-  if (prec == 32) {
-    if (dir < 0)
-      k_pen_col<float, -1><<<grid, kPenThreads, smem, st>>>(P, (float2*)spec, sstride, jobs);
-    else
-      k_pen_col<float, 1><<<grid, kPenThreads, smem, st>>>(P, (float2*)spec, sstride, jobs);
-  } else {
-    if (dir < 0)
-      k_pen_col<double, -1><<<grid, kPenThreads, smem, st>>>(P, (double2*)spec, sstride, jobs);
-    else
-      k_pen_col<double, 1><<<grid, kPenThreads, smem, st>>>(P, (double2*)spec, sstride, jobs);
+  switch (code) {
+#define PSATD_ARM(c, N, R1, R2)                                                                        \
+  case c:                                                                                              \
+    if (prec == 32 && dir < 0)                                                                         \
+      k_pen_col<float, -1, R1, R2><<<grid, kPenThreads, smem, st>>>(P, (float2*)spec, sstride, jobs);   \
+    else if (prec == 32)                                                                               \
+      k_pen_col<float, 1, R1, R2><<<grid, kPenThreads, smem, st>>>(P, (float2*)spec, sstride, jobs);    \
+    else if (dir < 0)                                                                                  \
+      k_pen_col<double, -1, R1, R2><<<grid, kPenThreads, smem, st>>>(P, (double2*)spec, sstride, jobs); \
+    else                                                                                               \
+      k_pen_col<double, 1, R1, R2><<<grid, kPenThreads, smem, st>>>(P, (double2*)spec, sstride, jobs);  \
+    break;
+    PSATD_PENCIL_LENGTHS(PSATD_ARM)
+#undef PSATD_ARM
+    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_z_pen(int prec, int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                         int64_t njobs, int smem, cudaStream_t st) {
+template <typename T, typename C2, int R1, int R2>
+cudaError_t launch_z_pen_t(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
+                           int64_t njobs, int smem, cudaStream_t st) {
+  constexpr int TX = sizeof(T) == 4 ? 8 : 4;
+  if constexpr (R1 * R2 <= pen_max_z<T>()) {
+    dim3 grid((unsigned)njobs);
+    if (form == kVacuum)
+      k_z_pen<T, kVacuum, TX, R1, R2><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs);
+    else if (form == kJForm)
+      k_z_pen<T, kJForm, TX, R1, R2><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs);
+    else
+      k_z_pen<T, kRhoForm, TX, R1, R2><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs);
+    return cudaGetLastError();
+  } else {
+    return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_z_pen(int prec, int form, int code, const DevPlan& P, void* spec, int64_t sstride,
+                         const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
-  dim3 grid((unsigned)njobs);
-#define PSATD_ZP(T, C2, FORMV, TXV) k_z_pen<T, FORMV, TXV><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs)
-  if (prec == 32) {
-    if (form == kVacuum) PSATD_ZP(float, float2, kVacuum, 8);
-    else if (form == kJForm) PSATD_ZP(float, float2, kJForm, 8);
-    else PSATD_ZP(float, float2, kRhoForm, 8);
-  } else {
-    if (form == kVacuum) PSATD_ZP(double, double2, kVacuum, 4);
-    else if (form == kJForm) PSATD_ZP(double, double2, kJForm, 4);
-    else PSATD_ZP(double, double2, kRhoForm, 4);
+  switch (code) {
+#define PSATD_ARM(c, N, R1, R2)                                                                         \
+  case c:                                                                                               \
+    return prec == 32 ? launch_z_pen_t<float, float2, R1, R2>(form, P, spec, sstride, jobs, njobs, smem, st) \
+                      : launch_z_pen_t<double, double2, R1, R2>(form, P, spec, sstride, jobs, njobs, smem, st);
+    PSATD_PENCIL_LENGTHS(PSATD_ARM)
+#undef PSATD_ARM
+    default: return cudaErrorInvalidValue;
   }
-#undef PSATD_ZP
-  return cudaGetLastError();
 }
 
-cudaError_t launch_pen_xi(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,
-                          const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
+cudaError_t launch_pen_xi(int prec, int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
   if (njobs <= 0 || nf <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs, nf);
-  if (prec == 32)
-    k_pen_xi<float><<<grid, kPenThreads, smem, st>>>(P, f, (const float2*)spec, sstride, jobs);
-  else
-    k_pen_xi<double><<<grid, kPenThreads, smem, st>>>(P, f, (const double2*)spec, sstride, jobs);
+  switch (code) {
+#define PSATD_ARM(c, N, R1, R2)                                                                              \
+  case c:                                                                                                    \
+    if (prec == 32)                                                                                          \
+      k_pen_xi<float, R1, R2><<<grid, kPenThreads, smem, st>>>(P, f, (const float2*)spec, sstride, jobs);     \
+    else                                                                                                     \
+      k_pen_xi<double, R1, R2><<<grid, kPenThreads, smem, st>>>(P, f, (const double2*)spec, sstride, jobs);   \
+    break;
+    PSATD_PENCIL_LENGTHS(PSATD_ARM)
+#undef PSATD_ARM
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
+}
+
+template <typename T, int R1, int R2>
+cudaError_t configure_pen_t(int smem) {
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* k) {
+    const cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (r != cudaSuccess) e = r;
+  };
+  constexpr int TX = sizeof(T) == 4 ? 8 : 4;
+  set((const void*)k_pen_xf<T, R1, R2>);
+  set((const void*)k_pen_xi<T, R1, R2>);
+  set((const void*)k_pen_col<T, -1, R1, R2>);
+  set((const void*)k_pen_col<T, 1, R1, R2>);
+  if constexpr (R1 * R2 <= pen_max_z<T>()) {
+    set((const void*)k_z_pen<T, kVacuum, TX, R1, R2>);
+    set((const void*)k_z_pen<T, kJForm, TX, R1, R2>);
+    set((const void*)k_z_pen<T, kRhoForm, TX, R1, R2>);
+  }
+  return e;
 }
 
 cudaError_t configure_pen_kernels(int prec, int smem) {
   cudaError_t e = cudaSuccess;
-#define PSATD_SET(K)                                                                            \
-  do {                                                                                          \
-    cudaError_t r = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
-    if (r != cudaSuccess) e = r;                                                                \
-  } while (0)
-  if (prec == 32) {
-    PSATD_SET(k_pen_xf<float>);
-    PSATD_SET((k_pen_col<float, -1>));
-    PSATD_SET((k_pen_col<float, 1>));
-    PSATD_SET(k_pen_xi<float>);
-    PSATD_SET((k_z_pen<float, kVacuum, 8>));
-    PSATD_SET((k_z_pen<float, kJForm, 8>));
-    PSATD_SET((k_z_pen<float, kRhoForm, 8>));
-  } else {
-    PSATD_SET(k_pen_xf<double>);
-    PSATD_SET((k_pen_col<double, -1>));
-    PSATD_SET((k_pen_col<double, 1>));
-    PSATD_SET(k_pen_xi<double>);
-    PSATD_SET((k_z_pen<double, kVacuum, 4>));
-    PSATD_SET((k_z_pen<double, kJForm, 4>));
-    PSATD_SET((k_z_pen<double, kRhoForm, 4>));
+#define PSATD_ARM(c, N, R1, R2)                                                                  \
+  {                                                                                              \
+    const cudaError_t r = prec == 32 ? configure_pen_t<float, R1, R2>(smem) : configure_pen_t<double, R1, R2>(smem); \
+    if (r != cudaSuccess) e = r;                                                                 \
   }
-#undef PSATD_SET
+  PSATD_PENCIL_LENGTHS(PSATD_ARM)
+#undef PSATD_ARM
   return e;
 }
 

@@ -304,6 +304,11 @@ struct psatd_plan {
   int fast_boxes = 0;
   std::vector<RowJob> pen_rows, pen_rows_int;                 // push, pencil boxes
   std::vector<ColJob> pen_ycols, pen_ycols_int, zpen;
+  struct PenGroup {
+    int code;                 // pencil-length code of the transformed axis
+    int64_t start, count;     // jobs of the list
+  };
+  std::vector<PenGroup> grp_rows, grp_rows_int, grp_ycols, grp_ycols_int, grp_z;
   int pen_boxes = 0;
   std::vector<CopyBlk> blocks;
   std::vector<XTile> tiles;                                   // every block (psatd_guard_exchange)
@@ -620,6 +625,23 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     P->smem_z = std::max(P->smem_z, n2 * FIN * nz * csz);
     P->smem_zonly = std::max(P->smem_zonly, n2 * nz * csz);
   }
+  // pencil jobs grouped by the FFT length of the axis each kernel transforms
+  // (one launch per group; boxes keep their order inside a group)
+  auto group = [&](auto& list, auto code_of, std::vector<psatd_plan::PenGroup>& groups) {
+    std::stable_sort(list.begin(), list.end(),
+                     [&](const auto& a, const auto& b) { return code_of(a) < code_of(b); });
+    for (int64_t i = 0; i < (int64_t)list.size(); ++i) {
+      const int c = code_of(list[i]);
+      if (groups.empty() || groups.back().code != c) groups.push_back({c, i, 0});
+      ++groups.back().count;
+    }
+  };
+  auto shape_of_box = [&](int box) -> const ShapeDev& { return P->hshapes[P->hboxes[box].shape]; };
+  group(P->pen_rows, [&](const RowJob& j) { return shape_of_box(j.box).px; }, P->grp_rows);
+  group(P->pen_rows_int, [&](const RowJob& j) { return shape_of_box(j.box).px; }, P->grp_rows_int);
+  group(P->pen_ycols, [&](const ColJob& j) { return shape_of_box(j.box).py; }, P->grp_ycols);
+  group(P->pen_ycols_int, [&](const ColJob& j) { return shape_of_box(j.box).py; }, P->grp_ycols_int);
+  group(P->zpen, [&](const ColJob& j) { return shape_of_box(j.box).pz; }, P->grp_z);
   if (P->fast_boxes && P->prec == 32) {
     // one register-kernel shape for every fast box, or none
     int code = -2;
@@ -1035,21 +1057,25 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
        }));
     launches += 2;
   }
-  if (!P->pen_rows.empty()) {
+  for (const auto& g : P->grp_rows) {
     CK(P, timed(P, 0, st, [&] {
-         return launch_pen_xf(P->prec, D, fp, FIN, P->d_ws, S, P->d_pen_rows, (int64_t)P->pen_rows.size(),
+         return launch_pen_xf(P->prec, g.code, D, fp, FIN, P->d_ws, S, P->d_pen_rows + g.start, g.count,
                               P->smem_penx, st);
        }));
+    ++launches;
+  }
+  for (const auto& g : P->grp_ycols) {
     CK(P, timed(P, 1, st, [&] {
-         return launch_pen_col(P->prec, -1, D, P->d_ws, S, FIN, P->d_pen_ycols, (int64_t)P->pen_ycols.size(),
+         return launch_pen_col(P->prec, -1, g.code, D, P->d_ws, S, FIN, P->d_pen_ycols + g.start, g.count,
                                P->smem_penc, st);
        }));
-    launches += 2;
+    ++launches;
   }
   // S1 (z) + S2 + S3 (z)
-  if (!P->zpen.empty()) {
+  for (const auto& g : P->grp_z) {
     CK(P, timed(P, 2, st, [&] {
-         return launch_z_pen(P->prec, P->form, D, P->d_ws, S, P->d_zpen, (int64_t)P->zpen.size(), P->smem_penz, st);
+         return launch_z_pen(P->prec, P->form, g.code, D, P->d_ws, S, P->d_zpen + g.start, g.count, P->smem_penz,
+                             st);
        }));
     ++launches;
   }
@@ -1095,16 +1121,19 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
        }));
     launches += 2;
   }
-  if (!P->pen_rows_int.empty()) {
+  for (const auto& g : P->grp_ycols_int) {
     CK(P, timed(P, 3, st, [&] {
-         return launch_pen_col(P->prec, 1, D, P->d_ws, S, FOUT, P->d_pen_ycols_int,
-                               (int64_t)P->pen_ycols_int.size(), P->smem_penc, st);
+         return launch_pen_col(P->prec, 1, g.code, D, P->d_ws, S, FOUT, P->d_pen_ycols_int + g.start, g.count,
+                               P->smem_penc, st);
        }));
+    ++launches;
+  }
+  for (const auto& g : P->grp_rows_int) {
     CK(P, timed(P, 4, st, [&] {
-         return launch_pen_xi(P->prec, D, fp, FOUT, P->d_ws, S, P->d_pen_rows_int, (int64_t)P->pen_rows_int.size(),
+         return launch_pen_xi(P->prec, g.code, D, fp, FOUT, P->d_ws, S, P->d_pen_rows_int + g.start, g.count,
                               P->smem_penxi, st);
        }));
-    launches += 2;
+    ++launches;
   }
   if (!P->step_tiles.empty()) {
     CK(P, timed(P, 5, st, [&] {

@@ -225,14 +225,15 @@ int pen_x_smem(int prec, int L, int nr);
 int pen_z_max(int prec);                                  // longest n2 of a pencil box
 int pen_col_tile(int prec);                               // mx columns of a y tile
 int pen_col_smem(int prec, int n1);
-cudaError_t launch_pen_xf(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,
-                          const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st);
-cudaError_t launch_pen_col(int prec, int dir, const DevPlan& P, void* spec, int64_t sstride, int nf,
+// one launch per length group: `code` = pencil code of the transformed axis
+cudaError_t launch_pen_xf(int prec, int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+cudaError_t launch_pen_col(int prec, int dir, int code, const DevPlan& P, void* spec, int64_t sstride, int nf,
                            const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
-cudaError_t launch_z_pen(int prec, int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                         int64_t njobs, int smem, cudaStream_t st);
-cudaError_t launch_pen_xi(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,
-                          const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+cudaError_t launch_z_pen(int prec, int form, int code, const DevPlan& P, void* spec, int64_t sstride,
+                         const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+cudaError_t launch_pen_xi(int prec, int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
+                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st);
 cudaError_t configure_pen_kernels(int prec, int smem_bytes);
 
 // ---- host helpers (plan.cpp) ------------------------------------------------
