@@ -64,6 +64,8 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", type=int, choices=(32, 64), default=None,
                     help="override the precision of a configuration workload")
+    ap.add_argument("--pencil", action="store_true",
+                    help="run the boxes the plane kernels would take on the pencil kernels")
     ap.add_argument("--no-errors", action="store_true",
                     help="configuration workloads: skip the error check against the reference")
     return ap.parse_args(argv)
@@ -260,7 +262,7 @@ def run_config(args):
     if prec == 32:
         fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
         src = {k: I.round_to(v, np.float32) for k, v in src.items()}
-    plan = Plan(lay, w.h, w.dt, c=w.c, eps0=w.eps0, precision=prec, sources=w.sources)
+    plan = Plan(lay, w.h, w.dt, c=w.c, eps0=w.eps0, precision=prec, sources=w.sources, pencil=args.pencil)
     errors = None
     if not args.no_errors:
         df = plan.pack_fields(fields)
@@ -297,6 +299,14 @@ def run_config(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     launches = plan.last_launch_count()
+    # per-kernel split from a few more steps with launch-level events (no graph)
+    A.psatd_plan_set_timing(plan.handle, True)
+    A.psatd_plan_kernel_times(plan.handle)
+    plan.push(df, ds, 3)
+    plan.sync()
+    kms, kn = A.psatd_plan_kernel_times(plan.handle)
+    A.psatd_plan_set_timing(plan.handle, False)
+    kernels = {A.KERNEL_NAMES[i]: {"launches": kn[i], "ms_per_step": kms[i] / 3} for i in range(len(kms)) if kn[i]}
     plan.close()
     fin, fout = {"vacuum": (6, 6), "J": (9, 6), "rho": (10, 7)}[w.sources]
     s = prec // 8
@@ -312,7 +322,7 @@ def run_config(args):
            "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": sab,
                              "achieved": sab / (step_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                              "frac": sab / (step_ms / 1e3) / 1e9 / peak, "peak_source": peak_src},
-           "gpu_launches": launches, "errors": errors}
+           "gpu_launches": launches, "kernels": kernels, "errors": errors}
     print(json.dumps(out), flush=True)
 
 
@@ -366,7 +376,7 @@ def run_gpu(args):
     lay = build_layout(args.workload)
     w = WORKLOADS[args.workload]
     h = (1.0, 1.0, 1.0)
-    plan = Plan(lay, h, w["dt"], precision=32, sources="vacuum")
+    plan = Plan(lay, h, w["dt"], precision=32, sources="vacuum", pencil=args.pencil)
     fac = I.laser_box_factors(lay, h)
     fields = {k: plan.pack_separable(fac[k]) for k in I.COMPONENTS}
     plan.guard_exchange(fields)

@@ -74,6 +74,15 @@ typedef enum {
 #define PSATD_GENERIC_KERNELS 0x10u /* diagnostics: run every box through the generic */
                                   /* kernels even where a fast path exists (the two  */
                                   /* agree to rounding)                              */
+#define PSATD_PENCIL_KERNELS 0x20u /* run every box the pencil kernels accept on     */
+                                  /* them (one kernel per axis pass)                 */
+#define PSATD_PLANE_KERNELS  0x40u /* run every box the plane kernels accept on them */
+                                  /* (x and y per z plane, register-resident where   */
+                                  /* the shape has register codelets).  Without      */
+                                  /* either flag: plane kernels when their register- */
+                                  /* resident form serves every plane-eligible box,  */
+                                  /* else pencil kernels; all families agree to      */
+                                  /* rounding                                        */
 
 /* One FFT box.  n[] counts cells including guards; each n[d] must be even,
  * 5-smooth (2^a 3^b 5^c), n[0] in [4, 1024], n[1], n[2] in [4, 512].

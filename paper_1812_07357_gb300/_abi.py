@@ -31,6 +31,8 @@ PSATD_VACUUM = 0x1
 PSATD_RHO_CONTINUITY = 0x2
 PSATD_NO_GRAPH = 0x8
 PSATD_GENERIC_KERNELS = 0x10
+PSATD_PENCIL_KERNELS = 0x20
+PSATD_PLANE_KERNELS = 0x40
 
 
 class psatd_box(Structure):

@@ -66,7 +66,9 @@ Err validate(const psatd_plan_desc* d) {
   if (!(d->eps0 > 0.0) || !std::isfinite(d->eps0)) return {PSATD_ERR_INVALID_ARG, "eps0 must be > 0"};
   for (int a = 0; a < 3; ++a)
     if (!(d->dx[a] > 0.0) || !std::isfinite(d->dx[a])) return {PSATD_ERR_INVALID_ARG, "dx must be > 0"};
-  const uint32_t known = PSATD_VACUUM | PSATD_RHO_CONTINUITY | PSATD_NO_GRAPH | PSATD_GENERIC_KERNELS;
+  const uint32_t known =
+      PSATD_VACUUM | PSATD_RHO_CONTINUITY | PSATD_NO_GRAPH | PSATD_GENERIC_KERNELS | PSATD_PENCIL_KERNELS |
+      PSATD_PLANE_KERNELS;
   if (d->flags & ~known) return {PSATD_ERR_INVALID_ARG, "unknown flag bits"};
   if ((d->flags & PSATD_VACUUM) && (d->flags & PSATD_RHO_CONTINUITY))
     return {PSATD_ERR_INVALID_ARG, "PSATD_VACUUM and PSATD_RHO_CONTINUITY exclude each other"};
@@ -531,6 +533,33 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   CK(P, cudaGetDevice(&dev));
   CK(P, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   const int tile = fast_tile(P->prec);
+  // Kernel family of each box: plane kernels (x+y per z plane) when the
+  // register-resident plane kernels serve every plane-eligible box (one FP32
+  // shape with register codelets); otherwise the pencil kernels (one launch
+  // per axis and FFT length) take the boxes they accept, which measured
+  // faster than the shared-memory plane kernels on mixed batches; the rest
+  // run on the generic kernels.  PSATD_PENCIL_KERNELS and PSATD_PLANE_KERNELS
+  // prefer one family outright, PSATD_GENERIC_KERNELS the generic kernels.
+  auto plane_ok = [&](const psatd_box& b, const ShapeDev& sh) {
+    const int L = b.n[0] / 2, n1 = b.n[1], n2 = b.n[2], hx = L + 1;
+    const int ni = n1 - b.ng_lo[1] - b.ng_hi[1];
+    const int sm_pf = 2 * n1 * sh.lp * csz, sm_pi = (2 * n1 * hx + ni * sh.hp) * csz;
+    return !(d.flags & PSATD_GENERIC_KERNELS) && sh.fx >= 0 && sh.fy >= 0 && sh.fz >= 0 &&
+           L <= fast_max_x(P->prec) && sm_pf <= optin && sm_pi <= optin &&
+           z_fast_smem(P->prec, P->form, n2) <= optin;
+  };
+  bool reg_planes = P->prec == 32;
+  {
+    int code = -2;
+    for (size_t bi = 0; bi < P->boxes.size() && reg_planes; ++bi) {
+      const psatd_box& b = P->boxes[bi];
+      const ShapeDev& sh = P->hshapes[P->hboxes[bi].shape];
+      if (!plane_ok(b, sh)) continue;
+      const int c = reg_shape_code(sh.L, b.n[1]);
+      if (c < 0 || (code != -2 && c != code)) reg_planes = false;
+      code = c;
+    }
+  }
   for (int bi = 0; bi < (int)P->boxes.size(); ++bi) {
     const psatd_box& b = P->boxes[bi];
     const int n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
@@ -539,9 +568,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     const int ni = n1 - b.ng_lo[1] - b.ng_hi[1];
     const int sm_pf = 2 * n1 * sh.lp * csz, sm_pi = (2 * n1 * hx + ni * sh.hp) * csz;
     const int sm_zf = z_fast_smem(P->prec, P->form, n2);
-    const bool fast = !(d.flags & PSATD_GENERIC_KERNELS) && sh.fx >= 0 && sh.fy >= 0 && sh.fz >= 0 &&
-                      L <= fast_max_x(P->prec) &&
-                      sm_pf <= optin && sm_pi <= optin && sm_zf <= optin;
+    const bool fast_ok = plane_ok(b, sh);
     const int rows = n1 * n2;
     const int nr = std::max(1, std::min(rows, kMaxPoints / L));
     for (int r = 0; r < rows; r += nr) P->rows_all.push_back({bi, r, std::min(nr, rows - r), 0});
@@ -549,8 +576,12 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       const int y0 = b.ng_lo[1], y1 = n1 - b.ng_hi[1];
       for (int y = y0; y < y1; y += nr) P->rows_int.push_back({bi, z * n1 + y, std::min(nr, y1 - y), 0});
     }
-    const bool pencil = !fast && !(d.flags & PSATD_GENERIC_KERNELS) && sh.px >= 0 && sh.py >= 0 && sh.pz >= 0 &&
-                        n2 <= pen_z_max(P->prec) && sm_zf <= optin && pen_col_smem(P->prec, n1) <= optin;
+    const bool pencil_ok = !(d.flags & PSATD_GENERIC_KERNELS) && sh.px >= 0 && sh.py >= 0 && sh.pz >= 0 &&
+                           n2 <= pen_z_max(P->prec) && sm_zf <= optin && pen_col_smem(P->prec, n1) <= optin;
+    const bool prefer_pencil =
+        (d.flags & PSATD_PENCIL_KERNELS) || (!(d.flags & PSATD_PLANE_KERNELS) && !reg_planes);
+    const bool fast = fast_ok && !(pencil_ok && prefer_pencil);
+    const bool pencil = !fast && pencil_ok;
     const bool generic = !fast && !pencil;   // the generic Stockham kernels
     if (fast) {
       ++P->fast_boxes;

@@ -37,8 +37,8 @@ def rel_l2(a, b):
     return (num / den) ** 0.5
 
 
-def run_push(lay, fields, src, nsteps, h, dt, prec, form):
-    plan = Plan(lay, h, dt, precision=prec, sources=form)
+def run_push(lay, fields, src, nsteps, h, dt, prec, form, **plan_kw):
+    plan = Plan(lay, h, dt, precision=prec, sources=form, **plan_kw)
     df = plan.pack_fields(fields)
     ds = plan.pack_fields(src) if form != "vacuum" else None
     plan.push(df, ds, nsteps)
@@ -50,11 +50,11 @@ def run_push(lay, fields, src, nsteps, h, dt, prec, form):
     return out
 
 
-def check_push(lay, fields, src, nsteps, h, dt, prec, form):
+def check_push(lay, fields, src, nsteps, h, dt, prec, form, **plan_kw):
     if prec == 32:
         fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
         src = {k: I.round_to(v, np.float32) for k, v in src.items()}
-    got = run_push(lay, fields, src, nsteps, h, dt, prec, form)
+    got = run_push(lay, fields, src, nsteps, h, dt, prec, form, **plan_kw)
     ref = O.push(lay, fields, src, nsteps, h, dt, form=form)
     comps = O.COMPS + (("rho",) if form == "rho" else ())
     err = O.rel_l2_fields(lay, got, ref, comps)
@@ -240,10 +240,12 @@ def test_errors_are_reported_not_raised_on_device():
 # ---------------------------------------------------------------------------
 
 def _fast_plan_check(lay, fields, src, nsteps, h, dt, prec, form, expect_fast):
-    plan = Plan(lay, h, dt, precision=prec, sources=form)
+    """The plane kernels (requested explicitly: without the flag, boxes whose
+    shape has no register plane kernels run on the pencil kernels)."""
+    plan = Plan(lay, h, dt, precision=prec, sources=form, plane=True)
     assert plan.fast_boxes == expect_fast, (plan.fast_boxes, expect_fast)
     plan.close()
-    return check_push(lay, fields, src, nsteps, h, dt, prec, form)
+    return check_push(lay, fields, src, nsteps, h, dt, prec, form, plane=True)
 
 
 @pytest.mark.parametrize("prec", [64, 32])
@@ -288,7 +290,7 @@ def test_fast_equals_generic_fp32():
     fields = {k: I.round_to(I.scatter_global(v, lay), np.float32) for k, v in f.items()}
     outs = []
     for generic in (False, True):
-        plan = Plan(lay, (1.0,) * 3, 0.9, precision=32, sources="vacuum", generic=generic)
+        plan = Plan(lay, (1.0,) * 3, 0.9, precision=32, sources="vacuum", generic=generic, plane=not generic)
         assert plan.fast_boxes == (0 if generic else 4)
         df = plan.pack_fields(fields)
         plan.push(df, None, 5)

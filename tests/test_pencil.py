@@ -23,9 +23,9 @@ def built():
     build.build()
 
 
-def _run(lay, fields, src, nsteps, h, dt, prec, form, generic=False):
+def _run(lay, fields, src, nsteps, h, dt, prec, form, **plan_kw):
     from paper_1812_07357_gb300.solver import Plan
-    plan = Plan(lay, h, dt, precision=prec, sources=form, generic=generic)
+    plan = Plan(lay, h, dt, precision=prec, sources=form, **plan_kw)
     paths = (plan.fast_boxes, plan.pencil_boxes)
     df = plan.pack_fields(fields)
     ds = plan.pack_fields(src) if form != "vacuum" else None
@@ -38,11 +38,11 @@ def _run(lay, fields, src, nsteps, h, dt, prec, form, generic=False):
     return out, paths
 
 
-def _check(lay, fields, src, nsteps, h, dt, prec, form, paths):
+def _check(lay, fields, src, nsteps, h, dt, prec, form, paths, **plan_kw):
     if prec == 32:
         fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
         src = {k: I.round_to(v, np.float32) for k, v in src.items()}
-    got, p = _run(lay, fields, src, nsteps, h, dt, prec, form)
+    got, p = _run(lay, fields, src, nsteps, h, dt, prec, form, **plan_kw)
     assert p == paths, p
     ref = O.push(lay, fields, src, nsteps, h, dt, form=form)
     comps = O.COMPS + (("rho",) if form == "rho" else ())
@@ -115,4 +115,41 @@ def test_mixed_plane_pencil_generic_boxes():
     rng = np.random.default_rng(25)
     fields = {k: [rng.standard_normal(b.shape) for b in lay.boxes] for k in O.COMPS}
     fields = {k: O.exchange(lay, v) for k, v in fields.items()}
-    _check(lay, fields, {}, 3, (1.0, 1.0, 1.0), 0.9, 64, "vacuum", (1, 1))
+    _check(lay, fields, {}, 3, (1.0, 1.0, 1.0), 0.9, 64, "vacuum", (1, 1), plane=True)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_pencil_flag_on_plane_boxes(prec):
+    """48^3 local boxes (no register plane kernels for this shape) on the
+    pencil kernels (PSATD_PENCIL_KERNELS, also the default here) and on the
+    plane kernels (PSATD_PLANE_KERNELS): against the oracle and each other."""
+    from paper_1812_07357_gb300.solver import Plan
+    lay = I.local_layout((64, 64, 64), (2, 2, 2), 8, 16)
+    f = I.laser_fields((64, 64, 64), wavelength=8.0, waist=8.0, duration=5.0)
+    fields = {k: I.scatter_global(v, lay) for k, v in f.items()}
+    if prec == 32:
+        fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
+    outs = []
+    for pencil in (True, False):
+        plan = Plan(lay, (1.0,) * 3, 0.9, precision=prec, sources="vacuum", pencil=pencil, plane=not pencil)
+        assert (plan.fast_boxes, plan.pencil_boxes) == ((0, 8) if pencil else (8, 0))
+        df = plan.pack_fields(fields)
+        plan.push(df, None, 3)
+        plan.sync()
+        outs.append(plan.unpack_fields(df))
+        plan.close()
+    ref = O.push(lay, fields, {}, 3, (1.0,) * 3, 0.9, form="vacuum")
+    assert O.rel_l2_fields(lay, outs[0], ref, O.COMPS) <= TOL[prec]
+    assert O.rel_l2_fields(lay, outs[0], outs[1], O.COMPS) <= TOL[prec]
+
+
+def test_default_family_choice():
+    """Without a flag: the register plane shape (n0/2 = 48, n1 = 96) takes the
+    plane kernels; other plane-eligible shapes take the pencil kernels."""
+    from paper_1812_07357_gb300.solver import Plan
+    reg = I.local_layout((128, 64, 32), (2, 1, 2), (16, 16, 4), 16)        # 96 x 96 x 24 boxes
+    other = I.local_layout((64, 64, 64), (2, 2, 2), 8, 16)                 # 48^3 boxes
+    for lay, prec, want in ((reg, 32, (4, 0)), (reg, 64, (0, 4)), (other, 32, (0, 8))):
+        plan = Plan(lay, (1.0,) * 3, 0.9, precision=prec, sources="vacuum")
+        assert (plan.fast_boxes, plan.pencil_boxes) == want, (lay.boxes[0].n, prec)
+        plan.close()
