@@ -70,6 +70,10 @@ typedef enum {
 #define PSATD_VACUUM         0x1u /* J = rho = 0: only E and B are read and written   */
 #define PSATD_RHO_CONTINUITY 0x2u /* rho is in/out, advanced by continuity; E takes   */
                                   /* its longitudinal part from Gauss's law (rho form) */
+#define PSATD_J_CONSTANT     0x4u /* J is constant during each psatd_push call (the */
+                                  /* time-constant current of the source workloads): */
+                                  /* its spectrum is computed once per call, not per */
+                                  /* step (no effect with PSATD_VACUUM)              */
 #define PSATD_NO_GRAPH       0x8u /* never capture multi-step pushes in a CUDA graph   */
 #define PSATD_GENERIC_KERNELS 0x10u /* diagnostics: run every box through the generic */
                                   /* kernels even where a fast path exists (the two  */

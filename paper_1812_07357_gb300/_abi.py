@@ -32,6 +32,7 @@ PSATD_RHO_CONTINUITY = 0x2
 PSATD_NO_GRAPH = 0x8
 PSATD_GENERIC_KERNELS = 0x10
 PSATD_PENCIL_KERNELS = 0x20
+PSATD_J_CONSTANT = 0x4
 PSATD_PLANE_KERNELS = 0x40
 
 

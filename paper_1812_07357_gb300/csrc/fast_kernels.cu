@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(kPlaneThreads, sizeof(T) == 4 ? 2 : 1)
 
 template <typename T, int FORM, int TX>
 __global__ void __launch_bounds__(kThreads, 2) k_z_fast(DevPlan P, cx<T>* spec, int64_t sstride,
-                                                        const ColJob* __restrict__ jobs) {
+                                                        const ColJob* __restrict__ jobs, int nft) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const ColJob J = jobs[blockIdx.x];
@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_z_fast(DevPlan P, cx<T>* spec, 
   switch (sh.fz) {
 #define PSATD_ARM(code, N, R1, R2) \
   case code:                                                                                     \
-    z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, nm, J.m0, J.plane, ts, nyq, bx.ng_lo[2], N - bx.ng_hi[2], sh, P); \
+    z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, nm, J.m0, J.plane, ts, nyq, bx.ng_lo[2], N - bx.ng_hi[2], nft, \
+                                sh, P);                                                                              \
     break;
     PSATD_FAST_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
@@ -406,11 +407,11 @@ cudaError_t plane_occupancy(int prec, int smem_fwd, int smem_inv, int* fwd_per_s
 }
 
 cudaError_t launch_z_fast(int prec, int form, const DevPlan& P, void* spec, int64_t sstride,
-                          const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
+                          const ColJob* jobs, int64_t njobs, int smem, int nft, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs);
 #define PSATD_ZF(T, C2, FORMV, TXV) \
-  k_z_fast<T, FORMV, TXV><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs)
+  k_z_fast<T, FORMV, TXV><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs, nft)
   if (prec == 32) {
     if (form == kVacuum) PSATD_ZF(float, float2, kVacuum, kTileF32);
     else if (form == kJForm) PSATD_ZF(float, float2, kJForm, kTileF32);

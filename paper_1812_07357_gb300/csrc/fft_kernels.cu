@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kThreads) k_col(DevPlan P, cx<T>* spec, int64_
 // smem layout [z][slot][t] with t the column inside the tile.
 template <typename T, int FORM>
 __global__ void __launch_bounds__(kThreads) k_z_update(DevPlan P, cx<T>* spec, int64_t sstride,
-                                                       const ColJob* __restrict__ jobs) {
+                                                       const ColJob* __restrict__ jobs, int nft) {
   constexpr int FIN = fields_in(FORM);
   constexpr int FOUT = fields_out(FORM);
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(kThreads) k_z_update(DevPlan P, cx<T>* spec, i
   }
   __syncthreads();
   const cx<T>* twz = cpool<T>(P) + sh.az.tw;
-  fft_smem<T, -1, true>(sm, row, 1, row, sh.az, twz);
+  // slots >= nft already hold their z spectrum (a cached constant current)
+  fft_smem<T, -1, true>(sm, nft * nm, 1, row, sh.az, twz);
   for (int e = threadIdx.x; e < n2 * nm; e += blockDim.x) {
     const int z = e / nm, t = e - z * nm;
     update_mode<T, FORM>(sm + z * row + t, nm, J.m0 + t, J.plane, z, sh, P);
@@ -297,11 +298,11 @@ cudaError_t launch_col(int prec, int dir, int axis, const DevPlan& P, void* spec
 }
 
 cudaError_t launch_z_update(int prec, int form, const DevPlan& P, void* spec, int64_t sstride,
-                            const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
+                            const ColJob* jobs, int64_t njobs, int smem, int nft, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs);
 #define PSATD_ZU(T, C2, FORMV) \
-  k_z_update<T, FORMV><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs)
+  k_z_update<T, FORMV><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs, nft)
   if (prec == 32) {
     if (form == kVacuum) PSATD_ZU(float, float2, kVacuum);
     else if (form == kJForm) PSATD_ZU(float, float2, kJForm);

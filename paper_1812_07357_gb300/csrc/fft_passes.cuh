@@ -115,12 +115,13 @@ __device__ __forceinline__ void load_rows_async(void* dst, const void* src, int 
 // ---------------------------------------------------------------------------
 template <typename T, int FORM, int TX, int R1, int R2>
 __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, int64_t zst, int nm, int m0,
-                                       int y, int tstride, bool nyq, int zlo, int zhi, const ShapeDev& sh,
-                                       const DevPlan& P) {
+                                       int y, int tstride, bool nyq, int zlo, int zhi, int nft,
+                                       const ShapeDev& sh, const DevPlan& P) {
   // column t of the tile is mode column (mx, my) = (m0 + t, y), or for a
   // Nyquist tile (mx = n0/2 for TX consecutive y) (m0, y + t); its spectrum
   // starts at g + t * tstride.  Only the interior z planes [zlo, zhi) are
-  // stored back: the inverse plane pass reads no others.
+  // stored back: the inverse plane pass reads no others.  Slots >= nft
+  // already hold their z spectrum (a cached constant current): loaded as is.
   constexpr int FIN = fields_in(FORM), FOUT = fields_out(FORM);
   constexpr int NCOL = FIN * TX;
   constexpr int NP = NCOL + ((24 - NCOL % 16) % 16);   // row pitch, = 8 (mod 16)
@@ -135,10 +136,12 @@ __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, in
     cx<T> v[R1];
 #pragma unroll
     for (int j = 0; j < R1; ++j) v[j] = p[j * R2 * zst];
-    Dft<T, R1, -1>::run(v);
-    if (n2) {
+    if (s < nft) {
+      Dft<T, R1, -1>::run(v);
+      if (n2) {
 #pragma unroll
-      for (int k = 1; k < R1; ++k) v[k] = cmul(v[k], tw[n2 * k]);
+        for (int k = 1; k < R1; ++k) v[k] = cmul(v[k], tw[n2 * k]);
+      }
     }
 #pragma unroll
     for (int j = 0; j < R1; ++j) buf[(j * R2 + n2) * NP + c] = v[j];
@@ -148,11 +151,12 @@ __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, in
   {
     constexpr int ITEMS = NCOL * R1;
     constexpr int MAXI = (ITEMS + kThreads - 1) / kThreads;
+    const int ncolt = nft * TX;   // columns that take the z FFT
     cx<T> u[MAXI][R2];
 #pragma unroll
     for (int i = 0; i < MAXI; ++i) {
       const int it = threadIdx.x + i * kThreads;
-      if (it < ITEMS) {
+      if (it < ITEMS && it % NCOL < ncolt) {
         const int k1 = it / NCOL, c = it - k1 * NCOL;
 #pragma unroll
         for (int j = 0; j < R2; ++j) u[i][j] = buf[(k1 * R2 + j) * NP + c];
@@ -163,7 +167,7 @@ __device__ __forceinline__ void z_body(cx<T>* buf, cx<T>* g, int64_t sstride, in
 #pragma unroll
     for (int i = 0; i < MAXI; ++i) {
       const int it = threadIdx.x + i * kThreads;
-      if (it < ITEMS) {
+      if (it < ITEMS && it % NCOL < ncolt) {
         const int k1 = it / NCOL, c = it - k1 * NCOL;
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) buf[(k1 + R1 * k2) * NP + c] = u[i][k2];

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(kPenThreads) k_pen_col(DevPlan P, cx<T>* spec,
 // ---------------------------------------------------------------------------
 template <typename T, int FORM, int TX, int R1, int R2>
 __global__ void __launch_bounds__(kThreads, 1) k_z_pen(DevPlan P, cx<T>* spec, int64_t sstride,
-                                                       const ColJob* __restrict__ jobs) {
+                                                       const ColJob* __restrict__ jobs, int nft) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const ColJob J = jobs[blockIdx.x];
@@ -169,7 +169,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_z_pen(DevPlan P, cx<T>* spec, i
   const bool nyq = J.nm < 0;
   const int nm = nyq ? -J.nm : J.nm, ts = nyq ? hx : 1;
   cx<T>* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
-  z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, nm, J.m0, J.plane, ts, nyq, bx.ng_lo[2], N - bx.ng_hi[2], sh, P);
+  z_body<T, FORM, TX, R1, R2>(buf, g, sstride, zst, nm, J.m0, J.plane, ts, nyq, bx.ng_lo[2], N - bx.ng_hi[2], nft,
+                              sh, P);
 }
 
 // ---------------------------------------------------------------------------
@@ -289,16 +290,16 @@ cudaError_t launch_pen_col(int prec, int dir, int code, const DevPlan& P, void* 
 
 template <typename T, typename C2, int R1, int R2>
 cudaError_t launch_z_pen_t(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                           int64_t njobs, int smem, cudaStream_t st) {
+                           int64_t njobs, int smem, int nft, cudaStream_t st) {
   constexpr int TX = sizeof(T) == 4 ? 8 : 4;
   if constexpr (R1 * R2 <= pen_max_z<T>()) {
     dim3 grid((unsigned)njobs);
     if (form == kVacuum)
-      k_z_pen<T, kVacuum, TX, R1, R2><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs);
+      k_z_pen<T, kVacuum, TX, R1, R2><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs, nft);
     else if (form == kJForm)
-      k_z_pen<T, kJForm, TX, R1, R2><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs);
+      k_z_pen<T, kJForm, TX, R1, R2><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs, nft);
     else
-      k_z_pen<T, kRhoForm, TX, R1, R2><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs);
+      k_z_pen<T, kRhoForm, TX, R1, R2><<<grid, kThreads, smem, st>>>(P, (C2*)spec, sstride, jobs, nft);
     return cudaGetLastError();
   } else {
     return cudaErrorInvalidValue;
@@ -306,13 +307,13 @@ cudaError_t launch_z_pen_t(int form, const DevPlan& P, void* spec, int64_t sstri
 }
 
 cudaError_t launch_z_pen(int prec, int form, int code, const DevPlan& P, void* spec, int64_t sstride,
-                         const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
+                         const ColJob* jobs, int64_t njobs, int smem, int nft, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   switch (code) {
 #define PSATD_ARM(c, N, R1, R2)                                                                         \
   case c:                                                                                               \
-    return prec == 32 ? launch_z_pen_t<float, float2, R1, R2>(form, P, spec, sstride, jobs, njobs, smem, st) \
-                      : launch_z_pen_t<double, double2, R1, R2>(form, P, spec, sstride, jobs, njobs, smem, st);
+    return prec == 32 ? launch_z_pen_t<float, float2, R1, R2>(form, P, spec, sstride, jobs, njobs, smem, nft, st) \
+                      : launch_z_pen_t<double, double2, R1, R2>(form, P, spec, sstride, jobs, njobs, smem, nft, st);
     PSATD_PENCIL_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
     default: return cudaErrorInvalidValue;

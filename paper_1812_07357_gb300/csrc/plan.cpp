@@ -67,8 +67,8 @@ Err validate(const psatd_plan_desc* d) {
   for (int a = 0; a < 3; ++a)
     if (!(d->dx[a] > 0.0) || !std::isfinite(d->dx[a])) return {PSATD_ERR_INVALID_ARG, "dx must be > 0"};
   const uint32_t known =
-      PSATD_VACUUM | PSATD_RHO_CONTINUITY | PSATD_NO_GRAPH | PSATD_GENERIC_KERNELS | PSATD_PENCIL_KERNELS |
-      PSATD_PLANE_KERNELS;
+      PSATD_VACUUM | PSATD_RHO_CONTINUITY | PSATD_J_CONSTANT | PSATD_NO_GRAPH | PSATD_GENERIC_KERNELS |
+      PSATD_PENCIL_KERNELS | PSATD_PLANE_KERNELS;
   if (d->flags & ~known) return {PSATD_ERR_INVALID_ARG, "unknown flag bits"};
   if ((d->flags & PSATD_VACUUM) && (d->flags & PSATD_RHO_CONTINUITY))
     return {PSATD_ERR_INVALID_ARG, "PSATD_VACUUM and PSATD_RHO_CONTINUITY exclude each other"};
@@ -1059,71 +1059,112 @@ psatd_status psatd_guard_exchange(psatd_plan* P, const psatd_fields* f, const ps
   }
 }
 
-// One step S1..S4 of every box on `st`; adds the launches to *launches.
-static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, cudaStream_t st,
-                              int64_t* launches_out) {
-  const int FIN = fields_in(P->form), FOUT = fields_out(P->form);
+// S1 along x and y of the field slots fp.p[0..nf) into spectrum slots
+// spec + f * spec_total, on every kernel family; adds the launches.
+static psatd_status forward_xy(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, int nf, void* spec,
+                               cudaStream_t st, int64_t* launches_out) {
   const int64_t S = P->spec_total;
   int64_t launches = 0;
-  // S1: forward x+y (fast boxes: one plane kernel; generic: x rows, y columns)
+  // fast boxes: one plane kernel; generic: x rows, y columns; pencil: x rows, y tiles
   if (!P->plane_fwd.empty() && P->reg_code >= 0) {
     CK(P, timed(P, 0, st, [&] {
-         return launch_plane_fwd_reg(P->reg_code, D, fp, FIN, P->d_ws, S, P->d_plane_fwd,
-                                     (int64_t)P->plane_fwd.size(), st);
+         return launch_plane_fwd_reg(P->reg_code, D, fp, nf, spec, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
+                                     st);
        }));
     ++launches;
   } else if (!P->plane_fwd.empty()) {
     CK(P, timed(P, 0, st, [&] {
-         return launch_plane_fwd(P->prec, D, fp, FIN, P->d_ws, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
+         return launch_plane_fwd(P->prec, D, fp, nf, spec, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
                                  P->buf_pf, P->smem_pf, P->grid_pf, st);
        }));
     ++launches;
   }
   if (!P->g_rows.empty()) {
     CK(P, timed(P, 0, st, [&] {
-         return launch_fwd_x(P->prec, D, fp, FIN, P->d_ws, S, P->d_g_rows, (int64_t)P->g_rows.size(), P->smem_fx, st);
+         return launch_fwd_x(P->prec, D, fp, nf, spec, S, P->d_g_rows, (int64_t)P->g_rows.size(), P->smem_fx, st);
        }));
     CK(P, timed(P, 1, st, [&] {
-         return launch_col(P->prec, -1, 1, D, P->d_ws, S, FIN, P->d_g_ycols, (int64_t)P->g_ycols.size(), P->smem_y, st);
+         return launch_col(P->prec, -1, 1, D, spec, S, nf, P->d_g_ycols, (int64_t)P->g_ycols.size(), P->smem_y, st);
        }));
     launches += 2;
   }
   for (const auto& g : P->grp_rows) {
     CK(P, timed(P, 0, st, [&] {
-         return launch_pen_xf(P->prec, g.code, D, fp, FIN, P->d_ws, S, P->d_pen_rows + g.start, g.count,
-                              P->smem_penx, st);
+         return launch_pen_xf(P->prec, g.code, D, fp, nf, spec, S, P->d_pen_rows + g.start, g.count, P->smem_penx,
+                              st);
        }));
     ++launches;
   }
   for (const auto& g : P->grp_ycols) {
     CK(P, timed(P, 1, st, [&] {
-         return launch_pen_col(P->prec, -1, g.code, D, P->d_ws, S, FIN, P->d_pen_ycols + g.start, g.count,
+         return launch_pen_col(P->prec, -1, g.code, D, spec, S, nf, P->d_pen_ycols + g.start, g.count,
                                P->smem_penc, st);
        }));
     ++launches;
+  }
+  *launches_out += launches;
+  return PSATD_OK;
+}
+
+// Field slots each step transforms: with PSATD_J_CONSTANT the current's
+// three slots (the last ones) keep the spectrum computed once per push.
+static int step_slots(const psatd_plan* P) {
+  const int FIN = fields_in(P->form);
+  return (P->desc.flags & PSATD_J_CONSTANT) && P->form != kVacuum ? FIN - 3 : FIN;
+}
+
+// The whole 3D spectrum of the (constant) current into its workspace slots.
+static psatd_status transform_current(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, cudaStream_t st,
+                                      int64_t* launches_out) {
+  const int nft = step_slots(P);
+  FieldPtrs fj{};
+  for (int a = 0; a < 3; ++a) fj.p[a] = fp.p[nft + a];
+  void* spec = static_cast<char*>(P->d_ws) + (size_t)nft * P->spec_total * P->csize;
+  const psatd_status r = forward_xy(P, D, fj, 3, spec, st, launches_out);
+  if (r != PSATD_OK) return r;
+  CK(P, timed(P, 2, st, [&] {
+       return launch_col(P->prec, -1, 2, D, spec, P->spec_total, 3, P->d_zcols, (int64_t)P->zcols.size(),
+                         P->smem_zonly, st);
+     }));
+  ++*launches_out;
+  return PSATD_OK;
+}
+
+// One step S1..S4 of every box on `st`; adds the launches to *launches.
+static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, cudaStream_t st,
+                              int64_t* launches_out) {
+  const int FOUT = fields_out(P->form), NFT = step_slots(P);
+  const int64_t S = P->spec_total;
+  int64_t launches = 0;
+  // S1: forward x+y of the slots transformed every step
+  {
+    const psatd_status r = forward_xy(P, D, fp, NFT, P->d_ws, st, &launches);
+    if (r != PSATD_OK) return r;
   }
   // S1 (z) + S2 + S3 (z)
   for (const auto& g : P->grp_z) {
     CK(P, timed(P, 2, st, [&] {
          return launch_z_pen(P->prec, P->form, g.code, D, P->d_ws, S, P->d_zpen + g.start, g.count, P->smem_penz,
-                             st);
+                             NFT, st);
        }));
     ++launches;
   }
   if (!P->zfast.empty() && P->reg_z) {
     CK(P, timed(P, 2, st, [&] {
-         return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, st);
+         return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, NFT, st);
        }));
     ++launches;
   } else if (!P->zfast.empty()) {
     CK(P, timed(P, 2, st, [&] {
-         return launch_z_fast(P->prec, P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->smem_zf, st);
+         return launch_z_fast(P->prec, P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->smem_zf, NFT,
+                              st);
        }));
     ++launches;
   }
   if (!P->g_zcols.empty()) {
     CK(P, timed(P, 2, st, [&] {
-         return launch_z_update(P->prec, P->form, D, P->d_ws, S, P->d_g_zcols, (int64_t)P->g_zcols.size(), P->smem_z, st);
+         return launch_z_update(P->prec, P->form, D, P->d_ws, S, P->d_g_zcols, (int64_t)P->g_zcols.size(), P->smem_z,
+                                NFT, st);
        }));
     ++launches;
   }
@@ -1235,10 +1276,14 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
     P->last_stream = st;
     const DevPlan D = P->dev();
     int64_t launches = 0;
+    if (nsteps > 0 && step_slots(P) < fields_in(P->form)) {
+      r = transform_current(P, D, fp, st, &launches);
+      if (r != PSATD_OK) return r;
+    }
     const bool graph = nsteps > 1 && !(P->desc.flags & PSATD_NO_GRAPH) && !P->timing && step_graph(P, D, fp, nf, st);
     if (graph) {
       for (int step = 0; step < nsteps; ++step) CK(P, cudaGraphLaunch(P->graph_exec, st));
-      launches = P->graph_launches * nsteps;
+      launches += P->graph_launches * nsteps;
     } else {
       for (int step = 0; step < nsteps; ++step) {
         r = push_step(P, D, fp, st, &launches);

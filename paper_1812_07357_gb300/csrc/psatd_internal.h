@@ -166,8 +166,9 @@ cudaError_t launch_col(int prec, int dir, int axis, const DevPlan& P, void* spec
                        int64_t sstride, int nf, const ColJob* jobs, int64_t njobs, int smem,
                        cudaStream_t st);
 // z forward FFT + k-space update + z inverse FFT, all slots of `form`.
+// nft: field slots transformed along z (the others hold a cached z spectrum)
 cudaError_t launch_z_update(int prec, int form, const DevPlan& P, void* spec, int64_t sstride,
-                            const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+                            const ColJob* jobs, int64_t njobs, int smem, int nft, cudaStream_t st);
 // C2R inverse along x with 1/(n0 n1 n2) into field slots; interior_only skips guards.
 cudaError_t launch_inv_x(int prec, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem,
@@ -194,7 +195,7 @@ cudaError_t launch_plane_inv(int prec, const DevPlan& P, const FieldPtrs& f, int
 // Resident CTAs per SM of the plane kernels at the given shared memory.
 cudaError_t plane_occupancy(int prec, int smem_fwd, int smem_inv, int* fwd_per_sm, int* inv_per_sm);
 cudaError_t launch_z_fast(int prec, int form, const DevPlan& P, void* spec, int64_t sstride,
-                          const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+                          const ColJob* jobs, int64_t njobs, int smem, int nft, cudaStream_t st);
 int fast_tile(int prec);                        // mx columns per k_z_fast job
 int fast_max_x(int prec);                       // longest n0/2 of a fast-path box
 int z_fast_smem(int prec, int form, int n2);    // bytes of shared memory of k_z_fast
@@ -216,7 +217,7 @@ int z_reg_ok(int n2);
 int z_reg_smem(int form, int n2);
 int z_reg_tile_width(int form);
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                         int64_t njobs, int n2, cudaStream_t st);
+                         int64_t njobs, int n2, int nft, cudaStream_t st);
 
 // ---- pencil kernels (pencil_kernels.cu): boxes of two-pass lengths too large
 // for the plane kernels; the z pass takes fast_tile(prec) mx columns per tile
@@ -231,7 +232,7 @@ cudaError_t launch_pen_xf(int prec, int code, const DevPlan& P, const FieldPtrs&
 cudaError_t launch_pen_col(int prec, int dir, int code, const DevPlan& P, void* spec, int64_t sstride, int nf,
                            const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
 cudaError_t launch_z_pen(int prec, int form, int code, const DevPlan& P, void* spec, int64_t sstride,
-                         const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+                         const ColJob* jobs, int64_t njobs, int smem, int nft, cudaStream_t st);
 cudaError_t launch_pen_xi(int prec, int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
                           int64_t sstride, const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st);
 cudaError_t configure_pen_kernels(int prec, int smem_bytes);

@@ -91,17 +91,18 @@ __device__ __forceinline__ void pair_join(float2* v, int half, Store&& st) {
 }
 
 // Same join, results left in v: v[i] is output row i + half*NY/4 and v[NY/4 + i]
-// output row i + half*NY/4 + NY/2.
+// output row i + half*NY/4 + NY/2.  `mask`: the lanes taking part (both
+// members of every pair in it).
 template <int NY, int DIR>
-__device__ __forceinline__ void pair_join_inplace(float2* v, int half) {
+__device__ __forceinline__ void pair_join_inplace(float2* v, int half, unsigned mask = 0xffffffffu) {
   constexpr int Q = NY / 4;
   static_for<0, Q>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     const float2 send = half ? v[i] : v[Q + i];
     const float2 keep = half ? v[Q + i] : v[i];
     float2 recv;
-    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 16);
-    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 16);
+    recv.x = __shfl_xor_sync(mask, send.x, 16);
+    recv.y = __shfl_xor_sync(mask, send.y, 16);
     const float2 e = half ? recv : keep;
     const float2 o = half ? keep : recv;
     const float2 w0 = root<NY, i, DIR>(), w1 = root<NY, Q + i, DIR>();
@@ -313,7 +314,7 @@ constexpr int z_reg_min_blocks() {
 
 template <int NZ, int FORM>
 __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>())
-    k_z_reg(DevPlan P, float2* spec, int64_t sstride, const ColJob* __restrict__ jobs) {
+    k_z_reg(DevPlan P, float2* spec, int64_t sstride, const ColJob* __restrict__ jobs, int nft) {
   constexpr int TX = z_reg_tile(FORM), FIN = fields_in(FORM), FOUT = fields_out(FORM);
   constexpr int NT = z_reg_threads<FORM>(), NP = z_reg_pitch(FORM);
   constexpr int H = NZ / 2, Q = NZ / 4;
@@ -339,14 +340,21 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
 #pragma unroll
     for (int m = 0; m < H; ++m) v[m] = src[2 * m * zst];
   }
-  Dft<float, H, -1>::run(v);
-  pair_join_inplace<NZ, -1>(v, half);
-  if (s < FIN) {
+  // slots >= nft already hold their z spectrum (a cached constant current):
+  // stored in natural z order without a transform.  Both members of a pair
+  // share the slot, so the lanes of the join are whole pairs.
+  const unsigned fmask = __ballot_sync(0xffffffffu, s < nft);
+  if (s < nft) {
+    Dft<float, H, -1>::run(v);
+    pair_join_inplace<NZ, -1>(v, half, fmask);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       buf[(i + half * Q) * NP + col] = v[i];
       buf[(i + half * Q + H) * NP + col] = v[Q + i];
     }
+  } else if (s < FIN) {
+#pragma unroll
+    for (int m = 0; m < H; ++m) buf[(2 * m + half) * NP + col] = v[m];
   }
   __syncthreads();
   // k-space update, two modes per thread: thread tid keeps the column pair
@@ -409,18 +417,18 @@ int z_reg_smem(int form, int n2) { return n2 * z_reg_pitch(form) * 8; }
 int z_reg_tile_width(int form) { return z_reg_tile(form); }
 
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                         int64_t njobs, int n2, cudaStream_t st) {
+                         int64_t njobs, int n2, int nft, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs);
   const int smem = z_reg_smem(form, n2);
 #define PSATD_ZL(NZV)                                                                                 \
   if (n2 == NZV) {                                                                                   \
     if (form == kVacuum)                                                                             \
-      k_z_reg<NZV, kVacuum><<<grid, z_reg_threads<kVacuum>(), smem, st>>>(P, (float2*)spec, sstride, jobs); \
+      k_z_reg<NZV, kVacuum><<<grid, z_reg_threads<kVacuum>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft); \
     else if (form == kJForm)                                                                         \
-      k_z_reg<NZV, kJForm><<<grid, z_reg_threads<kJForm>(), smem, st>>>(P, (float2*)spec, sstride, jobs);   \
+      k_z_reg<NZV, kJForm><<<grid, z_reg_threads<kJForm>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft); \
     else                                                                                             \
-      k_z_reg<NZV, kRhoForm><<<grid, z_reg_threads<kRhoForm>(), smem, st>>>(P, (float2*)spec, sstride, jobs); \
+      k_z_reg<NZV, kRhoForm><<<grid, z_reg_threads<kRhoForm>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft); \
   }
   PSATD_REG_Z(PSATD_ZL)
 #undef PSATD_ZL

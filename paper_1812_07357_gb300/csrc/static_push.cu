@@ -239,7 +239,7 @@ extern "C" psatd_status psatd_push_box_static(const int32_t n[3], int32_t order_
   for (int step = 0; step < nsteps; ++step) {
     PSATD_CK(launch_fwd_x(32, P, fp, FIN, ws, spec, drows, (int64_t)rows.size(), nr * L * 8, st));
     PSATD_CK(launch_col(32, -1, 1, P, ws, spec, FIN, dy, (int64_t)ycols.size(), n1 * ny * 8, st));
-    PSATD_CK(launch_z_update(32, kVacuum, P, ws, spec, dz, (int64_t)zcols.size(), n2 * FIN * nz * 8, st));
+    PSATD_CK(launch_z_update(32, kVacuum, P, ws, spec, dz, (int64_t)zcols.size(), n2 * FIN * nz * 8, FIN, st));
     PSATD_CK(launch_col(32, 1, 1, P, ws, spec, FIN, dy, (int64_t)ycols.size(), n1 * ny * 8, st));
     PSATD_CK(launch_inv_x(32, P, fp, FIN, ws, spec, drows, (int64_t)rows.size(), nr * (hx + L) * 8, 1, st));
   }
