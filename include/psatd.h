@@ -217,6 +217,49 @@ const char* psatd_status_string(psatd_status s);
  * psatd_plan_create / psatd_plan_validate when plan is NULL.  Never NULL. */
 const char* psatd_last_error(const psatd_plan* plan);
 
+/* ---- Dual-grid coupling (paper Sec. 3.2.1, "dual grid decomposition") ------
+ * A second decomposition G1 of the plan's global domain -- e.g. the grid of the
+ * particle and particle-mesh operations of a PIC code, with its own sub-domain
+ * boundaries and thin guard layers -- coupled to the plan's FFT boxes G2.
+ * Every cell of every destination box (guards included) takes the value of the
+ * source grid's interior cell with the same global index (periodic axes wrap;
+ * non-periodic axes give 0 outside the domain):
+ *   PSATD_G1_TO_G2  fills the FFT boxes, guards included, before a push (the
+ *                   guard exchange of the FFT grid is then already done);
+ *   PSATD_G2_TO_G1  copies the pushed fields back (the FFT grid's guard cells
+ *                   are not read; G1's guards get their owners' new values).
+ * G1 boxes use psatd_box: n counts cells including guards (any size >= 1, no
+ * FFT constraint), origin is the global index of the first interior cell; the
+ * interiors must tile the domain exactly.  Not for PSATD_DECOMP_INDEPENDENT. */
+typedef struct psatd_coupling psatd_coupling;
+#define PSATD_G1_TO_G2 0
+#define PSATD_G2_TO_G1 1
+
+/* Host-only: the copy blocks of one direction (src_box indexes the source
+ * grid, dst_box the destination grid; src_box = -1: zero fill).  Same output
+ * convention as psatd_exchange_blocks. */
+psatd_status psatd_coupling_blocks(const psatd_plan_desc* g2, int32_t num_g1_boxes, const psatd_box* g1_boxes,
+                                   int32_t direction, psatd_copy_block* out, int64_t cap, int64_t* count);
+
+/* Build the coupling of `plan` (G2) with the G1 boxes: validates them,
+ * computes both directions' copy blocks and uploads them (plan's device).
+ * The coupling borrows the plan: destroy it before the plan. */
+psatd_status psatd_coupling_create(psatd_plan* plan, int32_t num_g1_boxes, const psatd_box* g1_boxes,
+                                   psatd_coupling** out);
+psatd_status psatd_coupling_destroy(psatd_coupling* coupling);
+
+/* Element offset and count of G1 box `box` in a G1 component buffer (boxes
+ * concatenated at 64-element-aligned offsets, x fastest, precision of the
+ * plan). */
+psatd_status psatd_coupling_layout(const psatd_coupling* coupling, int32_t box, int64_t* elem_offset,
+                                   int64_t* elems);
+
+/* Copy `nfields` component buffers (device pointers, 16-byte aligned, same
+ * component order on both grids) in `direction` on `stream`, asynchronously:
+ * one batched copy kernel.  Source and destination buffers must not overlap. */
+psatd_status psatd_couple(psatd_coupling* coupling, int32_t direction, void* const* g1_fields,
+                          void* const* g2_fields, int32_t nfields, void* stream);
+
 /* Number of kernel launches issued by the last psatd_push call (host count). */
 int64_t psatd_last_launch_count(const psatd_plan* plan);
 

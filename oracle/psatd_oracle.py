@@ -271,21 +271,8 @@ def _interior_slices(box):
     return tuple(slice(box.ng_lo[d], box.n[d] - box.ng_hi[d]) for d in (2, 1, 0))
 
 
-def exchange(layout, arrays):
-    """Return new per-box arrays whose guards hold the owning interior values.
-
-    Non-independent layouts: the box interiors tile the global domain; the
-    global field is assembled from them and every padded cell reads the
-    global cell at origin - ng_lo + i (periodic axes wrap, non-periodic axes
-    give 0 outside the domain).  Independent boxes wrap onto their own
-    interior."""
-    out = []
-    if layout.kind == "independent":
-        for b, a in zip(layout.boxes, arrays):
-            inner = a[_interior_slices(b)]
-            idx = [(np.arange(b.n[d]) - b.ng_lo[d]) % b.interior[d] for d in range(3)]
-            out.append(np.ascontiguousarray(inner[np.ix_(idx[2], idx[1], idx[0])]))
-        return out
+def _assemble(layout, arrays):
+    """The global field from the box interiors (they must tile the domain)."""
     gn = layout.global_n
     G = np.zeros((gn[2], gn[1], gn[0]))
     cover = np.zeros(G.shape, dtype=np.int64)
@@ -296,8 +283,17 @@ def exchange(layout, arrays):
         cover[dst] += 1
     if not (cover == 1).all():
         raise ValueError("box interiors do not tile the global domain")
+    return G
+
+
+def _sample(layout, G):
+    """Per-box arrays whose every padded cell reads the global cell at
+    origin - ng_lo + i (periodic axes wrap, non-periodic axes give 0 outside
+    the domain)."""
+    gn = layout.global_n
     Gz = np.zeros((gn[2] + 1, gn[1] + 1, gn[0] + 1))
     Gz[:-1, :-1, :-1] = G                      # index -1 reads the zero plane
+    out = []
     for b in layout.boxes:
         idx = []
         for d in range(3):
@@ -309,6 +305,37 @@ def exchange(layout, arrays):
             idx.append(g)
         out.append(np.ascontiguousarray(Gz[np.ix_(idx[2], idx[1], idx[0])]))
     return out
+
+
+def exchange(layout, arrays):
+    """Return new per-box arrays whose guards hold the owning interior values.
+
+    Non-independent layouts: the box interiors tile the global domain; the
+    global field is assembled from them and every padded cell reads the
+    global cell at origin - ng_lo + i (periodic axes wrap, non-periodic axes
+    give 0 outside the domain).  Independent boxes wrap onto their own
+    interior."""
+    if layout.kind == "independent":
+        out = []
+        for b, a in zip(layout.boxes, arrays):
+            inner = a[_interior_slices(b)]
+            idx = [(np.arange(b.n[d]) - b.ng_lo[d]) % b.interior[d] for d in range(3)]
+            out.append(np.ascontiguousarray(inner[np.ix_(idx[2], idx[1], idx[0])]))
+        return out
+    return _sample(layout, _assemble(layout, arrays))
+
+
+def couple(src_layout, src_arrays, dst_layout):
+    """Dual-grid coupling (paper Sec. 3.2.1, dual grid decomposition): two
+    decompositions of the same global domain; every cell of every destination
+    box (guards included) takes the value of the source-layout interior cell
+    with the same global index (periodic wrap; 0 outside a non-periodic
+    domain).  G1 -> G2 fills the FFT grid, guards included; G2 -> G1 copies
+    the FFT grid's interiors back."""
+    if tuple(src_layout.global_n) != tuple(dst_layout.global_n) or \
+            tuple(src_layout.periodic) != tuple(dst_layout.periodic):
+        raise ValueError("layouts of different domains")
+    return _sample(dst_layout, _assemble(src_layout, src_arrays))
 
 
 # ----------------------------------------------------------------------------

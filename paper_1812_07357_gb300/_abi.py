@@ -93,7 +93,16 @@ _SIGS = {
     "psatd_plan_pencil_boxes": (c_int32, [c_void_p]),
     "psatd_push_box_static": (c_int32, [POINTER(c_int32), c_int32, POINTER(c_double), c_double,
                                         c_double, POINTER(psatd_fields), c_int32, c_void_p]),
+    "psatd_coupling_blocks": (c_int32, [POINTER(psatd_plan_desc), c_int32, POINTER(psatd_box), c_int32,
+                                        POINTER(psatd_copy_block), c_int64, POINTER(c_int64)]),
+    "psatd_coupling_create": (c_int32, [c_void_p, c_int32, POINTER(psatd_box), POINTER(c_void_p)]),
+    "psatd_coupling_destroy": (c_int32, [c_void_p]),
+    "psatd_coupling_layout": (c_int32, [c_void_p, c_int32, POINTER(c_int64), POINTER(c_int64)]),
+    "psatd_couple": (c_int32, [c_void_p, c_int32, POINTER(c_void_p), POINTER(c_void_p), c_int32, c_void_p]),
 }
+
+PSATD_G1_TO_G2 = 0
+PSATD_G2_TO_G1 = 1
 
 PSATD_STATIC_SCRATCH_BYTES = 64 << 20
 
@@ -151,6 +160,54 @@ def psatd_exchange_blocks(desc: psatd_plan_desc):
     arr = (psatd_copy_block * max(n.value, 1))()
     _check(load().psatd_exchange_blocks(ctypes.byref(desc), arr, n.value, ctypes.byref(n)))
     return [arr[i] for i in range(n.value)]
+
+
+def _box_array(boxes):
+    arr = (psatd_box * max(len(boxes), 1))()
+    for i, b in enumerate(boxes):
+        arr[i].n[:] = list(b.n)
+        arr[i].ng_lo[:] = list(b.ng_lo)
+        arr[i].ng_hi[:] = list(b.ng_hi)
+        arr[i].origin[:] = list(b.origin)
+        arr[i].order_p = int(b.p)
+    return arr
+
+
+def psatd_coupling_blocks(desc: psatd_plan_desc, g1_boxes, direction: int):
+    """Host-only copy blocks of a dual-grid coupling (G1 boxes: objects with
+    n, ng_lo, ng_hi, origin, p)."""
+    arr = _box_array(g1_boxes)
+    n = c_int64(0)
+    _check(load().psatd_coupling_blocks(ctypes.byref(desc), len(g1_boxes), arr, direction, None, 0,
+                                        ctypes.byref(n)))
+    out = (psatd_copy_block * max(n.value, 1))()
+    _check(load().psatd_coupling_blocks(ctypes.byref(desc), len(g1_boxes), arr, direction, out, n.value,
+                                        ctypes.byref(n)))
+    return [out[i] for i in range(n.value)]
+
+
+def psatd_coupling_create(plan: int, g1_boxes) -> int:
+    arr = _box_array(g1_boxes)
+    out = c_void_p()
+    _check(load().psatd_coupling_create(c_void_p(plan), len(g1_boxes), arr, ctypes.byref(out)), plan)
+    return out.value
+
+
+def psatd_coupling_destroy(coupling: int):
+    _check(load().psatd_coupling_destroy(c_void_p(coupling)))
+
+
+def psatd_coupling_layout(coupling: int, box: int):
+    off, n = c_int64(), c_int64()
+    _check(load().psatd_coupling_layout(c_void_p(coupling), box, ctypes.byref(off), ctypes.byref(n)))
+    return off.value, n.value
+
+
+def psatd_couple(coupling: int, direction: int, g1_ptrs, g2_ptrs, stream: int, plan: int = None):
+    n = len(g1_ptrs)
+    a1 = (c_void_p * n)(*g1_ptrs)
+    a2 = (c_void_p * n)(*g2_ptrs)
+    _check(load().psatd_couple(c_void_p(coupling), direction, a1, a2, n, c_void_p(stream)), plan)
 
 
 def psatd_plan_create(desc: psatd_plan_desc, stream: int = 0) -> int:

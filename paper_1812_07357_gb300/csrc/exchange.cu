@@ -1,4 +1,5 @@
-// S4: guard-cell exchange between batched boxes (paper Fig. 1, step (ii)).
+// S4: guard-cell exchange between batched boxes (paper Fig. 1, step (ii)),
+// and the dual-grid coupling copies between two layouts (paper Sec. 3.2.1).
 //
 // The host precomputes copy blocks, each a 3D region of guard cells of one
 // box whose values live in the interior of one source box (or outside a
@@ -24,7 +25,7 @@ __device__ __forceinline__ int fdiv(int e, unsigned m) { return m ? (int)__umulh
 constexpr int kBatch = 4;   // units loaded before any is stored (bytes in flight)
 
 template <typename T, int V>
-__device__ __forceinline__ void copy_tile(T* base, const CopyBlk& b, const XTile& t, const BoxDev& db,
+__device__ __forceinline__ void copy_tile(T* dbase, const T* sbase, const CopyBlk& b, const XTile& t, const BoxDev& db,
                                           int64_t sfoff, int64_t sn0, int64_t sn1) {
   using Vec = typename std::conditional<V == 1, T, float4>::type;
   const int ex = b.ext[0], ey = b.ext[1];
@@ -52,34 +53,39 @@ __device__ __forceinline__ void copy_tile(T* base, const CopyBlk& b, const XTile
         } else {
           const int64_t s = sfoff + ((int64_t)(b.src_lo[2] + rz) * sn1 + (b.src_lo[1] + ry)) * sn0 +
                             b.src_lo[0] + x;
-          v[i] = *reinterpret_cast<const Vec*>(base + s);
+          v[i] = *reinterpret_cast<const Vec*>(sbase + s);
         }
       }
     }
 #pragma unroll
     for (int i = 0; i < kBatch; ++i)
-      if (d[i] >= 0) *reinterpret_cast<Vec*>(base + d[i]) = v[i];
+      if (d[i] >= 0) *reinterpret_cast<Vec*>(dbase + d[i]) = v[i];
   }
 }
 
+// dst and src boxes may belong to two layouts (the plan's boxes for the
+// guard exchange; the two grids of a dual-grid coupling); field slot
+// blockIdx.y is read from S.p and written to Dst.p.
 template <typename T>
-__global__ void __launch_bounds__(256) k_exchange(DevPlan P, FieldPtrs F, const CopyBlk* __restrict__ blocks,
+__global__ void __launch_bounds__(256) k_exchange(const BoxDev* __restrict__ dboxes, const BoxDev* __restrict__ sboxes,
+                                                  FieldPtrs Dst, FieldPtrs S, const CopyBlk* __restrict__ blocks,
                                                   const XTile* __restrict__ tiles) {
   const XTile t = tiles[blockIdx.x];
   const CopyBlk b = blocks[t.blk];
-  T* base = reinterpret_cast<T*>(F.p[blockIdx.y]);
-  const BoxDev db = P.boxes[b.dst_box];
+  T* dbase = reinterpret_cast<T*>(Dst.p[blockIdx.y]);
+  const T* sbase = reinterpret_cast<const T*>(S.p[blockIdx.y]);
+  const BoxDev db = dboxes[b.dst_box];
   int64_t sfoff = 0, sn0 = 0, sn1 = 0;
   if (b.src_box >= 0) {
-    const BoxDev sb = P.boxes[b.src_box];
+    const BoxDev sb = sboxes[b.src_box];
     sfoff = sb.foff;
     sn0 = sb.n[0];
     sn1 = sb.n[1];
   }
   if (t.vec > 1)
-    copy_tile<T, 16 / sizeof(T)>(base, b, t, db, sfoff, sn0, sn1);
+    copy_tile<T, 16 / sizeof(T)>(dbase, sbase, b, t, db, sfoff, sn0, sn1);
   else
-    copy_tile<T, 1>(base, b, t, db, sfoff, sn0, sn1);
+    copy_tile<T, 1>(dbase, sbase, b, t, db, sfoff, sn0, sn1);
 }
 
 }  // namespace
@@ -87,12 +93,18 @@ __global__ void __launch_bounds__(256) k_exchange(DevPlan P, FieldPtrs F, const 
 cudaError_t launch_exchange(int prec, const DevPlan& P, const FieldPtrs& f, int nf,
                             const CopyBlk* blocks, const XTile* tiles, int64_t ntiles,
                             cudaStream_t st) {
+  return launch_copy_blocks(prec, P.boxes, P.boxes, f, f, nf, blocks, tiles, ntiles, st);
+}
+
+cudaError_t launch_copy_blocks(int prec, const BoxDev* dboxes, const BoxDev* sboxes, const FieldPtrs& dst,
+                               const FieldPtrs& src, int nf, const CopyBlk* blocks, const XTile* tiles,
+                               int64_t ntiles, cudaStream_t st) {
   if (ntiles <= 0 || nf <= 0) return cudaSuccess;
   dim3 grid((unsigned)ntiles, nf);
   if (prec == 32)
-    k_exchange<float><<<grid, 256, 0, st>>>(P, f, blocks, tiles);
+    k_exchange<float><<<grid, 256, 0, st>>>(dboxes, sboxes, dst, src, blocks, tiles);
   else
-    k_exchange<double><<<grid, 256, 0, st>>>(P, f, blocks, tiles);
+    k_exchange<double><<<grid, 256, 0, st>>>(dboxes, sboxes, dst, src, blocks, tiles);
   return cudaGetLastError();
 }
 

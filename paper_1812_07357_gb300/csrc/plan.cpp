@@ -901,6 +901,145 @@ cudaError_t timed(psatd_plan* P, int kind, cudaStream_t st, F&& launch) {
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// ---------------------------------------------------------------------------
+// dual-grid coupling (paper Sec. 3.2.1): copy blocks between two layouts of
+// one global domain.  Every cell of every destination box (guards included)
+// reads the source-layout interior cell with the same global index.
+// ---------------------------------------------------------------------------
+namespace {
+
+std::vector<CopyBlk> coupling_blocks(const std::vector<psatd_box>& dst, const std::vector<psatd_box>& src,
+                                     const int64_t N[3], const bool per[3]) {
+  std::vector<CopyBlk> out;
+  for (int b = 0; b < (int)dst.size(); ++b) {
+    const psatd_box& B = dst[b];
+    std::vector<Seg> sg3[3];
+    for (int a = 0; a < 3; ++a) sg3[a] = axis_segments(B.origin[a] - B.ng_lo[a], B.n[a], N[a], per[a]);
+    for (const Seg& sz : sg3[2])
+      for (const Seg& sy : sg3[1])
+        for (const Seg& sx : sg3[0]) {
+          const Seg* sg[3] = {&sx, &sy, &sz};
+          if (sx.outside || sy.outside || sz.outside) {
+            CopyBlk c{};
+            c.dst_box = b;
+            c.src_box = -1;
+            for (int a = 0; a < 3; ++a) {
+              c.dst_lo[a] = (int32_t)sg[a]->dst;
+              c.ext[a] = (int32_t)sg[a]->len;
+            }
+            out.push_back(c);
+            continue;
+          }
+          for (int sb = 0; sb < (int)src.size(); ++sb) {
+            const psatd_box& S = src[sb];
+            int64_t lo[3], hi[3];
+            bool empty = false;
+            for (int a = 0; a < 3; ++a) {
+              const int64_t sm = S.n[a] - S.ng_lo[a] - S.ng_hi[a];
+              lo[a] = std::max(sg[a]->g, S.origin[a]);
+              hi[a] = std::min(sg[a]->g + sg[a]->len, S.origin[a] + sm);
+              if (hi[a] <= lo[a]) empty = true;
+            }
+            if (empty) continue;
+            CopyBlk c{};
+            c.dst_box = b;
+            c.src_box = sb;
+            for (int a = 0; a < 3; ++a) {
+              c.dst_lo[a] = (int32_t)(sg[a]->dst + (lo[a] - sg[a]->g));
+              c.src_lo[a] = (int32_t)(lo[a] - S.origin[a] + S.ng_lo[a]);
+              c.ext[a] = (int32_t)(hi[a] - lo[a]);
+            }
+            out.push_back(c);
+          }
+        }
+  }
+  return out;
+}
+
+// Tiles of up to ~2048 units (16-byte units where both rows allow them).
+std::vector<XTile> block_tiles(const std::vector<CopyBlk>& blocks, const std::vector<psatd_box>& dst,
+                               const std::vector<psatd_box>& src, int v16) {
+  std::vector<XTile> tiles;
+  for (int i = 0; i < (int)blocks.size(); ++i) {
+    const CopyBlk& c = blocks[i];
+    const int rows = c.ext[1] * c.ext[2];
+    bool vec = c.ext[0] % v16 == 0 && c.dst_lo[0] % v16 == 0 && dst[c.dst_box].n[0] % v16 == 0;
+    if (c.src_box >= 0) vec = vec && c.src_lo[0] % v16 == 0 && src[c.src_box].n[0] % v16 == 0;
+    const int unit = vec ? v16 : 1;
+    const int per = std::max(1, 2048 * unit / std::max(1, c.ext[0]));
+    for (int r = 0; r < rows; r += per) tiles.push_back({i, r, std::min(per, rows - r), vec ? v16 : 1});
+  }
+  return tiles;
+}
+
+// G1 boxes: positive interiors inside the domain that tile it exactly.
+Err validate_g1(const psatd_plan_desc& d, int32_t n, const psatd_box* g1) {
+  if (d.decomp == PSATD_DECOMP_INDEPENDENT) return {PSATD_ERR_INVALID_ARG, "independent boxes share no domain"};
+  if (n <= 0 || !g1) return {PSATD_ERR_INVALID_ARG, "no G1 boxes"};
+  int64_t vol = 0;
+  for (int b = 0; b < n; ++b) {
+    int64_t v = 1;
+    for (int a = 0; a < 3; ++a) {
+      const psatd_box& B = g1[b];
+      const int64_t m = (int64_t)B.n[a] - B.ng_lo[a] - B.ng_hi[a];
+      if (B.ng_lo[a] < 0 || B.ng_hi[a] < 0 || m < 1)
+        return {PSATD_ERR_INVALID_ARG, fmt("G1 box %d: empty interior or negative guards", b)};
+      if (B.origin[a] < 0 || B.origin[a] + m > d.global_n[a])
+        return {PSATD_ERR_INVALID_ARG, fmt("G1 box %d: interior outside the domain", b)};
+      v *= m;
+    }
+    vol += v;
+  }
+  if (vol != (int64_t)d.global_n[0] * d.global_n[1] * d.global_n[2])
+    return {PSATD_ERR_INVALID_ARG, "G1 interiors do not tile the domain"};
+  for (int b = 0; b < n; ++b)
+    for (int c = b + 1; c < n; ++c) {
+      bool overlap = true;
+      for (int a = 0; a < 3; ++a) {
+        const psatd_box &B = g1[b], &C = g1[c];
+        const int64_t mb = B.n[a] - B.ng_lo[a] - B.ng_hi[a], mc = C.n[a] - C.ng_lo[a] - C.ng_hi[a];
+        overlap = overlap && B.origin[a] < C.origin[a] + mc && C.origin[a] < B.origin[a] + mb;
+      }
+      if (overlap) return {PSATD_ERR_INVALID_ARG, fmt("G1 boxes %d and %d overlap", b, c)};
+    }
+  return {PSATD_OK, ""};
+}
+
+void domain_of(const psatd_plan_desc& d, int64_t N[3], bool per[3]) {
+  for (int a = 0; a < 3; ++a) {
+    N[a] = d.global_n[a];
+    per[a] = d.periodic[a] != 0;
+  }
+}
+
+}  // namespace
+
+struct psatd_coupling {
+  psatd_plan* plan = nullptr;
+  std::vector<psatd_box> g1;
+  std::vector<BoxDev> hg1;
+  int64_t field_total = 0;
+  std::vector<CopyBlk> blk[2];
+  std::vector<XTile> tiles[2];
+  BoxDev* d_g1 = nullptr;
+  CopyBlk* d_blk[2] = {nullptr, nullptr};
+  XTile* d_tiles[2] = {nullptr, nullptr};
+  std::vector<void*> allocs;
+  ~psatd_coupling() {
+    cudaDeviceSynchronize();
+    for (void* q : allocs) cudaFree(q);
+  }
+  template <typename V>
+  cudaError_t up(const std::vector<V>& h, V** dptr) {
+    *dptr = nullptr;
+    if (h.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)dptr, h.size() * sizeof(V));
+    if (e != cudaSuccess) return e;
+    allocs.push_back(*dptr);
+    return cudaMemcpy(*dptr, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice);
+  }
+};
+
 extern "C" {
 
 psatd_status psatd_plan_validate(const psatd_plan_desc* desc, char* msg, size_t msg_len) {
@@ -1385,6 +1524,122 @@ psatd_status psatd_plan_kernel_times(psatd_plan* P, double* ms, int64_t* launche
     P->ev_pool.push_back(r.b);
   }
   P->recs.clear();
+  return PSATD_OK;
+}
+
+psatd_status psatd_coupling_blocks(const psatd_plan_desc* g2, int32_t num_g1_boxes, const psatd_box* g1_boxes,
+                                   int32_t direction, psatd_copy_block* out, int64_t cap, int64_t* count) {
+  try {
+    if (!count || cap < 0 || (cap > 0 && !out) || (direction != PSATD_G1_TO_G2 && direction != PSATD_G2_TO_G1))
+      return fail(nullptr, PSATD_ERR_INVALID_ARG, "bad arguments");
+    Err e = validate(g2);
+    if (e.st == PSATD_OK) e = validate_g1(*g2, num_g1_boxes, g1_boxes);
+    if (e.st != PSATD_OK) return fail(nullptr, e.st, e.msg);
+    const std::vector<psatd_box> a(g2->boxes, g2->boxes + g2->num_boxes), b(g1_boxes, g1_boxes + num_g1_boxes);
+    int64_t N[3];
+    bool per[3];
+    domain_of(*g2, N, per);
+    const std::vector<CopyBlk> blocks =
+        direction == PSATD_G1_TO_G2 ? coupling_blocks(a, b, N, per) : coupling_blocks(b, a, N, per);
+    *count = (int64_t)blocks.size();
+    for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)blocks.size()); ++i) {
+      out[i].dst_box = blocks[i].dst_box;
+      out[i].src_box = blocks[i].src_box;
+      for (int k = 0; k < 3; ++k) {
+        out[i].dst_lo[k] = blocks[i].dst_lo[k];
+        out[i].src_lo[k] = blocks[i].src_lo[k];
+        out[i].ext[k] = blocks[i].ext[k];
+      }
+    }
+    return PSATD_OK;
+  } catch (...) {
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "internal error");
+  }
+}
+
+psatd_status psatd_coupling_create(psatd_plan* plan, int32_t num_g1_boxes, const psatd_box* g1_boxes,
+                                   psatd_coupling** out) {
+  if (!out) return fail(nullptr, PSATD_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!plan) return fail(nullptr, PSATD_ERR_INVALID_ARG, "plan is NULL");
+  try {
+    Err e = validate_g1(plan->desc, num_g1_boxes, g1_boxes);
+    if (e.st != PSATD_OK) return fail(plan, e.st, e.msg);
+    auto* C = new psatd_coupling();
+    C->plan = plan;
+    C->g1.assign(g1_boxes, g1_boxes + num_g1_boxes);
+    int64_t foff = 0;
+    for (const psatd_box& b : C->g1) {
+      BoxDev x{};
+      for (int a = 0; a < 3; ++a) {
+        x.n[a] = b.n[a];
+        x.ng_lo[a] = b.ng_lo[a];
+        x.ng_hi[a] = b.ng_hi[a];
+      }
+      x.foff = foff;
+      foff += align_up((int64_t)b.n[0] * b.n[1] * b.n[2], 64);
+      C->hg1.push_back(x);
+    }
+    C->field_total = foff;
+    int64_t N[3];
+    bool per[3];
+    domain_of(plan->desc, N, per);
+    const int v16 = 16 / (int)plan->rsize;
+    C->blk[PSATD_G1_TO_G2] = coupling_blocks(plan->boxes, C->g1, N, per);
+    C->blk[PSATD_G2_TO_G1] = coupling_blocks(C->g1, plan->boxes, N, per);
+    C->tiles[PSATD_G1_TO_G2] = block_tiles(C->blk[PSATD_G1_TO_G2], plan->boxes, C->g1, v16);
+    C->tiles[PSATD_G2_TO_G1] = block_tiles(C->blk[PSATD_G2_TO_G1], C->g1, plan->boxes, v16);
+    cudaError_t ce = C->up(C->hg1, &C->d_g1);
+    for (int d = 0; d < 2 && ce == cudaSuccess; ++d) {
+      ce = C->up(C->blk[d], &C->d_blk[d]);
+      if (ce == cudaSuccess) ce = C->up(C->tiles[d], &C->d_tiles[d]);
+    }
+    if (ce != cudaSuccess) {
+      delete C;
+      return fail(plan, ce == cudaErrorMemoryAllocation ? PSATD_ERR_OUT_OF_MEMORY : PSATD_ERR_CUDA,
+                  fmt("coupling: %s", cudaGetErrorString(ce)));
+    }
+    *out = C;
+    return PSATD_OK;
+  } catch (...) {
+    return fail(plan, PSATD_ERR_INVALID_ARG, "internal error");
+  }
+}
+
+psatd_status psatd_coupling_destroy(psatd_coupling* c) {
+  delete c;
+  return PSATD_OK;
+}
+
+psatd_status psatd_coupling_layout(const psatd_coupling* c, int32_t box, int64_t* off, int64_t* elems) {
+  if (!c || !off || !elems || box < 0 || box >= (int32_t)c->g1.size()) return PSATD_ERR_INVALID_ARG;
+  const psatd_box& b = c->g1[box];
+  *off = c->hg1[box].foff;
+  *elems = (int64_t)b.n[0] * b.n[1] * b.n[2];
+  return PSATD_OK;
+}
+
+psatd_status psatd_couple(psatd_coupling* c, int32_t direction, void* const* g1_fields, void* const* g2_fields,
+                          int32_t nfields, void* stream) {
+  if (!c) return PSATD_ERR_INVALID_ARG;
+  psatd_plan* P = c->plan;
+  if ((direction != PSATD_G1_TO_G2 && direction != PSATD_G2_TO_G1) || nfields < 1 || nfields > 10 || !g1_fields ||
+      !g2_fields)
+    return fail(P, PSATD_ERR_INVALID_ARG, "bad direction, field count or field arrays");
+  FieldPtrs f1{}, f2{};
+  for (int i = 0; i < nfields; ++i) {
+    f1.p[i] = g1_fields[i];
+    f2.p[i] = g2_fields[i];
+    if (!f1.p[i] || !f2.p[i] || !aligned16(f1.p[i]) || !aligned16(f2.p[i]))
+      return fail(P, PSATD_ERR_INVALID_ARG, fmt("field %d NULL or not 16-byte aligned", i));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  const bool to_fft = direction == PSATD_G1_TO_G2;
+  CK(P, launch_copy_blocks(P->prec, to_fft ? P->d_boxes : c->d_g1, to_fft ? c->d_g1 : P->d_boxes,
+                           to_fft ? f2 : f1, to_fft ? f1 : f2, nfields, c->d_blk[direction], c->d_tiles[direction],
+                           (int64_t)c->tiles[direction].size(), st));
+  P->last_launches = c->tiles[direction].empty() ? 0 : 1;
   return PSATD_OK;
 }
 

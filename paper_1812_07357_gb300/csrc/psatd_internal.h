@@ -177,6 +177,11 @@ cudaError_t launch_inv_x(int prec, const DevPlan& P, const FieldPtrs& f, int nf,
 cudaError_t launch_exchange(int prec, const DevPlan& P, const FieldPtrs& f, int nf,
                             const CopyBlk* blocks, const XTile* tiles, int64_t ntiles,
                             cudaStream_t st);
+// Copy blocks whose destination boxes (dboxes, buffers dst) and source boxes
+// (sboxes, buffers src) may belong to two different layouts.
+cudaError_t launch_copy_blocks(int prec, const BoxDev* dboxes, const BoxDev* sboxes, const FieldPtrs& dst,
+                               const FieldPtrs& src, int nf, const CopyBlk* blocks, const XTile* tiles,
+                               int64_t ntiles, cudaStream_t st);
 // Maximum dynamic shared memory opt-in for all kernels of a precision.
 cudaError_t configure_kernels(int prec, int smem_bytes);
 

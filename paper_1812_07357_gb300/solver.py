@@ -179,3 +179,48 @@ class Plan:
 
     def last_launch_count(self) -> int:
         return A.psatd_last_launch_count(self.handle)
+
+
+class Coupling:
+    """Dual-grid coupling of a plan's FFT boxes (G2) with a second
+    decomposition G1 of the same domain (an ``inputs.Layout`` whose boxes may
+    have any sizes and guard widths): ``to_fft`` fills every G2 cell from the
+    G1 interiors, ``from_fft`` every G1 cell from the G2 interiors."""
+
+    def __init__(self, plan, g1_layout):
+        self.plan = plan
+        self.g1 = g1_layout
+        self.handle = A.psatd_coupling_create(plan.handle, g1_layout.boxes)
+        self.offsets = [A.psatd_coupling_layout(self.handle, i) for i in range(len(g1_layout.boxes))]
+        last = self.offsets[-1]
+        self.elems = last[0] + last[1] + 64
+
+    def close(self):
+        if self.handle:
+            A.psatd_coupling_destroy(self.handle)
+            self.handle = None
+
+    def empty(self):
+        return self.plan.torch.zeros(self.elems, dtype=self.plan.dtype, device="cuda")
+
+    def pack(self, arrays: List[np.ndarray]):
+        t = self.empty()
+        for (off, n), a in zip(self.offsets, arrays):
+            t[off:off + n] = self.plan.torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(
+                device="cuda", dtype=self.plan.dtype)
+        return t
+
+    def unpack(self, t) -> List[np.ndarray]:
+        h = t.detach().to("cpu", dtype=self.plan.torch.float64).numpy()
+        return [h[off:off + n].reshape(b.shape).copy() for (off, n), b in zip(self.offsets, self.g1.boxes)]
+
+    def _run(self, direction, g1: Dict, g2: Dict):
+        keys = [k for k in g1 if k in g2]
+        A.psatd_couple(self.handle, direction, [g1[k].data_ptr() for k in keys], [g2[k].data_ptr() for k in keys],
+                       self.plan.stream.cuda_stream, self.plan.handle)
+
+    def to_fft(self, g1: Dict, g2: Dict):
+        self._run(A.PSATD_G1_TO_G2, g1, g2)
+
+    def from_fft(self, g2: Dict, g1: Dict):
+        self._run(A.PSATD_G2_TO_G1, g1, g2)

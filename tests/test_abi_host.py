@@ -169,3 +169,62 @@ def test_exchange_block_count_local_512():
     assert len(blocks) == 512 * 26
     vol = sum(b.ext[0] * b.ext[1] * b.ext[2] for b in blocks)
     assert vol == lay.guard_cells
+
+
+# ---------------------------------------------------------------------------
+# dual-grid coupling (host-only block computation)
+# ---------------------------------------------------------------------------
+
+def _apply_coupling(blocks, dst_arrays, src_arrays):
+    out = [a.copy() for a in dst_arrays]
+    for bl in blocks:
+        ex, ey, ez = bl.ext
+        dx, dy, dz = bl.dst_lo
+        if bl.src_box < 0:
+            out[bl.dst_box][dz:dz + ez, dy:dy + ey, dx:dx + ex] = 0.0
+        else:
+            sx, sy, sz = bl.src_lo
+            out[bl.dst_box][dz:dz + ez, dy:dy + ey, dx:dx + ex] = \
+                src_arrays[bl.src_box][sz:sz + ez, sy:sy + ey, sx:sx + ex]
+    return out
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 1, 1)])
+def test_coupling_blocks_match_oracle(lib, periodic):
+    g2 = I.hybrid_layout((32, 12, 10), (2, 1, 1), 4, 8, periodic=periodic)     # FFT grid
+    g1 = I.local_layout((32, 12, 10), (4, 3, 2), (1, 2, 1), 4, periodic=periodic)   # particle grid
+    rng = np.random.default_rng(5)
+    a1 = [rng.standard_normal(b.shape) for b in g1.boxes]
+    a2 = [rng.standard_normal(b.shape) for b in g2.boxes]
+    d = _desc(g2)
+    fwd = A.psatd_coupling_blocks(d, g1.boxes, A.PSATD_G1_TO_G2)
+    for g, r in zip(_apply_coupling(fwd, [np.full(b.shape, np.nan) for b in g2.boxes], a1), O.couple(g1, a1, g2)):
+        assert np.array_equal(g, r)          # every G2 cell written
+    back = A.psatd_coupling_blocks(d, g1.boxes, A.PSATD_G2_TO_G1)
+    for g, r in zip(_apply_coupling(back, [np.full(b.shape, np.nan) for b in g1.boxes], a2), O.couple(g2, a2, g1)):
+        assert np.array_equal(g, r)
+    # sources read interior cells only
+    for blocks, src in ((fwd, g1), (back, g2)):
+        for bl in blocks:
+            if bl.src_box >= 0:
+                sb = src.boxes[bl.src_box]
+                assert all(sb.ng_lo[k] <= bl.src_lo[k] and bl.src_lo[k] + bl.ext[k] <= sb.n[k] - sb.ng_hi[k]
+                           for k in range(3))
+
+
+def test_coupling_rejects_bad_g1(lib):
+    g2 = I.local_layout((16, 16, 16), (2, 2, 2), 4, 4)
+    d = _desc(g2)
+    gap = I.local_layout((16, 16, 16), (2, 2, 2), 1, 4).boxes[:-1]                       # a hole
+    over = list(I.local_layout((16, 16, 16), (2, 2, 2), 1, 4).boxes)
+    over[1] = I.Box(over[1].n, over[1].ng_lo, over[1].ng_hi, (4, 0, 0), 4)                 # overlap + hole
+    outside = [I.Box((18, 18, 18), (1,) * 3, (1,) * 3, (8, 0, 0), 4)]                      # past the domain
+    for boxes in (gap, over, outside):
+        with pytest.raises(A.PsatdError) as e:
+            A.psatd_coupling_blocks(d, boxes, A.PSATD_G1_TO_G2)
+        assert e.value.status == A.PSATD_ERR_INVALID_ARG
+    with pytest.raises(A.PsatdError):
+        A.psatd_coupling_blocks(d, I.local_layout((16, 16, 16), (2, 2, 2), 1, 4).boxes, 2)
+    ind = I.independent_layout(seed=3, nboxes=2, sizes=(8, 10), ngs=(1,), min_interior=4)
+    with pytest.raises(A.PsatdError):
+        A.psatd_coupling_blocks(_desc(ind), ind.boxes, A.PSATD_G1_TO_G2)

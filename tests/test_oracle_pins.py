@@ -508,3 +508,66 @@ def test_workload_memory_ratio_local_vs_hybrid():
     loc = I.local_layout((1024, 256, 256), (16, 4, 4), 64, 64)
     assert loc.cells / hyb.cells == 18.0
     assert abs(O.memory_gain(1, 4) * 9 - 18.0) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Dual-grid coupling (Sec. 3.2.1): cell-by-cell owner search, round trip
+# ---------------------------------------------------------------------------
+
+def _brute_couple(src, arrays, dst):
+    out = []
+    for b in dst.boxes:
+        a = np.zeros(b.shape)
+        for kz in range(b.n[2]):
+            for ky in range(b.n[1]):
+                for kx in range(b.n[0]):
+                    loc = (kx, ky, kz)
+                    g = [b.origin[d] - b.ng_lo[d] + loc[d] for d in range(3)]
+                    outside = False
+                    for d in range(3):
+                        if dst.periodic[d]:
+                            g[d] %= dst.global_n[d]
+                        elif not 0 <= g[d] < dst.global_n[d]:
+                            outside = True
+                    if outside:
+                        continue
+                    hits = [s for s, sb in enumerate(src.boxes)
+                            if all(sb.origin[d] <= g[d] < sb.origin[d] + sb.interior[d] for d in range(3))]
+                    assert len(hits) == 1
+                    sb = src.boxes[hits[0]]
+                    li = tuple(g[d] - sb.origin[d] + sb.ng_lo[d] for d in range(3))
+                    a[kz, ky, kx] = arrays[hits[0]][li[2], li[1], li[0]]
+        out.append(a)
+    return out
+
+
+@pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 1, 0)])
+def test_couple_matches_owner_search(periodic):
+    rng = np.random.default_rng(19)
+    g1 = I.local_layout((12, 8, 8), (3, 2, 2), 1, 4, periodic=periodic)      # particle grid, thin guards
+    g2 = I.local_layout((12, 8, 8), (2, 1, 2), (2, 3, 2), 4, periodic=periodic)   # FFT grid, wide guards
+    a1 = [rng.standard_normal(b.shape) for b in g1.boxes]
+    got = O.couple(g1, a1, g2)
+    for g, r in zip(got, _brute_couple(g1, a1, g2)):
+        assert np.array_equal(g, r)
+    a2 = [rng.standard_normal(b.shape) for b in g2.boxes]
+    back = O.couple(g2, a2, g1)
+    for g, r in zip(back, _brute_couple(g2, a2, g1)):
+        assert np.array_equal(g, r)
+
+
+def test_couple_round_trip_is_identity_on_consistent_fields():
+    rng = np.random.default_rng(20)
+    g1 = I.local_layout((16, 12, 8), (4, 3, 2), 1, 4)
+    g2 = I.hybrid_layout((16, 12, 8), (2, 1, 1), 3, 4)
+    a1 = O.exchange(g1, [rng.standard_normal(b.shape) for b in g1.boxes])
+    a2 = O.couple(g1, a1, g2)
+    assert all(np.array_equal(x, y) for x, y in zip(O.exchange(g2, a2), a2))   # G2 guards filled too
+    for x, y in zip(O.couple(g2, a2, g1), a1):
+        assert np.array_equal(x, y)
+
+
+def test_couple_rejects_different_domains():
+    with pytest.raises(ValueError):
+        O.couple(I.local_layout((8, 8, 8), (2, 1, 1), 1, 4), [np.zeros((10, 10, 6))] * 2,
+                 I.local_layout((8, 8, 12), (2, 1, 1), 1, 4))
