@@ -80,6 +80,12 @@ typedef enum {
                                   /* agree to rounding)                              */
 #define PSATD_PENCIL_KERNELS 0x20u /* run every box the pencil kernels accept on     */
                                   /* them (one kernel per axis pass)                 */
+#define PSATD_NODAL          0x80u /* collocated variant (not in the paper, which   */
+                                  /* uses staggered stencils): every component at   */
+                                  /* the cell nodes, order-p centred symbol         */
+                                  /* K = sum_l beta_l sin(l k h)/(l h), beta_l the  */
+                                  /* Lagrange weights at 0 of the nodes l^2, no Yee */
+                                  /* phase shifts                                   */
 #define PSATD_PLANE_KERNELS  0x40u /* run every box the plane kernels accept on them */
                                   /* (x and y per z plane, register-resident where   */
                                   /* the shape has register codelets).  Without      */

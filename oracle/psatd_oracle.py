@@ -127,6 +127,48 @@ def modified_wavenumber(k, h: float, p: int):
     return K
 
 
+def nodal_weights(p: int):
+    """Weights beta_l, l = 1..p/2, of the order-p centred difference on a
+    collocated (nodal) grid
+
+        f'(x) ~ sum_l beta_l [f(x + l h) - f(x - l h)] / (2 l h),
+
+    exact to order h^p: sum_l beta_l l^(2j) = delta_j0 for j = 0..p/2-1, the
+    Lagrange basis of the nodes l^2 evaluated at 0 (exact rationals).  This
+    variant (all components at the cell nodes, no Yee shifts) is not in the
+    paper, which uses staggered stencils; p = 0 returns None."""
+    if p == 0:
+        return None
+    if p < 2 or p % 2:
+        raise ValueError("order p must be even and >= 2, or 0 for infinite")
+    q = p // 2
+    out = []
+    for l in range(1, q + 1):
+        b = Fraction(1)
+        for j in range(1, q + 1):
+            if j != l:
+                b *= Fraction(j * j, j * j - l * l)
+        out.append(b)
+    return out
+
+
+def modified_wavenumber_nodal(k, h: float, p: int):
+    """Fourier symbol K(k) = sum_l beta_l sin(l k h)/(l h) of the order-p
+    centred nodal difference (D f = i K f); K = k for p = 0 except at the
+    Nyquist wavenumber |k| = pi/h, where K = 0: on a collocated grid the
+    Nyquist mode is its own mirror image (k = -k), so only K = 0 keeps the
+    derivative of a real field real (finite p gives 0 there by itself)."""
+    k = np.asarray(k, dtype=np.float64)
+    if p == 0:
+        K = k.copy()
+        K[np.isclose(np.abs(k * h), np.pi, rtol=0, atol=1e-12)] = 0.0
+        return K
+    K = np.zeros_like(k)
+    for l, b in enumerate(nodal_weights(p), start=1):
+        K += float(b) * np.sin(l * k * h) / (l * h)
+    return K
+
+
 def axis_wavenumbers(n: int, h: float):
     """True wavenumber of every index of an n-point periodic axis."""
     m = np.arange(n)
@@ -216,31 +258,35 @@ def update_modes(E, B, J, R, K, dt, c=1.0, eps0=1.0, form="vacuum"):
     return En, Bn, Rn
 
 
-def _box_k(shape_zyx, h, p):
+def _box_k(shape_zyx, h, p, nodal=False):
     """Broadcastable (k, K) grids for a box: true and modified wavenumbers."""
     nz, ny, nx = shape_zyx
     kx = axis_wavenumbers(nx, h[0])[None, None, :]
     ky = axis_wavenumbers(ny, h[1])[None, :, None]
     kz = axis_wavenumbers(nz, h[2])[:, None, None]
-    Kx = modified_wavenumber(kx, h[0], p)
-    Ky = modified_wavenumber(ky, h[1], p)
-    Kz = modified_wavenumber(kz, h[2], p)
+    mw = modified_wavenumber_nodal if nodal else modified_wavenumber
+    Kx = mw(kx, h[0], p)
+    Ky = mw(ky, h[1], p)
+    Kz = mw(kz, h[2], p)
     return (kx, ky, kz), (Kx, Ky, Kz)
 
 
-def _shift(k, comp, h, sign):
+def _shift(k, comp, h, sign, nodal=False):
+    if nodal:                     # every component at the cell nodes
+        return 1.0
     s = YEE[comp]
     return np.exp(sign * 1j * (k[0] * s[0] * h[0] + k[1] * s[1] * h[1] + k[2] * s[2] * h[2]))
 
 
-def push_box(f, src, h, p, dt, c=1.0, eps0=1.0, form="vacuum", return_imag=False):
+def push_box(f, src, h, p, dt, c=1.0, eps0=1.0, form="vacuum", return_imag=False, nodal=False):
     """One PSATD step on one periodic box.
 
     f: dict Ex..Bz -> (nz, ny, nx) float64 arrays; src: dict Jx, Jy, Jz[, rho]
-    or None.  Returns a new dict (with 'rho' when form == 'rho')."""
+    or None.  Returns a new dict (with 'rho' when form == 'rho').  nodal: the
+    collocated variant (nodal_weights, no Yee shifts)."""
     shape = f["Ex"].shape
-    k, K = _box_k(shape, h, p)
-    cen = lambda a, comp: fft3(a) * _shift(k, comp, h, -1.0)
+    k, K = _box_k(shape, h, p, nodal)
+    cen = lambda a, comp: fft3(a) * _shift(k, comp, h, -1.0, nodal)
     E = tuple(cen(f[c_], c_) for c_ in ("Ex", "Ey", "Ez"))
     B = tuple(cen(f[c_], c_) for c_ in ("Bx", "By", "Bz"))
     J = R = None
@@ -251,7 +297,7 @@ def push_box(f, src, h, p, dt, c=1.0, eps0=1.0, form="vacuum", return_imag=False
     En, Bn, Rn = update_modes(E, B, J, R, K, dt, c, eps0, form)
     out, imag = {}, 0.0
     for comp, a in zip(("Ex", "Ey", "Ez", "Bx", "By", "Bz"), list(En) + list(Bn)):
-        r = ifft3(a * _shift(k, comp, h, +1.0))
+        r = ifft3(a * _shift(k, comp, h, +1.0, nodal))
         imag = max(imag, float(np.abs(r.imag).max()))
         out[comp] = r.real.copy()
     if Rn is not None:
@@ -346,7 +392,7 @@ COMPS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
 def push(layout, fields, src, nsteps, h, dt, c=1.0, eps0=1.0, form="vacuum",
-         boxes=None):
+         boxes=None, nodal=False):
     """Advance ``fields`` (dict comp -> list of per-box arrays) by ``nsteps``
     steps: every step advances each box (Sec. 1.3 local FFT), then exchanges
     guards.  With form 'rho', ``src['rho']`` is advanced too and returned in
@@ -366,7 +412,7 @@ def push(layout, fields, src, nsteps, h, dt, c=1.0, eps0=1.0, form="vacuum",
                 sb = {k: src[k][b] for k in ("Jx", "Jy", "Jz")}
                 if form == "rho":
                     sb["rho"] = rho[b]
-            o = push_box(fb, sb, h, box.p, dt, c, eps0, form)
+            o = push_box(fb, sb, h, box.p, dt, c, eps0, form, nodal=nodal)
             for k in COMPS:
                 new[k][b] = o[k]
             if form == "rho":

@@ -34,6 +34,7 @@ PSATD_GENERIC_KERNELS = 0x10
 PSATD_PENCIL_KERNELS = 0x20
 PSATD_J_CONSTANT = 0x4
 PSATD_PLANE_KERNELS = 0x40
+PSATD_NODAL = 0x80
 
 
 class psatd_box(Structure):

@@ -68,7 +68,7 @@ Err validate(const psatd_plan_desc* d) {
     if (!(d->dx[a] > 0.0) || !std::isfinite(d->dx[a])) return {PSATD_ERR_INVALID_ARG, "dx must be > 0"};
   const uint32_t known =
       PSATD_VACUUM | PSATD_RHO_CONTINUITY | PSATD_J_CONSTANT | PSATD_NO_GRAPH | PSATD_GENERIC_KERNELS |
-      PSATD_PENCIL_KERNELS | PSATD_PLANE_KERNELS;
+      PSATD_PENCIL_KERNELS | PSATD_PLANE_KERNELS | PSATD_NODAL;
   if (d->flags & ~known) return {PSATD_ERR_INVALID_ARG, "unknown flag bits"};
   if ((d->flags & PSATD_VACUUM) && (d->flags & PSATD_RHO_CONTINUITY))
     return {PSATD_ERR_INVALID_ARG, "PSATD_VACUUM and PSATD_RHO_CONTINUITY exclude each other"};
@@ -263,16 +263,17 @@ bool radix_plan(int n, AxisPlan& ap) {
 
 
 // Order-p staggered stencil weights (see tables.cu for their use):
-std::vector<double> stencil_alpha(int p) {
-  // alpha_l = prod_{j != l} (2j-1)^2 / ((2j-1)^2 - (2l-1)^2), l = 1..p/2
+std::vector<double> stencil_alpha(int p, bool nodal) {
+  // staggered: alpha_l = prod_{j != l} (2j-1)^2 / ((2j-1)^2 - (2l-1)^2), l = 1..p/2
+  // nodal:     beta_l  = prod_{j != l} j^2 / (j^2 - l^2)
   const int q = p / 2;
   std::vector<double> a(q);
   for (int l = 1; l <= q; ++l) {
     double v = 1.0;
-    const double xl = (double)(2 * l - 1) * (2 * l - 1);
+    const double xl = nodal ? (double)l * l : (double)(2 * l - 1) * (2 * l - 1);
     for (int j = 1; j <= q; ++j) {
       if (j == l) continue;
-      const double xj = (double)(2 * j - 1) * (2 * j - 1);
+      const double xj = nodal ? (double)j * j : (double)(2 * j - 1) * (2 * j - 1);
       v *= xj / (xj - xl);
     }
     a[l - 1] = v;
@@ -835,7 +836,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   for (const ShapeDev& s : P->hshapes) {
     if (s.p == 0 || alpha_of.count(s.p)) continue;
     alpha_of[s.p] = (int64_t)halpha.size();
-    auto a = stencil_alpha(s.p);
+    auto a = stencil_alpha(s.p, (d.flags & PSATD_NODAL) != 0);
     halpha.insert(halpha.end(), a.begin(), a.end());
   }
   if (e == cudaSuccess) e = tmp_alloc(halpha.size() * 8, (void**)&alpha);
@@ -848,9 +849,10 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     const int q = s.p / 2;
     const double* al = q ? alpha + alpha_of[s.p] : alpha;
     e = gen_post(c64 + s.post, s.n[0], st);
-    if (e == cudaSuccess) e = gen_axis(r64 + s.kx, c64 + s.phx, s.hx, s.n[0], d.dx[0], q, al, st);
-    if (e == cudaSuccess) e = gen_axis(r64 + s.ky, c64 + s.phy, s.n[1], s.n[1], d.dx[1], q, al, st);
-    if (e == cudaSuccess) e = gen_axis(r64 + s.kz, c64 + s.phz, s.n[2], s.n[2], d.dx[2], q, al, st);
+    const int nodal = (d.flags & PSATD_NODAL) != 0;
+    if (e == cudaSuccess) e = gen_axis(r64 + s.kx, c64 + s.phx, s.hx, s.n[0], d.dx[0], q, al, nodal, st);
+    if (e == cudaSuccess) e = gen_axis(r64 + s.ky, c64 + s.phy, s.n[1], s.n[1], d.dx[1], q, al, nodal, st);
+    if (e == cudaSuccess) e = gen_axis(r64 + s.kz, c64 + s.phz, s.n[2], s.n[2], d.dx[2], q, al, nodal, st);
     if (e == cudaSuccess)
       e = gen_coef(q64 + s.coef, s.hx, s.n[1], s.n[2], r64 + s.kx, r64 + s.ky, r64 + s.kz, d.c, d.dt, st);
   }

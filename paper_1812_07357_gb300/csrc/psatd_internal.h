@@ -245,8 +245,9 @@ cudaError_t configure_pen_kernels(int prec, int smem_bytes);
 // ---- host helpers (plan.cpp) ------------------------------------------------
 // Radix schedule of a complex FFT length (false if it is not 5-smooth).
 bool radix_plan(int n, AxisPlan& ap);
-// Weights alpha_l, l = 1..p/2, of the order-p staggered difference.
-std::vector<double> stencil_alpha(int p);
+// Weights alpha_l, l = 1..p/2, of the order-p staggered difference
+// (nodal: beta_l of the centred collocated difference).
+std::vector<double> stencil_alpha(int p, bool nodal = false);
 // Text returned by psatd_last_error(NULL) on this thread.
 void set_thread_error(const char* msg);
 
@@ -254,7 +255,7 @@ void set_thread_error(const char* msg);
 cudaError_t gen_twiddles(double2* out, int n, cudaStream_t st);
 cudaError_t gen_post(double2* out, int n0, cudaStream_t st);
 cudaError_t gen_axis(double* K, double2* ph, int count, int n, double h, int q,
-                     const double* alpha_dev, cudaStream_t st);
+                     const double* alpha_dev, int nodal, cudaStream_t st);
 cudaError_t gen_coef(Coef4<double>* out, int hx, int n1, int n2, const double* kx,
                      const double* ky, const double* kz, double c, double dt, cudaStream_t st);
 cudaError_t convert_pools(const double* r64, float* r32, int64_t nr, const double2* c64,

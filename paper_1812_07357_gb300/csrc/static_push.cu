@@ -217,9 +217,9 @@ extern "C" psatd_status psatd_push_box_static(const int32_t n[3], int32_t order_
   PSATD_CK(gen_twiddles(c64 + s.ay.tw, n1, st));
   PSATD_CK(gen_twiddles(c64 + s.az.tw, n2, st));
   PSATD_CK(gen_post(c64 + s.post, n0, st));
-  PSATD_CK(gen_axis(r64 + s.kx, c64 + s.phx, hx, n0, dx[0], q, al, st));
-  PSATD_CK(gen_axis(r64 + s.ky, c64 + s.phy, n1, n1, dx[1], q, al, st));
-  PSATD_CK(gen_axis(r64 + s.kz, c64 + s.phz, n2, n2, dx[2], q, al, st));
+  PSATD_CK(gen_axis(r64 + s.kx, c64 + s.phx, hx, n0, dx[0], q, al, 0, st));
+  PSATD_CK(gen_axis(r64 + s.ky, c64 + s.phy, n1, n1, dx[1], q, al, 0, st));
+  PSATD_CK(gen_axis(r64 + s.kz, c64 + s.phz, n2, n2, dx[2], q, al, 0, st));
   PSATD_CK(gen_coef(q64, hx, n1, n2, r64 + s.kx, r64 + s.ky, r64 + s.kz, c, dt, st));
   PSATD_CK(convert_pools(r64, reinterpret_cast<float*>(A + o_r32), rtot, c64,
                          reinterpret_cast<float2*>(A + o_c32), ctot, q64,

@@ -30,25 +30,38 @@ __global__ void g_post(double2* out, int n0) {
 // Index m of an n-point axis has k = 2 pi mt/(n h), mt = m (m <= n/2) else m - n.
 // K(k) = sum_l alpha_l 2 sin((2l-1) k h/2)/((2l-1) h)   (q = p/2 terms), or k (q = 0).
 // ph = exp(i k h/2).
+// nodal = 0: staggered K = sum_l alpha_l 2 sin((2l-1) k h/2) / ((2l-1) h) and the
+// half-cell phase exp(i k h/2); nodal = 1: collocated K = sum_l beta_l
+// sin(l k h) / (l h) and no phase (weights in `alpha`).
 __global__ void g_axis(double* K, double2* ph, int count, int n, double h, int q,
-                       const double* __restrict__ alpha) {
+                       const double* __restrict__ alpha, int nodal) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= count) return;
   const int mt = (2 * m <= n) ? m : m - n;
   double k;
   if (q == 0) {
-    k = 2.0 * M_PI * (double)mt / ((double)n * h);
+    // collocated infinite order: the Nyquist index is its own mirror image,
+    // only K = 0 keeps the derivative of a real field real
+    k = (nodal && 2 * mt == n) ? 0.0 : 2.0 * M_PI * (double)mt / ((double)n * h);
   } else {
     k = 0.0;
     for (int l = 1; l <= q; ++l) {
-      const int o = 2 * l - 1;
-      k += alpha[l - 1] * 2.0 * sinpi((double)(o * mt) / (double)n) / ((double)o * h);
+      if (nodal) {
+        k += alpha[l - 1] * sinpi((double)(2 * l * mt) / (double)n) / ((double)l * h);
+      } else {
+        const int o = 2 * l - 1;
+        k += alpha[l - 1] * 2.0 * sinpi((double)(o * mt) / (double)n) / ((double)o * h);
+      }
     }
   }
   K[m] = k;
-  double s, c;
-  sincospi((double)mt / (double)n, &s, &c);
-  ph[m] = make_double2(c, s);
+  if (nodal) {
+    ph[m] = make_double2(1.0, 0.0);
+  } else {
+    double s, c;
+    sincospi((double)mt / (double)n, &s, &c);
+    ph[m] = make_double2(c, s);
+  }
 }
 
 // theta = c dt |K|:  C = cos theta,  Sw = dt sin(theta)/theta,
@@ -111,8 +124,8 @@ cudaError_t gen_post(double2* out, int n0, cudaStream_t st) {
   return cudaGetLastError();
 }
 cudaError_t gen_axis(double* K, double2* ph, int count, int n, double h, int q,
-                     const double* alpha_dev, cudaStream_t st) {
-  g_axis<<<nblk(count), 256, 0, st>>>(K, ph, count, n, h, q, alpha_dev);
+                     const double* alpha_dev, int nodal, cudaStream_t st) {
+  g_axis<<<nblk(count), 256, 0, st>>>(K, ph, count, n, h, q, alpha_dev, nodal);
   return cudaGetLastError();
 }
 cudaError_t gen_coef(Coef4<double>* out, int hx, int n1, int n2, const double* kx, const double* ky,

@@ -18,7 +18,7 @@ COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
 def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no_graph=False,
-              generic=False, pencil=False, plane=False, j_constant=False):
+              generic=False, pencil=False, plane=False, j_constant=False, nodal=False):
     """psatd_plan_desc for an ``inputs.Layout``; the returned object keeps the
     box array alive (attribute ``_boxes``)."""
     nb = len(layout.boxes)
@@ -49,6 +49,8 @@ def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no
         flags |= A.PSATD_PLANE_KERNELS
     if j_constant:
         flags |= A.PSATD_J_CONSTANT
+    if nodal:
+        flags |= A.PSATD_NODAL
     d.flags = flags
     d._boxes = arr
     return d
@@ -58,7 +60,8 @@ class Plan:
     """A PSATD plan on the current CUDA device."""
 
     def __init__(self, layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum",
-                 stream=None, no_graph=False, generic=False, pencil=False, plane=False, j_constant=False):
+                 stream=None, no_graph=False, generic=False, pencil=False, plane=False, j_constant=False,
+                 nodal=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -70,7 +73,7 @@ class Plan:
         self.cdtype = torch.complex64 if precision == 32 else torch.complex128
         self.np_dtype = np.float32 if precision == 32 else np.float64
         self.desc = make_desc(layout, h, dt, c, eps0, precision, sources, no_graph, generic, pencil, plane,
-                              j_constant)
+                              j_constant, nodal)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = A.psatd_plan_create(self.desc, self.stream.cuda_stream)
         self.offsets = [A.psatd_plan_layout(self.handle, i) for i in range(len(layout.boxes))]

@@ -571,3 +571,103 @@ def test_couple_rejects_different_domains():
     with pytest.raises(ValueError):
         O.couple(I.local_layout((8, 8, 8), (2, 1, 1), 1, 4), [np.zeros((10, 10, 6))] * 2,
                  I.local_layout((8, 8, 12), (2, 1, 1), 1, 4))
+
+
+# ---------------------------------------------------------------------------
+# Nodal (collocated) variant: centred weights, symbol, conservation
+# ---------------------------------------------------------------------------
+
+def test_nodal_weights_low_orders_and_exactness():
+    assert O.nodal_weights(2) == [Fraction(1)]
+    assert O.nodal_weights(4) == [Fraction(4, 3), Fraction(-1, 3)]
+    # the classical 4th-order centred coefficients 2/3 and -1/12 (beta_l / (2 l))
+    b = O.nodal_weights(4)
+    assert [b[0] / 2, b[1] / 4] == [Fraction(2, 3), Fraction(-1, 12)]
+    for p in (2, 4, 8, 16, 32):
+        b = O.nodal_weights(p)
+        for j in range(p // 2):
+            assert sum(x * l ** (2 * j) for l, x in enumerate(b, start=1)) == (1 if j == 0 else 0)
+    assert O.nodal_weights(0) is None
+
+
+def _centred_diff(f, axis, p, h):
+    """Order-p centred difference on a periodic nodal grid, cell by cell, with
+    weights from the exactness system sum_l beta_l l^(2j) = delta_j0 solved
+    by exact elimination (independent of the oracle's Lagrange formula)."""
+    q = p // 2
+    A = [[Fraction(l ** (2 * j)) for l in range(1, q + 1)] + [Fraction(int(j == 0))] for j in range(q)]
+    for c in range(q):                            # exact Gauss-Jordan over the rationals
+        piv = next(r for r in range(c, q) if A[r][c] != 0)
+        A[c], A[piv] = A[piv], A[c]
+        for r in range(q):
+            if r != c and A[r][c] != 0:
+                fac = A[r][c] / A[c][c]
+                A[r] = [a - fac * b for a, b in zip(A[r], A[c])]
+    w = [float(A[r][q] / A[r][r]) for r in range(q)]   # beta_l
+    out = np.zeros_like(f)
+    for l, b in enumerate(w, start=1):
+        out += b * (np.roll(f, -l, axis) - np.roll(f, l, axis)) / (2 * l * h)
+    return out
+
+
+@pytest.mark.parametrize("p", [2, 4, 8, 16])
+def test_nodal_wavenumber_is_stencil_eigenvalue_and_order(p):
+    n, h = 24, 0.7
+    x = np.arange(n)
+    for m in range(0, n // 2 + 1):
+        k = 2 * np.pi * m / (n * h)
+        f = np.exp(1j * k * x * h).reshape(1, 1, n)
+        lam = (_centred_diff(f, 2, p, h) / f).ravel()
+        assert np.allclose(lam, 1j * O.modified_wavenumber_nodal(k, h, p), atol=1e-11, rtol=0)
+    e1 = abs(O.modified_wavenumber_nodal(0.2, 1.0, p) - 0.2)
+    e2 = abs(O.modified_wavenumber_nodal(0.1, 1.0, p) - 0.1)
+    if p <= 8:
+        assert 2 ** (p + 1) * 0.8 < e1 / e2 < 2 ** (p + 1) * 1.2
+
+
+def test_nodal_push_conserves_energy_and_div_b():
+    rng = np.random.default_rng(31)
+    n, p = 16, 8
+    lay = I.global_layout((n, n, n), p)
+    f = {k: [rng.standard_normal((n, n, n))] for k in O.COMPS}
+    # a divergence-free B (curl of a random potential with the same centred stencil)
+    A_ = [rng.standard_normal((n, n, n)) for _ in range(3)]
+    dd = lambda a, ax: _centred_diff(a, ax, p, 1.0)
+    f["Bx"] = [dd(A_[2], 1) - dd(A_[1], 0)]
+    f["By"] = [dd(A_[0], 0) - dd(A_[2], 2)]
+    f["Bz"] = [dd(A_[1], 2) - dd(A_[0], 1)]
+    out = O.push(lay, f, {}, 5, (1.0,) * 3, 0.7, nodal=True)
+    e0 = sum(float(np.sum(f[k][0] ** 2)) for k in O.COMPS)
+    e1 = sum(float(np.sum(out[k][0] ** 2)) for k in O.COMPS)
+    assert abs(e1 - e0) <= 1e-12 * e0
+    divb = dd(out["Bx"][0], 2) + dd(out["By"][0], 1) + dd(out["Bz"][0], 0)
+    assert np.abs(divb).max() <= 1e-11 * max(1.0, np.abs(out["Bx"][0]).max())
+
+
+def test_nodal_plane_wave_dispersion():
+    """A single transverse mode rotates with omega = c K_nodal per step."""
+    n, p, dt, h = 16, 4, 0.6, 1.0
+    lay = I.global_layout((n, n, n), p)
+    m = 3
+    k = 2 * np.pi * m / (n * h)
+    x = np.arange(n) * h
+    ey = np.cos(k * x)[None, None, :] * np.ones((n, n, 1))
+    K = O.modified_wavenumber_nodal(k, h, p)
+    bz = ey.copy()                                   # B = E / c for a +x wave with the nodal K
+    f = {c: [np.zeros((n, n, n))] for c in O.COMPS}
+    f["Ey"] = [ey]
+    f["Bz"] = [bz]
+    out = O.push(lay, f, {}, 1, (h,) * 3, dt, nodal=True)
+    want = np.cos(k * x - K * dt)[None, None, :] * np.ones((n, n, 1))
+    assert np.abs(out["Ey"][0] - want).max() <= 1e-12
+
+
+def test_nodal_infinite_order_keeps_fields_real():
+    """At p = infinity the collocated symbol is 0 at Nyquist; the push of a
+    real field stays real (imaginary part of the inverse FFT at rounding)."""
+    rng = np.random.default_rng(33)
+    f = {k: rng.standard_normal((8, 10, 12)) for k in O.COMPS}
+    K = O.modified_wavenumber_nodal(O.axis_wavenumbers(12, 1.0), 1.0, 0)
+    assert K[6] == 0.0 and K[5] == O.axis_wavenumbers(12, 1.0)[5]
+    _, imag = O.push_box(f, None, (1.0,) * 3, 0, 0.7, nodal=True, return_imag=True)
+    assert imag <= 1e-13
