@@ -223,7 +223,7 @@ const char* psatd_status_string(psatd_status s);
  * psatd_plan_create / psatd_plan_validate when plan is NULL.  Never NULL. */
 const char* psatd_last_error(const psatd_plan* plan);
 
-/* ---- Dual-grid coupling (paper Sec. 3.2.1, "dual grid decomposition") ------
+/* ---- Dual-grid coupling (paper Sec. 2.5.2, "dual grid decomposition") ------
  * A second decomposition G1 of the plan's global domain -- e.g. the grid of the
  * particle and particle-mesh operations of a PIC code, with its own sub-domain
  * boundaries and thin guard layers -- coupled to the plan's FFT boxes G2.

@@ -372,7 +372,7 @@ def exchange(layout, arrays):
 
 
 def couple(src_layout, src_arrays, dst_layout):
-    """Dual-grid coupling (paper Sec. 3.2.1, dual grid decomposition): two
+    """Dual-grid coupling (paper Sec. 2.5.2, dual grid decomposition): two
     decompositions of the same global domain; every cell of every destination
     box (guards included) takes the value of the source-layout interior cell
     with the same global index (periodic wrap; 0 outside a non-periodic

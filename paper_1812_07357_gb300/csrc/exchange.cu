@@ -1,5 +1,5 @@
 // S4: guard-cell exchange between batched boxes (paper Fig. 1, step (ii)),
-// and the dual-grid coupling copies between two layouts (paper Sec. 3.2.1).
+// and the dual-grid coupling copies between two layouts (paper Sec. 2.5.2).
 //
 // The host precomputes copy blocks, each a 3D region of guard cells of one
 // box whose values live in the interior of one source box (or outside a

@@ -904,7 +904,7 @@ cudaError_t timed(psatd_plan* P, int kind, cudaStream_t st, F&& launch) {
 // C ABI
 // ===========================================================================
 // ---------------------------------------------------------------------------
-// dual-grid coupling (paper Sec. 3.2.1): copy blocks between two layouts of
+// dual-grid coupling (paper Sec. 2.5.2): copy blocks between two layouts of
 // one global domain.  Every cell of every destination box (guards included)
 // reads the source-layout interior cell with the same global index.
 // ---------------------------------------------------------------------------

@@ -1,4 +1,4 @@
-"""Dual-grid coupling on the GPU (paper Sec. 3.2.1): the copies G1 -> G2 and
+"""Dual-grid coupling on the GPU (paper Sec. 2.5.2): the copies G1 -> G2 and
 G2 -> G1 are bit-exact against the oracle's coupling, and a dual-grid cycle
 (fill the FFT grid from the particle grid, push it, copy the fields back)
 matches the oracle running the same cycle."""

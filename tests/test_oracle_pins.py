@@ -511,7 +511,7 @@ def test_workload_memory_ratio_local_vs_hybrid():
 
 
 # ---------------------------------------------------------------------------
-# Dual-grid coupling (Sec. 3.2.1): cell-by-cell owner search, round trip
+# Dual-grid coupling (Sec. 2.5.2): cell-by-cell owner search, round trip
 # ---------------------------------------------------------------------------
 
 def _brute_couple(src, arrays, dst):
