@@ -194,33 +194,98 @@ __device__ __forceinline__ ModeXY2 mode_xy2(int mxa, int mya, int mxb, int myb, 
   return r;
 }
 
+// Per-z quantities of modes A and B at mz: K_z, the Yee phase and the
+// coefficient quads.
+struct ModeZ2 {
+  float kz;
+  float2 pz;
+  Coef4<float2> q;
+};
+
+__device__ __forceinline__ ModeZ2 mode_z2(const ModeXY2& m, int mz, const ShapeDev& sh, const DevPlan& P) {
+  const int n1 = sh.n[1], n2 = sh.n[2];
+  ModeZ2 r;
+  r.kz = rpool<float>(P)[sh.kz + mz];
+  r.pz = cpool<float>(P)[sh.phz + mz];
+  const int mzr = mz <= n2 - mz ? mz : n2 - mz;
+  const int64_t zoff = (int64_t)mzr * (n1 / 2 + 1) * sh.hx;
+  const float4 qa = reinterpret_cast<const float4*>(P.coef)[m.qa + zoff];
+  const float4 qb = reinterpret_cast<const float4*>(P.coef)[m.qb + zoff];
+  r.q.c = make_float2(qa.x, qb.x);
+  r.q.s = make_float2(qa.y, qb.y);
+  r.q.x1 = make_float2(qa.z, qb.z);
+  r.q.x3 = make_float2(qa.w, qb.w);
+  return r;
+}
+
+// A and B of one slot: the float4 (re A, im A, re B, im B) at md.
+__device__ __forceinline__ C2 load2(const float2* md) {
+  const float4 w = *reinterpret_cast<const float4*>(md);
+  return C2{make_float2(w.x, w.z), make_float2(w.y, w.w)};
+}
+__device__ __forceinline__ void store2(float2* md, C2 v) {
+  *reinterpret_cast<float4*>(md) = make_float4(v.x.x, v.y.x, v.x.y, v.y.y);
+}
+
 // md: mode A of field slot 0 (16-byte aligned); slot f of A and B is the
 // float4 at md + f * fs (complex elements).
 template <int FORM>
 __device__ __forceinline__ void update_mode_z2(float2* md, int fs, const ModeXY2& m, int mz, const ShapeDev& sh,
                                                const DevPlan& P) {
-  const int n1 = sh.n[1], n2 = sh.n[2];
-  const float kz = rpool<float>(P)[sh.kz + mz];
-  const float2 pz1 = cpool<float>(P)[sh.phz + mz];
-  const int mzr = mz <= n2 - mz ? mz : n2 - mz;
-  const int64_t zoff = (int64_t)mzr * (n1 / 2 + 1) * sh.hx;
-  const float4 qa = reinterpret_cast<const float4*>(P.coef)[m.qa + zoff];
-  const float4 qb = reinterpret_cast<const float4*>(P.coef)[m.qb + zoff];
-  Coef4<float2> q;
-  q.c = make_float2(qa.x, qb.x);
-  q.s = make_float2(qa.y, qb.y);
-  q.x1 = make_float2(qa.z, qb.z);
-  q.x3 = make_float2(qa.w, qb.w);
+  const ModeZ2 z = mode_z2(m, mz, sh, P);
   C2 v[fields_in(FORM)];
 #pragma unroll
-  for (int f = 0; f < fields_in(FORM); ++f) {
-    const float4 w = *reinterpret_cast<const float4*>(md + f * fs);
-    v[f] = C2{make_float2(w.x, w.z), make_float2(w.y, w.w)};
-  }
-  update_core<float2, C2, FORM>(v, m.Kx, m.Ky, make_float2(kz, kz), m.px, m.py, pack2(pz1, pz1), m.pxy, q, P);
+  for (int f = 0; f < fields_in(FORM); ++f) v[f] = load2(md + f * fs);
+  update_core<float2, C2, FORM>(v, m.Kx, m.Ky, make_float2(z.kz, z.kz), m.px, m.py, pack2(z.pz, z.pz), m.pxy, z.q,
+                                P);
 #pragma unroll
-  for (int f = 0; f < fields_out(FORM); ++f)
-    *reinterpret_cast<float4*>(md + f * fs) = make_float4(v[f].x.x, v[f].y.x, v[f].x.y, v[f].y.y);
+  for (int f = 0; f < fields_out(FORM); ++f) store2(md + f * fs, v[f]);
+}
+
+// Modes k and k + NZ/2 of columns A and B, with the last radix-2 stage of the
+// forward z FFT before the update and the first stage of the inverse after
+// it.  lo / hi: slot 0 of the rows k and NZ/2 + k.  For slots f < nft those
+// rows hold the half-length DFTs of the even and odd z samples, E[k] and
+// O[k]; with w = exp(-2 pi i k / NZ) the modes are
+//   X[k] = E[k] + w O[k],   X[k + NZ/2] = E[k] - w O[k],
+// and after the update the rows receive the inputs of the half-length
+// inverse DFTs of the even and odd z samples,
+//   E'[k] = X'[k] + X'[k + NZ/2],   O'[k] = conj(w) (X'[k] - X'[k + NZ/2]).
+// Slots f >= nft (a cached current spectrum) already hold X in natural z
+// order, so rows k and NZ/2 + k are the two modes themselves.
+template <int FORM, int NZ>
+__device__ __forceinline__ void update_pair_z2(float2* lo, float2* hi, int fs, const ModeXY2& m, int k, float2 w,
+                                               int nft, const ShapeDev& sh, const DevPlan& P) {
+  constexpr int FIN = fields_in(FORM), FOUT = fields_out(FORM);
+  const C2 W{make_float2(w.x, w.x), make_float2(w.y, w.y)};
+  C2 a[FIN], b[FIN];
+#pragma unroll
+  for (int f = 0; f < FIN; ++f) {
+    const C2 e = load2(lo + f * fs), o = load2(hi + f * fs);
+    if (f < nft) {
+      const C2 t = cmul(o, W);
+      a[f] = e + t;
+      b[f] = e - t;
+    } else {
+      a[f] = e;
+      b[f] = o;
+    }
+  }
+  {
+    const ModeZ2 z = mode_z2(m, k, sh, P);
+    update_core<float2, C2, FORM>(a, m.Kx, m.Ky, make_float2(z.kz, z.kz), m.px, m.py, pack2(z.pz, z.pz), m.pxy, z.q,
+                                  P);
+  }
+  {
+    const ModeZ2 z = mode_z2(m, k + NZ / 2, sh, P);
+    update_core<float2, C2, FORM>(b, m.Kx, m.Ky, make_float2(z.kz, z.kz), m.px, m.py, pack2(z.pz, z.pz), m.pxy, z.q,
+                                  P);
+  }
+#pragma unroll
+  for (int f = 0; f < FOUT; ++f) {
+    store2(lo + f * fs, a[f] + b[f]);
+    store2(hi + f * fs, cmulc(a[f] - b[f], W));
+  }
 }
 
 template <typename T, int FORM>

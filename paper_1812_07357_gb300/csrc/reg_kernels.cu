@@ -9,10 +9,13 @@
 //                    whose operands cross between the pair with shuffles.
 //   k_plane_inv_reg  the mirror image, keeping interior rows and cells only,
 //                    and writing the guard cells the plane feeds (fused S4).
-//   k_z_reg          z FFT of every field slot of a tile of columns (a thread
-//                    pair per column, loads straight from HBM into registers),
-//                    the k-space update of every mode through shared memory,
-//                    and the inverse z FFT of the output slots back to HBM.
+//   k_z_reg          z FFT of every field slot of a tile of columns: a thread
+//                    pair per column (loads straight from HBM into registers)
+//                    does the half-length DFTs of the even and odd z samples,
+//                    the update threads do the radix-2 stage and the k-space
+//                    update of every mode in shared memory, then the inverse
+//                    radix-2 stage, and the pairs the half-length inverse DFTs
+//                    of the output slots back to HBM.
 //
 // Twiddle factors are compile-time constants (unit_roots.h).
 #include <cuda_runtime.h>
@@ -317,10 +320,10 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
     k_z_reg(DevPlan P, float2* spec, int64_t sstride, const ColJob* __restrict__ jobs, int nft) {
   constexpr int TX = z_reg_tile(FORM), FIN = fields_in(FORM), FOUT = fields_out(FORM);
   constexpr int NT = z_reg_threads<FORM>(), NP = z_reg_pitch(FORM);
-  constexpr int H = NZ / 2, Q = NZ / 4;
+  constexpr int H = NZ / 2;
   static_assert(NT % (2 * TX) == 0, "update threads keep one column");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* buf = reinterpret_cast<float2*>(smem_raw);    // [z][slot * TX + t], pitch NP
+  float2* buf = reinterpret_cast<float2*>(smem_raw);    // [row][slot * TX + t], pitch NP
   const ColJob J = jobs[blockIdx.x];
   const BoxDev bx = P.boxes[J.box];
   const ShapeDev& sh = P.shapes[bx.shape];
@@ -330,6 +333,7 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
   const bool nyq = J.nm < 0;
   const int nm = nyq ? -J.nm : J.nm, ts = nyq ? hx : 1;
   float2* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
+  // thread pair per (slot, column): member `half` holds the z samples 2m + half
   const int tid = threadIdx.x, half = pair_half(tid), col = pair_index(tid);
   const int s = col / TX, t = col - s * TX;
   const bool live = t < nm && s < FIN;
@@ -340,61 +344,60 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
 #pragma unroll
     for (int m = 0; m < H; ++m) v[m] = src[2 * m * zst];
   }
-  // slots >= nft already hold their z spectrum (a cached constant current):
-  // stored in natural z order without a transform.  Both members of a pair
-  // share the slot, so the lanes of the join are whole pairs.
-  const unsigned fmask = __ballot_sync(0xffffffffu, s < nft);
+  // half-length forward DFT of the member's samples into row half * H + k;
+  // slots >= nft already hold their z spectrum (a cached constant current) in
+  // natural z order and are stored as they are.
   if (s < nft) {
     Dft<float, H, -1>::run(v);
-    pair_join_inplace<NZ, -1>(v, half, fmask);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      buf[(i + half * Q) * NP + col] = v[i];
-      buf[(i + half * Q + H) * NP + col] = v[Q + i];
-    }
+    for (int k = 0; k < H; ++k) buf[(half * H + k) * NP + col] = v[k];
   } else if (s < FIN) {
 #pragma unroll
     for (int m = 0; m < H; ++m) buf[(2 * m + half) * NP + col] = v[m];
   }
   __syncthreads();
-  // k-space update, two modes per thread: thread tid keeps the column pair
-  // (2 tp, 2 tp + 1), tp = tid % (TX/2), and walks z with a compile-time trip
-  // count (unrolled, so the table loads of all its modes are in flight
-  // together).  A pair whose second column is past the tile computes it on
-  // dead data (clamped table indices) and only writes dead shared memory.
+  // k-space update of the column pair (2 tp, 2 tp + 1), tp = tid % (TX/2),
+  // modes k and k + H for k = tid / (TX/2) + i NT/(TX/2) (unrolled), with the
+  // radix-2 stages of both z transforms.  A pair whose second column is past
+  // the tile computes it on dead data (clamped table indices) and only writes
+  // dead shared memory.
   {
-    constexpr int TP = TX / 2, ZS = NT / TP, NIT = (NZ + ZS - 1) / ZS;
+    constexpr int TP = TX / 2, ZS = NT / TP, NIT = (H + ZS - 1) / ZS;
     static_assert(TX % 2 == 0 && NT % TP == 0, "column pairs");
-    const int tp = tid % TP, z0 = tid / TP;
+    const int tp = tid % TP, k0 = tid / TP;
     const int ta = 2 * tp;
     if (ta < nm) {
       const int mxa = nyq ? J.m0 : J.m0 + ta, mya = nyq ? J.plane + ta : J.plane;
       const int mxb = nyq ? J.m0 : mxa + 1, myb = nyq ? min(mya + 1, n1 - 1) : J.plane;
       const ModeXY2 xy = mode_xy2(mxa, mya, mxb, myb, sh, P);
 #pragma unroll
-      for (int j = 0; j < NIT; ++j) {
-        const int z = z0 + j * ZS;
-        if (NZ % ZS == 0 || z < NZ) update_mode_z2<FORM>(buf + z * NP + ta, TX, xy, z, sh, P);
+      for (int it = 0; it < NIT; ++it) {
+        const int k = k0 + it * ZS;
+        if (H % ZS == 0 || k < H) {
+          float2 w;
+          sincospif((float)(2 * k) / (float)NZ, &w.y, &w.x);
+          w.y = -w.y;   // exp(-2 pi i k / NZ)
+          update_pair_z2<FORM, NZ>(buf + k * NP + ta, buf + (k + H) * NP + ta, TX, xy, k, w, nft, sh, P);
+        }
       }
     }
   }
   __syncthreads();
-  // inverse of the output slots; threads of the remaining slots repeat the
-  // last output slot (the pair shuffles need both lanes) and store nothing.
-  // Only interior z planes are stored: the inverse plane pass reads no others.
+  // half-length inverse DFTs: member `half` gives the z samples 2m + half of
+  // the output slots; threads of the remaining slots repeat the last output
+  // slot and store nothing.  Only interior z planes are stored: the inverse
+  // plane pass reads no others.
   const int so = s < FOUT ? s : FOUT - 1;
 #pragma unroll
-  for (int m = 0; m < H; ++m) v[m] = buf[(2 * m + half) * NP + so * TX + t];
+  for (int k = 0; k < H; ++k) v[k] = buf[(half * H + k) * NP + so * TX + t];
   Dft<float, H, 1>::run(v);
-  pair_join_inplace<NZ, 1>(v, half);
   if (live && s < FOUT) {
     const int zlo = bx.ng_lo[2], zhi = NZ - bx.ng_hi[2];
-    float2* dst = g + s * sstride + (int64_t)t * ts;
+    float2* dst = g + s * sstride + (int64_t)t * ts + half * zst;
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int z1 = i + half * Q, z2 = z1 + H;
-      if (z1 >= zlo && z1 < zhi) dst[z1 * zst] = v[i];
-      if (z2 >= zlo && z2 < zhi) dst[z2 * zst] = v[Q + i];
+    for (int m = 0; m < H; ++m) {
+      const int z = 2 * m + half;
+      if (z >= zlo && z < zhi) dst[2 * m * zst] = v[m];
     }
   }
 }
