@@ -218,33 +218,132 @@ __device__ __forceinline__ ModeZ2 mode_z2(const ModeXY2& m, int mz, const ShapeD
   return r;
 }
 
-// A and B of one slot: the float4 (re A, im A, re B, im B) at md.
+// A and B of one slot as the 16 bytes at md: (re A, re B, im A, im B) in the
+// "re-first" order, (im A, im B, re A, re B) in the "im-first" order, so that
+// both two-lane halves are register pairs as loaded.
+template <bool IM_FIRST>
 __device__ __forceinline__ C2 load2(const float2* md) {
   const float4 w = *reinterpret_cast<const float4*>(md);
-  return C2{make_float2(w.x, w.z), make_float2(w.y, w.w)};
+  return IM_FIRST ? C2{make_float2(w.z, w.w), make_float2(w.x, w.y)} : C2{make_float2(w.x, w.y), make_float2(w.z, w.w)};
 }
+template <bool IM_FIRST>
 __device__ __forceinline__ void store2(float2* md, C2 v) {
-  *reinterpret_cast<float4*>(md) = make_float4(v.x.x, v.y.x, v.x.y, v.y.y);
+  *reinterpret_cast<float4*>(md) =
+      IM_FIRST ? make_float4(v.y.x, v.y.y, v.x.x, v.x.y) : make_float4(v.x.x, v.x.y, v.y.x, v.y.y);
 }
 
-// md: mode A of field slot 0 (16-byte aligned); slot f of A and B is the
-// float4 at md + f * fs (complex elements).
+// ---- the packed update, written instruction by instruction -----------------
+// The same update as update_core for (float2, C2), with every real operation
+// a two-lane FMUL / FFMA of sm_100+ and the negated operands formed once per
+// mode pair (a subtraction a - b c is fma(-b, c, a)), so that no lane shuffles
+// or per-use negations are needed.
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
+
+// m conj(p) and n p for a phase p with npy = -p.y
+__device__ __forceinline__ C2 cmulc_n(C2 m, C2 p, float2 npy) {
+  return C2{fma2(m.y, p.y, mul2(m.x, p.x)), fma2(m.x, npy, mul2(m.y, p.x))};
+}
+__device__ __forceinline__ C2 cmul_n(C2 n, C2 p, float2 npy) {
+  return C2{fma2(n.y, npy, mul2(n.x, p.x)), fma2(n.x, p.y, mul2(n.y, p.x))};
+}
+// a u - b v for real a, b given as (a, -b)
+__device__ __forceinline__ C2 cross1(float2 a, C2 u, float2 nb, C2 v) {
+  return C2{fma2(nb, v.x, mul2(a, u.x)), fma2(nb, v.y, mul2(a, u.y))};
+}
+__device__ __forceinline__ C2 dot3(float2 kx, C2 x, float2 ky, C2 y, float2 kz, C2 z) {
+  return C2{fma2(kz, z.x, fma2(ky, y.x, mul2(kx, x.x))), fma2(kz, z.y, fma2(ky, y.y, mul2(kx, x.y)))};
+}
+
 template <int FORM>
-__device__ __forceinline__ void update_mode_z2(float2* md, int fs, const ModeXY2& m, int mz, const ShapeDev& sh,
-                                               const DevPlan& P) {
-  const ModeZ2 z = mode_z2(m, mz, sh, P);
-  C2 v[fields_in(FORM)];
-#pragma unroll
-  for (int f = 0; f < fields_in(FORM); ++f) v[f] = load2(md + f * fs);
-  update_core<float2, C2, FORM>(v, m.Kx, m.Ky, make_float2(z.kz, z.kz), m.px, m.py, pack2(z.pz, z.pz), m.pxy, z.q,
-                                P);
-#pragma unroll
-  for (int f = 0; f < fields_out(FORM); ++f) store2(md + f * fs, v[f]);
+__device__ __forceinline__ void update_core2(C2* m, float2 Kx, float2 Ky, float2 Kz, C2 px, C2 py, C2 pz, C2 pxy,
+                                             const Coef4<float2>& q, const DevPlan& P) {
+  const float2 npx = neg2(px.y), npy = neg2(py.y), npz = neg2(pz.y), npxy = neg2(pxy.y);
+  const C2 pyz = cmul_n(py, pz, npz), pxz = cmul_n(px, pz, npz);
+  const float2 npyz = neg2(pyz.y), npxz = neg2(pxz.y);
+  const float2 nKx = neg2(Kx), nKy = neg2(Ky), nKz = neg2(Kz);
+  // centred spectra
+  const C2 ex = cmulc_n(m[0], px, npx), ey = cmulc_n(m[1], py, npy), ez = cmulc_n(m[2], pz, npz);
+  const C2 bx = cmulc_n(m[3], pyz, npyz), by = cmulc_n(m[4], pxz, npxz), bz = cmulc_n(m[5], pxy, npxy);
+  const float2 cc = bcast<float2>(P.cc);
+  // K x B, K x E, K.B
+  const C2 kbx = cross1(Ky, bz, nKz, by), kby = cross1(Kz, bx, nKx, bz), kbz = cross1(Kx, by, nKy, bx);
+  const C2 kex = cross1(Ky, ez, nKz, ey), key = cross1(Kz, ex, nKx, ez), kez = cross1(Kx, ey, nKy, ex);
+  const C2 kdb = dot3(Kx, bx, Ky, by, Kz, bz);
+  const float2 x1x = mul2(q.x1, Kx), x1y = mul2(q.x1, Ky), x1z = mul2(q.x1, Kz);
+  const float2 S = q.s, nS = neg2(q.s), csw = mul2(cc, q.s), ncsw = neg2(csw), C = q.c;
+  // B' = C B + X1 K (K.B) - i Sw K x E      (-i S (u + i v) = S v - i S u)
+  auto bnew = [&](C2 b, float2 x1k, C2 ke) {
+    return C2{fma2(S, ke.y, fma2(x1k, kdb.x, mul2(C, b.x))), fma2(nS, ke.x, fma2(x1k, kdb.y, mul2(C, b.y)))};
+  };
+  C2 nbx = bnew(bx, x1x, kex), nby = bnew(by, x1y, key), nbz = bnew(bz, x1z, kez);
+  // + i csw K x B                            (i c (u + i v) = -c v + i c u)
+  auto ecurl = [&](C2 e, C2 kb) { return C2{fma2(ncsw, kb.y, mul2(C, e.x)), fma2(csw, kb.x, mul2(C, e.y))}; };
+  C2 nex = ecurl(ex, kbx), ney = ecurl(ey, kby), nez = ecurl(ez, kbz);
+  if (FORM == kRhoForm || FORM == kJForm) {
+    constexpr int J0 = FORM == kRhoForm ? 7 : 6;
+    const C2 jx = cmulc_n(m[J0], px, npx), jy = cmulc_n(m[J0 + 1], py, npy), jz = cmulc_n(m[J0 + 2], pz, npz);
+    const float2 ieps = bcast<float2>(P.ieps);
+    const float2 na = neg2(mul2(q.s, ieps));                       // -Sw/eps0
+    const C2 kdj = dot3(Kx, jx, Ky, jy, Kz, jz);
+    // B' += i (X1/c^2) K x J / eps0
+    const float2 x2 = mul2(q.x1, bcast<float2>(P.icce)), nx2 = neg2(x2);
+    const C2 kjx = cross1(Ky, jz, nKz, jy), kjy = cross1(Kz, jx, nKx, jz), kjz = cross1(Kx, jy, nKy, jx);
+    auto bj = [&](C2 b, C2 kj) { return C2{fma2(nx2, kj.y, b.x), fma2(x2, kj.x, b.y)}; };
+    nbx = bj(nbx, kjx);
+    nby = bj(nby, kjy);
+    nbz = bj(nbz, kjz);
+    if (FORM == kRhoForm) {
+      // rho' = rho - i dt K.J ; E' += -Sw J/eps0 + i K (Y1 rho' + Y2 rho)/eps0
+      const C2 rho = m[6];
+      const float2 dt = bcast<float2>(P.dt), ndt = neg2(dt);
+      const C2 rhon{fma2(dt, kdj.y, rho.x), fma2(ndt, kdj.x, rho.y)};
+      const float2 y1 = mul2(q.x3, bcast<float2>(P.idt));
+      const float2 y2 = neg2(q.x1 + y1);
+      const C2 t{fma2(y2, rho.x, mul2(y1, rhon.x)), fma2(y2, rho.y, mul2(y1, rhon.y))};   // g = i t
+      const float2 kix = mul2(Kx, ieps), kiy = mul2(Ky, ieps), kiz = mul2(Kz, ieps);
+      auto er = [&](C2 e, C2 j, float2 ki) {
+        return C2{fma2(neg2(ki), t.y, fma2(na, j.x, e.x)), fma2(ki, t.x, fma2(na, j.y, e.y))};
+      };
+      nex = er(nex, jx, kix);
+      ney = er(ney, jy, kiy);
+      nez = er(nez, jz, kiz);
+      m[6] = rhon;
+    } else {
+      // E' += X1 K (K.E) - Sw J/eps0 + X3 K (K.J)/eps0
+      const C2 kde = dot3(Kx, ex, Ky, ey, Kz, ez);
+      const float2 b = mul2(q.x3, ieps);
+      const float2 bkx = mul2(b, Kx), bky = mul2(b, Ky), bkz = mul2(b, Kz);
+      auto ej = [&](C2 e, C2 j, float2 x1k, float2 bk) {
+        return C2{fma2(bk, kdj.x, fma2(na, j.x, fma2(x1k, kde.x, e.x))),
+                  fma2(bk, kdj.y, fma2(na, j.y, fma2(x1k, kde.y, e.y)))};
+      };
+      nex = ej(nex, jx, x1x, bkx);
+      ney = ej(ney, jy, x1y, bky);
+      nez = ej(nez, jz, x1z, bkz);
+    }
+  } else {
+    // E' += X1 K (K.E)
+    const C2 kde = dot3(Kx, ex, Ky, ey, Kz, ez);
+    auto eg = [&](C2 e, float2 x1k) { return C2{fma2(x1k, kde.x, e.x), fma2(x1k, kde.y, e.y)}; };
+    nex = eg(nex, x1x);
+    ney = eg(ney, x1y);
+    nez = eg(nez, x1z);
+  }
+  // back to the staggered sample positions
+  m[0] = cmul_n(nex, px, npx);
+  m[1] = cmul_n(ney, py, npy);
+  m[2] = cmul_n(nez, pz, npz);
+  m[3] = cmul_n(nbx, pyz, npyz);
+  m[4] = cmul_n(nby, pxz, npxz);
+  m[5] = cmul_n(nbz, pxy, npxy);
 }
 
 // Modes k and k + NZ/2 of columns A and B, with the last radix-2 stage of the
 // forward z FFT before the update and the first stage of the inverse after
-// it.  lo / hi: slot 0 of the rows k and NZ/2 + k.  For slots f < nft those
+// it.  lo / hi: slot 0 of the rows k (re-first order) and NZ/2 + k (im-first
+// order).  For slots f < nft those
 // rows hold the half-length DFTs of the even and odd z samples, E[k] and
 // O[k]; with w = exp(-2 pi i k / NZ) the modes are
 //   X[k] = E[k] + w O[k],   X[k + NZ/2] = E[k] - w O[k],
@@ -261,7 +360,7 @@ __device__ __forceinline__ void update_pair_z2(float2* lo, float2* hi, int fs, c
   C2 a[FIN], b[FIN];
 #pragma unroll
   for (int f = 0; f < FIN; ++f) {
-    const C2 e = load2(lo + f * fs), o = load2(hi + f * fs);
+    const C2 e = load2<false>(lo + f * fs), o = load2<true>(hi + f * fs);
     if (f < nft) {
       const C2 t = cmul(o, W);
       a[f] = e + t;
@@ -273,18 +372,16 @@ __device__ __forceinline__ void update_pair_z2(float2* lo, float2* hi, int fs, c
   }
   {
     const ModeZ2 z = mode_z2(m, k, sh, P);
-    update_core<float2, C2, FORM>(a, m.Kx, m.Ky, make_float2(z.kz, z.kz), m.px, m.py, pack2(z.pz, z.pz), m.pxy, z.q,
-                                  P);
+    update_core2<FORM>(a, m.Kx, m.Ky, make_float2(z.kz, z.kz), m.px, m.py, pack2(z.pz, z.pz), m.pxy, z.q, P);
   }
   {
     const ModeZ2 z = mode_z2(m, k + NZ / 2, sh, P);
-    update_core<float2, C2, FORM>(b, m.Kx, m.Ky, make_float2(z.kz, z.kz), m.px, m.py, pack2(z.pz, z.pz), m.pxy, z.q,
-                                  P);
+    update_core2<FORM>(b, m.Kx, m.Ky, make_float2(z.kz, z.kz), m.px, m.py, pack2(z.pz, z.pz), m.pxy, z.q, P);
   }
 #pragma unroll
   for (int f = 0; f < FOUT; ++f) {
-    store2(lo + f * fs, a[f] + b[f]);
-    store2(hi + f * fs, cmulc(a[f] - b[f], W));
+    store2<false>(lo + f * fs, a[f] + b[f]);
+    store2<true>(hi + f * fs, cmulc(a[f] - b[f], W));
   }
 }
 

@@ -347,13 +347,28 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
   // half-length forward DFT of the member's samples into row half * H + k;
   // slots >= nft already hold their z spectrum (a cached constant current) in
   // natural z order and are stored as they are.
+  // Shared-memory layout of a row: per slot, per column pair (2j, 2j + 1),
+  // the 16 bytes (re 2j, re 2j+1, im 2j, im 2j+1) in rows [0, H) and
+  // (im 2j, im 2j+1, re 2j, re 2j+1) in rows [H, NZ): the update threads load
+  // the real and imaginary parts of two columns as register pairs, and the
+  // two halves of a warp storing rows k and H + k hit disjoint banks.
+  float* bw = reinterpret_cast<float*>(buf);
+  const int q0 = 2 * s * TX + 4 * (t >> 1) + (t & 1);      // word of re in a re-first row
   if (s < nft) {
     Dft<float, H, -1>::run(v);
+    const int re = q0 + 2 * half, im = q0 + 2 - 2 * half;
 #pragma unroll
-    for (int k = 0; k < H; ++k) buf[(half * H + k) * NP + col] = v[k];
+    for (int k = 0; k < H; ++k) {
+      bw[(half * H + k) * 2 * NP + re] = v[k].x;
+      bw[(half * H + k) * 2 * NP + im] = v[k].y;
+    }
   } else if (s < FIN) {
 #pragma unroll
-    for (int m = 0; m < H; ++m) buf[(2 * m + half) * NP + col] = v[m];
+    for (int m = 0; m < H; ++m) {
+      const int z = 2 * m + half, sw = 2 * m >= H ? 2 : 0;
+      bw[z * 2 * NP + q0 + sw] = v[m].x;
+      bw[z * 2 * NP + q0 + 2 - sw] = v[m].y;
+    }
   }
   __syncthreads();
   // k-space update of the column pair (2 tp, 2 tp + 1), tp = tid % (TX/2),
@@ -387,9 +402,13 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
   // the output slots; threads of the remaining slots repeat the last output
   // slot and store nothing.  Only interior z planes are stored: the inverse
   // plane pass reads no others.
-  const int so = s < FOUT ? s : FOUT - 1;
+  {
+    const int so = s < FOUT ? s : FOUT - 1;
+    const int qo = 2 * so * TX + 4 * (t >> 1) + (t & 1);
+    const int re = qo + 2 * half, im = qo + 2 - 2 * half;
 #pragma unroll
-  for (int k = 0; k < H; ++k) v[k] = buf[(half * H + k) * NP + so * TX + t];
+    for (int k = 0; k < H; ++k) v[k] = make_float2(bw[(half * H + k) * 2 * NP + re], bw[(half * H + k) * 2 * NP + im]);
+  }
   Dft<float, H, 1>::run(v);
   if (live && s < FOUT) {
     const int zlo = bx.ng_lo[2], zhi = NZ - bx.ng_hi[2];
