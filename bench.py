@@ -197,7 +197,7 @@ def build_layout(name):
     return I.hybrid_layout(w["global_n"], w["nsub"], w["ng"], w["p"])
 
 
-def kernel_bytes(layout, s=4, fin=6, fout=6, fused=True):
+def kernel_bytes(layout, s=4, fin=6, fout=6, fused=True, guard_frac=1.0):
     """Compulsory bytes of one launch of every kernel kind (each kernel reads
     its inputs once and writes its outputs once).  Kinds: forward x(+y),
     generic y forward, z + update, generic y inverse, inverse (y+)x, exchange.
@@ -205,7 +205,9 @@ def kernel_bytes(layout, s=4, fin=6, fout=6, fused=True):
     4 carry the plane kernels' bytes and kinds 1 and 3 do not launch; its z
     kernel stores the interior z planes only, and with `fused` the inverse
     plane kernel also writes the guard cells its plane feeds (the exchange
-    kind then does not launch)."""
+    kind then does not launch) -- in the fraction `guard_frac` of its launches
+    (the deferred exchange stores them in the last step of a push only; the
+    forward pass reads every padded cell either way)."""
     C = sum(b.cells for b in layout.boxes)
     M = sum((b.n[0] // 2 + 1) * b.n[1] * b.n[2] for b in layout.boxes)
     Mz = sum((b.n[0] // 2 + 1) * b.n[1] * b.interior[2] for b in layout.boxes)
@@ -223,7 +225,7 @@ def kernel_bytes(layout, s=4, fin=6, fout=6, fused=True):
                      0,
                      fin * M * c + fout * Mz * c,       # z kernel: all planes in, interior z out
                      0,
-                     fout * (Mz * c + I_ * s + (G * s if fused else 0)),   # plane inverse
+                     fout * (Mz * c + I_ * s + (guard_frac * G * s if fused else 0)),   # plane inverse
                      fout * 2 * G * s]}
 
 
@@ -385,8 +387,7 @@ def run_gpu(args):
     plan.sync()
     stream = plan.stream
 
-    for _ in range(args.warmup):
-        plan.push(fields, None, 1)
+    plan.push(fields, None, args.warmup)
     plan.sync()
     A.psatd_plan_set_timing(plan.handle, True)
     A.psatd_plan_kernel_times(plan.handle)   # discard warm-up records
@@ -396,13 +397,14 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    launches = 0
+    # the K timed steps are one push (with the deferred exchange, each step's
+    # guard exchange is done by the next step's forward gather; the last step
+    # stores the guards)
     with torch.cuda.stream(stream):
         e0.record(stream)
-        for _ in range(args.steps):
-            plan.push(fields, None, 1)
-            launches += plan.last_launch_count()
+        plan.push(fields, None, args.steps)
         e1.record(stream)
+    launches = plan.last_launch_count()
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
@@ -414,7 +416,8 @@ def run_gpu(args):
     interior = lay.interior_cells
     value = total_units(interior * args.steps, world) / (ms_max / 1e3)
     peak, peak_src = measured_peaks()
-    kb = kernel_bytes(lay, fused=kn[5] == 0)["fast" if plan.fast_boxes == len(lay.boxes) else "generic"]
+    gfrac = 1.0 / args.steps if plan.deferred_exchange else 1.0
+    kb = kernel_bytes(lay, fused=kn[5] == 0, guard_frac=gfrac)["fast" if plan.fast_boxes == len(lay.boxes) else "generic"]
     avg = [kms[i] / kn[i] if kn[i] else 0.0 for i in range(len(kms))]
     dom = max(range(len(avg)), key=lambda i: avg[i])
     ach = kb[dom] / (avg[dom] / 1e3) / 1e9
@@ -434,7 +437,9 @@ def run_gpu(args):
                    "interior_cells": interior, "padded_cells": lay.cells,
                    "l2": "inputs larger than L2 (%.1f GB of fields)" % (6 * lay.cells * 4 / 1e9),
                    "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "fast_boxes": plan.fast_boxes},
+                   "fast_boxes": plan.fast_boxes,
+                   "guard_exchange": "deferred into the next step's forward gather; guards stored by the last step"
+                                     if plan.deferred_exchange else "stored every step"},
         "roofline": {"bound": "hbm", "kernel": A.KERNEL_NAMES[dom], "achieved": ach,
                      "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": kb[dom], "avg_launch_ms": avg[dom],

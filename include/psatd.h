@@ -93,6 +93,14 @@ typedef enum {
                                   /* resident form serves every plane-eligible box,  */
                                   /* else pencil kernels; all families agree to      */
                                   /* rounding                                        */
+#define PSATD_EAGER_EXCHANGE 0x100u /* store the guard cells in every step.  Without */
+                                  /* it, plans whose boxes all run on the register  */
+                                  /* plane kernels defer each step's guard exchange */
+                                  /* into the next step's forward pass, which reads */
+                                  /* every guard cell from the interior cell owning */
+                                  /* it (the value the exchange would store), and   */
+                                  /* only the last step of a push stores the guards */
+                                  /* (paper Fig. 1, step (ii)); results are equal   */
 
 /* One FFT box.  n[] counts cells including guards; each n[d] must be even,
  * 5-smooth (2^a 3^b 5^c), n[0] in [4, 1024], n[1], n[2] in [4, 512].
@@ -193,7 +201,8 @@ psatd_status psatd_guard_exchange(psatd_plan* plan, const psatd_fields* fields,
 
 /* Advance `nsteps` >= 0 steps of S1..S4 in place on `fields` (and rho).
  * Guards of E, B must be consistent on entry (psatd_guard_exchange) and are
- * consistent on return.  Asynchronous on `stream`. */
+ * consistent on return; between the steps of one call they may stay stale
+ * in memory (PSATD_EAGER_EXCHANGE).  Asynchronous on `stream`. */
 psatd_status psatd_push(psatd_plan* plan, const psatd_fields* fields,
                         const psatd_sources* src, int32_t nsteps, void* stream);
 
@@ -280,6 +289,11 @@ int32_t psatd_plan_fast_boxes(const psatd_plan* plan);
  * kernels.  -1 for a NULL plan.  No counterpart in the paper (a property of
  * this implementation's kernel selection). */
 int32_t psatd_plan_pencil_boxes(const psatd_plan* plan);
+
+/* 1 when the plan defers each step's guard exchange into the next step's
+ * forward pass (see PSATD_EAGER_EXCHANGE), 0 when every step stores its
+ * guards, -1 for a NULL plan. */
+int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
 
 /* Kernel kinds reported by psatd_plan_kernel_times. */
 #define PSATD_KERNEL_KINDS 6 /* 0 fwd_x, 1 col forward, 2 z_update, 3 col inverse, 4 inv_x, 5 exchange */

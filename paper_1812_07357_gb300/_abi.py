@@ -35,6 +35,7 @@ PSATD_PENCIL_KERNELS = 0x20
 PSATD_J_CONSTANT = 0x4
 PSATD_PLANE_KERNELS = 0x40
 PSATD_NODAL = 0x80
+PSATD_EAGER_EXCHANGE = 0x100
 
 
 class psatd_box(Structure):
@@ -92,6 +93,7 @@ _SIGS = {
     "psatd_plan_kernel_times": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32]),
     "psatd_plan_fast_boxes": (c_int32, [c_void_p]),
     "psatd_plan_pencil_boxes": (c_int32, [c_void_p]),
+    "psatd_plan_deferred_exchange": (c_int32, [c_void_p]),
     "psatd_push_box_static": (c_int32, [POINTER(c_int32), c_int32, POINTER(c_double), c_double,
                                         c_double, POINTER(psatd_fields), c_int32, c_void_p]),
     "psatd_coupling_blocks": (c_int32, [POINTER(psatd_plan_desc), c_int32, POINTER(psatd_box), c_int32,
@@ -307,3 +309,7 @@ def psatd_plan_fast_boxes(plan: int) -> int:
 
 def psatd_plan_pencil_boxes(plan: int) -> int:
     return int(load().psatd_plan_pencil_boxes(c_void_p(plan)))
+
+
+def psatd_plan_deferred_exchange(plan: int) -> int:
+    return int(load().psatd_plan_deferred_exchange(c_void_p(plan)))

@@ -68,7 +68,7 @@ Err validate(const psatd_plan_desc* d) {
     if (!(d->dx[a] > 0.0) || !std::isfinite(d->dx[a])) return {PSATD_ERR_INVALID_ARG, "dx must be > 0"};
   const uint32_t known =
       PSATD_VACUUM | PSATD_RHO_CONTINUITY | PSATD_J_CONSTANT | PSATD_NO_GRAPH | PSATD_GENERIC_KERNELS |
-      PSATD_PENCIL_KERNELS | PSATD_PLANE_KERNELS | PSATD_NODAL;
+      PSATD_PENCIL_KERNELS | PSATD_PLANE_KERNELS | PSATD_NODAL | PSATD_EAGER_EXCHANGE;
   if (d->flags & ~known) return {PSATD_ERR_INVALID_ARG, "unknown flag bits"};
   if ((d->flags & PSATD_VACUUM) && (d->flags & PSATD_RHO_CONTINUITY))
     return {PSATD_ERR_INVALID_ARG, "PSATD_VACUUM and PSATD_RHO_CONTINUITY exclude each other"};
@@ -318,6 +318,10 @@ struct psatd_plan {
   std::vector<XTile> step_tiles;                              // blocks not fused into the inverse
   std::vector<int> seg_start;                                 // fused exchange, CSR per plane_inv
   std::vector<GuardSeg> segs;
+  bool deferred = false;                                      // deferred exchange (gather in S1)
+  std::vector<int> gseg_start;                                // its CSR per plane_fwd
+  std::vector<GatherSeg> gsegs;
+  std::vector<GatherGrid> ggrid;                              // or one 3 x 3 grid per plane_fwd
 
   int64_t field_total = 0;  // elements per field buffer
   int64_t spec_total = 0;   // complex elements per spectrum slot
@@ -345,6 +349,9 @@ struct psatd_plan {
   XTile* d_step_tiles = nullptr;
   int* d_seg_start = nullptr;
   GuardSeg* d_segs = nullptr;
+  int* d_gseg_start = nullptr;
+  GatherSeg* d_gsegs = nullptr;
+  GatherGrid* d_ggrid = nullptr;
   void *d_rpool = nullptr, *d_cpool = nullptr, *d_coef = nullptr;
   void* d_ws = nullptr;
   size_t plan_bytes = 0;
@@ -353,12 +360,13 @@ struct psatd_plan {
   cudaStream_t last_stream = nullptr;
   int64_t last_launches = 0;
 
-  // multi-step pushes replay one captured step (CUDA graph) per field set
-  cudaGraphExec_t graph_exec = nullptr;
+  // multi-step pushes replay captured steps (CUDA graphs) per field set, one
+  // per step variant: 2 * (forward gathers) + (inverse writes the guards)
+  cudaGraphExec_t graph_exec[4] = {};
   cudaStream_t cap_stream = nullptr;   // capture only; never executes work
   FieldPtrs graph_fp{};
   int graph_nf = 0;
-  int64_t graph_launches = 0;
+  int64_t graph_launches[4] = {};
 
   // per-kernel timing (diagnostics)
   bool timing = false;
@@ -382,7 +390,8 @@ struct psatd_plan {
 
   ~psatd_plan() {
     cudaDeviceSynchronize();
-    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    for (cudaGraphExec_t g : graph_exec)
+      if (g) cudaGraphExecDestroy(g);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     for (void* p : allocs) cudaFree(p);
     for (auto& r : recs) {
@@ -444,6 +453,129 @@ cudaError_t dalloc(psatd_plan* p, size_t bytes, void** d) {
   return cudaSuccess;
 }
 
+
+// Deferred guard exchange.  When every box runs on the register plane kernels
+// (so every guard block is fed by an inverse plane pass), a step need not
+// store its guard cells: the next step's forward plane pass reads every
+// guard cell straight from the interior cell that owns it, which is the
+// value the exchange would have stored there, and only the last step of a
+// push stores the guards.  Per forward plane job (box b, plane z): the
+// rectangles of blocks that feed b's plane z, then the cells no block feeds
+// (interior, and guards outside a non-periodic domain) from b itself.
+static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint32_t flags) {
+  P->deferred = false;
+  if ((flags & PSATD_EAGER_EXCHANGE) || P->reg_code < 0 || P->plane_fwd.empty() || P->segs.empty() ||
+      !P->step_tiles.empty() || !P->g_rows.empty() || !P->pen_rows.empty())
+    return;
+  for (char f : box_fast)
+    if (!f) return;
+  const int nb = (int)P->boxes.size();
+  std::vector<std::vector<int>> by_dst(nb);
+  for (int i = 0; i < (int)P->blocks.size(); ++i)
+    if (P->blocks[i].src_box >= 0) by_dst[P->blocks[i].dst_box].push_back(i);
+  const int v16 = 16 / (int)P->rsize;
+  std::vector<GatherSeg> out;
+  std::vector<int> start(P->plane_fwd.size() + 1, 0);
+  auto emit = [&](int64_t src_off, int spitch, int dy, int dx, int ny, int nx) {
+    GatherSeg g{};
+    g.src_off = src_off;
+    g.spitch = spitch;
+    g.dy = dy;
+    g.dx = dx;
+    g.ny = ny;
+    g.nx = nx;
+    g.vec = nx % v16 == 0 && dx % v16 == 0 && src_off % v16 == 0 && spitch % v16 == 0;
+    out.push_back(g);
+  };
+  for (size_t j = 0; j < P->plane_fwd.size(); ++j) {
+    const int b = P->plane_fwd[j].x, z = P->plane_fwd[j].y;
+    const psatd_box& B = P->boxes[b];
+    const int n0 = B.n[0], n1 = B.n[1];
+    // covered[y]: x intervals of row y fed by a block
+    std::vector<std::vector<std::pair<int, int>>> covered(n1);
+    for (int bi : by_dst[b]) {
+      const CopyBlk& c = P->blocks[bi];
+      if (z < c.dst_lo[2] || z >= c.dst_lo[2] + c.ext[2]) continue;
+      const psatd_box& S = P->boxes[c.src_box];
+      const int64_t off = P->hboxes[c.src_box].foff +
+                          ((int64_t)(c.src_lo[2] + z - c.dst_lo[2]) * S.n[1] + c.src_lo[1]) * S.n[0] + c.src_lo[0];
+      emit(off, S.n[0], c.dst_lo[1], c.dst_lo[0], c.ext[1], c.ext[0]);
+      for (int y = c.dst_lo[1]; y < c.dst_lo[1] + c.ext[1]; ++y) covered[y].push_back({c.dst_lo[0], c.dst_lo[0] + c.ext[0]});
+    }
+    // the rest of each row from the box itself; equal consecutive rows merge
+    auto gaps = [&](int y) {
+      auto iv = covered[y];
+      std::sort(iv.begin(), iv.end());
+      std::vector<std::pair<int, int>> g;
+      int x = 0;
+      for (const auto& v : iv) {
+        if (v.first > x) g.push_back({x, v.first});
+        x = std::max(x, v.second);
+      }
+      if (x < n0) g.push_back({x, n0});
+      return g;
+    };
+    const int64_t base = P->hboxes[b].foff + (int64_t)z * n1 * n0;
+    int y0 = 0;
+    std::vector<std::pair<int, int>> cur = gaps(0);
+    for (int y = 1; y <= n1; ++y) {
+      std::vector<std::pair<int, int>> nx = y < n1 ? gaps(y) : std::vector<std::pair<int, int>>{{-1, -1}};
+      if (y < n1 && nx == cur) continue;
+      for (const auto& g : cur) emit(base + (int64_t)y0 * n0 + g.first, n0, y0, g.first, y - y0, g.second - g.first);
+      y0 = y;
+      cur.swap(nx);
+    }
+    start[j + 1] = (int)out.size();
+  }
+  P->gseg_start.swap(start);
+  P->gsegs.swap(out);
+  P->deferred = true;
+  // the 3 x 3 grid form of every plane, when each one has it
+  std::vector<GatherGrid> grids(P->plane_fwd.size());
+  for (size_t j = 0; j < P->plane_fwd.size(); ++j) {
+    const psatd_box& B = P->boxes[P->plane_fwd[j].x];
+    std::vector<int> xs{0, B.n[0]}, ys{0, B.n[1]};
+    bool vec = true;
+    for (int i = P->gseg_start[j]; i < P->gseg_start[j + 1]; ++i) {
+      const GatherSeg& g = P->gsegs[i];
+      xs.push_back(g.dx);
+      xs.push_back(g.dx + g.nx);
+      ys.push_back(g.dy);
+      ys.push_back(g.dy + g.ny);
+      vec = vec && g.vec;
+    }
+    for (auto* v : {&xs, &ys}) {
+      std::sort(v->begin(), v->end());
+      v->erase(std::unique(v->begin(), v->end()), v->end());
+    }
+    if (!vec || xs.size() > 4 || ys.size() > 4) return;   // keep the rectangle lists
+    while (xs.size() < 4) xs.push_back(B.n[0]);
+    while (ys.size() < 4) ys.push_back(B.n[1]);
+    GatherGrid gg{};
+    gg.x1 = xs[1];
+    gg.x2 = xs[2];
+    gg.y1 = ys[1];
+    gg.y2 = ys[2];
+    for (int iy = 0; iy < 3; ++iy)
+      for (int ix = 0; ix < 3; ++ix) {
+        if (ys[iy] == ys[iy + 1] || xs[ix] == xs[ix + 1]) continue;   // empty cell
+        bool found = false;
+        for (int i = P->gseg_start[j]; i < P->gseg_start[j + 1] && !found; ++i) {
+          const GatherSeg& g = P->gsegs[i];
+          if (g.dy <= ys[iy] && ys[iy + 1] <= g.dy + g.ny && g.dx <= xs[ix] && xs[ix + 1] <= g.dx + g.nx) {
+            gg.base[3 * iy + ix] = g.src_off + (int64_t)(ys[iy] - g.dy) * g.spitch + (xs[ix] - g.dx);
+            gg.pitch[3 * iy + ix] = g.spitch;
+            found = true;
+          }
+        }
+        if (!found) return;
+      }
+    grids[j] = gg;
+  }
+  P->ggrid.swap(grids);
+  P->gsegs.clear();
+  P->gseg_start.clear();
+}
 
 psatd_status build(psatd_plan* P, cudaStream_t st) {
   const psatd_plan_desc& d = P->desc;
@@ -758,6 +890,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     P->seg_start[i + 1] = P->seg_start[i] + (int)per_plane[i].size();
     P->segs.insert(P->segs.end(), per_plane[i].begin(), per_plane[i].end());
   }
+  build_gather(P, box_fast, d.flags);
   for (int i = 0; i < (int)P->blocks.size(); ++i) {
     const CopyBlk& c = P->blocks[i];
     const bool fused = c.src_box >= 0 && box_fast[c.src_box];
@@ -801,6 +934,9 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   CK(P, upload(P, P->step_tiles, &P->d_step_tiles));
   CK(P, upload(P, P->seg_start, &P->d_seg_start));
   CK(P, upload(P, P->segs, &P->d_segs));
+  CK(P, upload(P, P->gseg_start, &P->d_gseg_start));
+  CK(P, upload(P, P->gsegs, &P->d_gsegs));
+  CK(P, upload(P, P->ggrid, &P->d_ggrid));
   CK(P, dalloc(P, (size_t)rtot * P->rsize, &P->d_rpool));
   CK(P, dalloc(P, (size_t)ctot * P->csize, &P->d_cpool));
   CK(P, dalloc(P, (size_t)qtot * 4 * P->rsize, &P->d_coef));
@@ -1203,14 +1339,15 @@ psatd_status psatd_guard_exchange(psatd_plan* P, const psatd_fields* f, const ps
 // S1 along x and y of the field slots fp.p[0..nf) into spectrum slots
 // spec + f * spec_total, on every kernel family; adds the launches.
 static psatd_status forward_xy(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, int nf, void* spec,
-                               cudaStream_t st, int64_t* launches_out) {
+                               cudaStream_t st, int64_t* launches_out, bool gather = false) {
   const int64_t S = P->spec_total;
   int64_t launches = 0;
   // fast boxes: one plane kernel; generic: x rows, y columns; pencil: x rows, y tiles
   if (!P->plane_fwd.empty() && P->reg_code >= 0) {
     CK(P, timed(P, 0, st, [&] {
          return launch_plane_fwd_reg(P->reg_code, D, fp, nf, spec, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
-                                     st);
+                                     gather && !P->gseg_start.empty() ? P->d_gseg_start : nullptr, P->d_gsegs,
+                                     gather && !P->ggrid.empty() ? P->d_ggrid : nullptr, fields_out(P->form), st);
        }));
     ++launches;
   } else if (!P->plane_fwd.empty()) {
@@ -1272,14 +1409,16 @@ static psatd_status transform_current(psatd_plan* P, const DevPlan& D, const Fie
 }
 
 // One step S1..S4 of every box on `st`; adds the launches to *launches.
+// gather: the forward pass reads guard cells from their owners (deferred
+// exchange); guards: the inverse pass stores the guard cells.
 static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, cudaStream_t st,
-                              int64_t* launches_out) {
+                              int64_t* launches_out, bool gather = false, bool guards = true) {
   const int FOUT = fields_out(P->form), NFT = step_slots(P);
   const int64_t S = P->spec_total;
   int64_t launches = 0;
   // S1: forward x+y of the slots transformed every step
   {
-    const psatd_status r = forward_xy(P, D, fp, NFT, P->d_ws, st, &launches);
+    const psatd_status r = forward_xy(P, D, fp, NFT, P->d_ws, st, &launches, gather);
     if (r != PSATD_OK) return r;
   }
   // S1 (z) + S2 + S3 (z)
@@ -1313,8 +1452,8 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
   if (!P->plane_inv.empty() && P->reg_code >= 0) {
     CK(P, timed(P, 4, st, [&] {
          return launch_plane_inv_reg(P->reg_code, D, fp, FOUT, P->d_ws, S, P->d_plane_inv,
-                                     (int64_t)P->plane_inv.size(), P->segs.empty() ? nullptr : P->d_seg_start,
-                                     P->d_segs, st);
+                                     (int64_t)P->plane_inv.size(),
+                                     P->segs.empty() || !guards ? nullptr : P->d_seg_start, P->d_segs, st);
        }));
     ++launches;
   } else if (!P->plane_inv.empty()) {
@@ -1359,34 +1498,41 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
   return PSATD_OK;
 }
 
-// Capture one step into a CUDA graph for the field set fp (kept until the
-// field pointers change).  The capture runs on a plan-owned stream (nothing
-// executes during capture), so the graph can then be launched on any stream,
-// the legacy default stream included.  Returns false, with nothing captured,
-// when the caller's stream is itself being captured or capture fails; the
-// push then launches the kernels directly.
-static bool step_graph(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, int nf, cudaStream_t st) {
+// Capture one step of variant v (2 * gather + guards, see push_step) into a
+// CUDA graph for the field set fp (kept until the field pointers change).
+// The capture runs on a plan-owned stream (nothing executes during capture),
+// so the graph can then be launched on any stream, the legacy default stream
+// included.  Returns false, with nothing captured, when the caller's stream
+// is itself being captured or capture fails; the push then launches the
+// kernels directly.
+static bool step_graph(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, int nf, cudaStream_t st, int v) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
     return false;
   }
-  if (P->graph_exec && nf == P->graph_nf && std::memcmp(&fp, &P->graph_fp, sizeof(FieldPtrs)) == 0) return true;
+  const bool same = nf == P->graph_nf && std::memcmp(&fp, &P->graph_fp, sizeof(FieldPtrs)) == 0;
+  if (same && P->graph_exec[v]) return true;
+  if (!same) {
+    for (cudaGraphExec_t& g : P->graph_exec)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+    P->graph_fp = fp;
+    P->graph_nf = nf;
+  }
   if (!P->cap_stream && cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     P->cap_stream = nullptr;
     cudaGetLastError();
     return false;
-  }
-  if (P->graph_exec) {
-    cudaGraphExecDestroy(P->graph_exec);
-    P->graph_exec = nullptr;
   }
   if (cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
   int64_t n = 0;
-  const psatd_status r = push_step(P, D, fp, P->cap_stream, &n);
+  const psatd_status r = push_step(P, D, fp, P->cap_stream, &n, (v & 2) != 0, (v & 1) != 0);
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(P->cap_stream, &g);
   cudaGraphExec_t x = nullptr;
@@ -1397,10 +1543,8 @@ static bool step_graph(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, int
     if (x) cudaGraphExecDestroy(x);
     return false;
   }
-  P->graph_exec = x;
-  P->graph_fp = fp;
-  P->graph_nf = nf;
-  P->graph_launches = n;
+  P->graph_exec[v] = x;
+  P->graph_launches[v] = n;
   return true;
 }
 
@@ -1421,13 +1565,18 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
       r = transform_current(P, D, fp, st, &launches);
       if (r != PSATD_OK) return r;
     }
-    const bool graph = nsteps > 1 && !(P->desc.flags & PSATD_NO_GRAPH) && !P->timing && step_graph(P, D, fp, nf, st);
-    if (graph) {
-      for (int step = 0; step < nsteps; ++step) CK(P, cudaGraphLaunch(P->graph_exec, st));
-      launches += P->graph_launches * nsteps;
-    } else {
-      for (int step = 0; step < nsteps; ++step) {
-        r = push_step(P, D, fp, st, &launches);
+    // with the deferred exchange the first step reads the caller's guards,
+    // later ones gather them, and the last one stores them
+    const bool use_graph = nsteps > 1 && !(P->desc.flags & PSATD_NO_GRAPH) && !P->timing;
+    for (int step = 0; step < nsteps; ++step) {
+      const bool gather = P->deferred && step > 0;
+      const bool guards = !P->deferred || step == nsteps - 1;
+      const int v = 2 * gather + guards;
+      if (use_graph && step_graph(P, D, fp, nf, st, v)) {
+        CK(P, cudaGraphLaunch(P->graph_exec[v], st));
+        launches += P->graph_launches[v];
+      } else {
+        r = push_step(P, D, fp, st, &launches, gather, guards);
         if (r != PSATD_OK) return r;
       }
     }
@@ -1503,6 +1652,8 @@ int64_t psatd_last_launch_count(const psatd_plan* p) { return p ? p->last_launch
 int32_t psatd_plan_fast_boxes(const psatd_plan* p) { return p ? p->fast_boxes : -1; }
 
 int32_t psatd_plan_pencil_boxes(const psatd_plan* p) { return p ? p->pen_boxes : -1; }
+
+int32_t psatd_plan_deferred_exchange(const psatd_plan* p) { return p ? (p->deferred ? 1 : 0) : -1; }
 
 psatd_status psatd_plan_set_timing(psatd_plan* P, int32_t enable) {
   if (!P) return PSATD_ERR_INVALID_ARG;

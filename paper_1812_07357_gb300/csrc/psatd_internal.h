@@ -121,6 +121,25 @@ struct GuardSeg {
   int32_t vec, pad;
 };
 
+// Deferred guard exchange: rows [dy, dy + ny) x columns [dx, dx + nx) of a
+// forward plane buffer are read from the field elements src_off + r * spitch
+// + c (the owning box's interior, or the box's own cells).
+struct GatherSeg {
+  int64_t src_off;
+  int32_t spitch, dy, dx, ny, nx, vec;
+};
+
+// The same gather when the plane splits into at most 3 x 3 rectangles at
+// columns x1 <= x2 and rows y1 <= y2 (guard faces of a local or hybrid box),
+// every rectangle copied in 16-byte units: rectangle (iy, ix) starts at field
+// element base[3 iy + ix], row pitch pitch[3 iy + ix].
+struct alignas(16) GatherGrid {
+  int64_t base[9];
+  int32_t pitch[9];
+  int32_t x1, x2, y1, y2;
+  int32_t pad[3];
+};
+
 // Up to 10 field slots (see Form).
 struct FieldPtrs {
   void* p[10];
@@ -212,7 +231,8 @@ int reg_shape_code(int L, int n1);
 int reg_fwd_smem(int code);
 int reg_inv_smem(int code);
 cudaError_t launch_plane_fwd_reg(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
-                                 int64_t sstride, const int2* jobs, int64_t nplanes, cudaStream_t st);
+                                 int64_t sstride, const int2* jobs, int64_t nplanes, const int* gstart,
+                                 const GatherSeg* gsegs, const GatherGrid* ggrid, int ngather, cudaStream_t st);
 cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
                                  int64_t sstride, const int2* jobs, int64_t nplanes, const int* seg_start,
                                  const GuardSeg* segs, cudaStream_t st);

@@ -2,7 +2,10 @@
 // y length NY have register codelets (L, NY/2 <= 48): every 1D FFT of a
 // plane is done inside registers, so a plane costs two block barriers.
 //
-//   k_plane_fwd_reg  x: one thread per row: the packed length-L complex FFT
+//   k_plane_fwd_reg  the plane is copied in whole, or, with the deferred guard
+//                    exchange, gathered rectangle by rectangle from the cells
+//                    that own it;
+//                    x: one thread per row: the packed length-L complex FFT
 //                    (z[m] = x[2m] + i x[2m+1]) and the R2C split, both in
 //                    registers; y: two threads per column, each a length-NY/2
 //                    FFT of the even / odd rows, joined by one radix-2 step
@@ -32,10 +35,15 @@ namespace psatd {
 namespace {
 
 constexpr int kRegThreads = 128;
+constexpr int kGatherTab = 64;   // gather rectangles of a plane staged in shared memory
 
 __device__ __forceinline__ void cp16(void* s, const void* g) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp4(void* s, const void* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
 }
 __device__ __forceinline__ void cp_commit_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
@@ -117,8 +125,10 @@ __device__ __forceinline__ void pair_join_inplace(float2* v, int half, unsigned 
 
 // ---------------------------------------------------------------------------
 template <int L, int NY>
-__global__ void __launch_bounds__(kRegThreads, 4) k_plane_fwd_reg(DevPlan P, FieldPtrs F, float2* spec,
-                                                                  int64_t sstride, const int2* __restrict__ jobs) {
+__global__ void __launch_bounds__(kRegThreads, 4)
+    k_plane_fwd_reg(DevPlan P, FieldPtrs F, float2* spec, int64_t sstride, const int2* __restrict__ jobs,
+                    const int* __restrict__ gstart, const GatherSeg* __restrict__ gsegs,
+                    const GatherGrid* __restrict__ ggrid, int ngather) {
   constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0);
   static_assert(NY <= kRegThreads && 2 * HX <= kRegThreads, "one thread per row / per half column");
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -126,11 +136,67 @@ __global__ void __launch_bounds__(kRegThreads, 4) k_plane_fwd_reg(DevPlan P, Fie
   const int2 J = jobs[blockIdx.x];
   const int f = blockIdx.y;
   const BoxDev bx = P.boxes[J.x];
-  const float* g = reinterpret_cast<const float*>(F.p[f]) + bx.foff + (int64_t)J.y * NY * N0;
   constexpr int UPR = N0 / 4;
-  for (int u = threadIdx.x; u < NY * UPR; u += kRegThreads) {
-    const int r = u / UPR, x = u - r * UPR;
-    cp16(buf + r * PF + 4 * x, g + 4 * u);
+  if (ggrid && f < ngather) {
+    // deferred exchange, plane of at most 3 x 3 rectangles: thread t copies
+    // the 16-byte column t % UPR of the rows t / UPR + k * RG
+    constexpr int RG = kRegThreads / UPR;
+    __shared__ GatherGrid gg;
+    static_assert(sizeof(GatherGrid) / 4 <= kRegThreads, "one word per thread");
+    if (threadIdx.x < sizeof(GatherGrid) / 4)
+      reinterpret_cast<int*>(&gg)[threadIdx.x] = reinterpret_cast<const int*>(ggrid + blockIdx.x)[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < RG * UPR) {
+      const float* fb = reinterpret_cast<const float*>(F.p[f]);
+      const int c = threadIdx.x % UPR, rg = threadIdx.x / UPR, x = 4 * c;
+      const int ix = (x >= gg.x1) + (x >= gg.x2);
+      const int xo = x - (ix == 0 ? 0 : ix == 1 ? gg.x1 : gg.x2);
+#pragma unroll
+      for (int iy = 0; iy < 3; ++iy) {   // row bands [ylo, yhi)
+        const int ylo = iy == 0 ? 0 : iy == 1 ? gg.y1 : gg.y2;
+        const int yhi = iy == 0 ? gg.y1 : iy == 1 ? gg.y2 : NY;
+        int r = ylo + (rg - ylo % RG + RG) % RG;   // first row >= ylo with r % RG == rg
+        const int pitch = gg.pitch[3 * iy + ix];
+        const float* src = fb + gg.base[3 * iy + ix] + (int64_t)(r - ylo) * pitch + xo;
+        const int64_t sstep = (int64_t)RG * pitch;
+        for (float* dst = buf + r * PF + x; r < yhi; r += RG, src += sstep, dst += RG * PF) cp16(dst, src);
+      }
+    }
+  } else if (gstart && f < ngather) {
+    // deferred exchange: every rectangle of the plane from the cells that own
+    // it (a neighbour's interior for the guard cells); the plane's rectangle
+    // list is staged in shared memory, then all threads copy one rectangle
+    // after the other
+    __shared__ GatherSeg tab[kGatherTab];
+    const float* fb = reinterpret_cast<const float*>(F.p[f]);
+    const int s0 = gstart[blockIdx.x], ns = gstart[blockIdx.x + 1] - s0;
+    if (threadIdx.x < kGatherTab && threadIdx.x < ns) tab[threadIdx.x] = gsegs[s0 + threadIdx.x];
+    __syncthreads();
+    for (int i = 0; i < ns; ++i) {
+      const GatherSeg gs = i < kGatherTab ? tab[i] : gsegs[s0 + i];
+      const float* src = fb + gs.src_off;
+      float* dst = buf + gs.dy * PF + gs.dx;
+      if (gs.vec) {
+        const int upr = gs.nx >> 2;
+        const unsigned m = magic(upr);
+        for (int u = threadIdx.x; u < gs.ny * upr; u += kRegThreads) {
+          const int r = fdiv(u, m), c = 4 * (u - r * upr);
+          cp16(dst + r * PF + c, src + (int64_t)r * gs.spitch + c);
+        }
+      } else {
+        const unsigned m = magic(gs.nx);
+        for (int u = threadIdx.x; u < gs.ny * gs.nx; u += kRegThreads) {
+          const int r = fdiv(u, m), c = u - r * gs.nx;
+          cp4(dst + r * PF + c, src + (int64_t)r * gs.spitch + c);
+        }
+      }
+    }
+  } else {
+    const float* g = reinterpret_cast<const float*>(F.p[f]) + bx.foff + (int64_t)J.y * NY * N0;
+    for (int u = threadIdx.x; u < NY * UPR; u += kRegThreads) {
+      const int r = u / UPR, x = u - r * UPR;
+      cp16(buf + r * PF + 4 * x, g + 4 * u);
+    }
   }
   cp_commit_wait_all();
   __syncthreads();
@@ -487,13 +553,14 @@ int reg_inv_smem(int code) {
 }
 
 cudaError_t launch_plane_fwd_reg(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
-                                 int64_t sstride, const int2* jobs, int64_t nplanes, cudaStream_t st) {
+                                 int64_t sstride, const int2* jobs, int64_t nplanes, const int* gstart,
+                                 const GatherSeg* gsegs, const GatherGrid* ggrid, int ngather, cudaStream_t st) {
   if (nplanes <= 0 || nf <= 0) return cudaSuccess;
   dim3 grid((unsigned)nplanes, nf);
 #define PSATD_RL(code_, LV, NYV)                                                                        \
   if (code == code_)                                                                                   \
     k_plane_fwd_reg<LV, NYV><<<grid, kRegThreads, reg_fwd_smem(code_), st>>>(P, f, (float2*)spec, sstride, \
-                                                                           jobs);
+                                                                           jobs, gstart, gsegs, ggrid, ngather);
   PSATD_REG_SHAPES(PSATD_RL)
 #undef PSATD_RL
   return cudaGetLastError();
@@ -513,25 +580,36 @@ cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f,
   return cudaGetLastError();
 }
 
+// Dynamic shared memory limits of the register kernels: what each launch
+// asks for (the gather table of the forward kernel is static shared memory
+// on top of it); `smem` is the device's opt-in maximum.
 cudaError_t configure_reg_kernels(int smem) {
   cudaError_t e = cudaSuccess;
 #define PSATD_RC(code, LV, NYV)                                                                          \
-  {                                                                                                      \
+  if (reg_fwd_smem(code) <= smem && reg_inv_smem(code) <= smem) {                                        \
     cudaError_t r = cudaFuncSetAttribute(k_plane_fwd_reg<LV, NYV>,                                        \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);            \
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, reg_fwd_smem(code)); \
     if (r != cudaSuccess) e = r;                                                                         \
-    r = cudaFuncSetAttribute(k_plane_inv_reg<LV, NYV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    r = cudaFuncSetAttribute(k_plane_inv_reg<LV, NYV>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                             reg_inv_smem(code));                                                        \
     if (r != cudaSuccess) e = r;                                                                         \
   }
   PSATD_REG_SHAPES(PSATD_RC)
 #undef PSATD_RC
 #define PSATD_ZS(NZV)                                                                                      \
   {                                                                                                        \
-    cudaError_t r = cudaFuncSetAttribute(k_z_reg<NZV, kVacuum>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem); \
+    cudaError_t r = cudaSuccess;                                                                           \
+    if (z_reg_smem(kVacuum, NZV) <= smem)                                                                  \
+      r = cudaFuncSetAttribute(k_z_reg<NZV, kVacuum>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                               z_reg_smem(kVacuum, NZV));                                                  \
     if (r != cudaSuccess) e = r;                                                                           \
-    r = cudaFuncSetAttribute(k_z_reg<NZV, kJForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);       \
+    if (z_reg_smem(kJForm, NZV) <= smem)                                                                   \
+      r = cudaFuncSetAttribute(k_z_reg<NZV, kJForm>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                               z_reg_smem(kJForm, NZV));                                                   \
     if (r != cudaSuccess) e = r;                                                                           \
-    r = cudaFuncSetAttribute(k_z_reg<NZV, kRhoForm>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
+    if (z_reg_smem(kRhoForm, NZV) <= smem)                                                                 \
+      r = cudaFuncSetAttribute(k_z_reg<NZV, kRhoForm>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                               z_reg_smem(kRhoForm, NZV));                                                 \
     if (r != cudaSuccess) e = r;                                                                           \
   }
   PSATD_REG_Z(PSATD_ZS)

@@ -18,7 +18,7 @@ COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
 def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no_graph=False,
-              generic=False, pencil=False, plane=False, j_constant=False, nodal=False):
+              generic=False, pencil=False, plane=False, j_constant=False, nodal=False, eager_exchange=False):
     """psatd_plan_desc for an ``inputs.Layout``; the returned object keeps the
     box array alive (attribute ``_boxes``)."""
     nb = len(layout.boxes)
@@ -51,6 +51,8 @@ def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no
         flags |= A.PSATD_J_CONSTANT
     if nodal:
         flags |= A.PSATD_NODAL
+    if eager_exchange:
+        flags |= A.PSATD_EAGER_EXCHANGE
     d.flags = flags
     d._boxes = arr
     return d
@@ -61,7 +63,7 @@ class Plan:
 
     def __init__(self, layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum",
                  stream=None, no_graph=False, generic=False, pencil=False, plane=False, j_constant=False,
-                 nodal=False):
+                 nodal=False, eager_exchange=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -73,7 +75,7 @@ class Plan:
         self.cdtype = torch.complex64 if precision == 32 else torch.complex128
         self.np_dtype = np.float32 if precision == 32 else np.float64
         self.desc = make_desc(layout, h, dt, c, eps0, precision, sources, no_graph, generic, pencil, plane,
-                              j_constant, nodal)
+                              j_constant, nodal, eager_exchange)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = A.psatd_plan_create(self.desc, self.stream.cuda_stream)
         self.offsets = [A.psatd_plan_layout(self.handle, i) for i in range(len(layout.boxes))]
@@ -84,6 +86,7 @@ class Plan:
         self.workspace_bytes = wb
         self.fast_boxes = A.psatd_plan_fast_boxes(self.handle)
         self.pencil_boxes = A.psatd_plan_pencil_boxes(self.handle)
+        self.deferred_exchange = bool(A.psatd_plan_deferred_exchange(self.handle))
         last = self.spec_offsets[-1]
         self.spec_elems = last[0] + last[1] + 64
 
