@@ -332,6 +332,7 @@ struct psatd_plan {
   int grid_pf = 0, grid_pi = 0;                // persistent grid sizes
   int reg_code = -1;                           // register plane kernels for every fast box
   int reg_z = 0;                               // register z kernel length (0: none)
+  int reg_zst = 0;                             // n1 * (n0/2 + 1) of every register-z box, else 0
 
   // device memory
   std::vector<void*> allocs;
@@ -827,6 +828,14 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       if (nz == -1) break;
     }
     if (nz > 0 && z_reg_ok(nz) && z_reg_smem(P->form, nz) <= optin) P->reg_z = nz;
+    // the z stride, when every fast box shares it
+    for (const ColJob& j : P->zfast) {
+      const int zs = P->boxes[j.box].n[1] * (P->boxes[j.box].n[0] / 2 + 1);
+      if (&j == &P->zfast.front())
+        P->reg_zst = zs;
+      else if (zs != P->reg_zst)
+        P->reg_zst = 0;
+    }
     // the register z kernel has its own tile width: re-tile (jobs are grouped by box)
     const int rt = z_reg_tile_width(P->form);
     if (P->reg_z && rt != tile) {
@@ -1431,7 +1440,8 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
   }
   if (!P->zfast.empty() && P->reg_z) {
     CK(P, timed(P, 2, st, [&] {
-         return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, NFT, st);
+         return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, P->reg_zst,
+                             NFT, st);
        }));
     ++launches;
   } else if (!P->zfast.empty()) {

@@ -381,7 +381,10 @@ constexpr int z_reg_min_blocks() {
   return 2;
 }
 
-template <int NZ, int FORM>
+// ZST > 0: every box of the launch has n1 * (n0/2 + 1) = ZST (the z stride of
+// the spectrum), a compile-time constant, so that the z-strided loads and
+// stores take immediate offsets.
+template <int NZ, int FORM, int ZST>
 __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>())
     k_z_reg(DevPlan P, float2* spec, int64_t sstride, const ColJob* __restrict__ jobs, int nft) {
   constexpr int TX = z_reg_tile(FORM), FIN = fields_in(FORM), FOUT = fields_out(FORM);
@@ -394,7 +397,7 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
   const BoxDev bx = P.boxes[J.box];
   const ShapeDev& sh = P.shapes[bx.shape];
   const int hx = sh.hx, n1 = bx.n[1];
-  const int64_t zst = (int64_t)n1 * hx;
+  const int64_t zst = ZST > 0 ? (int64_t)ZST : (int64_t)n1 * hx;
   // column t: mode column (m0 + t, y), or (m0 = n0/2, y + t) for a Nyquist tile
   const bool nyq = J.nm < 0;
   const int nm = nyq ? -J.nm : J.nm, ts = nyq ? hx : 1;
@@ -504,22 +507,38 @@ int z_reg_smem(int form, int n2) { return n2 * z_reg_pitch(form) * 8; }
 
 int z_reg_tile_width(int form) { return z_reg_tile(form); }
 
+// z strides with their own instantiation: the register plane shape 96 x 96
+constexpr int kRegZst = 96 * 49;
+
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                         int64_t njobs, int n2, int nft, cudaStream_t st) {
+                         int64_t njobs, int n2, int zst, int nft, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs);
   const int smem = z_reg_smem(form, n2);
-#define PSATD_ZL(NZV)                                                                                 \
-  if (n2 == NZV) {                                                                                   \
-    if (form == kVacuum)                                                                             \
-      k_z_reg<NZV, kVacuum><<<grid, z_reg_threads<kVacuum>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft); \
-    else if (form == kJForm)                                                                         \
-      k_z_reg<NZV, kJForm><<<grid, z_reg_threads<kJForm>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft); \
-    else                                                                                             \
-      k_z_reg<NZV, kRhoForm><<<grid, z_reg_threads<kRhoForm>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft); \
+#define PSATD_ZF(NZV, F, ZS) \
+  k_z_reg<NZV, F, ZS><<<grid, z_reg_threads<F>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft)
+#define PSATD_ZL(NZV)                                                    \
+  if (n2 == NZV) {                                                      \
+    if (form == kVacuum) {                                              \
+      if (zst == kRegZst)                                               \
+        PSATD_ZF(NZV, kVacuum, kRegZst);                                \
+      else                                                              \
+        PSATD_ZF(NZV, kVacuum, 0);                                      \
+    } else if (form == kJForm) {                                        \
+      if (zst == kRegZst)                                               \
+        PSATD_ZF(NZV, kJForm, kRegZst);                                 \
+      else                                                              \
+        PSATD_ZF(NZV, kJForm, 0);                                       \
+    } else {                                                            \
+      if (zst == kRegZst)                                               \
+        PSATD_ZF(NZV, kRhoForm, kRegZst);                               \
+      else                                                              \
+        PSATD_ZF(NZV, kRhoForm, 0);                                     \
+    }                                                                   \
   }
   PSATD_REG_Z(PSATD_ZL)
 #undef PSATD_ZL
+#undef PSATD_ZF
   return cudaGetLastError();
 }
 
@@ -596,24 +615,23 @@ cudaError_t configure_reg_kernels(int smem) {
   }
   PSATD_REG_SHAPES(PSATD_RC)
 #undef PSATD_RC
-#define PSATD_ZS(NZV)                                                                                      \
-  {                                                                                                        \
-    cudaError_t r = cudaSuccess;                                                                           \
-    if (z_reg_smem(kVacuum, NZV) <= smem)                                                                  \
-      r = cudaFuncSetAttribute(k_z_reg<NZV, kVacuum>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
-                               z_reg_smem(kVacuum, NZV));                                                  \
-    if (r != cudaSuccess) e = r;                                                                           \
-    if (z_reg_smem(kJForm, NZV) <= smem)                                                                   \
-      r = cudaFuncSetAttribute(k_z_reg<NZV, kJForm>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                               z_reg_smem(kJForm, NZV));                                                   \
-    if (r != cudaSuccess) e = r;                                                                           \
-    if (z_reg_smem(kRhoForm, NZV) <= smem)                                                                 \
-      r = cudaFuncSetAttribute(k_z_reg<NZV, kRhoForm>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
-                               z_reg_smem(kRhoForm, NZV));                                                 \
-    if (r != cudaSuccess) e = r;                                                                           \
+#define PSATD_ZA(NZV, F, ZS)                                                                      \
+  if (z_reg_smem(F, NZV) <= smem) {                                                               \
+    const cudaError_t r = cudaFuncSetAttribute(k_z_reg<NZV, F, ZS>,                               \
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                               z_reg_smem(F, NZV));                               \
+    if (r != cudaSuccess) e = r;                                                                  \
   }
+#define PSATD_ZS(NZV)                 \
+  PSATD_ZA(NZV, kVacuum, 0)           \
+  PSATD_ZA(NZV, kJForm, 0)            \
+  PSATD_ZA(NZV, kRhoForm, 0)          \
+  PSATD_ZA(NZV, kVacuum, kRegZst)     \
+  PSATD_ZA(NZV, kJForm, kRegZst)      \
+  PSATD_ZA(NZV, kRhoForm, kRegZst)
   PSATD_REG_Z(PSATD_ZS)
 #undef PSATD_ZS
+#undef PSATD_ZA
   return e;
 }
 
