@@ -2,9 +2,10 @@
 //
 // Dft<T, R, DIR>::run(v) replaces v[0..R) by y_k = sum_t v_t exp(DIR 2 pi i t k / R)
 // (DIR = -1 forward, +1 inverse, unnormalised).  R in {2,3,4,5,8} are written
-// out; the other sizes are composed from two smaller codelets (decimation in
-// time, R = A*B) whose internal twiddles exp(DIR 2 pi i m / R) are
-// compile-time constants (unit_roots.h).
+// out; the other sizes are composed from two smaller codelets: coprime
+// factors by the prime-factor mapping (no twiddles), powers of two by
+// decimation in time (R = A*B) with internal twiddles exp(DIR 2 pi i m / R)
+// as compile-time constants (unit_roots.h).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -231,24 +232,60 @@ struct DftComposite {
   }
 };
 
+// R = A * B with A, B coprime by the prime-factor (Good-Thomas) mapping: with
+// input index n = (B n1 + A n2) mod R and output index
+// k = (B tB k1 + A tA k2) mod R, tB = B^-1 mod A, tA = A^-1 mod B, the R-point
+// DFT is exactly the two-dimensional A x B DFT of the re-indexed input, with
+// no twiddle factors (the index maps are compile-time register renamings).
+constexpr int inv_mod(int a, int m) {
+  int r = 1;
+  while ((a * r) % m != 1 % m) ++r;
+  return r;
+}
+constexpr int gcd_int(int a, int b) { return b == 0 ? a : gcd_int(b, a % b); }
+
+template <typename T, int A, int B, int DIR>
+struct DftPfa {
+  static_assert(gcd_int(A, B) == 1, "prime-factor lengths must be coprime");
+  static __device__ __forceinline__ void run(cx<T>* v) {
+    constexpr int R = A * B, TB = inv_mod(B % A, A), TA = inv_mod(A % B, B);
+    cx<T> u[B][A];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) {
+#pragma unroll
+      for (int n1 = 0; n1 < A; ++n1) u[n2][n1] = v[(B * n1 + A * n2) % R];
+      Dft<T, A, DIR>::run(u[n2]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      cx<T> w[B];
+#pragma unroll
+      for (int n2 = 0; n2 < B; ++n2) w[n2] = u[n2][k1];
+      Dft<T, B, DIR>::run(w);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) v[(B * TB * k1 + A * TA * k2) % R] = w[k2];
+    }
+  }
+};
+
 template <typename T, int DIR>
-struct Dft<T, 6, DIR> : DftComposite<T, 3, 2, DIR> {};
+struct Dft<T, 6, DIR> : DftPfa<T, 3, 2, DIR> {};
 template <typename T, int DIR>
-struct Dft<T, 10, DIR> : DftComposite<T, 5, 2, DIR> {};
+struct Dft<T, 10, DIR> : DftPfa<T, 5, 2, DIR> {};
 template <typename T, int DIR>
-struct Dft<T, 12, DIR> : DftComposite<T, 4, 3, DIR> {};
+struct Dft<T, 12, DIR> : DftPfa<T, 4, 3, DIR> {};
 template <typename T, int DIR>
 struct Dft<T, 16, DIR> : DftComposite<T, 4, 4, DIR> {};
 // register-resident lengths of the one-thread-per-line kernels
 template <typename T, int DIR>
-struct Dft<T, 24, DIR> : DftComposite<T, 8, 3, DIR> {};
+struct Dft<T, 24, DIR> : DftPfa<T, 8, 3, DIR> {};
 template <typename T, int DIR>
-struct Dft<T, 30, DIR> : DftComposite<T, 10, 3, DIR> {};
+struct Dft<T, 30, DIR> : DftPfa<T, 10, 3, DIR> {};
 template <typename T, int DIR>
 struct Dft<T, 32, DIR> : DftComposite<T, 8, 4, DIR> {};
 template <typename T, int DIR>
-struct Dft<T, 40, DIR> : DftComposite<T, 8, 5, DIR> {};
+struct Dft<T, 40, DIR> : DftPfa<T, 8, 5, DIR> {};
 template <typename T, int DIR>
-struct Dft<T, 48, DIR> : DftComposite<T, 16, 3, DIR> {};
+struct Dft<T, 48, DIR> : DftPfa<T, 16, 3, DIR> {};
 
 }  // namespace psatd
