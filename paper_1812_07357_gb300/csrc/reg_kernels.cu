@@ -362,6 +362,26 @@ __global__ void __launch_bounds__(kRegThreads, 4) k_plane_inv_reg(DevPlan P, Fie
 }
 
 // ---------------------------------------------------------------------------
+// exp(-2 pi i k / NZ), k < NZ/2: the twiddles of the radix-2 z stage, rounded
+// from the compile-time FP64 roots
+template <int NZ>
+struct HalfTwiddles {
+  float2 w[NZ / 2];
+};
+template <int NZ>
+constexpr HalfTwiddles<NZ> half_twiddles() {
+  HalfTwiddles<NZ> t{};
+  for (int k = 0; k < NZ / 2; ++k) t.w[k] = float2{(float)root_cos(NZ, k), (float)-root_sin(NZ, k)};
+  return t;
+}
+__constant__ HalfTwiddles<96> kTw96 = half_twiddles<96>();
+__constant__ HalfTwiddles<48> kTw48 = half_twiddles<48>();
+template <int NZ>
+__device__ __forceinline__ float2 half_twiddle(int k) {
+  static_assert(NZ == 96 || NZ == 48, "register z lengths");
+  return NZ == 96 ? kTw96.w[k] : kTw48.w[k];
+}
+
 // mx columns (or Nyquist-column y rows) per z tile: 16 (128-byte rows of a
 // slot) for the 6-slot vacuum form, 8 for the forms with sources
 constexpr int z_reg_tile(int form) { return form == kVacuum ? 16 : 8; }
@@ -458,9 +478,7 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
       for (int it = 0; it < NIT; ++it) {
         const int k = k0 + it * ZS;
         if (H % ZS == 0 || k < H) {
-          float2 w;
-          sincospif((float)(2 * k) / (float)NZ, &w.y, &w.x);
-          w.y = -w.y;   // exp(-2 pi i k / NZ)
+          const float2 w = half_twiddle<NZ>(k);   // exp(-2 pi i k / NZ)
           update_pair_z2<FORM, NZ>(buf + k * NP + ta, buf + (k + H) * NP + ta, TX, xy, k, w, nft, sh, P);
         }
       }
