@@ -95,7 +95,9 @@ typedef enum {
                                   /* rounding                                        */
 #define PSATD_EAGER_EXCHANGE 0x100u /* store the guard cells in every step.  Without */
                                   /* it, plans whose boxes all run on the register  */
-                                  /* plane kernels defer each step's guard exchange */
+                                  /* plane kernels (or all on the pencil kernels,   */
+                                  /* when each plane's guard faces form at most 3x3 */
+                                  /* rectangles) defer each step's guard exchange   */
                                   /* into the next step's forward pass, which reads */
                                   /* every guard cell from the interior cell owning */
                                   /* it (the value the exchange would store), and   */

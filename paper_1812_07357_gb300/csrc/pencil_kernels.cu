@@ -31,6 +31,7 @@ namespace psatd {
 namespace {
 
 constexpr int kPenThreads = 256;
+constexpr int kGatherRows = 64;   // row descriptors of the deferred-exchange gather per chunk
 constexpr int kPenMaxi = 2;   // rows * R1 <= kPenMaxi * kPenThreads for the x passes
 
 template <typename T>
@@ -108,7 +109,8 @@ __device__ __forceinline__ void pen_xf_body(cx<T>* buf, int nr, const cx<T>* __r
 
 template <typename T, int R1, int R2>
 __global__ void __launch_bounds__(kPenThreads) k_pen_xf(DevPlan P, FieldPtrs F, cx<T>* spec, int64_t sstride,
-                                                        const RowJob* __restrict__ jobs) {
+                                                        const RowJob* __restrict__ jobs,
+                                                        const GatherGrid* __restrict__ ggrid, int ngather) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const RowJob J = jobs[blockIdx.x];
@@ -116,9 +118,44 @@ __global__ void __launch_bounds__(kPenThreads) k_pen_xf(DevPlan P, FieldPtrs F, 
   const BoxDev bx = P.boxes[J.box];
   const ShapeDev& sh = P.shapes[bx.shape];
   const int n0 = bx.n[0], L = sh.L, hx = sh.hx, LP = pen_x_pitch(L);
-  // rows r0 .. r0+nr-1 are contiguous in the field buffer
-  const T* g = reinterpret_cast<const T*>(F.p[f]) + bx.foff + (int64_t)J.r0 * n0;
-  load_rows_async(buf, g, J.nr, n0 * (int)sizeof(T), LP * (int)sizeof(cx<T>));
+  if (ggrid && f < ngather) {
+    // deferred exchange: the three x bands of each row from the cells that
+    // own them (gather grid of the row's plane); row descriptors in chunks
+    constexpr int VE = 16 / (int)sizeof(T);   // elements per 16-byte unit
+    __shared__ int64_t rsrc[kGatherRows][3];
+    __shared__ int rx[kGatherRows][2];
+    const T* fb = reinterpret_cast<const T*>(F.p[f]);
+    const int n1 = bx.n[1], upr = n0 / VE;
+    const unsigned mu = magic(upr);
+    for (int rb = 0; rb < J.nr; rb += kGatherRows) {
+      const int nrb = min(kGatherRows, J.nr - rb);
+      if (threadIdx.x < nrb) {
+        const int r = J.r0 + rb + threadIdx.x;
+        const int z = r / n1, y = r - z * n1;
+        const GatherGrid& G = ggrid[bx.gplane + z];
+        const int iy = (y >= G.y1) + (y >= G.y2);
+        const int dy = y - (iy == 0 ? 0 : iy == 1 ? G.y1 : G.y2);
+        // element x of band ix is at rsrc[ix] + x
+        rsrc[threadIdx.x][0] = G.base[3 * iy] + (int64_t)dy * G.pitch[3 * iy];
+        rsrc[threadIdx.x][1] = G.base[3 * iy + 1] + (int64_t)dy * G.pitch[3 * iy + 1] - G.x1;
+        rsrc[threadIdx.x][2] = G.base[3 * iy + 2] + (int64_t)dy * G.pitch[3 * iy + 2] - G.x2;
+        rx[threadIdx.x][0] = G.x1;
+        rx[threadIdx.x][1] = G.x2;
+      }
+      __syncthreads();
+      for (int u = threadIdx.x; u < nrb * upr; u += kPenThreads) {
+        const int i = fdiv(u, mu), x = (u - i * upr) * VE;
+        const int ix = (x >= rx[i][0]) + (x >= rx[i][1]);
+        cp16(reinterpret_cast<char*>(buf) + (size_t)(rb + i) * LP * sizeof(cx<T>) + (size_t)x * sizeof(T),
+             fb + rsrc[i][ix] + x);
+      }
+      __syncthreads();   // the descriptors of the next chunk overwrite these
+    }
+  } else {
+    // rows r0 .. r0+nr-1 are contiguous in the field buffer
+    const T* g = reinterpret_cast<const T*>(F.p[f]) + bx.foff + (int64_t)J.r0 * n0;
+    load_rows_async(buf, g, J.nr, n0 * (int)sizeof(T), LP * (int)sizeof(cx<T>));
+  }
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   pen_xf_body<T, R1, R2>(buf, J.nr, ctab<T>(P) + sh.ax.tw, ctab<T>(P) + sh.post);
@@ -247,16 +284,19 @@ int pen_col_smem(int prec, int n1) { return n1 * pen_col_tile(prec) * (prec == 3
 // axis the kernel transforms (x for the row kernels, y for the column
 // kernels, z for the z kernel); every job of the launch has that length.
 cudaError_t launch_pen_xf(int prec, int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
-                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st) {
+                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem, const GatherGrid* ggrid,
+                          int ngather, cudaStream_t st) {
   if (njobs <= 0 || nf <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs, nf);
   switch (code) {
 #define PSATD_ARM(c, N, R1, R2)                                                                       \
   case c:                                                                                             \
     if (prec == 32)                                                                                   \
-      k_pen_xf<float, R1, R2><<<grid, kPenThreads, smem, st>>>(P, f, (float2*)spec, sstride, jobs);    \
+      k_pen_xf<float, R1, R2><<<grid, kPenThreads, smem, st>>>(P, f, (float2*)spec, sstride, jobs, ggrid, \
+                                                               ngather);                              \
     else                                                                                              \
-      k_pen_xf<double, R1, R2><<<grid, kPenThreads, smem, st>>>(P, f, (double2*)spec, sstride, jobs);  \
+      k_pen_xf<double, R1, R2><<<grid, kPenThreads, smem, st>>>(P, f, (double2*)spec, sstride, jobs, ggrid, \
+                                                                ngather);                             \
     break;
     PSATD_PENCIL_LENGTHS(PSATD_ARM)
 #undef PSATD_ARM
@@ -342,8 +382,11 @@ cudaError_t launch_pen_xi(int prec, int code, const DevPlan& P, const FieldPtrs&
 template <typename T, int R1, int R2>
 cudaError_t configure_pen_t(int smem) {
   cudaError_t e = cudaSuccess;
-  auto set = [&](const void* k) {
-    const cudaError_t r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  auto set = [&](const void* k) {   // the opt-in maximum less the kernel's static shared memory
+    cudaFuncAttributes fa{};
+    cudaError_t r = cudaFuncGetAttributes(&fa, k);
+    if (r == cudaSuccess)
+      r = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem - (int)fa.sharedSizeBytes);
     if (r != cudaSuccess) e = r;
   };
   constexpr int TX = sizeof(T) == 4 ? 8 : 4;

@@ -456,27 +456,36 @@ cudaError_t dalloc(psatd_plan* p, size_t bytes, void** d) {
 
 
 // Deferred guard exchange.  When every box runs on the register plane kernels
-// (so every guard block is fed by an inverse plane pass), a step need not
-// store its guard cells: the next step's forward plane pass reads every
-// guard cell straight from the interior cell that owns it, which is the
-// value the exchange would have stored there, and only the last step of a
-// push stores the guards.  Per forward plane job (box b, plane z): the
-// rectangles of blocks that feed b's plane z, then the cells no block feeds
-// (interior, and guards outside a non-periodic domain) from b itself.
+// (every guard block fed by an inverse plane pass) or every box on the pencil
+// kernels (guard blocks stored by the step's exchange kernel), a step need
+// not store its guard cells: the next step's forward x pass reads every guard
+// cell straight from the interior cell that owns it, which is the value the
+// exchange would have stored there, and only the last step of a push stores
+// the guards.  Per plane (box b, plane z): the rectangles of blocks that feed
+// b's plane z, then the cells no block feeds (interior, and guards outside a
+// non-periodic domain) from b itself.
 static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint32_t flags) {
   P->deferred = false;
-  if ((flags & PSATD_EAGER_EXCHANGE) || P->reg_code < 0 || P->plane_fwd.empty() || P->segs.empty() ||
-      !P->step_tiles.empty() || !P->g_rows.empty() || !P->pen_rows.empty())
-    return;
-  for (char f : box_fast)
-    if (!f) return;
   const int nb = (int)P->boxes.size();
+  // register plane plans (guards stored by the inverse plane pass), or plans
+  // whose boxes all run on the pencil kernels (guards stored by the step's
+  // exchange kernel; those take the 3 x 3 grid form only)
+  const bool reg = P->reg_code >= 0 && !P->plane_fwd.empty() && !P->segs.empty() && P->step_tiles.empty() &&
+                   P->g_rows.empty() && P->pen_rows.empty() &&
+                   std::all_of(box_fast.begin(), box_fast.end(), [](char f) { return f != 0; });
+  const bool pen = P->pen_boxes == nb && !P->step_tiles.empty();
+  if ((flags & PSATD_EAGER_EXCHANGE) || !(reg || pen)) return;
+  // every plane of every box, box-major (for register plane plans, the
+  // forward plane jobs themselves)
+  std::vector<int2> planes;
+  for (int b = 0; b < nb; ++b)
+    for (int z = 0; z < P->boxes[b].n[2]; ++z) planes.push_back(make_int2(b, z));
   std::vector<std::vector<int>> by_dst(nb);
   for (int i = 0; i < (int)P->blocks.size(); ++i)
     if (P->blocks[i].src_box >= 0) by_dst[P->blocks[i].dst_box].push_back(i);
   const int v16 = 16 / (int)P->rsize;
   std::vector<GatherSeg> out;
-  std::vector<int> start(P->plane_fwd.size() + 1, 0);
+  std::vector<int> start(planes.size() + 1, 0);
   auto emit = [&](int64_t src_off, int spitch, int dy, int dx, int ny, int nx) {
     GatherSeg g{};
     g.src_off = src_off;
@@ -488,8 +497,8 @@ static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint3
     g.vec = nx % v16 == 0 && dx % v16 == 0 && src_off % v16 == 0 && spitch % v16 == 0;
     out.push_back(g);
   };
-  for (size_t j = 0; j < P->plane_fwd.size(); ++j) {
-    const int b = P->plane_fwd[j].x, z = P->plane_fwd[j].y;
+  for (size_t j = 0; j < planes.size(); ++j) {
+    const int b = planes[j].x, z = planes[j].y;
     const psatd_box& B = P->boxes[b];
     const int n0 = B.n[0], n1 = B.n[1];
     // covered[y]: x intervals of row y fed by a block
@@ -530,11 +539,11 @@ static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint3
   }
   P->gseg_start.swap(start);
   P->gsegs.swap(out);
-  P->deferred = true;
+  P->deferred = reg;
   // the 3 x 3 grid form of every plane, when each one has it
-  std::vector<GatherGrid> grids(P->plane_fwd.size());
-  for (size_t j = 0; j < P->plane_fwd.size(); ++j) {
-    const psatd_box& B = P->boxes[P->plane_fwd[j].x];
+  std::vector<GatherGrid> grids(planes.size());
+  for (size_t j = 0; j < planes.size(); ++j) {
+    const psatd_box& B = P->boxes[planes[j].x];
     std::vector<int> xs{0, B.n[0]}, ys{0, B.n[1]};
     bool vec = true;
     for (int i = P->gseg_start[j]; i < P->gseg_start[j + 1]; ++i) {
@@ -549,7 +558,10 @@ static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint3
       std::sort(v->begin(), v->end());
       v->erase(std::unique(v->begin(), v->end()), v->end());
     }
-    if (!vec || xs.size() > 4 || ys.size() > 4) return;   // keep the rectangle lists
+    if (!vec || xs.size() > 4 || ys.size() > 4) {   // register planes keep the rectangle lists
+      if (!reg) P->gsegs.clear(), P->gseg_start.clear();
+      return;
+    }
     while (xs.size() < 4) xs.push_back(B.n[0]);
     while (ys.size() < 4) ys.push_back(B.n[1]);
     GatherGrid gg{};
@@ -569,13 +581,17 @@ static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint3
             found = true;
           }
         }
-        if (!found) return;
+        if (!found) {
+          if (!reg) P->gsegs.clear(), P->gseg_start.clear();
+          return;
+        }
       }
     grids[j] = gg;
   }
   P->ggrid.swap(grids);
   P->gsegs.clear();
   P->gseg_start.clear();
+  P->deferred = true;
 }
 
 psatd_status build(psatd_plan* P, cudaStream_t st) {
@@ -644,6 +660,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   }
   // ---- boxes
   int64_t foff = 0, soff = 0;
+  int32_t gplane = 0;
   for (const psatd_box& b : P->boxes) {
     BoxDev x{};
     for (int a = 0; a < 3; ++a) {
@@ -652,6 +669,8 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       x.ng_hi[a] = b.ng_hi[a];
     }
     x.shape = shape_of[std::make_tuple(b.n[0], b.n[1], b.n[2], b.order_p)];
+    x.gplane = gplane;
+    gplane += b.n[2];
     x.foff = foff;
     x.soff = soff;
     foff += align_up((int64_t)b.n[0] * b.n[1] * b.n[2], 64);
@@ -899,7 +918,6 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     P->seg_start[i + 1] = P->seg_start[i] + (int)per_plane[i].size();
     P->segs.insert(P->segs.end(), per_plane[i].begin(), per_plane[i].end());
   }
-  build_gather(P, box_fast, d.flags);
   for (int i = 0; i < (int)P->blocks.size(); ++i) {
     const CopyBlk& c = P->blocks[i];
     const bool fused = c.src_box >= 0 && box_fast[c.src_box];
@@ -917,6 +935,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       if (stepwise) P->step_tiles.push_back({i, r, std::min(per, rows - r), vec ? v16 : 1});
     }
   }
+  build_gather(P, box_fast, d.flags);
   // ---- device memory
   CK(P, upload(P, P->hboxes, &P->d_boxes));
   CK(P, upload(P, P->hshapes, &P->d_shapes));
@@ -1378,6 +1397,7 @@ static psatd_status forward_xy(psatd_plan* P, const DevPlan& D, const FieldPtrs&
   for (const auto& g : P->grp_rows) {
     CK(P, timed(P, 0, st, [&] {
          return launch_pen_xf(P->prec, g.code, D, fp, nf, spec, S, P->d_pen_rows + g.start, g.count, P->smem_penx,
+                              gather && P->deferred && !P->ggrid.empty() ? P->d_ggrid : nullptr, fields_out(P->form),
                               st);
        }));
     ++launches;
@@ -1497,7 +1517,7 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
        }));
     ++launches;
   }
-  if (!P->step_tiles.empty()) {
+  if (!P->step_tiles.empty() && guards) {
     CK(P, timed(P, 5, st, [&] {
          return launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_step_tiles, (int64_t)P->step_tiles.size(),
                                 st);

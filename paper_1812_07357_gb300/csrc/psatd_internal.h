@@ -84,6 +84,7 @@ struct BoxDev {
   int32_t ng_lo[3];
   int32_t ng_hi[3];
   int32_t shape;
+  int32_t gplane;                 // index of the box's plane z = 0 in the gather grids
   int64_t foff;                   // element offset in every field buffer
   int64_t soff;                   // complex-element offset in every spectrum slot
 };
@@ -253,8 +254,10 @@ int pen_z_max(int prec);                                  // longest n2 of a pen
 int pen_col_tile(int prec);                               // mx columns of a y tile
 int pen_col_smem(int prec, int n1);
 // one launch per length group: `code` = pencil code of the transformed axis
+// ggrid (deferred exchange): the gather grid of every plane, box b's plane z
+// at boxes[b].gplane + z, used for the slots f < ngather; null: plain rows
 cudaError_t launch_pen_xf(int prec, int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec,
-                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem, cudaStream_t st);
+                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem, const GatherGrid* ggrid, int ngather, cudaStream_t st);
 cudaError_t launch_pen_col(int prec, int dir, int code, const DevPlan& P, void* spec, int64_t sstride, int nf,
                            const ColJob* jobs, int64_t njobs, int smem, cudaStream_t st);
 cudaError_t launch_z_pen(int prec, int form, int code, const DevPlan& P, void* spec, int64_t sstride,

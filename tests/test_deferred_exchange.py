@@ -104,16 +104,63 @@ def test_sources_deferred_equals_eager(form, jc):
     _same(a, b)
 
 
-def test_not_deferred_off_the_register_planes():
+def test_which_plans_defer():
     from paper_1812_07357_gb300.solver import Plan
     lay = _layout()
-    for kw in ({"generic": True}, {"pencil": True}, {"eager_exchange": True}):
+    for kw, want in (({"generic": True}, False), ({"pencil": True}, True), ({"eager_exchange": True}, False),
+                     ({"pencil": True, "eager_exchange": True}, False), ({}, True)):
         plan = Plan(lay, (1.0, 1.0, 1.0), 0.9, precision=32, sources="vacuum", **kw)
-        assert not plan.deferred_exchange, kw
+        assert plan.deferred_exchange == want, kw
         plan.close()
     plan = Plan(I.global_layout((96, 96, 48), 8), (1.0, 1.0, 1.0), 0.9, precision=32, sources="vacuum")
     assert not plan.deferred_exchange      # no guards
     plan.close()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_pencil_local_deferred_equals_eager(prec):
+    """192 x 96 x 96 local boxes on the pencil kernels: the x-forward pass
+    gathers every row's three x bands from their owners."""
+    from paper_1812_07357_gb300.solver import Plan
+    lay = I.local_layout((256, 64, 64), (2, 2, 2), 32, 16)
+    f = I.laser_fields((256, 64, 64), wavelength=8.0, waist=10.0, duration=8.0)
+    fields = {k: I.scatter_global(v, lay) for k, v in f.items()}
+    if prec == 32:
+        fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
+    outs = []
+    for eager in (False, True):
+        plan = Plan(lay, (1.0, 1.0, 1.0), 0.9, precision=prec, sources="vacuum", eager_exchange=eager)
+        assert plan.pencil_boxes == 8 and plan.deferred_exchange == (not eager)
+        df = plan.pack_fields(fields)
+        plan.push(df, None, 4)
+        plan.sync()
+        outs.append(plan.unpack_fields(df))
+        plan.close()
+    _same(outs[0], outs[1])
+    ref = O.push(lay, fields, {}, 4, (1.0, 1.0, 1.0), 0.9, form="vacuum")
+    assert O.rel_l2_fields(lay, outs[0], ref, O.COMPS) <= {32: 2e-5, 64: 1e-12}[prec]
+
+
+def test_pencil_independent_rho_deferred_equals_eager():
+    """Self-periodic boxes of different sizes (guards wrap onto the box's own
+    interior), rho form, on the pencil kernels."""
+    from paper_1812_07357_gb300.solver import Plan
+    sizes = [(160, 24, 32), (192, 30, 40), (256, 32, 24)]
+    boxes = [I.Box(n, (4, 4, 4), (4, 4, 4), (0, 0, 0), p) for n, p in zip(sizes, (8, 16, 0))]
+    lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
+    rng = np.random.default_rng(53)
+    js = {k: [] for k in ("Jx", "Jy", "Jz")}
+    for b in lay.boxes:
+        j = I.band_limited_current(b.interior, rng)
+        for k in js:
+            js[k].append(j[k])
+    src = {k: I.round_to(I.scatter_self(v, lay), np.float32) for k, v in js.items()}
+    src["rho"] = I.zeros(lay)
+    fields = {k: I.zeros(lay) for k in O.COMPS}
+    a, da = _run(lay, fields, src, [3], form="rho")
+    b, _ = _run(lay, fields, src, [3], form="rho", eager_exchange=True)
+    assert da
+    _same(a, b)
 
 
 def test_guards_wider_than_neighbours():
