@@ -41,6 +41,14 @@ __device__ __forceinline__ void cp16(void* s, const void* g) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
 }
+// global load of one complex value with a 256-byte L2 fetch: the z tiles of
+// neighbouring column groups (run by neighbouring CTAs) read the adjacent
+// 128-byte pieces of the same spectrum rows
+__device__ __forceinline__ float2 ld_l2_256(const float2* p) {
+  float2 r;
+  asm("ld.global.L2::256B.v2.f32 {%0, %1}, [%2];\n" : "=f"(r.x), "=f"(r.y) : "l"(p));
+  return r;
+}
 __device__ __forceinline__ void cp4(void* s, const void* g) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(g) : "memory");
@@ -431,7 +439,7 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
   {
     const float2* src = g + sc * sstride + (int64_t)tc * ts + half * zst;
 #pragma unroll
-    for (int m = 0; m < H; ++m) v[m] = src[2 * m * zst];
+    for (int m = 0; m < H; ++m) v[m] = ld_l2_256(src + 2 * m * zst);
   }
   // half-length forward DFT of the member's samples into row half * H + k;
   // slots >= nft already hold their z spectrum (a cached constant current) in
