@@ -177,6 +177,20 @@ psatd_status psatd_plan_validate(const psatd_plan_desc* desc, char* msg, size_t 
 psatd_status psatd_exchange_blocks(const psatd_plan_desc* desc, psatd_copy_block* out,
                                    int64_t cap, int64_t* count);
 
+/* Host-only: where the deferred guard exchange (see PSATD_EAGER_EXCHANGE)
+ * makes the forward pass read plane z of box `box` (paper Fig. 1, step (ii)
+ * folded into the next step).  For every cell (y, x) of the padded plane, at
+ * index y * n[0] + x of the caller's arrays of n[0] * n[1] entries:
+ * src_box / src_cell = the box and the linear cell index (x fastest, then y,
+ * then z) of the cell whose value is read there -- the owning interior cell
+ * for a guard cell that has an owner, the cell itself otherwise.  *is_grid = 1
+ * when the plane is the 3 x 3 rectangle grid the kernels use (the indices are
+ * then produced from that grid form), 0 when only the rectangle list applies.
+ * Errors: PSATD_ERR_INVALID_ARG for an invalid description, box or plane, or
+ * a NULL output. */
+psatd_status psatd_plane_gather(const psatd_plan_desc* desc, int32_t box, int32_t z,
+                                int32_t* src_box, int64_t* src_cell, int32_t* is_grid);
+
 /* Build a plan: validate, build the copy blocks and work lists, allocate the
  * spectral workspace and tables, and generate the FP64 tables (twiddles,
  * modified wavenumbers k_p, Yee phase factors, PSATD coefficients) with

@@ -96,6 +96,8 @@ _SIGS = {
     "psatd_plan_deferred_exchange": (c_int32, [c_void_p]),
     "psatd_push_box_static": (c_int32, [POINTER(c_int32), c_int32, POINTER(c_double), c_double,
                                         c_double, POINTER(psatd_fields), c_int32, c_void_p]),
+    "psatd_plane_gather": (c_int32, [POINTER(psatd_plan_desc), c_int32, c_int32, POINTER(c_int32), POINTER(c_int64),
+                                     POINTER(c_int32)]),
     "psatd_coupling_blocks": (c_int32, [POINTER(psatd_plan_desc), c_int32, POINTER(psatd_box), c_int32,
                                         POINTER(psatd_copy_block), c_int64, POINTER(c_int64)]),
     "psatd_coupling_create": (c_int32, [c_void_p, c_int32, POINTER(psatd_box), POINTER(c_void_p)]),
@@ -174,6 +176,20 @@ def _box_array(boxes):
         arr[i].origin[:] = list(b.origin)
         arr[i].order_p = int(b.p)
     return arr
+
+
+def psatd_plane_gather(desc: psatd_plan_desc, box: int, z: int):
+    """Host-only: (src_box, src_cell, is_grid) of plane z of `box` under the
+    deferred guard exchange; the arrays have shape (n1, n0)."""
+    import numpy as np
+    b = desc.boxes[box]
+    n0, n1 = int(b.n[0]), int(b.n[1])
+    sb = np.empty(n0 * n1, dtype=np.int32)
+    sc = np.empty(n0 * n1, dtype=np.int64)
+    g = c_int32(0)
+    _check(load().psatd_plane_gather(ctypes.byref(desc), box, z, sb.ctypes.data_as(POINTER(c_int32)),
+                                     sc.ctypes.data_as(POINTER(c_int64)), ctypes.byref(g)))
+    return sb.reshape(n1, n0), sc.reshape(n1, n0), bool(g.value)
 
 
 def psatd_coupling_blocks(desc: psatd_plan_desc, g1_boxes, direction: int):

@@ -455,37 +455,15 @@ cudaError_t dalloc(psatd_plan* p, size_t bytes, void** d) {
 }
 
 
-// Deferred guard exchange.  When every box runs on the register plane kernels
-// (every guard block fed by an inverse plane pass) or every box on the pencil
-// kernels (guard blocks stored by the step's exchange kernel), a step need
-// not store its guard cells: the next step's forward x pass reads every guard
-// cell straight from the interior cell that owns it, which is the value the
-// exchange would have stored there, and only the last step of a push stores
-// the guards.  Per plane (box b, plane z): the rectangles of blocks that feed
-// b's plane z, then the cells no block feeds (interior, and guards outside a
-// non-periodic domain) from b itself.
-static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint32_t flags) {
-  P->deferred = false;
-  const int nb = (int)P->boxes.size();
-  // register plane plans (guards stored by the inverse plane pass), or plans
-  // whose boxes all run on the pencil kernels (guards stored by the step's
-  // exchange kernel; those take the 3 x 3 grid form only)
-  const bool reg = P->reg_code >= 0 && !P->plane_fwd.empty() && !P->segs.empty() && P->step_tiles.empty() &&
-                   P->g_rows.empty() && P->pen_rows.empty() &&
-                   std::all_of(box_fast.begin(), box_fast.end(), [](char f) { return f != 0; });
-  const bool pen = P->pen_boxes == nb && !P->step_tiles.empty();
-  if ((flags & PSATD_EAGER_EXCHANGE) || !(reg || pen)) return;
-  // every plane of every box, box-major (for register plane plans, the
-  // forward plane jobs themselves)
-  std::vector<int2> planes;
-  for (int b = 0; b < nb; ++b)
-    for (int z = 0; z < P->boxes[b].n[2]; ++z) planes.push_back(make_int2(b, z));
-  std::vector<std::vector<int>> by_dst(nb);
-  for (int i = 0; i < (int)P->blocks.size(); ++i)
-    if (P->blocks[i].src_box >= 0) by_dst[P->blocks[i].dst_box].push_back(i);
-  const int v16 = 16 / (int)P->rsize;
-  std::vector<GatherSeg> out;
-  std::vector<int> start(planes.size() + 1, 0);
+// Gather rectangles of plane z of box b for the deferred guard exchange: the
+// rectangles of the exchange blocks that feed b's plane z (read from the
+// owning interiors), then the cells no block feeds (interior, and guards
+// outside a non-periodic domain) from b itself, consecutive equal rows merged.
+// foff: element offset of every box in a field buffer; by_dst: the blocks
+// (with a source box) of every destination box; v16: elements per 16 bytes.
+static void plane_segs(const std::vector<psatd_box>& boxes, const std::vector<int64_t>& foff,
+                       const std::vector<CopyBlk>& blocks, const std::vector<std::vector<int>>& by_dst, int b, int z,
+                       int v16, std::vector<GatherSeg>* out) {
   auto emit = [&](int64_t src_off, int spitch, int dy, int dx, int ny, int nx) {
     GatherSeg g{};
     g.src_off = src_off;
@@ -495,102 +473,132 @@ static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint3
     g.ny = ny;
     g.nx = nx;
     g.vec = nx % v16 == 0 && dx % v16 == 0 && src_off % v16 == 0 && spitch % v16 == 0;
-    out.push_back(g);
+    out->push_back(g);
   };
-  for (size_t j = 0; j < planes.size(); ++j) {
-    const int b = planes[j].x, z = planes[j].y;
-    const psatd_box& B = P->boxes[b];
-    const int n0 = B.n[0], n1 = B.n[1];
-    // covered[y]: x intervals of row y fed by a block
-    std::vector<std::vector<std::pair<int, int>>> covered(n1);
-    for (int bi : by_dst[b]) {
-      const CopyBlk& c = P->blocks[bi];
-      if (z < c.dst_lo[2] || z >= c.dst_lo[2] + c.ext[2]) continue;
-      const psatd_box& S = P->boxes[c.src_box];
-      const int64_t off = P->hboxes[c.src_box].foff +
-                          ((int64_t)(c.src_lo[2] + z - c.dst_lo[2]) * S.n[1] + c.src_lo[1]) * S.n[0] + c.src_lo[0];
-      emit(off, S.n[0], c.dst_lo[1], c.dst_lo[0], c.ext[1], c.ext[0]);
-      for (int y = c.dst_lo[1]; y < c.dst_lo[1] + c.ext[1]; ++y) covered[y].push_back({c.dst_lo[0], c.dst_lo[0] + c.ext[0]});
-    }
-    // the rest of each row from the box itself; equal consecutive rows merge
-    auto gaps = [&](int y) {
-      auto iv = covered[y];
-      std::sort(iv.begin(), iv.end());
-      std::vector<std::pair<int, int>> g;
-      int x = 0;
-      for (const auto& v : iv) {
-        if (v.first > x) g.push_back({x, v.first});
-        x = std::max(x, v.second);
-      }
-      if (x < n0) g.push_back({x, n0});
-      return g;
-    };
-    const int64_t base = P->hboxes[b].foff + (int64_t)z * n1 * n0;
-    int y0 = 0;
-    std::vector<std::pair<int, int>> cur = gaps(0);
-    for (int y = 1; y <= n1; ++y) {
-      std::vector<std::pair<int, int>> nx = y < n1 ? gaps(y) : std::vector<std::pair<int, int>>{{-1, -1}};
-      if (y < n1 && nx == cur) continue;
-      for (const auto& g : cur) emit(base + (int64_t)y0 * n0 + g.first, n0, y0, g.first, y - y0, g.second - g.first);
-      y0 = y;
-      cur.swap(nx);
-    }
-    start[j + 1] = (int)out.size();
+  const psatd_box& B = boxes[b];
+  const int n0 = B.n[0], n1 = B.n[1];
+  // covered[y]: x intervals of row y fed by a block
+  std::vector<std::vector<std::pair<int, int>>> covered(n1);
+  for (int bi : by_dst[b]) {
+    const CopyBlk& c = blocks[bi];
+    if (z < c.dst_lo[2] || z >= c.dst_lo[2] + c.ext[2]) continue;
+    const psatd_box& S = boxes[c.src_box];
+    const int64_t off =
+        foff[c.src_box] + ((int64_t)(c.src_lo[2] + z - c.dst_lo[2]) * S.n[1] + c.src_lo[1]) * S.n[0] + c.src_lo[0];
+    emit(off, S.n[0], c.dst_lo[1], c.dst_lo[0], c.ext[1], c.ext[0]);
+    for (int y = c.dst_lo[1]; y < c.dst_lo[1] + c.ext[1]; ++y) covered[y].push_back({c.dst_lo[0], c.dst_lo[0] + c.ext[0]});
   }
-  P->gseg_start.swap(start);
-  P->gsegs.swap(out);
-  P->deferred = reg;
-  // the 3 x 3 grid form of every plane, when each one has it
-  std::vector<GatherGrid> grids(planes.size());
-  for (size_t j = 0; j < planes.size(); ++j) {
-    const psatd_box& B = P->boxes[planes[j].x];
-    std::vector<int> xs{0, B.n[0]}, ys{0, B.n[1]};
-    bool vec = true;
-    for (int i = P->gseg_start[j]; i < P->gseg_start[j + 1]; ++i) {
-      const GatherSeg& g = P->gsegs[i];
-      xs.push_back(g.dx);
-      xs.push_back(g.dx + g.nx);
-      ys.push_back(g.dy);
-      ys.push_back(g.dy + g.ny);
-      vec = vec && g.vec;
+  auto gaps = [&](int y) {
+    auto iv = covered[y];
+    std::sort(iv.begin(), iv.end());
+    std::vector<std::pair<int, int>> g;
+    int x = 0;
+    for (const auto& v : iv) {
+      if (v.first > x) g.push_back({x, v.first});
+      x = std::max(x, v.second);
     }
-    for (auto* v : {&xs, &ys}) {
-      std::sort(v->begin(), v->end());
-      v->erase(std::unique(v->begin(), v->end()), v->end());
-    }
-    if (!vec || xs.size() > 4 || ys.size() > 4) {   // register planes keep the rectangle lists
-      if (!reg) P->gsegs.clear(), P->gseg_start.clear();
-      return;
-    }
-    while (xs.size() < 4) xs.push_back(B.n[0]);
-    while (ys.size() < 4) ys.push_back(B.n[1]);
-    GatherGrid gg{};
-    gg.x1 = xs[1];
-    gg.x2 = xs[2];
-    gg.y1 = ys[1];
-    gg.y2 = ys[2];
-    for (int iy = 0; iy < 3; ++iy)
-      for (int ix = 0; ix < 3; ++ix) {
-        if (ys[iy] == ys[iy + 1] || xs[ix] == xs[ix + 1]) continue;   // empty cell
-        bool found = false;
-        for (int i = P->gseg_start[j]; i < P->gseg_start[j + 1] && !found; ++i) {
-          const GatherSeg& g = P->gsegs[i];
-          if (g.dy <= ys[iy] && ys[iy + 1] <= g.dy + g.ny && g.dx <= xs[ix] && xs[ix + 1] <= g.dx + g.nx) {
-            gg.base[3 * iy + ix] = g.src_off + (int64_t)(ys[iy] - g.dy) * g.spitch + (xs[ix] - g.dx);
-            gg.pitch[3 * iy + ix] = g.spitch;
-            found = true;
-          }
-        }
-        if (!found) {
-          if (!reg) P->gsegs.clear(), P->gseg_start.clear();
-          return;
+    if (x < n0) g.push_back({x, n0});
+    return g;
+  };
+  const int64_t base = foff[b] + (int64_t)z * n1 * n0;
+  int y0 = 0;
+  std::vector<std::pair<int, int>> cur = gaps(0);
+  for (int y = 1; y <= n1; ++y) {
+    std::vector<std::pair<int, int>> nx = y < n1 ? gaps(y) : std::vector<std::pair<int, int>>{{-1, -1}};
+    if (y < n1 && nx == cur) continue;
+    for (const auto& g : cur) emit(base + (int64_t)y0 * n0 + g.first, n0, y0, g.first, y - y0, g.second - g.first);
+    y0 = y;
+    cur.swap(nx);
+  }
+}
+
+// The 3 x 3 grid form of a plane's rectangles (n0 x n1 plane), or false when
+// the plane splits into more bands or a rectangle is not in 16-byte units.
+static bool plane_grid(const GatherSeg* segs, int ns, int n0, int n1, GatherGrid* out) {
+  std::vector<int> xs{0, n0}, ys{0, n1};
+  for (int i = 0; i < ns; ++i) {
+    if (!segs[i].vec) return false;
+    xs.push_back(segs[i].dx);
+    xs.push_back(segs[i].dx + segs[i].nx);
+    ys.push_back(segs[i].dy);
+    ys.push_back(segs[i].dy + segs[i].ny);
+  }
+  for (auto* v : {&xs, &ys}) {
+    std::sort(v->begin(), v->end());
+    v->erase(std::unique(v->begin(), v->end()), v->end());
+  }
+  if (xs.size() > 4 || ys.size() > 4) return false;
+  while (xs.size() < 4) xs.push_back(n0);
+  while (ys.size() < 4) ys.push_back(n1);
+  GatherGrid gg{};
+  gg.x1 = xs[1];
+  gg.x2 = xs[2];
+  gg.y1 = ys[1];
+  gg.y2 = ys[2];
+  for (int iy = 0; iy < 3; ++iy)
+    for (int ix = 0; ix < 3; ++ix) {
+      if (ys[iy] == ys[iy + 1] || xs[ix] == xs[ix + 1]) continue;   // empty cell
+      bool found = false;
+      for (int i = 0; i < ns && !found; ++i) {
+        const GatherSeg& g = segs[i];
+        if (g.dy <= ys[iy] && ys[iy + 1] <= g.dy + g.ny && g.dx <= xs[ix] && xs[ix + 1] <= g.dx + g.nx) {
+          gg.base[3 * iy + ix] = g.src_off + (int64_t)(ys[iy] - g.dy) * g.spitch + (xs[ix] - g.dx);
+          gg.pitch[3 * iy + ix] = g.spitch;
+          found = true;
         }
       }
-    grids[j] = gg;
+      if (!found) return false;
+    }
+  *out = gg;
+  return true;
+}
+
+// Deferred guard exchange.  When every box runs on the register plane kernels
+// (every guard block fed by an inverse plane pass) or every box on the pencil
+// kernels (guard blocks stored by the step's exchange kernel), a step need
+// not store its guard cells: the next step's forward x pass reads every guard
+// cell straight from the interior cell that owns it, which is the value the
+// exchange would have stored there, and only the last step of a push stores
+// the guards.  Register plane plans keep rectangle lists where a plane is not
+// a 3 x 3 grid; pencil plans take the grid form only.
+static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint32_t flags) {
+  P->deferred = false;
+  const int nb = (int)P->boxes.size();
+  const bool reg = P->reg_code >= 0 && !P->plane_fwd.empty() && !P->segs.empty() && P->step_tiles.empty() &&
+                   P->g_rows.empty() && P->pen_rows.empty() &&
+                   std::all_of(box_fast.begin(), box_fast.end(), [](char f) { return f != 0; });
+  const bool pen = P->pen_boxes == nb && !P->step_tiles.empty();
+  if ((flags & PSATD_EAGER_EXCHANGE) || !(reg || pen)) return;
+  std::vector<int64_t> foff(nb);
+  for (int b = 0; b < nb; ++b) foff[b] = P->hboxes[b].foff;
+  std::vector<std::vector<int>> by_dst(nb);
+  for (int i = 0; i < (int)P->blocks.size(); ++i)
+    if (P->blocks[i].src_box >= 0) by_dst[P->blocks[i].dst_box].push_back(i);
+  const int v16 = 16 / (int)P->rsize;
+  // every plane of every box, box-major (for register plane plans, the
+  // forward plane jobs themselves)
+  std::vector<GatherSeg> segs;
+  std::vector<int> start{0};
+  std::vector<GatherGrid> grids;
+  bool all_grid = true;
+  for (int b = 0; b < nb; ++b)
+    for (int z = 0; z < P->boxes[b].n[2]; ++z) {
+      plane_segs(P->boxes, foff, P->blocks, by_dst, b, z, v16, &segs);
+      GatherGrid gg{};
+      if (all_grid)
+        all_grid = plane_grid(segs.data() + start.back(), (int)segs.size() - start.back(), P->boxes[b].n[0],
+                              P->boxes[b].n[1], &gg);
+      grids.push_back(gg);
+      start.push_back((int)segs.size());
+    }
+  if (all_grid) {
+    P->ggrid.swap(grids);
+  } else if (reg) {
+    P->gseg_start.swap(start);
+    P->gsegs.swap(segs);
+  } else {
+    return;
   }
-  P->ggrid.swap(grids);
-  P->gsegs.clear();
-  P->gseg_start.clear();
   P->deferred = true;
 }
 
@@ -1237,6 +1245,55 @@ psatd_status psatd_exchange_blocks(const psatd_plan_desc* desc, psatd_copy_block
         o.ext[a] = b[i].ext[a];
       }
     }
+    return PSATD_OK;
+  } catch (...) {
+    return fail(nullptr, PSATD_ERR_INVALID_ARG, "internal error");
+  }
+}
+
+psatd_status psatd_plane_gather(const psatd_plan_desc* desc, int32_t box, int32_t z, int32_t* src_box,
+                                int64_t* src_cell, int32_t* is_grid) {
+  try {
+    if (!src_box || !src_cell || !is_grid) return fail(nullptr, PSATD_ERR_INVALID_ARG, "NULL output");
+    Err e = validate(desc);
+    if (e.st != PSATD_OK) return fail(nullptr, e.st, e.msg);
+    if (box < 0 || box >= desc->num_boxes || z < 0 || z >= desc->boxes[box].n[2])
+      return fail(nullptr, PSATD_ERR_INVALID_ARG, "box or plane out of range");
+    const int nb = desc->num_boxes;
+    const std::vector<psatd_box> boxes(desc->boxes, desc->boxes + nb);
+    // box offsets in a field buffer, as the plan lays them out
+    std::vector<int64_t> foff(nb + 1, 0);
+    for (int b = 0; b < nb; ++b)
+      foff[b + 1] = foff[b] + align_up((int64_t)boxes[b].n[0] * boxes[b].n[1] * boxes[b].n[2], 64);
+    const std::vector<CopyBlk> blocks = build_blocks(desc);
+    std::vector<std::vector<int>> by_dst(nb);
+    for (int i = 0; i < (int)blocks.size(); ++i)
+      if (blocks[i].src_box >= 0) by_dst[blocks[i].dst_box].push_back(i);
+    std::vector<GatherSeg> segs;
+    plane_segs(boxes, foff, blocks, by_dst, box, z, desc->precision == 32 ? 4 : 2, &segs);
+    const int n0 = boxes[box].n[0], n1 = boxes[box].n[1];
+    GatherGrid gg{};
+    const bool grid = plane_grid(segs.data(), (int)segs.size(), n0, n1, &gg);
+    *is_grid = grid ? 1 : 0;
+    for (int y = 0; y < n1; ++y)
+      for (int x = 0; x < n0; ++x) {
+        int64_t off = -1;
+        if (grid) {
+          const int iy = (y >= gg.y1) + (y >= gg.y2), ix = (x >= gg.x1) + (x >= gg.x2);
+          const int ylo = iy == 0 ? 0 : iy == 1 ? gg.y1 : gg.y2, xlo = ix == 0 ? 0 : ix == 1 ? gg.x1 : gg.x2;
+          off = gg.base[3 * iy + ix] + (int64_t)(y - ylo) * gg.pitch[3 * iy + ix] + (x - xlo);
+        } else {
+          for (const GatherSeg& g : segs)
+            if (y >= g.dy && y < g.dy + g.ny && x >= g.dx && x < g.dx + g.nx) {
+              off = g.src_off + (int64_t)(y - g.dy) * g.spitch + (x - g.dx);
+              break;
+            }
+        }
+        if (off < 0) return fail(nullptr, PSATD_ERR_INVALID_ARG, "internal error: uncovered cell");
+        const int sb = (int)(std::upper_bound(foff.begin(), foff.end(), off) - foff.begin()) - 1;
+        src_box[(int64_t)y * n0 + x] = sb;
+        src_cell[(int64_t)y * n0 + x] = off - foff[sb];
+      }
     return PSATD_OK;
   } catch (...) {
     return fail(nullptr, PSATD_ERR_INVALID_ARG, "internal error");
