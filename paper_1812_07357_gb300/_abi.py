@@ -182,8 +182,11 @@ def psatd_plane_gather(desc: psatd_plan_desc, box: int, z: int):
     """Host-only: (src_box, src_cell, is_grid) of plane z of `box` under the
     deferred guard exchange; the arrays have shape (n1, n0)."""
     import numpy as np
-    b = desc.boxes[box]
-    n0, n1 = int(b.n[0]), int(b.n[1])
+    if 0 <= box < desc.num_boxes:
+        b = desc.boxes[box]
+        n0, n1 = int(b.n[0]), int(b.n[1])
+    else:
+        n0 = n1 = 1          # the call reports the bad index without writing
     sb = np.empty(n0 * n1, dtype=np.int32)
     sc = np.empty(n0 * n1, dtype=np.int64)
     g = c_int32(0)
