@@ -42,6 +42,16 @@ def test_kernel_bytes_fast_path():
     assert kb[1] == kb[3] == 0
     # without the fused exchange the inverse kernel writes no guard cells
     assert bench.kernel_bytes(lay, fused=False)["fast"][4] == kb[4] - 6 * lay.guard_cells * 4
+    # deferred exchange timed over a 20-step push: one guard-storing launch in 20
+    kd = bench.kernel_bytes(lay, fused=True, guard_frac=1 / 20)["fast"]
+    assert kd[4] == pytest.approx(kb[4] - 6 * lay.guard_cells * 4 * 19 / 20)
+    assert kd[0] == kb[0] and kd[2] == kb[2]     # the forward pass reads every padded cell either way
+
+
+def test_inverse_bytes_of_a_middle_step_at_full_size():
+    # 6 x (8 x 49 x 96 x 64 x 512 spectrum in + 4 x 512^3 interior out)
+    lay = bench.build_layout("local_512")
+    assert bench.kernel_bytes(lay, guard_frac=0.0)["fast"][4] == 10_619_977_728
 
 
 def _rank_main(rank, world, port, out_dir):
