@@ -197,6 +197,17 @@ def build_layout(name):
     return I.hybrid_layout(w["global_n"], w["nsub"], w["ng"], w["p"])
 
 
+def workload_config(name, lay, w, world):
+    """The ``config`` object of a line: the workload alone (both arms)."""
+    return {"workload": name, "decomposition": lay.kind,
+            "global_n": list(lay.global_n), "boxes": len(lay.boxes),
+            "box_n": list(lay.boxes[0].n), "ng": lay.boxes[0].ng_lo[0],
+            "order_p": lay.boxes[0].p, "dt": w["dt"], "tables": "f64-generated",
+            "interior_cells": lay.interior_cells, "padded_cells": lay.cells,
+            "l2": "inputs larger than L2 (%.1f GB of fields)" % (6 * lay.cells * 4 / 1e9),
+            "parallelism": "replicas" if world > 1 else "1 GPU"}
+
+
 def kernel_bytes(layout, s=4, fin=6, fout=6, fused=True, guard_frac=1.0):
     """Compulsory bytes of one launch of every kernel kind (each kernel reads
     its inputs once and writes its outputs once).  Kinds: forward x(+y),
@@ -389,17 +400,16 @@ def run_gpu(args):
 
     plan.push(fields, None, args.warmup)
     plan.sync()
-    A.psatd_plan_set_timing(plan.handle, True)
-    A.psatd_plan_kernel_times(plan.handle)   # discard warm-up records
 
     clocks = ClockSampler(local).start() if rank == 0 else None
     barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    # the K timed steps are one push (with the deferred exchange, each step's
-    # guard exchange is done by the next step's forward gather; the last step
-    # stores the guards)
+    # the K timed steps are one push, launched as the product runs it (one
+    # replayed CUDA graph per step variant; with the deferred exchange each
+    # step's guard exchange is done by the next step's forward gather and the
+    # last step stores the guards)
     with torch.cuda.stream(stream):
         e0.record(stream)
         plan.push(fields, None, args.steps)
@@ -408,10 +418,16 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1)
-    clk = clocks.stop() if clocks else None
+    ms_max = reduce_max(ms, dev if world > 1 else None)
+    # per-kernel device times: a second push of the same K steps with CUDA
+    # events recorded around every launch on the plan's stream (direct
+    # launches; the kernels are the same as in the graph)
+    A.psatd_plan_set_timing(plan.handle, True)
+    A.psatd_plan_kernel_times(plan.handle)
+    plan.push(fields, None, args.steps)
     kms, kn = A.psatd_plan_kernel_times(plan.handle)
     A.psatd_plan_set_timing(plan.handle, False)
-    ms_max = reduce_max(ms, dev if world > 1 else None)
+    clk = clocks.stop() if clocks else None
 
     interior = lay.interior_cells
     value = total_units(interior * args.steps, world) / (ms_max / 1e3)
@@ -430,27 +446,24 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "decomposition": lay.kind,
-                   "global_n": list(lay.global_n), "boxes": len(lay.boxes),
-                   "box_n": list(lay.boxes[0].n), "ng": lay.boxes[0].ng_lo[0],
-                   "order_p": lay.boxes[0].p, "dt": w["dt"], "tables": "f64-generated",
-                   "interior_cells": interior, "padded_cells": lay.cells,
-                   "l2": "inputs larger than L2 (%.1f GB of fields)" % (6 * lay.cells * 4 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "fast_boxes": plan.fast_boxes,
-                   "guard_exchange": "deferred into the next step's forward gather; guards stored by the last step"
-                                     if plan.deferred_exchange else "stored every step"},
+        "config": workload_config(args.workload, lay, w, world),
+        "plan": {"fast_boxes": plan.fast_boxes,
+                 "guard_exchange": "deferred into the next step's forward gather; guards stored by the last step"
+                                   if plan.deferred_exchange else "stored every step"},
         "roofline": {"bound": "hbm", "kernel": A.KERNEL_NAMES[dom], "achieved": ach,
                      "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": kb[dom], "avg_launch_ms": avg[dom],
-                     "peak_source": peak_src},
+                     "peak_source": peak_src,
+                     "step_frac": sab / (step_ms / 1e3) / 1e9 / peak},
         "step_roofline": {"algorithmic_bytes_per_step": sab,
                           "achieved": sab / (step_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                          "frac": sab / (step_ms / 1e3) / 1e9 / peak},
+                          "frac": sab / (step_ms / 1e3) / 1e9 / peak, "peak_source": peak_src},
         "kernels": {A.KERNEL_NAMES[i]: {"launches": kn[i], "total_ms": kms[i], "avg_ms": avg[i],
                                         "bytes_per_launch": kb[i],
-                                        "gbps": (kb[i] / (avg[i] / 1e3) / 1e9) if avg[i] else None}
+                                        "gbps": (kb[i] / (avg[i] / 1e3) / 1e9) if avg[i] else None,
+                                        "frac": (kb[i] / (avg[i] / 1e3) / 1e9 / peak) if avg[i] else None}
                     for i in range(len(kms))},
+        "kernel_timing": "second push of the same K steps, CUDA events around every launch on the plan's stream",
         "gpu_launches": launches,
         "clocks": clk,
         "memory": dict(zip(("field_bytes", "workspace_bytes"), A.psatd_plan_memory(plan.handle))),
@@ -497,35 +510,40 @@ def run_e2e(plan, fields, args, lay, world):
             "steps": args.e2e_steps, "ms_per_step": ms / args.e2e_steps}
 
 
-def run_fp64_plain(lay, w, fac, nbox=2, nsteps=3):
-    """Plain FP64 GPU push: same kernels in double, one box per plan (no
-    batching), on a sample of boxes of the same workload."""
+def run_fp64_plain(lay, w, fac, nsteps=2):
+    """Plain FP64 GPU push: the same kernels in double, one box per push call
+    (no batching), over every box of the workload.  All boxes share one shape,
+    so one single-box plan (self-periodic box, direct launches) pushes each
+    box's own field buffers in turn; the timed region covers all boxes."""
     import torch
     from paper_1812_07357_gb300 import inputs as I
     from paper_1812_07357_gb300.solver import Plan
-    tot_ms = 0.0
-    cells = 0
-    for b in range(nbox):
-        box = lay.boxes[b]
-        sub = I.Layout("independent", (0, 0, 0), (1, 1, 1), [box])
-        plan = Plan(sub, (1.0,) * 3, w["dt"], precision=64, sources="vacuum")
-        f = {k: plan.pack_separable([fac[k][b]] if fac[k] is not None else None)
-             for k in I.COMPONENTS}
-        plan.push(f, None, 1)
-        plan.sync()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(plan.stream):
-            e0.record(plan.stream)
+    box = lay.boxes[0]
+    assert all(b.n == box.n and b.p == box.p for b in lay.boxes)
+    sub = I.Layout("independent", (0, 0, 0), (1, 1, 1), [box])
+    plan = Plan(sub, (1.0,) * 3, w["dt"], precision=64, sources="vacuum", no_graph=True)
+    per_box = []
+    for b in range(len(lay.boxes)):
+        per_box.append({k: plan.pack_separable([fac[k][b]] if fac[k] is not None else None)
+                        for k in I.COMPONENTS})
+    plan.push(per_box[0], None, 1)
+    plan.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(plan.stream):
+        e0.record(plan.stream)
+        for f in per_box:
             plan.push(f, None, nsteps)
-            e1.record(plan.stream)
-        torch.cuda.synchronize()
-        tot_ms += e0.elapsed_time(e1)
-        cells += box.interior_cells * nsteps
-        plan.close()
-    return {"value": cells / (tot_ms / 1e3), "unit": UNIT,
-            "sample": f"{nbox} boxes x {nsteps} steps, FP64, one box per plan (unbatched); "
-                      "guard exchange of a self-periodic box"}
+        e1.record(plan.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    cells = sum(b.interior_cells for b in lay.boxes) * nsteps
+    plan.close()
+    del per_box
+    torch.cuda.empty_cache()
+    return {"value": cells / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / nsteps,
+            "sample": f"all {len(lay.boxes)} boxes x {nsteps} steps, FP64, one box per push call "
+                      "(unbatched, direct launches); guard exchange of a self-periodic box"}
 
 
 def oracle_sample(lay, w, fac, target_s=12.0, max_boxes=64):
@@ -553,9 +571,9 @@ def oracle_sample(lay, w, fac, target_s=12.0, max_boxes=64):
         done += 1
         cells += box.interior_cells
     dt = time.perf_counter() - t0
-    return {"value": cells / dt, "unit": UNIT, "cores": O._WORKERS, "kind": "oracle",
-            "sample": f"{done} of {len(lay.boxes)} boxes x 1 step (S1-S3 per box, FP64 numpy/"
-                      f"scipy.fft oracle), {dt:.1f} s"}
+    return {"value": cells / dt, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+            "sample": f"{done} of {len(lay.boxes)} boxes x 1 step (S1-S3 per box, FP64 C++ oracle "
+                      f"with its own FFT, OpenMP), {dt:.1f} s"}
 
 
 def kernel_source_digest():
@@ -611,14 +629,13 @@ def run_reference(args):
     cells = lay.boxes[0].interior_cells * args.steps
     value = cells / dt
     cb = {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
-          "sample": f"1 of {len(lay.boxes)} boxes per step (S1-S3 of one box, FP64 oracle)"}
+          "sample": f"1 of {len(lay.boxes)} boxes per step (S1-S3 of one box, FP64 C++ oracle, "
+                    f"{vals[0]['cores']} OpenMP threads)"}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "impl": "reference",
-           "config": {"workload": args.workload, "decomposition": lay.kind,
-                      "boxes": len(lay.boxes), "box_n": list(lay.boxes[0].n),
-                      "order_p": lay.boxes[0].p, "dt": w["dt"]},
+           "config": workload_config(args.workload, lay, w, world),
            "cpu_baseline": cb,
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)

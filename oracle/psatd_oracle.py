@@ -1,172 +1,182 @@
-"""FP64 reference implementation ("oracle") of the PSATD Maxwell push.
+"""FP64 reference implementation ("oracle") of the PSATD Maxwell push:
+Python interface to liboracle.so, built from oracle/psatd_oracle.cpp (plain
+C++, its own mixed-radix FFT, OpenMP over FFT lines and modes).
 
 TEST INFRASTRUCTURE.  Only the test-suite, the smoke check of the package
 entry point and the CPU-baseline leg of the benchmark import this module.  The
 product path (the CUDA library and its Python binding) never imports it, and
 this module imports nothing from the product package.
 
-What it computes (one step = advance every box, then exchange guards; paper
-Fig. 1 caption, steps (i) and (ii)):
+The method (paper Sec. 1.1 for PSATD, Sec. 1.3 and Fig. 1 for the local
+decomposition, Sec. 2.1 for the hybrid one), the readings of what the paper
+leaves unsaid (update equations, stencil, Yee positions, Fourier convention)
+and the FFT are stated in psatd_oracle.cpp.  This module only moves arrays
+in and out; the helpers that are not arithmetic of the method (error
+metrics, interior slices) and the paper's memory model (Sec. 2.2 eqs. (1)-(6),
+Sec. 2.3 eq. (7)) are plain Python.
 
-1. per box, a 3D FFT of every field component over the whole padded box
-   (guards included), the box being treated as periodic (Sec. 1.3: local
-   shared-memory FFTs on sub-domains padded with n_g guard cells);
-2. the per-mode analytical update of Maxwell's equations in Fourier space
-   (Sec. 1.1: PSATD, exact in time for every mode), with the derivative
-   replaced by the Fourier symbol of an order-p staggered finite-difference
-   stencil of width p/2 (Sec. 1.1; p -> infinity gives the pure spectral
-   operator) and Yee-staggered field positions;
-3. the inverse 3D FFT;
-4. the guard exchange: every guard cell receives the value of the interior
-   cell that owns the same global position (Fig. 1a/1b, step (ii)).
-
-The paper states the principle of PSATD but prints none of its equations
-(they are in its references).  The update used here is derived directly from
-Maxwell's equations with the current J held constant over the step:
-
-    dE/dt = c^2 (i K x B) - J/eps0,     dB/dt = -(i K x E),
-
-whose exact solution over dt, with K = |K|, theta = c K dt, C = cos(theta),
-
-    Sw = sin(theta)/(c K)         = dt * sinc(theta)
-    X1 = (1 - C)/K^2              = (c dt)^2/2 * sinc(theta/2)^2
-    X3 = (Sw - dt)/K^2            = c^2 dt^3 (sinc(theta) - 1)/theta^2
-
-is ("J form"):
-
-    E' = C E + X1 K (K.E) + i c^2 Sw K x B - Sw J/eps0 + X3 K (K.J)/eps0
-    B' = C B + X1 K (K.B) - i Sw K x E + i (X1/c^2) K x J/eps0
-
-The X1 K(K.E), X1 K(K.B) terms carry the longitudinal parts (E_L moves only
-with J_L, B_L is constant).  With charge density (the "rho form") rho is
-advanced by continuity, rho' = rho - i dt K.J, and E takes its longitudinal
-part from Gauss's law at the new time:
-
-    E' = C E + i c^2 Sw K x B - Sw J/eps0 + i K (Y1 rho' + Y2 rho)/eps0,
-    Y1 = X3/dt,  Y2 = -X1 - X3/dt.
-
-Both forms agree whenever Gauss's law holds at the start of the step.
-
-Fourier convention: forward transform unnormalised with exp(-2 pi i m j/N),
-inverse with 1/N; the derivative becomes +i K.  Index m of an axis of N
-cells maps to k = 2 pi m~/(N h) with m~ = m for m <= N/2, m - N otherwise
-(so the Nyquist index takes k = +pi/h).  A component sampled at offset s
-(in cells) is brought to the "centred" spectrum by exp(-i k.s h) before the
-update and back by exp(+i k.s h) afterwards.
+Array conventions: a box's array has shape (n_z, n_y, n_x) (x fastest in
+memory); a field is a dict component -> list of per-box arrays.
 """
 from __future__ import annotations
 
+import ctypes
 import math
 import os
-from fractions import Fraction
+import subprocess
 
 import numpy as np
-from scipy import fft as _fft
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "psatd_oracle.cpp")
+LIB = os.path.join(HERE, "liboracle.so")
 
 # Yee offsets (cells) of every component: E and J on edges, B on faces,
-# rho on nodes.
+# rho on nodes (the order of the C++ table).
 YEE = {
     "Ex": (0.5, 0.0, 0.0), "Ey": (0.0, 0.5, 0.0), "Ez": (0.0, 0.0, 0.5),
     "Bx": (0.0, 0.5, 0.5), "By": (0.5, 0.0, 0.5), "Bz": (0.5, 0.5, 0.0),
     "Jx": (0.5, 0.0, 0.0), "Jy": (0.0, 0.5, 0.0), "Jz": (0.0, 0.0, 0.5),
     "rho": (0.0, 0.0, 0.0),
 }
+COMPS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
+_FORMS = {"vacuum": 0, "J": 1, "rho": 2}
+_KINDS = {"global": 0, "local": 1, "hybrid": 2, "independent": 3}
 
-_WORKERS = int(os.environ.get("PSATD_ORACLE_THREADS", "0")) or (os.cpu_count() or 1)
 
+def build(force: bool = False) -> str:
+    """Compile liboracle.so next to its source (g++ -O2 -fopenmp)."""
+    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
+        return LIB
+    tmp = LIB + ".%d.tmp" % os.getpid()
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, SRC]
+    if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+        subprocess.run(cmd, check=True)          # no OpenMP runtime: one thread
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class _Box(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32 * 3), ("ng_lo", ctypes.c_int32 * 3), ("ng_hi", ctypes.c_int32 * 3),
+                ("origin", ctypes.c_int64 * 3), ("p", ctypes.c_int32)]
+
+
+class _Layout(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("global_n", ctypes.c_int32 * 3), ("periodic", ctypes.c_int32 * 3),
+                ("nbox", ctypes.c_int32), ("boxes", ctypes.POINTER(_Box))]
+
+
+_lib = None
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P, I32, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        lib.oracle_threads.restype = I32
+        lib.oracle_fft3.argtypes = [I32, I32, I32, I32, I32, P]
+        lib.oracle_weights.argtypes = [I32, I32, P]
+        lib.oracle_modified_wavenumber.argtypes = [I64, P, D, I32, I32, P]
+        lib.oracle_coefficients.argtypes = [I64, P, D, D, P, P, P, P]
+        lib.oracle_update_modes.argtypes = [I64, PP, PP, PP, P, PP, D, D, D, I32]
+        lib.oracle_exchange.argtypes = [ctypes.POINTER(_Layout), P]
+        lib.oracle_couple.argtypes = [ctypes.POINTER(_Layout), P, ctypes.POINTER(_Layout), P]
+        lib.oracle_push.argtypes = [ctypes.POINTER(_Layout), PP, PP, P, I32, P, D, D, D, I32, I32, I32, P]
+        for f in ("oracle_fft3", "oracle_weights", "oracle_modified_wavenumber", "oracle_coefficients",
+                  "oracle_update_modes", "oracle_exchange", "oracle_couple", "oracle_push"):
+            getattr(lib, f).restype = I32
+        _lib = lib
+    return _lib
+
+
+def threads() -> int:
+    """OpenMP threads the oracle uses (OMP_NUM_THREADS, else every core)."""
+    return int(_L().oracle_threads())
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle: {what} failed (code {rc})")
+
+
+# ----------------------------------------------------------------------------
+# FFT
+# ----------------------------------------------------------------------------
 
 def fft3(a):
-    """Unnormalised forward 3D DFT (library FFT as one step)."""
-    return _fft.fftn(a, workers=_WORKERS)
+    """Unnormalised forward 3D DFT of an (n_z, n_y, n_x) array."""
+    x = np.array(a, dtype=np.complex128, order="C", copy=True)
+    nz, ny, nx = x.shape
+    _check(_L().oracle_fft3(nx, ny, nz, -1, 64, _ptr(x)), "fft3")
+    return x
 
 
 def ifft3(a):
     """Inverse 3D DFT with the 1/N factor."""
-    return _fft.ifftn(a, workers=_WORKERS)
+    x = np.array(a, dtype=np.complex128, order="C", copy=True)
+    nz, ny, nx = x.shape
+    _check(_L().oracle_fft3(nx, ny, nz, 1, 64, _ptr(x)), "ifft3")
+    return x / x.size
+
+
+def fft3_f32(a):
+    """The same forward transform in FP32 arithmetic (the rounding model)."""
+    x = np.array(a, dtype=np.complex64, order="C", copy=True)
+    nz, ny, nx = x.shape
+    _check(_L().oracle_fft3(nx, ny, nz, -1, 32, _ptr(x)), "fft3")
+    return x
 
 
 # ----------------------------------------------------------------------------
-# Order-p staggered stencil (Sec. 1.1: order p, stencil of width p/2)
+# Stencil, wavenumbers, coefficients, per-mode update
 # ----------------------------------------------------------------------------
 
-def stencil_weights(p: int):
-    """Weights alpha_l, l = 1..p/2, of the order-p staggered centred difference
-
-        f'(x) ~ sum_l alpha_l [f(x + (2l-1)h/2) - f(x - (2l-1)h/2)] / ((2l-1) h).
-
-    Exactness to order h^p requires sum_l alpha_l (2l-1)^(2j) = delta_j0 for
-    j = 0..p/2-1, whose solution is the Lagrange basis of the nodes (2l-1)^2
-    evaluated at 0.  Computed in exact rational arithmetic.  p = 0 (infinite
-    order) has no stencil and returns None."""
+def _weights(p, nodal):
     if p == 0:
         return None
     if p < 2 or p % 2:
         raise ValueError("order p must be even and >= 2, or 0 for infinite")
-    q = p // 2
-    nodes = [(2 * l - 1) ** 2 for l in range(1, q + 1)]
-    out = []
-    for l in range(q):
-        a = Fraction(1)
-        for j in range(q):
-            if j != l:
-                a *= Fraction(nodes[j], nodes[j] - nodes[l])
-        out.append(a)
-    return out
+    out = np.zeros(p // 2)
+    _check(_L().oracle_weights(p, int(nodal), _ptr(out)), "weights")
+    return [float(v) for v in out]
 
 
-def modified_wavenumber(k, h: float, p: int):
-    """Fourier symbol K(k) of the order-p staggered difference (D f = i K f
-    in centred form); the pure spectral operator K = k for p = 0."""
-    k = np.asarray(k, dtype=np.float64)
-    if p == 0:
-        return k.copy()
-    K = np.zeros_like(k)
-    for l, a in enumerate(stencil_weights(p), start=1):
-        m = 2 * l - 1
-        K += float(a) * 2.0 * np.sin(m * k * h / 2.0) / (m * h)
-    return K
+def stencil_weights(p: int):
+    """alpha_l, l = 1..p/2, of the order-p staggered difference (floats);
+    None for infinite order (p = 0)."""
+    return _weights(p, False)
 
 
 def nodal_weights(p: int):
-    """Weights beta_l, l = 1..p/2, of the order-p centred difference on a
-    collocated (nodal) grid
+    """beta_l, l = 1..p/2, of the order-p centred nodal difference."""
+    return _weights(p, True)
 
-        f'(x) ~ sum_l beta_l [f(x + l h) - f(x - l h)] / (2 l h),
 
-    exact to order h^p: sum_l beta_l l^(2j) = delta_j0 for j = 0..p/2-1, the
-    Lagrange basis of the nodes l^2 evaluated at 0 (exact rationals).  This
-    variant (all components at the cell nodes, no Yee shifts) is not in the
-    paper, which uses staggered stencils; p = 0 returns None."""
-    if p == 0:
-        return None
-    if p < 2 or p % 2:
-        raise ValueError("order p must be even and >= 2, or 0 for infinite")
-    q = p // 2
-    out = []
-    for l in range(1, q + 1):
-        b = Fraction(1)
-        for j in range(1, q + 1):
-            if j != l:
-                b *= Fraction(j * j, j * j - l * l)
-        out.append(b)
-    return out
+def _mw(k, h, p, nodal):
+    k = np.asarray(k, dtype=np.float64)
+    flat = np.ascontiguousarray(k.ravel())
+    out = np.zeros_like(flat)
+    _check(_L().oracle_modified_wavenumber(flat.size, _ptr(flat), float(h), int(p), int(nodal), _ptr(out)),
+           "modified_wavenumber")
+    out = out.reshape(k.shape)
+    return float(out) if out.ndim == 0 else out
+
+
+def modified_wavenumber(k, h: float, p: int):
+    """Fourier symbol K(k) of the order-p staggered difference."""
+    return _mw(k, h, p, False)
 
 
 def modified_wavenumber_nodal(k, h: float, p: int):
-    """Fourier symbol K(k) = sum_l beta_l sin(l k h)/(l h) of the order-p
-    centred nodal difference (D f = i K f); K = k for p = 0 except at the
-    Nyquist wavenumber |k| = pi/h, where K = 0: on a collocated grid the
-    Nyquist mode is its own mirror image (k = -k), so only K = 0 keeps the
-    derivative of a real field real (finite p gives 0 there by itself)."""
-    k = np.asarray(k, dtype=np.float64)
-    if p == 0:
-        K = k.copy()
-        K[np.isclose(np.abs(k * h), np.pi, rtol=0, atol=1e-12)] = 0.0
-        return K
-    K = np.zeros_like(k)
-    for l, b in enumerate(nodal_weights(p), start=1):
-        K += float(b) * np.sin(l * k * h) / (l * h)
-    return K
+    """Fourier symbol K(k) of the order-p centred nodal difference (K = 0 at
+    the Nyquist wavenumber for infinite order)."""
+    return _mw(k, h, p, True)
 
 
 def axis_wavenumbers(n: int, h: float):
@@ -176,257 +186,155 @@ def axis_wavenumbers(n: int, h: float):
     return 2.0 * np.pi * mt / (n * h)
 
 
-# ----------------------------------------------------------------------------
-# Per-mode coefficients and update (Sec. 1.1, PSATD)
-# ----------------------------------------------------------------------------
-
-def _sinc(x):
-    x = np.asarray(x, dtype=np.float64)
-    out = np.ones_like(x)
-    nz = x != 0
-    out[nz] = np.sin(x[nz]) / x[nz]
-    return out
-
-
 def coefficients(K2, c: float, dt: float):
-    """C, Sw, X1, X3 of the module docstring as functions of K^2.
-
-    1 - C is evaluated as 2 sin^2(theta/2) (through sinc(theta/2)) so that it
-    keeps full relative precision at small theta; (sinc(theta) - 1)/theta^2
-    uses its Taylor series below theta = 0.1, where the difference would
-    cancel, and takes the value -1/6 at K = 0."""
-    K2 = np.asarray(K2, dtype=np.float64)
-    th = c * dt * np.sqrt(K2)
-    C = np.cos(th)
-    Sw = dt * _sinc(th)
-    X1 = 0.5 * (c * dt) ** 2 * _sinc(0.5 * th) ** 2
-    t2 = th * th
-    small = np.abs(th) < 0.1
-    g = np.empty_like(th)
-    # (sinc(t) - 1)/t^2 = sum_{j>=1} (-1)^j t^(2j-2)/(2j+1)!
-    ts = t2[small]
-    g[small] = (-1.0 / 6 + ts * (1.0 / 120 + ts * (-1.0 / 5040 + ts * (1.0 / 362880
-               + ts * (-1.0 / 39916800)))))
-    big = ~small
-    g[big] = (np.sin(th[big]) / th[big] - 1.0) / t2[big]
-    X3 = c * c * dt ** 3 * g
-    return C, Sw, X1, X3
+    """C, Sw, X1, X3 as functions of K^2."""
+    K2 = np.ascontiguousarray(np.asarray(K2, dtype=np.float64).ravel())
+    outs = [np.zeros_like(K2) for _ in range(4)]
+    _check(_L().oracle_coefficients(K2.size, _ptr(K2), float(c), float(dt), *[_ptr(o) for o in outs]),
+           "coefficients")
+    return tuple(outs)
 
 
-def _cross(a, b):
-    return (a[1] * b[2] - a[2] * b[1],
-            a[2] * b[0] - a[0] * b[2],
-            a[0] * b[1] - a[1] * b[0])
-
-
-def _dot(a, b):
-    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
+def _pp(arrs):
+    return (ctypes.c_void_p * len(arrs))(*[a.ctypes.data for a in arrs])
 
 
 def update_modes(E, B, J, R, K, dt, c=1.0, eps0=1.0, form="vacuum"):
-    """Advance centred spectra by one step of dt.
-
-    E, B: 3-tuples of complex arrays; J: 3-tuple or None; R: rho array or
-    None; K: 3-tuple of real arrays (modified wavenumber components).
-    form: 'vacuum' (J = rho = 0), 'J' (J form) or 'rho' (rho form).
-    Returns (E', B', rho') with rho' None unless form == 'rho'."""
-    K2 = _dot(K, K)
-    C, Sw, X1, X3 = coefficients(K2, c, dt)
-    KxB = _cross(K, B)
-    KxE = _cross(K, E)
-    KdB = _dot(K, B)
-    Bn = [C * B[d] + X1 * K[d] * KdB - 1j * Sw * KxE[d] for d in range(3)]
-    if form == "rho":
-        KdJ = _dot(K, J)
-        Rn = R - 1j * dt * KdJ
-        Y1 = X3 / dt
-        Y2 = -X1 - X3 / dt
-        En = [C * E[d] + 1j * c * c * Sw * KxB[d] - Sw * J[d] / eps0
-              + 1j * K[d] * (Y1 * Rn + Y2 * R) / eps0 for d in range(3)]
-    else:
-        KdE = _dot(K, E)
-        En = [C * E[d] + X1 * K[d] * KdE + 1j * c * c * Sw * KxB[d] for d in range(3)]
-        Rn = None
-        if form == "J":
-            KdJ = _dot(K, J)
-            En = [En[d] - Sw * J[d] / eps0 + X3 * K[d] * KdJ / eps0 for d in range(3)]
-        elif form != "vacuum":
-            raise ValueError(form)
-    if form in ("J", "rho"):
-        KxJ = _cross(K, J)
-        Bn = [Bn[d] + 1j * (X1 / (c * c)) * KxJ[d] / eps0 for d in range(3)]
-    return En, Bn, Rn
-
-
-def _box_k(shape_zyx, h, p, nodal=False):
-    """Broadcastable (k, K) grids for a box: true and modified wavenumbers."""
-    nz, ny, nx = shape_zyx
-    kx = axis_wavenumbers(nx, h[0])[None, None, :]
-    ky = axis_wavenumbers(ny, h[1])[None, :, None]
-    kz = axis_wavenumbers(nz, h[2])[:, None, None]
-    mw = modified_wavenumber_nodal if nodal else modified_wavenumber
-    Kx = mw(kx, h[0], p)
-    Ky = mw(ky, h[1], p)
-    Kz = mw(kz, h[2], p)
-    return (kx, ky, kz), (Kx, Ky, Kz)
-
-
-def _shift(k, comp, h, sign, nodal=False):
-    if nodal:                     # every component at the cell nodes
-        return 1.0
-    s = YEE[comp]
-    return np.exp(sign * 1j * (k[0] * s[0] * h[0] + k[1] * s[1] * h[1] + k[2] * s[2] * h[2]))
-
-
-def push_box(f, src, h, p, dt, c=1.0, eps0=1.0, form="vacuum", return_imag=False, nodal=False):
-    """One PSATD step on one periodic box.
-
-    f: dict Ex..Bz -> (nz, ny, nx) float64 arrays; src: dict Jx, Jy, Jz[, rho]
-    or None.  Returns a new dict (with 'rho' when form == 'rho').  nodal: the
-    collocated variant (nodal_weights, no Yee shifts)."""
-    shape = f["Ex"].shape
-    k, K = _box_k(shape, h, p, nodal)
-    cen = lambda a, comp: fft3(a) * _shift(k, comp, h, -1.0, nodal)
-    E = tuple(cen(f[c_], c_) for c_ in ("Ex", "Ey", "Ez"))
-    B = tuple(cen(f[c_], c_) for c_ in ("Bx", "By", "Bz"))
-    J = R = None
-    if form in ("J", "rho"):
-        J = tuple(cen(src[c_], c_) for c_ in ("Jx", "Jy", "Jz"))
-    if form == "rho":
-        R = cen(src["rho"], "rho")
-    En, Bn, Rn = update_modes(E, B, J, R, K, dt, c, eps0, form)
-    out, imag = {}, 0.0
-    for comp, a in zip(("Ex", "Ey", "Ez", "Bx", "By", "Bz"), list(En) + list(Bn)):
-        r = ifft3(a * _shift(k, comp, h, +1.0, nodal))
-        imag = max(imag, float(np.abs(r.imag).max()))
-        out[comp] = r.real.copy()
-    if Rn is not None:
-        r = ifft3(Rn)
-        imag = max(imag, float(np.abs(r.imag).max()))
-        out["rho"] = r.real.copy()
-    if return_imag:
-        return out, imag
-    return out
+    """Advance centred spectra by one step (3-tuples of complex arrays E, B,
+    J or None, R or None; K a 3-tuple of real arrays).  Returns (E', B', R')."""
+    shape = np.broadcast(*E, *B, *K).shape
+    cv = lambda a: np.ascontiguousarray(np.broadcast_to(a, shape), dtype=np.complex128).ravel().copy()
+    rv = lambda a: np.ascontiguousarray(np.broadcast_to(a, shape), dtype=np.float64).ravel().copy()
+    e = [cv(x) for x in E]
+    b = [cv(x) for x in B]
+    j = [cv(x) for x in J] if J is not None and form != "vacuum" else None
+    r = cv(R) if form == "rho" else None
+    k = [rv(x) for x in K]
+    n = e[0].size
+    _check(_L().oracle_update_modes(n, _pp(e), _pp(b), _pp(j) if j else None, _ptr(r) if r is not None else None,
+                                    _pp(k), float(dt), float(c), float(eps0), _FORMS[form]), "update_modes")
+    En = tuple(x.reshape(shape) for x in e)
+    Bn = tuple(x.reshape(shape) for x in b)
+    return En, Bn, (r.reshape(shape) if r is not None else None)
 
 
 # ----------------------------------------------------------------------------
-# Guard exchange (Fig. 1, step (ii); Sec. 2.1 for groups)
+# Layouts, push, exchange, coupling
 # ----------------------------------------------------------------------------
 
-def _interior_slices(box):
-    return tuple(slice(box.ng_lo[d], box.n[d] - box.ng_hi[d]) for d in (2, 1, 0))
+def _layout(layout):
+    nb = len(layout.boxes)
+    arr = (_Box * nb)()
+    for i, b in enumerate(layout.boxes):
+        arr[i].n[:] = list(b.n)
+        arr[i].ng_lo[:] = list(b.ng_lo)
+        arr[i].ng_hi[:] = list(b.ng_hi)
+        arr[i].origin[:] = list(b.origin)
+        arr[i].p = int(b.p)
+    L = _Layout()
+    L.kind = _KINDS[layout.kind]
+    L.global_n[:] = [int(v) for v in layout.global_n]
+    L.periodic[:] = [int(v) for v in layout.periodic]
+    L.nbox = nb
+    L.boxes = ctypes.cast(arr, ctypes.POINTER(_Box))
+    L._keep = arr
+    return L
 
 
-def _assemble(layout, arrays):
-    """The global field from the box interiors (they must tile the domain)."""
-    gn = layout.global_n
-    G = np.zeros((gn[2], gn[1], gn[0]))
-    cover = np.zeros(G.shape, dtype=np.int64)
-    for b, a in zip(layout.boxes, arrays):
-        o, m = b.origin, b.interior
-        dst = (slice(o[2], o[2] + m[2]), slice(o[1], o[1] + m[1]), slice(o[0], o[0] + m[0]))
-        G[dst] = a[_interior_slices(b)]
-        cover[dst] += 1
-    if not (cover == 1).all():
-        raise ValueError("box interiors do not tile the global domain")
-    return G
+def _pack(layout, arrays):
+    return np.concatenate([np.ascontiguousarray(a, dtype=np.float64).ravel() for a in arrays]) \
+        if arrays else np.zeros(0)
 
 
-def _sample(layout, G):
-    """Per-box arrays whose every padded cell reads the global cell at
-    origin - ng_lo + i (periodic axes wrap, non-periodic axes give 0 outside
-    the domain)."""
-    gn = layout.global_n
-    Gz = np.zeros((gn[2] + 1, gn[1] + 1, gn[0] + 1))
-    Gz[:-1, :-1, :-1] = G                      # index -1 reads the zero plane
-    out = []
+def _unpack(layout, flat):
+    out, off = [], 0
     for b in layout.boxes:
-        idx = []
-        for d in range(3):
-            g = b.origin[d] - b.ng_lo[d] + np.arange(b.n[d])
-            if layout.periodic[d]:
-                g = g % gn[d]
-            else:
-                g = np.where((g >= 0) & (g < gn[d]), g, -1)
-            idx.append(g)
-        out.append(np.ascontiguousarray(Gz[np.ix_(idx[2], idx[1], idx[0])]))
+        n = b.n[0] * b.n[1] * b.n[2]
+        out.append(flat[off:off + n].reshape(b.n[2], b.n[1], b.n[0]).copy())
+        off += n
     return out
 
 
 def exchange(layout, arrays):
-    """Return new per-box arrays whose guards hold the owning interior values.
-
-    Non-independent layouts: the box interiors tile the global domain; the
-    global field is assembled from them and every padded cell reads the
-    global cell at origin - ng_lo + i (periodic axes wrap, non-periodic axes
-    give 0 outside the domain).  Independent boxes wrap onto their own
-    interior."""
-    if layout.kind == "independent":
-        out = []
-        for b, a in zip(layout.boxes, arrays):
-            inner = a[_interior_slices(b)]
-            idx = [(np.arange(b.n[d]) - b.ng_lo[d]) % b.interior[d] for d in range(3)]
-            out.append(np.ascontiguousarray(inner[np.ix_(idx[2], idx[1], idx[0])]))
-        return out
-    return _sample(layout, _assemble(layout, arrays))
+    """New per-box arrays whose guards hold the owning interior values."""
+    L = _layout(layout)
+    flat = _pack(layout, arrays)
+    _check(_L().oracle_exchange(ctypes.byref(L), _ptr(flat)), "exchange (interiors must tile the domain)")
+    return _unpack(layout, flat)
 
 
 def couple(src_layout, src_arrays, dst_layout):
-    """Dual-grid coupling (paper Sec. 2.5.2, dual grid decomposition): two
-    decompositions of the same global domain; every cell of every destination
-    box (guards included) takes the value of the source-layout interior cell
-    with the same global index (periodic wrap; 0 outside a non-periodic
-    domain).  G1 -> G2 fills the FFT grid, guards included; G2 -> G1 copies
-    the FFT grid's interiors back."""
-    if tuple(src_layout.global_n) != tuple(dst_layout.global_n) or \
-            tuple(src_layout.periodic) != tuple(dst_layout.periodic):
+    """Dual-grid coupling (paper Sec. 2.5.2): every destination cell takes the
+    source interior cell with the same global index."""
+    S, Dl = _layout(src_layout), _layout(dst_layout)
+    flat = _pack(src_layout, src_arrays)
+    n = sum(b.n[0] * b.n[1] * b.n[2] for b in dst_layout.boxes)
+    out = np.zeros(n)
+    rc = _L().oracle_couple(ctypes.byref(S), _ptr(flat), ctypes.byref(Dl), _ptr(out))
+    if rc == 3:
         raise ValueError("layouts of different domains")
-    return _sample(dst_layout, _assemble(src_layout, src_arrays))
+    _check(rc, "couple")
+    return _unpack(dst_layout, out)
 
 
-# ----------------------------------------------------------------------------
-# Whole push over a layout
-# ----------------------------------------------------------------------------
-
-COMPS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
-
-
-def push(layout, fields, src, nsteps, h, dt, c=1.0, eps0=1.0, form="vacuum",
-         boxes=None, nodal=False):
+def push(layout, fields, src, nsteps, h, dt, c=1.0, eps0=1.0, form="vacuum", boxes=None, nodal=False,
+         precision=64, return_imag=False):
     """Advance ``fields`` (dict comp -> list of per-box arrays) by ``nsteps``
-    steps: every step advances each box (Sec. 1.3 local FFT), then exchanges
-    guards.  With form 'rho', ``src['rho']`` is advanced too and returned in
-    the output dict.  ``boxes`` restricts the advance to a subset (no
-    exchange then), for sampled checks of large layouts."""
-    cur = {k: list(v) for k, v in fields.items()}
-    rho = list(src["rho"]) if form == "rho" else None
-    sel = range(len(layout.boxes)) if boxes is None else boxes
-    for _ in range(nsteps):
-        new = {k: list(v) for k, v in cur.items()}
-        new_rho = list(rho) if rho is not None else None
-        for b in sel:
-            box = layout.boxes[b]
-            fb = {k: cur[k][b] for k in COMPS}
-            sb = None
-            if form in ("J", "rho"):
-                sb = {k: src[k][b] for k in ("Jx", "Jy", "Jz")}
-                if form == "rho":
-                    sb["rho"] = rho[b]
-            o = push_box(fb, sb, h, box.p, dt, c, eps0, form, nodal=nodal)
-            for k in COMPS:
-                new[k][b] = o[k]
-            if form == "rho":
-                new_rho[b] = o["rho"]
-        has_guards = any(g for b in layout.boxes for g in b.ng_lo + b.ng_hi)
-        if boxes is None and has_guards:
-            for k in COMPS:
-                new[k] = exchange(layout, new[k])
-            if new_rho is not None:
-                new_rho = exchange(layout, new_rho)
-        cur, rho = new, new_rho
-    if rho is not None:
-        cur["rho"] = rho
-    return cur
+    steps: every step advances each box, then exchanges guards.  With form
+    'rho', ``src['rho']`` is advanced too and returned in the output dict.
+    ``boxes`` restricts the advance to a subset (no exchange then).
+    precision 32 runs the FP32 rounding model instead of the oracle."""
+    L = _layout(layout)
+    f = [_pack(layout, fields[k]) for k in COMPS]
+    s = None
+    if form in ("J", "rho"):
+        s = [_pack(layout, src[k]) for k in ("Jx", "Jy", "Jz")]
+        s.append(_pack(layout, src["rho"]) if form == "rho" else np.zeros(1))
+    mask = None
+    if boxes is not None:
+        mask = np.zeros(len(layout.boxes), np.uint8)
+        mask[list(boxes)] = 1
+    imag = np.zeros(1)
+    hh = np.asarray(h, dtype=np.float64)
+    rc = _L().oracle_push(ctypes.byref(L), _pp(f), _pp(s) if s else None,
+                          _ptr(mask) if mask is not None else None, int(nsteps), _ptr(hh), float(dt), float(c),
+                          float(eps0), _FORMS[form], int(nodal), int(precision), _ptr(imag))
+    _check(rc, "push")
+    out = {k: _unpack(layout, a) for k, a in zip(COMPS, f)}
+    if form == "rho":
+        out["rho"] = _unpack(layout, s[3])
+    if return_imag:
+        return out, float(imag[0])
+    return out
+
+
+class _OneBox:
+    def __init__(self, shape, p):
+        self.n = (shape[2], shape[1], shape[0])
+        self.ng_lo = self.ng_hi = (0, 0, 0)
+        self.origin = (0, 0, 0)
+        self.p = p
+
+
+class _OneLayout:
+    def __init__(self, shape, p):
+        self.kind = "independent"
+        self.global_n = (0, 0, 0)
+        self.periodic = (1, 1, 1)
+        self.boxes = [_OneBox(shape, p)]
+
+
+def push_box(f, src, h, p, dt, c=1.0, eps0=1.0, form="vacuum", return_imag=False, nodal=False, precision=64):
+    """One PSATD step of one periodic box.  f: dict Ex..Bz -> (nz, ny, nx)
+    arrays; src: dict Jx, Jy, Jz[, rho] or None.  Returns a new dict (with
+    'rho' in the rho form), and the largest imaginary part of the inverse
+    transforms when return_imag."""
+    lay = _OneLayout(f["Ex"].shape, p)
+    fl = {k: [f[k]] for k in COMPS}
+    sl = {k: [v] for k, v in src.items()} if src else {}
+    out, imag = push(lay, fl, sl, 1, h, dt, c, eps0, form, nodal=nodal, precision=precision, return_imag=True)
+    out = {k: v[0] for k, v in out.items()}
+    return (out, imag) if return_imag else out
 
 
 # ----------------------------------------------------------------------------
@@ -456,6 +364,10 @@ def guard_gain(d, n_mpi):
 # ----------------------------------------------------------------------------
 # Error metrics (relative L2 and max norm over interior cells)
 # ----------------------------------------------------------------------------
+
+def _interior_slices(box):
+    return tuple(slice(box.ng_lo[d], box.n[d] - box.ng_hi[d]) for d in (2, 1, 0))
+
 
 def interior(layout, arrays):
     return [a[_interior_slices(b)] for b, a in zip(layout.boxes, arrays)]

@@ -20,8 +20,9 @@
 // corrupt each other's results.
 //
 // The first call on a device looks up the array's device address with
-// cudaGetSymbolAddress and raises the kernels' shared-memory limit; make that
-// first call before any stream capture.
+// cudaGetSymbolAddress, reads the device's opt-in shared-memory maximum and
+// raises the kernels' shared-memory limit to it; make that first call before
+// any stream capture.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,6 +48,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_arena[kMaxDevices] = {};
 bool g_configured[kMaxDevices] = {};
+int g_optin[kMaxDevices] = {};
 
 size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -148,7 +150,6 @@ extern "C" psatd_status psatd_push_box_static(const int32_t n[3], int32_t order_
   for (int y = 0; y < n1; ++y)
     for (int m = 0; m < hx; m += nz) zcols.push_back({0, y, m, std::min(nz, hx - m)});
   const int smem = std::max({nr * L * 8, n1 * ny * 8, n2 * FIN * nz * 8, nr * (hx + L) * 8});
-  if (smem > 227 * 1024) return err(PSATD_ERR_UNSUPPORTED_SIZE, "box needs %d B of shared memory", smem);
   const std::vector<double> alpha = order_p ? stencil_alpha(order_p) : std::vector<double>(1, 0.0);
 
   // ---- carve the arena: [box][shape][rows][ycols][zcols][alpha][r32][c32][q32][r64][c64][q64][spectra]
@@ -178,6 +179,7 @@ extern "C" psatd_status psatd_push_box_static(const int32_t n[3], int32_t order_
   if (e != cudaSuccess) return err(PSATD_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return err(PSATD_ERR_CUDA, "device %d out of range", dev);
   unsigned char* A = nullptr;
+  int optin = 0;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_arena[dev]) {
@@ -187,8 +189,21 @@ extern "C" psatd_status psatd_push_box_static(const int32_t n[3], int32_t order_
         return err(PSATD_ERR_CUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
       g_arena[dev] = static_cast<unsigned char*>(p);
     }
+    if (!g_optin[dev]) {
+      // the device's per-block opt-in shared-memory maximum bounds both the
+      // size check below and the kernels' dynamic shared-memory attribute
+      e = cudaDeviceGetAttribute(&g_optin[dev], cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      if (e != cudaSuccess || g_optin[dev] <= 0) {
+        g_optin[dev] = 0;
+        return err(PSATD_ERR_CUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+      }
+    }
+    optin = g_optin[dev];
+    if (smem > optin)
+      return err(PSATD_ERR_UNSUPPORTED_SIZE, "box needs %d B of shared memory per block; the device allows %d B",
+                 smem, optin);
     if (!g_configured[dev]) {
-      e = configure_kernels(32, 227 * 1024);
+      e = configure_kernels(32, optin);
       if (e != cudaSuccess) return err(PSATD_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
       g_configured[dev] = true;
     }

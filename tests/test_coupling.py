@@ -7,6 +7,7 @@ import pytest
 
 from oracle import psatd_oracle as O
 from paper_1812_07357_gb300 import inputs as I
+from _parity import assert_fields
 
 pytestmark = pytest.mark.gpu
 
@@ -81,6 +82,6 @@ def test_dual_grid_cycle(prec):
         ref = {k: O.couple(g2, r2[k], g1) for k in O.COMPS}
     plan.sync()
     got = {k: cp.unpack(d1[k]) for k in O.COMPS}
-    assert O.rel_l2_fields(g1, got, ref, O.COMPS) <= TOL[prec]
+    assert_fields(g1, got, ref, O.COMPS, prec)
     cp.close()
     plan.close()

@@ -6,6 +6,7 @@ import pytest
 
 from oracle import psatd_oracle as O
 from paper_1812_07357_gb300 import inputs as I
+from _parity import assert_fields
 
 pytestmark = pytest.mark.gpu
 
@@ -65,7 +66,7 @@ def _check(lay, prec, form, nsteps=3, **plan_kw):
     plan.close()
     ref = O.push(lay, fields, src, nsteps, (1.0, 1.0, 1.0), 0.9, form=form)
     comps = O.COMPS + (("rho",) if form == "rho" else ())
-    assert O.rel_l2_fields(lay, got, ref, comps) <= TOL[prec]
+    assert_fields(lay, got, ref, comps, prec)
     for k in ("Jx", "Jy", "Jz"):   # the current is read only
         for a, b in zip(jgot[k], src[k]):
             assert np.array_equal(a, b)

@@ -5,6 +5,7 @@ import pytest
 
 from oracle import psatd_oracle as O
 from paper_1812_07357_gb300 import inputs as I
+from _parity import assert_fields
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +45,7 @@ def _check(lay, prec, form, paths, nsteps=3, **kw):
     plan.close()
     ref = O.push(lay, fields, src, nsteps, (1.0, 0.9, 1.1), 0.8, form=form, nodal=True)
     comps = O.COMPS + (("rho",) if form == "rho" else ())
-    assert O.rel_l2_fields(lay, got, ref, comps) <= TOL[prec]
+    assert_fields(lay, got, ref, comps, prec)
 
 
 @pytest.mark.parametrize("prec", [64, 32])

@@ -4,6 +4,10 @@ Each check uses an independent route: a brute-force DFT, exact rational
 arithmetic, real-space finite-difference stencils applied cell by cell, the
 matrix exponential of the Maxwell generator, analytic plane waves, invariants
 of Maxwell's equations, and the values the paper prints for its memory model.
+
+Every pin runs against both implementations: the oracle (C++ with its own
+FFT, oracle/psatd_oracle.cpp) and the numpy/scipy cross-check
+(oracle/psatd_numpy.py).
 """
 import math
 import os
@@ -13,10 +17,17 @@ import numpy as np
 import pytest
 import scipy.linalg
 
-from oracle import psatd_oracle as O
+from oracle import psatd_numpy, psatd_oracle
 from paper_1812_07357_gb300 import inputs as I
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+IMPLS = {"cpp": psatd_oracle, "numpy": psatd_numpy}
+
+
+@pytest.fixture(params=sorted(IMPLS))
+def O(request):
+    """The implementation under test."""
+    return IMPLS[request.param]
 
 
 # ---------------------------------------------------------------------------
@@ -66,7 +77,7 @@ AX = {"x": 2, "y": 1, "z": 0}
 
 def D(f, comp, d, p, h=1.0):
     """Derivative along axis d ('x','y','z') of component ``comp`` (Yee)."""
-    s = O.YEE[comp]["xyz".index(d)]
+    s = psatd_oracle.YEE[comp]["xyz".index(d)]
     return stag_diff(f, AX[d], p, h, from_half=(s == 0.5))
 
 
@@ -79,7 +90,7 @@ def div_E(f, p):
 
 
 def energy(f):
-    return sum(float(np.sum(f[k] ** 2)) for k in O.COMPS)
+    return sum(float(np.sum(f[k] ** 2)) for k in psatd_oracle.COMPS)
 
 
 def one_box(layout, d):
@@ -98,7 +109,7 @@ def _five_smooth(n):
 
 
 @pytest.mark.parametrize("n", [n for n in range(2, 65, 2) if _five_smooth(n)])
-def test_fft_1d_matches_direct_dft(n):
+def test_fft_1d_matches_direct_dft(O, n):
     rng = np.random.default_rng(n)
     x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
     got = O.fft3(x.reshape(1, 1, n)).ravel()
@@ -107,7 +118,7 @@ def test_fft_1d_matches_direct_dft(n):
 
 
 @pytest.mark.parametrize("shape", [(4, 6, 10), (6, 4, 8), (10, 12, 6)])
-def test_fft_3d_matches_direct_dft(shape):
+def test_fft_3d_matches_direct_dft(O, shape):
     rng = np.random.default_rng(1)
     a = rng.standard_normal(shape)
     nz, ny, nx = shape
@@ -128,28 +139,50 @@ def test_fft_3d_matches_direct_dft(shape):
 # Stencil weights and modified wavenumber (Sec. 1.1: order p, width p/2)
 # ---------------------------------------------------------------------------
 
-def test_stencil_weights_low_orders():
-    assert O.stencil_weights(2) == [Fraction(1)]
-    assert O.stencil_weights(4) == [Fraction(9, 8), Fraction(-1, 8)]
+def _same(w, exact, rel=4e-15):
+    """w (exact rationals, or floats of the C++ oracle) against exact values:
+    equal for rationals, within `rel` relative for floats."""
+    assert len(w) == len(exact)
+    for a, e in zip(w, exact):
+        if isinstance(a, Fraction):
+            assert a == e
+        else:
+            assert abs(Fraction(a) - e) <= rel * abs(e), (a, e)
+
+
+def _exactness(w, nodes_pow, p):
+    """sum_l w_l node_l^(2j) = delta_j0 for j < p/2: exact for rationals; for
+    floats within 1e-13 of the magnitude of the terms (summed exactly)."""
+    for j in range(p // 2):
+        terms = [Fraction(a) * nodes_pow(l) ** (2 * j) for l, a in enumerate(w, start=1)]
+        s = sum(terms)
+        want = 1 if j == 0 else 0
+        if all(isinstance(a, Fraction) for a in w):
+            assert s == want
+        else:
+            assert abs(s - want) <= Fraction(1, 10 ** 13) * sum(abs(t) for t in terms), (p, j)
+
+
+def test_stencil_weights_low_orders(O):
+    _same(O.stencil_weights(2), [Fraction(1)])
+    _same(O.stencil_weights(4), [Fraction(9, 8), Fraction(-1, 8)])
     # the classical 4th-order staggered coefficients 9/8 and -1/24
     w = O.stencil_weights(4)
-    assert [w[0] / 1, w[1] / 3] == [Fraction(9, 8), Fraction(-1, 24)]
+    _same([w[0] / 1, w[1] / 3], [Fraction(9, 8), Fraction(-1, 24)])
     assert O.stencil_weights(0) is None
 
 
 @pytest.mark.parametrize("p", [2, 4, 6, 8, 16, 32, 64])
-def test_stencil_weights_exactness(p):
+def test_stencil_weights_exactness(O, p):
     w = O.stencil_weights(p)
     assert len(w) == p // 2            # stencil of width p/2 per side
-    for j in range(p // 2):
-        s = sum(a * (2 * l - 1) ** (2 * j) for l, a in enumerate(w, start=1))
-        assert s == (1 if j == 0 else 0)
+    _exactness(w, lambda l: 2 * l - 1, p)
     if p <= 16:
-        assert w == vandermonde_weights(p)
+        _same(w, vandermonde_weights(p), rel=1e-14)
 
 
 @pytest.mark.parametrize("p", [2, 4, 8, 16])
-def test_modified_wavenumber_is_stencil_eigenvalue(p):
+def test_modified_wavenumber_is_stencil_eigenvalue(O, p):
     n, h = 24, 0.7
     x = np.arange(n)
     for m in range(0, n // 2 + 1):
@@ -163,7 +196,7 @@ def test_modified_wavenumber_is_stencil_eigenvalue(p):
 
 
 @pytest.mark.parametrize("p", [2, 4, 8])
-def test_modified_wavenumber_order(p):
+def test_modified_wavenumber_order(O, p):
     h = 1.0
     e1 = abs(O.modified_wavenumber(0.2, h, p) - 0.2)
     e2 = abs(O.modified_wavenumber(0.1, h, p) - 0.1)
@@ -172,7 +205,7 @@ def test_modified_wavenumber_order(p):
     assert O.modified_wavenumber(0.3, h, 0) == 0.3
 
 
-def test_modified_wavenumber_monotone():
+def test_modified_wavenumber_monotone(O):
     # K strictly increasing on (0, pi/h]: K = 0 only at k = 0.
     k = np.linspace(1e-6, np.pi, 2000)
     for p in (2, 4, 8, 16, 32, 64):
@@ -199,7 +232,7 @@ def _generator(K, c, eps0):
 
 
 @pytest.mark.parametrize("form", ["vacuum", "J", "rho"])
-def test_update_equals_matrix_exponential(form):
+def test_update_equals_matrix_exponential(O, form):
     rng = np.random.default_rng(7)
     c, eps0, dt = 1.3, 0.8, 0.9
     Ks = [rng.standard_normal(3) * s for s in (2.0, 1.0, 0.3, 1e-3, 1e-6)]
@@ -225,7 +258,7 @@ def test_update_equals_matrix_exponential(form):
             assert abs(Rn[0] - ref[12]) <= 1e-12 * (abs(ref[12]) + 1)
 
 
-def test_coefficients_small_theta_continuity():
+def test_coefficients_small_theta_continuity(O):
     # the Taylor branch and the direct branch meet smoothly at theta = 0.1
     K2 = np.array([(0.1 * (1 - 1e-9)) ** 2, (0.1 * (1 + 1e-9)) ** 2])
     C, Sw, X1, X3 = O.coefficients(K2, 1.0, 1.0)
@@ -240,7 +273,7 @@ def test_coefficients_small_theta_continuity():
 # Whole push: analytic solutions and invariants
 # ---------------------------------------------------------------------------
 
-def test_plane_waves_analytic_infinite_order():
+def test_plane_waves_analytic_infinite_order(O):
     """32^3, p = infinity, dt = 0.5, 64 steps: exact to rounding (Sec. 1.1:
     accurate to machine precision, no numerical dispersion)."""
     w = I.make_workload("plane_waves_32")
@@ -250,7 +283,7 @@ def test_plane_waves_analytic_infinite_order():
     assert O.rel_l2_fields(w.layout, out, refb, O.COMPS) < 1e-12
 
 
-def test_no_courant_limit_in_vacuum():
+def test_no_courant_limit_in_vacuum(O):
     """dt = 5 cells at infinite order still matches the analytic waves."""
     n = 16
     lay = I.global_layout((n, n, n), 0)
@@ -262,7 +295,7 @@ def test_no_courant_limit_in_vacuum():
 
 
 @pytest.mark.parametrize("p", [2, 4, 16])
-def test_dispersion_relation_finite_order(p):
+def test_dispersion_relation_finite_order(O, p):
     """A standing wave E_y = cos(kx) oscillates with omega = c K_p(k), K_p
     the eigenvalue of the real-space stencil."""
     n, h, dt, c = 32, 1.0, 0.3, 1.0
@@ -282,7 +315,7 @@ def test_dispersion_relation_finite_order(p):
         assert abs(ratio - math.cos(c * Kp * dt)) < 1e-13
 
 
-def test_divB_stays_zero_under_stencil_divergence():
+def test_divB_stays_zero_under_stencil_divergence(O):
     rng = np.random.default_rng(11)
     n, p = 12, 8
     lay = I.global_layout((n, n + 4, n - 2), p)
@@ -300,7 +333,7 @@ def test_divB_stays_zero_under_stencil_divergence():
 
 
 @pytest.mark.parametrize("form", ["rho", "J"])
-def test_gauss_law_kept_with_continuity_consistent_current(form):
+def test_gauss_law_kept_with_continuity_consistent_current(O, form):
     rng = np.random.default_rng(12)
     n, p, dt = 12, 4, 0.9
     lay = I.global_layout((n, n, n), p)
@@ -322,7 +355,7 @@ def test_gauss_law_kept_with_continuity_consistent_current(form):
             assert np.abs(outj[k][0] - fb[k]).max() < 1e-11
 
 
-def test_vacuum_energy_conserved():
+def test_vacuum_energy_conserved(O):
     rng = np.random.default_rng(13)
     lay = I.global_layout((10, 12, 8), 16)
     shp = lay.boxes[0].shape
@@ -333,7 +366,7 @@ def test_vacuum_energy_conserved():
     assert abs(e1 - e0) < 1e-12 * e0
 
 
-def test_time_reversal():
+def test_time_reversal(O):
     rng = np.random.default_rng(14)
     lay = I.global_layout((12, 10, 8), 8)
     shp = lay.boxes[0].shape
@@ -345,7 +378,7 @@ def test_time_reversal():
 
 
 @pytest.mark.parametrize("form", ["vacuum", "J", "rho"])
-def test_semigroup(form):
+def test_semigroup(O, form):
     rng = np.random.default_rng(15)
     lay = I.global_layout((8, 10, 12), 16)
     shp = lay.boxes[0].shape
@@ -360,7 +393,7 @@ def test_semigroup(form):
         assert np.abs(a[k][0] - b[k][0]).max() < 1e-11 * (1 + np.abs(b[k][0]).max())
 
 
-def test_result_is_real():
+def test_result_is_real(O):
     rng = np.random.default_rng(16)
     f = {k: rng.standard_normal((8, 10, 12)) for k in O.COMPS}
     s = {k: rng.standard_normal((8, 10, 12)) for k in ("Jx", "Jy", "Jz", "rho")}
@@ -411,7 +444,7 @@ def _brute_exchange(layout, arrays):
 
 
 @pytest.mark.parametrize("kind", ["local", "local_open", "hybrid", "independent"])
-def test_exchange_matches_owner_search(kind):
+def test_exchange_matches_owner_search(O, kind):
     rng = np.random.default_rng(17)
     if kind == "local":
         lay = I.local_layout((12, 8, 8), (3, 2, 2), 2, 4)
@@ -432,7 +465,7 @@ def test_exchange_matches_owner_search(kind):
 # Decompositions: local -> global as guards grow (Sec. 1.3)
 # ---------------------------------------------------------------------------
 
-def test_local_converges_to_global_with_guards():
+def test_local_converges_to_global_with_guards(O):
     gsz, p, dt, steps = 32, 8, 0.9, 6
     f = I.laser_fields((gsz,) * 3, wavelength=8.0, waist=5.0, duration=4.0)
     glay = I.global_layout((gsz,) * 3, p)
@@ -450,7 +483,7 @@ def test_local_converges_to_global_with_guards():
     assert errs[-1] < 0.05 * errs[0]
 
 
-def test_hybrid_single_group_equals_global():
+def test_hybrid_single_group_equals_global(O):
     """A hybrid layout with one group on every axis is the global solver."""
     gsz = (16, 12, 10)
     f = I.laser_fields(gsz, wavelength=6.0, waist=3.0, duration=3.0)
@@ -476,7 +509,7 @@ def _golden():
     return rows
 
 
-def test_memory_model_printed_values():
+def test_memory_model_printed_values(O):
     for name, d, nm, v in _golden():
         if name == "local_max":
             n, n_g = 4096.0, 16
@@ -489,7 +522,7 @@ def test_memory_model_printed_values():
             assert abs(O.guard_gain(d, nm) - 8 / 0.96) < 1e-12
 
 
-def test_memory_gain_is_ratio_of_eqs_1_and_3():
+def test_memory_gain_is_ratio_of_eqs_1_and_3(O):
     n, n_g = 1024.0, 8
     n_p = n / n_g
     for n_mpi in (1, 2, 4, 8, 32):
@@ -501,7 +534,7 @@ def test_memory_gain_is_ratio_of_eqs_1_and_3():
     assert abs(O.memory_gain(3, 1) - 1.0) < 1e-15
 
 
-def test_workload_memory_ratio_local_vs_hybrid():
+def test_workload_memory_ratio_local_vs_hybrid(O):
     """The one-GPU hybrid/local workloads: padded-cell ratio 18 = the d = 1
     gain at n_mpi = 4 (eq. (6)) times 3 x 3 for the two axes the group spans."""
     hyb = I.hybrid_layout((1024, 256, 256), (4, 1, 1), 64, 64)
@@ -542,7 +575,7 @@ def _brute_couple(src, arrays, dst):
 
 
 @pytest.mark.parametrize("periodic", [(1, 1, 1), (0, 1, 0)])
-def test_couple_matches_owner_search(periodic):
+def test_couple_matches_owner_search(O, periodic):
     rng = np.random.default_rng(19)
     g1 = I.local_layout((12, 8, 8), (3, 2, 2), 1, 4, periodic=periodic)      # particle grid, thin guards
     g2 = I.local_layout((12, 8, 8), (2, 1, 2), (2, 3, 2), 4, periodic=periodic)   # FFT grid, wide guards
@@ -556,7 +589,7 @@ def test_couple_matches_owner_search(periodic):
         assert np.array_equal(g, r)
 
 
-def test_couple_round_trip_is_identity_on_consistent_fields():
+def test_couple_round_trip_is_identity_on_consistent_fields(O):
     rng = np.random.default_rng(20)
     g1 = I.local_layout((16, 12, 8), (4, 3, 2), 1, 4)
     g2 = I.hybrid_layout((16, 12, 8), (2, 1, 1), 3, 4)
@@ -567,7 +600,7 @@ def test_couple_round_trip_is_identity_on_consistent_fields():
         assert np.array_equal(x, y)
 
 
-def test_couple_rejects_different_domains():
+def test_couple_rejects_different_domains(O):
     with pytest.raises(ValueError):
         O.couple(I.local_layout((8, 8, 8), (2, 1, 1), 1, 4), [np.zeros((10, 10, 6))] * 2,
                  I.local_layout((8, 8, 12), (2, 1, 1), 1, 4))
@@ -577,16 +610,14 @@ def test_couple_rejects_different_domains():
 # Nodal (collocated) variant: centred weights, symbol, conservation
 # ---------------------------------------------------------------------------
 
-def test_nodal_weights_low_orders_and_exactness():
-    assert O.nodal_weights(2) == [Fraction(1)]
-    assert O.nodal_weights(4) == [Fraction(4, 3), Fraction(-1, 3)]
+def test_nodal_weights_low_orders_and_exactness(O):
+    _same(O.nodal_weights(2), [Fraction(1)])
+    _same(O.nodal_weights(4), [Fraction(4, 3), Fraction(-1, 3)])
     # the classical 4th-order centred coefficients 2/3 and -1/12 (beta_l / (2 l))
     b = O.nodal_weights(4)
-    assert [b[0] / 2, b[1] / 4] == [Fraction(2, 3), Fraction(-1, 12)]
+    _same([b[0] / 2, b[1] / 4], [Fraction(2, 3), Fraction(-1, 12)])
     for p in (2, 4, 8, 16, 32):
-        b = O.nodal_weights(p)
-        for j in range(p // 2):
-            assert sum(x * l ** (2 * j) for l, x in enumerate(b, start=1)) == (1 if j == 0 else 0)
+        _exactness(O.nodal_weights(p), lambda l: l, p)
     assert O.nodal_weights(0) is None
 
 
@@ -611,7 +642,7 @@ def _centred_diff(f, axis, p, h):
 
 
 @pytest.mark.parametrize("p", [2, 4, 8, 16])
-def test_nodal_wavenumber_is_stencil_eigenvalue_and_order(p):
+def test_nodal_wavenumber_is_stencil_eigenvalue_and_order(O, p):
     n, h = 24, 0.7
     x = np.arange(n)
     for m in range(0, n // 2 + 1):
@@ -625,7 +656,7 @@ def test_nodal_wavenumber_is_stencil_eigenvalue_and_order(p):
         assert 2 ** (p + 1) * 0.8 < e1 / e2 < 2 ** (p + 1) * 1.2
 
 
-def test_nodal_push_conserves_energy_and_div_b():
+def test_nodal_push_conserves_energy_and_div_b(O):
     rng = np.random.default_rng(31)
     n, p = 16, 8
     lay = I.global_layout((n, n, n), p)
@@ -644,7 +675,7 @@ def test_nodal_push_conserves_energy_and_div_b():
     assert np.abs(divb).max() <= 1e-11 * max(1.0, np.abs(out["Bx"][0]).max())
 
 
-def test_nodal_plane_wave_dispersion():
+def test_nodal_plane_wave_dispersion(O):
     """A single transverse mode rotates with omega = c K_nodal per step."""
     n, p, dt, h = 16, 4, 0.6, 1.0
     lay = I.global_layout((n, n, n), p)
@@ -662,7 +693,7 @@ def test_nodal_plane_wave_dispersion():
     assert np.abs(out["Ey"][0] - want).max() <= 1e-12
 
 
-def test_nodal_infinite_order_keeps_fields_real():
+def test_nodal_infinite_order_keeps_fields_real(O):
     """At p = infinity the collocated symbol is 0 at Nyquist; the push of a
     real field stays real (imaginary part of the inverse FFT at rounding)."""
     rng = np.random.default_rng(33)
@@ -671,3 +702,46 @@ def test_nodal_infinite_order_keeps_fields_real():
     assert K[6] == 0.0 and K[5] == O.axis_wavenumbers(12, 1.0)[5]
     _, imag = O.push_box(f, None, (1.0,) * 3, 0, 0.7, nodal=True, return_imag=True)
     assert imag <= 1e-13
+
+
+# ---------------------------------------------------------------------------
+# The two implementations against each other, and the FP32 rounding model
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["local_vacuum", "local_rho_inf", "hybrid_J", "independent_rho_nodal",
+                                  "open_J_nodal"])
+def test_cpp_and_numpy_oracles_agree(case):
+    rng = np.random.default_rng(51)
+    lay, form, nodal = {
+        "local_vacuum": (I.local_layout((24, 16, 16), (2, 2, 1), 3, 8), "vacuum", False),
+        "local_rho_inf": (I.local_layout((24, 16, 16), (2, 2, 1), 3, 0), "rho", False),
+        "hybrid_J": (I.hybrid_layout((32, 12, 10), (2, 1, 1), 4, 4), "J", False),
+        "independent_rho_nodal": (I.independent_layout(seed=3, nboxes=3, sizes=(8, 10, 12), ngs=(1, 2),
+                                                       min_interior=4), "rho", True),
+        "open_J_nodal": (I.local_layout((24, 16, 16), (2, 2, 1), 3, 8, periodic=(0, 1, 0)), "J", True),
+    }[case]
+    f = {k: psatd_oracle.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes])
+         for k in psatd_oracle.COMPS}
+    s = {k: psatd_oracle.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes])
+         for k in ("Jx", "Jy", "Jz", "rho")}
+    a = psatd_oracle.push(lay, f, s, 3, (1.0, 0.9, 1.1), 0.7, form=form, nodal=nodal)
+    b = psatd_numpy.push(lay, f, s, 3, (1.0, 0.9, 1.1), 0.7, form=form, nodal=nodal)
+    for k in a:
+        for x, y in zip(a[k], b[k]):
+            assert np.abs(x - y).max() <= 1e-13 * (1 + np.abs(y).max()), (case, k)
+
+
+def test_fp32_rounding_model():
+    """precision=32 runs the same steps in FP32: close to the FP64 push at the
+    level of FP32 rounding, but not equal to it (it really rounds)."""
+    rng = np.random.default_rng(52)
+    lay = I.local_layout((32, 16, 16), (2, 1, 1), 4, 8)
+    f = {k: psatd_oracle.exchange(lay, I.round_to([rng.standard_normal(b.shape) for b in lay.boxes], np.float32))
+         for k in psatd_oracle.COMPS}
+    a = psatd_oracle.push(lay, f, {}, 4, (1.0,) * 3, 0.9)
+    b = psatd_oracle.push(lay, f, {}, 4, (1.0,) * 3, 0.9, precision=32)
+    err = psatd_oracle.rel_l2_fields(lay, b, a, psatd_oracle.COMPS)
+    assert 1e-8 < err < 2e-6, err
+    for k in b:          # every value is an FP32 number
+        for x in b[k]:
+            assert np.array_equal(x, x.astype(np.float32).astype(np.float64))

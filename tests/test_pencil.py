@@ -8,6 +8,7 @@ import pytest
 
 from oracle import psatd_oracle as O
 from paper_1812_07357_gb300 import inputs as I
+from _parity import assert_fields
 
 pytestmark = pytest.mark.gpu
 
@@ -46,8 +47,7 @@ def _check(lay, fields, src, nsteps, h, dt, prec, form, paths, **plan_kw):
     assert p == paths, p
     ref = O.push(lay, fields, src, nsteps, h, dt, form=form)
     comps = O.COMPS + (("rho",) if form == "rho" else ())
-    err = O.rel_l2_fields(lay, got, ref, comps)
-    assert err <= TOL[prec], err
+    assert_fields(lay, got, ref, comps, prec)
     for k in comps:   # guards too (exchange ran)
         for g, r in zip(got[k], ref[k]):
             assert np.abs(g - r).max() <= 50 * TOL[prec] * max(1.0, float(np.abs(r).max())) * nsteps ** 0.5
@@ -139,8 +139,8 @@ def test_pencil_flag_on_plane_boxes(prec):
         outs.append(plan.unpack_fields(df))
         plan.close()
     ref = O.push(lay, fields, {}, 3, (1.0,) * 3, 0.9, form="vacuum")
-    assert O.rel_l2_fields(lay, outs[0], ref, O.COMPS) <= TOL[prec]
-    assert O.rel_l2_fields(lay, outs[0], outs[1], O.COMPS) <= TOL[prec]
+    assert_fields(lay, outs[0], ref, O.COMPS, prec)
+    assert_fields(lay, outs[0], outs[1], O.COMPS, prec)
 
 
 def test_default_family_choice():

@@ -2,13 +2,16 @@
 memory (for example code running under a framework that owns every device
 allocation).  It keeps its workspace and tables in the library's static
 device array instead of cudaMalloc'd plan memory, so its results must equal
-those of the ordinary plan-based psatd_push on the same box.
+those of the ordinary plan-based psatd_push on the same box, and both must
+match the FP64 oracle.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test.
 """
 import numpy as np
 import pytest
+
+from _parity import assert_fields
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +48,11 @@ def test_static_push_matches_plan_push_on_two_calls(env):
     got = {k: torch.from_numpy(v.ravel().copy()).cuda() for k, v in f.items()}
     cells = n[0] * n[1] * n[2]
     stream = plan.stream.cuda_stream
+    # the FP64 oracle on the same FP32 inputs, 3 and 6 steps: an anchor that
+    # does not go through the plan's code path
+    from oracle import psatd_oracle as O
+    f64 = {k: [v.astype(np.float64)] for k, v in f.items()}
+    want = [O.push(lay, f64, {}, 3, dx, dt, c=c), O.push(lay, f64, {}, 6, dx, dt, c=c)]
     for call in range(2):
         plan.push(ref, None, 3)
         A.psatd_push_box_static(n, p, dx, dt, c, Plan.fields_struct(got), 3, stream)
@@ -52,6 +60,8 @@ def test_static_push_matches_plan_push_on_two_calls(env):
         for k in COMPS:
             err = _rel_l2(got[k], ref[k][:cells])
             assert err <= FP32_TOL, (call, k, err)
+        out = {k: [got[k].cpu().numpy().astype(np.float64).reshape(n[2], n[1], n[0])] for k in COMPS}
+        assert_fields(lay, out, want[call], COMPS, 32, what=f"static push, call {call}")
     plan.close()
 
 
