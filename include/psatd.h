@@ -311,6 +311,21 @@ int32_t psatd_plan_pencil_boxes(const psatd_plan* plan);
  * guards, -1 for a NULL plan. */
 int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
 
+/* ---- Tuning knobs (no counterpart in the paper: launch parameters of this
+ * implementation's kernels, chosen per plan by measurement -- see the
+ * autotuner of the Python package).  Setting a knob drops the plan's captured
+ * CUDA graphs; results do not depend on any knob.
+ *   PSATD_TUNE_Z_PREFETCH  register z kernel (the fused z FFT + update pass):
+ *                          every CTA first prefetches into L2 the input tile of
+ *                          the CTA launched `value` blocks after it (0 = off;
+ *                          0 <= value <= 2^20).
+ * psatd_plan_tune returns PSATD_ERR_INVALID_ARG for an unknown knob or a
+ * value out of range; psatd_plan_tuning returns the knob's value, or -1 for an
+ * unknown knob, a NULL plan, or a plan whose kernels do not use the knob. */
+#define PSATD_TUNE_Z_PREFETCH 1
+psatd_status psatd_plan_tune(psatd_plan* plan, int32_t knob, int32_t value);
+int32_t psatd_plan_tuning(const psatd_plan* plan, int32_t knob);
+
 /* Kernel kinds reported by psatd_plan_kernel_times. */
 #define PSATD_KERNEL_KINDS 6 /* 0 fwd_x, 1 col forward, 2 z_update, 3 col inverse, 4 inv_x, 5 exchange */
 

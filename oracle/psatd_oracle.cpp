@@ -55,6 +55,29 @@
 // DFT for any other factor), twiddles cos/sin(2 pi j/N) in double.  The whole
 // complex spectrum is computed (no real-to-complex shortcut).
 //
+// Absorbing layers (PML; the paper only states that the solver supports the
+// two-step perfectly matched layer of its reference [shapoval2019two], with
+// no equations).  Reading, derived here from Maxwell's equations in vacuum:
+// each component is split by derivative direction (Berenger), e.g.
+//     E_x = E_xy + E_xz,  dE_xy/dt + s_y E_xy = c^2 dB_z/dy,
+//                         dE_xz/dt + s_z E_xz = -c^2 dB_y/dz,
+// and likewise for E_y (y-z... parts z, x), E_z (x, y), B_x (y, z), B_y (z, x),
+// B_z (x, y) with dB/dt = -curl E.  One step is two exact sub-steps:
+//  (1) s = 0: the split parts sum to the usual fields, so E, B take the
+//      ordinary PSATD step, and each split part gains the time integral of
+//      its own derivative term over the step, which depends on E^n, B^n only.
+//      With the mode solution E(t), B(t) of the update above (vacuum),
+//        I[E] = int_0^dt E = Sw E - X3 K (K.E) + i X1 K x B,
+//        I[B] = int_0^dt B = Sw B - X3 K (K.B) - i (X1/c^2) K x E,
+//      so e.g. dE_xy = i c^2 K_y I[B_z], dB_xy = -i K_y I[E_z];
+//  (2) each split part along direction d is multiplied by exp(-s_d dt) (the
+//      exact solution of dF/dt = -s_d F), and the component is the sum again.
+// One split part per component is stored (E_xy, E_yz, E_zx, B_xy, B_yz,
+// B_zx); the other is the component minus it.  s_d = s_max,d (xi/w_d)^m at
+// depth xi (cells) into a layer of w_d cells on each face of axis d of the
+// global domain, evaluated at the component's Yee position; 0 outside the
+// layers.  The layers hold no current (vacuum form only).
+//
 // The push is a template on the arithmetic type.  double is the oracle.  The
 // float instantiation (precision 32) carries out the same steps in FP32
 // arithmetic and storage, with the twiddles, phases and coefficients computed
@@ -302,12 +325,19 @@ ModeCoef<T> mode_coef(const double K[3], double c, double eps0, double dt) {
 // f: 6 real arrays (E, B) in/out; j: 3 real arrays or nullptr; rho in/out or
 // nullptr.  Cells x fastest.  Returns the largest |imaginary part| met in the
 // inverse transforms (a real result needs Hermitian spectra).
+// Split parts stored per component (PML): E_x along y, E_y along z, E_z
+// along x, B_x along y, B_y along z, B_z along x.
+const int kSplitDir[6] = {1, 2, 0, 1, 2, 0};
+
 template <typename T>
 double push_box(int nx, int ny, int nz, const double h[3], int p, double dt, double c, double eps0, int form,
-                bool nodal, T* const* f, const T* const* j, T* rho) {
+                bool nodal, T* const* f, const T* const* j, T* rho, T* const* dsplit = nullptr) {
   const int64_t N = (int64_t)nx * ny * nz;
   const int nslots = form == kVacuum ? 6 : form == kJ ? 9 : 10;
   std::vector<std::vector<cx<T>>> S(nslots, std::vector<cx<T>>(N));
+  // increments of the stored split parts (centred, then shifted like their
+  // components), when asked for
+  std::vector<std::vector<cx<T>>> D(dsplit ? 6 : 0, std::vector<cx<T>>(N));
   // slots 0-5: E, B; 6-8: J; 9: rho (component index into kYee)
   for (int s = 0; s < nslots; ++s) {
     const T* src = s < 6 ? f[s] : s < 9 ? j[s - 6] : rho;
@@ -347,7 +377,27 @@ double push_box(int nx, int ny, int nz, const double h[3], int p, double dt, dou
       J[d] = form != kVacuum ? mul(S[6 + d][idx], ph[6 + d]) : cx<T>(0, 0);
     }
     if (form == kRho) R = mul(S[9][idx], ph[9]);
-    update_mode(E, B, J, &R, mode_coef<T>(KK, c, eps0, dt), form);
+    const ModeCoef<T> mc = mode_coef<T>(KK, c, eps0, dt);
+    if (dsplit) {
+      // time integrals of E and B over the step (vacuum mode solution)
+      const T* K = mc.K;
+      const cx<T> I(0, 1);
+      const cx<T> KdE = K[0] * E[0] + K[1] * E[1] + K[2] * E[2];
+      const cx<T> KdB = K[0] * B[0] + K[1] * B[1] + K[2] * B[2];
+      const cx<T> KxE[3] = {K[1] * E[2] - K[2] * E[1], K[2] * E[0] - K[0] * E[2], K[0] * E[1] - K[1] * E[0]};
+      const cx<T> KxB[3] = {K[1] * B[2] - K[2] * B[1], K[2] * B[0] - K[0] * B[2], K[0] * B[1] - K[1] * B[0]};
+      cx<T> IE[3], IB[3];
+      for (int d = 0; d < 3; ++d) {
+        IE[d] = mc.Sw * E[d] - mc.X3 * K[d] * KdE + mul(I, mc.X1 * KxB[d]);
+        IB[d] = mc.Sw * B[d] - mc.X3 * K[d] * KdB - mul(I, mc.X1 * mc.icc * KxE[d]);
+      }
+      // dE_xy = i c^2 K_y I[B_z], dE_yz = i c^2 K_z I[B_x], dE_zx = i c^2 K_x I[B_y]
+      // dB_xy = -i K_y I[E_z],    dB_yz = -i K_z I[E_x],    dB_zx = -i K_x I[E_y]
+      const cx<T> d6[6] = {mul(I, mc.cc * K[1] * IB[2]), mul(I, mc.cc * K[2] * IB[0]), mul(I, mc.cc * K[0] * IB[1]),
+                           -mul(I, K[1] * IE[2]), -mul(I, K[2] * IE[0]), -mul(I, K[0] * IE[1])};
+      for (int q = 0; q < 6; ++q) D[q][idx] = mul(d6[q], std::conj(ph[q]));
+    }
+    update_mode(E, B, J, &R, mc, form);
     for (int d = 0; d < 3; ++d) {
       S[d][idx] = mul(E[d], std::conj(ph[d]));
       S[3 + d][idx] = mul(B[d], std::conj(ph[3 + d]));
@@ -368,6 +418,11 @@ double push_box(int nx, int ny, int nz, const double h[3], int p, double dt, dou
       im = std::max(im, (double)std::fabs(S[s][i].imag() * inv));
     }
     imag = std::max(imag, im);
+  }
+  for (int q = 0; q < (dsplit ? 6 : 0); ++q) {
+    fft3(D[q].data(), nx, ny, nz, +1);
+#pragma omp parallel for schedule(static) if (N >= 65536)
+    for (int64_t i = 0; i < N; ++i) dsplit[q][i] = D[q][i].real() * inv;
   }
   return imag;
 }
@@ -573,10 +628,63 @@ int exchange(const oracle_layout* L, double* data) {
   return 0;
 }
 
+}  // namespace
+
+extern "C" {
+// Absorbing layers on both faces of every axis d with width[d] > 0 (cells):
+// conductivity s_max[d] (xi/width[d])^order at depth xi into the layer.
+typedef struct {
+  int32_t width[3];
+  double sigma_max[3];
+  int32_t order;
+} oracle_pml;
+}
+
+namespace {
+
+// s_d at position pos (cells, Yee offset included) of an axis of n cells.
+double pml_sigma(const oracle_pml* P, int d, double pos, int64_t n) {
+  const double w = P->width[d];
+  if (w <= 0) return 0.0;
+  double xi = 0.0;
+  if (pos < w)
+    xi = w - pos;
+  else if (pos > n - w)
+    xi = pos - (n - w);
+  xi = std::min(xi, w);
+  return xi > 0 ? P->sigma_max[d] * std::pow(xi / w, (double)P->order) : 0.0;
+}
+
+// Step (2) of the PML on the interior cells of box i: add the split-part
+// increments, damp both parts, and rebuild the components.
+template <typename T>
+void pml_damp(const oracle_layout* L, int i, const oracle_pml* P, double dt, T* const* f, const T* const* dsp,
+              double* const* split, int64_t off) {
+  const oracle_box& b = L->boxes[i];
+  for (int q = 0; q < 6; ++q) {
+    const int axis = q % 3, sa = kSplitDir[q], sb = 3 - axis - sa;
+    const double* yee = kYee[q];
+    for (int64_t z = b.ng_lo[2]; z < b.n[2] - b.ng_hi[2]; ++z)
+      for (int64_t y = b.ng_lo[1]; y < b.n[1] - b.ng_hi[1]; ++y)
+        for (int64_t x = b.ng_lo[0]; x < b.n[0] - b.ng_hi[0]; ++x) {
+          const int64_t li = x + b.n[0] * (y + b.n[1] * z);
+          const double pos[3] = {b.origin[0] + (x - b.ng_lo[0]) + yee[0], b.origin[1] + (y - b.ng_lo[1]) + yee[1],
+                                 b.origin[2] + (z - b.ng_lo[2]) + yee[2]};
+          const T ea = (T)std::exp(-pml_sigma(P, sa, pos[sa], L->global_n[sa]) * dt);
+          const T eb = (T)std::exp(-pml_sigma(P, sb, pos[sb], L->global_n[sb]) * dt);
+          const T ps = (T)split[q][off + li] + dsp[q][li];
+          const T po = f[q][li] - ps;
+          const T ns = ea * ps, no = eb * po;
+          f[q][li] = ns + no;
+          split[q][off + li] = (double)ns;
+        }
+  }
+}
+
 template <typename T>
 int push_layout(const oracle_layout* L, double* const* fields, double* const* src, const uint8_t* mask,
                 int nsteps, const double h[3], double dt, double c, double eps0, int form, bool nodal,
-                double* max_imag) {
+                double* max_imag, const oracle_pml* pml = nullptr, double* const* split = nullptr) {
   const bool guards = has_guards(L);
   double imag = 0;
   int64_t off = 0;
@@ -607,8 +715,13 @@ int push_layout(const oracle_layout* L, double* const* fields, double* const* sr
       for (int s = 0; s < 6; ++s) fp[s] = f[s].data();
       if (form != kVacuum)
         for (int s = 0; s < 3; ++s) jp[s] = jj[s].data();
+      std::vector<std::vector<T>> dsp(pml ? 6 : 0, std::vector<T>(N));
+      T* dp[6];
+      for (int q = 0; q < (pml ? 6 : 0); ++q) dp[q] = dsp[q].data();
       imag = std::max(imag, push_box<T>(b.n[0], b.n[1], b.n[2], h, b.p, dt, c, eps0, form, nodal, fp,
-                                        form != kVacuum ? jp : nullptr, form == kRho ? r[0].data() : nullptr));
+                                        form != kVacuum ? jp : nullptr, form == kRho ? r[0].data() : nullptr,
+                                        pml ? dp : nullptr));
+      if (pml) pml_damp<T>(L, i, pml, dt, fp, dp, split, offs[i]);
       for (int s = 0; s < 6; ++s)
         for (int64_t q = 0; q < N; ++q) fields[s][offs[i] + q] = (double)f[s][q];
       if (form == kRho)
@@ -658,16 +771,24 @@ int oracle_couple(const oracle_layout* src, const double* src_data, const oracle
 // form: 0 vacuum, 1 J form, 2 rho form.  precision: 64 (the oracle) or 32
 // (the FP32 rounding model).  *max_imag (may be NULL): largest imaginary part
 // met in an inverse transform.
+//
+// pml (may be NULL): absorbing layers; then split holds the 6 stored split
+// parts (E_xy, E_yz, E_zx, B_xy, B_yz, B_zx; same layout as the fields,
+// interior cells in/out) and the form must be vacuum on a global, local or
+// hybrid layout (the layers sit on the faces of the global domain).
 int oracle_push(const oracle_layout* L, double* const* fields, double* const* src, const uint8_t* mask,
                 int nsteps, const double* h, double dt, double c, double eps0, int form, int nodal,
-                int precision, double* max_imag) {
+                int precision, double* max_imag, const oracle_pml* pml, double* const* split) {
   if (!L || !fields || !h || nsteps < 0 || form < 0 || form > 2) return 1;
   if (form != kVacuum && (!src || !src[0] || !src[1] || !src[2])) return 1;
   if (form == kRho && !src[3]) return 1;
+  if (pml && (!split || form != kVacuum || L->kind == 3 || nodal || pml->order < 0)) return 1;
   if (precision == 64)
-    return push_layout<double>(L, fields, src, mask, nsteps, h, dt, c, eps0, form, nodal != 0, max_imag);
+    return push_layout<double>(L, fields, src, mask, nsteps, h, dt, c, eps0, form, nodal != 0, max_imag, pml,
+                               split);
   if (precision == 32)
-    return push_layout<float>(L, fields, src, mask, nsteps, h, dt, c, eps0, form, nodal != 0, max_imag);
+    return push_layout<float>(L, fields, src, mask, nsteps, h, dt, c, eps0, form, nodal != 0, max_imag, pml,
+                              split);
   return 1;
 }
 

@@ -61,6 +61,15 @@ class _Box(ctypes.Structure):
                 ("origin", ctypes.c_int64 * 3), ("p", ctypes.c_int32)]
 
 
+class _Pml(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32 * 3), ("sigma_max", ctypes.c_double * 3), ("order", ctypes.c_int32)]
+
+
+# the stored split part of every component in the PML (the other part is the
+# component minus it): E_x along y, E_y along z, E_z along x, same for B
+SPLIT = ("Exy", "Eyz", "Ezx", "Bxy", "Byz", "Bzx")
+
+
 class _Layout(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("global_n", ctypes.c_int32 * 3), ("periodic", ctypes.c_int32 * 3),
                 ("nbox", ctypes.c_int32), ("boxes", ctypes.POINTER(_Box))]
@@ -83,7 +92,8 @@ def _L():
         lib.oracle_update_modes.argtypes = [I64, PP, PP, PP, P, PP, D, D, D, I32]
         lib.oracle_exchange.argtypes = [ctypes.POINTER(_Layout), P]
         lib.oracle_couple.argtypes = [ctypes.POINTER(_Layout), P, ctypes.POINTER(_Layout), P]
-        lib.oracle_push.argtypes = [ctypes.POINTER(_Layout), PP, PP, P, I32, P, D, D, D, I32, I32, I32, P]
+        lib.oracle_push.argtypes = [ctypes.POINTER(_Layout), PP, PP, P, I32, P, D, D, D, I32, I32, I32, P,
+                                    ctypes.POINTER(_Pml), PP]
         for f in ("oracle_fft3", "oracle_weights", "oracle_modified_wavenumber", "oracle_coefficients",
                   "oracle_update_modes", "oracle_exchange", "oracle_couple", "oracle_push"):
             getattr(lib, f).restype = I32
@@ -278,12 +288,16 @@ def couple(src_layout, src_arrays, dst_layout):
 
 
 def push(layout, fields, src, nsteps, h, dt, c=1.0, eps0=1.0, form="vacuum", boxes=None, nodal=False,
-         precision=64, return_imag=False):
+         precision=64, return_imag=False, pml=None):
     """Advance ``fields`` (dict comp -> list of per-box arrays) by ``nsteps``
     steps: every step advances each box, then exchanges guards.  With form
     'rho', ``src['rho']`` is advanced too and returned in the output dict.
     ``boxes`` restricts the advance to a subset (no exchange then).
-    precision 32 runs the FP32 rounding model instead of the oracle."""
+    precision 32 runs the FP32 rounding model instead of the oracle.
+
+    pml: absorbing layers, dict(width=(wx, wy, wz), sigma_max=(sx, sy, sz),
+    order=m); the stored split parts are read from ``fields[SPLIT[i]]`` when
+    present (else zero) and returned in the output dict (vacuum form)."""
     L = _layout(layout)
     f = [_pack(layout, fields[k]) for k in COMPS]
     s = None
@@ -296,11 +310,21 @@ def push(layout, fields, src, nsteps, h, dt, c=1.0, eps0=1.0, form="vacuum", box
         mask[list(boxes)] = 1
     imag = np.zeros(1)
     hh = np.asarray(h, dtype=np.float64)
+    pm, sp = None, None
+    if pml is not None:
+        pm = _Pml()
+        pm.width[:] = [int(v) for v in pml["width"]]
+        pm.sigma_max[:] = [float(v) for v in pml["sigma_max"]]
+        pm.order = int(pml["order"])
+        sp = [_pack(layout, fields[k]) if k in fields else np.zeros(f[0].size) for k in SPLIT]
     rc = _L().oracle_push(ctypes.byref(L), _pp(f), _pp(s) if s else None,
                           _ptr(mask) if mask is not None else None, int(nsteps), _ptr(hh), float(dt), float(c),
-                          float(eps0), _FORMS[form], int(nodal), int(precision), _ptr(imag))
+                          float(eps0), _FORMS[form], int(nodal), int(precision), _ptr(imag),
+                          ctypes.byref(pm) if pm is not None else None, _pp(sp) if sp else None)
     _check(rc, "push")
     out = {k: _unpack(layout, a) for k, a in zip(COMPS, f)}
+    if sp:
+        out.update({k: _unpack(layout, a) for k, a in zip(SPLIT, sp)})
     if form == "rho":
         out["rho"] = _unpack(layout, s[3])
     if return_imag:

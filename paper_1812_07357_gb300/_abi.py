@@ -90,6 +90,8 @@ _SIGS = {
     "psatd_last_error": (c_char_p, [c_void_p]),
     "psatd_last_launch_count": (c_int64, [c_void_p]),
     "psatd_plan_set_timing": (c_int32, [c_void_p, c_int32]),
+    "psatd_plan_tune": (c_int32, [c_void_p, c_int32, c_int32]),
+    "psatd_plan_tuning": (c_int32, [c_void_p, c_int32]),
     "psatd_plan_kernel_times": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32]),
     "psatd_plan_fast_boxes": (c_int32, [c_void_p]),
     "psatd_plan_pencil_boxes": (c_int32, [c_void_p]),
@@ -303,6 +305,17 @@ def psatd_last_launch_count(plan: int) -> int:
 
 def psatd_plan_set_timing(plan: int, enable: bool):
     _check(load().psatd_plan_set_timing(c_void_p(plan), 1 if enable else 0), plan)
+
+
+PSATD_TUNE_Z_PREFETCH = 1
+
+
+def psatd_plan_tune(plan: int, knob: int, value: int):
+    _check(load().psatd_plan_tune(c_void_p(plan), int(knob), int(value)), plan)
+
+
+def psatd_plan_tuning(plan: int, knob: int) -> int:
+    return int(load().psatd_plan_tuning(c_void_p(plan), int(knob)))
 
 
 def psatd_plan_kernel_times(plan: int):

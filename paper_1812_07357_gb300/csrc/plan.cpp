@@ -333,6 +333,7 @@ struct psatd_plan {
   int reg_code = -1;                           // register plane kernels for every fast box
   int reg_z = 0;                               // register z kernel length (0: none)
   int reg_zst = 0;                             // n1 * (n0/2 + 1) of every register-z box, else 0
+  int z_prefetch = 0;                          // register z kernel: L2 prefetch distance in CTAs
 
   // device memory
   std::vector<void*> allocs;
@@ -1518,7 +1519,7 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
   if (!P->zfast.empty() && P->reg_z) {
     CK(P, timed(P, 2, st, [&] {
          return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, P->reg_zst,
-                             NFT, st);
+                             NFT, P->z_prefetch, st);
        }));
     ++launches;
   } else if (!P->zfast.empty()) {
@@ -1741,6 +1742,35 @@ int32_t psatd_plan_fast_boxes(const psatd_plan* p) { return p ? p->fast_boxes : 
 int32_t psatd_plan_pencil_boxes(const psatd_plan* p) { return p ? p->pen_boxes : -1; }
 
 int32_t psatd_plan_deferred_exchange(const psatd_plan* p) { return p ? (p->deferred ? 1 : 0) : -1; }
+
+psatd_status psatd_plan_tune(psatd_plan* P, int32_t knob, int32_t value) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  switch (knob) {
+    case PSATD_TUNE_Z_PREFETCH:
+      if (value < 0 || value > (1 << 20)) return fail(P, PSATD_ERR_INVALID_ARG, "prefetch distance out of range");
+      P->z_prefetch = value;
+      break;
+    default:
+      return fail(P, PSATD_ERR_INVALID_ARG, "unknown tuning knob");
+  }
+  // captured graphs hold the old launch parameters
+  for (cudaGraphExec_t& g : P->graph_exec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  return PSATD_OK;
+}
+
+int32_t psatd_plan_tuning(const psatd_plan* P, int32_t knob) {
+  if (!P) return -1;
+  switch (knob) {
+    case PSATD_TUNE_Z_PREFETCH:
+      return P->reg_z ? P->z_prefetch : -1;
+    default:
+      return -1;
+  }
+}
 
 psatd_status psatd_plan_set_timing(psatd_plan* P, int32_t enable) {
   if (!P) return PSATD_ERR_INVALID_ARG;

@@ -243,8 +243,10 @@ int z_reg_ok(int n2);
 int z_reg_smem(int form, int n2);
 int z_reg_tile_width(int form);
 // zst: n1 * (n0/2 + 1) shared by every box of the job list, else 0
+// pf_dist > 0: every CTA first prefetches into L2 the tile of the CTA
+// launched pf_dist blocks after it
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                         int64_t njobs, int n2, int zst, int nft, cudaStream_t st);
+                         int64_t njobs, int n2, int zst, int nft, int pf_dist, cudaStream_t st);
 
 // ---- pencil kernels (pencil_kernels.cu): boxes of two-pass lengths too large
 // for the plane kernels; the z pass takes fast_tile(prec) mx columns per tile

@@ -412,9 +412,29 @@ constexpr int z_reg_min_blocks() {
 // ZST > 0: every box of the launch has n1 * (n0/2 + 1) = ZST (the z stride of
 // the spectrum), a compile-time constant, so that the z-strided loads and
 // stores take immediate offsets.
+// L2 prefetch of the input rows of z tile `job` (every slot, every z plane;
+// a row of at most TX complex values spans at most two 128-byte lines).
+// Nyquist-column tiles (scattered values) are not prefetched.
+template <int NZ, int FORM>
+__device__ __forceinline__ void prefetch_z_tile(const DevPlan& P, const float2* spec, int64_t sstride,
+                                                const ColJob& J) {
+  constexpr int FIN = fields_in(FORM), NT = z_reg_threads<FORM>();
+  if (J.nm < 0) return;
+  const BoxDev bx = P.boxes[J.box];
+  const int hx = P.shapes[bx.shape].hx;
+  const int64_t zst = (int64_t)bx.n[1] * hx;
+  const float2* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
+  for (int r = threadIdx.x; r < 2 * FIN * NZ; r += NT) {
+    const int row = r >> 1, s = row / NZ, z = row - s * NZ;
+    const float2* a = g + s * sstride + z * zst + (r & 1) * (J.nm - 1);
+    asm volatile("prefetch.global.L2::evict_last [%0];\n" ::"l"(a));
+  }
+}
+
 template <int NZ, int FORM, int ZST>
 __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>())
-    k_z_reg(DevPlan P, float2* spec, int64_t sstride, const ColJob* __restrict__ jobs, int nft) {
+    k_z_reg(DevPlan P, float2* spec, int64_t sstride, const ColJob* __restrict__ jobs, int nft, int njobs,
+            int pf_dist) {
   constexpr int TX = z_reg_tile(FORM), FIN = fields_in(FORM), FOUT = fields_out(FORM);
   constexpr int NT = z_reg_threads<FORM>(), NP = z_reg_pitch(FORM);
   constexpr int H = NZ / 2;
@@ -422,6 +442,10 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* buf = reinterpret_cast<float2*>(smem_raw);    // [row][slot * TX + t], pitch NP
   const ColJob J = jobs[blockIdx.x];
+  // the tile that a CTA launched about pf_dist blocks later will read: fetched
+  // into L2 now, so that its loads hit L2 instead of waiting on HBM
+  if (pf_dist > 0 && (int)blockIdx.x + pf_dist < njobs)
+    prefetch_z_tile<NZ, FORM>(P, spec, sstride, jobs[blockIdx.x + pf_dist]);
   const BoxDev bx = P.boxes[J.box];
   const ShapeDev& sh = P.shapes[bx.shape];
   const int hx = sh.hx, n1 = bx.n[1];
@@ -537,12 +561,13 @@ int z_reg_tile_width(int form) { return z_reg_tile(form); }
 constexpr int kRegZst = 96 * 49;
 
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                         int64_t njobs, int n2, int zst, int nft, cudaStream_t st) {
+                         int64_t njobs, int n2, int zst, int nft, int pf_dist, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs);
   const int smem = z_reg_smem(form, n2);
-#define PSATD_ZF(NZV, F, ZS) \
-  k_z_reg<NZV, F, ZS><<<grid, z_reg_threads<F>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft)
+#define PSATD_ZF(NZV, F, ZS)                                                                      \
+  k_z_reg<NZV, F, ZS><<<grid, z_reg_threads<F>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft, \
+                                                               (int)njobs, pf_dist)
 #define PSATD_ZL(NZV)                                                    \
   if (n2 == NZV) {                                                      \
     if (form == kVacuum) {                                              \

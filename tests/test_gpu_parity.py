@@ -336,3 +336,21 @@ def test_register_z_kernel_sources(form):
         src["rho"] = [np.zeros(shp)]
         fields = {k: [np.zeros(shp)] for k in O.COMPS}
     _fast_plan_check(lay, fields, src, 3, (1.0, 1.0, 1.0), 0.9, 32, form, 1)
+
+
+def test_global_reference_lengths_fp64_long_step():
+    """The global single-box FP64 reference of the benchmark's error leg runs
+    the generic kernels at lengths 512 (512^3 domain) and 1024, 256 (the
+    1024 x 256 x 256 domain), one step of 400 dt (no Courant limit, Sec.
+    1.1).  Each length on a self-periodic box with short other axes, against
+    the oracle's same step."""
+    boxes = [I.Box(n, (0, 0, 0), (0, 0, 0), (0, 0, 0), p) for n, p in
+             [((512, 16, 16), 32), ((16, 512, 16), 32), ((16, 16, 512), 32),
+              ((1024, 16, 16), 64), ((16, 256, 16), 64), ((16, 16, 256), 0)]]
+    lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
+    rng = np.random.default_rng(29)
+    fields = {k: [rng.standard_normal(b.shape) for b in lay.boxes] for k in O.COMPS}
+    plan = Plan(lay, (1.0,) * 3, 400 * 0.9, precision=64, sources="vacuum")
+    assert (plan.fast_boxes, plan.pencil_boxes) == (0, 0)
+    plan.close()
+    check_push(lay, fields, {}, 1, (1.0,) * 3, 400 * 0.9, 64, "vacuum")
