@@ -745,3 +745,77 @@ def test_fp32_rounding_model():
     for k in b:          # every value is an FP32 number
         for x in b[k]:
             assert np.array_equal(x, x.astype(np.float32).astype(np.float64))
+
+
+# ---------------------------------------------------------------------------
+# Absorbing layers (two-step split-field PML; the paper, Sec. 3.1 end, only
+# names the method): the oracle's layers against closed forms
+# ---------------------------------------------------------------------------
+
+def _pulse_along_x(nx, ny, nz, x0=128.0, tau=10.0, lam=16.0):
+    x = np.arange(nx)
+    g = lambda xs: np.exp(-((xs - x0) / tau) ** 2) * np.cos(2 * np.pi / lam * (xs - x0))
+    f = {k: np.zeros((nz, ny, nx)) for k in psatd_oracle.COMPS}
+    f["Ey"][:] = g(x + 0.0)[None, None, :]          # E_y at (i, j + 1/2, k): x offset 0
+    f["Bz"][:] = g(x + 0.5)[None, None, :]          # B_z at (i + 1/2, j + 1/2, k)
+    return f
+
+
+def test_pml_without_conductivity_is_the_plain_push():
+    rng = np.random.default_rng(61)
+    lay = I.local_layout((32, 16, 16), (2, 1, 1), 4, 8)
+    f = {k: psatd_oracle.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes])
+         for k in psatd_oracle.COMPS}
+    a = psatd_oracle.push(lay, f, {}, 3, (1.0,) * 3, 0.7)
+    b = psatd_oracle.push(lay, f, {}, 3, (1.0,) * 3, 0.7,
+                          pml=dict(width=(6, 4, 0), sigma_max=(0.0, 0.0, 0.0), order=2))
+    for k in psatd_oracle.COMPS:
+        for x, y in zip(a[k], b[k]):
+            assert np.abs(x - y).max() <= 1e-13 * (1 + np.abs(y).max())
+
+
+@pytest.mark.parametrize("smax,order,p", [(0.1875, 2, 0), (0.09375, 2, 16), (0.25, 3, 0)])
+def test_pml_normal_incidence_transmission_and_reflection(smax, order, p):
+    """A pulse along +x in a periodic 256-cell box with layers of w = 32 cells
+    on both x faces: after one lap (it crosses both layers) its amplitude is
+    exp(-int s dx / c) = exp(-2 s_max w / (c (m + 1))), the attenuation of a
+    continuous matched layer at normal incidence; a continuous PML reflects
+    nothing, so the field left behind the pulse once it is inside the layer
+    stays at the discretisation level; the energy never grows."""
+    nx, w, dt = 256, 32, 0.5
+    lay = I.global_layout((nx, 4, 4), p)
+    f0 = _pulse_along_x(nx, 4, 4)
+    cur = {k: [v] for k, v in f0.items()}
+    pml = dict(width=(w, 0, 0), sigma_max=(smax, 0.0, 0.0), order=order)
+    e_prev = sum(float(np.sum(v ** 2)) for v in f0.values())
+    refl = None
+    for s in range(int(256 / dt)):
+        cur = psatd_oracle.push(lay, cur, {}, 1, (1.0,) * 3, dt, pml=pml)
+        e = sum(float(np.sum(cur[k][0] ** 2)) for k in psatd_oracle.COMPS)
+        assert e <= e_prev * (1 + 1e-12)
+        e_prev = e
+        if (s + 1) * dt == 112:          # pulse centre at x = 240, inside the high-x layer
+            ey = cur["Ey"][0][0, 0]
+            refl = float(np.sqrt(np.sum(ey[40:200] ** 2) / np.sum(f0["Ey"][0, 0] ** 2)))
+    amp = float(np.abs(cur["Ey"][0][0, 0]).max())
+    ana = math.exp(-2 * smax * w / (order + 1))
+    assert abs(amp / ana - 1) < 0.01, (amp, ana)
+    assert refl < 1e-5, refl
+
+
+def test_pml_split_parts_sum_to_the_fields():
+    """A wave along x has d/dy = d/dz = 0: started with the whole of B_z in
+    its x part (B_zx = B_z) and E_y in its x part (E_yz = 0), the y part of
+    B_z and the z part of E_y must stay exactly 0 in and outside the layers,
+    i.e. the stored parts keep summing to the components."""
+    nx = 64
+    lay = I.global_layout((nx, 8, 8), 8)
+    f0 = _pulse_along_x(nx, 8, 8, x0=40.0, tau=4.0, lam=8.0)
+    cur = {k: [v] for k, v in f0.items()}
+    cur["Bzx"] = [f0["Bz"].copy()]
+    pml = dict(width=(8, 0, 0), sigma_max=(0.5, 0.0, 0.0), order=2)
+    for _ in range(40):
+        cur = psatd_oracle.push(lay, cur, {}, 1, (1.0,) * 3, 0.5, pml=pml)
+    scale = np.abs(f0["Bz"]).max()
+    assert np.abs(cur["Bz"][0] - cur["Bzx"][0]).max() < 1e-12 * scale
+    assert np.abs(cur["Eyz"][0]).max() < 1e-12 * scale
