@@ -118,6 +118,31 @@ typedef struct {
   int32_t order_p;
 } psatd_box;
 
+/* Absorbing layers (perfectly matched layers, PML).  The paper (end of its
+ * Sec. 2.6) states that the solver supports the two-step PML of its
+ * reference [shapoval2019two] and prints no equations; this library's
+ * reading, derived from Maxwell's equations: every component is the sum of
+ * two split parts, one per derivative direction (E_x = E_xy + E_xz with
+ * dE_xy/dt = c^2 dB_z/dy - s_y E_xy, and so on for every component), and a
+ * step is (1) the ordinary PSATD step of E and B, each split part gaining
+ * the exact time integral of its derivative term over the step, then (2)
+ * every split part along direction d multiplied by exp(-s_d dt).  Layers of
+ * width[d] cells sit inside the global domain on both faces of axis d
+ * (0: none), with conductivity s_d = sigma_max[d] (xi/width[d])^order at a
+ * depth xi (cells) into the layer, evaluated at each component's Yee
+ * position.  Requirements: PSATD_VACUUM (no current in the layers), not
+ * PSATD_NODAL, not PSATD_DECOMP_INDEPENDENT, 0 <= width[d] <= global_n[d]/2,
+ * sigma_max[d] >= 0, 0 <= order <= 16; the plan then runs the generic
+ * kernels and stores the guards every step.  The plan owns one stored split
+ * part per component (E_xy, E_yz, E_zx, B_xy, B_yz, B_zx; the other part is
+ * the component minus it), zero at creation: start with fields that vanish
+ * inside the layers, or set the parts through psatd_plan_pml_part. */
+typedef struct {
+  int32_t width[3];
+  double sigma_max[3];
+  int32_t order;
+} psatd_pml;
+
 /* Plan description.  global_n/periodic describe the global domain (ignored
  * for PSATD_DECOMP_INDEPENDENT); box interiors must tile it exactly.
  * Non-periodic axes fill guard cells outside the domain with 0.
@@ -137,6 +162,7 @@ typedef struct {
   int32_t num_boxes;
   const psatd_box* boxes;
   uint32_t flags;
+  const psatd_pml* pml;   /* absorbing layers, or NULL (read during create) */
 } psatd_plan_desc;
 
 typedef struct psatd_plan psatd_plan;
@@ -290,6 +316,12 @@ psatd_status psatd_coupling_layout(const psatd_coupling* coupling, int32_t box, 
  * one batched copy kernel.  Source and destination buffers must not overlap. */
 psatd_status psatd_couple(psatd_coupling* coupling, int32_t direction, void* const* g1_fields,
                           void* const* g2_fields, int32_t nfields, void* stream);
+
+/* Device pointer of stored split part q (0..5: E_xy, E_yz, E_zx, B_xy, B_yz,
+ * B_zx) of a plan with absorbing layers: one plan-owned buffer with the
+ * layout of a field buffer (interior cells meaningful), read and written by
+ * every psatd_push.  PSATD_ERR_STATE for a plan without layers. */
+psatd_status psatd_plan_pml_part(const psatd_plan* plan, int32_t q, void** part);
 
 /* Number of kernel launches issued by the last psatd_push call (host count). */
 int64_t psatd_last_launch_count(const psatd_plan* plan);

@@ -43,11 +43,15 @@ class psatd_box(Structure):
                 ("origin", c_int64 * 3), ("order_p", c_int32)]
 
 
+class psatd_pml(Structure):
+    _fields_ = [("width", c_int32 * 3), ("sigma_max", c_double * 3), ("order", c_int32)]
+
+
 class psatd_plan_desc(Structure):
     _fields_ = [("global_n", c_int32 * 3), ("periodic", c_int32 * 3), ("dx", c_double * 3),
                 ("dt", c_double), ("c", c_double), ("eps0", c_double), ("precision", c_int32),
                 ("decomp", c_int32), ("num_boxes", c_int32), ("boxes", POINTER(psatd_box)),
-                ("flags", c_uint32)]
+                ("flags", c_uint32), ("pml", POINTER(psatd_pml))]
 
 
 class psatd_fields(Structure):
@@ -91,6 +95,7 @@ _SIGS = {
     "psatd_last_launch_count": (c_int64, [c_void_p]),
     "psatd_plan_set_timing": (c_int32, [c_void_p, c_int32]),
     "psatd_plan_tune": (c_int32, [c_void_p, c_int32, c_int32]),
+    "psatd_plan_pml_part": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
     "psatd_plan_tuning": (c_int32, [c_void_p, c_int32]),
     "psatd_plan_kernel_times": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32]),
     "psatd_plan_fast_boxes": (c_int32, [c_void_p]),
@@ -308,6 +313,12 @@ def psatd_plan_set_timing(plan: int, enable: bool):
 
 
 PSATD_TUNE_Z_PREFETCH = 1
+
+
+def psatd_plan_pml_part(plan: int, q: int) -> int:
+    out = c_void_p()
+    _check(load().psatd_plan_pml_part(c_void_p(plan), int(q), ctypes.byref(out)), plan)
+    return out.value
 
 
 def psatd_plan_tune(plan: int, knob: int, value: int):

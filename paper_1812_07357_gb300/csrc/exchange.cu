@@ -10,6 +10,7 @@
 // units, a thread moves 16 bytes at a time (XTile::vec > 1).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "psatd_internal.h"
@@ -88,7 +89,63 @@ __global__ void __launch_bounds__(256) k_exchange(const BoxDev* __restrict__ dbo
     copy_tile<T, 1>(dbase, sbase, b, t, db, sfoff, sn0, sn1);
 }
 
+// Absorbing layers, step (2) (the split-field PML: each component is the sum
+// of two parts, one per derivative direction; the part along direction d
+// decays by exp(-s_d dt) over the step).  For component q the stored part is
+// along kStored[q] and the other part along the remaining direction; with
+// the step's increment of the stored part (slot 6 + q of f):
+//   stored* = stored + increment,  other* = component - stored*,
+//   stored' = e_stored stored*,    other' = e_other other*,
+//   component = stored' + other'.
+// Grid: x strides over the interior cells of box blockIdx.y of the list.
+__constant__ int kStored[6] = {1, 2, 0, 1, 2, 0};    // E_xy, E_yz, E_zx, B_xy, B_yz, B_zx
+// Yee offset of component q along axis d, in half cells (0 or 1)
+__constant__ int kYeeHalf[6][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 1}, {1, 1, 0}};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_pml_damp(DevPlan P, FieldPtrs F, FieldPtrs S, const PmlBox* __restrict__ boxes,
+                                                  const T* __restrict__ tab, PmlTab t) {
+  const PmlBox pb = boxes[blockIdx.y];
+  const BoxDev bx = P.boxes[pb.box];
+  const int m0 = bx.n[0] - bx.ng_lo[0] - bx.ng_hi[0], m1 = bx.n[1] - bx.ng_lo[1] - bx.ng_hi[1];
+  const int m2 = bx.n[2] - bx.ng_lo[2] - bx.ng_hi[2];
+  const int64_t cells = (int64_t)m0 * m1 * m2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cells; e += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % m0), y = (int)((e / m0) % m1), z = (int)(e / ((int64_t)m0 * m1));
+    const int g[3] = {pb.origin[0] + x, pb.origin[1] + y, pb.origin[2] + z};
+    const int64_t li =
+        bx.foff + ((int64_t)(z + bx.ng_lo[2]) * bx.n[1] + (y + bx.ng_lo[1])) * bx.n[0] + (x + bx.ng_lo[0]);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int axis = q % 3, sa = kStored[q], sb = 3 - axis - sa;
+      const T ea = tab[t.off[sa][kYeeHalf[q][sa]] + g[sa]];
+      const T eb = tab[t.off[sb][kYeeHalf[q][sb]] + g[sb]];
+      T* f = reinterpret_cast<T*>(F.p[q]) + li;
+      T* sp = reinterpret_cast<T*>(S.p[q]) + li;
+      const T ps = *sp + reinterpret_cast<const T*>(F.p[6 + q])[li];
+      const T po = *f - ps;
+      const T ns = ea * ps;
+      *f = ns + eb * po;
+      *sp = ns;
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_pml_damp(int prec, const DevPlan& P, const FieldPtrs& f, const FieldPtrs& parts,
+                            const PmlBox* boxes, int nboxes, const void* tab, const PmlTab& t, cudaStream_t st) {
+  for (int b0 = 0; b0 < nboxes; b0 += 65535) {
+    dim3 grid(64, (unsigned)std::min(65535, nboxes - b0));
+    if (prec == 32)
+      k_pml_damp<float><<<grid, 256, 0, st>>>(P, f, parts, boxes + b0, (const float*)tab, t);
+    else
+      k_pml_damp<double><<<grid, 256, 0, st>>>(P, f, parts, boxes + b0, (const double*)tab, t);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_exchange(int prec, const DevPlan& P, const FieldPtrs& f, int nf,
                             const CopyBlk* blocks, const XTile* tiles, int64_t ntiles,

@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_z_update(DevPlan P, cx<T>* spec, i
                                                        const ColJob* __restrict__ jobs, int nft) {
   constexpr int FIN = fields_in(FORM);
   constexpr int FOUT = fields_out(FORM);
+  constexpr int NS = spec_slots(FORM);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* sm = reinterpret_cast<cx<T>*>(smem_raw);
   const ColJob J = jobs[blockIdx.x];
@@ -192,13 +193,13 @@ __global__ void __launch_bounds__(kThreads) k_z_update(DevPlan P, cx<T>* spec, i
   const ShapeDev& sh = P.shapes[bx.shape];
   const int hx = sh.hx, n1 = bx.n[1], n2 = bx.n[2];
   const int nm = J.nm;
-  const int row = FIN * nm;
+  const int row = NS * nm, rowi = FIN * nm;
   const int64_t zstride = (int64_t)n1 * hx;
   cx<T>* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
-  for (int e = threadIdx.x; e < n2 * row; e += blockDim.x) {
-    const int z = e / row, r = e - z * row;
+  for (int e = threadIdx.x; e < n2 * rowi; e += blockDim.x) {
+    const int z = e / rowi, r = e - z * rowi;
     const int s = r / nm, t = r - s * nm;
-    sm[e] = g[s * sstride + z * zstride + t];
+    sm[z * row + r] = g[s * sstride + z * zstride + t];
   }
   __syncthreads();
   const cx<T>* twz = cpool<T>(P) + sh.az.tw;
@@ -306,10 +307,12 @@ cudaError_t launch_z_update(int prec, int form, const DevPlan& P, void* spec, in
   if (prec == 32) {
     if (form == kVacuum) PSATD_ZU(float, float2, kVacuum);
     else if (form == kJForm) PSATD_ZU(float, float2, kJForm);
+    else if (form == kPml) PSATD_ZU(float, float2, kPml);
     else PSATD_ZU(float, float2, kRhoForm);
   } else {
     if (form == kVacuum) PSATD_ZU(double, double2, kVacuum);
     else if (form == kJForm) PSATD_ZU(double, double2, kJForm);
+    else if (form == kPml) PSATD_ZU(double, double2, kPml);
     else PSATD_ZU(double, double2, kRhoForm);
   }
 #undef PSATD_ZU
@@ -344,6 +347,7 @@ cudaError_t configure_kernels(int prec, int smem) {
     PSATD_SET((k_z_update<float, kVacuum>));
     PSATD_SET((k_z_update<float, kJForm>));
     PSATD_SET((k_z_update<float, kRhoForm>));
+    PSATD_SET((k_z_update<float, kPml>));
     PSATD_SET(k_inv_x<float>);
   } else {
     PSATD_SET(k_fwd_x<double>);
@@ -352,6 +356,7 @@ cudaError_t configure_kernels(int prec, int smem) {
     PSATD_SET((k_z_update<double, kVacuum>));
     PSATD_SET((k_z_update<double, kJForm>));
     PSATD_SET((k_z_update<double, kRhoForm>));
+    PSATD_SET((k_z_update<double, kPml>));
     PSATD_SET(k_inv_x<double>);
   }
 #undef PSATD_SET

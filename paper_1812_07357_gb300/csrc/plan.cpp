@@ -88,6 +88,19 @@ Err validate(const psatd_plan_desc* d) {
     if (!(b.order_p == 0 || (b.order_p >= 2 && b.order_p <= 256 && b.order_p % 2 == 0)))
       return {PSATD_ERR_UNSUPPORTED_ORDER, fmt("box %d: order %d is not 0 or even in [2, 256]", i, b.order_p)};
   }
+  if (d->pml) {
+    if (!(d->flags & PSATD_VACUUM)) return {PSATD_ERR_INVALID_ARG, "absorbing layers need PSATD_VACUUM"};
+    if (d->flags & PSATD_NODAL) return {PSATD_ERR_INVALID_ARG, "absorbing layers need the staggered grid"};
+    if (d->decomp == PSATD_DECOMP_INDEPENDENT)
+      return {PSATD_ERR_INVALID_ARG, "absorbing layers need a global domain"};
+    if (d->pml->order < 0 || d->pml->order > 16) return {PSATD_ERR_INVALID_ARG, "PML order not in [0, 16]"};
+    for (int a = 0; a < 3; ++a) {
+      if (d->pml->width[a] < 0 || 2 * d->pml->width[a] > d->global_n[a])
+        return {PSATD_ERR_INVALID_ARG, fmt("PML width %d not in [0, global_n/2] on axis %d", d->pml->width[a], a)};
+      if (!(d->pml->sigma_max[a] >= 0.0) || !std::isfinite(d->pml->sigma_max[a]))
+        return {PSATD_ERR_INVALID_ARG, "PML sigma_max must be finite and >= 0"};
+    }
+  }
   if (d->decomp == PSATD_DECOMP_INDEPENDENT) return {PSATD_OK, ""};
   for (int a = 0; a < 3; ++a) {
     if (d->global_n[a] < 1) return {PSATD_ERR_INVALID_ARG, "global_n must be >= 1"};
@@ -334,6 +347,15 @@ struct psatd_plan {
   int reg_z = 0;                               // register z kernel length (0: none)
   int reg_zst = 0;                             // n1 * (n0/2 + 1) of every register-z box, else 0
   int z_prefetch = 0;                          // register z kernel: L2 prefetch distance in CTAs
+  // absorbing layers (form kPml): the description, boxes with layer cells,
+  // damping table, stored split parts and their per-step increments
+  psatd_pml pml{};
+  std::vector<PmlBox> pml_boxes;
+  PmlTab pml_tab{};
+  PmlBox* d_pml_boxes = nullptr;
+  void* d_pml_tab = nullptr;
+  void* pml_parts[6] = {};
+  void* pml_inc[6] = {};
 
   // device memory
   std::vector<void*> allocs;
@@ -706,7 +728,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     const int L = b.n[0] / 2, n1 = b.n[1], n2 = b.n[2], hx = L + 1;
     const int ni = n1 - b.ng_lo[1] - b.ng_hi[1];
     const int sm_pf = 2 * n1 * sh.lp * csz, sm_pi = (2 * n1 * hx + ni * sh.hp) * csz;
-    return !(d.flags & PSATD_GENERIC_KERNELS) && sh.fx >= 0 && sh.fy >= 0 && sh.fz >= 0 &&
+    return !(d.flags & PSATD_GENERIC_KERNELS) && P->form != kPml && sh.fx >= 0 && sh.fy >= 0 && sh.fz >= 0 &&
            L <= fast_max_x(P->prec) && sm_pf <= optin && sm_pi <= optin &&
            z_fast_smem(P->prec, P->form, n2) <= optin;
   };
@@ -738,7 +760,8 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       const int y0 = b.ng_lo[1], y1 = n1 - b.ng_hi[1];
       for (int y = y0; y < y1; y += nr) P->rows_int.push_back({bi, z * n1 + y, std::min(nr, y1 - y), 0});
     }
-    const bool pencil_ok = !(d.flags & PSATD_GENERIC_KERNELS) && sh.px >= 0 && sh.py >= 0 && sh.pz >= 0 &&
+    const bool pencil_ok = !(d.flags & PSATD_GENERIC_KERNELS) && P->form != kPml && sh.px >= 0 && sh.py >= 0 &&
+                           sh.pz >= 0 &&
                            n2 <= pen_z_max(P->prec) && sm_zf <= optin && pen_col_smem(P->prec, n1) <= optin;
     const bool prefer_pencil =
         (d.flags & PSATD_PENCIL_KERNELS) || (!(d.flags & PSATD_PLANE_KERNELS) && !reg_planes);
@@ -807,7 +830,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       }
     }
     P->smem_y = std::max(P->smem_y, n1 * ny * csz);
-    int nz = std::max(1, zbudget / (n2 * FIN * csz));
+    int nz = std::max(1, zbudget / (n2 * spec_slots(P->form) * csz));
     if (nz >= 4) nz = nz / 4 * 4;
     nz = std::min(nz, hx);
     for (int y = 0; y < n1; ++y)
@@ -815,7 +838,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
         P->zcols.push_back({bi, y, m, std::min(nz, hx - m)});
         if (generic) P->g_zcols.push_back({bi, y, m, std::min(nz, hx - m)});
       }
-    P->smem_z = std::max(P->smem_z, n2 * FIN * nz * csz);
+    P->smem_z = std::max(P->smem_z, n2 * spec_slots(P->form) * nz * csz);
     P->smem_zonly = std::max(P->smem_zonly, n2 * nz * csz);
   }
   // pencil jobs grouped by the FFT length of the axis each kernel transforms
@@ -977,7 +1000,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   CK(P, dalloc(P, (size_t)rtot * P->rsize, &P->d_rpool));
   CK(P, dalloc(P, (size_t)ctot * P->csize, &P->d_cpool));
   CK(P, dalloc(P, (size_t)qtot * 4 * P->rsize, &P->d_coef));
-  CK(P, dalloc(P, (size_t)FIN * P->spec_total * P->csize, &P->d_ws));
+  CK(P, dalloc(P, (size_t)spec_slots(P->form) * P->spec_total * P->csize, &P->d_ws));
   // ---- FP64 tables
   double *r64 = nullptr, *alpha = nullptr;
   double2* c64 = nullptr;
@@ -1053,6 +1076,62 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     P->grid_pf = (int)std::min<int64_t>((int64_t)occ_f * sms, (int64_t)P->plane_fwd.size() * FINv);
     P->grid_pi = (int)std::min<int64_t>((int64_t)occ_i * sms, (int64_t)P->plane_inv.size() * FOUTv);
   }
+  return PSATD_OK;
+}
+
+// Absorbing layers: the boxes whose interiors reach into a layer, the
+// damping table exp(-s_d(g + o/2) dt) per axis d, Yee offset o and global
+// index g (FP64, rounded once), the stored split parts (zero) and the
+// buffers of their per-step increments.
+psatd_status build_pml(psatd_plan* P, cudaStream_t st) {
+  if (P->form != kPml) return PSATD_OK;
+  const psatd_plan_desc& d = P->desc;
+  for (int i = 0; i < (int)P->boxes.size(); ++i) {
+    const psatd_box& b = P->boxes[i];
+    bool touches = false;
+    for (int a = 0; a < 3; ++a) {
+      const int64_t w = P->pml.width[a], m = b.n[a] - b.ng_lo[a] - b.ng_hi[a];
+      if (w > 0 && (b.origin[a] < w || b.origin[a] + m > d.global_n[a] - w)) touches = true;
+    }
+    if (touches)
+      P->pml_boxes.push_back(PmlBox{i, {(int32_t)b.origin[0], (int32_t)b.origin[1], (int32_t)b.origin[2]}});
+  }
+  std::vector<double> tab;
+  for (int a = 0; a < 3; ++a)
+    for (int o = 0; o < 2; ++o) {
+      P->pml_tab.off[a][o] = (int64_t)tab.size();
+      const double N = d.global_n[a], w = P->pml.width[a];
+      for (int g = 0; g < d.global_n[a]; ++g) {
+        const double pos = g + 0.5 * o;
+        double xi = 0.0;
+        if (w > 0 && pos < w)
+          xi = w - pos;
+        else if (w > 0 && pos > N - w)
+          xi = pos - (N - w);
+        xi = std::min(xi, w);
+        const double sig = xi > 0 ? P->pml.sigma_max[a] * std::pow(xi / w, (double)P->pml.order) : 0.0;
+        tab.push_back(std::exp(-sig * d.dt));
+      }
+    }
+  if (P->prec == 32) {
+    std::vector<float> t32(tab.begin(), tab.end());
+    float* dt32 = nullptr;
+    CK(P, upload(P, t32, &dt32));
+    P->d_pml_tab = dt32;
+  } else {
+    double* dt64 = nullptr;
+    CK(P, upload(P, tab, &dt64));
+    P->d_pml_tab = dt64;
+  }
+  CK(P, upload(P, P->pml_boxes, &P->d_pml_boxes));
+  const size_t bytes = (size_t)P->field_total * P->rsize;
+  for (int q = 0; q < 6; ++q) {
+    CK(P, dalloc(P, bytes, &P->pml_parts[q]));
+    CK(P, dalloc(P, bytes, &P->pml_inc[q]));
+    CK(P, cudaMemsetAsync(P->pml_parts[q], 0, bytes, st));
+    CK(P, cudaMemsetAsync(P->pml_inc[q], 0, bytes, st));
+  }
+  CK(P, cudaStreamSynchronize(st));
   return PSATD_OK;
 }
 
@@ -1316,6 +1395,11 @@ psatd_status psatd_plan_create(const psatd_plan_desc* desc, void* stream, psatd_
     P->csize = P->prec == 32 ? 8 : 16;
     P->rsize = P->prec == 32 ? 4 : 8;
     P->form = (desc->flags & PSATD_VACUUM) ? kVacuum : (desc->flags & PSATD_RHO_CONTINUITY) ? kRhoForm : kJForm;
+    if (desc->pml) {
+      P->pml = *desc->pml;
+      P->desc.pml = &P->pml;
+      P->form = kPml;
+    }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) {
@@ -1324,6 +1408,7 @@ psatd_status psatd_plan_create(const psatd_plan_desc* desc, void* stream, psatd_
       return fail(nullptr, PSATD_ERR_CUDA, m);
     }
     psatd_status s = build(P, (cudaStream_t)stream);
+    if (s == PSATD_OK) s = build_pml(P, (cudaStream_t)stream);
     if (s != PSATD_OK) {
       std::string m = P->last_error != "no error" ? P->last_error : g_thread_error;
       delete P;
@@ -1401,6 +1486,8 @@ static psatd_status gather_fields(psatd_plan* P, const psatd_fields* f, const ps
     if (!fp->p[i]) return fail(P, PSATD_ERR_INVALID_ARG, fmt("field slot %d is NULL", i));
     if (!aligned16(fp->p[i])) return fail(P, PSATD_ERR_INVALID_ARG, fmt("field slot %d not 16-byte aligned", i));
   }
+  if (P->form == kPml && with_sources_for_form)   // the inverse pass writes the split-part increments there
+    for (int q = 0; q < 6; ++q) fp->p[6 + q] = P->pml_inc[q];
   *nf = n;
   return PSATD_OK;
 }
@@ -1575,9 +1662,20 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
        }));
     ++launches;
   }
+  if (P->form == kPml && !P->pml_boxes.empty()) {
+    // absorbing layers, step (2): damp the split parts, rebuild the components
+    FieldPtrs parts{};
+    for (int q = 0; q < 6; ++q) parts.p[q] = P->pml_parts[q];
+    CK(P, timed(P, 4, st, [&] {
+         return launch_pml_damp(P->prec, D, fp, parts, P->d_pml_boxes, (int)P->pml_boxes.size(), P->d_pml_tab,
+                                P->pml_tab, st);
+       }));
+    ++launches;
+  }
   if (!P->step_tiles.empty() && guards) {
+    const int nex = P->form == kPml ? 6 : FOUT;   // components only, not the increments
     CK(P, timed(P, 5, st, [&] {
-         return launch_exchange(P->prec, D, fp, FOUT, P->d_blocks, P->d_step_tiles, (int64_t)P->step_tiles.size(),
+         return launch_exchange(P->prec, D, fp, nex, P->d_blocks, P->d_step_tiles, (int64_t)P->step_tiles.size(),
                                 st);
        }));
     ++launches;
@@ -1733,6 +1831,13 @@ const char* psatd_status_string(psatd_status s) {
 
 const char* psatd_last_error(const psatd_plan* p) {
   return p ? p->last_error.c_str() : g_thread_error.c_str();
+}
+
+psatd_status psatd_plan_pml_part(const psatd_plan* p, int32_t q, void** part) {
+  if (!p || !part || q < 0 || q >= 6) return PSATD_ERR_INVALID_ARG;
+  if (p->form != kPml) return PSATD_ERR_STATE;
+  *part = p->pml_parts[q];
+  return PSATD_OK;
 }
 
 int64_t psatd_last_launch_count(const psatd_plan* p) { return p ? p->last_launches : 0; }

@@ -20,10 +20,15 @@ constexpr int kMaxPoints = kThreads * kPointsPerThread;  // points of one FFT ch
 //   kVacuum: E 0-2, B 3-5                      (6 in, 6 out)
 //   kJForm : E 0-2, B 3-5, J 6-8               (9 in, 6 out)
 //   kRhoForm: E 0-2, B 3-5, rho 6, J 7-9       (10 in, 7 out)
-enum Form { kVacuum = 0, kJForm = 1, kRhoForm = 2 };
+//   kPml   : E 0-2, B 3-5 in; E, B and the increments of the stored split
+//            parts E_xy, E_yz, E_zx, B_xy, B_yz, B_zx in 6-11 out (vacuum
+//            with absorbing layers; generic kernels only)
+enum Form { kVacuum = 0, kJForm = 1, kRhoForm = 2, kPml = 3 };
 
-constexpr int fields_in(int form) { return form == kVacuum ? 6 : form == kJForm ? 9 : 10; }
-constexpr int fields_out(int form) { return form == kRhoForm ? 7 : 6; }
+constexpr int fields_in(int form) { return form == kVacuum || form == kPml ? 6 : form == kJForm ? 9 : 10; }
+constexpr int fields_out(int form) { return form == kRhoForm ? 7 : form == kPml ? 12 : 6; }
+// spectrum slots a step needs (inputs and outputs share them)
+constexpr int spec_slots(int form) { return fields_in(form) > fields_out(form) ? fields_in(form) : fields_out(form); }
 
 // Radix schedule of one complex FFT length.
 struct AxisPlan {
@@ -141,9 +146,9 @@ struct alignas(16) GatherGrid {
   int32_t pad[3];
 };
 
-// Up to 10 field slots (see Form).
+// Up to 12 field slots (see Form).
 struct FieldPtrs {
-  void* p[10];
+  void* p[12];
 };
 
 template <typename T>
@@ -194,6 +199,22 @@ cudaError_t launch_inv_x(int prec, const DevPlan& P, const FieldPtrs& f, int nf,
                          int64_t sstride, const RowJob* jobs, int64_t njobs, int smem,
                          int interior_only, cudaStream_t st);
 // Guard exchange of `nf` field slots.
+// Absorbing layers, step (2): one box of the layers' list.  Damping table
+// (type T): for axis d and Yee offset o (0: cell, 1: half cell), entry
+// tab[d][o] + g = exp(-s_d(g + o/2) dt) for global index g.
+struct PmlBox {
+  int32_t box;
+  int32_t origin[3];
+};
+struct PmlTab {
+  int64_t off[3][2];
+};
+// f: the 6 components (updated in place) and, in slots 6-11, the increments of
+// the stored split parts; parts: the 6 stored split parts (in place); every
+// interior cell of every listed box.
+cudaError_t launch_pml_damp(int prec, const DevPlan& P, const FieldPtrs& f, const FieldPtrs& parts,
+                            const PmlBox* boxes, int nboxes, const void* tab, const PmlTab& t, cudaStream_t st);
+
 cudaError_t launch_exchange(int prec, const DevPlan& P, const FieldPtrs& f, int nf,
                             const CopyBlk* blocks, const XTile* tiles, int64_t ntiles,
                             cudaStream_t st);

@@ -141,6 +141,28 @@ __device__ __forceinline__ void update_core(C* m, T Kx, T Ky, T Kz, C px, C py, 
       nbz = nbz + rmul(x2, times_i(rmul(Kx, jy) - rmul(Ky, jx)));
     }
   }
+  if constexpr (FORM == kPml) {
+    // increments of the stored split parts over the step (absorbing layers):
+    // the time integrals of the mode solution,
+    //   I[E] = Sw E - X3 K (K.E) + i X1 K x B,
+    //   I[B] = Sw B - X3 K (K.B) - i (X1/c^2) K x E,
+    // give dE_xy = i c^2 K_y I[B_z], dE_yz = i c^2 K_z I[B_x], dE_zx = i c^2 K_x I[B_y],
+    //      dB_xy = -i K_y I[E_z],    dB_yz = -i K_z I[E_x],    dB_zx = -i K_x I[E_y]
+    const C kde = rmul(Kx, ex) + rmul(Ky, ey) + rmul(Kz, ez);
+    const T x1c = q.x1 * bcast<T>(P.icce * P.eps0);
+    const C iex = rmul(q.s, ex) - rmul(q.x3 * Kx, kde) + rmul(q.x1, times_i(kbx));
+    const C iey = rmul(q.s, ey) - rmul(q.x3 * Ky, kde) + rmul(q.x1, times_i(kby));
+    const C iez = rmul(q.s, ez) - rmul(q.x3 * Kz, kde) + rmul(q.x1, times_i(kbz));
+    const C ibx = rmul(q.s, bx) - rmul(q.x3 * Kx, kdb) - rmul(x1c, times_i(kex));
+    const C iby = rmul(q.s, by) - rmul(q.x3 * Ky, kdb) - rmul(x1c, times_i(key));
+    const C ibz = rmul(q.s, bz) - rmul(q.x3 * Kz, kdb) - rmul(x1c, times_i(kez));
+    m[6] = cmul(rmul(cc * Ky, times_i(ibz)), px);
+    m[7] = cmul(rmul(cc * Kz, times_i(ibx)), py);
+    m[8] = cmul(rmul(cc * Kx, times_i(iby)), pz);
+    m[9] = cmul(rmul(-Ky, times_i(iez)), pyz);
+    m[10] = cmul(rmul(-Kz, times_i(iex)), pxz);
+    m[11] = cmul(rmul(-Kx, times_i(iey)), pxy);
+  }
   // back to the staggered sample positions: F^ = exp(+i k.s h) F~
   m[0] = cmul(nex, px);
   m[1] = cmul(ney, py);
@@ -161,7 +183,7 @@ __device__ __forceinline__ void update_mode_z(cx<T>* md, int fs, const ModeXY<T>
   const int mzr = mz <= n2 - mz ? mz : n2 - mz;
   const Coef4<T> q =
       reinterpret_cast<const Coef4<T>*>(P.coef)[m.qbase + (int64_t)mzr * (n1 / 2 + 1) * sh.hx];
-  C v[fields_in(FORM)];
+  C v[spec_slots(FORM)];
 #pragma unroll
   for (int f = 0; f < fields_in(FORM); ++f) v[f] = md[f * fs];
   update_core<T, C, FORM>(v, m.Kx, m.Ky, Kz, m.px, m.py, pz, m.pxy, q, P);

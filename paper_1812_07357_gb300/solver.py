@@ -18,9 +18,11 @@ COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 
 def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no_graph=False,
-              generic=False, pencil=False, plane=False, j_constant=False, nodal=False, eager_exchange=False):
+              generic=False, pencil=False, plane=False, j_constant=False, nodal=False, eager_exchange=False,
+              pml=None):
     """psatd_plan_desc for an ``inputs.Layout``; the returned object keeps the
-    box array alive (attribute ``_boxes``)."""
+    box array alive (attribute ``_boxes``).  pml: absorbing layers,
+    dict(width=(wx, wy, wz), sigma_max=(sx, sy, sz), order=m), or None."""
     nb = len(layout.boxes)
     arr = (A.psatd_box * nb)()
     for i, b in enumerate(layout.boxes):
@@ -55,6 +57,13 @@ def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no
         flags |= A.PSATD_EAGER_EXCHANGE
     d.flags = flags
     d._boxes = arr
+    if pml is not None:
+        pm = A.psatd_pml()
+        pm.width[:] = [int(v) for v in pml["width"]]
+        pm.sigma_max[:] = [float(v) for v in pml["sigma_max"]]
+        pm.order = int(pml["order"])
+        d.pml = ctypes.pointer(pm)
+        d._pml = pm
     return d
 
 
@@ -63,7 +72,7 @@ class Plan:
 
     def __init__(self, layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum",
                  stream=None, no_graph=False, generic=False, pencil=False, plane=False, j_constant=False,
-                 nodal=False, eager_exchange=False):
+                 nodal=False, eager_exchange=False, pml=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -75,7 +84,7 @@ class Plan:
         self.cdtype = torch.complex64 if precision == 32 else torch.complex128
         self.np_dtype = np.float32 if precision == 32 else np.float64
         self.desc = make_desc(layout, h, dt, c, eps0, precision, sources, no_graph, generic, pencil, plane,
-                              j_constant, nodal, eager_exchange)
+                              j_constant, nodal, eager_exchange, pml)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = A.psatd_plan_create(self.desc, self.stream.cuda_stream)
         self.offsets = [A.psatd_plan_layout(self.handle, i) for i in range(len(layout.boxes))]
@@ -183,8 +192,28 @@ class Plan:
     def sync(self):
         A.psatd_sync_status(self.handle)
 
+    # the stored split parts of the absorbing layers (plan-owned device memory)
+    PML_PARTS = ("Exy", "Eyz", "Ezx", "Bxy", "Byz", "Bzx")
+
+    def pml_parts(self):
+        """{name: tensor} views of the plan's stored split parts (same layout
+        as a field buffer; zero-copy through __cuda_array_interface__)."""
+        out = {}
+        for q, name in enumerate(self.PML_PARTS):
+            ptr = A.psatd_plan_pml_part(self.handle, q)
+            out[name] = self.torch.as_tensor(_DeviceArray(ptr, self.field_elems, self.precision), device="cuda")
+        return out
+
     def last_launch_count(self) -> int:
         return A.psatd_last_launch_count(self.handle)
+
+
+class _DeviceArray:
+    """A device buffer owned by the library, exposed to torch without a copy."""
+
+    def __init__(self, ptr, n, precision):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f4" if precision == 32 else "<f8",
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
 
 
 class Coupling:

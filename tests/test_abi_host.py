@@ -228,3 +228,26 @@ def test_coupling_rejects_bad_g1(lib):
     ind = I.independent_layout(seed=3, nboxes=2, sizes=(8, 10), ngs=(1,), min_interior=4)
     with pytest.raises(A.PsatdError):
         A.psatd_coupling_blocks(_desc(ind), ind.boxes, A.PSATD_G1_TO_G2)
+
+
+@pytest.mark.parametrize("case", ["ok", "sources", "nodal", "independent", "wide", "sigma", "order"])
+def test_validate_absorbing_layers(lib, case):
+    lay = I.local_layout((32, 16, 16), (2, 1, 1), 4, 8)
+    pml = dict(width=(4, 2, 0), sigma_max=(1.0, 0.5, 0.0), order=2)
+    kw = {"sources": "vacuum"}
+    if case == "sources":
+        kw["sources"] = "J"
+    elif case == "nodal":
+        kw["nodal"] = True
+    elif case == "independent":
+        lay = I.independent_layout(nboxes=3)
+    elif case == "wide":
+        pml["width"] = (17, 0, 0)
+    elif case == "sigma":
+        pml["sigma_max"] = (-1.0, 0.0, 0.0)
+    elif case == "order":
+        pml["order"] = 17
+    st, msg = A.psatd_plan_validate(_desc(lay, pml=pml, **kw))
+    assert (st == A.PSATD_OK) == (case == "ok"), (case, msg)
+    if case != "ok":
+        assert st == A.PSATD_ERR_INVALID_ARG, msg

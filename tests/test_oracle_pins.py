@@ -748,8 +748,8 @@ def test_fp32_rounding_model():
 
 
 # ---------------------------------------------------------------------------
-# Absorbing layers (two-step split-field PML; the paper, Sec. 3.1 end, only
-# names the method): the oracle's layers against closed forms
+# Absorbing layers (two-step split-field PML; the paper, end of Sec. 2.6,
+# only names the method): the oracle's layers against closed forms
 # ---------------------------------------------------------------------------
 
 def _pulse_along_x(nx, ny, nz, x0=128.0, tau=10.0, lam=16.0):
