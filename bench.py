@@ -68,6 +68,8 @@ def parse(argv=None):
                     help="override the precision of a configuration workload")
     ap.add_argument("--pencil", action="store_true",
                     help="run the boxes the plane kernels would take on the pencil kernels")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose the kernel family and launch knobs by measurement (cached per layout)")
     ap.add_argument("--no-errors", action="store_true",
                     help="skip the error check against the reference (the configuration's full step count)")
     return ap.parse_args(argv)
@@ -278,8 +280,17 @@ def run_config(args):
         fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
         src = {k: I.round_to(v, np.float32) for k, v in src.items()}
     # the source workloads keep J constant in time: its spectrum is computed once per push call
-    plan = Plan(lay, w.h, w.dt, c=w.c, eps0=w.eps0, precision=prec, sources=w.sources, pencil=args.pencil,
-                j_constant=w.sources != "vacuum")
+    tune = None
+    if args.autotune:
+        from paper_1812_07357_gb300 import autotune as AT
+        tune = AT.tune(lay, w.h, w.dt, precision=prec, sources=w.sources, c=w.c, eps0=w.eps0,
+                       j_constant=w.sources != "vacuum")
+        plan = Plan(lay, w.h, w.dt, c=w.c, eps0=w.eps0, precision=prec, sources=w.sources,
+                    j_constant=w.sources != "vacuum", tuning=tune["tuning"] or None,
+                    **AT.family_kwargs(tune["family"]))
+    else:
+        plan = Plan(lay, w.h, w.dt, c=w.c, eps0=w.eps0, precision=prec, sources=w.sources, pencil=args.pencil,
+                    j_constant=w.sources != "vacuum")
     errors = None
     if not args.no_errors:
         df = plan.pack_fields(fields)
@@ -339,7 +350,9 @@ def run_config(args):
            "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": sab,
                              "achieved": sab / (step_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                              "frac": sab / (step_ms / 1e3) / 1e9 / peak, "peak_source": peak_src},
-           "gpu_launches": launches, "kernels": kernels, "errors": errors}
+           "gpu_launches": launches, "kernels": kernels, "errors": errors,
+           "tuning": {"family": tune["family"], "knobs": tune["tuning"], "cached": tune["cached"],
+                      "trials": len(tune["trials"])} if tune else None}
     print(json.dumps(out), flush=True)
 
 
@@ -393,7 +406,14 @@ def run_gpu(args):
     lay = build_layout(args.workload)
     w = WORKLOADS[args.workload]
     h = (1.0, 1.0, 1.0)
-    plan = Plan(lay, h, w["dt"], precision=32, sources="vacuum", pencil=args.pencil)
+    tune = None
+    if args.autotune:
+        from paper_1812_07357_gb300 import autotune as AT
+        tune = AT.tune(lay, h, w["dt"], precision=32, sources="vacuum")
+        plan = Plan(lay, h, w["dt"], precision=32, sources="vacuum", tuning=tune["tuning"] or None,
+                    **AT.family_kwargs(tune["family"]))
+    else:
+        plan = Plan(lay, h, w["dt"], precision=32, sources="vacuum", pencil=args.pencil)
     fac = I.laser_box_factors(lay, h)
     fields = {k: plan.pack_separable(fac[k]) for k in I.COMPONENTS}
     plan.guard_exchange(fields)
@@ -467,6 +487,8 @@ def run_gpu(args):
                     for i in range(len(kms))},
         "kernel_timing": "second push of the same K steps, CUDA events around every launch on the plan's stream",
         "gpu_launches": launches,
+        "tuning": {"family": tune["family"], "knobs": tune["tuning"], "cached": tune["cached"],
+                   "trials": len(tune["trials"])} if tune else None,
         "clocks": clk,
         "memory": dict(zip(("field_bytes", "workspace_bytes"), A.psatd_plan_memory(plan.handle))),
     }

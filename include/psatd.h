@@ -163,6 +163,9 @@ typedef struct {
   const psatd_box* boxes;
   uint32_t flags;
   const psatd_pml* pml;   /* absorbing layers, or NULL (read during create) */
+  const int32_t* tuning;  /* (knob, value) pairs ended by knob 0, at most 16
+                             pairs, or NULL: PSATD_TUNE_* launch parameters
+                             (read during create) */
 } psatd_plan_desc;
 
 typedef struct psatd_plan psatd_plan;
@@ -345,16 +348,27 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
 
 /* ---- Tuning knobs (no counterpart in the paper: launch parameters of this
  * implementation's kernels, chosen per plan by measurement -- see the
- * autotuner of the Python package).  Setting a knob drops the plan's captured
- * CUDA graphs; results do not depend on any knob.
- *   PSATD_TUNE_Z_PREFETCH  register z kernel (the fused z FFT + update pass):
- *                          every CTA first prefetches into L2 the input tile of
- *                          the CTA launched `value` blocks after it (0 = off;
- *                          0 <= value <= 2^20).
- * psatd_plan_tune returns PSATD_ERR_INVALID_ARG for an unknown knob or a
- * value out of range; psatd_plan_tuning returns the knob's value, or -1 for an
- * unknown knob, a NULL plan, or a plan whose kernels do not use the knob. */
+ * autotuner of the Python package).  Results do not depend on any knob.
+ * Every knob can be given at plan creation (psatd_plan_desc.tuning); the
+ * ones marked "runtime" can also be changed later with psatd_plan_tune,
+ * which drops the plan's captured CUDA graphs.
+ *   PSATD_TUNE_Z_PREFETCH    (runtime) register z kernel (the fused z FFT +
+ *                            update pass): every CTA first prefetches into L2
+ *                            the input tile of the CTA launched `value` blocks
+ *                            after it (0 = off; 0 <= value <= 2^20).
+ *   PSATD_TUNE_PENCIL_ROWS_KB  pencil x-pass batching: shared memory (KiB)
+ *                            for the rows one CTA transforms (8 .. 200;
+ *                            default 64).
+ *   PSATD_TUNE_Z_TILE        mx columns per tile of the shared-memory plane
+ *                            family's and the pencil family's z pass (1 ..
+ *                            8 in FP32, 1 .. 4 in FP64; default the maximum).
+ * psatd_plan_create and psatd_plan_validate return PSATD_ERR_INVALID_ARG for
+ * an unknown knob or a value out of range, psatd_plan_tune also for a knob
+ * that is not runtime; psatd_plan_tuning returns the knob's value, or -1 for
+ * an unknown knob, a NULL plan, or a plan whose kernels do not use the knob. */
 #define PSATD_TUNE_Z_PREFETCH 1
+#define PSATD_TUNE_PENCIL_ROWS_KB 2
+#define PSATD_TUNE_Z_TILE 3
 psatd_status psatd_plan_tune(psatd_plan* plan, int32_t knob, int32_t value);
 int32_t psatd_plan_tuning(const psatd_plan* plan, int32_t knob);
 

@@ -51,7 +51,7 @@ class psatd_plan_desc(Structure):
     _fields_ = [("global_n", c_int32 * 3), ("periodic", c_int32 * 3), ("dx", c_double * 3),
                 ("dt", c_double), ("c", c_double), ("eps0", c_double), ("precision", c_int32),
                 ("decomp", c_int32), ("num_boxes", c_int32), ("boxes", POINTER(psatd_box)),
-                ("flags", c_uint32), ("pml", POINTER(psatd_pml))]
+                ("flags", c_uint32), ("pml", POINTER(psatd_pml)), ("tuning", POINTER(c_int32))]
 
 
 class psatd_fields(Structure):
@@ -313,6 +313,10 @@ def psatd_plan_set_timing(plan: int, enable: bool):
 
 
 PSATD_TUNE_Z_PREFETCH = 1
+PSATD_TUNE_PENCIL_ROWS_KB = 2
+PSATD_TUNE_Z_TILE = 3
+TUNE_KNOBS = {"z_prefetch": PSATD_TUNE_Z_PREFETCH, "pencil_rows_kb": PSATD_TUNE_PENCIL_ROWS_KB,
+              "z_tile": PSATD_TUNE_Z_TILE}
 
 
 def psatd_plan_pml_part(plan: int, q: int) -> int:

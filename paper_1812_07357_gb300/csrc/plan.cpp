@@ -88,6 +88,17 @@ Err validate(const psatd_plan_desc* d) {
     if (!(b.order_p == 0 || (b.order_p >= 2 && b.order_p <= 256 && b.order_p % 2 == 0)))
       return {PSATD_ERR_UNSUPPORTED_ORDER, fmt("box %d: order %d is not 0 or even in [2, 256]", i, b.order_p)};
   }
+  if (d->tuning) {
+    int i = 0;
+    for (; i < 16 && d->tuning[2 * i] != 0; ++i) {
+      const int32_t k = d->tuning[2 * i], v = d->tuning[2 * i + 1];
+      const bool ok = (k == PSATD_TUNE_Z_PREFETCH && v >= 0 && v <= (1 << 20)) ||
+                      (k == PSATD_TUNE_PENCIL_ROWS_KB && v >= 8 && v <= 200) ||
+                      (k == PSATD_TUNE_Z_TILE && v >= 1 && v <= fast_tile(d->precision == 64 ? 64 : 32));
+      if (!ok) return {PSATD_ERR_INVALID_ARG, fmt("tuning knob %d: value %d unknown or out of range", k, v)};
+    }
+    if (i == 16 && d->tuning[32] != 0) return {PSATD_ERR_INVALID_ARG, "more than 16 tuning pairs"};
+  }
   if (d->pml) {
     if (!(d->flags & PSATD_VACUUM)) return {PSATD_ERR_INVALID_ARG, "absorbing layers need PSATD_VACUUM"};
     if (d->flags & PSATD_NODAL) return {PSATD_ERR_INVALID_ARG, "absorbing layers need the staggered grid"};
@@ -347,6 +358,8 @@ struct psatd_plan {
   int reg_z = 0;                               // register z kernel length (0: none)
   int reg_zst = 0;                             // n1 * (n0/2 + 1) of every register-z box, else 0
   int z_prefetch = 0;                          // register z kernel: L2 prefetch distance in CTAs
+  int pen_rows_kb = 64;                        // pencil x pass: shared memory for one CTA's rows
+  int z_tile = 0;                              // plane/pencil z tile columns (0: the kernel maximum)
   // absorbing layers (form kPml): the description, boxes with layer cells,
   // damping table, stored split parts and their per-step increments
   psatd_pml pml{};
@@ -716,7 +729,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   int dev = 0, optin = 0;
   CK(P, cudaGetDevice(&dev));
   CK(P, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  const int tile = fast_tile(P->prec);
+  const int tile = P->z_tile > 0 ? std::min(P->z_tile, fast_tile(P->prec)) : fast_tile(P->prec);
   // Kernel family of each box: plane kernels (x+y per z plane) when the
   // register-resident plane kernels serve every plane-eligible box (one FP32
   // shape with register codelets); otherwise the pencil kernels (one launch
@@ -785,10 +798,10 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     } else if (pencil) {
       // pencil kernels: x rows, y tiles, z tiles (+ update), y tiles, x rows
       ++P->pen_boxes;
-      const int pr = pen_rows(P->prec, L, rows, 64 * 1024);
+      const int pr = pen_rows(P->prec, L, rows, P->pen_rows_kb * 1024);
       for (int r = 0; r < rows; r += pr) P->pen_rows.push_back({bi, r, std::min(pr, rows - r), 0});
       const int y0 = b.ng_lo[1], y1 = n1 - b.ng_hi[1];
-      const int pri = pen_rows(P->prec, L, y1 - y0, 64 * 1024);
+      const int pri = pen_rows(P->prec, L, y1 - y0, P->pen_rows_kb * 1024);
       for (int z = b.ng_lo[2]; z < n2 - b.ng_hi[2]; ++z)
         for (int y = y0; y < y1; y += pri) P->pen_rows_int.push_back({bi, z * n1 + y, std::min(pri, y1 - y), 0});
       const int ct = pen_col_tile(P->prec);
@@ -1400,6 +1413,13 @@ psatd_status psatd_plan_create(const psatd_plan_desc* desc, void* stream, psatd_
       P->desc.pml = &P->pml;
       P->form = kPml;
     }
+    P->desc.tuning = nullptr;   // read here only
+    for (int i = 0; desc->tuning && i < 16 && desc->tuning[2 * i] != 0; ++i) {
+      const int32_t k = desc->tuning[2 * i], v = desc->tuning[2 * i + 1];
+      if (k == PSATD_TUNE_Z_PREFETCH) P->z_prefetch = v;
+      if (k == PSATD_TUNE_PENCIL_ROWS_KB) P->pen_rows_kb = v;
+      if (k == PSATD_TUNE_Z_TILE) P->z_tile = v;
+    }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce != cudaSuccess) {
@@ -1855,6 +1875,9 @@ psatd_status psatd_plan_tune(psatd_plan* P, int32_t knob, int32_t value) {
       if (value < 0 || value > (1 << 20)) return fail(P, PSATD_ERR_INVALID_ARG, "prefetch distance out of range");
       P->z_prefetch = value;
       break;
+    case PSATD_TUNE_PENCIL_ROWS_KB:
+    case PSATD_TUNE_Z_TILE:
+      return fail(P, PSATD_ERR_INVALID_ARG, "this knob is set at plan creation only");
     default:
       return fail(P, PSATD_ERR_INVALID_ARG, "unknown tuning knob");
   }
@@ -1872,6 +1895,12 @@ int32_t psatd_plan_tuning(const psatd_plan* P, int32_t knob) {
   switch (knob) {
     case PSATD_TUNE_Z_PREFETCH:
       return P->reg_z ? P->z_prefetch : -1;
+    case PSATD_TUNE_PENCIL_ROWS_KB:
+      return P->pen_boxes ? P->pen_rows_kb : -1;
+    case PSATD_TUNE_Z_TILE:
+      return (P->pen_boxes || (P->fast_boxes && !P->reg_z))
+                 ? (P->z_tile > 0 ? std::min(P->z_tile, fast_tile(P->prec)) : fast_tile(P->prec))
+                 : -1;
     default:
       return -1;
   }

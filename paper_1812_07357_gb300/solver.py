@@ -19,10 +19,11 @@ COMPONENTS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
 
 def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no_graph=False,
               generic=False, pencil=False, plane=False, j_constant=False, nodal=False, eager_exchange=False,
-              pml=None):
+              pml=None, tuning=None):
     """psatd_plan_desc for an ``inputs.Layout``; the returned object keeps the
     box array alive (attribute ``_boxes``).  pml: absorbing layers,
-    dict(width=(wx, wy, wz), sigma_max=(sx, sy, sz), order=m), or None."""
+    dict(width=(wx, wy, wz), sigma_max=(sx, sy, sz), order=m), or None.
+    tuning: {knob name (see _abi.TUNE_KNOBS): value} launch parameters."""
     nb = len(layout.boxes)
     arr = (A.psatd_box * nb)()
     for i, b in enumerate(layout.boxes):
@@ -64,6 +65,11 @@ def make_desc(layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum", no
         pm.order = int(pml["order"])
         d.pml = ctypes.pointer(pm)
         d._pml = pm
+    if tuning:
+        pairs = [v for k, x in sorted(tuning.items()) for v in (A.TUNE_KNOBS[k], int(x))] + [0, 0]
+        arr_t = (ctypes.c_int32 * len(pairs))(*pairs)
+        d.tuning = ctypes.cast(arr_t, ctypes.POINTER(ctypes.c_int32))
+        d._tuning = arr_t
     return d
 
 
@@ -72,7 +78,7 @@ class Plan:
 
     def __init__(self, layout, h, dt, c=1.0, eps0=1.0, precision=32, sources="vacuum",
                  stream=None, no_graph=False, generic=False, pencil=False, plane=False, j_constant=False,
-                 nodal=False, eager_exchange=False, pml=None):
+                 nodal=False, eager_exchange=False, pml=None, tuning=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -84,7 +90,7 @@ class Plan:
         self.cdtype = torch.complex64 if precision == 32 else torch.complex128
         self.np_dtype = np.float32 if precision == 32 else np.float64
         self.desc = make_desc(layout, h, dt, c, eps0, precision, sources, no_graph, generic, pencil, plane,
-                              j_constant, nodal, eager_exchange, pml)
+                              j_constant, nodal, eager_exchange, pml, tuning)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.handle = A.psatd_plan_create(self.desc, self.stream.cuda_stream)
         self.offsets = [A.psatd_plan_layout(self.handle, i) for i in range(len(layout.boxes))]
@@ -206,6 +212,15 @@ class Plan:
 
     def last_launch_count(self) -> int:
         return A.psatd_last_launch_count(self.handle)
+
+    def tuning(self):
+        """{knob name: value} of the knobs this plan's kernels use."""
+        out = {}
+        for name, k in A.TUNE_KNOBS.items():
+            v = A.psatd_plan_tuning(self.handle, k)
+            if v >= 0:
+                out[name] = v
+        return out
 
 
 class _DeviceArray:
