@@ -251,6 +251,21 @@ psatd_status psatd_guard_exchange(psatd_plan* plan, const psatd_fields* fields,
 psatd_status psatd_push(psatd_plan* plan, const psatd_fields* fields,
                         const psatd_sources* src, int32_t nsteps, void* stream);
 
+/* psatd_push for fields in HOST memory (no counterpart in the paper: the
+ * host path of a caller whose fields live on the CPU).  in / out: six host
+ * component buffers each (same layout as the device buffers, field_bytes
+ * each; they may be the same buffers; page-locked memory copies fastest).
+ * The fields are copied to plan-owned device staging buffers (allocated by
+ * the first call, 6 x field_bytes, kept until psatd_plan_destroy; that first
+ * call therefore allocates and should come before any stream capture), one
+ * copy stream per component; then `nsteps` steps run as in psatd_push
+ * (`src`: device sources as there), and the results are copied back the same
+ * way.  Asynchronous on `stream`: the host buffers must stay valid, and `in`
+ * unchanged, until `stream` has passed this call; work queued on `stream`
+ * afterwards sees the results in `out`.  Errors as psatd_push. */
+psatd_status psatd_push_host(psatd_plan* plan, const psatd_fields* in, const psatd_fields* out,
+                             const psatd_sources* src, int32_t nsteps, void* stream);
+
 /* S1 alone for one component: unnormalised 3D R2C FFT of every box of
  * `field` (device, one component buffer) into `spectrum` (device, complex
  * float2/double2, box b at psatd_plan_spectrum_layout offset, element

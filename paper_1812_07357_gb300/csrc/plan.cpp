@@ -401,6 +401,10 @@ struct psatd_plan {
   // per step variant: 2 * (forward gathers) + (inverse writes the guards)
   cudaGraphExec_t graph_exec[4] = {};
   cudaStream_t cap_stream = nullptr;   // capture only; never executes work
+  // host-buffer push: device staging fields and one copy stream per component
+  void* host_stage[6] = {};
+  cudaStream_t copy_streams[6] = {};
+  cudaEvent_t copy_events[7] = {};
   FieldPtrs graph_fp{};
   int graph_nf = 0;
   int64_t graph_launches[4] = {};
@@ -430,6 +434,10 @@ struct psatd_plan {
     for (cudaGraphExec_t g : graph_exec)
       if (g) cudaGraphExecDestroy(g);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    for (cudaStream_t c : copy_streams)
+      if (c) cudaStreamDestroy(c);
+    for (cudaEvent_t e : copy_events)
+      if (e) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     for (auto& r : recs) {
       ev_pool.push_back(r.a);
@@ -1787,6 +1795,58 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
       }
     }
     P->last_launches = launches;
+    return PSATD_OK;
+  } catch (...) {
+    return fail(P, PSATD_ERR_INVALID_ARG, "internal error");
+  }
+}
+
+psatd_status psatd_push_host(psatd_plan* P, const psatd_fields* in, const psatd_fields* out,
+                             const psatd_sources* s, int32_t nsteps, void* stream) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  if (!in || !out) return fail(P, PSATD_ERR_INVALID_ARG, "host field sets must not be NULL");
+  for (int a = 0; a < 3; ++a)
+    if (!in->E[a] || !in->B[a] || !out->E[a] || !out->B[a])
+      return fail(P, PSATD_ERR_INVALID_ARG, "a host field pointer is NULL");
+  if (nsteps < 0) return fail(P, PSATD_ERR_INVALID_ARG, "nsteps < 0");
+  try {
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)P->field_total * P->rsize;
+    if (!P->host_stage[0]) {
+      for (int c = 0; c < 6; ++c) {
+        CK(P, dalloc(P, bytes, &P->host_stage[c]));
+        CK(P, cudaStreamCreateWithFlags(&P->copy_streams[c], cudaStreamNonBlocking));
+      }
+      for (cudaEvent_t& e : P->copy_events) CK(P, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    const void* src[6] = {in->E[0], in->E[1], in->E[2], in->B[0], in->B[1], in->B[2]};
+    void* dst[6] = {out->E[0], out->E[1], out->E[2], out->B[0], out->B[1], out->B[2]};
+    // host -> device: every component on its own copy stream, after the
+    // caller's earlier work on `stream`
+    CK(P, cudaEventRecord(P->copy_events[6], st));
+    for (int c = 0; c < 6; ++c) {
+      CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
+      CK(P, cudaMemcpyAsync(P->host_stage[c], src[c], bytes, cudaMemcpyHostToDevice, P->copy_streams[c]));
+      CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
+      CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
+    }
+    psatd_fields dev{};
+    for (int a = 0; a < 3; ++a) {
+      dev.E[a] = P->host_stage[a];
+      dev.B[a] = P->host_stage[3 + a];
+    }
+    const psatd_status r = psatd_push(P, &dev, s, nsteps, stream);
+    if (r != PSATD_OK) return r;
+    // device -> host, again one copy stream per component; `stream` waits
+    // for all of them, so work queued after this call sees the results
+    CK(P, cudaEventRecord(P->copy_events[6], st));
+    for (int c = 0; c < 6; ++c) {
+      CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
+      CK(P, cudaMemcpyAsync(dst[c], P->host_stage[c], bytes, cudaMemcpyDeviceToHost, P->copy_streams[c]));
+      CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
+      CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
+    }
+    P->last_stream = st;
     return PSATD_OK;
   } catch (...) {
     return fail(P, PSATD_ERR_INVALID_ARG, "internal error");

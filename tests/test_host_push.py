@@ -1,0 +1,52 @@
+"""psatd_push_host: fields in host memory, copied to the plan's device
+staging buffers and back inside the call.  The result must equal the
+device-buffer push bit for bit (same kernels, same data) and match the
+oracle; separate in/out host buffers leave the input untouched."""
+import numpy as np
+import pytest
+
+from oracle import psatd_oracle as O
+from paper_1812_07357_gb300 import inputs as I
+from _parity import assert_fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_07357_gb300 import build
+    build.build()
+    return t
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_host_push_equals_device_push_and_oracle(torch, prec):
+    from paper_1812_07357_gb300.solver import Plan
+    lay = I.local_layout((128, 64, 32), (2, 1, 2), (16, 16, 4), 16)     # register kernels in FP32
+    f = I.laser_fields((128, 64, 32), wavelength=8.0, waist=10.0, duration=6.0)
+    fields = {k: I.scatter_global(v, lay) for k, v in f.items()}
+    if prec == 32:
+        fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
+    plan = Plan(lay, (1.0,) * 3, 0.9, precision=prec, sources="vacuum")
+    dev = plan.pack_fields(fields)
+    host_in = {k: v.cpu().pin_memory() for k, v in dev.items()}
+    keep = {k: v.clone() for k, v in host_in.items()}
+    host_out = {k: torch.empty_like(v).pin_memory() for k, v in host_in.items()}
+    plan.push(dev, None, 3)
+    plan.push_host(host_in, host_out, None, 3)
+    plan.sync()
+    torch.cuda.synchronize()
+    for k in O.COMPS:
+        assert torch.equal(host_out[k], dev[k].cpu()), k
+        assert torch.equal(host_in[k], keep[k]), k
+    # in place, twice more
+    plan.push_host(host_out, None, None, 2)
+    plan.push(dev, None, 2)
+    torch.cuda.synchronize()
+    got = {k: plan.unpack(host_out[k].cuda()) for k in O.COMPS}
+    plan.close()
+    ref = O.push(lay, fields, {}, 5, (1.0,) * 3, 0.9)
+    assert_fields(lay, got, ref, O.COMPS, prec)
