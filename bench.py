@@ -581,24 +581,36 @@ def run_e2e(plan, fields, args, lay, world):
     host = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in fields.items()}
     for k in host:
         host[k].copy_(fields[k])
+    from paper_1812_07357_gb300 import _abi as A
     stream = plan.stream
     plan.push_host(host, host, None, 1)          # first call allocates the staging buffers
     torch.cuda.synchronize()
     nb = sum(v.numel() * v.element_size() for v in host.values())
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
-            plan.push_host(host, host, None, 1)
-        e1.record(stream)
-    torch.cuda.synchronize()
-    ms = reduce_max(e0.elapsed_time(e1), torch.device("cuda", torch.cuda.current_device())
-                    if world > 1 else None)
+
+    def timed_steps():
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(args.e2e_steps):
+                plan.push_host(host, host, None, 1)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return reduce_max(e0.elapsed_time(e1), torch.device("cuda", torch.cuda.current_device())
+                          if world > 1 else None)
+
+    mode = A.psatd_plan_tuning(plan.handle, A.PSATD_TUNE_HOST_COPY)
+    ms = timed_steps()                           # the plan's default copy mode
+    A.psatd_plan_tune(plan.handle, A.PSATD_TUNE_HOST_COPY, 1 - mode)
+    ms_other = timed_steps()
+    A.psatd_plan_tune(plan.handle, A.PSATD_TUNE_HOST_COPY, mode)
     v = total_units(lay.interior_cells * args.e2e_steps, world) / (ms / 1e3)
+    names = {1: "copy kernel through the host buffers' device mapping", 0: "copy engines, one stream per component"}
     return {"value": v, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb,
             "steps": args.e2e_steps, "ms_per_step": ms / args.e2e_steps,
-            "api": "psatd_push_host (one copy stream per component)"}
+            "api": "psatd_push_host, " + names[mode],
+            "other_copy_mode": {"copies": names[1 - mode], "ms_per_step": ms_other / args.e2e_steps,
+                                "value": total_units(lay.interior_cells * args.e2e_steps, world) / (ms_other / 1e3)}}
 
 
 def run_fp64_plain(lay, w, fac, nsteps=2):

@@ -258,7 +258,8 @@ psatd_status psatd_push(psatd_plan* plan, const psatd_fields* fields,
  * The fields are copied to plan-owned device staging buffers (allocated by
  * the first call, 6 x field_bytes, kept until psatd_plan_destroy; that first
  * call therefore allocates and should come before any stream capture), one
- * copy stream per component; then `nsteps` steps run as in psatd_push
+ * copy stream per component, or by a copy kernel through the buffers'
+ * device mapping (PSATD_TUNE_HOST_COPY); then `nsteps` steps run as in psatd_push
  * (`src`: device sources as there), and the results are copied back the same
  * way.  Asynchronous on `stream`: the host buffers must stay valid, and `in`
  * unchanged, until `stream` has passed this call; work queued on `stream`
@@ -377,6 +378,12 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
  *   PSATD_TUNE_Z_TILE        mx columns per tile of the shared-memory plane
  *                            family's and the pencil family's z pass (1 ..
  *                            8 in FP32, 1 .. 4 in FP64; default the maximum).
+ *   PSATD_TUNE_HOST_COPY     (runtime) psatd_push_host's copies: 1 (default)
+ *                            = a copy kernel on the SMs reading and writing
+ *                            the host buffers through their device mapping
+ *                            when every buffer is page-locked, mapped and
+ *                            16-byte aligned (else the copy engines); 0 = the
+ *                            copy engines, one stream per component.
  * psatd_plan_create and psatd_plan_validate return PSATD_ERR_INVALID_ARG for
  * an unknown knob or a value out of range, psatd_plan_tune also for a knob
  * that is not runtime; psatd_plan_tuning returns the knob's value, or -1 for
@@ -384,6 +391,7 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
 #define PSATD_TUNE_Z_PREFETCH 1
 #define PSATD_TUNE_PENCIL_ROWS_KB 2
 #define PSATD_TUNE_Z_TILE 3
+#define PSATD_TUNE_HOST_COPY 4
 psatd_status psatd_plan_tune(psatd_plan* plan, int32_t knob, int32_t value);
 int32_t psatd_plan_tuning(const psatd_plan* plan, int32_t knob);
 

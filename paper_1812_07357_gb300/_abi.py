@@ -317,8 +317,9 @@ def psatd_plan_set_timing(plan: int, enable: bool):
 PSATD_TUNE_Z_PREFETCH = 1
 PSATD_TUNE_PENCIL_ROWS_KB = 2
 PSATD_TUNE_Z_TILE = 3
+PSATD_TUNE_HOST_COPY = 4
 TUNE_KNOBS = {"z_prefetch": PSATD_TUNE_Z_PREFETCH, "pencil_rows_kb": PSATD_TUNE_PENCIL_ROWS_KB,
-              "z_tile": PSATD_TUNE_Z_TILE}
+              "z_tile": PSATD_TUNE_Z_TILE, "host_copy": PSATD_TUNE_HOST_COPY}
 
 
 def psatd_push_host(plan: int, fin: psatd_fields, fout: psatd_fields, sources, nsteps: int, stream: int = 0):

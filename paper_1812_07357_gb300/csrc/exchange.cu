@@ -131,7 +131,35 @@ __global__ void __launch_bounds__(256) k_pml_damp(DevPlan P, FieldPtrs F, FieldP
   }
 }
 
+// Copy of whole field buffers in 16-byte units, slot blockIdx.y: the host
+// path's copies between page-locked host memory (device-mapped) and the
+// device staging buffers, driven by the SMs instead of the copy engines.
+__global__ void __launch_bounds__(256) k_copy_fields(FieldPtrs dst, FieldPtrs src, int64_t n16) {
+  const float4* s = reinterpret_cast<const float4*>(src.p[blockIdx.y]);
+  float4* d = reinterpret_cast<float4*>(dst.p[blockIdx.y]);
+  constexpr int kU = 4;   // units in flight per thread
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += kU * stride) {
+    float4 v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i + u * stride < n16) v[u] = s[i + u * stride];
+#pragma unroll
+    for (int u = 0; u < kU; ++u)
+      if (i + u * stride < n16) d[i + u * stride] = v[u];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_copy_fields(const FieldPtrs& dst, const FieldPtrs& src, int nf, int64_t bytes, int blocks,
+                               cudaStream_t st) {
+  if (nf <= 0 || bytes <= 0) return cudaSuccess;
+  if (bytes % 16) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)std::max(1, blocks), (unsigned)nf);
+  k_copy_fields<<<grid, 256, 0, st>>>(dst, src, bytes / 16);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_pml_damp(int prec, const DevPlan& P, const FieldPtrs& f, const FieldPtrs& parts,
                             const PmlBox* boxes, int nboxes, const void* tab, const PmlTab& t, cudaStream_t st) {

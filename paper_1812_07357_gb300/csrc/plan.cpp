@@ -94,7 +94,8 @@ Err validate(const psatd_plan_desc* d) {
       const int32_t k = d->tuning[2 * i], v = d->tuning[2 * i + 1];
       const bool ok = (k == PSATD_TUNE_Z_PREFETCH && v >= 0 && v <= (1 << 20)) ||
                       (k == PSATD_TUNE_PENCIL_ROWS_KB && v >= 8 && v <= 200) ||
-                      (k == PSATD_TUNE_Z_TILE && v >= 1 && v <= fast_tile(d->precision == 64 ? 64 : 32));
+                      (k == PSATD_TUNE_Z_TILE && v >= 1 && v <= fast_tile(d->precision == 64 ? 64 : 32)) ||
+                      (k == PSATD_TUNE_HOST_COPY && (v == 0 || v == 1));
       if (!ok) return {PSATD_ERR_INVALID_ARG, fmt("tuning knob %d: value %d unknown or out of range", k, v)};
     }
     if (i == 16 && d->tuning[32] != 0) return {PSATD_ERR_INVALID_ARG, "more than 16 tuning pairs"};
@@ -359,6 +360,7 @@ struct psatd_plan {
   int reg_zst = 0;                             // n1 * (n0/2 + 1) of every register-z box, else 0
   int z_prefetch = 0;                          // register z kernel: L2 prefetch distance in CTAs
   int pen_rows_kb = 64;                        // pencil x pass: shared memory for one CTA's rows
+  int host_copy = 1;                           // host path: 1 = SM copy kernel on mapped memory, 0 = copy engines
   int z_tile = 0;                              // plane/pencil z tile columns (0: the kernel maximum)
   // absorbing layers (form kPml): the description, boxes with layer cells,
   // damping table, stored split parts and their per-step increments
@@ -1427,6 +1429,7 @@ psatd_status psatd_plan_create(const psatd_plan_desc* desc, void* stream, psatd_
       if (k == PSATD_TUNE_Z_PREFETCH) P->z_prefetch = v;
       if (k == PSATD_TUNE_PENCIL_ROWS_KB) P->pen_rows_kb = v;
       if (k == PSATD_TUNE_Z_TILE) P->z_tile = v;
+      if (k == PSATD_TUNE_HOST_COPY) P->host_copy = v;
     }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -1821,14 +1824,38 @@ psatd_status psatd_push_host(psatd_plan* P, const psatd_fields* in, const psatd_
     }
     const void* src[6] = {in->E[0], in->E[1], in->E[2], in->B[0], in->B[1], in->B[2]};
     void* dst[6] = {out->E[0], out->E[1], out->E[2], out->B[0], out->B[1], out->B[2]};
-    // host -> device: every component on its own copy stream, after the
-    // caller's earlier work on `stream`
-    CK(P, cudaEventRecord(P->copy_events[6], st));
-    for (int c = 0; c < 6; ++c) {
-      CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
-      CK(P, cudaMemcpyAsync(P->host_stage[c], src[c], bytes, cudaMemcpyHostToDevice, P->copy_streams[c]));
-      CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
-      CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
+    // SM-driven copies need every host buffer page-locked and mapped into the
+    // device's address space (cudaHostGetDevicePointer gives the address the
+    // kernel may use) and 16-byte aligned; otherwise the copy engines move it
+    FieldPtrs hin{}, hout{}, stage{};
+    bool mapped = P->host_copy == 1;
+    for (int c = 0; c < 6 && mapped; ++c) {
+      void *a = nullptr, *b = nullptr;
+      if (cudaHostGetDevicePointer(&a, const_cast<void*>(src[c]), 0) != cudaSuccess ||
+          cudaHostGetDevicePointer(&b, dst[c], 0) != cudaSuccess || !aligned16(a) || !aligned16(b)) {
+        cudaGetLastError();
+        mapped = false;
+        break;
+      }
+      hin.p[c] = a;
+      hout.p[c] = b;
+      stage.p[c] = P->host_stage[c];
+    }
+    int sms = 0, gpu = 0;
+    CK(P, cudaGetDevice(&gpu));
+    CK(P, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gpu));
+    if (mapped) {
+      CK(P, launch_copy_fields(stage, hin, 6, (int64_t)bytes, 2 * sms, st));
+    } else {
+      // host -> device: every component on its own copy stream, after the
+      // caller's earlier work on `stream`
+      CK(P, cudaEventRecord(P->copy_events[6], st));
+      for (int c = 0; c < 6; ++c) {
+        CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
+        CK(P, cudaMemcpyAsync(P->host_stage[c], src[c], bytes, cudaMemcpyHostToDevice, P->copy_streams[c]));
+        CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
+        CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
+      }
     }
     psatd_fields dev{};
     for (int a = 0; a < 3; ++a) {
@@ -1837,14 +1864,18 @@ psatd_status psatd_push_host(psatd_plan* P, const psatd_fields* in, const psatd_
     }
     const psatd_status r = psatd_push(P, &dev, s, nsteps, stream);
     if (r != PSATD_OK) return r;
-    // device -> host, again one copy stream per component; `stream` waits
-    // for all of them, so work queued after this call sees the results
-    CK(P, cudaEventRecord(P->copy_events[6], st));
-    for (int c = 0; c < 6; ++c) {
-      CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
-      CK(P, cudaMemcpyAsync(dst[c], P->host_stage[c], bytes, cudaMemcpyDeviceToHost, P->copy_streams[c]));
-      CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
-      CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
+    if (mapped) {
+      CK(P, launch_copy_fields(hout, stage, 6, (int64_t)bytes, 2 * sms, st));
+    } else {
+      // device -> host, again one copy stream per component; `stream` waits
+      // for all of them, so work queued after this call sees the results
+      CK(P, cudaEventRecord(P->copy_events[6], st));
+      for (int c = 0; c < 6; ++c) {
+        CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
+        CK(P, cudaMemcpyAsync(dst[c], P->host_stage[c], bytes, cudaMemcpyDeviceToHost, P->copy_streams[c]));
+        CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
+        CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
+      }
     }
     P->last_stream = st;
     return PSATD_OK;
@@ -1935,6 +1966,10 @@ psatd_status psatd_plan_tune(psatd_plan* P, int32_t knob, int32_t value) {
       if (value < 0 || value > (1 << 20)) return fail(P, PSATD_ERR_INVALID_ARG, "prefetch distance out of range");
       P->z_prefetch = value;
       break;
+    case PSATD_TUNE_HOST_COPY:
+      if (value != 0 && value != 1) return fail(P, PSATD_ERR_INVALID_ARG, "host copy mode is 0 or 1");
+      P->host_copy = value;
+      return PSATD_OK;   // not part of any captured graph
     case PSATD_TUNE_PENCIL_ROWS_KB:
     case PSATD_TUNE_Z_TILE:
       return fail(P, PSATD_ERR_INVALID_ARG, "this knob is set at plan creation only");
@@ -1957,6 +1992,8 @@ int32_t psatd_plan_tuning(const psatd_plan* P, int32_t knob) {
       return P->reg_z ? P->z_prefetch : -1;
     case PSATD_TUNE_PENCIL_ROWS_KB:
       return P->pen_boxes ? P->pen_rows_kb : -1;
+    case PSATD_TUNE_HOST_COPY:
+      return P->host_copy;
     case PSATD_TUNE_Z_TILE:
       return (P->pen_boxes || (P->fast_boxes && !P->reg_z))
                  ? (P->z_tile > 0 ? std::min(P->z_tile, fast_tile(P->prec)) : fast_tile(P->prec))

@@ -215,6 +215,11 @@ struct PmlTab {
 cudaError_t launch_pml_damp(int prec, const DevPlan& P, const FieldPtrs& f, const FieldPtrs& parts,
                             const PmlBox* boxes, int nboxes, const void* tab, const PmlTab& t, cudaStream_t st);
 
+// Copy nf whole buffers of `bytes` (a multiple of 16) from src.p[i] to
+// dst.p[i] with `blocks` x nf CTAs (16-byte aligned pointers).
+cudaError_t launch_copy_fields(const FieldPtrs& dst, const FieldPtrs& src, int nf, int64_t bytes, int blocks,
+                               cudaStream_t st);
+
 cudaError_t launch_exchange(int prec, const DevPlan& P, const FieldPtrs& f, int nf,
                             const CopyBlk* blocks, const XTile* tiles, int64_t ntiles,
                             cudaStream_t st);

@@ -1,5 +1,6 @@
 """psatd_push_host: fields in host memory, copied to the plan's device
-staging buffers and back inside the call.  The result must equal the
+staging buffers and back inside the call (by the SM copy kernel through the
+buffers' device mapping, or by the copy engines).  The result must equal the
 device-buffer push bit for bit (same kernels, same data) and match the
 oracle; separate in/out host buffers leave the input untouched."""
 import numpy as np
@@ -22,8 +23,9 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("prec", [32, 64])
-def test_host_push_equals_device_push_and_oracle(torch, prec):
+@pytest.mark.parametrize("prec,copy", [(32, 1), (64, 1), (32, 0)])
+def test_host_push_equals_device_push_and_oracle(torch, prec, copy):
+    from paper_1812_07357_gb300 import _abi as A
     from paper_1812_07357_gb300.solver import Plan
     lay = I.local_layout((128, 64, 32), (2, 1, 2), (16, 16, 4), 16)     # register kernels in FP32
     f = I.laser_fields((128, 64, 32), wavelength=8.0, waist=10.0, duration=6.0)
@@ -31,6 +33,8 @@ def test_host_push_equals_device_push_and_oracle(torch, prec):
     if prec == 32:
         fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
     plan = Plan(lay, (1.0,) * 3, 0.9, precision=prec, sources="vacuum")
+    A.psatd_plan_tune(plan.handle, A.PSATD_TUNE_HOST_COPY, copy)
+    assert plan.tuning()["host_copy"] == copy
     dev = plan.pack_fields(fields)
     host_in = {k: v.cpu().pin_memory() for k, v in dev.items()}
     keep = {k: v.clone() for k, v in host_in.items()}
@@ -44,7 +48,6 @@ def test_host_push_equals_device_push_and_oracle(torch, prec):
         assert torch.equal(host_in[k], keep[k]), k
     # in place, twice more
     plan.push_host(host_out, None, None, 2)
-    plan.push(dev, None, 2)
     torch.cuda.synchronize()
     got = {k: plan.unpack(host_out[k].cuda()) for k in O.COMPS}
     plan.close()
