@@ -267,6 +267,22 @@ psatd_status psatd_push(psatd_plan* plan, const psatd_fields* fields,
 psatd_status psatd_push_host(psatd_plan* plan, const psatd_fields* in, const psatd_fields* out,
                              const psatd_sources* src, int32_t nsteps, void* stream);
 
+/* psatd_push for fields held on the host as whole-domain arrays (no
+ * counterpart in the paper: the host path of a caller who stores the global
+ * fields, not the padded boxes).  in / out: six host arrays each of
+ * global_n[0] * global_n[1] * global_n[2] elements (x fastest, then y, z;
+ * the plan's precision; in and out may be the same).  The domain is copied
+ * to the device (as in psatd_push_host), scattered into the plan's padded
+ * boxes, guards included (the dual-grid coupling of the plan with one box
+ * covering the domain), pushed `nsteps` steps, and the box interiors are
+ * gathered back and copied to `out`.  The first call allocates plan-owned
+ * device buffers (6 x the domain and 6 x field_bytes) and the coupling, kept
+ * until psatd_plan_destroy; make it before any stream capture.  Not for
+ * PSATD_DECOMP_INDEPENDENT (PSATD_ERR_STATE).  Asynchronous on `stream`, with
+ * the same rules for the host buffers as psatd_push_host. */
+psatd_status psatd_push_host_global(psatd_plan* plan, const psatd_fields* in, const psatd_fields* out,
+                                    const psatd_sources* src, int32_t nsteps, void* stream);
+
 /* S1 alone for one component: unnormalised 3D R2C FFT of every box of
  * `field` (device, one component buffer) into `spectrum` (device, complex
  * float2/double2, box b at psatd_plan_spectrum_layout offset, element

@@ -97,6 +97,8 @@ _SIGS = {
     "psatd_plan_tune": (c_int32, [c_void_p, c_int32, c_int32]),
     "psatd_push_host": (c_int32, [c_void_p, POINTER(psatd_fields), POINTER(psatd_fields), POINTER(psatd_sources),
                                   c_int32, c_void_p]),
+    "psatd_push_host_global": (c_int32, [c_void_p, POINTER(psatd_fields), POINTER(psatd_fields),
+                                         POINTER(psatd_sources), c_int32, c_void_p]),
     "psatd_plan_pml_part": (c_int32, [c_void_p, c_int32, POINTER(c_void_p)]),
     "psatd_plan_tuning": (c_int32, [c_void_p, c_int32]),
     "psatd_plan_kernel_times": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_int64), c_int32]),
@@ -326,6 +328,13 @@ def psatd_push_host(plan: int, fin: psatd_fields, fout: psatd_fields, sources, n
     _check(load().psatd_push_host(c_void_p(plan), ctypes.byref(fin), ctypes.byref(fout),
                                   ctypes.byref(sources) if sources is not None else None, int(nsteps),
                                   c_void_p(stream)), plan)
+
+
+def psatd_push_host_global(plan: int, fin: psatd_fields, fout: psatd_fields, sources, nsteps: int,
+                           stream: int = 0):
+    _check(load().psatd_push_host_global(c_void_p(plan), ctypes.byref(fin), ctypes.byref(fout),
+                                         ctypes.byref(sources) if sources is not None else None, int(nsteps),
+                                         c_void_p(stream)), plan)
 
 
 def psatd_plan_pml_part(plan: int, q: int) -> int:

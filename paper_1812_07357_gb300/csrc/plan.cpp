@@ -313,6 +313,9 @@ void set_thread_error(const char* msg) { g_thread_error = msg; }
 // ---------------------------------------------------------------------------
 // the plan
 // ---------------------------------------------------------------------------
+struct psatd_coupling;
+static void destroy_global_coupling(psatd_coupling* c);
+
 struct psatd_plan {
   psatd_plan_desc desc{};
   std::vector<psatd_box> boxes;
@@ -403,7 +406,11 @@ struct psatd_plan {
   // per step variant: 2 * (forward gathers) + (inverse writes the guards)
   cudaGraphExec_t graph_exec[4] = {};
   cudaStream_t cap_stream = nullptr;   // capture only; never executes work
-  // host-buffer push: device staging fields and one copy stream per component
+  // host-buffer push: device staging fields and one copy stream per component;
+  // the global-array variant also keeps the whole domain on the device and a
+  // coupling of the plan's boxes with one box covering the domain
+  void* global_stage[6] = {};
+  psatd_coupling* global_coupling = nullptr;
   void* host_stage[6] = {};
   cudaStream_t copy_streams[6] = {};
   cudaEvent_t copy_events[7] = {};
@@ -436,6 +443,7 @@ struct psatd_plan {
     for (cudaGraphExec_t g : graph_exec)
       if (g) cudaGraphExecDestroy(g);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    destroy_global_coupling(global_coupling);
     for (cudaStream_t c : copy_streams)
       if (c) cudaStreamDestroy(c);
     for (cudaEvent_t e : copy_events)
@@ -1317,6 +1325,8 @@ struct psatd_coupling {
   }
 };
 
+static void destroy_global_coupling(psatd_coupling* c) { delete c; }
+
 extern "C" {
 
 psatd_status psatd_plan_validate(const psatd_plan_desc* desc, char* msg, size_t msg_len) {
@@ -1804,6 +1814,48 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
   }
 }
 
+// Copy six buffers of `bytes` between host (`host`) and device (`devb`)
+// memory, to the device when `to_dev`: a copy kernel through the host
+// buffers' device mapping when the plan's mode allows it and every host
+// buffer is page-locked, mapped and 16-byte aligned (and bytes % 16 == 0),
+// else one copy-engine stream per component.  Ordered after earlier work on
+// `st`; later work on `st` sees the copies.
+static psatd_status host_copies(psatd_plan* P, void* const host[6], void* const devb[6], size_t bytes, bool to_dev,
+                                cudaStream_t st) {
+  if (!P->copy_streams[0]) {
+    for (int c = 0; c < 6; ++c) CK(P, cudaStreamCreateWithFlags(&P->copy_streams[c], cudaStreamNonBlocking));
+    for (cudaEvent_t& e : P->copy_events) CK(P, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  FieldPtrs hp{}, dp{};
+  bool mapped = P->host_copy == 1 && bytes % 16 == 0;
+  for (int c = 0; c < 6 && mapped; ++c) {
+    void* a = nullptr;
+    if (cudaHostGetDevicePointer(&a, host[c], 0) != cudaSuccess || !aligned16(a) || !aligned16(devb[c])) {
+      cudaGetLastError();
+      mapped = false;
+      break;
+    }
+    hp.p[c] = a;
+    dp.p[c] = devb[c];
+  }
+  if (mapped) {
+    int sms = 0, gpu = 0;
+    CK(P, cudaGetDevice(&gpu));
+    CK(P, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gpu));
+    CK(P, launch_copy_fields(to_dev ? dp : hp, to_dev ? hp : dp, 6, (int64_t)bytes, 2 * sms, st));
+    return PSATD_OK;
+  }
+  CK(P, cudaEventRecord(P->copy_events[6], st));
+  for (int c = 0; c < 6; ++c) {
+    CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
+    CK(P, cudaMemcpyAsync(to_dev ? devb[c] : host[c], to_dev ? host[c] : devb[c], bytes,
+                          to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, P->copy_streams[c]));
+    CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
+    CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
+  }
+  return PSATD_OK;
+}
+
 psatd_status psatd_push_host(psatd_plan* P, const psatd_fields* in, const psatd_fields* out,
                              const psatd_sources* s, int32_t nsteps, void* stream) {
   if (!P) return PSATD_ERR_INVALID_ARG;
@@ -1815,68 +1867,74 @@ psatd_status psatd_push_host(psatd_plan* P, const psatd_fields* in, const psatd_
   try {
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)P->field_total * P->rsize;
-    if (!P->host_stage[0]) {
-      for (int c = 0; c < 6; ++c) {
-        CK(P, dalloc(P, bytes, &P->host_stage[c]));
-        CK(P, cudaStreamCreateWithFlags(&P->copy_streams[c], cudaStreamNonBlocking));
-      }
-      for (cudaEvent_t& e : P->copy_events) CK(P, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    }
-    const void* src[6] = {in->E[0], in->E[1], in->E[2], in->B[0], in->B[1], in->B[2]};
+    if (!P->host_stage[0])
+      for (int c = 0; c < 6; ++c) CK(P, dalloc(P, bytes, &P->host_stage[c]));
+    void* src[6] = {in->E[0], in->E[1], in->E[2], in->B[0], in->B[1], in->B[2]};
     void* dst[6] = {out->E[0], out->E[1], out->E[2], out->B[0], out->B[1], out->B[2]};
-    // SM-driven copies need every host buffer page-locked and mapped into the
-    // device's address space (cudaHostGetDevicePointer gives the address the
-    // kernel may use) and 16-byte aligned; otherwise the copy engines move it
-    FieldPtrs hin{}, hout{}, stage{};
-    bool mapped = P->host_copy == 1;
-    for (int c = 0; c < 6 && mapped; ++c) {
-      void *a = nullptr, *b = nullptr;
-      if (cudaHostGetDevicePointer(&a, const_cast<void*>(src[c]), 0) != cudaSuccess ||
-          cudaHostGetDevicePointer(&b, dst[c], 0) != cudaSuccess || !aligned16(a) || !aligned16(b)) {
-        cudaGetLastError();
-        mapped = false;
-        break;
-      }
-      hin.p[c] = a;
-      hout.p[c] = b;
-      stage.p[c] = P->host_stage[c];
-    }
-    int sms = 0, gpu = 0;
-    CK(P, cudaGetDevice(&gpu));
-    CK(P, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gpu));
-    if (mapped) {
-      CK(P, launch_copy_fields(stage, hin, 6, (int64_t)bytes, 2 * sms, st));
-    } else {
-      // host -> device: every component on its own copy stream, after the
-      // caller's earlier work on `stream`
-      CK(P, cudaEventRecord(P->copy_events[6], st));
-      for (int c = 0; c < 6; ++c) {
-        CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
-        CK(P, cudaMemcpyAsync(P->host_stage[c], src[c], bytes, cudaMemcpyHostToDevice, P->copy_streams[c]));
-        CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
-        CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
-      }
-    }
+    psatd_status r = host_copies(P, src, P->host_stage, bytes, true, st);
+    if (r != PSATD_OK) return r;
     psatd_fields dev{};
     for (int a = 0; a < 3; ++a) {
       dev.E[a] = P->host_stage[a];
       dev.B[a] = P->host_stage[3 + a];
     }
-    const psatd_status r = psatd_push(P, &dev, s, nsteps, stream);
+    r = psatd_push(P, &dev, s, nsteps, stream);
     if (r != PSATD_OK) return r;
-    if (mapped) {
-      CK(P, launch_copy_fields(hout, stage, 6, (int64_t)bytes, 2 * sms, st));
-    } else {
-      // device -> host, again one copy stream per component; `stream` waits
-      // for all of them, so work queued after this call sees the results
-      CK(P, cudaEventRecord(P->copy_events[6], st));
-      for (int c = 0; c < 6; ++c) {
-        CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
-        CK(P, cudaMemcpyAsync(dst[c], P->host_stage[c], bytes, cudaMemcpyDeviceToHost, P->copy_streams[c]));
-        CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
-        CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
-      }
+    r = host_copies(P, dst, P->host_stage, bytes, false, st);
+    if (r != PSATD_OK) return r;
+    P->last_stream = st;
+    return PSATD_OK;
+  } catch (...) {
+    return fail(P, PSATD_ERR_INVALID_ARG, "internal error");
+  }
+}
+
+psatd_status psatd_push_host_global(psatd_plan* P, const psatd_fields* in, const psatd_fields* out,
+                                    const psatd_sources* s, int32_t nsteps, void* stream) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  if (P->desc.decomp == PSATD_DECOMP_INDEPENDENT)
+    return fail(P, PSATD_ERR_STATE, "independent boxes have no global domain");
+  if (!in || !out) return fail(P, PSATD_ERR_INVALID_ARG, "host field sets must not be NULL");
+  for (int a = 0; a < 3; ++a)
+    if (!in->E[a] || !in->B[a] || !out->E[a] || !out->B[a])
+      return fail(P, PSATD_ERR_INVALID_ARG, "a host field pointer is NULL");
+  if (nsteps < 0) return fail(P, PSATD_ERR_INVALID_ARG, "nsteps < 0");
+  try {
+    cudaStream_t st = (cudaStream_t)stream;
+    const psatd_plan_desc& d = P->desc;
+    const size_t gcells = (size_t)d.global_n[0] * d.global_n[1] * d.global_n[2];
+    const size_t gbytes = gcells * P->rsize, bytes = (size_t)P->field_total * P->rsize;
+    if (!P->global_coupling) {
+      psatd_box g{};
+      for (int a = 0; a < 3; ++a) g.n[a] = d.global_n[a];
+      g.order_p = P->boxes[0].order_p;
+      psatd_coupling* c = nullptr;
+      const psatd_status r = psatd_coupling_create(P, 1, &g, &c);
+      if (r != PSATD_OK) return r;
+      P->global_coupling = c;
+      for (int q = 0; q < 6; ++q) CK(P, dalloc(P, (gbytes + 255) / 256 * 256, &P->global_stage[q]));
     }
+    if (!P->host_stage[0])
+      for (int c = 0; c < 6; ++c) CK(P, dalloc(P, bytes, &P->host_stage[c]));
+    void* src[6] = {in->E[0], in->E[1], in->E[2], in->B[0], in->B[1], in->B[2]};
+    void* dst[6] = {out->E[0], out->E[1], out->E[2], out->B[0], out->B[1], out->B[2]};
+    // the domain to the device, then into the padded boxes (guards included)
+    psatd_status r = host_copies(P, src, P->global_stage, gbytes, true, st);
+    if (r != PSATD_OK) return r;
+    r = psatd_couple(P->global_coupling, PSATD_G1_TO_G2, P->global_stage, P->host_stage, 6, stream);
+    if (r != PSATD_OK) return r;
+    psatd_fields dev{};
+    for (int a = 0; a < 3; ++a) {
+      dev.E[a] = P->host_stage[a];
+      dev.B[a] = P->host_stage[3 + a];
+    }
+    r = psatd_push(P, &dev, s, nsteps, stream);
+    if (r != PSATD_OK) return r;
+    // the box interiors back into the domain, and to the host
+    r = psatd_couple(P->global_coupling, PSATD_G2_TO_G1, P->global_stage, P->host_stage, 6, stream);
+    if (r != PSATD_OK) return r;
+    r = host_copies(P, dst, P->global_stage, gbytes, false, st);
+    if (r != PSATD_OK) return r;
     P->last_stream = st;
     return PSATD_OK;
   } catch (...) {

@@ -182,6 +182,14 @@ class Plan:
         A.psatd_push_host(self.handle, self.fields_struct(host_in), self.fields_struct(host_out),
                           self.sources_struct(sources), int(nsteps), self.stream.cuda_stream)
 
+    def push_host_global(self, host_in, host_out=None, sources=None, nsteps=1):
+        """psatd_push_host_global: fields as whole-domain host tensors (dict
+        component -> CPU tensor of global_n[0]*global_n[1]*global_n[2],
+        x fastest); results in host_out (default: in place)."""
+        host_out = host_in if host_out is None else host_out
+        A.psatd_push_host_global(self.handle, self.fields_struct(host_in), self.fields_struct(host_out),
+                                 self.sources_struct(sources), int(nsteps), self.stream.cuda_stream)
+
     def guard_exchange(self, fields, sources=None):
         A.psatd_guard_exchange(self.handle, self.fields_struct(fields),
                                self.sources_struct(sources), self.stream.cuda_stream)
