@@ -387,7 +387,8 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
  *   PSATD_TUNE_Z_PREFETCH    (runtime) register z kernel (the fused z FFT +
  *                            update pass): every CTA first prefetches into L2
  *                            the input tile of the CTA launched `value` blocks
- *                            after it (0 = off; 0 <= value <= 2^20).
+ *                            after it (0 = off; 0 <= value <= 2^20;
+ *                            default 64).
  *   PSATD_TUNE_PENCIL_ROWS_KB  pencil x-pass batching: shared memory (KiB)
  *                            for the rows one CTA transforms (8 .. 200;
  *                            default 64).

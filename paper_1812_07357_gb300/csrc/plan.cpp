@@ -361,7 +361,8 @@ struct psatd_plan {
   int reg_code = -1;                           // register plane kernels for every fast box
   int reg_z = 0;                               // register z kernel length (0: none)
   int reg_zst = 0;                             // n1 * (n0/2 + 1) of every register-z box, else 0
-  int z_prefetch = 0;                          // register z kernel: L2 prefetch distance in CTAs
+  int z_prefetch = 64;                         // register z kernel: L2 prefetch distance in CTAs (64: measured
+                                               // best of 0 .. 1216 on 512 boxes of 96^3)
   int pen_rows_kb = 64;                        // pencil x pass: shared memory for one CTA's rows
   int host_copy = 1;                           // host path: 1 = SM copy kernel on mapped memory, 0 = copy engines
   int z_tile = 0;                              // plane/pencil z tile columns (0: the kernel maximum)
