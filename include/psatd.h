@@ -401,6 +401,10 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
  *                            when every buffer is page-locked, mapped and
  *                            16-byte aligned (else the copy engines); 0 = the
  *                            copy engines, one stream per component.
+ *   PSATD_TUNE_PENCIL_REG_Z  FP32 boxes on the pencil kernels whose z length
+ *                            has a register z kernel (48, 60, 80, 96, 120):
+ *                            1 (default) = that kernel does their z pass,
+ *                            0 = the shared-memory pencil z kernel.
  * psatd_plan_create and psatd_plan_validate return PSATD_ERR_INVALID_ARG for
  * an unknown knob or a value out of range, psatd_plan_tune also for a knob
  * that is not runtime; psatd_plan_tuning returns the knob's value, or -1 for
@@ -409,6 +413,7 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
 #define PSATD_TUNE_PENCIL_ROWS_KB 2
 #define PSATD_TUNE_Z_TILE 3
 #define PSATD_TUNE_HOST_COPY 4
+#define PSATD_TUNE_PENCIL_REG_Z 5
 psatd_status psatd_plan_tune(psatd_plan* plan, int32_t knob, int32_t value);
 int32_t psatd_plan_tuning(const psatd_plan* plan, int32_t knob);
 

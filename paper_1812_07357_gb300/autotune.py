@@ -14,7 +14,9 @@ tuned:
   smaller CTAs for small boxes);
 * ``pencil_rows_kb``: pencil batching -- the shared memory, hence the number
   of x rows, of one pencil CTA;
-* ``z_prefetch``: the register z kernel's L2 prefetch distance.
+* ``z_prefetch``: the register z kernel's L2 prefetch distance;
+* ``pencil_reg_z``: the register z kernel or the shared-memory one for the z
+  pass of pencil boxes whose z length has both.
 
 The FFT radix order of every length is fixed at build time (two-pass
 factorisations and prime-factor codelets per length), so it is not searched.
@@ -34,6 +36,7 @@ from . import _abi as A
 
 FAMILIES = ("default", "plane", "pencil", "generic")
 KNOB_VALUES = {
+    "pencil_reg_z": (1, 0),
     "z_tile": {32: (8, 4, 2), 64: (4, 2)},
     "pencil_rows_kb": (16, 32, 64, 128),
     "z_prefetch": (0, 64, 152),
@@ -76,7 +79,7 @@ def search(measure: Callable[[str, Dict[str, int]], Tuple[float, Dict[str, int]]
         if best is None or ms < best[2]:
             best = (fam, {}, ms, used)
     fam, tun, ms, used = best
-    for knob in ("z_tile", "pencil_rows_kb", "z_prefetch"):
+    for knob in ("pencil_reg_z", "z_tile", "pencil_rows_kb", "z_prefetch"):
         if knob not in used:
             continue
         values = KNOB_VALUES[knob][precision] if isinstance(KNOB_VALUES[knob], dict) else KNOB_VALUES[knob]

@@ -287,5 +287,7 @@ template <typename T, int DIR>
 struct Dft<T, 40, DIR> : DftPfa<T, 8, 5, DIR> {};
 template <typename T, int DIR>
 struct Dft<T, 48, DIR> : DftPfa<T, 16, 3, DIR> {};
+template <typename T, int DIR>
+struct Dft<T, 60, DIR> : DftPfa<T, 12, 5, DIR> {};
 
 }  // namespace psatd

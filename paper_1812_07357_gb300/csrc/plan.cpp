@@ -95,7 +95,8 @@ Err validate(const psatd_plan_desc* d) {
       const bool ok = (k == PSATD_TUNE_Z_PREFETCH && v >= 0 && v <= (1 << 20)) ||
                       (k == PSATD_TUNE_PENCIL_ROWS_KB && v >= 8 && v <= 200) ||
                       (k == PSATD_TUNE_Z_TILE && v >= 1 && v <= fast_tile(d->precision == 64 ? 64 : 32)) ||
-                      (k == PSATD_TUNE_HOST_COPY && (v == 0 || v == 1));
+                      (k == PSATD_TUNE_HOST_COPY && (v == 0 || v == 1)) ||
+                      (k == PSATD_TUNE_PENCIL_REG_Z && (v == 0 || v == 1));
       if (!ok) return {PSATD_ERR_INVALID_ARG, fmt("tuning knob %d: value %d unknown or out of range", k, v)};
     }
     if (i == 16 && d->tuning[32] != 0) return {PSATD_ERR_INVALID_ARG, "more than 16 tuning pairs"};
@@ -340,6 +341,9 @@ struct psatd_plan {
     int64_t start, count;     // jobs of the list
   };
   std::vector<PenGroup> grp_rows, grp_rows_int, grp_ycols, grp_ycols_int, grp_z;
+  std::vector<ColJob> zpen_reg;              // pencil boxes whose z pass runs on the register z kernel
+  std::vector<PenGroup> grp_zreg;            // ... grouped by z length (code = n2)
+  int pen_reg_z = 1;                         // tuning: register z kernel for pencil boxes where one exists
   int pen_boxes = 0;
   std::vector<CopyBlk> blocks;
   std::vector<XTile> tiles;                                   // every block (psatd_guard_exchange)
@@ -386,7 +390,7 @@ struct psatd_plan {
   ColJob *d_g_ycols = nullptr, *d_g_ycols_int = nullptr, *d_g_zcols = nullptr, *d_zfast = nullptr;
   int2 *d_plane_fwd = nullptr, *d_plane_inv = nullptr;
   RowJob *d_pen_rows = nullptr, *d_pen_rows_int = nullptr;
-  ColJob *d_pen_ycols = nullptr, *d_pen_ycols_int = nullptr, *d_zpen = nullptr;
+  ColJob *d_pen_ycols = nullptr, *d_pen_ycols_int = nullptr, *d_zpen = nullptr, *d_zpen_reg = nullptr;
   CopyBlk* d_blocks = nullptr;
   XTile* d_tiles = nullptr;
   XTile* d_step_tiles = nullptr;
@@ -885,6 +889,29 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     }
   };
   auto shape_of_box = [&](int box) -> const ShapeDev& { return P->hshapes[P->hboxes[box].shape]; };
+  // FP32 pencil boxes whose z length has a register z kernel: that kernel
+  // does their z pass (z FFT, update, inverse z FFT), its jobs re-tiled to
+  // its own tile width; the shared-memory pencil z kernel keeps the rest
+  if (P->prec == 32 && P->pen_reg_z && !P->zpen.empty()) {
+    const int rt = z_reg_tile_width(P->form);
+    std::vector<ColJob> keep;
+    std::vector<char> done(P->boxes.size(), 0);
+    for (const ColJob& j : P->zpen) {
+      const psatd_box& b = P->boxes[j.box];
+      if (!(z_reg_ok(b.n[2]) && z_reg_smem(P->form, b.n[2]) <= optin)) {
+        keep.push_back(j);
+        continue;
+      }
+      if (done[j.box]) continue;
+      done[j.box] = 1;
+      const int L = b.n[0] / 2, n1 = b.n[1];
+      for (int y = 0; y < n1; ++y)
+        for (int m = 0; m < L; m += rt) P->zpen_reg.push_back({j.box, y, m, std::min(rt, L - m)});
+      for (int y = 0; y < n1; y += rt) P->zpen_reg.push_back({j.box, y, L, -std::min(rt, n1 - y)});
+    }
+    P->zpen.swap(keep);
+  }
+  group(P->zpen_reg, [&](const ColJob& j) { return P->boxes[j.box].n[2]; }, P->grp_zreg);
   group(P->pen_rows, [&](const RowJob& j) { return shape_of_box(j.box).px; }, P->grp_rows);
   group(P->pen_rows_int, [&](const RowJob& j) { return shape_of_box(j.box).px; }, P->grp_rows_int);
   group(P->pen_ycols, [&](const ColJob& j) { return shape_of_box(j.box).py; }, P->grp_ycols);
@@ -1021,6 +1048,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   CK(P, upload(P, P->pen_ycols, &P->d_pen_ycols));
   CK(P, upload(P, P->pen_ycols_int, &P->d_pen_ycols_int));
   CK(P, upload(P, P->zpen, &P->d_zpen));
+  CK(P, upload(P, P->zpen_reg, &P->d_zpen_reg));
   CK(P, upload(P, P->blocks, &P->d_blocks));
   CK(P, upload(P, P->tiles, &P->d_tiles));
   CK(P, upload(P, P->step_tiles, &P->d_step_tiles));
@@ -1441,6 +1469,7 @@ psatd_status psatd_plan_create(const psatd_plan_desc* desc, void* stream, psatd_
       if (k == PSATD_TUNE_PENCIL_ROWS_KB) P->pen_rows_kb = v;
       if (k == PSATD_TUNE_Z_TILE) P->z_tile = v;
       if (k == PSATD_TUNE_HOST_COPY) P->host_copy = v;
+      if (k == PSATD_TUNE_PENCIL_REG_Z) P->pen_reg_z = v;
     }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -1638,6 +1667,13 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
     if (r != PSATD_OK) return r;
   }
   // S1 (z) + S2 + S3 (z)
+  for (const auto& g : P->grp_zreg) {
+    CK(P, timed(P, 2, st, [&] {
+         return launch_z_reg(P->form, D, P->d_ws, S, P->d_zpen_reg + g.start, g.count, g.code, 0, NFT, P->z_prefetch,
+                             st);
+       }));
+    ++launches;
+  }
   for (const auto& g : P->grp_z) {
     CK(P, timed(P, 2, st, [&] {
          return launch_z_pen(P->prec, P->form, g.code, D, P->d_ws, S, P->d_zpen + g.start, g.count, P->smem_penz,
@@ -2031,6 +2067,7 @@ psatd_status psatd_plan_tune(psatd_plan* P, int32_t knob, int32_t value) {
       return PSATD_OK;   // not part of any captured graph
     case PSATD_TUNE_PENCIL_ROWS_KB:
     case PSATD_TUNE_Z_TILE:
+    case PSATD_TUNE_PENCIL_REG_Z:
       return fail(P, PSATD_ERR_INVALID_ARG, "this knob is set at plan creation only");
     default:
       return fail(P, PSATD_ERR_INVALID_ARG, "unknown tuning knob");
@@ -2048,11 +2085,13 @@ int32_t psatd_plan_tuning(const psatd_plan* P, int32_t knob) {
   if (!P) return -1;
   switch (knob) {
     case PSATD_TUNE_Z_PREFETCH:
-      return P->reg_z ? P->z_prefetch : -1;
+      return P->reg_z || !P->zpen_reg.empty() ? P->z_prefetch : -1;
     case PSATD_TUNE_PENCIL_ROWS_KB:
       return P->pen_boxes ? P->pen_rows_kb : -1;
     case PSATD_TUNE_HOST_COPY:
       return P->host_copy;
+    case PSATD_TUNE_PENCIL_REG_Z:
+      return P->pen_boxes && P->prec == 32 ? P->pen_reg_z : -1;
     case PSATD_TUNE_Z_TILE:
       return (P->pen_boxes || (P->fast_boxes && !P->reg_z))
                  ? (P->z_tile > 0 ? std::min(P->z_tile, fast_tile(P->prec)) : fast_tile(P->prec))

@@ -384,10 +384,17 @@ constexpr HalfTwiddles<NZ> half_twiddles() {
 }
 __constant__ HalfTwiddles<96> kTw96 = half_twiddles<96>();
 __constant__ HalfTwiddles<48> kTw48 = half_twiddles<48>();
+__constant__ HalfTwiddles<60> kTw60 = half_twiddles<60>();
+__constant__ HalfTwiddles<80> kTw80 = half_twiddles<80>();
+__constant__ HalfTwiddles<120> kTw120 = half_twiddles<120>();
 template <int NZ>
 __device__ __forceinline__ float2 half_twiddle(int k) {
-  static_assert(NZ == 96 || NZ == 48, "register z lengths");
-  return NZ == 96 ? kTw96.w[k] : kTw48.w[k];
+  static_assert(NZ == 96 || NZ == 48 || NZ == 60 || NZ == 80 || NZ == 120, "register z lengths");
+  if constexpr (NZ == 96) return kTw96.w[k];
+  else if constexpr (NZ == 48) return kTw48.w[k];
+  else if constexpr (NZ == 60) return kTw60.w[k];
+  else if constexpr (NZ == 80) return kTw80.w[k];
+  else return kTw120.w[k];
 }
 
 // mx columns (or Nyquist-column y rows) per z tile: 16 (128-byte rows of a
@@ -543,7 +550,7 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
 }  // namespace
 
 // z lengths with a register z kernel: X(NZ)
-#define PSATD_REG_Z(X) X(96) X(48)
+#define PSATD_REG_Z(X) X(96) X(48) X(60) X(80) X(120)
 
 int z_reg_ok(int n2) {
 #define PSATD_ZC(NZV) \

@@ -187,3 +187,47 @@ def test_pencil_local_192_boxes_and_hybrid_384_groups():
     f = I.laser_fields((1024, 48, 48), wavelength=16.0, waist=12.0, duration=20.0)
     _check(lay, {k: I.scatter_global(v, lay) for k, v in f.items()}, {}, 2, (1.0,) * 3, 0.9, 32, "vacuum",
            (0, 4))
+
+
+@pytest.mark.parametrize("form", ["vacuum", "rho"])
+def test_pencil_boxes_z_pass_on_register_kernel_and_shared_memory_kernel(form):
+    """FP32 pencil boxes with z lengths 48, 60, 80, 96, 120 (the uneven
+    batch's): their z pass runs on the register z kernel (default) or on the
+    shared-memory pencil z kernel (tuning knob); both against the oracle, and
+    each other."""
+    from paper_1812_07357_gb300.solver import Plan
+    sizes = [(160, 24, 48), (48, 160, 60), (60, 48, 80), (80, 60, 96), (48, 48, 120)]
+    boxes = [I.Box(n, (4, 4, 4), (4, 4, 4), (0, 0, 0), p) for n, p in zip(sizes, (8, 16, 32, 0, 16))]
+    lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
+    rng = np.random.default_rng(28)
+    if form == "rho":
+        js = {k: [] for k in ("Jx", "Jy", "Jz")}
+        for b in lay.boxes:
+            j = I.band_limited_current(b.interior, rng)
+            for k in js:
+                js[k].append(j[k])
+        src = {k: I.round_to(I.scatter_self(v, lay), np.float32) for k, v in js.items()}
+        src["rho"] = I.zeros(lay)
+        fields = {k: I.zeros(lay) for k in O.COMPS}
+    else:
+        src = {}
+        fields = {k: I.round_to(O.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes]), np.float32)
+                  for k in O.COMPS}
+    comps = O.COMPS + (("rho",) if form == "rho" else ())
+    ref = O.push(lay, fields, src, 3, (1.0,) * 3, 0.9, form=form)
+    outs = []
+    for reg in (1, 0):
+        plan = Plan(lay, (1.0,) * 3, 0.9, precision=32, sources=form, pencil=True, j_constant=form == "rho",
+                    tuning={"pencil_reg_z": reg})
+        assert plan.pencil_boxes == 5 and plan.tuning().get("pencil_reg_z") == reg
+        df = plan.pack_fields(fields)
+        ds = plan.pack_fields(src) if form == "rho" else None
+        plan.push(df, ds, 3)
+        plan.sync()
+        got = plan.unpack_fields(df)
+        if form == "rho":
+            got["rho"] = plan.unpack(ds["rho"])
+        plan.close()
+        assert_fields(lay, got, ref, comps, 32, what=f"pencil_reg_z={reg}")
+        outs.append(got)
+    assert_fields(lay, outs[0], outs[1], comps, 32, what="register vs shared-memory z pass")
