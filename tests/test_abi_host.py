@@ -251,3 +251,10 @@ def test_validate_absorbing_layers(lib, case):
     assert (st == A.PSATD_OK) == (case == "ok"), (case, msg)
     if case != "ok":
         assert st == A.PSATD_ERR_INVALID_ARG, msg
+
+
+def test_validate_rejects_an_empty_plan(lib):
+    d = _desc(I.global_layout((16, 16, 16), 8))
+    d.num_boxes = 0
+    st, msg = A.psatd_plan_validate(d)
+    assert st == A.PSATD_ERR_INVALID_ARG and "box" in msg

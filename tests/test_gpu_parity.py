@@ -354,3 +354,56 @@ def test_global_reference_lengths_fp64_long_step():
     assert (plan.fast_boxes, plan.pencil_boxes) == (0, 0)
     plan.close()
     check_push(lay, fields, {}, 1, (1.0,) * 3, 400 * 0.9, 64, "vacuum")
+
+
+# ---------------------------------------------------------------------------
+# edge cases: the smallest boxes, one-sided guards, the largest box
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_smallest_boxes_and_one_sided_guards(prec):
+    """Self-periodic boxes at the size limits' low end (4 cells on an axis,
+    one guard) and with different guard widths on the two faces of an axis,
+    J form, 3 steps."""
+    boxes = [I.Box((4, 4, 4), (1, 1, 1), (1, 1, 1), (0, 0, 0), 2),
+             I.Box((4, 6, 8), (1, 2, 0), (1, 0, 3), (0, 0, 0), 4),
+             I.Box((24, 20, 18), (2, 3, 1), (4, 1, 3), (0, 0, 0), 8),
+             I.Box((30, 10, 6), (0, 1, 2), (5, 2, 0), (0, 0, 0), 0)]
+    lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
+    rng = np.random.default_rng(33)
+    fields = {k: O.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes]) for k in O.COMPS}
+    src = {k: O.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes]) for k in ("Jx", "Jy", "Jz")}
+    check_push(lay, fields, src, 3, (1.0, 0.8, 1.2), 0.6, prec, "J")
+
+
+def test_largest_box_fft_sampled_modes_and_round_trip():
+    """The largest box the ABI accepts (1024 x 512 x 512 cells, FP32): the
+    forward transform at sampled modes against the DFT summed directly in
+    FP64 (separable phases, all 2.7e8 cells), and the inverse of the forward
+    transform against the input (a property at any size)."""
+    import torch
+    n0, n1, n2 = 1024, 512, 512
+    lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), [I.Box((n0, n1, n2), (0,) * 3, (0,) * 3, (0, 0, 0), 0)])
+    plan = Plan(lay, (1.0,) * 3, 0.5, precision=32)
+    gen = torch.Generator(device="cuda").manual_seed(34)
+    x = torch.randn(n0 * n1 * n2, generator=gen, device="cuda", dtype=torch.float32)
+    spec = plan.forward_fft(x)
+    back = plan.inverse_fft(spec.clone())
+    plan.sync()
+    rel = float((back - x).double().norm() / x.double().norm())
+    assert rel <= FFT_TOL[32], rel
+    xs = x.view(n2, n1, n0).double().cpu().numpy()
+    sv = spec[: (n0 // 2 + 1) * n1 * n2].view(n2, n1, n0 // 2 + 1).cpu().numpy()
+    rng = np.random.default_rng(35)
+    modes = [(0, 0, 0), (n0 // 2, n1 // 2, n2 // 2), (1, n1 - 1, 3)] + \
+            [(int(rng.integers(0, n0 // 2 + 1)), int(rng.integers(0, n1)), int(rng.integers(0, n2))) for _ in range(3)]
+    scale = float(np.sqrt(np.sum(xs ** 2)))          # |X(m)| ~ ||x|| for white noise
+    for mx, my, mz in modes:
+        ex = np.exp(-2j * np.pi * mx * np.arange(n0) / n0)
+        ey = np.exp(-2j * np.pi * my * np.arange(n1) / n1)
+        ez = np.exp(-2j * np.pi * mz * np.arange(n2) / n2)
+        ax = xs @ ex.real + 1j * (xs @ ex.imag)           # no complex copy of the 2 GB array
+        want = ez @ (ax @ ey)
+        got = complex(sv[mz, my, mx])
+        assert abs(got - want) <= FFT_TOL[32] * scale, (mx, my, mz, got, want)
+    plan.close()
