@@ -405,13 +405,6 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
  *                            has a register z kernel (48, 60, 80, 96, 120):
  *                            1 (default) = that kernel does their z pass,
  *                            0 = the shared-memory pencil z kernel.
- *   PSATD_TUNE_Z_STAGE       (runtime) register z kernel: 1 (default) = each
- *                            CTA stages its tile in shared memory with bulk
- *                            copies (one per field slot and z row, completing
- *                            on an mbarrier with a bounded wait: a wait that
- *                            runs out makes psatd_sync_status return
- *                            PSATD_ERR_TIMEOUT), 0 = every thread loads its
- *                            z samples from global memory.
  * psatd_plan_create and psatd_plan_validate return PSATD_ERR_INVALID_ARG for
  * an unknown knob or a value out of range, psatd_plan_tune also for a knob
  * that is not runtime; psatd_plan_tuning returns the knob's value, or -1 for
@@ -421,7 +414,6 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
 #define PSATD_TUNE_Z_TILE 3
 #define PSATD_TUNE_HOST_COPY 4
 #define PSATD_TUNE_PENCIL_REG_Z 5
-#define PSATD_TUNE_Z_STAGE 6
 psatd_status psatd_plan_tune(psatd_plan* plan, int32_t knob, int32_t value);
 int32_t psatd_plan_tuning(const psatd_plan* plan, int32_t knob);
 

@@ -96,8 +96,7 @@ Err validate(const psatd_plan_desc* d) {
                       (k == PSATD_TUNE_PENCIL_ROWS_KB && v >= 8 && v <= 200) ||
                       (k == PSATD_TUNE_Z_TILE && v >= 1 && v <= fast_tile(d->precision == 64 ? 64 : 32)) ||
                       (k == PSATD_TUNE_HOST_COPY && (v == 0 || v == 1)) ||
-                      (k == PSATD_TUNE_PENCIL_REG_Z && (v == 0 || v == 1)) ||
-                      (k == PSATD_TUNE_Z_STAGE && (v == 0 || v == 1));
+                      (k == PSATD_TUNE_PENCIL_REG_Z && (v == 0 || v == 1));
       if (!ok) return {PSATD_ERR_INVALID_ARG, fmt("tuning knob %d: value %d unknown or out of range", k, v)};
     }
     if (i == 16 && d->tuning[32] != 0) return {PSATD_ERR_INVALID_ARG, "more than 16 tuning pairs"};
@@ -345,7 +344,6 @@ struct psatd_plan {
   std::vector<ColJob> zpen_reg;              // pencil boxes whose z pass runs on the register z kernel
   std::vector<PenGroup> grp_zreg;            // ... grouped by z length (code = n2)
   int pen_reg_z = 1;                         // tuning: register z kernel for pencil boxes where one exists
-  int z_stage = 1;                           // tuning: register z kernel stages its tile by bulk copies
   int pen_boxes = 0;
   std::vector<CopyBlk> blocks;
   std::vector<XTile> tiles;                                   // every block (psatd_guard_exchange)
@@ -403,7 +401,6 @@ struct psatd_plan {
   GatherGrid* d_ggrid = nullptr;
   void *d_rpool = nullptr, *d_cpool = nullptr, *d_coef = nullptr;
   void* d_ws = nullptr;
-  int* d_status = nullptr;   // device status word: bit 0 = a bounded device-side wait ran out
   size_t plan_bytes = 0;
 
   std::string last_error = "no error";
@@ -436,14 +433,13 @@ struct psatd_plan {
   std::vector<Rec> recs;
 
   DevPlan dev() const {
-    DevPlan P{};
+    DevPlan P;
     P.boxes = d_boxes;
     P.shapes = d_shapes;
     P.rpool = d_rpool;
     P.cpool = d_cpool;
     P.coef = d_coef;
     set_constants(P, desc.c, desc.eps0, desc.dt);
-    P.status = d_status;
     return P;
   }
 
@@ -1064,11 +1060,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   CK(P, dalloc(P, (size_t)rtot * P->rsize, &P->d_rpool));
   CK(P, dalloc(P, (size_t)ctot * P->csize, &P->d_cpool));
   CK(P, dalloc(P, (size_t)qtot * 4 * P->rsize, &P->d_coef));
-  // (+256 bytes: the register z kernel's bulk copies of a tile's rows may
-  // read up to one tile width past the last row)
-  CK(P, dalloc(P, (size_t)spec_slots(P->form) * P->spec_total * P->csize + 256, &P->d_ws));
-  CK(P, dalloc(P, sizeof(int), (void**)&P->d_status));
-  CK(P, cudaMemsetAsync(P->d_status, 0, sizeof(int), st));
+  CK(P, dalloc(P, (size_t)spec_slots(P->form) * P->spec_total * P->csize, &P->d_ws));
   // ---- FP64 tables
   double *r64 = nullptr, *alpha = nullptr;
   double2* c64 = nullptr;
@@ -1478,7 +1470,6 @@ psatd_status psatd_plan_create(const psatd_plan_desc* desc, void* stream, psatd_
       if (k == PSATD_TUNE_Z_TILE) P->z_tile = v;
       if (k == PSATD_TUNE_HOST_COPY) P->host_copy = v;
       if (k == PSATD_TUNE_PENCIL_REG_Z) P->pen_reg_z = v;
-      if (k == PSATD_TUNE_Z_STAGE) P->z_stage = v;
     }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -1679,7 +1670,7 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
   for (const auto& g : P->grp_zreg) {
     CK(P, timed(P, 2, st, [&] {
          return launch_z_reg(P->form, D, P->d_ws, S, P->d_zpen_reg + g.start, g.count, g.code, 0, NFT, P->z_prefetch,
-                             P->z_stage, st);
+                             st);
        }));
     ++launches;
   }
@@ -1693,7 +1684,7 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
   if (!P->zfast.empty() && P->reg_z) {
     CK(P, timed(P, 2, st, [&] {
          return launch_z_reg(P->form, D, P->d_ws, S, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, P->reg_zst,
-                             NFT, P->z_prefetch, P->z_stage, st);
+                             NFT, P->z_prefetch, st);
        }));
     ++launches;
   } else if (!P->zfast.empty()) {
@@ -2027,15 +2018,6 @@ psatd_status psatd_sync_status(psatd_plan* P) {
   cudaError_t e = cudaStreamSynchronize(P->last_stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return fail(P, PSATD_ERR_CUDA, fmt("device error: %s", cudaGetErrorString(e)));
-  if (P->d_status) {
-    int word = 0;
-    e = cudaMemcpy(&word, P->d_status, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return fail(P, PSATD_ERR_CUDA, fmt("status word: %s", cudaGetErrorString(e)));
-    if (word) {
-      cudaMemset(P->d_status, 0, sizeof(int));
-      return fail(P, PSATD_ERR_TIMEOUT, "a bounded device-side wait ran out (its kernel left its work undone)");
-    }
-  }
   return PSATD_OK;
 }
 
@@ -2083,10 +2065,6 @@ psatd_status psatd_plan_tune(psatd_plan* P, int32_t knob, int32_t value) {
       if (value != 0 && value != 1) return fail(P, PSATD_ERR_INVALID_ARG, "host copy mode is 0 or 1");
       P->host_copy = value;
       return PSATD_OK;   // not part of any captured graph
-    case PSATD_TUNE_Z_STAGE:
-      if (value != 0 && value != 1) return fail(P, PSATD_ERR_INVALID_ARG, "z staging is 0 or 1");
-      P->z_stage = value;
-      break;
     case PSATD_TUNE_PENCIL_ROWS_KB:
     case PSATD_TUNE_Z_TILE:
     case PSATD_TUNE_PENCIL_REG_Z:
@@ -2114,8 +2092,6 @@ int32_t psatd_plan_tuning(const psatd_plan* P, int32_t knob) {
       return P->host_copy;
     case PSATD_TUNE_PENCIL_REG_Z:
       return P->pen_boxes && P->prec == 32 ? P->pen_reg_z : -1;
-    case PSATD_TUNE_Z_STAGE:
-      return P->reg_z || !P->zpen_reg.empty() ? P->z_stage : -1;
     case PSATD_TUNE_Z_TILE:
       return (P->pen_boxes || (P->fast_boxes && !P->reg_z))
                  ? (P->z_tile > 0 ? std::min(P->z_tile, fast_tile(P->prec)) : fast_tile(P->prec))

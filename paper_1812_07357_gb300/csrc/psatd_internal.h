@@ -168,7 +168,6 @@ struct DevPlan {
   const void* coef;               // Coef4<T>[]
   double c, eps0, dt;
   double cc, ieps, idt, icce;     // c^2, 1/eps0, 1/dt, 1/(c^2 eps0)
-  int* status;                    // device status word (bit 0: a bounded wait ran out), or NULL
 };
 
 inline void set_constants(DevPlan& P, double c, double eps0, double dt) {
@@ -267,16 +266,13 @@ cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f,
 cudaError_t configure_reg_kernels(int smem_bytes);
 // register z kernel (FP32, tiles of z_reg_tile_width(form) columns) for z length n2
 int z_reg_ok(int n2);
-int z_reg_smem(int form, int n2);   // dynamic shared memory of a launch (staging included)
+int z_reg_smem(int form, int n2);
 int z_reg_tile_width(int form);
 // zst: n1 * (n0/2 + 1) shared by every box of the job list, else 0
 // pf_dist > 0: every CTA first prefetches into L2 the tile of the CTA
-// launched pf_dist blocks after it.  stage != 0: the tile is staged in
-// shared memory by bulk copies (cp.async.bulk, one per slot and z row)
-// instead of each thread loading its samples from global memory; the spectrum
-// buffer must then have 16 bytes of slack past its last element.
+// launched pf_dist blocks after it
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                         int64_t njobs, int n2, int zst, int nft, int pf_dist, int stage, cudaStream_t st);
+                         int64_t njobs, int n2, int zst, int nft, int pf_dist, cudaStream_t st);
 
 // ---- pencil kernels (pencil_kernels.cu): boxes of two-pass lengths too large
 // for the plane kernels; the z pass takes fast_tile(prec) mx columns per tile

@@ -57,40 +57,6 @@ __device__ __forceinline__ void cp_commit_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// ---- bulk copies into shared memory completing on an mbarrier --------------
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-// one bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-// wait for phase `parity` of the barrier, at most `limit` polls (each poll
-// may suspend the thread for a while); false when the limit ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, int limit) {
-  for (int i = 0; i < limit; ++i) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-constexpr int kWaitPolls = 1 << 22;
-
 __device__ __forceinline__ unsigned magic(int d) { return 0xFFFFFFFFu / (unsigned)d + 1u; }
 __device__ __forceinline__ int fdiv(int e, unsigned m) { return m ? (int)__umulhi((unsigned)e, m) : e; }
 
@@ -472,25 +438,16 @@ __device__ __forceinline__ void prefetch_z_tile(const DevPlan& P, const float2* 
   }
 }
 
-// staged row of a z tile: the tile's TX columns with one more on each side,
-// so that the copy starts on the 16-byte boundary at or before the first
-// column (the spectrum rows hold n0/2 + 1 complex values: odd for the even
-// n0 of the register shapes, so half of the rows start mid-way)
-constexpr int z_stage_row(int form) { return z_reg_tile(form) + 2; }
-
 template <int NZ, int FORM, int ZST>
 __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>())
     k_z_reg(DevPlan P, float2* spec, int64_t sstride, const ColJob* __restrict__ jobs, int nft, int njobs,
-            int pf_dist, int stage) {
+            int pf_dist) {
   constexpr int TX = z_reg_tile(FORM), FIN = fields_in(FORM), FOUT = fields_out(FORM);
   constexpr int NT = z_reg_threads<FORM>(), NP = z_reg_pitch(FORM);
   constexpr int H = NZ / 2;
-  constexpr int RW = z_stage_row(FORM);          // complex values per staged row
   static_assert(NT % (2 * TX) == 0, "update threads keep one column");
-  static_assert((RW * 8) % 16 == 0, "bulk copies move 16-byte units");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* buf = reinterpret_cast<float2*>(smem_raw);    // [row][slot * TX + t], pitch NP
-  __shared__ __align__(8) uint64_t bar;
   const ColJob J = jobs[blockIdx.x];
   // the tile that a CTA launched about pf_dist blocks later will read: fetched
   // into L2 now, so that its loads hit L2 instead of waiting on HBM
@@ -510,36 +467,7 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
   const bool live = t < nm && s < FIN;
   const int tc = t < nm ? t : 0, sc = s < FIN ? s : FIN - 1;
   float2 v[H];
-  if (stage && !nyq) {
-    // the tile (every slot, every z row) into shared memory by bulk copies:
-    // row r = s * NZ + z of RW complex values from the 16-byte boundary at
-    // or before column m0 (odd = 1 when that is one value earlier); then
-    // every thread reads its samples there
-    const int odd = (int)((reinterpret_cast<uintptr_t>(g) >> 3) & 1);
-    const char* base = reinterpret_cast<const char*>(g - odd);
-    float2* st = buf;
-    if (tid == 0) {
-      mbar_init(&bar, 1);
-      mbar_expect_tx(&bar, (unsigned)(FIN * NZ * RW * 8));
-    }
-    __syncthreads();
-    for (int r = tid; r < FIN * NZ; r += NT) {
-      const int s2 = r / NZ, z = r - s2 * NZ;
-      bulk_g2s(st + r * RW, base + ((int64_t)s2 * sstride + (int64_t)z * zst) * 8, RW * 8, &bar);
-    }
-    const bool late = !mbar_wait(&bar, 0, kWaitPolls);
-    if (__syncthreads_or(late)) {
-      // the copies did not land in time (a decision every thread shares):
-      // report, give the copies in flight a second bounded wait, leave
-      if (tid == 0 && P.status) atomicOr(P.status, 1);
-      mbar_wait(&bar, 0, kWaitPolls);
-      return;
-    }
-    const float2* sp = st + (int64_t)sc * NZ * RW + tc + odd + half * RW;
-#pragma unroll
-    for (int m = 0; m < H; ++m) v[m] = sp[2 * m * RW];
-    __syncthreads();   // the working layout below overwrites the staged tile
-  } else {
+  {
     const float2* src = g + sc * sstride + (int64_t)tc * ts + half * zst;
 #pragma unroll
     for (int m = 0; m < H; ++m) v[m] = ld_l2_256(src + 2 * m * zst);
@@ -632,10 +560,7 @@ int z_reg_ok(int n2) {
   return 0;
 }
 
-int z_reg_smem(int form, int n2) {
-  const int work = n2 * z_reg_pitch(form) * 8, staged = fields_in(form) * n2 * z_stage_row(form) * 8;
-  return work > staged ? work : staged;
-}
+int z_reg_smem(int form, int n2) { return n2 * z_reg_pitch(form) * 8; }
 
 int z_reg_tile_width(int form) { return z_reg_tile(form); }
 
@@ -643,13 +568,13 @@ int z_reg_tile_width(int form) { return z_reg_tile(form); }
 constexpr int kRegZst = 96 * 49;
 
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
-                         int64_t njobs, int n2, int zst, int nft, int pf_dist, int stage, cudaStream_t st) {
+                         int64_t njobs, int n2, int zst, int nft, int pf_dist, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
   dim3 grid((unsigned)njobs);
   const int smem = z_reg_smem(form, n2);
 #define PSATD_ZF(NZV, F, ZS)                                                                      \
   k_z_reg<NZV, F, ZS><<<grid, z_reg_threads<F>(), smem, st>>>(P, (float2*)spec, sstride, jobs, nft, \
-                                                               (int)njobs, pf_dist, stage)
+                                                               (int)njobs, pf_dist)
 #define PSATD_ZL(NZV)                                                    \
   if (n2 == NZV) {                                                      \
     if (form == kVacuum) {                                              \

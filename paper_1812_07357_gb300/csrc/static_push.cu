@@ -240,7 +240,7 @@ extern "C" psatd_status psatd_push_box_static(const int32_t n[3], int32_t order_
                          reinterpret_cast<float2*>(A + o_c32), ctot, q64,
                          reinterpret_cast<Coef4<float>*>(A + o_q32), qtot, st));
   // ---- the push: S1 forward FFT, S2 update, S3 inverse FFT (no guards)
-  DevPlan P{};
+  DevPlan P;
   P.boxes = reinterpret_cast<const BoxDev*>(A + o_box);
   P.shapes = reinterpret_cast<const ShapeDev*>(A + o_shape);
   P.rpool = A + o_r32;
