@@ -401,10 +401,24 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
  *                            when every buffer is page-locked, mapped and
  *                            16-byte aligned (else the copy engines); 0 = the
  *                            copy engines, one stream per component.
- *   PSATD_TUNE_PENCIL_REG_Z  FP32 boxes on the pencil kernels whose z length
- *                            has a register z kernel (48, 60, 80, 96, 120):
- *                            1 (default) = that kernel does their z pass,
- *                            0 = the shared-memory pencil z kernel.
+ *   PSATD_TUNE_PENCIL_REG_Z  FP32 boxes whose z length has a register z
+ *                            kernel (48, 60, 80, 96, 120), on the pencil
+ *                            kernels, or on the plane kernels in a batch of
+ *                            several z lengths: 1 (default) = that kernel
+ *                            does their z pass, 0 = the shared-memory z
+ *                            kernel of their family.
+ *   PSATD_TUNE_Z_ONE_LAUNCH  (runtime) those boxes' z pass: 0 (default) = one
+ *                            launch per z length, 1 = one persistent launch
+ *                            for every z length (2 CTAs per SM, each taking
+ *                            every grid-th tile in turn and prefetching its
+ *                            next tile into L2).
+ *   PSATD_TUNE_REG_PLANES    FP32 boxes whose plane shape (n0/2, n1) has
+ *                            register plane kernels (n0/2 in 24, 30, 40, 48,
+ *                            60; n1 in 48, 60, 80, 96, 120): 1 (default) =
+ *                            those kernels (one launch per shape), 0 = the
+ *                            family the box would take without them (pencil,
+ *                            or the shared-memory plane kernels with
+ *                            PSATD_PLANE_KERNELS).
  * psatd_plan_create and psatd_plan_validate return PSATD_ERR_INVALID_ARG for
  * an unknown knob or a value out of range, psatd_plan_tune also for a knob
  * that is not runtime; psatd_plan_tuning returns the knob's value, or -1 for
@@ -414,6 +428,8 @@ int32_t psatd_plan_deferred_exchange(const psatd_plan* plan);
 #define PSATD_TUNE_Z_TILE 3
 #define PSATD_TUNE_HOST_COPY 4
 #define PSATD_TUNE_PENCIL_REG_Z 5
+#define PSATD_TUNE_Z_ONE_LAUNCH 6
+#define PSATD_TUNE_REG_PLANES 7
 psatd_status psatd_plan_tune(psatd_plan* plan, int32_t knob, int32_t value);
 int32_t psatd_plan_tuning(const psatd_plan* plan, int32_t knob);
 

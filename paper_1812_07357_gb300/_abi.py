@@ -321,9 +321,12 @@ PSATD_TUNE_PENCIL_ROWS_KB = 2
 PSATD_TUNE_Z_TILE = 3
 PSATD_TUNE_HOST_COPY = 4
 PSATD_TUNE_PENCIL_REG_Z = 5
+PSATD_TUNE_Z_ONE_LAUNCH = 6
+PSATD_TUNE_REG_PLANES = 7
 TUNE_KNOBS = {"z_prefetch": PSATD_TUNE_Z_PREFETCH, "pencil_rows_kb": PSATD_TUNE_PENCIL_ROWS_KB,
               "z_tile": PSATD_TUNE_Z_TILE, "host_copy": PSATD_TUNE_HOST_COPY,
-              "pencil_reg_z": PSATD_TUNE_PENCIL_REG_Z}
+              "pencil_reg_z": PSATD_TUNE_PENCIL_REG_Z, "z_one_launch": PSATD_TUNE_Z_ONE_LAUNCH,
+              "reg_planes": PSATD_TUNE_REG_PLANES}
 
 
 def psatd_push_host(plan: int, fin: psatd_fields, fout: psatd_fields, sources, nsteps: int, stream: int = 0):

@@ -8,15 +8,19 @@ of ranks per group depends on the machine and the problem size) and leaves
 the automation for later.  Here the per-box work of one GPU is what is
 tuned:
 
-* kernel family (``PSATD_*_KERNELS``): register/shared-memory plane kernels,
-  pencil kernels or generic kernels, for the boxes each family takes;
+* kernel family (``PSATD_*_KERNELS``): plane kernels, pencil kernels or
+  generic kernels, for the boxes each family takes;
+* ``reg_planes``: the register plane kernels for the FP32 boxes whose plane
+  shape has them, or the family those boxes take without them;
 * ``z_tile``: mx columns per z tile of the plane and pencil families (more,
   smaller CTAs for small boxes);
 * ``pencil_rows_kb``: pencil batching -- the shared memory, hence the number
   of x rows, of one pencil CTA;
 * ``z_prefetch``: the register z kernel's L2 prefetch distance;
 * ``pencil_reg_z``: the register z kernel or the shared-memory one for the z
-  pass of pencil boxes whose z length has both.
+  pass of pencil boxes whose z length has both;
+* ``z_one_launch``: those boxes' z pass in one persistent launch for every z
+  length, or one launch per length.
 
 The FFT radix order of every length is fixed at build time (two-pass
 factorisations and prime-factor codelets per length), so it is not searched.
@@ -36,7 +40,9 @@ from . import _abi as A
 
 FAMILIES = ("default", "plane", "pencil", "generic")
 KNOB_VALUES = {
+    "reg_planes": (1, 0),
     "pencil_reg_z": (1, 0),
+    "z_one_launch": (0, 1),
     "z_tile": {32: (8, 4, 2), 64: (4, 2)},
     "pencil_rows_kb": (16, 32, 64, 128),
     "z_prefetch": (0, 64, 152),
@@ -79,17 +85,19 @@ def search(measure: Callable[[str, Dict[str, int]], Tuple[float, Dict[str, int]]
         if best is None or ms < best[2]:
             best = (fam, {}, ms, used)
     fam, tun, ms, used = best
-    for knob in ("pencil_reg_z", "z_tile", "pencil_rows_kb", "z_prefetch"):
-        if knob not in used:
+    for knob in ("reg_planes", "pencil_reg_z", "z_one_launch", "z_tile", "pencil_rows_kb", "z_prefetch"):
+        if knob not in used:                    # not used by the best plan so far
             continue
         values = KNOB_VALUES[knob][precision] if isinstance(KNOB_VALUES[knob], dict) else KNOB_VALUES[knob]
         for v in values:
-            if used.get(knob) == v and knob not in tun:
-                continue                        # the plan's default: already measured
+            if used.get(knob) == v:
+                continue                        # the best plan's own value: already measured
             t = dict(tun, **{knob: v})
-            m, _ = run(fam, t)
+            m, u = run(fam, t)
             if m < ms:
-                tun, ms = t, m
+                tun, ms, used = t, m, u
+    # keep only the knobs the chosen plan uses
+    tun = {k: v for k, v in tun.items() if k in used}
     return fam, tun, ms, trials
 
 

@@ -96,7 +96,9 @@ Err validate(const psatd_plan_desc* d) {
                       (k == PSATD_TUNE_PENCIL_ROWS_KB && v >= 8 && v <= 200) ||
                       (k == PSATD_TUNE_Z_TILE && v >= 1 && v <= fast_tile(d->precision == 64 ? 64 : 32)) ||
                       (k == PSATD_TUNE_HOST_COPY && (v == 0 || v == 1)) ||
-                      (k == PSATD_TUNE_PENCIL_REG_Z && (v == 0 || v == 1));
+                      (k == PSATD_TUNE_PENCIL_REG_Z && (v == 0 || v == 1)) ||
+                      (k == PSATD_TUNE_Z_ONE_LAUNCH && (v == 0 || v == 1)) ||
+                      (k == PSATD_TUNE_REG_PLANES && (v == 0 || v == 1));
       if (!ok) return {PSATD_ERR_INVALID_ARG, fmt("tuning knob %d: value %d unknown or out of range", k, v)};
     }
     if (i == 16 && d->tuning[32] != 0) return {PSATD_ERR_INVALID_ARG, "more than 16 tuning pairs"};
@@ -341,9 +343,16 @@ struct psatd_plan {
     int64_t start, count;     // jobs of the list
   };
   std::vector<PenGroup> grp_rows, grp_rows_int, grp_ycols, grp_ycols_int, grp_z;
-  std::vector<ColJob> zpen_reg;              // pencil boxes whose z pass runs on the register z kernel
+  std::vector<ColJob> zpen_reg;              // boxes of several z lengths whose z pass runs on the register z kernel
   std::vector<PenGroup> grp_zreg;            // ... grouped by z length (code = n2)
-  int pen_reg_z = 1;                         // tuning: register z kernel for pencil boxes where one exists
+  std::vector<PenGroup> grp_pf, grp_pi;      // register plane jobs grouped by plane shape (code: reg_shape_code)
+  int pen_reg_z = 1;                         // tuning: register z kernel for those boxes where one exists
+  bool pen_reg_z_used = false;               // ... and whether the plan has such boxes
+  int reg_planes = 1;                        // tuning: register plane kernels for the boxes whose shape has them
+  bool reg_planes_used = false;              // ... and whether the plan has such boxes
+  int z_one_launch = 0;                      // tuning: those boxes' z pass in one persistent launch (measured
+                                             // slower on the 300-box uneven batch: 7.07 against 5.11 ms)
+  int sms = 0;                               // multiprocessors of the plan's device
   int pen_boxes = 0;
   std::vector<CopyBlk> blocks;
   std::vector<XTile> tiles;                                   // every block (psatd_guard_exchange)
@@ -362,7 +371,6 @@ struct psatd_plan {
   int smem_penx = 0, smem_penxi = 0, smem_penc = 0, smem_penz = 0;
   int buf_pf = 0, buf_pi = 0, rows_pi = 0;     // complex elements per plane buffer
   int grid_pf = 0, grid_pi = 0;                // persistent grid sizes
-  int reg_code = -1;                           // register plane kernels for every fast box
   int reg_z = 0;                               // register z kernel length (0: none)
   int reg_zst = 0;                             // n1 * (n0/2 + 1) of every register-z box, else 0
   int z_prefetch = 64;                         // register z kernel: L2 prefetch distance in CTAs (64: measured
@@ -623,7 +631,7 @@ static bool plane_grid(const GatherSeg* segs, int ns, int n0, int n1, GatherGrid
 static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint32_t flags) {
   P->deferred = false;
   const int nb = (int)P->boxes.size();
-  const bool reg = P->reg_code >= 0 && !P->plane_fwd.empty() && !P->segs.empty() && P->step_tiles.empty() &&
+  const bool reg = !P->grp_pf.empty() && !P->segs.empty() && P->step_tiles.empty() &&
                    P->g_rows.empty() && P->pen_rows.empty() &&
                    std::all_of(box_fast.begin(), box_fast.end(), [](char f) { return f != 0; });
   const bool pen = P->pen_boxes == nb && !P->step_tiles.empty();
@@ -634,22 +642,29 @@ static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint3
   for (int i = 0; i < (int)P->blocks.size(); ++i)
     if (P->blocks[i].src_box >= 0) by_dst[P->blocks[i].dst_box].push_back(i);
   const int v16 = 16 / (int)P->rsize;
-  // every plane of every box, box-major (for register plane plans, the
-  // forward plane jobs themselves)
+  // every plane of every box: for register plane plans in the order of the
+  // forward plane jobs (grouped by plane shape), else box-major
+  std::vector<int2> planes;
+  if (reg) {
+    planes = P->plane_fwd;
+  } else {
+    for (int b = 0; b < nb; ++b)
+      for (int z = 0; z < P->boxes[b].n[2]; ++z) planes.push_back(make_int2(b, z));
+  }
   std::vector<GatherSeg> segs;
   std::vector<int> start{0};
   std::vector<GatherGrid> grids;
   bool all_grid = true;
-  for (int b = 0; b < nb; ++b)
-    for (int z = 0; z < P->boxes[b].n[2]; ++z) {
-      plane_segs(P->boxes, foff, P->blocks, by_dst, b, z, v16, &segs);
-      GatherGrid gg{};
-      if (all_grid)
-        all_grid = plane_grid(segs.data() + start.back(), (int)segs.size() - start.back(), P->boxes[b].n[0],
-                              P->boxes[b].n[1], &gg);
-      grids.push_back(gg);
-      start.push_back((int)segs.size());
-    }
+  for (const int2& pl : planes) {
+    const int b = pl.x, z = pl.y;
+    plane_segs(P->boxes, foff, P->blocks, by_dst, b, z, v16, &segs);
+    GatherGrid gg{};
+    if (all_grid)
+      all_grid = plane_grid(segs.data() + start.back(), (int)segs.size() - start.back(), P->boxes[b].n[0],
+                            P->boxes[b].n[1], &gg);
+    grids.push_back(gg);
+    start.push_back((int)segs.size());
+  }
   if (all_grid) {
     P->ggrid.swap(grids);
   } else if (reg) {
@@ -752,13 +767,14 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   int dev = 0, optin = 0;
   CK(P, cudaGetDevice(&dev));
   CK(P, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  CK(P, cudaDeviceGetAttribute(&P->sms, cudaDevAttrMultiProcessorCount, dev));
   const int tile = P->z_tile > 0 ? std::min(P->z_tile, fast_tile(P->prec)) : fast_tile(P->prec);
-  // Kernel family of each box: plane kernels (x+y per z plane) when the
-  // register-resident plane kernels serve every plane-eligible box (one FP32
-  // shape with register codelets); otherwise the pencil kernels (one launch
-  // per axis and FFT length) take the boxes they accept, which measured
-  // faster than the shared-memory plane kernels on mixed batches; the rest
-  // run on the generic kernels.  PSATD_PENCIL_KERNELS and PSATD_PLANE_KERNELS
+  // Kernel family of each box: plane kernels (x+y per z plane) for the boxes
+  // whose plane shape has register-resident plane kernels (FP32, one launch
+  // per shape); otherwise the pencil kernels (one launch per axis and FFT
+  // length) take the boxes they accept, which measured faster than the
+  // shared-memory plane kernels on mixed batches; the rest run on the
+  // generic kernels.  PSATD_PENCIL_KERNELS and PSATD_PLANE_KERNELS
   // prefer one family outright, PSATD_GENERIC_KERNELS the generic kernels.
   auto plane_ok = [&](const psatd_box& b, const ShapeDev& sh) {
     const int L = b.n[0] / 2, n1 = b.n[1], n2 = b.n[2], hx = L + 1;
@@ -768,18 +784,15 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
            L <= fast_max_x(P->prec) && sm_pf <= optin && sm_pi <= optin &&
            z_fast_smem(P->prec, P->form, n2) <= optin;
   };
-  bool reg_planes = P->prec == 32;
-  {
-    int code = -2;
-    for (size_t bi = 0; bi < P->boxes.size() && reg_planes; ++bi) {
-      const psatd_box& b = P->boxes[bi];
-      const ShapeDev& sh = P->hshapes[P->hboxes[bi].shape];
-      if (!plane_ok(b, sh)) continue;
-      const int c = reg_shape_code(sh.L, b.n[1]);
-      if (c < 0 || (code != -2 && c != code)) reg_planes = false;
-      code = c;
-    }
-  }
+  // register plane shape of a box, or -1
+  auto reg_code_of = [&](const psatd_box& b, const ShapeDev& sh) {
+    if (P->prec != 32 || !plane_ok(b, sh)) return -1;
+    const int c = reg_shape_code(sh.L, b.n[1]);
+    if (c < 0 || reg_fwd_smem(c) > optin || reg_inv_smem(c) > optin) return -1;
+    P->reg_planes_used = true;
+    return P->reg_planes ? c : -1;
+  };
+  std::vector<int> box_reg(P->boxes.size(), -1);
   for (int bi = 0; bi < (int)P->boxes.size(); ++bi) {
     const psatd_box& b = P->boxes[bi];
     const int n0 = b.n[0], n1 = b.n[1], n2 = b.n[2];
@@ -799,8 +812,9 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     const bool pencil_ok = !(d.flags & PSATD_GENERIC_KERNELS) && P->form != kPml && sh.px >= 0 && sh.py >= 0 &&
                            sh.pz >= 0 &&
                            n2 <= pen_z_max(P->prec) && sm_zf <= optin && pen_col_smem(P->prec, n1) <= optin;
+    box_reg[bi] = reg_code_of(b, sh);
     const bool prefer_pencil =
-        (d.flags & PSATD_PENCIL_KERNELS) || (!(d.flags & PSATD_PLANE_KERNELS) && !reg_planes);
+        (d.flags & PSATD_PENCIL_KERNELS) || (!(d.flags & PSATD_PLANE_KERNELS) && box_reg[bi] < 0);
     const bool fast = fast_ok && !(pencil_ok && prefer_pencil);
     const bool pencil = !fast && pencil_ok;
     const bool generic = !fast && !pencil;   // the generic Stockham kernels
@@ -892,13 +906,14 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   // FP32 pencil boxes whose z length has a register z kernel: that kernel
   // does their z pass (z FFT, update, inverse z FFT), its jobs re-tiled to
   // its own tile width; the shared-memory pencil z kernel keeps the rest
+  if (P->prec == 32 && !P->zpen.empty()) P->pen_reg_z_used = true;
   if (P->prec == 32 && P->pen_reg_z && !P->zpen.empty()) {
     const int rt = z_reg_tile_width(P->form);
     std::vector<ColJob> keep;
     std::vector<char> done(P->boxes.size(), 0);
     for (const ColJob& j : P->zpen) {
       const psatd_box& b = P->boxes[j.box];
-      if (!(z_reg_ok(b.n[2]) && z_reg_smem(P->form, b.n[2]) <= optin)) {
+      if (!(z_reg_ok(b.n[2]) && z_reg_smem(P->form, b.n[2]) <= optin && z_reg_multi_smem(P->form) <= optin)) {
         keep.push_back(j);
         continue;
       }
@@ -911,25 +926,50 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     }
     P->zpen.swap(keep);
   }
+  if (P->fast_boxes && P->prec == 32) {
+    // register plane kernels when every fast box has a register shape: the
+    // plane jobs grouped by shape (one launch each), box order kept in a group
+    const bool all_reg = std::all_of(P->plane_fwd.begin(), P->plane_fwd.end(),
+                                     [&](const int2& j) { return box_reg[j.x] >= 0; });
+    if (all_reg) {
+      group(P->plane_fwd, [&](const int2& j) { return box_reg[j.x]; }, P->grp_pf);
+      group(P->plane_inv, [&](const int2& j) { return box_reg[j.x]; }, P->grp_pi);
+    }
+    // one register z length for every fast box: its own launch (below);
+    // several lengths, each with a register z kernel: the z jobs join the
+    // register z list of the pencil boxes
+    int nz = -2;
+    for (const ColJob& j : P->zfast) {
+      const int n2 = P->boxes[j.box].n[2];
+      nz = (nz == -2 || nz == n2) ? n2 : -1;
+      if (nz == -1) break;
+    }
+    const bool zreg_all = std::all_of(P->zfast.begin(), P->zfast.end(), [&](const ColJob& j) {
+      const int n2 = P->boxes[j.box].n[2];
+      return z_reg_ok(n2) && z_reg_smem(P->form, n2) <= optin && z_reg_multi_smem(P->form) <= optin;
+    });
+    if (nz == -1 && all_reg && zreg_all) P->pen_reg_z_used = true;
+    if (nz == -1 && all_reg && zreg_all && P->pen_reg_z) {
+      const int rt = z_reg_tile_width(P->form);
+      int last = -1;
+      for (const ColJob& j : P->zfast) {
+        if (j.box == last) continue;
+        last = j.box;
+        const int L = P->boxes[j.box].n[0] / 2, n1 = P->boxes[j.box].n[1];
+        for (int y = 0; y < n1; ++y)
+          for (int m = 0; m < L; m += rt) P->zpen_reg.push_back({j.box, y, m, std::min(rt, L - m)});
+        for (int y = 0; y < n1; y += rt) P->zpen_reg.push_back({j.box, y, L, -std::min(rt, n1 - y)});
+      }
+      P->zfast.clear();
+    }
+  }
   group(P->zpen_reg, [&](const ColJob& j) { return P->boxes[j.box].n[2]; }, P->grp_zreg);
   group(P->pen_rows, [&](const RowJob& j) { return shape_of_box(j.box).px; }, P->grp_rows);
   group(P->pen_rows_int, [&](const RowJob& j) { return shape_of_box(j.box).px; }, P->grp_rows_int);
   group(P->pen_ycols, [&](const ColJob& j) { return shape_of_box(j.box).py; }, P->grp_ycols);
   group(P->pen_ycols_int, [&](const ColJob& j) { return shape_of_box(j.box).py; }, P->grp_ycols_int);
   group(P->zpen, [&](const ColJob& j) { return shape_of_box(j.box).pz; }, P->grp_z);
-  if (P->fast_boxes && P->prec == 32) {
-    // one register-kernel shape for every fast box, or none
-    int code = -2;
-    for (size_t bi = 0; bi < P->boxes.size() && code != -1; ++bi) {
-      const psatd_box& b = P->boxes[bi];
-      const ShapeDev& sh = P->hshapes[P->hboxes[bi].shape];
-      const bool fastb = std::find_if(P->plane_fwd.begin(), P->plane_fwd.end(),
-                                      [&](const int2& j) { return j.x == (int)bi; }) != P->plane_fwd.end();
-      if (!fastb) continue;
-      const int c = reg_shape_code(sh.L, b.n[1]);
-      code = (code == -2 || code == c) ? c : -1;
-    }
-    if (code >= 0 && reg_fwd_smem(code) <= optin && reg_inv_smem(code) <= optin) P->reg_code = code;
+  if (P->fast_boxes && P->prec == 32 && !P->zfast.empty()) {
     // one register z length for every fast box, or none
     int nz = -2;
     for (const ColJob& j : P->zfast) {
@@ -1470,6 +1510,8 @@ psatd_status psatd_plan_create(const psatd_plan_desc* desc, void* stream, psatd_
       if (k == PSATD_TUNE_Z_TILE) P->z_tile = v;
       if (k == PSATD_TUNE_HOST_COPY) P->host_copy = v;
       if (k == PSATD_TUNE_PENCIL_REG_Z) P->pen_reg_z = v;
+      if (k == PSATD_TUNE_Z_ONE_LAUNCH) P->z_one_launch = v;
+      if (k == PSATD_TUNE_REG_PLANES) P->reg_planes = v;
     }
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -1587,13 +1629,17 @@ static psatd_status forward_xy(psatd_plan* P, const DevPlan& D, const FieldPtrs&
   const int64_t S = P->spec_total;
   int64_t launches = 0;
   // fast boxes: one plane kernel; generic: x rows, y columns; pencil: x rows, y tiles
-  if (!P->plane_fwd.empty() && P->reg_code >= 0) {
-    CK(P, timed(P, 0, st, [&] {
-         return launch_plane_fwd_reg(P->reg_code, D, fp, nf, spec, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
-                                     gather && !P->gseg_start.empty() ? P->d_gseg_start : nullptr, P->d_gsegs,
-                                     gather && !P->ggrid.empty() ? P->d_ggrid : nullptr, fields_out(P->form), st);
-       }));
-    ++launches;
+  if (!P->grp_pf.empty()) {
+    // one launch per register plane shape; the gather tables are indexed by plane_fwd position
+    for (const auto& g : P->grp_pf) {
+      CK(P, timed(P, 0, st, [&] {
+           return launch_plane_fwd_reg(g.code, D, fp, nf, spec, S, P->d_plane_fwd + g.start, g.count,
+                                       gather && !P->gseg_start.empty() ? P->d_gseg_start + g.start : nullptr,
+                                       P->d_gsegs, gather && !P->ggrid.empty() ? P->d_ggrid + g.start : nullptr,
+                                       fields_out(P->form), st);
+         }));
+      ++launches;
+    }
   } else if (!P->plane_fwd.empty()) {
     CK(P, timed(P, 0, st, [&] {
          return launch_plane_fwd(P->prec, D, fp, nf, spec, S, P->d_plane_fwd, (int64_t)P->plane_fwd.size(),
@@ -1667,7 +1713,15 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
     if (r != PSATD_OK) return r;
   }
   // S1 (z) + S2 + S3 (z)
-  for (const auto& g : P->grp_zreg) {
+  if (P->z_one_launch && !P->zpen_reg.empty()) {
+    // every register-z length in one persistent launch, 2 CTAs per SM
+    CK(P, timed(P, 2, st, [&] {
+         return launch_z_reg_multi(P->form, D, P->d_ws, S, P->d_zpen_reg, (int64_t)P->zpen_reg.size(),
+                                   2 * std::max(1, P->sms), P->z_prefetch > 0, NFT, st);
+       }));
+    ++launches;
+  }
+  for (const auto& g : P->z_one_launch ? std::vector<psatd_plan::PenGroup>() : P->grp_zreg) {
     CK(P, timed(P, 2, st, [&] {
          return launch_z_reg(P->form, D, P->d_ws, S, P->d_zpen_reg + g.start, g.count, g.code, 0, NFT, P->z_prefetch,
                              st);
@@ -1702,13 +1756,16 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
     ++launches;
   }
   // S3: inverse y+x, interior cells only
-  if (!P->plane_inv.empty() && P->reg_code >= 0) {
-    CK(P, timed(P, 4, st, [&] {
-         return launch_plane_inv_reg(P->reg_code, D, fp, FOUT, P->d_ws, S, P->d_plane_inv,
-                                     (int64_t)P->plane_inv.size(),
-                                     P->segs.empty() || !guards ? nullptr : P->d_seg_start, P->d_segs, st);
-       }));
-    ++launches;
+  if (!P->grp_pi.empty()) {
+    // one launch per register plane shape; the guard segments are indexed by plane_inv position
+    for (const auto& g : P->grp_pi) {
+      CK(P, timed(P, 4, st, [&] {
+           return launch_plane_inv_reg(g.code, D, fp, FOUT, P->d_ws, S, P->d_plane_inv + g.start, g.count,
+                                       P->segs.empty() || !guards ? nullptr : P->d_seg_start + g.start, P->d_segs,
+                                       st);
+         }));
+      ++launches;
+    }
   } else if (!P->plane_inv.empty()) {
     CK(P, timed(P, 4, st, [&] {
          return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv, (int64_t)P->plane_inv.size(),
@@ -2065,9 +2122,14 @@ psatd_status psatd_plan_tune(psatd_plan* P, int32_t knob, int32_t value) {
       if (value != 0 && value != 1) return fail(P, PSATD_ERR_INVALID_ARG, "host copy mode is 0 or 1");
       P->host_copy = value;
       return PSATD_OK;   // not part of any captured graph
+    case PSATD_TUNE_Z_ONE_LAUNCH:
+      if (value != 0 && value != 1) return fail(P, PSATD_ERR_INVALID_ARG, "one-launch z pass is 0 or 1");
+      P->z_one_launch = value;
+      break;
     case PSATD_TUNE_PENCIL_ROWS_KB:
     case PSATD_TUNE_Z_TILE:
     case PSATD_TUNE_PENCIL_REG_Z:
+    case PSATD_TUNE_REG_PLANES:
       return fail(P, PSATD_ERR_INVALID_ARG, "this knob is set at plan creation only");
     default:
       return fail(P, PSATD_ERR_INVALID_ARG, "unknown tuning knob");
@@ -2091,7 +2153,11 @@ int32_t psatd_plan_tuning(const psatd_plan* P, int32_t knob) {
     case PSATD_TUNE_HOST_COPY:
       return P->host_copy;
     case PSATD_TUNE_PENCIL_REG_Z:
-      return P->pen_boxes && P->prec == 32 ? P->pen_reg_z : -1;
+      return P->pen_reg_z_used ? P->pen_reg_z : -1;
+    case PSATD_TUNE_REG_PLANES:
+      return P->reg_planes_used ? P->reg_planes : -1;
+    case PSATD_TUNE_Z_ONE_LAUNCH:
+      return P->zpen_reg.empty() ? -1 : P->z_one_launch;
     case PSATD_TUNE_Z_TILE:
       return (P->pen_boxes || (P->fast_boxes && !P->reg_z))
                  ? (P->z_tile > 0 ? std::min(P->z_tile, fast_tile(P->prec)) : fast_tile(P->prec))

@@ -264,6 +264,22 @@ cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f,
                                  int64_t sstride, const int2* jobs, int64_t nplanes, const int* seg_start,
                                  const GuardSeg* segs, cudaStream_t st);
 cudaError_t configure_reg_kernels(int smem_bytes);
+// the plane shapes are instantiated in three translation units
+// (reg_planes_<part>.cu); each exports its launchers in namespace plane_part<part>
+#define PSATD_DECLARE_PLANE_PART(NS)                                                                       \
+  namespace NS {                                                                                           \
+  cudaError_t launch_fwd(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,  \
+                         const int2* jobs, int64_t nplanes, const int* gstart, const GatherSeg* gsegs,      \
+                         const GatherGrid* ggrid, int ngather, cudaStream_t st);                           \
+  cudaError_t launch_inv(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,  \
+                         const int2* jobs, int64_t nplanes, const int* seg_start, const GuardSeg* segs,     \
+                         cudaStream_t st);                                                                 \
+  cudaError_t configure(int smem_bytes);                                                                   \
+  }
+PSATD_DECLARE_PLANE_PART(plane_part0)
+PSATD_DECLARE_PLANE_PART(plane_part1)
+PSATD_DECLARE_PLANE_PART(plane_part2)
+#undef PSATD_DECLARE_PLANE_PART
 // register z kernel (FP32, tiles of z_reg_tile_width(form) columns) for z length n2
 int z_reg_ok(int n2);
 int z_reg_smem(int form, int n2);
@@ -273,6 +289,12 @@ int z_reg_tile_width(int form);
 // launched pf_dist blocks after it
 cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
                          int64_t njobs, int n2, int zst, int nft, int pf_dist, cudaStream_t st);
+// The register z pass of boxes of several z lengths (every one z_reg_ok) in
+// one persistent launch of at most `grid` CTAs; prefetch != 0: every CTA
+// prefetches into L2 the tile of its next job.
+cudaError_t launch_z_reg_multi(int form, const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs,
+                               int64_t njobs, int grid, int prefetch, int nft, cudaStream_t st);
+int z_reg_multi_smem(int form);
 
 // ---- pencil kernels (pencil_kernels.cu): boxes of two-pass lengths too large
 // for the plane kernels; the z pass takes fast_tile(prec) mx columns per tile

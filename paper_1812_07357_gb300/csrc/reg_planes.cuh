@@ -1,0 +1,381 @@
+// Register-resident plane kernels (FP32) for boxes whose x half-length L and
+// y length NY have register codelets (L, NY/2 in the codelet set, L <= 63,
+// NY <= 128): every 1D FFT of a plane is done inside registers, so a plane
+// costs two block barriers.
+//
+//   k_plane_fwd_reg  the plane is copied in whole, or, with the deferred guard
+//                    exchange, gathered rectangle by rectangle from the cells
+//                    that own it;
+//                    x: one thread per row: the packed length-L complex FFT
+//                    (z[m] = x[2m] + i x[2m+1]) and the R2C split, both in
+//                    registers; y: two threads per column, each a length-NY/2
+//                    FFT of the even / odd rows, joined by one radix-2 step
+//                    whose operands cross between the pair with shuffles.
+//   k_plane_inv_reg  the mirror image, keeping interior rows and cells only,
+//                    and writing the guard cells the plane feeds (fused S4).
+//
+// The shapes are instantiated in three translation units (reg_planes_<part>.cu,
+// PSATD_PLANE_PART = part), each taking its share of PSATD_REG_SHAPES.
+#pragma once
+#include "reg_common.cuh"
+
+namespace psatd {
+
+// Register plane shapes X(code, L, NY, part): x half-lengths 24, 30, 40, 48, 60
+// by y lengths 48, 60, 80, 96, 120 (code 0: the 96 x 96 plane of 96^3 boxes)
+#define PSATD_REG_SHAPES(X)                                                                        \
+  X(0, 48, 96, 0) X(1, 24, 48, 0) X(2, 24, 60, 0) X(3, 24, 80, 0) X(4, 24, 96, 0) X(5, 24, 120, 0) \
+  X(6, 30, 48, 1) X(7, 30, 60, 1) X(8, 30, 80, 1) X(9, 30, 96, 1) X(10, 30, 120, 1)               \
+  X(11, 40, 48, 1) X(12, 40, 60, 1) X(13, 40, 80, 1) X(14, 40, 96, 1) X(15, 40, 120, 1)           \
+  X(16, 48, 48, 2) X(17, 48, 60, 2) X(18, 48, 80, 2) X(19, 48, 120, 2)                            \
+  X(20, 60, 48, 2) X(21, 60, 60, 2) X(22, 60, 80, 2) X(23, 60, 96, 2) X(24, 60, 120, 2)
+
+namespace {
+
+// resident CTAs per SM the register budget is cut for: 4 up to the 96 x 96
+// plane (128 registers per thread), 3 above (168)
+template <int L, int NY>
+constexpr int reg_plane_min_blocks() {
+  return (L <= 48 && NY <= 96) ? 4 : 3;
+}
+
+// ---------------------------------------------------------------------------
+template <int L, int NY>
+__global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>())
+    k_plane_fwd_reg(DevPlan P, FieldPtrs F, float2* spec, int64_t sstride, const int2* __restrict__ jobs,
+                    const int* __restrict__ gstart, const GatherSeg* __restrict__ gsegs,
+                    const GatherGrid* __restrict__ ggrid, int ngather) {
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0);
+  static_assert(NY <= kRegThreads && 2 * HX <= kRegThreads, "one thread per row / per half column");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* buf = reinterpret_cast<float*>(smem_raw);
+  const int2 J = jobs[blockIdx.x];
+  const int f = blockIdx.y;
+  const BoxDev bx = P.boxes[J.x];
+  constexpr int UPR = N0 / 4;
+  if (ggrid && f < ngather) {
+    // deferred exchange, plane of at most 3 x 3 rectangles: thread t copies
+    // the 16-byte column t % UPR of the rows t / UPR + k * RG
+    constexpr int RG = kRegThreads / UPR;
+    __shared__ GatherGrid gg;
+    static_assert(sizeof(GatherGrid) / 4 <= kRegThreads, "one word per thread");
+    if (threadIdx.x < sizeof(GatherGrid) / 4)
+      reinterpret_cast<int*>(&gg)[threadIdx.x] = reinterpret_cast<const int*>(ggrid + blockIdx.x)[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < RG * UPR) {
+      const float* fb = reinterpret_cast<const float*>(F.p[f]);
+      const int c = threadIdx.x % UPR, rg = threadIdx.x / UPR, x = 4 * c;
+      const int ix = (x >= gg.x1) + (x >= gg.x2);
+      const int xo = x - (ix == 0 ? 0 : ix == 1 ? gg.x1 : gg.x2);
+#pragma unroll
+      for (int iy = 0; iy < 3; ++iy) {   // row bands [ylo, yhi)
+        const int ylo = iy == 0 ? 0 : iy == 1 ? gg.y1 : gg.y2;
+        const int yhi = iy == 0 ? gg.y1 : iy == 1 ? gg.y2 : NY;
+        int r = ylo + (rg - ylo % RG + RG) % RG;   // first row >= ylo with r % RG == rg
+        const int pitch = gg.pitch[3 * iy + ix];
+        const float* src = fb + gg.base[3 * iy + ix] + (int64_t)(r - ylo) * pitch + xo;
+        const int64_t sstep = (int64_t)RG * pitch;
+        for (float* dst = buf + r * PF + x; r < yhi; r += RG, src += sstep, dst += RG * PF) cp16(dst, src);
+      }
+    }
+  } else if (gstart && f < ngather) {
+    // deferred exchange: every rectangle of the plane from the cells that own
+    // it (a neighbour's interior for the guard cells); the plane's rectangle
+    // list is staged in shared memory, then all threads copy one rectangle
+    // after the other
+    __shared__ GatherSeg tab[kGatherTab];
+    const float* fb = reinterpret_cast<const float*>(F.p[f]);
+    const int s0 = gstart[blockIdx.x], ns = gstart[blockIdx.x + 1] - s0;
+    if (threadIdx.x < kGatherTab && threadIdx.x < ns) tab[threadIdx.x] = gsegs[s0 + threadIdx.x];
+    __syncthreads();
+    for (int i = 0; i < ns; ++i) {
+      const GatherSeg gs = i < kGatherTab ? tab[i] : gsegs[s0 + i];
+      const float* src = fb + gs.src_off;
+      float* dst = buf + gs.dy * PF + gs.dx;
+      if (gs.vec) {
+        const int upr = gs.nx >> 2;
+        const unsigned m = magic(upr);
+        for (int u = threadIdx.x; u < gs.ny * upr; u += kRegThreads) {
+          const int r = fdiv(u, m), c = 4 * (u - r * upr);
+          cp16(dst + r * PF + c, src + (int64_t)r * gs.spitch + c);
+        }
+      } else {
+        const unsigned m = magic(gs.nx);
+        for (int u = threadIdx.x; u < gs.ny * gs.nx; u += kRegThreads) {
+          const int r = fdiv(u, m), c = u - r * gs.nx;
+          cp4(dst + r * PF + c, src + (int64_t)r * gs.spitch + c);
+        }
+      }
+    }
+  } else {
+    const float* g = reinterpret_cast<const float*>(F.p[f]) + bx.foff + (int64_t)J.y * NY * N0;
+    for (int u = threadIdx.x; u < NY * UPR; u += kRegThreads) {
+      const int r = u / UPR, x = u - r * UPR;
+      cp16(buf + r * PF + 4 * x, g + 4 * u);
+    }
+  }
+  cp_commit_wait_all();
+  __syncthreads();
+  // x: row r -> half spectrum X[0..L] written back into the same row
+  if (threadIdx.x < NY) {
+    float* row = buf + threadIdx.x * PF;
+    float2 z[L];
+#pragma unroll
+    for (int j = 0; j < L / 2; ++j) {
+      const float4 q = reinterpret_cast<const float4*>(row)[j];
+      z[2 * j] = make_float2(q.x, q.y);
+      z[2 * j + 1] = make_float2(q.z, q.w);
+    }
+    Dft<float, L, -1>::run(z);
+    float2* xr = reinterpret_cast<float2*>(row);
+    // X[k] = (Z[k] + conj Z[L-k])/2 - i w^k (Z[k] - conj Z[L-k])/2, w = exp(-2 pi i / N0)
+    static_for<0, L / 2 + 1>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const float2 a = z[k % L], b = z[(L - k) % L];
+      const float2 A = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+      const float2 Bv = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
+      if constexpr (k == 0) {
+        xr[0] = make_float2(A.x + Bv.x, A.y + Bv.y);
+        xr[L] = make_float2(A.x - Bv.x, A.y - Bv.y);
+      } else {
+        xr[k] = A + cmul(root<N0, k, -1>(), Bv);
+        if constexpr (2 * k != L) xr[L - k] = conjg(A) + cmul(root<N0, L - k, -1>(), conjg(Bv));
+      }
+    });
+  }
+  __syncthreads();
+  // y: thread pair per column c; threads past the last column repeat it
+  {
+    const int t = threadIdx.x;
+    const int half = pair_half(t);
+    const int c = min(pair_index(t), HX - 1);
+    const bool live = pair_index(t) < HX;
+    const float2* xs = reinterpret_cast<const float2*>(buf);
+    float2 v[NY / 2];
+#pragma unroll
+    for (int m = 0; m < NY / 2; ++m) v[m] = xs[(2 * m + half) * (PF / 2) + c];
+    Dft<float, NY / 2, -1>::run(v);
+    float2* out = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX + c;
+    pair_join<NY, -1>(v, half, [&](int y, float2 val) {
+      if (live) out[y * HX] = val;
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename V>
+__device__ __forceinline__ void copy_rect_w(const float* src, int spitch, float* dst, int64_t dpitch, int ny,
+                                            int nx, int tid, int nthreads) {
+  constexpr int W = sizeof(V) / 4;
+  const int upr = nx / W;
+  const unsigned m = magic(upr);
+  for (int u = tid; u < ny * upr; u += nthreads) {
+    const int r = fdiv(u, m), c = (u - r * upr) * W;
+    *reinterpret_cast<V*>(dst + r * dpitch + c) = *reinterpret_cast<const V*>(src + r * spitch + c);
+  }
+}
+
+template <int L, int NY>
+__global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>()) k_plane_inv_reg(DevPlan P, FieldPtrs F, const float2* spec,
+                                                                  int64_t sstride, const int2* __restrict__ jobs,
+                                                                  const int* __restrict__ seg_start,
+                                                                  const GuardSeg* __restrict__ segs) {
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0), Q = NY / 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // one buffer: first the NY x HX spectrum plane (pitch HX), then, once it is
+  // consumed, the interior rows (pitch PF floats): X values, then real cells
+  float2* sp = reinterpret_cast<float2*>(smem_raw);
+  float* rows = reinterpret_cast<float*>(smem_raw);
+  const int2 J = jobs[blockIdx.x];
+  const int f = blockIdx.y;
+  const BoxDev bx = P.boxes[J.x];
+  const int ylo = bx.ng_lo[1], yhi = NY - bx.ng_hi[1], ni = yhi - ylo;
+  const int xlo = bx.ng_lo[0], nxi = N0 - bx.ng_lo[0] - bx.ng_hi[0];
+  const float2* g = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX;
+  constexpr int UNITS = NY * HX / 2;   // 16-byte units of the contiguous plane
+  for (int u = threadIdx.x; u < UNITS; u += kRegThreads) cp16(sp + 2 * u, g + 2 * u);
+  cp_commit_wait_all();
+  __syncthreads();
+  // y: thread pair per column, inverse; outputs kept in v until the plane is consumed
+  const int t = threadIdx.x;
+  const int half = pair_half(t);
+  const int c = min(pair_index(t), HX - 1);
+  const bool live = pair_index(t) < HX;
+  float2 v[NY / 2];
+#pragma unroll
+  for (int m = 0; m < NY / 2; ++m) v[m] = sp[(2 * m + half) * HX + c];
+  Dft<float, NY / 2, 1>::run(v);
+  pair_join_inplace<NY, 1>(v, half);
+  __syncthreads();
+  if (live) {
+    float2* rs = reinterpret_cast<float2*>(rows);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int y1 = i + half * Q, y2 = y1 + NY / 2;
+      if (y1 >= ylo && y1 < yhi) rs[(y1 - ylo) * (PF / 2) + c] = v[i];
+      if (y2 >= ylo && y2 < yhi) rs[(y2 - ylo) * (PF / 2) + c] = v[Q + i];
+    }
+  }
+  __syncthreads();
+  // x: thread per interior row: C2R merge, inverse packed FFT, interior cells
+  // written back into the thread's own row
+  const float scale = __frcp_rn((float)(N0 * NY * bx.n[2]));   // exact integer < 2^24
+  const bool vec_rows = (nxi % 4 == 0) && (xlo % 4 == 0);
+  if (threadIdx.x < ni) {
+    float* row = rows + threadIdx.x * PF;
+    const float2* xr = reinterpret_cast<const float2*>(row);
+    float2 z[L];
+    // Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), w = exp(-2 pi i / N0)
+    static_for<0, L / 2 + 1>([&](auto kc) {
+      constexpr int k = decltype(kc)::value;
+      const float2 a = xr[k], b = xr[L - k];
+      z[k] = (a + conjg(b)) + times_i(cmul(a - conjg(b), root<N0, k, 1>()));
+      if constexpr (k != 0 && 2 * k != L)
+        z[L - k] = (b + conjg(a)) + times_i(cmul(b - conjg(a), root<N0, L - k, 1>()));
+    });
+    Dft<float, L, 1>::run(z);
+    float* o = row - xlo;
+    if (vec_rows) {
+#pragma unroll
+      for (int m = 0; m < L; m += 2) {
+        const int x = 2 * m;
+        if (x >= xlo && x < xlo + nxi)
+          *reinterpret_cast<float4*>(o + x) =
+              make_float4(scale * z[m].x, scale * z[m].y, scale * z[m + 1].x, scale * z[m + 1].y);
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < L; ++m) {
+        const int x = 2 * m;
+        if (x >= xlo && x < xlo + nxi) o[x] = scale * z[m].x;
+        if (x + 1 >= xlo && x + 1 < xlo + nxi) o[x + 1] = scale * z[m].y;
+      }
+    }
+  }
+  __syncthreads();
+  // interior cells to this box, then the guard cells this plane feeds
+  float* fbase = reinterpret_cast<float*>(F.p[f]);
+  float* own = fbase + bx.foff + ((int64_t)J.y * NY + ylo) * N0 + xlo;
+  if (vec_rows)
+    copy_rect_w<float4>(rows, PF, own, N0, ni, nxi, threadIdx.x, kRegThreads);
+  else
+    copy_rect_w<float>(rows, PF, own, N0, ni, nxi, threadIdx.x, kRegThreads);
+  if (seg_start) {
+    const int p = blockIdx.x;
+    const int s1 = seg_start[p + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kRegThreads >> 5;
+    for (int si = seg_start[p] + warp; si < s1; si += nw) {
+      const GuardSeg gs = segs[si];
+      const BoxDev db = P.boxes[gs.dst_box];
+      float* dst = fbase + db.foff + ((int64_t)gs.dst_z * db.n[1] + gs.dy) * db.n[0] + gs.dx;
+      const float* src = rows + (gs.sy - ylo) * PF + (gs.sx - xlo);
+      if (gs.vec > 1 && vec_rows)
+        copy_rect_w<float4>(src, PF, dst, db.n[0], gs.ny, gs.nx, lane, 32);
+      else
+        copy_rect_w<float>(src, PF, dst, db.n[0], gs.ny, gs.nx, lane, 32);
+    }
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// The launchers of one part (PSATD_PLANE_PART): every shape of the part, by code.
+#ifdef PSATD_PLANE_PART
+#define PSATD_PART_CAT2(a, b) a##b
+#define PSATD_PART_CAT(a, b) PSATD_PART_CAT2(a, b)
+namespace {
+
+// bytes of dynamic shared memory: the real plane with its row pitch (forward);
+// the spectrum plane or the interior rows, whichever is larger (inverse)
+template <int L, int NY>
+constexpr int plane_fwd_bytes() {
+  return NY * row_pitch(2 * L) * 4;
+}
+template <int L, int NY>
+constexpr int plane_inv_bytes() {
+  return NY * (L + 1) * 8 > NY * row_pitch(2 * L) * 4 ? NY * (L + 1) * 8 : NY * row_pitch(2 * L) * 4;
+}
+
+template <int CODE, int L, int NY, int PART>
+bool plane_fwd_shape(int code, dim3 grid, const DevPlan& P, const FieldPtrs& f, void* spec, int64_t sstride,
+                     const int2* jobs, const int* gstart, const GatherSeg* gsegs, const GatherGrid* ggrid,
+                     int ngather, cudaStream_t st) {
+  if constexpr (PART == PSATD_PLANE_PART) {
+    if (code != CODE) return false;
+    k_plane_fwd_reg<L, NY><<<grid, kRegThreads, plane_fwd_bytes<L, NY>(), st>>>(P, f, (float2*)spec, sstride, jobs,
+                                                                               gstart, gsegs, ggrid, ngather);
+    return true;
+  } else {
+    return false;
+  }
+}
+
+template <int CODE, int L, int NY, int PART>
+bool plane_inv_shape(int code, dim3 grid, const DevPlan& P, const FieldPtrs& f, void* spec, int64_t sstride,
+                     const int2* jobs, const int* seg_start, const GuardSeg* segs, cudaStream_t st) {
+  if constexpr (PART == PSATD_PLANE_PART) {
+    if (code != CODE) return false;
+    k_plane_inv_reg<L, NY><<<grid, kRegThreads, plane_inv_bytes<L, NY>(), st>>>(P, f, (const float2*)spec, sstride,
+                                                                               jobs, seg_start, segs);
+    return true;
+  } else {
+    return false;
+  }
+}
+
+template <int L, int NY, int PART>
+void plane_configure_shape(int smem, cudaError_t* e) {
+  if constexpr (PART == PSATD_PLANE_PART) {
+    if (plane_fwd_bytes<L, NY>() > smem || plane_inv_bytes<L, NY>() > smem) return;
+    cudaError_t r = cudaFuncSetAttribute(k_plane_fwd_reg<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         plane_fwd_bytes<L, NY>());
+    if (r != cudaSuccess) *e = r;
+    r = cudaFuncSetAttribute(k_plane_inv_reg<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             plane_inv_bytes<L, NY>());
+    if (r != cudaSuccess) *e = r;
+  }
+}
+
+}  // namespace
+
+namespace PSATD_PART_CAT(plane_part, PSATD_PLANE_PART) {
+
+cudaError_t launch_fwd(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,
+                       const int2* jobs, int64_t nplanes, const int* gstart, const GatherSeg* gsegs,
+                       const GatherGrid* ggrid, int ngather, cudaStream_t st) {
+  if (nplanes <= 0 || nf <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)nplanes, nf);
+#define PSATD_RL(c, LV, NYV, PART) \
+  ||plane_fwd_shape<c, LV, NYV, PART>(code, grid, P, f, spec, sstride, jobs, gstart, gsegs, ggrid, ngather, st)
+  const bool hit = false PSATD_REG_SHAPES(PSATD_RL);
+#undef PSATD_RL
+  return hit ? cudaGetLastError() : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_inv(int code, const DevPlan& P, const FieldPtrs& f, int nf, void* spec, int64_t sstride,
+                       const int2* jobs, int64_t nplanes, const int* seg_start, const GuardSeg* segs,
+                       cudaStream_t st) {
+  if (nplanes <= 0 || nf <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)nplanes, nf);
+#define PSATD_RL(c, LV, NYV, PART) \
+  ||plane_inv_shape<c, LV, NYV, PART>(code, grid, P, f, spec, sstride, jobs, seg_start, segs, st)
+  const bool hit = false PSATD_REG_SHAPES(PSATD_RL);
+#undef PSATD_RL
+  return hit ? cudaGetLastError() : cudaErrorInvalidValue;
+}
+
+cudaError_t configure(int smem) {
+  cudaError_t e = cudaSuccess;
+#define PSATD_RC(c, LV, NYV, PART) plane_configure_shape<LV, NYV, PART>(smem, &e);
+  PSATD_REG_SHAPES(PSATD_RC)
+#undef PSATD_RC
+  return e;
+}
+
+}  // namespace plane_part<PSATD_PLANE_PART>
+#undef PSATD_PART_CAT
+#undef PSATD_PART_CAT2
+#endif  // PSATD_PLANE_PART
+
+}  // namespace psatd

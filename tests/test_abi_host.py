@@ -258,3 +258,25 @@ def test_validate_rejects_an_empty_plan(lib):
     d.num_boxes = 0
     st, msg = A.psatd_plan_validate(d)
     assert st == A.PSATD_ERR_INVALID_ARG and "box" in msg
+
+
+def test_header_constants_match_the_binding():
+    """Every PSATD_* integer constant of include/psatd.h that the ctypes
+    binding names has the header's value; every tuning knob is in TUNE_KNOBS."""
+    txt = open(os.path.join(ROOT, "include", "psatd.h")).read()
+    consts = {k: int(v) for k, v in re.findall(r"^#define\s+(PSATD_\w+)\s+(-?\d+)\s*(?:/\*.*)?$", txt, re.M)}
+    named = [k for k in consts if hasattr(A, k)]
+    assert len(named) >= 10
+    for k in named:
+        assert getattr(A, k) == consts[k], k
+    knobs = {v for k, v in consts.items() if k.startswith("PSATD_TUNE_")}
+    assert knobs == set(A.TUNE_KNOBS.values())
+
+
+@pytest.mark.parametrize("knob,value", [("reg_planes", 2), ("pencil_reg_z", -1), ("z_one_launch", 3),
+                                        ("z_tile", 0), ("pencil_rows_kb", 4)])
+def test_validate_rejects_bad_tuning(lib, knob, value):
+    lay = I.global_layout((48, 48, 48), 4)
+    d = make_desc(lay, (1.0,) * 3, 0.5, tuning={knob: value})
+    st, msg = A.psatd_plan_validate(d)
+    assert st == A.PSATD_ERR_INVALID_ARG and "tuning knob" in msg, (st, msg)

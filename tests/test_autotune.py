@@ -78,3 +78,25 @@ def test_tuned_plan_matches_the_oracle(tmp_path):
     plan.close()
     ref = O.push(lay, fields, src, 4, (1.0,) * 3, 0.9, form="rho")
     assert_fields(lay, got, ref, O.COMPS + ("rho",), 32, what=f"tuned plan {c['family']} {c['tuning']}")
+
+
+def test_search_skips_and_drops_knobs_the_chosen_plan_does_not_use(tmp_path):
+    """A knob that the best plan no longer uses (z_one_launch once
+    pencil_reg_z = 0 won) is neither searched nor kept in the result."""
+    calls = []
+
+    def measure(family, tuning):
+        calls.append((family, dict(tuning)))
+        base = {"default": 5.0, "plane": 7.0, "pencil": 6.0, "generic": 9.0}[family]
+        reg_z = tuning.get("pencil_reg_z", 1)
+        ms = base - (0.5 if reg_z == 0 else 0.0)
+        used = {"pencil_reg_z": reg_z}
+        if reg_z:
+            used["z_one_launch"] = tuning.get("z_one_launch", 0)
+        return ms, used
+
+    lay = I.independent_layout(seed=3, nboxes=5, sizes=(48, 60), ngs=(4,), min_interior=16)
+    c = T.tune(lay, (1.0,) * 3, 0.9, cache=str(tmp_path / "t.json"), measure=measure, device="test")
+    assert (c["family"], c["tuning"], c["ms_per_step"]) == ("default", {"pencil_reg_z": 0}, 4.5)
+    assert len(calls) == 4 + 1
+    assert not any("z_one_launch" in t for _, t in calls)

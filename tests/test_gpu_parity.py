@@ -240,11 +240,15 @@ def test_errors_are_reported_not_raised_on_device():
 
 def _fast_plan_check(lay, fields, src, nsteps, h, dt, prec, form, expect_fast):
     """The plane kernels (requested explicitly: without the flag, boxes whose
-    shape has no register plane kernels run on the pencil kernels)."""
-    plan = Plan(lay, h, dt, precision=prec, sources=form, plane=True)
-    assert plan.fast_boxes == expect_fast, (plan.fast_boxes, expect_fast)
-    plan.close()
-    return check_push(lay, fields, src, nsteps, h, dt, prec, form, plane=True)
+    shape has no register plane kernels run on the pencil kernels); in FP32
+    both the register plane kernels, where the shape has them, and the
+    shared-memory plane kernels (reg_planes knob 0)."""
+    for tuning in ((None, {"reg_planes": 0}) if prec == 32 else (None,)):
+        plan = Plan(lay, h, dt, precision=prec, sources=form, plane=True, tuning=tuning)
+        assert plan.fast_boxes == expect_fast, (plan.fast_boxes, expect_fast)
+        plan.close()
+        got = check_push(lay, fields, src, nsteps, h, dt, prec, form, plane=True, tuning=tuning)
+    return got
 
 
 @pytest.mark.parametrize("prec", [64, 32])

@@ -76,8 +76,8 @@ def _check(lay, prec, form, nsteps=3, **plan_kw):
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("form", ["rho", "J"])
 def test_jconst_pencil_local(prec, form):
-    lay = I.local_layout((64, 64, 64), (2, 2, 2), 8, 16)          # 48^3 boxes: pencil by default
-    assert _check(lay, prec, form) == (0, 8)
+    lay = I.local_layout((64, 64, 64), (2, 2, 2), 8, 16)          # 48^3 boxes on the pencil kernels
+    assert _check(lay, prec, form, pencil=True) == (0, 8)
 
 
 @pytest.mark.parametrize("form", ["rho", "J"])

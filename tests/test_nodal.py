@@ -51,7 +51,7 @@ def _check(lay, prec, form, paths, nsteps=3, **kw):
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("form", ["vacuum", "rho"])
 def test_nodal_pencil(prec, form):
-    _check(I.local_layout((64, 64, 64), (2, 2, 2), 8, 16), prec, form, (0, 8))
+    _check(I.local_layout((64, 64, 64), (2, 2, 2), 8, 16), prec, form, (0, 8), pencil=True)
 
 
 @pytest.mark.parametrize("form", ["vacuum", "J"])

@@ -120,9 +120,9 @@ def test_mixed_plane_pencil_generic_boxes():
 
 @pytest.mark.parametrize("prec", [64, 32])
 def test_pencil_flag_on_plane_boxes(prec):
-    """48^3 local boxes (no register plane kernels for this shape) on the
-    pencil kernels (PSATD_PENCIL_KERNELS, also the default here) and on the
-    plane kernels (PSATD_PLANE_KERNELS): against the oracle and each other."""
+    """48^3 local boxes on the pencil kernels (PSATD_PENCIL_KERNELS) and on
+    the plane kernels (PSATD_PLANE_KERNELS: the register plane kernels in
+    FP32): against the oracle and each other."""
     from paper_1812_07357_gb300.solver import Plan
     lay = I.local_layout((64, 64, 64), (2, 2, 2), 8, 16)
     f = I.laser_fields((64, 64, 64), wavelength=8.0, waist=8.0, duration=5.0)
@@ -144,14 +144,20 @@ def test_pencil_flag_on_plane_boxes(prec):
 
 
 def test_default_family_choice():
-    """Without a flag: the register plane shape (n0/2 = 48, n1 = 96) takes the
-    plane kernels; other plane-eligible shapes take the pencil kernels."""
+    """Without a flag: FP32 boxes whose plane shape has register plane kernels
+    (n0/2 in 24 .. 60, n1 in 48 .. 120) take the plane kernels, unless the
+    reg_planes knob is 0; FP64 boxes and other plane-eligible shapes (64^3:
+    n0/2 = 32) take the pencil kernels."""
     from paper_1812_07357_gb300.solver import Plan
     reg = I.local_layout((128, 64, 32), (2, 1, 2), (16, 16, 4), 16)        # 96 x 96 x 24 boxes
-    other = I.local_layout((64, 64, 64), (2, 2, 2), 8, 16)                 # 48^3 boxes
-    for lay, prec, want in ((reg, 32, (4, 0)), (reg, 64, (0, 4)), (other, 32, (0, 8))):
-        plan = Plan(lay, (1.0,) * 3, 0.9, precision=prec, sources="vacuum")
-        assert (plan.fast_boxes, plan.pencil_boxes) == want, (lay.boxes[0].n, prec)
+    reg48 = I.local_layout((64, 64, 64), (2, 2, 2), 8, 16)                 # 48^3 boxes
+    other = I.local_layout((96, 96, 96), (2, 2, 2), 8, 16)                 # 64^3 boxes
+    for lay, prec, tun, want in ((reg, 32, None, (4, 0)), (reg, 64, None, (0, 4)), (reg48, 32, None, (8, 0)),
+                                 (reg48, 32, {"reg_planes": 0}, (0, 8)), (other, 32, None, (0, 8))):
+        plan = Plan(lay, (1.0,) * 3, 0.9, precision=prec, sources="vacuum", tuning=tun)
+        assert (plan.fast_boxes, plan.pencil_boxes) == want, (lay.boxes[0].n, prec, tun)
+        assert plan.tuning().get("reg_planes", -1) == (-1 if lay is other or prec == 64 else
+                                                      (tun or {}).get("reg_planes", 1))
         plan.close()
 
 
@@ -189,45 +195,50 @@ def test_pencil_local_192_boxes_and_hybrid_384_groups():
            (0, 4))
 
 
-@pytest.mark.parametrize("form", ["vacuum", "rho"])
+@pytest.mark.parametrize("form", ["vacuum", "J", "rho"])
 def test_pencil_boxes_z_pass_on_register_kernel_and_shared_memory_kernel(form):
     """FP32 pencil boxes with z lengths 48, 60, 80, 96, 120 (the uneven
-    batch's): their z pass runs on the register z kernel (default) or on the
-    shared-memory pencil z kernel (tuning knob); both against the oracle, and
-    each other."""
+    batch's): their z pass runs on the register z kernel, one launch per
+    length (default) or every length in one persistent launch, or on the
+    shared-memory pencil z kernel (tuning knobs); each against the oracle, and
+    against each other."""
     from paper_1812_07357_gb300.solver import Plan
     sizes = [(160, 24, 48), (48, 160, 60), (60, 48, 80), (80, 60, 96), (48, 48, 120)]
     boxes = [I.Box(n, (4, 4, 4), (4, 4, 4), (0, 0, 0), p) for n, p in zip(sizes, (8, 16, 32, 0, 16))]
     lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
     rng = np.random.default_rng(28)
-    if form == "rho":
+    if form != "vacuum":
         js = {k: [] for k in ("Jx", "Jy", "Jz")}
         for b in lay.boxes:
             j = I.band_limited_current(b.interior, rng)
             for k in js:
                 js[k].append(j[k])
         src = {k: I.round_to(I.scatter_self(v, lay), np.float32) for k, v in js.items()}
-        src["rho"] = I.zeros(lay)
-        fields = {k: I.zeros(lay) for k in O.COMPS}
+        if form == "rho":
+            src["rho"] = I.zeros(lay)
     else:
         src = {}
-        fields = {k: I.round_to(O.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes]), np.float32)
-                  for k in O.COMPS}
+    fields = {k: I.round_to(O.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes]), np.float32)
+              for k in O.COMPS}
     comps = O.COMPS + (("rho",) if form == "rho" else ())
     ref = O.push(lay, fields, src, 3, (1.0,) * 3, 0.9, form=form)
     outs = []
-    for reg in (1, 0):
-        plan = Plan(lay, (1.0,) * 3, 0.9, precision=32, sources=form, pencil=True, j_constant=form == "rho",
-                    tuning={"pencil_reg_z": reg})
-        assert plan.pencil_boxes == 5 and plan.tuning().get("pencil_reg_z") == reg
+    for tuning in ({"pencil_reg_z": 1, "z_one_launch": 1}, {"pencil_reg_z": 1, "z_one_launch": 0},
+                   {"pencil_reg_z": 0}):
+        plan = Plan(lay, (1.0,) * 3, 0.9, precision=32, sources=form, pencil=True, j_constant=form != "vacuum",
+                    tuning=tuning)
+        used = plan.tuning()
+        assert plan.pencil_boxes == 5 and used.get("pencil_reg_z") == tuning["pencil_reg_z"]
+        assert used.get("z_one_launch", -1) == tuning.get("z_one_launch", -1)
         df = plan.pack_fields(fields)
-        ds = plan.pack_fields(src) if form == "rho" else None
+        ds = plan.pack_fields(src) if form != "vacuum" else None
         plan.push(df, ds, 3)
         plan.sync()
         got = plan.unpack_fields(df)
         if form == "rho":
             got["rho"] = plan.unpack(ds["rho"])
         plan.close()
-        assert_fields(lay, got, ref, comps, 32, what=f"pencil_reg_z={reg}")
+        assert_fields(lay, got, ref, comps, 32, what=f"tuning {tuning}")
         outs.append(got)
-    assert_fields(lay, outs[0], outs[1], comps, 32, what="register vs shared-memory z pass")
+    for got in outs[1:]:
+        assert_fields(lay, outs[0], got, comps, 32, what="z pass variants against each other")
