@@ -20,7 +20,7 @@ LIB = os.path.join(LIBDIR, "libpsatd.so")
 BUILD = os.path.join(PKG, "_build")
 
 SOURCES = ["plan.cpp", "tables.cu", "fft_kernels.cu", "fast_kernels.cu", "reg_kernels.cu", "reg_planes_0.cu",
-           "reg_planes_1.cu", "reg_planes_2.cu", "pencil_kernels.cu", "exchange.cu", "static_push.cu"]
+           "reg_planes_1.cu", "reg_planes_2.cu", "reg_planes_3.cu", "pencil_kernels.cu", "exchange.cu", "static_push.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

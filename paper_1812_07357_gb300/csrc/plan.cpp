@@ -631,7 +631,7 @@ static bool plane_grid(const GatherSeg* segs, int ns, int n0, int n1, GatherGrid
 static void build_gather(psatd_plan* P, const std::vector<char>& box_fast, uint32_t flags) {
   P->deferred = false;
   const int nb = (int)P->boxes.size();
-  const bool reg = !P->grp_pf.empty() && !P->segs.empty() && P->step_tiles.empty() &&
+  const bool reg = !P->grp_pf.empty() && P->grp_pf.front().code >= 0 && !P->segs.empty() && P->step_tiles.empty() &&
                    P->g_rows.empty() && P->pen_rows.empty() &&
                    std::all_of(box_fast.begin(), box_fast.end(), [](char f) { return f != 0; });
   const bool pen = P->pen_boxes == nb && !P->step_tiles.empty();
@@ -785,10 +785,18 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
            z_fast_smem(P->prec, P->form, n2) <= optin;
   };
   // register plane shape of a box, or -1
+  // register plane shape of a box, or -1: a shape with register plane
+  // kernels and a z-pass kernel for its z length (register z, shared-memory
+  // plane z or pencil z)
   auto reg_code_of = [&](const psatd_box& b, const ShapeDev& sh) {
-    if (P->prec != 32 || !plane_ok(b, sh)) return -1;
+    if (P->prec != 32 || (d.flags & PSATD_GENERIC_KERNELS) || P->form == kPml) return -1;
     const int c = reg_shape_code(sh.L, b.n[1]);
     if (c < 0 || reg_fwd_smem(c) > optin || reg_inv_smem(c) > optin) return -1;
+    const int n2 = b.n[2], szf = z_fast_smem(P->prec, P->form, n2);
+    const bool zr = z_reg_ok(n2) && z_reg_smem(P->form, n2) <= optin;
+    const bool zf = sh.fz >= 0 && szf <= optin;
+    const bool zp = sh.pz >= 0 && n2 <= pen_z_max(P->prec) && szf <= optin;
+    if (!(zr || zf || zp)) return -1;
     P->reg_planes_used = true;
     return P->reg_planes ? c : -1;
   };
@@ -815,7 +823,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     box_reg[bi] = reg_code_of(b, sh);
     const bool prefer_pencil =
         (d.flags & PSATD_PENCIL_KERNELS) || (!(d.flags & PSATD_PLANE_KERNELS) && box_reg[bi] < 0);
-    const bool fast = fast_ok && !(pencil_ok && prefer_pencil);
+    const bool fast = (fast_ok || box_reg[bi] >= 0) && !(pencil_ok && prefer_pencil);
     const bool pencil = !fast && pencil_ok;
     const bool generic = !fast && !pencil;   // the generic Stockham kernels
     if (fast) {
@@ -824,14 +832,23 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
         P->plane_fwd.push_back(make_int2(bi, z));
         if (z >= b.ng_lo[2] && z < n2 - b.ng_hi[2]) P->plane_inv.push_back(make_int2(bi, z));
       }
+      // z pass: the shared-memory plane z kernel (or the register z kernel,
+      // chosen below) where the z length has one, else the pencil z kernel
+      const bool zf = sh.fz >= 0 && sm_zf <= optin;
+      std::vector<ColJob>& zl = zf ? P->zfast : P->zpen;
       for (int y = 0; y < n1; ++y)
-        for (int m = 0; m < L; m += tile) P->zfast.push_back({bi, y, m, std::min(tile, L - m)});
+        for (int m = 0; m < L; m += tile) zl.push_back({bi, y, m, std::min(tile, L - m)});
       // the Nyquist column mx = L in tiles of consecutive y (negative count)
-      for (int y = 0; y < n1; y += tile) P->zfast.push_back({bi, y, L, -std::min(tile, n1 - y)});
-      P->buf_pf = std::max(P->buf_pf, n1 * sh.lp);
-      P->buf_pi = std::max(P->buf_pi, n1 * hx);
-      P->rows_pi = std::max(P->rows_pi, ni * sh.hp);
-      P->smem_zf = std::max(P->smem_zf, sm_zf);
+      for (int y = 0; y < n1; y += tile) zl.push_back({bi, y, L, -std::min(tile, n1 - y)});
+      if (zf)
+        P->smem_zf = std::max(P->smem_zf, sm_zf);
+      else
+        P->smem_penz = std::max(P->smem_penz, sm_zf);
+      if (fast_ok) {   // buffers of the shared-memory plane kernels
+        P->buf_pf = std::max(P->buf_pf, n1 * sh.lp);
+        P->buf_pi = std::max(P->buf_pi, n1 * hx);
+        P->rows_pi = std::max(P->rows_pi, ni * sh.hp);
+      }
     } else if (pencil) {
       // pencil kernels: x rows, y tiles, z tiles (+ update), y tiles, x rows
       ++P->pen_boxes;
@@ -927,11 +944,15 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     P->zpen.swap(keep);
   }
   if (P->fast_boxes && P->prec == 32) {
-    // register plane kernels when every fast box has a register shape: the
-    // plane jobs grouped by shape (one launch each), box order kept in a group
+    // register plane kernels for the fast boxes with a register shape: the
+    // plane jobs grouped by shape (one launch each), box order kept in a
+    // group; the other fast boxes (code -1, first) on the shared-memory plane
+    // kernels
     const bool all_reg = std::all_of(P->plane_fwd.begin(), P->plane_fwd.end(),
                                      [&](const int2& j) { return box_reg[j.x] >= 0; });
-    if (all_reg) {
+    const bool any_reg = std::any_of(P->plane_fwd.begin(), P->plane_fwd.end(),
+                                     [&](const int2& j) { return box_reg[j.x] >= 0; });
+    if (any_reg) {
       group(P->plane_fwd, [&](const int2& j) { return box_reg[j.x]; }, P->grp_pf);
       group(P->plane_inv, [&](const int2& j) { return box_reg[j.x]; }, P->grp_pi);
     }
@@ -1632,6 +1653,14 @@ static psatd_status forward_xy(psatd_plan* P, const DevPlan& D, const FieldPtrs&
   if (!P->grp_pf.empty()) {
     // one launch per register plane shape; the gather tables are indexed by plane_fwd position
     for (const auto& g : P->grp_pf) {
+      if (g.code < 0) {
+        CK(P, timed(P, 0, st, [&] {
+             return launch_plane_fwd(P->prec, D, fp, nf, spec, S, P->d_plane_fwd + g.start, g.count, P->buf_pf,
+                                     P->smem_pf, P->grid_pf, st);
+           }));
+        ++launches;
+        continue;
+      }
       CK(P, timed(P, 0, st, [&] {
            return launch_plane_fwd_reg(g.code, D, fp, nf, spec, S, P->d_plane_fwd + g.start, g.count,
                                        gather && !P->gseg_start.empty() ? P->d_gseg_start + g.start : nullptr,
@@ -1759,6 +1788,15 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
   if (!P->grp_pi.empty()) {
     // one launch per register plane shape; the guard segments are indexed by plane_inv position
     for (const auto& g : P->grp_pi) {
+      if (g.code < 0) {
+        CK(P, timed(P, 4, st, [&] {
+             return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv + g.start, g.count, P->buf_pi,
+                                     P->smem_pi, P->grid_pi, P->segs.empty() ? nullptr : P->d_seg_start + g.start,
+                                     P->d_segs, st);
+           }));
+        ++launches;
+        continue;
+      }
       CK(P, timed(P, 4, st, [&] {
            return launch_plane_inv_reg(g.code, D, fp, FOUT, P->d_ws, S, P->d_plane_inv + g.start, g.count,
                                        P->segs.empty() || !guards ? nullptr : P->d_seg_start + g.start, P->d_segs,

@@ -264,7 +264,7 @@ cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f,
                                  int64_t sstride, const int2* jobs, int64_t nplanes, const int* seg_start,
                                  const GuardSeg* segs, cudaStream_t st);
 cudaError_t configure_reg_kernels(int smem_bytes);
-// the plane shapes are instantiated in three translation units
+// the plane shapes are instantiated in four translation units
 // (reg_planes_<part>.cu); each exports its launchers in namespace plane_part<part>
 #define PSATD_DECLARE_PLANE_PART(NS)                                                                       \
   namespace NS {                                                                                           \
@@ -279,6 +279,7 @@ cudaError_t configure_reg_kernels(int smem_bytes);
 PSATD_DECLARE_PLANE_PART(plane_part0)
 PSATD_DECLARE_PLANE_PART(plane_part1)
 PSATD_DECLARE_PLANE_PART(plane_part2)
+PSATD_DECLARE_PLANE_PART(plane_part3)
 #undef PSATD_DECLARE_PLANE_PART
 // register z kernel (FP32, tiles of z_reg_tile_width(form) columns) for z length n2
 int z_reg_ok(int n2);

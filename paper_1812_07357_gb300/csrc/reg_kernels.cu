@@ -363,6 +363,7 @@ cudaError_t launch_plane_fwd_reg(int code, const DevPlan& P, const FieldPtrs& f,
     case 0: return plane_part0::launch_fwd(code, P, f, nf, spec, sstride, jobs, nplanes, gstart, gsegs, ggrid, ngather, st);
     case 1: return plane_part1::launch_fwd(code, P, f, nf, spec, sstride, jobs, nplanes, gstart, gsegs, ggrid, ngather, st);
     case 2: return plane_part2::launch_fwd(code, P, f, nf, spec, sstride, jobs, nplanes, gstart, gsegs, ggrid, ngather, st);
+    case 3: return plane_part3::launch_fwd(code, P, f, nf, spec, sstride, jobs, nplanes, gstart, gsegs, ggrid, ngather, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -374,6 +375,7 @@ cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f,
     case 0: return plane_part0::launch_inv(code, P, f, nf, spec, sstride, jobs, nplanes, seg_start, segs, st);
     case 1: return plane_part1::launch_inv(code, P, f, nf, spec, sstride, jobs, nplanes, seg_start, segs, st);
     case 2: return plane_part2::launch_inv(code, P, f, nf, spec, sstride, jobs, nplanes, seg_start, segs, st);
+    case 3: return plane_part3::launch_inv(code, P, f, nf, spec, sstride, jobs, nplanes, seg_start, segs, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -383,7 +385,8 @@ cudaError_t launch_plane_inv_reg(int code, const DevPlan& P, const FieldPtrs& f,
 // on top of it); `smem` is the device's opt-in maximum.
 cudaError_t configure_reg_kernels(int smem) {
   cudaError_t e = cudaSuccess;
-  for (cudaError_t r : {plane_part0::configure(smem), plane_part1::configure(smem), plane_part2::configure(smem)})
+  for (cudaError_t r : {plane_part0::configure(smem), plane_part1::configure(smem), plane_part2::configure(smem),
+                        plane_part3::configure(smem)})
     if (r != cudaSuccess) e = r;
 #define PSATD_ZA(NZV, F, ZS)                                                                      \
   if (z_reg_smem(F, NZV) <= smem) {                                                               \

@@ -14,7 +14,12 @@
 //   k_plane_inv_reg  the mirror image, keeping interior rows and cells only,
 //                    and writing the guard cells the plane feeds (fused S4).
 //
-// The shapes are instantiated in three translation units (reg_planes_<part>.cu,
+//   k_plane_*_wide   planes too wide for those (n0/2 > 60 or NY > 120): 2
+//                    threads per row and 2 or 4 per column, each a register
+//                    DFT of every 2nd (4th) sample, combined through shared
+//                    memory.
+//
+// The shapes are instantiated in four translation units (reg_planes_<part>.cu,
 // PSATD_PLANE_PART = part), each taking its share of PSATD_REG_SHAPES.
 #pragma once
 #include "reg_common.cuh"
@@ -22,13 +27,15 @@
 namespace psatd {
 
 // Register plane shapes X(code, L, NY, part): x half-lengths 24, 30, 40, 48, 60
-// by y lengths 48, 60, 80, 96, 120 (code 0: the 96 x 96 plane of 96^3 boxes)
+// by y lengths 48, 60, 80, 96, 120 (code 0: the 96 x 96 plane of 96^3 boxes),
+// and the wide planes 128 x 128 and 192 x 192 (k_plane_*_wide)
 #define PSATD_REG_SHAPES(X)                                                                        \
   X(0, 48, 96, 0) X(1, 24, 48, 0) X(2, 24, 60, 0) X(3, 24, 80, 0) X(4, 24, 96, 0) X(5, 24, 120, 0) \
   X(6, 30, 48, 1) X(7, 30, 60, 1) X(8, 30, 80, 1) X(9, 30, 96, 1) X(10, 30, 120, 1)               \
   X(11, 40, 48, 1) X(12, 40, 60, 1) X(13, 40, 80, 1) X(14, 40, 96, 1) X(15, 40, 120, 1)           \
   X(16, 48, 48, 2) X(17, 48, 60, 2) X(18, 48, 80, 2) X(19, 48, 120, 2)                            \
-  X(20, 60, 48, 2) X(21, 60, 60, 2) X(22, 60, 80, 2) X(23, 60, 96, 2) X(24, 60, 120, 2)
+  X(20, 60, 48, 2) X(21, 60, 60, 2) X(22, 60, 80, 2) X(23, 60, 96, 2) X(24, 60, 120, 2)                     \
+  X(25, 64, 128, 3) X(26, 96, 192, 3)
 
 namespace {
 
@@ -39,26 +46,23 @@ constexpr int reg_plane_min_blocks() {
   return (L <= 48 && NY <= 96) ? 4 : 3;
 }
 
-// ---------------------------------------------------------------------------
-template <int L, int NY>
-__global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>())
-    k_plane_fwd_reg(DevPlan P, FieldPtrs F, float2* spec, int64_t sstride, const int2* __restrict__ jobs,
-                    const int* __restrict__ gstart, const GatherSeg* __restrict__ gsegs,
-                    const GatherGrid* __restrict__ ggrid, int ngather) {
-  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0);
-  static_assert(NY <= kRegThreads && 2 * HX <= kRegThreads, "one thread per row / per half column");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* buf = reinterpret_cast<float*>(smem_raw);
-  const int2 J = jobs[blockIdx.x];
-  const int f = blockIdx.y;
-  const BoxDev bx = P.boxes[J.x];
+// The real N0 x NY plane J.y of field f into shared memory (pitch
+// row_pitch(N0) floats), by NT threads: copied in whole from the box, or, with
+// the deferred guard exchange, gathered from the cells that own it (a 3 x 3
+// grid of rectangles, or the plane's rectangle list).  Ends with a barrier.
+template <int N0, int NY, int NT>
+__device__ __forceinline__ void plane_load(const DevPlan& P, const FieldPtrs& F, float* buf, const int2& J, int f,
+                                           const BoxDev& bx, const int* __restrict__ gstart,
+                                           const GatherSeg* __restrict__ gsegs, const GatherGrid* __restrict__ ggrid,
+                                           int ngather) {
+  constexpr int PF = row_pitch(N0);
   constexpr int UPR = N0 / 4;
   if (ggrid && f < ngather) {
     // deferred exchange, plane of at most 3 x 3 rectangles: thread t copies
     // the 16-byte column t % UPR of the rows t / UPR + k * RG
-    constexpr int RG = kRegThreads / UPR;
+    constexpr int RG = NT / UPR;
     __shared__ GatherGrid gg;
-    static_assert(sizeof(GatherGrid) / 4 <= kRegThreads, "one word per thread");
+    static_assert(sizeof(GatherGrid) / 4 <= NT, "one word per thread");
     if (threadIdx.x < sizeof(GatherGrid) / 4)
       reinterpret_cast<int*>(&gg)[threadIdx.x] = reinterpret_cast<const int*>(ggrid + blockIdx.x)[threadIdx.x];
     __syncthreads();
@@ -95,13 +99,13 @@ __global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>())
       if (gs.vec) {
         const int upr = gs.nx >> 2;
         const unsigned m = magic(upr);
-        for (int u = threadIdx.x; u < gs.ny * upr; u += kRegThreads) {
+        for (int u = threadIdx.x; u < gs.ny * upr; u += NT) {
           const int r = fdiv(u, m), c = 4 * (u - r * upr);
           cp16(dst + r * PF + c, src + (int64_t)r * gs.spitch + c);
         }
       } else {
         const unsigned m = magic(gs.nx);
-        for (int u = threadIdx.x; u < gs.ny * gs.nx; u += kRegThreads) {
+        for (int u = threadIdx.x; u < gs.ny * gs.nx; u += NT) {
           const int r = fdiv(u, m), c = u - r * gs.nx;
           cp4(dst + r * PF + c, src + (int64_t)r * gs.spitch + c);
         }
@@ -109,13 +113,29 @@ __global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>())
     }
   } else {
     const float* g = reinterpret_cast<const float*>(F.p[f]) + bx.foff + (int64_t)J.y * NY * N0;
-    for (int u = threadIdx.x; u < NY * UPR; u += kRegThreads) {
+    for (int u = threadIdx.x; u < NY * UPR; u += NT) {
       const int r = u / UPR, x = u - r * UPR;
       cp16(buf + r * PF + 4 * x, g + 4 * u);
     }
   }
   cp_commit_wait_all();
   __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+template <int L, int NY>
+__global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>())
+    k_plane_fwd_reg(DevPlan P, FieldPtrs F, float2* spec, int64_t sstride, const int2* __restrict__ jobs,
+                    const int* __restrict__ gstart, const GatherSeg* __restrict__ gsegs,
+                    const GatherGrid* __restrict__ ggrid, int ngather) {
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0);
+  static_assert(NY <= kRegThreads && 2 * HX <= kRegThreads, "one thread per row / per half column");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* buf = reinterpret_cast<float*>(smem_raw);
+  const int2 J = jobs[blockIdx.x];
+  const int f = blockIdx.y;
+  const BoxDev bx = P.boxes[J.x];
+  plane_load<N0, NY, kRegThreads>(P, F, buf, J, f, bx, gstart, gsegs, ggrid, ngather);
   // x: row r -> half spectrum X[0..L] written back into the same row
   if (threadIdx.x < NY) {
     float* row = buf + threadIdx.x * PF;
@@ -172,6 +192,40 @@ __device__ __forceinline__ void copy_rect_w(const float* src, int spitch, float*
   for (int u = tid; u < ny * upr; u += nthreads) {
     const int r = fdiv(u, m), c = (u - r * upr) * W;
     *reinterpret_cast<V*>(dst + r * dpitch + c) = *reinterpret_cast<const V*>(src + r * spitch + c);
+  }
+}
+
+// The interior cells of a plane (rows: ni interior rows of pitch
+// row_pitch(N0) floats in shared memory, the first interior cell at xlo) to
+// field f of their box, then the guard rectangles this plane feeds in other
+// boxes (seg_start: CSR of the guard segments per plane job), by NT threads.
+template <int N0, int NY, int NT>
+__device__ __forceinline__ void plane_store(const DevPlan& P, const FieldPtrs& F, const float* rows, const int2& J,
+                                            int f, const BoxDev& bx, int ylo, int ni, int xlo, int nxi,
+                                            bool vec_rows, const int* __restrict__ seg_start,
+                                            const GuardSeg* __restrict__ segs) {
+  constexpr int PF = row_pitch(N0);
+  // interior cells to this box, then the guard cells this plane feeds
+  float* fbase = reinterpret_cast<float*>(F.p[f]);
+  float* own = fbase + bx.foff + ((int64_t)J.y * NY + ylo) * N0 + xlo;
+  if (vec_rows)
+    copy_rect_w<float4>(rows, PF, own, N0, ni, nxi, threadIdx.x, NT);
+  else
+    copy_rect_w<float>(rows, PF, own, N0, ni, nxi, threadIdx.x, NT);
+  if (seg_start) {
+    const int p = blockIdx.x;
+    const int s1 = seg_start[p + 1];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = NT >> 5;
+    for (int si = seg_start[p] + warp; si < s1; si += nw) {
+      const GuardSeg gs = segs[si];
+      const BoxDev db = P.boxes[gs.dst_box];
+      float* dst = fbase + db.foff + ((int64_t)gs.dst_z * db.n[1] + gs.dy) * db.n[0] + gs.dx;
+      const float* src = rows + (gs.sy - ylo) * PF + (gs.sx - xlo);
+      if (gs.vec > 1 && vec_rows)
+        copy_rect_w<float4>(src, PF, dst, db.n[0], gs.ny, gs.nx, lane, 32);
+      else
+        copy_rect_w<float>(src, PF, dst, db.n[0], gs.ny, gs.nx, lane, 32);
+    }
   }
 }
 
@@ -253,28 +307,345 @@ __global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>()) k_
     }
   }
   __syncthreads();
-  // interior cells to this box, then the guard cells this plane feeds
-  float* fbase = reinterpret_cast<float*>(F.p[f]);
-  float* own = fbase + bx.foff + ((int64_t)J.y * NY + ylo) * N0 + xlo;
-  if (vec_rows)
-    copy_rect_w<float4>(rows, PF, own, N0, ni, nxi, threadIdx.x, kRegThreads);
+  plane_store<N0, NY, kRegThreads>(P, F, rows, J, f, bx, ylo, ni, xlo, nxi, vec_rows, seg_start, segs);
+}
+
+// ---------------------------------------------------------------------------
+// Wide register plane kernels: planes too wide for one thread per row
+// (n0/2 > 60) or a thread pair per column (n1 > 120).  GX threads share a row
+// and GY a column; each does the length-L/GX (NY/GY) register DFT of every
+// GX-th (GY-th) sample, twiddled, and the GX- (GY-) point combination of the
+// partial transforms goes through shared memory (decimation in time:
+// X[k + (R/G) p] = sum_q w_R^{q k} w_G^{q p} DFT_{R/G}(x[G j + q])[k]).
+template <int L, int NY>
+constexpr bool plane_is_wide() {
+  return L > 60 || NY > 120;
+}
+template <int L, int NY>
+constexpr int wide_gx() {
+  return L > 60 ? 2 : 1;
+}
+template <int L, int NY>
+constexpr int wide_gy() {
+  return NY > 120 ? 4 : 2;
+}
+template <int L, int NY>
+constexpr int wide_threads() {
+  constexpr int a = NY * wide_gx<L, NY>(), b = (L + 1) * wide_gy<L, NY>();
+  return ((a > b ? a : b) + 31) / 32 * 32;
+}
+// one CTA per SM above 113 KB of shared memory, else two
+template <int L, int NY>
+constexpr int wide_min_blocks() {
+  return NY * row_pitch(2 * L) * 4 > 113 * 1024 ? 1 : 2;
+}
+// threads of a plane CTA of either kind
+template <int L, int NY>
+constexpr int plane_threads() {
+  if constexpr (plane_is_wide<L, NY>())
+    return wide_threads<L, NY>();
   else
-    copy_rect_w<float>(rows, PF, own, N0, ni, nxi, threadIdx.x, kRegThreads);
-  if (seg_start) {
-    const int p = blockIdx.x;
-    const int s1 = seg_start[p + 1];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kRegThreads >> 5;
-    for (int si = seg_start[p] + warp; si < s1; si += nw) {
-      const GuardSeg gs = segs[si];
-      const BoxDev db = P.boxes[gs.dst_box];
-      float* dst = fbase + db.foff + ((int64_t)gs.dst_z * db.n[1] + gs.dy) * db.n[0] + gs.dx;
-      const float* src = rows + (gs.sy - ylo) * PF + (gs.sx - xlo);
-      if (gs.vec > 1 && vec_rows)
-        copy_rect_w<float4>(src, PF, dst, db.n[0], gs.ny, gs.nx, lane, 32);
-      else
-        copy_rect_w<float>(src, PF, dst, db.n[0], gs.ny, gs.nx, lane, 32);
+    return kRegThreads;
+}
+
+// w_R^(q K) (sign DIR) for a run-time q < G <= 4 and a compile-time K
+template <int R, int K, int G, int DIR>
+__device__ __forceinline__ float2 root_q(int q) {
+  float2 w = make_float2(1.f, 0.f);
+  if constexpr (G > 1) w = q == 1 ? root<R, K % R, DIR>() : w;
+  if constexpr (G > 2) w = q == 2 ? root<R, (2 * K) % R, DIR>() : w;
+  if constexpr (G > 3) w = q == 3 ? root<R, (3 * K) % R, DIR>() : w;
+  return w;
+}
+
+template <int L, int NY>
+__global__ void __launch_bounds__(wide_threads<L, NY>(), wide_min_blocks<L, NY>())
+    k_plane_fwd_wide(DevPlan P, FieldPtrs F, float2* spec, int64_t sstride, const int2* __restrict__ jobs,
+                     const int* __restrict__ gstart, const GatherSeg* __restrict__ gsegs,
+                     const GatherGrid* __restrict__ ggrid, int ngather) {
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0), PC = PF / 2;
+  constexpr int GX = wide_gx<L, NY>(), GY = wide_gy<L, NY>(), NT = wide_threads<L, NY>();
+  constexpr int LX = L / GX, LY = NY / GY, LXP = GX > 1 ? LX + 1 : LX;
+  static_assert(L % GX == 0 && NY % GY == 0 && LY % GY == 0 && GX * LXP <= PC, "wide plane shape");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* buf = reinterpret_cast<float*>(smem_raw);
+  float2* cb = reinterpret_cast<float2*>(smem_raw);
+  const int2 J = jobs[blockIdx.x];
+  const int f = blockIdx.y;
+  const BoxDev bx = P.boxes[J.x];
+  plane_load<N0, NY, NT>(P, F, buf, J, f, bx, gstart, gsegs, ggrid, ngather);
+  const int t = threadIdx.x;
+  // x, stage 1: thread (row r, q): DFT of the packed samples z[q + GX j]
+  // (z[m] = x[2m] + i x[2m+1]), twiddled; back into the row at q * LXP + k
+  {
+    const int r = t / GX, q = t - r * GX;
+    const bool live = r < NY;
+    float2 v[LX];
+    if (live) {
+      const float2* row = cb + r * PC;
+#pragma unroll
+      for (int j = 0; j < LX; ++j) v[j] = row[q + GX * j];
+      Dft<float, LX, -1>::run(v);
+      static_for<1, LX>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        v[k] = cmul(v[k], root_q<L, k, GX, -1>(q));
+      });
+    }
+    __syncthreads();
+    if (live) {
+      float2* row = cb + r * PC + q * LXP;
+#pragma unroll
+      for (int k = 0; k < LX; ++k) row[k] = v[k];
     }
   }
+  __syncthreads();
+  // x, stage 2: Z[k] = sum_p w_GX^{p (k / LX)} Z_p[k mod LX], then the R2C
+  // split X[k] = (Z[k] + conj Z[L-k])/2 - i w^k (Z[k] - conj Z[L-k])/2
+  // (w = exp(-2 pi i / N0)) for k = q + GX j <= L/2 and its partner L - k
+  {
+    const int r = t / GX, q = t - r * GX;
+    const bool live = r < NY;
+    constexpr int NK = (L / 2 + GX) / GX;   // k = q + GX j, j < NK (some past L/2)
+    float2 lo[NK], hi[NK];
+    if (live) {
+      const float2* row = cb + r * PC;
+      auto zval = [&](int k) {   // Z[k], 0 <= k < L
+        const int kk = k % LX, p = k / LX;
+        float2 a[GX];
+#pragma unroll
+        for (int s = 0; s < GX; ++s) a[s] = row[s * LXP + kk];
+        float2 z = a[0];
+#pragma unroll
+        for (int s = 1; s < GX; ++s) {
+          // w_GX^{s p}: GX <= 2 here, so +-1
+          z = (s * p) % 2 ? z - a[s] : z + a[s];
+        }
+        return z;
+      };
+      static_for<0, NK>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        const int k = q + GX * j;
+        if (k <= L / 2) {
+          const float2 a = zval(k), b = zval((L - k) % L);
+          const float2 A = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+          const float2 Bv = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
+          // w^k and w^(L-k) for k = GX j + q (q < GX <= 2)
+          const float2 wk = GX > 1 && q == 1 ? root<N0, GX * j + 1, -1>() : root<N0, GX * j, -1>();
+          const float2 wl = GX > 1 && q == 1 ? root<N0, L - GX * j - 1, -1>() : root<N0, L - GX * j, -1>();
+          if (k == 0) {
+            lo[j] = make_float2(A.x + Bv.x, A.y + Bv.y);
+            hi[j] = make_float2(A.x - Bv.x, A.y - Bv.y);
+          } else {
+            lo[j] = A + cmul(wk, Bv);
+            hi[j] = conjg(A) + cmul(wl, conjg(Bv));
+          }
+        }
+      });
+    }
+    static_assert(GX <= 2, "the x combination handles GX <= 2");
+    __syncthreads();
+    if (live) {
+      float2* row = cb + r * PC;
+      static_for<0, NK>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        const int k = q + GX * j;
+        if (k <= L / 2) {
+          row[k] = lo[j];
+          if (k == 0) row[L] = hi[j];
+          else if (2 * k != L) row[L - k] = hi[j];
+        }
+      });
+    }
+  }
+  __syncthreads();
+  // y, stage 1: thread (column c, q): DFT of the rows q + GY j, twiddled;
+  // back into rows q * LY + k
+  {
+    const int q = t / HX, c = t - q * HX;
+    const bool live = q < GY;
+    float2 v[LY];
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < LY; ++j) v[j] = cb[(q + GY * j) * PC + c];
+      Dft<float, LY, -1>::run(v);
+      static_for<1, LY>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        v[k] = cmul(v[k], root_q<NY, k, GY, -1>(q));
+      });
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll
+      for (int k = 0; k < LY; ++k) cb[(q * LY + k) * PC + c] = v[k];
+    }
+  }
+  __syncthreads();
+  // y, stage 2: thread (c, q) combines k in [q LY/GY, (q+1) LY/GY) over the
+  // GY partial transforms and stores rows k + LY p of the spectrum plane
+  {
+    const int q = t / HX, c = t - q * HX;
+    if (q < GY) {
+      float2* out = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX + c;
+      constexpr int KQ = LY / GY;
+#pragma unroll
+      for (int i = 0; i < KQ; ++i) {
+        const int k = q * KQ + i;
+        float2 a[GY];
+#pragma unroll
+        for (int p = 0; p < GY; ++p) a[p] = cb[(p * LY + k) * PC + c];
+        Dft<float, GY, -1>::run(a);
+#pragma unroll
+        for (int p = 0; p < GY; ++p) out[(k + LY * p) * HX] = a[p];
+      }
+    }
+  }
+}
+
+template <int L, int NY>
+__global__ void __launch_bounds__(wide_threads<L, NY>(), wide_min_blocks<L, NY>())
+    k_plane_inv_wide(DevPlan P, FieldPtrs F, const float2* spec, int64_t sstride, const int2* __restrict__ jobs,
+                     const int* __restrict__ seg_start, const GuardSeg* __restrict__ segs) {
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0), PC = PF / 2;
+  constexpr int GX = wide_gx<L, NY>(), GY = wide_gy<L, NY>(), NT = wide_threads<L, NY>();
+  constexpr int LX = L / GX, LY = NY / GY, LXP = GX > 1 ? LX + 1 : LX;
+  static_assert(GX <= 2 && LX % GX == 0 && LY % GY == 0 && GX * LXP <= PC, "wide plane shape");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // one buffer: first the NY x HX spectrum plane (pitch HX), then the interior
+  // rows (pitch PF floats)
+  float2* sp = reinterpret_cast<float2*>(smem_raw);
+  float2* cb = reinterpret_cast<float2*>(smem_raw);
+  float* rows = reinterpret_cast<float*>(smem_raw);
+  const int2 J = jobs[blockIdx.x];
+  const int f = blockIdx.y;
+  const BoxDev bx = P.boxes[J.x];
+  const int ylo = bx.ng_lo[1], yhi = NY - bx.ng_hi[1], ni = yhi - ylo;
+  const int xlo = bx.ng_lo[0], nxi = N0 - bx.ng_lo[0] - bx.ng_hi[0];
+  {
+    const float2* g = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX;
+    constexpr int UNITS = NY * HX / 2;   // 16-byte units of the contiguous plane
+    for (int u = threadIdx.x; u < UNITS; u += NT) cp16(sp + 2 * u, g + 2 * u);
+    cp_commit_wait_all();
+    __syncthreads();
+  }
+  const int t = threadIdx.x;
+  // y, stage 1 (inverse): thread (c, q): DFT of rows q + GY j, twiddled
+  {
+    const int q = t / HX, c = t - q * HX;
+    const bool live = q < GY;
+    float2 v[LY];
+    if (live) {
+#pragma unroll
+      for (int j = 0; j < LY; ++j) v[j] = sp[(q + GY * j) * HX + c];
+      Dft<float, LY, 1>::run(v);
+      static_for<1, LY>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        v[k] = cmul(v[k], root_q<NY, k, GY, 1>(q));
+      });
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll
+      for (int k = 0; k < LY; ++k) sp[(q * LY + k) * HX + c] = v[k];
+    }
+  }
+  __syncthreads();
+  // y, stage 2: combination; interior rows kept in registers until the plane
+  // is consumed, then stored as rows of pitch PF floats
+  {
+    const int q = t / HX, c = t - q * HX;
+    const bool live = q < GY;
+    constexpr int KQ = LY / GY;
+    float2 a[KQ][GY];
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < KQ; ++i) {
+        const int k = q * KQ + i;
+#pragma unroll
+        for (int p = 0; p < GY; ++p) a[i][p] = sp[(p * LY + k) * HX + c];
+        Dft<float, GY, 1>::run(a[i]);
+      }
+    }
+    __syncthreads();
+    if (live) {
+#pragma unroll
+      for (int i = 0; i < KQ; ++i) {
+#pragma unroll
+        for (int p = 0; p < GY; ++p) {
+          const int y = q * KQ + i + LY * p;
+          if (y >= ylo && y < yhi) cb[(y - ylo) * PC + c] = a[i][p];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // x, stage 1 (interior rows): thread (r, q): C2R merge
+  // Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]) at k = q + GX j,
+  // inverse DFT over j, twiddled; back into the row at q * LXP + k
+  {
+    const int r = t / GX, q = t - r * GX;
+    const bool live = r < ni;
+    float2 v[LX];
+    if (live) {
+      const float2* xr = cb + r * PC;
+      static_for<0, LX>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        const int k = q + GX * j;
+        const float2 a = xr[k], b = xr[L - k];
+        const float2 w = GX > 1 && q == 1 ? root<N0, GX * j + 1, 1>() : root<N0, GX * j, 1>();
+        v[j] = (a + conjg(b)) + times_i(cmul(a - conjg(b), w));
+      });
+      Dft<float, LX, 1>::run(v);
+      static_for<1, LX>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        v[k] = cmul(v[k], root_q<L, k, GX, 1>(q));
+      });
+    }
+    __syncthreads();
+    if (live) {
+      float2* row = cb + r * PC + q * LXP;
+#pragma unroll
+      for (int k = 0; k < LX; ++k) row[k] = v[k];
+    }
+  }
+  __syncthreads();
+  // x, stage 2: z[m + LX p] = sum_s w_GX^{s p} Z_s[m] for m in the thread's
+  // share; cells 2m, 2m+1 (interior ones) written back into the row from x = 0
+  const float scale = __frcp_rn((float)(N0 * NY * bx.n[2]));   // exact integer < 2^24
+  {
+    const int r = t / GX, q = t - r * GX;
+    const bool live = r < ni;
+    constexpr int MQ = LX / GX;
+    float2 z[MQ][GX];
+    if (live) {
+      const float2* row = cb + r * PC;
+#pragma unroll
+      for (int i = 0; i < MQ; ++i) {
+        const int m = q * MQ + i;
+        float2 a[GX];
+#pragma unroll
+        for (int s = 0; s < GX; ++s) a[s] = row[s * LXP + m];
+        Dft<float, GX, 1>::run(a);
+#pragma unroll
+        for (int p = 0; p < GX; ++p) z[i][p] = a[p];
+      }
+    }
+    __syncthreads();
+    if (live) {
+      float* o = rows + r * PF - xlo;
+#pragma unroll
+      for (int i = 0; i < MQ; ++i) {
+#pragma unroll
+        for (int p = 0; p < GX; ++p) {
+          const int x = 2 * (q * MQ + i + LX * p);
+          if (x >= xlo && x < xlo + nxi) o[x] = scale * z[i][p].x;
+          if (x + 1 >= xlo && x + 1 < xlo + nxi) o[x + 1] = scale * z[i][p].y;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  const bool vec_rows = (nxi % 4 == 0) && (xlo % 4 == 0);
+  plane_store<N0, NY, NT>(P, F, rows, J, f, bx, ylo, ni, xlo, nxi, vec_rows, seg_start, segs);
 }
 
 }  // namespace
@@ -303,8 +674,12 @@ bool plane_fwd_shape(int code, dim3 grid, const DevPlan& P, const FieldPtrs& f, 
                      int ngather, cudaStream_t st) {
   if constexpr (PART == PSATD_PLANE_PART) {
     if (code != CODE) return false;
-    k_plane_fwd_reg<L, NY><<<grid, kRegThreads, plane_fwd_bytes<L, NY>(), st>>>(P, f, (float2*)spec, sstride, jobs,
-                                                                               gstart, gsegs, ggrid, ngather);
+    if constexpr (plane_is_wide<L, NY>())
+      k_plane_fwd_wide<L, NY><<<grid, wide_threads<L, NY>(), plane_fwd_bytes<L, NY>(), st>>>(
+          P, f, (float2*)spec, sstride, jobs, gstart, gsegs, ggrid, ngather);
+    else
+      k_plane_fwd_reg<L, NY><<<grid, kRegThreads, plane_fwd_bytes<L, NY>(), st>>>(P, f, (float2*)spec, sstride,
+                                                                                 jobs, gstart, gsegs, ggrid, ngather);
     return true;
   } else {
     return false;
@@ -316,8 +691,12 @@ bool plane_inv_shape(int code, dim3 grid, const DevPlan& P, const FieldPtrs& f, 
                      const int2* jobs, const int* seg_start, const GuardSeg* segs, cudaStream_t st) {
   if constexpr (PART == PSATD_PLANE_PART) {
     if (code != CODE) return false;
-    k_plane_inv_reg<L, NY><<<grid, kRegThreads, plane_inv_bytes<L, NY>(), st>>>(P, f, (const float2*)spec, sstride,
-                                                                               jobs, seg_start, segs);
+    if constexpr (plane_is_wide<L, NY>())
+      k_plane_inv_wide<L, NY><<<grid, wide_threads<L, NY>(), plane_inv_bytes<L, NY>(), st>>>(
+          P, f, (const float2*)spec, sstride, jobs, seg_start, segs);
+    else
+      k_plane_inv_reg<L, NY><<<grid, kRegThreads, plane_inv_bytes<L, NY>(), st>>>(P, f, (const float2*)spec,
+                                                                                 sstride, jobs, seg_start, segs);
     return true;
   } else {
     return false;
@@ -328,12 +707,20 @@ template <int L, int NY, int PART>
 void plane_configure_shape(int smem, cudaError_t* e) {
   if constexpr (PART == PSATD_PLANE_PART) {
     if (plane_fwd_bytes<L, NY>() > smem || plane_inv_bytes<L, NY>() > smem) return;
-    cudaError_t r = cudaFuncSetAttribute(k_plane_fwd_reg<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         plane_fwd_bytes<L, NY>());
+    cudaError_t r, r2;
+    if constexpr (plane_is_wide<L, NY>()) {
+      r = cudaFuncSetAttribute(k_plane_fwd_wide<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               plane_fwd_bytes<L, NY>());
+      r2 = cudaFuncSetAttribute(k_plane_inv_wide<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                plane_inv_bytes<L, NY>());
+    } else {
+      r = cudaFuncSetAttribute(k_plane_fwd_reg<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               plane_fwd_bytes<L, NY>());
+      r2 = cudaFuncSetAttribute(k_plane_inv_reg<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                plane_inv_bytes<L, NY>());
+    }
     if (r != cudaSuccess) *e = r;
-    r = cudaFuncSetAttribute(k_plane_inv_reg<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             plane_inv_bytes<L, NY>());
-    if (r != cudaSuccess) *e = r;
+    if (r2 != cudaSuccess) *e = r2;
   }
 }
 

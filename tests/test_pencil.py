@@ -168,26 +168,33 @@ def test_pencil_lengths_of_the_1024_workloads(prec):
     along y and z (local 192^3 boxes, hybrid 256 x 256 planes), on
     self-periodic boxes with short other axes; p = 64 and infinite order;
     J form.  In FP64 the pencil z pass stops at 128, so the boxes with z = 192
-    and 256 run on the generic kernels there."""
+    and 256 run on the generic kernels there.  In FP32 on the pencil kernels
+    (flag), and by default, where the two 48 x 48-plane boxes with z = 192
+    and 256 take the register plane kernels with the pencil z kernel."""
     sizes = [(384, 48, 48), (48, 192, 48), (48, 256, 48), (48, 48, 192), (48, 48, 256)]
     boxes = [I.Box(n, (8, 8, 8), (8, 8, 8), (0, 0, 0), p) for n, p in zip(sizes, (64, 0, 64, 0, 64))]
     lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
     rng = np.random.default_rng(27)
     fields = {k: O.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes]) for k in O.COMPS}
     src = {k: O.exchange(lay, [rng.standard_normal(b.shape) for b in lay.boxes]) for k in ("Jx", "Jy", "Jz")}
-    _check(lay, fields, src, 2, (1.0, 1.0, 1.0), 0.9, prec, "J", (0, 5) if prec == 32 else (0, 3))
+    if prec == 32:
+        _check(lay, fields, src, 2, (1.0, 1.0, 1.0), 0.9, prec, "J", (0, 5), pencil=True)
+        _check(lay, fields, src, 2, (1.0, 1.0, 1.0), 0.9, prec, "J", (2, 3))
+    else:
+        _check(lay, fields, src, 2, (1.0, 1.0, 1.0), 0.9, prec, "J", (0, 3))
 
 
 def test_pencil_local_192_boxes_and_hybrid_384_groups():
     """Two local 192^3 boxes (64^3 interior + 64 guards, the local 1024
-    workload's box) and four hybrid groups of 384 x 48 x 48 (256 cells + 64
-    guards on the x faces; y, z periodic inside the group), p = 64, laser,
-    FP32, 2 steps with the guard exchange."""
+    workload's box; on the pencil kernels by flag, the default being the wide
+    register plane kernels) and four hybrid groups of 384 x 48 x 48 (256 cells
+    + 64 guards on the x faces; y, z periodic inside the group), p = 64,
+    laser, FP32, 2 steps with the guard exchange."""
     lay = I.local_layout((128, 64, 64), (2, 1, 1), 64, 64)
     assert all(b.n == (192, 192, 192) for b in lay.boxes)
     f = I.laser_fields((128, 64, 64), wavelength=8.0, waist=12.0, duration=8.0)
     _check(lay, {k: I.scatter_global(v, lay) for k, v in f.items()}, {}, 2, (1.0,) * 3, 0.9, 32, "vacuum",
-           (0, 2))
+           (0, 2), pencil=True)
     lay = I.hybrid_layout((1024, 48, 48), (4, 1, 1), 64, 64)
     assert all(b.n == (384, 48, 48) for b in lay.boxes)
     f = I.laser_fields((1024, 48, 48), wavelength=16.0, waist=12.0, duration=20.0)

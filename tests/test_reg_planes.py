@@ -157,3 +157,60 @@ def test_register_planes_deferred_equals_eager():
     for k in O.COMPS:
         for x, y in zip(a[k], b[k]):
             assert np.array_equal(x, y), k
+
+
+# ---------------------------------------------------------------------------
+# wide planes (k_plane_*_wide): 128 x 128 and 192 x 192
+# ---------------------------------------------------------------------------
+
+def test_wide_planes_local_192_laser():
+    """Two local 192^3 boxes (64^3 interior + 64 guards, the local 1024
+    workload's box), p = 64, laser, 3 steps: wide plane kernels (2 threads
+    per row, 4 per column), the pencil z kernel for z = 192, the deferred
+    exchange; against the oracle and against the pencil kernels."""
+    lay = I.local_layout((128, 64, 64), (2, 1, 1), 64, 64)
+    assert all(b.n == (192, 192, 192) for b in lay.boxes)
+    f = I.laser_fields((128, 64, 64), wavelength=8.0, waist=12.0, duration=8.0)
+    fields = {k: I.round_to(I.scatter_global(v, lay), np.float32) for k, v in f.items()}
+    ref = O.push(lay, fields, {}, 3, (1.0, 0.9, 1.1), 0.8, form="vacuum")
+    got, (nfast, npen, deferred, tun) = _push(lay, fields, {}, "vacuum", 3)
+    assert (nfast, npen) == (2, 0) and deferred and tun.get("reg_planes") == 1
+    assert_fields(lay, got, ref, O.COMPS, 32, what="wide 192 x 192 planes")
+    pen, (nfast, npen, _, _) = _push(lay, fields, {}, "vacuum", 3, pencil=True)
+    assert (nfast, npen) == (0, 2)
+    assert_fields(lay, got, pen, O.COMPS, 32, what="wide planes vs pencil kernels")
+
+
+@pytest.mark.parametrize("form", ["vacuum", "rho"])
+@pytest.mark.parametrize("sizes", [
+    # several z lengths: 128, 96, 60 on the shared-memory plane z kernel, 192 on the pencil z kernel
+    [(128, 128, 128), (128, 128, 192), (192, 192, 60), (128, 128, 96)],
+    # one z length with a register z kernel: 96 on the register z kernel
+    [(128, 128, 96), (192, 192, 96)],
+], ids=["mixed_z", "z96"])
+def test_wide_planes_with_every_z_route(form, sizes):
+    """Self-periodic 128 x 128 and 192 x 192 planes with the z pass on each
+    of its kernels; against the oracle."""
+    boxes = [I.Box(n, (6,) * 3, (6,) * 3, (0, 0, 0), p) for n, p in zip(sizes, (16, 0, 32, 8))]
+    lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
+    fields, src = _inputs(lay, form, 67)
+    comps = O.COMPS + (("rho",) if form == "rho" else ())
+    ref = O.push(lay, fields, src, 3, (1.0, 0.9, 1.1), 0.8, form=form)
+    got, (nfast, npen, deferred, _) = _push(lay, fields, src, form, 3)
+    assert (nfast, npen) == (len(boxes), 0) and deferred
+    assert_fields(lay, got, ref, comps, 32, what=f"wide planes, {sizes}, {form} form")
+
+
+def test_wide_planes_beside_shared_memory_planes():
+    """The plane family forced on a batch with a shape that has no register
+    plane kernels (64 x 64 planes: the shared-memory plane kernels, launched
+    on their own job range) and one that has (128 x 128): against the
+    oracle."""
+    sizes = [(64, 64, 64), (128, 128, 64)]
+    boxes = [I.Box(n, (4,) * 3, (4,) * 3, (0, 0, 0), p) for n, p in zip(sizes, (16, 32))]
+    lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
+    fields, src = _inputs(lay, "vacuum", 68)
+    ref = O.push(lay, fields, src, 3, (1.0, 0.9, 1.1), 0.8, form="vacuum")
+    got, (nfast, npen, deferred, _) = _push(lay, fields, src, "vacuum", 3, plane=True)
+    assert (nfast, npen) == (2, 0) and not deferred
+    assert_fields(lay, got, ref, O.COMPS, 32, what="wide and shared-memory plane kernels in one plan")
