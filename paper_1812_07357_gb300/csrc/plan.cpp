@@ -350,6 +350,7 @@ struct psatd_plan {
   bool pen_reg_z_used = false;               // ... and whether the plan has such boxes
   int reg_planes = 1;                        // tuning: register plane kernels for the boxes whose shape has them
   bool reg_planes_used = false;              // ... and whether the plan has such boxes
+  bool zreg_multi = false;                   // every length of zpen_reg has the persistent multi-length kernel
   int z_one_launch = 0;                      // tuning: those boxes' z pass in one persistent launch (measured
                                              // slower on the 300-box uneven batch: 7.07 against 5.11 ms)
   int sms = 0;                               // multiprocessors of the plan's device
@@ -925,7 +926,6 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
   // its own tile width; the shared-memory pencil z kernel keeps the rest
   if (P->prec == 32 && !P->zpen.empty()) P->pen_reg_z_used = true;
   if (P->prec == 32 && P->pen_reg_z && !P->zpen.empty()) {
-    const int rt = z_reg_tile_width(P->form);
     std::vector<ColJob> keep;
     std::vector<char> done(P->boxes.size(), 0);
     for (const ColJob& j : P->zpen) {
@@ -936,7 +936,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
       }
       if (done[j.box]) continue;
       done[j.box] = 1;
-      const int L = b.n[0] / 2, n1 = b.n[1];
+      const int L = b.n[0] / 2, n1 = b.n[1], rt = z_reg_tile_width(P->form, b.n[2]);
       for (int y = 0; y < n1; ++y)
         for (int m = 0; m < L; m += rt) P->zpen_reg.push_back({j.box, y, m, std::min(rt, L - m)});
       for (int y = 0; y < n1; y += rt) P->zpen_reg.push_back({j.box, y, L, -std::min(rt, n1 - y)});
@@ -971,12 +971,12 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     });
     if (nz == -1 && all_reg && zreg_all) P->pen_reg_z_used = true;
     if (nz == -1 && all_reg && zreg_all && P->pen_reg_z) {
-      const int rt = z_reg_tile_width(P->form);
       int last = -1;
       for (const ColJob& j : P->zfast) {
         if (j.box == last) continue;
         last = j.box;
         const int L = P->boxes[j.box].n[0] / 2, n1 = P->boxes[j.box].n[1];
+        const int rt = z_reg_tile_width(P->form, P->boxes[j.box].n[2]);
         for (int y = 0; y < n1; ++y)
           for (int m = 0; m < L; m += rt) P->zpen_reg.push_back({j.box, y, m, std::min(rt, L - m)});
         for (int y = 0; y < n1; y += rt) P->zpen_reg.push_back({j.box, y, L, -std::min(rt, n1 - y)});
@@ -985,6 +985,9 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
     }
   }
   group(P->zpen_reg, [&](const ColJob& j) { return P->boxes[j.box].n[2]; }, P->grp_zreg);
+  P->zreg_multi = !P->zpen_reg.empty() && std::all_of(P->grp_zreg.begin(), P->grp_zreg.end(), [](const auto& g) {
+    return z_reg_multi_ok(g.code) != 0;
+  });
   group(P->pen_rows, [&](const RowJob& j) { return shape_of_box(j.box).px; }, P->grp_rows);
   group(P->pen_rows_int, [&](const RowJob& j) { return shape_of_box(j.box).px; }, P->grp_rows_int);
   group(P->pen_ycols, [&](const ColJob& j) { return shape_of_box(j.box).py; }, P->grp_ycols);
@@ -1008,7 +1011,7 @@ psatd_status build(psatd_plan* P, cudaStream_t st) {
         P->reg_zst = 0;
     }
     // the register z kernel has its own tile width: re-tile (jobs are grouped by box)
-    const int rt = z_reg_tile_width(P->form);
+    const int rt = P->reg_z ? z_reg_tile_width(P->form, P->reg_z) : tile;
     if (P->reg_z && rt != tile) {
       std::vector<ColJob> zt;
       int last = -1;
@@ -1742,7 +1745,8 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
     if (r != PSATD_OK) return r;
   }
   // S1 (z) + S2 + S3 (z)
-  if (P->z_one_launch && !P->zpen_reg.empty()) {
+  const bool one_launch = P->z_one_launch && P->zreg_multi;
+  if (one_launch) {
     // every register-z length in one persistent launch, 2 CTAs per SM
     CK(P, timed(P, 2, st, [&] {
          return launch_z_reg_multi(P->form, D, P->d_ws, S, P->d_zpen_reg, (int64_t)P->zpen_reg.size(),
@@ -1750,7 +1754,7 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
        }));
     ++launches;
   }
-  for (const auto& g : P->z_one_launch ? std::vector<psatd_plan::PenGroup>() : P->grp_zreg) {
+  for (const auto& g : one_launch ? std::vector<psatd_plan::PenGroup>() : P->grp_zreg) {
     CK(P, timed(P, 2, st, [&] {
          return launch_z_reg(P->form, D, P->d_ws, S, P->d_zpen_reg + g.start, g.count, g.code, 0, NFT, P->z_prefetch,
                              st);
@@ -2195,7 +2199,7 @@ int32_t psatd_plan_tuning(const psatd_plan* P, int32_t knob) {
     case PSATD_TUNE_REG_PLANES:
       return P->reg_planes_used ? P->reg_planes : -1;
     case PSATD_TUNE_Z_ONE_LAUNCH:
-      return P->zpen_reg.empty() ? -1 : P->z_one_launch;
+      return P->zreg_multi ? P->z_one_launch : -1;
     case PSATD_TUNE_Z_TILE:
       return (P->pen_boxes || (P->fast_boxes && !P->reg_z))
                  ? (P->z_tile > 0 ? std::min(P->z_tile, fast_tile(P->prec)) : fast_tile(P->prec))

@@ -281,10 +281,12 @@ PSATD_DECLARE_PLANE_PART(plane_part1)
 PSATD_DECLARE_PLANE_PART(plane_part2)
 PSATD_DECLARE_PLANE_PART(plane_part3)
 #undef PSATD_DECLARE_PLANE_PART
-// register z kernel (FP32, tiles of z_reg_tile_width(form) columns) for z length n2
+// register z kernel (FP32, tiles of z_reg_tile_width(form, n2) columns) for z
+// length n2 (thread pairs per column; thread quads for 128 and 192)
 int z_reg_ok(int n2);
+int z_reg_multi_ok(int n2);   // a length the persistent multi-length kernel takes
 int z_reg_smem(int form, int n2);
-int z_reg_tile_width(int form);
+int z_reg_tile_width(int form, int n2);
 // zst: n1 * (n0/2 + 1) shared by every box of the job list, else 0
 // pf_dist > 0: every CTA first prefetches into L2 the tile of the CTA
 // launched pf_dist blocks after it

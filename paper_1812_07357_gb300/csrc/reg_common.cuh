@@ -91,7 +91,8 @@ __device__ __forceinline__ void pair_join(float2* v, int half, Store&& st) {
 // Same join, results left in v: v[i] is output row i + half*NY/4 and v[NY/4 + i]
 // output row i + half*NY/4 + NY/2.  `mask`: the lanes taking part (both
 // members of every pair in it).
-template <int NY, int DIR>
+// LANEX: the lane distance of the two members (16 by default).
+template <int NY, int DIR, int LANEX = 16>
 __device__ __forceinline__ void pair_join_inplace(float2* v, int half, unsigned mask = 0xffffffffu) {
   constexpr int Q = NY / 4;
   static_for<0, Q>([&](auto ic) {
@@ -99,14 +100,37 @@ __device__ __forceinline__ void pair_join_inplace(float2* v, int half, unsigned 
     const float2 send = half ? v[i] : v[Q + i];
     const float2 keep = half ? v[Q + i] : v[i];
     float2 recv;
-    recv.x = __shfl_xor_sync(mask, send.x, 16);
-    recv.y = __shfl_xor_sync(mask, send.y, 16);
+    recv.x = __shfl_xor_sync(mask, send.x, LANEX);
+    recv.y = __shfl_xor_sync(mask, send.y, LANEX);
     const float2 e = half ? recv : keep;
     const float2 o = half ? keep : recv;
     const float2 w0 = root<NY, i, DIR>(), w1 = root<NY, Q + i, DIR>();
     const float2 t = cmul(o, half ? w1 : w0);
     v[i] = e + t;
     v[Q + i] = e - t;
+  });
+}
+
+// The inverse of the join (decimation in frequency): on entry the member
+// holds outputs v[i] = X[i + half*NY/4] and v[NY/4 + i] = X[i + half*NY/4 +
+// NY/2] of a length-NY transform; on exit v[k], k < NY/2, holds
+// (X[k] + (-1)^half X[k + NY/2]) w^(half k) (w = exp(DIR 2 pi i / NY)), whose
+// length-NY/2 DFT (sign DIR) gives the samples 2j + half.
+template <int NY, int DIR, int LANEX = 16>
+__device__ __forceinline__ void pair_split_inplace(float2* v, int half, unsigned mask = 0xffffffffu) {
+  constexpr int Q = NY / 4;
+  static_for<0, Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const float2 a = v[i], b = v[Q + i];
+    const float2 w0 = root<NY, i, DIR>(), w1 = root<NY, Q + i, DIR>();
+    const float2 a0 = a + b, a1 = cmul(a - b, half ? w1 : w0);
+    const float2 send = half ? a0 : a1;
+    const float2 keep = half ? a1 : a0;
+    float2 recv;
+    recv.x = __shfl_xor_sync(mask, send.x, LANEX);
+    recv.y = __shfl_xor_sync(mask, send.y, LANEX);
+    v[i] = half ? recv : keep;
+    v[Q + i] = half ? keep : recv;
   });
 }
 

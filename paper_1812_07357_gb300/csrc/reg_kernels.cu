@@ -44,14 +44,19 @@ __constant__ HalfTwiddles<48> kTw48 = half_twiddles<48>();
 __constant__ HalfTwiddles<60> kTw60 = half_twiddles<60>();
 __constant__ HalfTwiddles<80> kTw80 = half_twiddles<80>();
 __constant__ HalfTwiddles<120> kTw120 = half_twiddles<120>();
+__constant__ HalfTwiddles<128> kTw128 = half_twiddles<128>();
+__constant__ HalfTwiddles<192> kTw192 = half_twiddles<192>();
 template <int NZ>
 __device__ __forceinline__ float2 half_twiddle(int k) {
-  static_assert(NZ == 96 || NZ == 48 || NZ == 60 || NZ == 80 || NZ == 120, "register z lengths");
+  static_assert(NZ == 96 || NZ == 48 || NZ == 60 || NZ == 80 || NZ == 120 || NZ == 128 || NZ == 192,
+                "register z lengths");
   if constexpr (NZ == 96) return kTw96.w[k];
   else if constexpr (NZ == 48) return kTw48.w[k];
   else if constexpr (NZ == 60) return kTw60.w[k];
   else if constexpr (NZ == 80) return kTw80.w[k];
-  else return kTw120.w[k];
+  else if constexpr (NZ == 120) return kTw120.w[k];
+  else if constexpr (NZ == 128) return kTw128.w[k];
+  else return kTw192.w[k];
 }
 
 // mx columns (or Nyquist-column y rows) per z tile: 16 (128-byte rows of a
@@ -79,10 +84,10 @@ constexpr int z_reg_min_blocks() {
 // L2 prefetch of the input rows of z tile `job` (every slot, every z plane;
 // a row of at most TX complex values spans at most two 128-byte lines).
 // Nyquist-column tiles (scattered values) are not prefetched.
-template <int NZ, int FORM>
+template <int NZ, int FORM, int NT = z_reg_threads<FORM>()>
 __device__ __forceinline__ void prefetch_z_tile(const DevPlan& P, const float2* spec, int64_t sstride,
                                                 const ColJob& J) {
-  constexpr int FIN = fields_in(FORM), NT = z_reg_threads<FORM>();
+  constexpr int FIN = fields_in(FORM);
   if (J.nm < 0) return;
   const BoxDev bx = P.boxes[J.box];
   const int hx = P.shapes[bx.shape].hx;
@@ -92,6 +97,36 @@ __device__ __forceinline__ void prefetch_z_tile(const DevPlan& P, const float2* 
     const int row = r >> 1, s = row / NZ, z = row - s * NZ;
     const float2* a = g + s * sstride + z * zst + (r & 1) * (J.nm - 1);
     asm volatile("prefetch.global.L2::evict_last [%0];\n" ::"l"(a));
+  }
+}
+
+// k-space update of one z tile held in shared memory as the half-length
+// spectra of the even z samples (rows [0, NZ/2)) and of the odd ones (rows
+// [NZ/2, NZ)), pitch NP: column pair (2 tp, 2 tp + 1), tp = tid % (TX/2),
+// modes k and k + H for k = tid / (TX/2) + i NT/(TX/2) (unrolled), with the
+// radix-2 stages of both z transforms.  A pair whose second column is past
+// the tile computes it on dead data (clamped table indices) and only writes
+// dead shared memory.
+template <int NZ, int FORM, int TX, int NT, int NP>
+__device__ __forceinline__ void z_tile_update(const DevPlan& P, float2* buf, const ColJob& J, bool nyq, int nm, int n1,
+                                              const ShapeDev& sh, int nft) {
+  constexpr int H = NZ / 2, TP = TX / 2, ZS = NT / TP, NIT = (H + ZS - 1) / ZS;
+  static_assert(TX % 2 == 0 && NT % TP == 0, "column pairs");
+  const int tid = threadIdx.x;
+  const int tp = tid % TP, k0 = tid / TP;
+  const int ta = 2 * tp;
+  if (ta < nm) {
+    const int mxa = nyq ? J.m0 : J.m0 + ta, mya = nyq ? J.plane + ta : J.plane;
+    const int mxb = nyq ? J.m0 : mxa + 1, myb = nyq ? min(mya + 1, n1 - 1) : J.plane;
+    const ModeXY2 xy = mode_xy2(mxa, mya, mxb, myb, sh, P);
+#pragma unroll
+    for (int it = 0; it < NIT; ++it) {
+      const int k = k0 + it * ZS;
+      if (H % ZS == 0 || k < H) {
+        const float2 w = half_twiddle<NZ>(k);   // exp(-2 pi i k / NZ)
+        update_pair_z2<FORM, NZ>(buf + k * NP + ta, buf + (k + H) * NP + ta, TX, xy, k, w, nft, sh, P);
+      }
+    }
   }
 }
 
@@ -150,30 +185,7 @@ __device__ __forceinline__ void z_reg_tile_job(const DevPlan& P, float2* spec, i
     }
   }
   __syncthreads();
-  // k-space update of the column pair (2 tp, 2 tp + 1), tp = tid % (TX/2),
-  // modes k and k + H for k = tid / (TX/2) + i NT/(TX/2) (unrolled), with the
-  // radix-2 stages of both z transforms.  A pair whose second column is past
-  // the tile computes it on dead data (clamped table indices) and only writes
-  // dead shared memory.
-  {
-    constexpr int TP = TX / 2, ZS = NT / TP, NIT = (H + ZS - 1) / ZS;
-    static_assert(TX % 2 == 0 && NT % TP == 0, "column pairs");
-    const int tp = tid % TP, k0 = tid / TP;
-    const int ta = 2 * tp;
-    if (ta < nm) {
-      const int mxa = nyq ? J.m0 : J.m0 + ta, mya = nyq ? J.plane + ta : J.plane;
-      const int mxb = nyq ? J.m0 : mxa + 1, myb = nyq ? min(mya + 1, n1 - 1) : J.plane;
-      const ModeXY2 xy = mode_xy2(mxa, mya, mxb, myb, sh, P);
-#pragma unroll
-      for (int it = 0; it < NIT; ++it) {
-        const int k = k0 + it * ZS;
-        if (H % ZS == 0 || k < H) {
-          const float2 w = half_twiddle<NZ>(k);   // exp(-2 pi i k / NZ)
-          update_pair_z2<FORM, NZ>(buf + k * NP + ta, buf + (k + H) * NP + ta, TX, xy, k, w, nft, sh, P);
-        }
-      }
-    }
-  }
+  z_tile_update<NZ, FORM, TX, NT, NP>(P, buf, J, nyq, nm, n1, sh, nft);
   __syncthreads();
   // half-length inverse DFTs: member `half` gives the z samples 2m + half of
   // the output slots; threads of the remaining slots repeat the last output
@@ -243,9 +255,140 @@ __global__ void __launch_bounds__(z_reg_threads<FORM>(), z_reg_min_blocks<FORM>(
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Quad register z kernel, for z lengths whose half-length DFT is too long for
+// one thread's registers (128, 192): four threads per (slot, column), lanes
+// l, l ^ 8, l ^ 16, l ^ 24 of a warp (half = lane bit 4: even / odd z; sub =
+// lane bit 3), each holding the samples 4j + 2 sub + half and running their
+// length-NZ/4 DFT; the two sub members join their transforms by shuffles into
+// the half-length spectrum of their half (rows of the pair kernel's layout),
+// the update stage is the pair kernel's, and the inverse mirrors the forward
+// (split by shuffles, length-NZ/4 inverse DFTs, interior z planes stored).
+#define PSATD_REG_Z4(X) X(128) X(192)
+// columns per tile: 8 (the 6-slot vacuum form), 4 with sources
+constexpr int z_reg4_tile(int form) { return form == kVacuum ? 8 : 4; }
+template <int FORM>
+constexpr int z_reg4_threads() {
+  return (4 * fields_in(FORM) * z_reg4_tile(FORM) + 31) / 32 * 32;
+}
+constexpr int z_reg4_pitch(int form) {
+  return fields_in(form) * z_reg4_tile(form) + ((24 - (fields_in(form) * z_reg4_tile(form)) % 16) % 16);
+}
+
+template <int NZ, int FORM>
+__device__ __forceinline__ void z_reg4_tile_job(const DevPlan& P, float2* spec, int64_t sstride, const ColJob& J,
+                                                int nft, unsigned char* smem_raw) {
+  constexpr int TX = z_reg4_tile(FORM), FIN = fields_in(FORM), FOUT = fields_out(FORM);
+  constexpr int NT = z_reg4_threads<FORM>(), NP = z_reg4_pitch(FORM);
+  constexpr int H = NZ / 2, Q = NZ / 4, Q2 = NZ / 8;
+  static_assert(NZ % 8 == 0 && NT % (2 * TX) == 0, "quad z tile");
+  float2* buf = reinterpret_cast<float2*>(smem_raw);    // [row][slot * TX + t], pitch NP
+  const BoxDev bx = P.boxes[J.box];
+  const ShapeDev& sh = P.shapes[bx.shape];
+  const int hx = sh.hx, n1 = bx.n[1];
+  const int64_t zst = (int64_t)n1 * hx;
+  const bool nyq = J.nm < 0;
+  const int nm = nyq ? -J.nm : J.nm, ts = nyq ? hx : 1;
+  float2* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int half = (lane >> 4) & 1, sub = (lane >> 3) & 1, quad = (lane & 7) + ((tid >> 5) << 3);
+  const int s = quad / TX, t = quad - s * TX;
+  const bool live = t < nm && s < FIN;
+  const int tc = t < nm ? t : 0, sc = s < FIN ? s : FIN - 1;
+  const int zoff = 2 * sub + half;   // the member's samples: z = 4m + zoff
+  float2 v[Q];
+  {
+    const float2* src = g + sc * sstride + (int64_t)tc * ts + zoff * zst;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) v[m] = ld_l2_256(src + 4 * m * zst);
+  }
+  // forward: length-Q DFT, join of the two sub members into the half-length
+  // spectrum rows half * H + k, k in {sub Q2 + i, sub Q2 + i + Q}; slots >= nft
+  // hold a cached z spectrum in natural z order, stored as they are
+  float* bw = reinterpret_cast<float*>(buf);
+  const int q0 = 2 * s * TX + 4 * (t >> 1) + (t & 1);      // word of re in a re-first row
+  // the lanes that transform (both sub members of a quad share s): the
+  // shuffles of the join name exactly these
+  const unsigned fmask = __ballot_sync(0xffffffffu, s < nft);
+  if (s < nft) {
+    Dft<float, Q, -1>::run(v);
+    pair_join_inplace<H, -1, 8>(v, sub, fmask);
+    const int re = q0 + 2 * half, im = q0 + 2 - 2 * half;
+#pragma unroll
+    for (int i = 0; i < Q2; ++i) {
+      const int k1 = sub * Q2 + i, k2 = k1 + Q;
+      bw[(half * H + k1) * 2 * NP + re] = v[i].x;
+      bw[(half * H + k1) * 2 * NP + im] = v[i].y;
+      bw[(half * H + k2) * 2 * NP + re] = v[Q2 + i].x;
+      bw[(half * H + k2) * 2 * NP + im] = v[Q2 + i].y;
+    }
+  } else if (s < FIN) {
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      const int z = 4 * m + zoff, sw = z >= H ? 2 : 0;
+      bw[z * 2 * NP + q0 + sw] = v[m].x;
+      bw[z * 2 * NP + q0 + 2 - sw] = v[m].y;
+    }
+  }
+  __syncthreads();
+  z_tile_update<NZ, FORM, TX, NT, NP>(P, buf, J, nyq, nm, n1, sh, nft);
+  __syncthreads();
+  // inverse: the member's rows of its half, split by shuffles, length-Q
+  // inverse DFT -> the samples 4m + zoff of the output slots
+  {
+    const int so = s < FOUT ? s : FOUT - 1;
+    const int qo = 2 * so * TX + 4 * (t >> 1) + (t & 1);
+    const int re = qo + 2 * half, im = qo + 2 - 2 * half;
+#pragma unroll
+    for (int i = 0; i < Q2; ++i) {
+      const int k1 = sub * Q2 + i, k2 = k1 + Q;
+      v[i] = make_float2(bw[(half * H + k1) * 2 * NP + re], bw[(half * H + k1) * 2 * NP + im]);
+      v[Q2 + i] = make_float2(bw[(half * H + k2) * 2 * NP + re], bw[(half * H + k2) * 2 * NP + im]);
+    }
+  }
+  pair_split_inplace<H, 1, 8>(v, sub);
+  Dft<float, Q, 1>::run(v);
+  if (live && s < FOUT) {
+    const int zlo = bx.ng_lo[2], zhi = NZ - bx.ng_hi[2];
+    float2* dst = g + s * sstride + (int64_t)t * ts + zoff * zst;
+#pragma unroll
+    for (int m = 0; m < Q; ++m) {
+      const int z = 4 * m + zoff;
+      if (z >= zlo && z < zhi) dst[4 * m * zst] = v[m];
+    }
+  }
+}
+
+template <int NZ, int FORM>
+__global__ void __launch_bounds__(z_reg4_threads<FORM>(), 2)
+    k_z_reg4(DevPlan P, float2* spec, int64_t sstride, const ColJob* __restrict__ jobs, int nft, int njobs,
+             int pf_dist) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ColJob J = jobs[blockIdx.x];
+  if (pf_dist > 0 && (int)blockIdx.x + pf_dist < njobs)
+    prefetch_z_tile<NZ, FORM, z_reg4_threads<FORM>()>(P, spec, sstride, jobs[blockIdx.x + pf_dist]);
+  z_reg4_tile_job<NZ, FORM>(P, spec, sstride, J, nft, smem_raw);
+}
 }  // namespace
 
+static bool z_reg_quad(int n2) {
+#define PSATD_ZC(NZV) \
+  if (n2 == NZV) return true;
+  PSATD_REG_Z4(PSATD_ZC)
+#undef PSATD_ZC
+  return false;
+}
+
 int z_reg_ok(int n2) {
+#define PSATD_ZC(NZV) \
+  if (n2 == NZV) return 1;
+  PSATD_REG_Z(PSATD_ZC)
+#undef PSATD_ZC
+  return z_reg_quad(n2) ? 1 : 0;
+}
+
+int z_reg_multi_ok(int n2) {
 #define PSATD_ZC(NZV) \
   if (n2 == NZV) return 1;
   PSATD_REG_Z(PSATD_ZC)
@@ -253,9 +396,9 @@ int z_reg_ok(int n2) {
   return 0;
 }
 
-int z_reg_smem(int form, int n2) { return n2 * z_reg_pitch(form) * 8; }
+int z_reg_smem(int form, int n2) { return n2 * (z_reg_quad(n2) ? z_reg4_pitch(form) : z_reg_pitch(form)) * 8; }
 
-int z_reg_tile_width(int form) { return z_reg_tile(form); }
+int z_reg_tile_width(int form, int n2) { return z_reg_quad(n2) ? z_reg4_tile(form) : z_reg_tile(form); }
 
 // z strides with their own instantiation: the register plane shape 96 x 96
 constexpr int kRegZst = 96 * 49;
@@ -290,6 +433,20 @@ cudaError_t launch_z_reg(int form, const DevPlan& P, void* spec, int64_t sstride
   PSATD_REG_Z(PSATD_ZL)
 #undef PSATD_ZL
 #undef PSATD_ZF
+#define PSATD_ZL(NZV)                                                                                     \
+  if (n2 == NZV) {                                                                                       \
+    if (form == kVacuum)                                                                                 \
+      k_z_reg4<NZV, kVacuum><<<grid, z_reg4_threads<kVacuum>(), smem, st>>>(P, (float2*)spec, sstride, jobs, \
+                                                                            nft, (int)njobs, pf_dist);    \
+    else if (form == kJForm)                                                                             \
+      k_z_reg4<NZV, kJForm><<<grid, z_reg4_threads<kJForm>(), smem, st>>>(P, (float2*)spec, sstride, jobs,   \
+                                                                          nft, (int)njobs, pf_dist);      \
+    else                                                                                                 \
+      k_z_reg4<NZV, kRhoForm><<<grid, z_reg4_threads<kRhoForm>(), smem, st>>>(P, (float2*)spec, sstride,     \
+                                                                              jobs, nft, (int)njobs, pf_dist); \
+  }
+  PSATD_REG_Z4(PSATD_ZL)
+#undef PSATD_ZL
   return cudaGetLastError();
 }
 
@@ -403,6 +560,16 @@ cudaError_t configure_reg_kernels(int smem) {
   PSATD_ZA(NZV, kJForm, kRegZst)      \
   PSATD_ZA(NZV, kRhoForm, kRegZst)
   PSATD_REG_Z(PSATD_ZS)
+#undef PSATD_ZS
+#undef PSATD_ZA
+#define PSATD_ZA(NZV, F)                                                                                  \
+  if (z_reg_smem(F, NZV) <= smem) {                                                                       \
+    const cudaError_t r =                                                                                 \
+        cudaFuncSetAttribute(k_z_reg4<NZV, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, z_reg_smem(F, NZV)); \
+    if (r != cudaSuccess) e = r;                                                                          \
+  }
+#define PSATD_ZS(NZV) PSATD_ZA(NZV, kVacuum) PSATD_ZA(NZV, kJForm) PSATD_ZA(NZV, kRhoForm)
+  PSATD_REG_Z4(PSATD_ZS)
 #undef PSATD_ZS
 #undef PSATD_ZA
 #define PSATD_ZMA(F)                                                                                \

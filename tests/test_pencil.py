@@ -205,13 +205,15 @@ def test_pencil_local_192_boxes_and_hybrid_384_groups():
 @pytest.mark.parametrize("form", ["vacuum", "J", "rho"])
 def test_pencil_boxes_z_pass_on_register_kernel_and_shared_memory_kernel(form):
     """FP32 pencil boxes with z lengths 48, 60, 80, 96, 120 (the uneven
-    batch's): their z pass runs on the register z kernel, one launch per
-    length (default) or every length in one persistent launch, or on the
-    shared-memory pencil z kernel (tuning knobs); each against the oracle, and
-    against each other."""
+    batch's), 128 and 192: their z pass runs on the register z kernels
+    (thread pairs up to 120, thread quads for 128 and 192), one launch per
+    length (default) or, where every length has it, in one persistent launch,
+    or on the shared-memory pencil z kernel (tuning knobs); each against the
+    oracle, and against each other."""
     from paper_1812_07357_gb300.solver import Plan
-    sizes = [(160, 24, 48), (48, 160, 60), (60, 48, 80), (80, 60, 96), (48, 48, 120)]
-    boxes = [I.Box(n, (4, 4, 4), (4, 4, 4), (0, 0, 0), p) for n, p in zip(sizes, (8, 16, 32, 0, 16))]
+    sizes = [(160, 24, 48), (48, 160, 60), (60, 48, 80), (80, 60, 96), (48, 48, 120), (48, 60, 128),
+             (60, 48, 192)]
+    boxes = [I.Box(n, (4, 4, 4), (4, 4, 4), (0, 0, 0), p) for n, p in zip(sizes, (8, 16, 32, 0, 16, 8, 0))]
     lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
     rng = np.random.default_rng(28)
     if form != "vacuum":
@@ -235,8 +237,8 @@ def test_pencil_boxes_z_pass_on_register_kernel_and_shared_memory_kernel(form):
         plan = Plan(lay, (1.0,) * 3, 0.9, precision=32, sources=form, pencil=True, j_constant=form != "vacuum",
                     tuning=tuning)
         used = plan.tuning()
-        assert plan.pencil_boxes == 5 and used.get("pencil_reg_z") == tuning["pencil_reg_z"]
-        assert used.get("z_one_launch", -1) == tuning.get("z_one_launch", -1)
+        assert plan.pencil_boxes == 7 and used.get("pencil_reg_z") == tuning["pencil_reg_z"]
+        assert "z_one_launch" not in used     # 128 and 192 have no persistent multi-length kernel
         df = plan.pack_fields(fields)
         ds = plan.pack_fields(src) if form != "vacuum" else None
         plan.push(df, ds, 3)

@@ -183,22 +183,28 @@ def test_wide_planes_local_192_laser():
 
 @pytest.mark.parametrize("form", ["vacuum", "rho"])
 @pytest.mark.parametrize("sizes", [
-    # several z lengths: 128, 96, 60 on the shared-memory plane z kernel, 192 on the pencil z kernel
+    # several z lengths: 128, 96, 60, 192
     [(128, 128, 128), (128, 128, 192), (192, 192, 60), (128, 128, 96)],
-    # one z length with a register z kernel: 96 on the register z kernel
+    # one z length: 96
     [(128, 128, 96), (192, 192, 96)],
 ], ids=["mixed_z", "z96"])
-def test_wide_planes_with_every_z_route(form, sizes):
+@pytest.mark.parametrize("reg_z", [1, 0])
+def test_wide_planes_with_every_z_route(form, sizes, reg_z):
     """Self-periodic 128 x 128 and 192 x 192 planes with the z pass on each
-    of its kernels; against the oracle."""
+    of its kernels: the register z kernels (thread pairs for 60 and 96,
+    thread quads for 128 and 192; knob pencil_reg_z = 1), or the
+    shared-memory plane z kernel (lengths up to 128) and the pencil z kernel
+    (192) with the knob at 0; the one-length batch on the register z kernel
+    either way.  Against the oracle."""
     boxes = [I.Box(n, (6,) * 3, (6,) * 3, (0, 0, 0), p) for n, p in zip(sizes, (16, 0, 32, 8))]
     lay = I.Layout("independent", (0, 0, 0), (1, 1, 1), boxes)
     fields, src = _inputs(lay, form, 67)
     comps = O.COMPS + (("rho",) if form == "rho" else ())
     ref = O.push(lay, fields, src, 3, (1.0, 0.9, 1.1), 0.8, form=form)
-    got, (nfast, npen, deferred, _) = _push(lay, fields, src, form, 3)
+    got, (nfast, npen, deferred, tun) = _push(lay, fields, src, form, 3, tuning={"pencil_reg_z": reg_z})
     assert (nfast, npen) == (len(boxes), 0) and deferred
-    assert_fields(lay, got, ref, comps, 32, what=f"wide planes, {sizes}, {form} form")
+    assert tun.get("pencil_reg_z", -1) == (reg_z if len(sizes) == 4 else -1)
+    assert_fields(lay, got, ref, comps, 32, what=f"wide planes, {sizes}, {form} form, pencil_reg_z {reg_z}")
 
 
 def test_wide_planes_beside_shared_memory_planes():
