@@ -22,6 +22,8 @@
 // The shapes are instantiated in four translation units (reg_planes_<part>.cu,
 // PSATD_PLANE_PART = part), each taking its share of PSATD_REG_SHAPES.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "reg_common.cuh"
 
 namespace psatd {
@@ -648,6 +650,250 @@ __global__ void __launch_bounds__(wide_threads<L, NY>(), wide_min_blocks<L, NY>(
   plane_store<N0, NY, NT>(P, F, rows, J, f, bx, ylo, ni, xlo, nxi, vec_rows, seg_start, segs);
 }
 
+
+// ---------------------------------------------------------------------------
+// Split wide forward plane kernel (planes above 113 KB: the 192 x 192 plane):
+// a cluster of two CTAs per plane, CTA rank h holding rows [h NY/2, (h+1) NY/2)
+// in its shared memory (half the plane, so that two CTAs fit an SM and one
+// CTA's loads overlap the other's transforms).  Each CTA does the x pass of
+// its rows; after a cluster barrier, the y pass of its half of the columns,
+// reading the other half of the rows from the peer CTA's shared memory
+// (distributed shared memory); a second cluster barrier before the buffers
+// are reused for the y combination.
+template <int L, int NY>
+constexpr bool plane_is_split() {
+  return plane_is_wide<L, NY>() && NY * row_pitch(2 * L) * 4 > 113 * 1024;
+}
+template <int L, int NY>
+constexpr int split_cols() {   // columns of rank 0 (rank 1: the rest)
+  return (L + 2) / 2;
+}
+template <int L, int NY>
+constexpr int split_threads() {
+  constexpr int a = (NY / 2) * wide_gx<L, NY>(), b = split_cols<L, NY>() * wide_gy<L, NY>();
+  return ((a > b ? a : b) + 31) / 32 * 32;
+}
+template <int L, int NY>
+constexpr int split_smem() {
+  constexpr int rows = (NY / 2) * row_pitch(2 * L) * 4, cols = NY * split_cols<L, NY>() * 8;
+  return rows > cols ? rows : cols;
+}
+
+// Rows [r0, r0 + NR) of the real N0 x NY plane J.y of field f into shared
+// memory (row r at buf + (r - r0) * row_pitch(N0)), by NT threads, as
+// plane_load (pj: the plane job's index in the gather tables).
+template <int N0, int NY, int NT, int NR>
+__device__ __forceinline__ void plane_load_rows(const FieldPtrs& F, float* buf, const int2& J, int f,
+                                                const BoxDev& bx, int pj, int r0,
+                                                const int* __restrict__ gstart, const GatherSeg* __restrict__ gsegs,
+                                                const GatherGrid* __restrict__ ggrid, int ngather) {
+  constexpr int PF = row_pitch(N0);
+  constexpr int UPR = N0 / 4;
+  const int r1 = r0 + NR;
+  if (ggrid && f < ngather) {
+    constexpr int RG = NT / UPR;
+    __shared__ GatherGrid gg;
+    static_assert(sizeof(GatherGrid) / 4 <= NT, "one word per thread");
+    if (threadIdx.x < sizeof(GatherGrid) / 4)
+      reinterpret_cast<int*>(&gg)[threadIdx.x] = reinterpret_cast<const int*>(ggrid + pj)[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x < RG * UPR) {
+      const float* fb = reinterpret_cast<const float*>(F.p[f]);
+      const int c = threadIdx.x % UPR, rg = threadIdx.x / UPR, x = 4 * c;
+      const int ix = (x >= gg.x1) + (x >= gg.x2);
+      const int xo = x - (ix == 0 ? 0 : ix == 1 ? gg.x1 : gg.x2);
+#pragma unroll
+      for (int iy = 0; iy < 3; ++iy) {   // row bands [ylo, yhi), clipped to [r0, r1)
+        const int ylo = iy == 0 ? 0 : iy == 1 ? gg.y1 : gg.y2;
+        const int yhi = iy == 0 ? gg.y1 : iy == 1 ? gg.y2 : NY;
+        const int a = max(ylo, r0), b = min(yhi, r1);
+        int r = a + (rg - a % RG + RG) % RG;   // first row >= a with r % RG == rg
+        const int pitch = gg.pitch[3 * iy + ix];
+        const float* src = fb + gg.base[3 * iy + ix] + (int64_t)(r - ylo) * pitch + xo;
+        const int64_t sstep = (int64_t)RG * pitch;
+        for (float* dst = buf + (r - r0) * PF + x; r < b; r += RG, src += sstep, dst += RG * PF) cp16(dst, src);
+      }
+    }
+  } else if (gstart && f < ngather) {
+    __shared__ GatherSeg tab[kGatherTab];
+    const float* fb = reinterpret_cast<const float*>(F.p[f]);
+    const int s0 = gstart[pj], ns = gstart[pj + 1] - s0;
+    if (threadIdx.x < kGatherTab && threadIdx.x < ns) tab[threadIdx.x] = gsegs[s0 + threadIdx.x];
+    __syncthreads();
+    for (int i = 0; i < ns; ++i) {
+      const GatherSeg gs = i < kGatherTab ? tab[i] : gsegs[s0 + i];
+      const int a = max(gs.dy, r0), b = min(gs.dy + gs.ny, r1);
+      if (a >= b) continue;
+      const int ny = b - a;
+      const float* src = fb + gs.src_off + (int64_t)(a - gs.dy) * gs.spitch;
+      float* dst = buf + (a - r0) * PF + gs.dx;
+      if (gs.vec) {
+        const int upr = gs.nx >> 2;
+        const unsigned m = magic(upr);
+        for (int u = threadIdx.x; u < ny * upr; u += NT) {
+          const int r = fdiv(u, m), c = 4 * (u - r * upr);
+          cp16(dst + r * PF + c, src + (int64_t)r * gs.spitch + c);
+        }
+      } else {
+        const unsigned m = magic(gs.nx);
+        for (int u = threadIdx.x; u < ny * gs.nx; u += NT) {
+          const int r = fdiv(u, m), c = u - r * gs.nx;
+          cp4(dst + r * PF + c, src + (int64_t)r * gs.spitch + c);
+        }
+      }
+    }
+  } else {
+    const float* g = reinterpret_cast<const float*>(F.p[f]) + bx.foff + ((int64_t)J.y * NY + r0) * N0;
+    for (int u = threadIdx.x; u < NR * UPR; u += NT) {
+      const int r = u / UPR, x = u - r * UPR;
+      cp16(buf + r * PF + 4 * x, g + 4 * u);
+    }
+  }
+  cp_commit_wait_all();
+  __syncthreads();
+}
+
+template <int L, int NY>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(split_threads<L, NY>(), 2)
+    k_plane_fwd_split(DevPlan P, FieldPtrs F, float2* spec, int64_t sstride, const int2* __restrict__ jobs,
+                      const int* __restrict__ gstart, const GatherSeg* __restrict__ gsegs,
+                      const GatherGrid* __restrict__ ggrid, int ngather) {
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0), PC = PF / 2;
+  constexpr int GX = wide_gx<L, NY>(), GY = wide_gy<L, NY>(), NT = split_threads<L, NY>();
+  constexpr int LX = L / GX, LY = NY / GY, LXP = GX > 1 ? LX + 1 : LX;
+  constexpr int NH = NY / 2, C0 = split_cols<L, NY>(), CP = C0;
+  static_assert(GX == 2 && NY % (2 * GY) == 0 && LY % GY == 0 && GX * LXP <= PC && LY % 2 == 0,
+                "split wide plane shape");
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* buf = reinterpret_cast<float*>(smem_raw);
+  float2* cb = reinterpret_cast<float2*>(smem_raw);
+  const int h = (int)cluster.block_rank();
+  const int pj = blockIdx.x >> 1;
+  const int2 J = jobs[pj];
+  const int f = blockIdx.y;
+  const BoxDev bx = P.boxes[J.x];
+  plane_load_rows<N0, NY, NT, NH>(F, buf, J, f, bx, pj, h * NH, gstart, gsegs, ggrid, ngather);
+  const int t = threadIdx.x;
+  // x, stage 1 on the CTA's rows (as k_plane_fwd_wide)
+  {
+    const int r = t / GX, q = t - r * GX;
+    const bool live = r < NH;
+    float2 v[LX];
+    if (live) {
+      const float2* row = cb + r * PC;
+#pragma unroll
+      for (int j = 0; j < LX; ++j) v[j] = row[q + GX * j];
+      Dft<float, LX, -1>::run(v);
+      static_for<1, LX>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        v[k] = cmul(v[k], root_q<L, k, GX, -1>(q));
+      });
+    }
+    __syncthreads();
+    if (live) {
+      float2* row = cb + r * PC + q * LXP;
+#pragma unroll
+      for (int k = 0; k < LX; ++k) row[k] = v[k];
+    }
+  }
+  __syncthreads();
+  // x, stage 2: combination and R2C split (as k_plane_fwd_wide)
+  {
+    const int r = t / GX, q = t - r * GX;
+    const bool live = r < NH;
+    constexpr int NK = (L / 2 + GX) / GX;
+    float2 lo[NK], hi[NK];
+    if (live) {
+      const float2* row = cb + r * PC;
+      auto zval = [&](int k) {
+        const int kk = k % LX, p = k / LX;
+        const float2 a0 = row[kk], a1 = row[LXP + kk];
+        return p ? a0 - a1 : a0 + a1;
+      };
+      static_for<0, NK>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        const int k = q + GX * j;
+        if (k <= L / 2) {
+          const float2 a = zval(k), b = zval((L - k) % L);
+          const float2 A = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+          const float2 Bv = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
+          const float2 wk = q == 1 ? root<N0, GX * j + 1, -1>() : root<N0, GX * j, -1>();
+          const float2 wl = q == 1 ? root<N0, L - GX * j - 1, -1>() : root<N0, L - GX * j, -1>();
+          if (k == 0) {
+            lo[j] = make_float2(A.x + Bv.x, A.y + Bv.y);
+            hi[j] = make_float2(A.x - Bv.x, A.y - Bv.y);
+          } else {
+            lo[j] = A + cmul(wk, Bv);
+            hi[j] = conjg(A) + cmul(wl, conjg(Bv));
+          }
+        }
+      });
+    }
+    __syncthreads();
+    if (live) {
+      float2* row = cb + r * PC;
+      static_for<0, NK>([&](auto jc) {
+        constexpr int j = decltype(jc)::value;
+        const int k = q + GX * j;
+        if (k <= L / 2) {
+          row[k] = lo[j];
+          if (k == 0) row[L] = hi[j];
+          else if (2 * k != L) row[L - k] = hi[j];
+        }
+      });
+    }
+  }
+  // every row of both halves transformed along x
+  cluster.sync();
+  // y, stage 1: thread (column c of this CTA's half, q): rows q + GY j, the
+  // first NH/GY of them in rank 0's buffer, the rest in rank 1's
+  const int c0 = h * C0, ncols = h ? HX - C0 : C0;
+  const int q = t / CP, cl = t - q * CP;
+  const bool ylive = q < GY && cl < ncols;
+  float2 v[LY];
+  {
+    const float2* half0 = cluster.map_shared_rank(cb, 0);
+    const float2* half1 = cluster.map_shared_rank(cb, 1);
+    const int c = c0 + (ylive ? cl : 0);
+    if (q < GY) {
+#pragma unroll
+      for (int j = 0; j < LY; ++j) {
+        const int rr = q + GY * j;   // compile-time owner: rows < NH in rank 0
+        v[j] = (j < LY / 2 ? half0 : half1)[(j < LY / 2 ? rr : rr - NH) * PC + c];
+      }
+      Dft<float, LY, -1>::run(v);
+      static_for<1, LY>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        v[k] = cmul(v[k], root_q<NY, k, GY, -1>(q));
+      });
+    }
+  }
+  // both CTAs have read what they need of the other's rows
+  cluster.sync();
+  if (ylive) {
+#pragma unroll
+    for (int k = 0; k < LY; ++k) cb[(q * LY + k) * CP + cl] = v[k];
+  }
+  __syncthreads();
+  // y, stage 2: combination, rows k + LY p of the spectrum plane, this CTA's columns
+  if (ylive) {
+    float2* out = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX + c0 + cl;
+    constexpr int KQ = LY / GY;
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) {
+      const int k = q * KQ + i;
+      float2 a[GY];
+#pragma unroll
+      for (int p = 0; p < GY; ++p) a[p] = cb[(p * LY + k) * CP + cl];
+      Dft<float, GY, -1>::run(a);
+#pragma unroll
+      for (int p = 0; p < GY; ++p) out[(k + LY * p) * HX] = a[p];
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -674,7 +920,10 @@ bool plane_fwd_shape(int code, dim3 grid, const DevPlan& P, const FieldPtrs& f, 
                      int ngather, cudaStream_t st) {
   if constexpr (PART == PSATD_PLANE_PART) {
     if (code != CODE) return false;
-    if constexpr (plane_is_wide<L, NY>())
+    if constexpr (plane_is_split<L, NY>())
+      k_plane_fwd_split<L, NY><<<dim3(2 * grid.x, grid.y), split_threads<L, NY>(), split_smem<L, NY>(), st>>>(
+          P, f, (float2*)spec, sstride, jobs, gstart, gsegs, ggrid, ngather);
+    else if constexpr (plane_is_wide<L, NY>())
       k_plane_fwd_wide<L, NY><<<grid, wide_threads<L, NY>(), plane_fwd_bytes<L, NY>(), st>>>(
           P, f, (float2*)spec, sstride, jobs, gstart, gsegs, ggrid, ngather);
     else
@@ -708,7 +957,12 @@ void plane_configure_shape(int smem, cudaError_t* e) {
   if constexpr (PART == PSATD_PLANE_PART) {
     if (plane_fwd_bytes<L, NY>() > smem || plane_inv_bytes<L, NY>() > smem) return;
     cudaError_t r, r2;
-    if constexpr (plane_is_wide<L, NY>()) {
+    if constexpr (plane_is_split<L, NY>()) {
+      r = cudaFuncSetAttribute(k_plane_fwd_split<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               split_smem<L, NY>());
+      r2 = cudaFuncSetAttribute(k_plane_inv_wide<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                plane_inv_bytes<L, NY>());
+    } else if constexpr (plane_is_wide<L, NY>()) {
       r = cudaFuncSetAttribute(k_plane_fwd_wide<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                plane_fwd_bytes<L, NY>());
       r2 = cudaFuncSetAttribute(k_plane_inv_wide<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
