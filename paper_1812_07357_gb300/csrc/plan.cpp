@@ -1723,6 +1723,31 @@ static psatd_status transform_current(psatd_plan* P, const DevPlan& D, const Fie
   void* spec = static_cast<char*>(P->d_ws) + (size_t)nft * P->spec_total * P->csize;
   const psatd_status r = forward_xy(P, D, fj, 3, spec, st, launches_out);
   if (r != PSATD_OK) return r;
+  // z: the register z-forward kernel over the step's register z tiles when
+  // every box's z pass is a thread-pair register z kernel with 8-column tiles,
+  // else the generic column kernel
+  const int rt = z_reg_tile_width(P->form, P->reg_z ? P->reg_z : 48);
+  const bool zreg = P->prec == 32 && P->zpen.empty() && P->g_zcols.empty() && rt == 8 &&
+                    (P->zfast.empty() || (P->reg_z && z_reg_multi_ok(P->reg_z))) &&
+                    std::all_of(P->grp_zreg.begin(), P->grp_zreg.end(),
+                                [](const auto& g) { return z_reg_multi_ok(g.code) != 0; }) &&
+                    (!P->zfast.empty() || !P->zpen_reg.empty());
+  if (zreg) {
+    for (const auto& g : P->grp_zreg) {
+      CK(P, timed(P, 2, st, [&] {
+           return launch_z_fwd_pair(D, spec, P->spec_total, P->d_zpen_reg + g.start, g.count, g.code, rt, 3, st);
+         }));
+      ++*launches_out;
+    }
+    if (!P->zfast.empty()) {
+      CK(P, timed(P, 2, st, [&] {
+           return launch_z_fwd_pair(D, spec, P->spec_total, P->d_zfast, (int64_t)P->zfast.size(), P->reg_z, rt, 3,
+                                    st);
+         }));
+      ++*launches_out;
+    }
+    return PSATD_OK;
+  }
   CK(P, timed(P, 2, st, [&] {
        return launch_col(P->prec, -1, 2, D, spec, P->spec_total, 3, P->d_zcols, (int64_t)P->zcols.size(),
                          P->smem_zonly, st);

@@ -287,6 +287,11 @@ int z_reg_ok(int n2);
 int z_reg_multi_ok(int n2);   // a length the persistent multi-length kernel takes
 int z_reg_smem(int form, int n2);
 int z_reg_tile_width(int form, int n2);
+// z-only forward FFT (natural z order) of slots [0, ns) of `spec` over the z
+// tiles `jobs` (tile columns `tile`, 8 required; n2 a thread-pair register z
+// length; 2 * ns * tile <= 64)
+cudaError_t launch_z_fwd_pair(const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs, int64_t njobs,
+                              int n2, int tile, int ns, cudaStream_t st);
 // zst: n1 * (n0/2 + 1) shared by every box of the job list, else 0
 // pf_dist > 0: every CTA first prefetches into L2 the tile of the CTA
 // launched pf_dist blocks after it

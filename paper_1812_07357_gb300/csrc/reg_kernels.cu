@@ -370,6 +370,46 @@ __global__ void __launch_bounds__(z_reg4_threads<FORM>(), 2)
     prefetch_z_tile<NZ, FORM, z_reg4_threads<FORM>()>(P, spec, sstride, jobs[blockIdx.x + pf_dist]);
   z_reg4_tile_job<NZ, FORM>(P, spec, sstride, J, nft, smem_raw);
 }
+
+// ---------------------------------------------------------------------------
+// z-only forward FFT in natural z order of `ns` slots (from slot 0 of `spec`)
+// over z tiles of boxes with a thread-pair register z length: the spectrum of
+// a constant current, computed once per push.  Thread pair per (slot,
+// column): member `half` holds the samples 2m + half, runs their half-length
+// DFT, and the pair joins by shuffles (lanes l, l ^ 16) into the outputs
+// i + half NZ/4 and i + half NZ/4 + NZ/2, stored to every z plane.
+constexpr int kZfwdTile = 8;   // columns per tile: the job lists' width with sources
+template <int NZ>
+__global__ void __launch_bounds__(64) k_z_fwd_pair(DevPlan P, float2* spec, int64_t sstride,
+                                                   const ColJob* __restrict__ jobs, int ns) {
+  constexpr int H = NZ / 2, Q = NZ / 4;
+  static_assert(NZ % 4 == 0, "pair join");
+  const ColJob J = jobs[blockIdx.x];
+  const BoxDev bx = P.boxes[J.box];
+  const int hx = P.shapes[bx.shape].hx;
+  const int64_t zst = (int64_t)bx.n[1] * hx;
+  const bool nyq = J.nm < 0;
+  const int nm = nyq ? -J.nm : J.nm, ts = nyq ? hx : 1;
+  float2* g = spec + bx.soff + (int64_t)J.plane * hx + J.m0;
+  const int tid = threadIdx.x, half = pair_half(tid), col = pair_index(tid);
+  const int s = col / kZfwdTile, t = col - s * kZfwdTile;
+  const bool live = t < nm && s < ns;
+  const int tc = t < nm ? t : 0, sc = s < ns ? s : ns - 1;
+  float2 v[H];
+  const float2* src = g + sc * sstride + (int64_t)tc * ts + half * zst;
+#pragma unroll
+  for (int m = 0; m < H; ++m) v[m] = src[2 * m * zst];
+  Dft<float, H, -1>::run(v);
+  pair_join_inplace<NZ, -1>(v, half);
+  if (live) {
+    float2* dst = g + s * sstride + (int64_t)t * ts;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      dst[(i + half * Q) * zst] = v[i];
+      dst[(i + half * Q + H) * zst] = v[Q + i];
+    }
+  }
+}
 }  // namespace
 
 static bool z_reg_quad(int n2) {
@@ -394,6 +434,21 @@ int z_reg_multi_ok(int n2) {
   PSATD_REG_Z(PSATD_ZC)
 #undef PSATD_ZC
   return 0;
+}
+
+cudaError_t launch_z_fwd_pair(const DevPlan& P, void* spec, int64_t sstride, const ColJob* jobs, int64_t njobs,
+                              int n2, int tile, int ns, cudaStream_t st) {
+  if (njobs <= 0) return cudaSuccess;
+  if (tile != kZfwdTile || ns < 1 || 2 * ns * kZfwdTile > 64) return cudaErrorInvalidValue;
+  bool hit = false;
+#define PSATD_ZW(NZV)                                                                                       \
+  if (n2 == NZV) {                                                                                         \
+    k_z_fwd_pair<NZV><<<(unsigned)njobs, 64, 0, st>>>(P, (float2*)spec, sstride, jobs, ns);                  \
+    hit = true;                                                                                            \
+  }
+  PSATD_REG_Z(PSATD_ZW)
+#undef PSATD_ZW
+  return hit ? cudaGetLastError() : cudaErrorInvalidValue;
 }
 
 int z_reg_smem(int form, int n2) { return n2 * (z_reg_quad(n2) ? z_reg4_pitch(form) : z_reg_pitch(form)) * 8; }
