@@ -41,11 +41,25 @@ namespace psatd {
 
 namespace {
 
-// resident CTAs per SM the register budget is cut for: 4 up to the 96 x 96
-// plane (128 registers per thread), 3 above (168)
+// Threads of the narrow plane kernels: one per row of the plane (x) and a
+// pair per complex column of the y pass, where the two real columns (mx = 0
+// and the x Nyquist column mx = L) share one complex column, so L columns
+// take 2 L threads; rounded up to whole warps.
+template <int L, int NY>
+constexpr int reg_plane_threads() {
+  return ((NY > 2 * L ? NY : 2 * L) + 31) / 32 * 32;
+}
+// register budget per thread: 128 up to the 96 x 96 plane, 168 above; the
+// resident CTAs per SM that budget allows (at most 8)
+template <int L, int NY>
+constexpr int reg_plane_regs() {
+  return (L <= 48 && NY <= 96) ? 128 : 168;
+}
 template <int L, int NY>
 constexpr int reg_plane_min_blocks() {
-  return (L <= 48 && NY <= 96) ? 4 : 3;
+  return 65536 / (reg_plane_threads<L, NY>() * reg_plane_regs<L, NY>()) < 8
+             ? 65536 / (reg_plane_threads<L, NY>() * reg_plane_regs<L, NY>())
+             : 8;
 }
 
 // The real N0 x NY plane J.y of field f into shared memory (pitch
@@ -126,18 +140,19 @@ __device__ __forceinline__ void plane_load(const DevPlan& P, const FieldPtrs& F,
 
 // ---------------------------------------------------------------------------
 template <int L, int NY>
-__global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>())
+__global__ void __launch_bounds__(reg_plane_threads<L, NY>(), reg_plane_min_blocks<L, NY>())
     k_plane_fwd_reg(DevPlan P, FieldPtrs F, float2* spec, int64_t sstride, const int2* __restrict__ jobs,
                     const int* __restrict__ gstart, const GatherSeg* __restrict__ gsegs,
                     const GatherGrid* __restrict__ ggrid, int ngather) {
-  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0);
-  static_assert(NY <= kRegThreads && 2 * HX <= kRegThreads, "one thread per row / per half column");
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0), NT = reg_plane_threads<L, NY>();
+  static_assert(NY <= NT && 2 * L <= NT, "one thread per row / per half column");
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float2 wsc[NY];   // y transform of the packed real columns
   float* buf = reinterpret_cast<float*>(smem_raw);
   const int2 J = jobs[blockIdx.x];
   const int f = blockIdx.y;
   const BoxDev bx = P.boxes[J.x];
-  plane_load<N0, NY, kRegThreads>(P, F, buf, J, f, bx, gstart, gsegs, ggrid, ngather);
+  plane_load<N0, NY, NT>(P, F, buf, J, f, bx, gstart, gsegs, ggrid, ngather);
   // x: row r -> half spectrum X[0..L] written back into the same row
   if (threadIdx.x < NY) {
     float* row = buf + threadIdx.x * PF;
@@ -157,8 +172,10 @@ __global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>())
       const float2 A = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
       const float2 Bv = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
       if constexpr (k == 0) {
-        xr[0] = make_float2(A.x + Bv.x, A.y + Bv.y);
-        xr[L] = make_float2(A.x - Bv.x, A.y - Bv.y);
+        // X[0] and X[L] of a real row are real: stored together as the
+        // complex value X[0] + i X[L] of column 0 (the y pass transforms the
+        // two real columns as one complex column)
+        xr[0] = make_float2(A.x + Bv.x, A.x - Bv.x);
       } else {
         xr[k] = A + cmul(root<N0, k, -1>(), Bv);
         if constexpr (2 * k != L) xr[L - k] = conjg(A) + cmul(root<N0, L - k, -1>(), conjg(Bv));
@@ -166,21 +183,36 @@ __global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>())
     });
   }
   __syncthreads();
-  // y: thread pair per column c; threads past the last column repeat it
+  // y: thread pair per complex column c in [0, L), column 0 holding the two
+  // real columns X[.][0] + i X[.][L]; pairs past L repeat column 0 and store
+  // nothing.  The packed pair stores its transform in shared memory.
   {
     const int t = threadIdx.x;
-    const int half = pair_half(t);
-    const int c = min(pair_index(t), HX - 1);
-    const bool live = pair_index(t) < HX;
+    const int half = pair_half(t), p = pair_index(t);
+    const bool packed = p == 0, live = p < L;
+    const int c = live ? p : 0;
     const float2* xs = reinterpret_cast<const float2*>(buf);
     float2 v[NY / 2];
 #pragma unroll
     for (int m = 0; m < NY / 2; ++m) v[m] = xs[(2 * m + half) * (PF / 2) + c];
     Dft<float, NY / 2, -1>::run(v);
-    float2* out = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX + c;
+    float2* out = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX;
+    float2* dst = packed ? wsc : out + c;
+    const int ds = packed ? 1 : HX;
     pair_join<NY, -1>(v, half, [&](int y, float2 val) {
-      if (live) out[y * HX] = val;
+      if (live) dst[y * ds] = val;
     });
+    // the packed pair is lanes 0 and 16 of warp 0: warp 0 splits its transform
+    // W = F0 + i FL into the spectra of the two real columns,
+    // F0[k] = (W[k] + conj W[-k])/2, FL[k] = (W[k] - conj W[-k])/(2i)
+    if (t < 32) {
+      __syncwarp();
+      for (int k = t; k < NY; k += 32) {
+        const float2 a = wsc[k], b = wsc[k == 0 ? 0 : NY - k];
+        out[k * HX] = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+        out[k * HX + L] = make_float2(0.5f * (a.y + b.y), 0.5f * (b.x - a.x));
+      }
+    }
   }
 }
 
@@ -232,11 +264,11 @@ __device__ __forceinline__ void plane_store(const DevPlan& P, const FieldPtrs& F
 }
 
 template <int L, int NY>
-__global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>()) k_plane_inv_reg(DevPlan P, FieldPtrs F, const float2* spec,
-                                                                  int64_t sstride, const int2* __restrict__ jobs,
-                                                                  const int* __restrict__ seg_start,
-                                                                  const GuardSeg* __restrict__ segs) {
-  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0), Q = NY / 4;
+__global__ void __launch_bounds__(reg_plane_threads<L, NY>(), reg_plane_min_blocks<L, NY>())
+    k_plane_inv_reg(DevPlan P, FieldPtrs F, const float2* spec, int64_t sstride, const int2* __restrict__ jobs,
+                    const int* __restrict__ seg_start, const GuardSeg* __restrict__ segs) {
+  constexpr int N0 = 2 * L, HX = L + 1, PF = row_pitch(N0), Q = NY / 4, NT = reg_plane_threads<L, NY>();
+  static_assert(NY <= NT && 2 * L <= NT, "one thread per row / per half column");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // one buffer: first the NY x HX spectrum plane (pitch HX), then, once it is
   // consumed, the interior rows (pitch PF floats): X values, then real cells
@@ -249,14 +281,24 @@ __global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>()) k_
   const int xlo = bx.ng_lo[0], nxi = N0 - bx.ng_lo[0] - bx.ng_hi[0];
   const float2* g = spec + f * sstride + bx.soff + (int64_t)J.y * NY * HX;
   constexpr int UNITS = NY * HX / 2;   // 16-byte units of the contiguous plane
-  for (int u = threadIdx.x; u < UNITS; u += kRegThreads) cp16(sp + 2 * u, g + 2 * u);
+  for (int u = threadIdx.x; u < UNITS; u += NT) cp16(sp + 2 * u, g + 2 * u);
   cp_commit_wait_all();
   __syncthreads();
-  // y: thread pair per column, inverse; outputs kept in v until the plane is consumed
+  // column 0 <- X[.][0] + i X[.][L]: the two columns whose y transforms are
+  // real (Hermitian in y), transformed as one complex column
+  if (threadIdx.x < NY) {
+    const float2 a = sp[threadIdx.x * HX], b = sp[threadIdx.x * HX + L];
+    sp[threadIdx.x * HX] = make_float2(a.x - b.y, a.y + b.x);
+  }
+  __syncthreads();
+  // y: thread pair per complex column c in [0, L), inverse (column 0: the
+  // real and imaginary parts of its result are the two real columns, left
+  // packed as x0 + i xL); pairs past L repeat column 0 and store nothing.
+  // Outputs kept in v until the plane is consumed.
   const int t = threadIdx.x;
-  const int half = pair_half(t);
-  const int c = min(pair_index(t), HX - 1);
-  const bool live = pair_index(t) < HX;
+  const int half = pair_half(t), p = pair_index(t);
+  const bool live = p < L;
+  const int c = live ? p : 0;
   float2 v[NY / 2];
 #pragma unroll
   for (int m = 0; m < NY / 2; ++m) v[m] = sp[(2 * m + half) * HX + c];
@@ -281,13 +323,18 @@ __global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>()) k_
     float* row = rows + threadIdx.x * PF;
     const float2* xr = reinterpret_cast<const float2*>(row);
     float2 z[L];
-    // Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), w = exp(-2 pi i / N0)
+    // Z'[k] = (X[k] + conj X[L-k]) + i w^-k (X[k] - conj X[L-k]), w = exp(-2 pi i / N0);
+    // k = 0 from the real X[0], X[L] packed in column 0: Z'[0] = (X0 + XL) + i (X0 - XL)
     static_for<0, L / 2 + 1>([&](auto kc) {
       constexpr int k = decltype(kc)::value;
-      const float2 a = xr[k], b = xr[L - k];
-      z[k] = (a + conjg(b)) + times_i(cmul(a - conjg(b), root<N0, k, 1>()));
-      if constexpr (k != 0 && 2 * k != L)
-        z[L - k] = (b + conjg(a)) + times_i(cmul(b - conjg(a), root<N0, L - k, 1>()));
+      if constexpr (k == 0) {
+        const float2 a = xr[0];
+        z[0] = make_float2(a.x + a.y, a.x - a.y);
+      } else {
+        const float2 a = xr[k], b = xr[L - k];
+        z[k] = (a + conjg(b)) + times_i(cmul(a - conjg(b), root<N0, k, 1>()));
+        if constexpr (2 * k != L) z[L - k] = (b + conjg(a)) + times_i(cmul(b - conjg(a), root<N0, L - k, 1>()));
+      }
     });
     Dft<float, L, 1>::run(z);
     float* o = row - xlo;
@@ -309,7 +356,7 @@ __global__ void __launch_bounds__(kRegThreads, reg_plane_min_blocks<L, NY>()) k_
     }
   }
   __syncthreads();
-  plane_store<N0, NY, kRegThreads>(P, F, rows, J, f, bx, ylo, ni, xlo, nxi, vec_rows, seg_start, segs);
+  plane_store<N0, NY, NT>(P, F, rows, J, f, bx, ylo, ni, xlo, nxi, vec_rows, seg_start, segs);
 }
 
 // ---------------------------------------------------------------------------
@@ -927,8 +974,8 @@ bool plane_fwd_shape(int code, dim3 grid, const DevPlan& P, const FieldPtrs& f, 
       k_plane_fwd_wide<L, NY><<<grid, wide_threads<L, NY>(), plane_fwd_bytes<L, NY>(), st>>>(
           P, f, (float2*)spec, sstride, jobs, gstart, gsegs, ggrid, ngather);
     else
-      k_plane_fwd_reg<L, NY><<<grid, kRegThreads, plane_fwd_bytes<L, NY>(), st>>>(P, f, (float2*)spec, sstride,
-                                                                                 jobs, gstart, gsegs, ggrid, ngather);
+      k_plane_fwd_reg<L, NY><<<grid, reg_plane_threads<L, NY>(), plane_fwd_bytes<L, NY>(), st>>>(
+          P, f, (float2*)spec, sstride, jobs, gstart, gsegs, ggrid, ngather);
     return true;
   } else {
     return false;
@@ -944,8 +991,8 @@ bool plane_inv_shape(int code, dim3 grid, const DevPlan& P, const FieldPtrs& f, 
       k_plane_inv_wide<L, NY><<<grid, wide_threads<L, NY>(), plane_inv_bytes<L, NY>(), st>>>(
           P, f, (const float2*)spec, sstride, jobs, seg_start, segs);
     else
-      k_plane_inv_reg<L, NY><<<grid, kRegThreads, plane_inv_bytes<L, NY>(), st>>>(P, f, (const float2*)spec,
-                                                                                 sstride, jobs, seg_start, segs);
+      k_plane_inv_reg<L, NY><<<grid, reg_plane_threads<L, NY>(), plane_inv_bytes<L, NY>(), st>>>(
+          P, f, (const float2*)spec, sstride, jobs, seg_start, segs);
     return true;
   } else {
     return false;
@@ -972,6 +1019,12 @@ void plane_configure_shape(int smem, cudaError_t* e) {
                                plane_fwd_bytes<L, NY>());
       r2 = cudaFuncSetAttribute(k_plane_inv_reg<L, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 plane_inv_bytes<L, NY>());
+      // the whole unified L1 as shared memory: room for every CTA the
+      // register budget allows
+      if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_plane_fwd_reg<L, NY>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      if (r2 == cudaSuccess)
+        r2 = cudaFuncSetAttribute(k_plane_inv_reg<L, NY>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
     if (r != cudaSuccess) *e = r;
     if (r2 != cudaSuccess) *e = r2;
