@@ -64,10 +64,14 @@ __device__ __forceinline__ float2 half_twiddle(int k) {
 constexpr int z_reg_tile(int form) { return form == kVacuum ? 16 : 8; }
 
 // fields_in * tile (slot, column) FFTs per tile, a thread pair each, rounded
-// up to whole warps (the pairs past the last slot compute a copy and store nothing)
+// up to whole warps; the forms with sources (8-column tiles, 144 or 160 pair
+// threads) take 192 threads, so that the update stage's (column pair, k)
+// items divide evenly among them for the z lengths 48 and 96 (one and two per
+// thread) and 6 warps are resident per CTA.  The pairs past the last slot
+// skip the transforms.
 template <int FORM>
 constexpr int z_reg_threads() {
-  return (2 * fields_in(FORM) * z_reg_tile(FORM) + 31) / 32 * 32;
+  return FORM == kVacuum ? (2 * fields_in(FORM) * z_reg_tile(FORM) + 31) / 32 * 32 : 192;
 }
 // shared-memory pitch (complex) of one z row: >= fields_in * tile, = 8 (mod 16)
 constexpr int z_reg_pitch(int form) {
@@ -188,24 +192,22 @@ __device__ __forceinline__ void z_reg_tile_job(const DevPlan& P, float2* spec, i
   z_tile_update<NZ, FORM, TX, NT, NP>(P, buf, J, nyq, nm, n1, sh, nft);
   __syncthreads();
   // half-length inverse DFTs: member `half` gives the z samples 2m + half of
-  // the output slots; threads of the remaining slots repeat the last output
-  // slot and store nothing.  Only interior z planes are stored: the inverse
-  // plane pass reads no others.
-  {
-    const int so = s < FOUT ? s : FOUT - 1;
-    const int qo = 2 * so * TX + 4 * (t >> 1) + (t & 1);
+  // the output slots; threads of the remaining slots have nothing to do.
+  // Only interior z planes are stored: the inverse plane pass reads no others.
+  if (s < FOUT) {
+    const int qo = 2 * s * TX + 4 * (t >> 1) + (t & 1);
     const int re = qo + 2 * half, im = qo + 2 - 2 * half;
 #pragma unroll
     for (int k = 0; k < H; ++k) v[k] = make_float2(bw[(half * H + k) * 2 * NP + re], bw[(half * H + k) * 2 * NP + im]);
-  }
-  Dft<float, H, 1>::run(v);
-  if (live && s < FOUT) {
-    const int zlo = bx.ng_lo[2], zhi = NZ - bx.ng_hi[2];
-    float2* dst = g + s * sstride + (int64_t)t * ts + half * zst;
+    Dft<float, H, 1>::run(v);
+    if (live) {
+      const int zlo = bx.ng_lo[2], zhi = NZ - bx.ng_hi[2];
+      float2* dst = g + s * sstride + (int64_t)t * ts + half * zst;
 #pragma unroll
-    for (int m = 0; m < H; ++m) {
-      const int z = 2 * m + half;
-      if (z >= zlo && z < zhi) dst[2 * m * zst] = v[m];
+      for (int m = 0; m < H; ++m) {
+        const int z = 2 * m + half;
+        if (z >= zlo && z < zhi) dst[2 * m * zst] = v[m];
+      }
     }
   }
 }
