@@ -298,6 +298,59 @@ psatd_status psatd_inverse_fft(psatd_plan* plan, void* spectrum, void* field, vo
 psatd_status psatd_plan_spectrum_layout(const psatd_plan* plan, int32_t box,
                                         int64_t* elem_offset, int64_t* elems);
 
+/* ---- One group spread over several ranks (paper Sec. 2.4.1: the group's
+ * FFT distributed over the MPI ranks of a sub-communicator, axis by axis with
+ * a transposition before each axis whose lines are split; Sec. 2.6: the
+ * "optimized communication strategy" keeps the spectrum in the transposed
+ * layout, solves Maxwell's equations there and starts the inverse transform
+ * from it, so a step moves the spectrum twice instead of four times).
+ *
+ * A plan of one box -- the group, periodic along y and z inside its FFT (no
+ * guards on the y and z faces) -- becomes rank `rank` of `world` ranks that
+ * share the group's FFT.  Real space is split in z slabs: the rank holds the
+ * planes [z0, z1) of the box (every y and x, x-face guards included).  After
+ * the x and y transforms, one all-to-all gives every rank the spectrum rows
+ * my in [y0, y1) for every z; the rank transforms z, updates every mode (the
+ * wavenumbers from the global indices) and transforms z back in that layout,
+ * and a second all-to-all returns the rows to the slabs for the inverse y and
+ * x transforms.  The library does the rank's device work; the caller moves
+ * the spectrum (NCCL, MPI, or copies): rank r sends the rows [y0_s, y1_s) of
+ * every plane of its slab to rank s, which stores them at z planes [z0_r,
+ * z1_r) of its rows buffer, and back.  Slabs and rows are split as evenly as
+ * possible, the larger parts first (the first n % world ranks have one more
+ * plane or row).  The device work runs on the generic kernels, in the plan's
+ * precision and form; a constant current is transformed every step.
+ *
+ * Buffers (caller-owned, device, 16-byte aligned, components contiguous):
+ *   slab fields (psatd_fields / psatd_sources as in psatd_push): per
+ *     component (z1 - z0) * n1 * n0 reals, x fastest;
+ *   slab spectrum: F components, each (z1 - z0) * n1 * (n0/2 + 1) complex in
+ *     the order (z, y, mx), component c at c * (z1 - z0) * n1 * (n0/2 + 1);
+ *   rows spectrum: F components, each n2 * (y1 - y0) * (n0/2 + 1) complex in
+ *     the order (z, y, mx);
+ *   F = 6 (vacuum), 9 (E, B, J), 10 (E, B, rho, J) slots in the order of the
+ *   fields and sources (psatd_dist_forward_xy writes all F; psatd_dist_z_update
+ *   reads F and writes E, B (and rho'); psatd_dist_inverse_yx reads those).
+ *
+ * psatd_plan_distribute: PSATD_ERR_INVALID_ARG for a plan of several boxes,
+ * y or z guards, absorbing layers, or rank/world outside 0 <= rank < world <=
+ * min(n1, n2); PSATD_ERR_STATE when the plan is already distributed.  Builds
+ * the rank's job lists (plan-owned device memory).  The other calls return
+ * PSATD_ERR_STATE before it, and are asynchronous on `stream`. */
+psatd_status psatd_plan_distribute(psatd_plan* plan, int32_t world, int32_t rank);
+/* The rank's slab [z0, z1) and spectrum rows [y0, y1) (any pointer may be NULL). */
+psatd_status psatd_dist_bounds(const psatd_plan* plan, int32_t* z0, int32_t* z1, int32_t* y0, int32_t* y1);
+/* S1 (x, y): R2C along x and FFT along y of every slot of the slab. */
+psatd_status psatd_dist_forward_xy(psatd_plan* plan, const psatd_fields* slab, const psatd_sources* sources,
+                                   void* slab_spectrum, void* stream);
+/* S1 (z), S2, S3 (z) on the rank's rows, in place. */
+psatd_status psatd_dist_z_update(psatd_plan* plan, void* rows_spectrum, void* stream);
+/* S3 (y, x): inverse y FFT and C2R along x (the group's 1/(n0 n1 n2)) of the
+ * output slots into the slab's interior x cells (x-face guards untouched);
+ * `slab_spectrum` is overwritten. */
+psatd_status psatd_dist_inverse_yx(psatd_plan* plan, void* slab_spectrum, const psatd_fields* slab,
+                                   const psatd_sources* sources, void* stream);
+
 /* Wait for the plan's last stream and return the first pending error
  * (CUDA error or device-side status word). */
 psatd_status psatd_sync_status(psatd_plan* plan);

@@ -89,6 +89,14 @@ _SIGS = {
     "psatd_inverse_fft": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "psatd_plan_spectrum_layout": (c_int32, [c_void_p, c_int32, POINTER(c_int64),
                                              POINTER(c_int64)]),
+    "psatd_plan_distribute": (c_int32, [c_void_p, c_int32, c_int32]),
+    "psatd_dist_bounds": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32),
+                                    POINTER(c_int32)]),
+    "psatd_dist_forward_xy": (c_int32, [c_void_p, POINTER(psatd_fields), POINTER(psatd_sources), c_void_p,
+                                        c_void_p]),
+    "psatd_dist_z_update": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "psatd_dist_inverse_yx": (c_int32, [c_void_p, c_void_p, POINTER(psatd_fields), POINTER(psatd_sources),
+                                        c_void_p]),
     "psatd_sync_status": (c_int32, [c_void_p]),
     "psatd_status_string": (c_char_p, [c_int32]),
     "psatd_last_error": (c_char_p, [c_void_p]),
@@ -294,6 +302,34 @@ def psatd_forward_fft(plan: int, field: int, spectrum: int, stream: int = 0):
 def psatd_inverse_fft(plan: int, spectrum: int, field: int, stream: int = 0):
     _check(load().psatd_inverse_fft(c_void_p(plan), c_void_p(spectrum), c_void_p(field),
                                     c_void_p(stream)), plan)
+
+
+def psatd_plan_distribute(plan: int, world: int, rank: int):
+    _check(load().psatd_plan_distribute(c_void_p(plan), world, rank), plan)
+
+
+def psatd_dist_bounds(plan: int):
+    """(z0, z1, y0, y1): the rank's z slab and spectrum rows."""
+    v = [c_int32() for _ in range(4)]
+    _check(load().psatd_dist_bounds(c_void_p(plan), *(ctypes.byref(x) for x in v)), plan)
+    return tuple(x.value for x in v)
+
+
+def psatd_dist_forward_xy(plan: int, slab: psatd_fields, src: psatd_sources | None, slab_spectrum: int,
+                          stream: int = 0):
+    _check(load().psatd_dist_forward_xy(c_void_p(plan), ctypes.byref(slab),
+                                        ctypes.byref(src) if src is not None else None, c_void_p(slab_spectrum),
+                                        c_void_p(stream)), plan)
+
+
+def psatd_dist_z_update(plan: int, rows: int, stream: int = 0):
+    _check(load().psatd_dist_z_update(c_void_p(plan), c_void_p(rows), c_void_p(stream)), plan)
+
+
+def psatd_dist_inverse_yx(plan: int, slab_spectrum: int, slab: psatd_fields, src: psatd_sources | None,
+                          stream: int = 0):
+    _check(load().psatd_dist_inverse_yx(c_void_p(plan), c_void_p(slab_spectrum), ctypes.byref(slab),
+                                        ctypes.byref(src) if src is not None else None, c_void_p(stream)), plan)
 
 
 def psatd_sync_status(plan: int):

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(kThreads) k_z_update(DevPlan P, cx<T>* spec, i
   fft_smem<T, -1, true>(sm, nft * nm, 1, row, sh.az, twz);
   for (int e = threadIdx.x; e < n2 * nm; e += blockDim.x) {
     const int z = e / nm, t = e - z * nm;
-    update_mode<T, FORM>(sm + z * row + t, nm, J.m0 + t, J.plane, z, sh, P);
+    update_mode<T, FORM>(sm + z * row + t, nm, J.m0 + t, J.plane + bx.yoff, z, sh, P);
   }
   __syncthreads();
   fft_smem<T, 1, true>(sm, FOUT * nm, 1, row, sh.az, twz);

@@ -346,6 +346,18 @@ struct psatd_plan {
   std::vector<ColJob> zpen_reg;              // boxes of several z lengths whose z pass runs on the register z kernel
   std::vector<PenGroup> grp_zreg;            // ... grouped by z length (code = n2)
   std::vector<PenGroup> grp_pf, grp_pi;      // register plane jobs grouped by plane shape (code: reg_shape_code)
+  // one group spread over ranks (psatd_plan_distribute): the rank's z slab
+  // [z0, z1) and spectrum rows [y0, y1), the plan's boxes followed by the slab
+  // box (every y, the slab's planes, the global n2 for the 1/N factor) and the
+  // rows box (y1 - y0 rows, every z, yoff = y0), and their job lists
+  struct Dist {
+    int world = 0, rank = 0, z0 = 0, z1 = 0, y0 = 0, y1 = 0;
+    BoxDev* d_boxes = nullptr;
+    RowJob* d_rows = nullptr;
+    ColJob *d_ycols = nullptr, *d_zcols = nullptr;
+    int64_t nrows = 0, nycols = 0, nzcols = 0;
+    int64_t s_slab = 0, s_rows = 0;   // complex elements per component of the slab spectrum / the rows
+  } dist;
   int pen_reg_z = 1;                         // tuning: register z kernel for those boxes where one exists
   bool pen_reg_z_used = false;               // ... and whether the plan has such boxes
   int reg_planes = 1;                        // tuning: register plane kernels for the boxes whose shape has them
@@ -2134,6 +2146,152 @@ psatd_status psatd_inverse_fft(psatd_plan* P, void* spectrum, void* field, void*
   CK(P, launch_col(P->prec, 1, 1, D, spectrum, S, 1, P->d_ycols_all, (int64_t)P->ycols_all.size(), P->smem_y, st));
   CK(P, launch_inv_x(P->prec, D, fp, 1, spectrum, S, P->d_rows_all, (int64_t)P->rows_all.size(), P->smem_ix, 0, st));
   P->last_launches = 3;
+  return PSATD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One group spread over ranks (paper Sec. 2.4.1 distributed FFT, Sec. 2.6
+// spectrum kept in the transposed layout): the rank's device work on its z
+// slab and its spectrum rows; the caller moves the spectrum between them.
+// ---------------------------------------------------------------------------
+namespace {
+// [0, n) split into `parts` ranges, sizes differing by at most one, the
+// larger ones first: range `i`
+void even_range(int n, int parts, int i, int* lo, int* hi) {
+  const int q = n / parts, r = n % parts;
+  *lo = i * q + std::min(i, r);
+  *hi = *lo + q + (i < r ? 1 : 0);
+}
+}  // namespace
+
+psatd_status psatd_plan_distribute(psatd_plan* P, int32_t world, int32_t rank) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  try {
+    if (P->dist.world) return fail(P, PSATD_ERR_STATE, "the plan is already distributed");
+    if (P->boxes.size() != 1) return fail(P, PSATD_ERR_INVALID_ARG, "a distributed group is a plan of one box");
+    if (P->form == kPml) return fail(P, PSATD_ERR_INVALID_ARG, "absorbing layers are not distributed");
+    const psatd_box& b = P->boxes[0];
+    if (b.ng_lo[1] || b.ng_hi[1] || b.ng_lo[2] || b.ng_hi[2])
+      return fail(P, PSATD_ERR_INVALID_ARG, "a distributed group has guards on its x faces only");
+    const int n0 = b.n[0], n1 = b.n[1], n2 = b.n[2], L = n0 / 2, hx = L + 1;
+    if (world < 1 || rank < 0 || rank >= world || world > n1 || world > n2)
+      return fail(P, PSATD_ERR_INVALID_ARG,
+                  fmt("rank %d of %d: need 0 <= rank < world <= min(n1, n2) = %d", rank, world, std::min(n1, n2)));
+    auto& d = P->dist;
+    even_range(n2, world, rank, &d.z0, &d.z1);
+    even_range(n1, world, rank, &d.y0, &d.y1);
+    const int nz = d.z1 - d.z0, ny = d.y1 - d.y0;
+    d.s_slab = (int64_t)nz * n1 * hx;
+    d.s_rows = (int64_t)n2 * ny * hx;
+    std::vector<BoxDev> hb = P->hboxes;
+    BoxDev slab = hb[0], rows = hb[0];
+    slab.ng_lo[1] = slab.ng_lo[2] = slab.ng_hi[1] = slab.ng_hi[2] = 0;
+    slab.foff = slab.soff = 0;
+    slab.yoff = 0;
+    rows = slab;
+    rows.n[1] = ny;
+    rows.yoff = d.y0;
+    const int ib = (int)hb.size();
+    hb.push_back(slab);
+    hb.push_back(rows);
+    // the tile sizes of the plan's generic kernels (its shared-memory limits hold)
+    const int csz = (int)P->csize;
+    std::vector<RowJob> rj;
+    const int nr = std::max(1, std::min(nz * n1, kMaxPoints / L));
+    for (int r = 0; r < nz * n1; r += nr) rj.push_back({ib, r, std::min(nr, nz * n1 - r), 0});
+    std::vector<ColJob> yc, zc;
+    int tyc = std::max(1, kMaxPoints / n1);
+    if (tyc >= 8) tyc = tyc / 8 * 8;
+    tyc = std::min(tyc, hx);
+    for (int z = 0; z < nz; ++z)
+      for (int m = 0; m < hx; m += tyc) yc.push_back({ib, z, m, std::min(tyc, hx - m)});
+    int tzc = std::max(1, 100 * 1024 / (n2 * spec_slots(P->form) * csz));
+    if (tzc >= 4) tzc = tzc / 4 * 4;
+    tzc = std::min(tzc, hx);
+    for (int y = 0; y < ny; ++y)
+      for (int m = 0; m < hx; m += tzc) zc.push_back({ib + 1, y, m, std::min(tzc, hx - m)});
+    if (nr * L * csz > P->smem_fx || nr * (hx + L) * csz > P->smem_ix || n1 * tyc * csz > P->smem_y ||
+        n2 * spec_slots(P->form) * tzc * csz > P->smem_z)
+      return fail(P, PSATD_ERR_UNSUPPORTED_SIZE, "slab tiles exceed the plan's shared memory");
+    CK(P, upload(P, hb, &d.d_boxes));
+    CK(P, upload(P, rj, &d.d_rows));
+    CK(P, upload(P, yc, &d.d_ycols));
+    CK(P, upload(P, zc, &d.d_zcols));
+    d.nrows = (int64_t)rj.size();
+    d.nycols = (int64_t)yc.size();
+    d.nzcols = (int64_t)zc.size();
+    d.world = world;
+    d.rank = rank;
+    return PSATD_OK;
+  } catch (...) {
+    return fail(P, PSATD_ERR_OUT_OF_MEMORY, "host allocation failed");
+  }
+}
+
+psatd_status psatd_dist_bounds(const psatd_plan* P, int32_t* z0, int32_t* z1, int32_t* y0, int32_t* y1) {
+  if (!P || !P->dist.world) return PSATD_ERR_INVALID_ARG;
+  if (z0) *z0 = P->dist.z0;
+  if (z1) *z1 = P->dist.z1;
+  if (y0) *y0 = P->dist.y0;
+  if (y1) *y1 = P->dist.y1;
+  return PSATD_OK;
+}
+
+psatd_status psatd_dist_forward_xy(psatd_plan* P, const psatd_fields* slab, const psatd_sources* src,
+                                   void* slab_spectrum, void* stream) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  if (!P->dist.world) return fail(P, PSATD_ERR_STATE, "psatd_plan_distribute first");
+  if (!slab_spectrum || !aligned16(slab_spectrum))
+    return fail(P, PSATD_ERR_INVALID_ARG, "slab spectrum NULL or not 16-byte aligned");
+  FieldPtrs fp{};
+  int nf = 0;
+  psatd_status r = gather_fields(P, slab, src, true, &fp, &nf);
+  if (r != PSATD_OK) return r;
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  DevPlan D = P->dev();
+  D.boxes = P->dist.d_boxes;
+  const auto& d = P->dist;
+  CK(P, launch_fwd_x(P->prec, D, fp, nf, slab_spectrum, d.s_slab, d.d_rows, d.nrows, P->smem_fx, st));
+  CK(P, launch_col(P->prec, -1, 1, D, slab_spectrum, d.s_slab, nf, d.d_ycols, d.nycols, P->smem_y, st));
+  P->last_launches = 2;
+  return PSATD_OK;
+}
+
+psatd_status psatd_dist_z_update(psatd_plan* P, void* rows, void* stream) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  if (!P->dist.world) return fail(P, PSATD_ERR_STATE, "psatd_plan_distribute first");
+  if (!rows || !aligned16(rows)) return fail(P, PSATD_ERR_INVALID_ARG, "rows NULL or not 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  DevPlan D = P->dev();
+  D.boxes = P->dist.d_boxes;
+  const auto& d = P->dist;
+  CK(P, launch_z_update(P->prec, P->form, D, rows, d.s_rows, d.d_zcols, d.nzcols, P->smem_z, fields_in(P->form),
+                        st));
+  P->last_launches = 1;
+  return PSATD_OK;
+}
+
+psatd_status psatd_dist_inverse_yx(psatd_plan* P, void* slab_spectrum, const psatd_fields* slab,
+                                   const psatd_sources* src, void* stream) {
+  if (!P) return PSATD_ERR_INVALID_ARG;
+  if (!P->dist.world) return fail(P, PSATD_ERR_STATE, "psatd_plan_distribute first");
+  if (!slab_spectrum || !aligned16(slab_spectrum))
+    return fail(P, PSATD_ERR_INVALID_ARG, "slab spectrum NULL or not 16-byte aligned");
+  FieldPtrs fp{};
+  int nf = 0;
+  psatd_status r = gather_fields(P, slab, src, true, &fp, &nf);
+  if (r != PSATD_OK) return r;
+  const int FOUT = fields_out(P->form);
+  cudaStream_t st = (cudaStream_t)stream;
+  P->last_stream = st;
+  DevPlan D = P->dev();
+  D.boxes = P->dist.d_boxes;
+  const auto& d = P->dist;
+  CK(P, launch_col(P->prec, 1, 1, D, slab_spectrum, d.s_slab, FOUT, d.d_ycols, d.nycols, P->smem_y, st));
+  CK(P, launch_inv_x(P->prec, D, fp, FOUT, slab_spectrum, d.s_slab, d.d_rows, d.nrows, P->smem_ix, 1, st));
+  P->last_launches = 2;
   return PSATD_OK;
 }
 

@@ -90,6 +90,7 @@ struct BoxDev {
   int32_t ng_hi[3];
   int32_t shape;
   int32_t gplane;                 // index of the box's plane z = 0 in the gather grids
+  int32_t yoff;                   // global index of the box's spectrum row my = 0 (rows of a distributed group)
   int64_t foff;                   // element offset in every field buffer
   int64_t soff;                   // complex-element offset in every spectrum slot
 };

@@ -30,10 +30,15 @@ four transpositions of an FFT that restores its input layout in both
 directions.  The transfers land in buffers of the receiving rank (NCCL on
 GPUs, gloo on CPUs), no remote memory is read in place.
 
-The per-rank transforms and the update are supplied by the caller
-(``GroupStep``); this module is the partition and the exchange.  On this
-machine only one GPU is available, so the multi-rank path is exercised with
-gloo ranks on the CPU (tests/test_distributed.py); it is unmeasured on GPUs.
+The per-rank transforms and the update are supplied to ``GroupStep`` as
+three callables; ``DeviceRank`` gives them on the GPU through libpsatd.so
+(psatd_plan_distribute and the psatd_dist_* calls: the rank's x, y
+transforms of its slab, its z transform + update + inverse z transform of
+its rows, its inverse y, x transforms), and this module does the partition
+and the exchange.  With one GPU per machine here, the multi-rank exchange is
+exercised with gloo ranks on the CPU, and the device work of several ranks
+with the exchange done by copies on one GPU; the path is unmeasured on
+several GPUs.
 """
 from __future__ import annotations
 
@@ -163,3 +168,77 @@ def split_components(fields: Dict[str, torch.Tensor], names: Sequence[str], t: S
     (n2, n1, n0), stacked: (C, |Z_r|, n1, n0)."""
     lo, hi = t.z_slab
     return torch.stack([fields[k][lo:hi] for k in names])
+
+
+class DeviceRank:
+    """The device work of rank `rank` of `world` for a ``GroupStep``: `plan`
+    (a ``solver.Plan`` of the group box alone) distributed with
+    psatd_plan_distribute.  Tensors live on the plan's device, components
+    stacked along the first axis in slot order (Ex, Ey, Ez, Bx, By, Bz, then
+    Jx, Jy, Jz with a current, or rho, Jx, Jy, Jz with a charge):
+      xy_forward(slab (F, |Z_r|, n1, n0)) -> (F, |Z_r|, n1, n0/2 + 1) complex;
+      z_update(rows (F, n2, |Y_r|, n0/2 + 1), y_lo) -> rows, in place;
+      yx_inverse(spec (F, |Z_r|, n1, n0/2 + 1)) -> (F_out, |Z_r|, n1, n0): the
+        output slots (E, B, and rho' with a charge) in a copy of the last
+        slab given to xy_forward, whose x-face guard cells are left as they
+        were.  `spec` is overwritten."""
+
+    def __init__(self, plan, world: int, rank: int):
+        from . import _abi as A
+        self.A = A
+        self.plan = plan
+        A.psatd_plan_distribute(plan.handle, int(world), int(rank))
+        self.z0, self.z1, self.y0, self.y1 = A.psatd_dist_bounds(plan.handle)
+        self.n0, self.n1, self.n2 = (int(v) for v in plan.layout.boxes[0].n)
+        self.hx = self.n0 // 2 + 1
+        self.nf = {"vacuum": 6, "J": 9, "rho": 10}[plan.sources]
+        self.nout = 7 if plan.sources == "rho" else 6
+        self._last = None
+
+    def _structs(self, slab):
+        A = self.A
+        es = slab.element_size() * slab.stride(0)
+        ptr = [slab.data_ptr() + i * es for i in range(slab.shape[0])]
+        f = A.psatd_fields()
+        for a in range(3):
+            f.E[a] = ptr[a]
+            f.B[a] = ptr[3 + a]
+        src = None
+        if self.plan.sources != "vacuum":
+            src = A.psatd_sources()
+            j0 = 6 if self.plan.sources == "J" else 7
+            for a in range(3):
+                src.J[a] = ptr[j0 + a] if j0 + a < len(ptr) else None
+            src.rho = ptr[6] if self.plan.sources == "rho" else None
+        return f, src
+
+    def _stream(self):
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+
+    def xy_forward(self, slab):
+        import torch
+        slab = slab.contiguous()
+        if slab.shape != (self.nf, self.z1 - self.z0, self.n1, self.n0):
+            raise ValueError(f"slab shape {tuple(slab.shape)}")
+        cdt = torch.complex64 if slab.dtype == torch.float32 else torch.complex128
+        spec = torch.empty((self.nf, self.z1 - self.z0, self.n1, self.hx), dtype=cdt, device=slab.device)
+        f, src = self._structs(slab)
+        self.A.psatd_dist_forward_xy(self.plan.handle, f, src, spec.data_ptr(), self._stream())
+        self._last = slab
+        return spec
+
+    def z_update(self, rows, y_lo):
+        if int(y_lo) != self.y0 or not rows.is_contiguous():
+            raise ValueError("rows of another rank, or not contiguous")
+        if rows.shape != (self.nf, self.n2, self.y1 - self.y0, self.hx):
+            raise ValueError(f"rows shape {tuple(rows.shape)}")
+        self.A.psatd_dist_z_update(self.plan.handle, rows.data_ptr(), self._stream())
+        return rows
+
+    def yx_inverse(self, spec):
+        spec = spec.contiguous()
+        out = self._last.clone()
+        f, src = self._structs(out)
+        self.A.psatd_dist_inverse_yx(self.plan.handle, spec.data_ptr(), f, src, self._stream())
+        return out[:self.nout]
