@@ -121,13 +121,47 @@ struct Dft<T, 2, DIR> {
   }
 };
 
+// FP32 products with FP64-accurate constants.  A constant rounded to FP32
+// carries a relative error of up to 3e-8 into every product, the same on
+// every call: an FFT and its inverse built on such roots of unity scale a mode
+// by |w|^2 != 1 per round trip (the FP32 roots of the small DFTs and of the
+// composite twiddles lie slightly inside the unit circle), and over the
+// hundreds of steps of a push that bias adds up linearly: an FP32 push lost
+// ~1e-7 of its amplitude per step.  So in FP32 a constant c = hi + lo (hi its
+// FP32 rounding, lo the FP32 rounding of the rest) multiplies as
+// fma(hi, a, lo * a): the exact product hi * a and the small lo * a are added
+// before the one rounding, which gives the correctly rounded c * a up to the
+// rounding of lo * a (adding lo * a after rounding hi * a would lose it: it is
+// below half a unit in the last place).  FP64 uses the plain products.
+__host__ __device__ constexpr float f32_hi(double v) { return (float)v; }
+__host__ __device__ constexpr float f32_lo(double v) { return (float)(v - (double)(float)v); }
+
+// s * x for a real constant s (FP32: head and tail)
+template <typename T>
+__device__ __forceinline__ T mul_exact(double s, T x) {
+  if constexpr (sizeof(T) == 4)
+    return __fmaf_rn(f32_hi(s), x, f32_lo(s) * x);
+  else
+    return T(s) * x;
+}
+template <typename T, typename C>
+__device__ __forceinline__ C rmul_exact(double s, C a) {
+  return mk<T>(mul_exact<T>(s, a.x), mul_exact<T>(s, a.y));
+}
+// a * (c + i s) for FP32 head/tail constants (ch, cl), (sh, sl): the tail
+// products first, then the head products, one rounding per fused step
+__device__ __forceinline__ float2 cmul_hl(float2 a, float ch, float cl, float sh, float sl) {
+  const float re = __fmaf_rn(a.x, ch, __fmaf_rn(-a.y, sh, __fmaf_rn(a.x, cl, -a.y * sl)));
+  const float im = __fmaf_rn(a.y, ch, __fmaf_rn(a.x, sh, __fmaf_rn(a.y, cl, a.x * sl)));
+  return make_float2(re, im);
+}
+
 template <typename T, int DIR>
 struct Dft<T, 3, DIR> {
   static __device__ __forceinline__ void run(cx<T>* v) {
-    const T h = T(0.86602540378443864676);  // sin(2 pi / 3)
     cx<T> s = v[1] + v[2], d = v[1] - v[2];
     cx<T> m = mk<T>(v[0].x - T(0.5) * s.x, v[0].y - T(0.5) * s.y);
-    cx<T> r = rmul(h, rot<DIR>(d));
+    cx<T> r = rmul_exact<T>(0.86602540378443864676, rot<DIR>(d));   // sin(2 pi / 3), FP32 head + tail
     v[0] = v[0] + s;
     v[1] = m + r;
     v[2] = m - r;
@@ -149,17 +183,20 @@ struct Dft<T, 4, DIR> {
 template <typename T, int DIR>
 struct Dft<T, 5, DIR> {
   static __device__ __forceinline__ void run(cx<T>* v) {
-    const T c1 = T(0.30901699437494742410);   // cos(2 pi/5)
-    const T c2 = T(-0.80901699437494742410);  // cos(4 pi/5)
-    const T s1 = T(0.95105651629515357212);   // sin(2 pi/5)
-    const T s2 = T(0.58778525229247312917);   // sin(4 pi/5)
+    constexpr double c1 = 0.30901699437494742410;   // cos(2 pi/5)
+    constexpr double c2 = -0.80901699437494742410;  // cos(4 pi/5)
+    constexpr double s1 = 0.95105651629515357212;   // sin(2 pi/5)
+    constexpr double s2 = 0.58778525229247312917;   // sin(4 pi/5)
     cx<T> a0 = v[0];
     cx<T> p1 = v[1] + v[4], d1 = v[1] - v[4];
     cx<T> p2 = v[2] + v[3], d2 = v[2] - v[3];
-    cx<T> m1 = mk<T>(a0.x + c1 * p1.x + c2 * p2.x, a0.y + c1 * p1.y + c2 * p2.y);
-    cx<T> m2 = mk<T>(a0.x + c2 * p1.x + c1 * p2.x, a0.y + c2 * p1.y + c1 * p2.y);
-    cx<T> n1 = mk<T>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y);
-    cx<T> n2 = mk<T>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y);
+    // products with the constants in FP32 head + tail (mul_exact)
+    cx<T> m1 = mk<T>(a0.x + mul_exact<T>(c1, p1.x) + mul_exact<T>(c2, p2.x),
+                     a0.y + mul_exact<T>(c1, p1.y) + mul_exact<T>(c2, p2.y));
+    cx<T> m2 = mk<T>(a0.x + mul_exact<T>(c2, p1.x) + mul_exact<T>(c1, p2.x),
+                     a0.y + mul_exact<T>(c2, p1.y) + mul_exact<T>(c1, p2.y));
+    cx<T> n1 = mk<T>(mul_exact<T>(s1, d1.x) + mul_exact<T>(s2, d2.x), mul_exact<T>(s1, d1.y) + mul_exact<T>(s2, d2.y));
+    cx<T> n2 = mk<T>(mul_exact<T>(s2, d1.x) - mul_exact<T>(s1, d2.x), mul_exact<T>(s2, d1.y) - mul_exact<T>(s1, d2.y));
     cx<T> r1 = rot<DIR>(n1), r2 = rot<DIR>(n2);
     v[0] = a0 + p1 + p2;
     v[1] = m1 + r1;
@@ -172,7 +209,7 @@ struct Dft<T, 5, DIR> {
 template <typename T, int DIR>
 struct Dft<T, 8, DIR> {
   static __device__ __forceinline__ void run(cx<T>* v) {
-    const T r2 = T(0.70710678118654752440);
+    constexpr double r2 = 0.70710678118654752440;   // cos(pi/4), split in FP32 (rmul_exact)
     cx<T> e[4] = {v[0], v[2], v[4], v[6]};
     cx<T> o[4] = {v[1], v[3], v[5], v[7]};
     Dft<T, 4, DIR>::run(e);
@@ -180,11 +217,11 @@ struct Dft<T, 8, DIR> {
     // o[k] *= exp(DIR i pi k / 4)
     cx<T> w1, w3;
     if (DIR < 0) {
-      w1 = mk<T>(r2 * (o[1].x + o[1].y), r2 * (o[1].y - o[1].x));
-      w3 = mk<T>(r2 * (o[3].y - o[3].x), -r2 * (o[3].x + o[3].y));
+      w1 = rmul_exact<T>(r2, mk<T>(o[1].x + o[1].y, o[1].y - o[1].x));
+      w3 = rmul_exact<T>(r2, mk<T>(o[3].y - o[3].x, -(o[3].x + o[3].y)));
     } else {
-      w1 = mk<T>(r2 * (o[1].x - o[1].y), r2 * (o[1].x + o[1].y));
-      w3 = mk<T>(-r2 * (o[3].x + o[3].y), r2 * (o[3].x - o[3].y));
+      w1 = rmul_exact<T>(r2, mk<T>(o[1].x - o[1].y, o[1].x + o[1].y));
+      w3 = rmul_exact<T>(r2, mk<T>(-(o[3].x + o[3].y), o[3].x - o[3].y));
     }
     cx<T> w2 = rot<DIR>(o[2]);
     v[0] = e[0] + o[0];
@@ -216,7 +253,20 @@ struct DftComposite {
         if constexpr (n2 > 0) {
           constexpr double c = root_cos(R, n2 * k1);
           constexpr double s = root_sin(R, n2 * k1);
-          u[n2][k1] = cmul(u[n2][k1], mk<T>(T(c), DIR < 0 ? T(-s) : T(s)));
+          constexpr double sd = DIR < 0 ? -s : s;
+          const cx<T> a = u[n2][k1];
+          if constexpr (c == 0.0) {
+            // w = +-i
+            u[n2][k1] = sd > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+          } else if constexpr (c == sd || c == -sd) {
+            // w = c (1 + i sd/c): |c| = sqrt(1/2), one head + tail product per lane
+            u[n2][k1] = c == sd ? rmul_exact<T>(c, mk<T>(a.x - a.y, a.x + a.y))
+                                : rmul_exact<T>(c, mk<T>(a.x + a.y, a.y - a.x));
+          } else if constexpr (sizeof(T) == 4) {
+            u[n2][k1] = cmul_hl(a, f32_hi(c), f32_lo(c), f32_hi(sd), f32_lo(sd));
+          } else {
+            u[n2][k1] = cmul(a, mk<T>(T(c), T(sd)));
+          }
         }
       });
     });
