@@ -190,13 +190,17 @@ struct Dft<T, 5, DIR> {
     cx<T> a0 = v[0];
     cx<T> p1 = v[1] + v[4], d1 = v[1] - v[4];
     cx<T> p2 = v[2] + v[3], d2 = v[2] - v[3];
-    // products with the constants in FP32 head + tail (mul_exact)
-    cx<T> m1 = mk<T>(a0.x + mul_exact<T>(c1, p1.x) + mul_exact<T>(c2, p2.x),
-                     a0.y + mul_exact<T>(c1, p1.y) + mul_exact<T>(c2, p2.y));
-    cx<T> m2 = mk<T>(a0.x + mul_exact<T>(c2, p1.x) + mul_exact<T>(c1, p2.x),
-                     a0.y + mul_exact<T>(c2, p1.y) + mul_exact<T>(c1, p2.y));
-    cx<T> n1 = mk<T>(mul_exact<T>(s1, d1.x) + mul_exact<T>(s2, d2.x), mul_exact<T>(s1, d1.y) + mul_exact<T>(s2, d2.y));
-    cx<T> n2 = mk<T>(mul_exact<T>(s2, d1.x) - mul_exact<T>(s1, d2.x), mul_exact<T>(s2, d1.y) - mul_exact<T>(s1, d2.y));
+    // u x + v y (+ w): the constants' tails first, then their heads (FP32)
+    auto dot2 = [](double u, T x, double v, T y, T w) -> T {
+      if constexpr (sizeof(T) == 4)
+        return __fmaf_rn(f32_hi(u), x, __fmaf_rn(f32_hi(v), y, __fmaf_rn(f32_lo(u), x, __fmaf_rn(f32_lo(v), y, w))));
+      else
+        return w + u * x + v * y;
+    };
+    cx<T> m1 = mk<T>(dot2(c1, p1.x, c2, p2.x, a0.x), dot2(c1, p1.y, c2, p2.y, a0.y));
+    cx<T> m2 = mk<T>(dot2(c2, p1.x, c1, p2.x, a0.x), dot2(c2, p1.y, c1, p2.y, a0.y));
+    cx<T> n1 = mk<T>(dot2(s1, d1.x, s2, d2.x, T(0)), dot2(s1, d1.y, s2, d2.y, T(0)));
+    cx<T> n2 = mk<T>(dot2(s2, d1.x, -s1, d2.x, T(0)), dot2(s2, d1.y, -s1, d2.y, T(0)));
     cx<T> r1 = rot<DIR>(n1), r2 = rot<DIR>(n2);
     v[0] = a0 + p1 + p2;
     v[1] = m1 + r1;

@@ -165,3 +165,15 @@ def test_local_128_fp32_against_fp64_same_decomposition_400_steps():
         plan.close()
     errs = assert_fields(lay, out[32], out[64], O.COMPS, 32, what="local 128^3 FP32 vs FP64, 400 steps")
     print("local_128 FP32 vs FP64 after 400 steps", errs)
+    # the decomposition's own error (guard truncation, paper Sec. 1.3): the
+    # FP64 local push against the FP64 global push (one step of 400 dt)
+    glay = I.global_layout(g, 32)
+    gp = Plan(glay, h, dt * steps, precision=64, sources="vacuum")
+    d64 = gp.pack_fields({k: [I.round_to(v, np.float32)] for k, v in f.items()})
+    gp.push(d64, None, 1)
+    gp.sync()
+    ref = gp.unpack_fields(d64)
+    gp.close()
+    want = {k: I.scatter_global(ref[k][0], lay) for k in O.COMPS}
+    trunc = assert_fields(lay, out[64], want, O.COMPS, 32, tol=1e-4, what="local 128^3 FP64 vs global, 400 steps")
+    print("local_128 FP64 (guard truncation) vs global after 400 steps", trunc)
