@@ -107,11 +107,11 @@ def test_local_128_after_400_steps_against_the_global_oracle():
     128^3 as 2 x 2 x 2 sub-domains of 64^3 with 16 guards (96^3 boxes, the
     benchmark's register kernels and deferred exchange), p = 32, the same
     laser pulse, all 400 steps, FP32, against the oracle's global single-box
-    push (one step of 400 dt).  The difference is the guard truncation of the
-    local decomposition (paper Sec. 1.3: the propagator has unbounded support,
-    n_g = 16 cuts it) plus FP32 rounding; it is stated per field, and bounded
-    by 1e-4 (the 512^3 benchmark's own figure is 3.9e-5).  The GPU's FP64
-    global push, the benchmark's reference, must equal the oracle's to 1e-12."""
+    push (one step of 400 dt).  The difference is FP32 rounding plus the guard
+    truncation of the local decomposition (paper Sec. 1.3: the propagator has
+    unbounded support, n_g = 16 cuts it), which is 1e-7 here (the next test);
+    it is held to the 2e-5 FP32 bound per field.  The GPU's FP64 global push,
+    the benchmark's reference, must equal the oracle's to 1e-12."""
     from paper_1812_07357_gb300.solver import Plan
     g, h, dt, steps = (128, 128, 128), (1.0, 1.0, 1.0), 0.9, 400
     f = I.laser_fields(g, h, 1.0, wavelength=16.0, waist=32.0, duration=20.0)
@@ -134,7 +134,7 @@ def test_local_128_after_400_steps_against_the_global_oracle():
     got = plan.unpack_fields(df)
     plan.close()
     want = {k: I.scatter_global(ref[k][0], lay) for k in O.COMPS}
-    errs = assert_fields(lay, got, want, O.COMPS, 32, tol=1e-4, what="local 128^3 vs global, 400 steps")
+    errs = assert_fields(lay, got, want, O.COMPS, 32, what="local 128^3 vs global, 400 steps")
     print("local_128 vs global after 400 steps", errs)
 
 
