@@ -597,6 +597,32 @@ def _global_host_fields(lay):
     return out
 
 
+def host_link_rates(nbytes=1 << 30):
+    """Copy rates between page-locked host memory and the device: one
+    cudaMemcpyAsync of nbytes each way (torch's copy of a pinned tensor),
+    best of 3 after one warm-up.  No host path can copy faster."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {}
+    for name, dst, src in (("h2d_gbs", d, h), ("d2h_gbs", h, d)):
+        best = float("inf")
+        for r in range(4):
+            with torch.cuda.stream(s):
+                e0.record(s)
+                dst.copy_(src, non_blocking=True)
+                e1.record(s)
+            s.synchronize()
+            if r > 0:
+                best = min(best, e0.elapsed_time(e1))
+        out[name] = nbytes / (best * 1e6)
+    del h, d
+    return out
+
+
 def run_e2e(plan, fields, args, lay, world):
     """Same metric end to end through the C ABI with HOST buffers: every step
     copies the six field components of the whole domain from page-locked host
@@ -625,6 +651,7 @@ def run_e2e(plan, fields, args, lay, world):
         return reduce_max(e0.elapsed_time(e1), torch.device("cuda", torch.cuda.current_device())
                           if world > 1 else None)
 
+    link = host_link_rates()
     rate = lambda ms: total_units(lay.interior_cells * args.e2e_steps, world) / (ms / 1e3)
     names = {1: "copy kernel through the host buffers' device mapping", 0: "copy engines, one stream per component"}
     mode = A.psatd_plan_tuning(plan.handle, A.PSATD_TUNE_HOST_COPY)
@@ -646,7 +673,12 @@ def run_e2e(plan, fields, args, lay, world):
             "other_copy_mode": {"copies": names[1 - mode], "ms_per_step": ms_other / args.e2e_steps,
                                 "value": rate(ms_other)},
             "padded_boxes_on_host": {"api": "psatd_push_host, " + names[mode], "ms_per_step": ms_boxes / args.e2e_steps,
-                                     "value": rate(ms_boxes), "h2d_bytes_per_step": nbb, "d2h_bytes_per_step": nbb}}
+                                     "value": rate(ms_boxes), "h2d_bytes_per_step": nbb, "d2h_bytes_per_step": nbb},
+            "host_link": {"h2d_gbs": link["h2d_gbs"], "d2h_gbs": link["d2h_gbs"],
+                          "copy_ms_per_step": nb / (link["h2d_gbs"] * 1e6) + nb / (link["d2h_gbs"] * 1e6),
+                          "what": "1 GiB cudaMemcpyAsync each way from page-locked memory; a step's input copy "
+                                  "precedes its push and the result copy follows it, so copy_ms_per_step plus "
+                                  "the device step bounds ms_per_step from below"}}
 
 
 def run_fp64_plain(lay, w, fac, nsteps=2):

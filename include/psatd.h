@@ -257,11 +257,16 @@ psatd_status psatd_push(psatd_plan* plan, const psatd_fields* fields,
  * each; they may be the same buffers; page-locked memory copies fastest).
  * The fields are copied to plan-owned device staging buffers (allocated by
  * the first call, 6 x field_bytes, kept until psatd_plan_destroy; that first
- * call therefore allocates and should come before any stream capture), one
- * copy stream per component, or by a copy kernel through the buffers'
- * device mapping (PSATD_TUNE_HOST_COPY); then `nsteps` steps run as in psatd_push
- * (`src`: device sources as there), and the results are copied back the same
- * way.  Asynchronous on `stream`: the host buffers must stay valid, and `in`
+ * call therefore allocates and should come before any stream capture), by
+ * the copy engines or by a copy kernel through the buffers' device mapping
+ * (PSATD_TUNE_HOST_COPY); then `nsteps` steps run as in psatd_push (`src`:
+ * device sources as there), and the results are copied back the same way.
+ * The copies run component by component on a plan-owned side stream; for
+ * the vacuum form the first step's forward x, y transforms and the last
+ * step's inverse y, x transforms also go component by component, so that
+ * the copy of one component overlaps the transforms of its neighbour (the
+ * same kernels on the same data: the results equal psatd_push's bit for
+ * bit).  Asynchronous on `stream`: the host buffers must stay valid, and `in`
  * unchanged, until `stream` has passed this call; work queued on `stream`
  * afterwards sees the results in `out`.  Errors as psatd_push. */
 psatd_status psatd_push_host(psatd_plan* plan, const psatd_fields* in, const psatd_fields* out,
@@ -275,7 +280,9 @@ psatd_status psatd_push_host(psatd_plan* plan, const psatd_fields* in, const psa
  * to the device (as in psatd_push_host), scattered into the plan's padded
  * boxes, guards included (the dual-grid coupling of the plan with one box
  * covering the domain), pushed `nsteps` steps, and the box interiors are
- * gathered back and copied to `out`.  The first call allocates plan-owned
+ * gathered back and copied to `out`, component by component as in
+ * psatd_push_host (the copy of one component also overlaps the scatter or
+ * the gather of its neighbour).  The first call allocates plan-owned
  * device buffers (6 x the domain and 6 x field_bytes) and the coupling, kept
  * until psatd_plan_destroy; make it before any stream capture.  Not for
  * PSATD_DECOMP_INDEPENDENT (PSATD_ERR_STATE).  Asynchronous on `stream`, with
@@ -411,7 +418,9 @@ psatd_status psatd_couple(psatd_coupling* coupling, int32_t direction, void* con
  * every psatd_push.  PSATD_ERR_STATE for a plan without layers. */
 psatd_status psatd_plan_pml_part(const psatd_plan* plan, int32_t q, void** part);
 
-/* Number of kernel launches issued by the last psatd_push call (host count). */
+/* Number of kernel launches issued by the last push call (psatd_push, or
+ * psatd_push_host_global with its copy kernels, scatters and gathers; host
+ * count). */
 int64_t psatd_last_launch_count(const psatd_plan* plan);
 
 /* Number of boxes that run on the fast plane kernels (all three FFT lengths

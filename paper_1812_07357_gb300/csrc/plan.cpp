@@ -1768,20 +1768,12 @@ static psatd_status transform_current(psatd_plan* P, const DevPlan& D, const Fie
   return PSATD_OK;
 }
 
-// One step S1..S4 of every box on `st`; adds the launches to *launches.
-// gather: the forward pass reads guard cells from their owners (deferred
-// exchange); guards: the inverse pass stores the guard cells.
-static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, cudaStream_t st,
-                              int64_t* launches_out, bool gather = false, bool guards = true) {
-  const int FOUT = fields_out(P->form), NFT = step_slots(P);
+// S1 (z) + S2 + S3 (z) of one step: every register-z, pencil and generic z
+// pass, on the plan's spectrum workspace.
+static psatd_status z_step(psatd_plan* P, const DevPlan& D, cudaStream_t st, int64_t* launches_out) {
+  const int NFT = step_slots(P);
   const int64_t S = P->spec_total;
   int64_t launches = 0;
-  // S1: forward x+y of the slots transformed every step
-  {
-    const psatd_status r = forward_xy(P, D, fp, NFT, P->d_ws, st, &launches, gather);
-    if (r != PSATD_OK) return r;
-  }
-  // S1 (z) + S2 + S3 (z)
   const bool one_launch = P->z_one_launch && P->zreg_multi;
   if (one_launch) {
     // every register-z length in one persistent launch, 2 CTAs per SM
@@ -1825,13 +1817,26 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
        }));
     ++launches;
   }
+  *launches_out += launches;
+  return PSATD_OK;
+}
+
+// S3 of one step for the output slots [0, nout) of fp, whose spectra start
+// at `spec` (slot f at spec + f * spec_total), then the absorbing layers'
+// damping and the eager guard exchange (with `guards`).  The kernels use the
+// slot index only to offset the field and spectrum pointers, so one slot c
+// alone is inverted by passing its field pointer as slot 0 and its spectrum.
+static psatd_status inverse_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, int nout, void* spec,
+                                 cudaStream_t st, int64_t* launches_out, bool guards) {
+  const int64_t S = P->spec_total;
+  int64_t launches = 0;
   // S3: inverse y+x, interior cells only
   if (!P->grp_pi.empty()) {
     // one launch per register plane shape; the guard segments are indexed by plane_inv position
     for (const auto& g : P->grp_pi) {
       if (g.code < 0) {
         CK(P, timed(P, 4, st, [&] {
-             return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv + g.start, g.count, P->buf_pi,
+             return launch_plane_inv(P->prec, D, fp, nout, spec, S, P->d_plane_inv + g.start, g.count, P->buf_pi,
                                      P->smem_pi, P->grid_pi, P->segs.empty() ? nullptr : P->d_seg_start + g.start,
                                      P->d_segs, st);
            }));
@@ -1839,7 +1844,7 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
         continue;
       }
       CK(P, timed(P, 4, st, [&] {
-           return launch_plane_inv_reg(g.code, D, fp, FOUT, P->d_ws, S, P->d_plane_inv + g.start, g.count,
+           return launch_plane_inv_reg(g.code, D, fp, nout, spec, S, P->d_plane_inv + g.start, g.count,
                                        P->segs.empty() || !guards ? nullptr : P->d_seg_start + g.start, P->d_segs,
                                        st);
          }));
@@ -1847,7 +1852,7 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
     }
   } else if (!P->plane_inv.empty()) {
     CK(P, timed(P, 4, st, [&] {
-         return launch_plane_inv(P->prec, D, fp, FOUT, P->d_ws, S, P->d_plane_inv, (int64_t)P->plane_inv.size(),
+         return launch_plane_inv(P->prec, D, fp, nout, spec, S, P->d_plane_inv, (int64_t)P->plane_inv.size(),
                                  P->buf_pi, P->smem_pi, P->grid_pi, P->segs.empty() ? nullptr : P->d_seg_start,
                                  P->d_segs, st);
        }));
@@ -1855,23 +1860,23 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
   }
   if (!P->g_rows.empty()) {
     CK(P, timed(P, 3, st, [&] {
-         return launch_col(P->prec, 1, 1, D, P->d_ws, S, FOUT, P->d_g_ycols_int, (int64_t)P->g_ycols_int.size(), P->smem_y, st);
+         return launch_col(P->prec, 1, 1, D, spec, S, nout, P->d_g_ycols_int, (int64_t)P->g_ycols_int.size(), P->smem_y, st);
        }));
     CK(P, timed(P, 4, st, [&] {
-         return launch_inv_x(P->prec, D, fp, FOUT, P->d_ws, S, P->d_g_rows_int, (int64_t)P->g_rows_int.size(), P->smem_ix, 1, st);
+         return launch_inv_x(P->prec, D, fp, nout, spec, S, P->d_g_rows_int, (int64_t)P->g_rows_int.size(), P->smem_ix, 1, st);
        }));
     launches += 2;
   }
   for (const auto& g : P->grp_ycols_int) {
     CK(P, timed(P, 3, st, [&] {
-         return launch_pen_col(P->prec, 1, g.code, D, P->d_ws, S, FOUT, P->d_pen_ycols_int + g.start, g.count,
+         return launch_pen_col(P->prec, 1, g.code, D, spec, S, nout, P->d_pen_ycols_int + g.start, g.count,
                                P->smem_penc, st);
        }));
     ++launches;
   }
   for (const auto& g : P->grp_rows_int) {
     CK(P, timed(P, 4, st, [&] {
-         return launch_pen_xi(P->prec, g.code, D, fp, FOUT, P->d_ws, S, P->d_pen_rows_int + g.start, g.count,
+         return launch_pen_xi(P->prec, g.code, D, fp, nout, spec, S, P->d_pen_rows_int + g.start, g.count,
                               P->smem_penxi, st);
        }));
     ++launches;
@@ -1887,7 +1892,7 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
     ++launches;
   }
   if (!P->step_tiles.empty() && guards) {
-    const int nex = P->form == kPml ? 6 : FOUT;   // components only, not the increments
+    const int nex = P->form == kPml ? 6 : nout;   // components only, not the increments
     CK(P, timed(P, 5, st, [&] {
          return launch_exchange(P->prec, D, fp, nex, P->d_blocks, P->d_step_tiles, (int64_t)P->step_tiles.size(),
                                 st);
@@ -1896,6 +1901,20 @@ static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& 
   }
   *launches_out += launches;
   return PSATD_OK;
+}
+
+// One step S1..S4 of every box on `st`; adds the launches to *launches.
+// gather: the forward pass reads guard cells from their owners (deferred
+// exchange); guards: the inverse pass stores the guard cells.
+static psatd_status push_step(psatd_plan* P, const DevPlan& D, const FieldPtrs& fp, cudaStream_t st,
+                              int64_t* launches_out, bool gather = false, bool guards = true) {
+  // S1: forward x+y of the slots transformed every step
+  psatd_status r = forward_xy(P, D, fp, step_slots(P), P->d_ws, st, launches_out, gather);
+  if (r != PSATD_OK) return r;
+  r = z_step(P, D, st, launches_out);
+  if (r != PSATD_OK) return r;
+  // S3: inverse y+x, interior cells only
+  return inverse_step(P, D, fp, fields_out(P->form), P->d_ws, st, launches_out, guards);
 }
 
 // Capture one step of variant v (2 * gather + guards, see push_step) into a
@@ -1987,19 +2006,19 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
   }
 }
 
-// Copy six buffers of `bytes` between host (`host`) and device (`devb`)
-// memory, to the device when `to_dev`: a copy kernel through the host
-// buffers' device mapping when the plan's mode allows it and every host
-// buffer is page-locked, mapped and 16-byte aligned (and bytes % 16 == 0),
-// else one copy-engine stream per component.  Ordered after earlier work on
-// `st`; later work on `st` sees the copies.
-static psatd_status host_copies(psatd_plan* P, void* const host[6], void* const devb[6], size_t bytes, bool to_dev,
-                                cudaStream_t st) {
+static psatd_status make_copy_streams(psatd_plan* P) {
   if (!P->copy_streams[0]) {
     for (int c = 0; c < 6; ++c) CK(P, cudaStreamCreateWithFlags(&P->copy_streams[c], cudaStreamNonBlocking));
     for (cudaEvent_t& e : P->copy_events) CK(P, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
-  FieldPtrs hp{}, dp{};
+  return PSATD_OK;
+}
+
+// Whether the six host buffers take the copy kernel (the plan's mode allows
+// it, each is page-locked and mapped, both sides 16-byte aligned and bytes %
+// 16 == 0); their device addresses in hp, the device buffers in dp.
+static bool host_mapped(const psatd_plan* P, void* const host[6], void* const devb[6], size_t bytes, FieldPtrs& hp,
+                        FieldPtrs& dp) {
   bool mapped = P->host_copy == 1 && bytes % 16 == 0;
   for (int c = 0; c < 6 && mapped; ++c) {
     void* a = nullptr;
@@ -2011,21 +2030,128 @@ static psatd_status host_copies(psatd_plan* P, void* const host[6], void* const 
     hp.p[c] = a;
     dp.p[c] = devb[c];
   }
-  if (mapped) {
-    int sms = 0, gpu = 0;
-    CK(P, cudaGetDevice(&gpu));
-    CK(P, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gpu));
-    CK(P, launch_copy_fields(to_dev ? dp : hp, to_dev ? hp : dp, 6, (int64_t)bytes, 2 * sms, st));
-    return PSATD_OK;
-  }
+  return mapped;
+}
+
+// The host paths' transfers and push, component by component.  Component c
+// is copied between the host buffer src[c] / dst[c] and the device buffer
+// stage[c] (nbytes) on a side stream, by the copy kernel through the host
+// buffers' device mapping when the plan's mode allows it (host_mapped), else
+// by the copy engines; with a coupling, stage[c] is the whole domain,
+// scattered into the padded boxes P->host_stage[c] (guards included) and
+// gathered back from their interiors, else stage[c] is host_stage[c].
+static psatd_status host_pipeline(psatd_plan* P, void* const src[6], void* const dst[6], void* const stage[6],
+                                  size_t nbytes, psatd_coupling* coupling, const psatd_sources* s, int nsteps,
+                                  cudaStream_t st) {
+  psatd_status r = make_copy_streams(P);
+  if (r != PSATD_OK) return r;
+  FieldPtrs hin{}, hout{}, dev_g{};
+  const bool mapped = host_mapped(P, src, stage, nbytes, hin, dev_g) &&
+                      host_mapped(P, dst, stage, nbytes, hout, dev_g);
+  int sms = 0, gpu = 0;
+  CK(P, cudaGetDevice(&gpu));
+  CK(P, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, gpu));
+  // Component by component, the host copies on a side stream overlap the
+  // scatter into the boxes and the forward x, y transforms of the previous
+  // component (and, on the way back, the inverse y, x transforms and the
+  // gather of the next one): component c's copy is ordered after the copy
+  // of c - 1 on the side stream, the work on c after its copy.  The forward
+  // and inverse passes go component by component for the vacuum form
+  // without sources (per-kernel timing off); otherwise psatd_push runs
+  // between the scatters and the gathers.
+  const bool split = P->form == kVacuum && !s && !P->timing && nsteps >= 1;
+  const DevPlan D = P->dev();
+  FieldPtrs fp{};
+  for (int c = 0; c < 6; ++c) fp.p[c] = P->host_stage[c];
+  const size_t sbytes = (size_t)P->spec_total * P->csize;   // the spectrum of one slot
+  auto slot_fields = [&](int c) {
+    FieldPtrs f1{};
+    f1.p[0] = P->host_stage[c];
+    return f1;
+  };
+  auto slot_spec = [&](int c) { return static_cast<void*>(static_cast<char*>(P->d_ws) + c * sbytes); };
+  cudaStream_t cs = P->copy_streams[0];
+  auto copy_one = [&](int c, bool to_dev) -> cudaError_t {
+    if (mapped) {
+      FieldPtrs h1{}, d1{};
+      h1.p[0] = to_dev ? hin.p[c] : hout.p[c];
+      d1.p[0] = stage[c];
+      return launch_copy_fields(to_dev ? d1 : h1, to_dev ? h1 : d1, 1, (int64_t)nbytes, 2 * sms, cs);
+    }
+    return cudaMemcpyAsync(to_dev ? stage[c] : dst[c], to_dev ? src[c] : stage[c], nbytes,
+                           to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, cs);
+  };
+  int64_t launches = 0;   // kernels of this call: copy kernels, scatters, transforms, gathers
   CK(P, cudaEventRecord(P->copy_events[6], st));
+  CK(P, cudaStreamWaitEvent(cs, P->copy_events[6], 0));
   for (int c = 0; c < 6; ++c) {
-    CK(P, cudaStreamWaitEvent(P->copy_streams[c], P->copy_events[6], 0));
-    CK(P, cudaMemcpyAsync(to_dev ? devb[c] : host[c], to_dev ? host[c] : devb[c], bytes,
-                          to_dev ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, P->copy_streams[c]));
-    CK(P, cudaEventRecord(P->copy_events[c], P->copy_streams[c]));
+    // component c to the device (with a coupling, scattered into the padded
+    // boxes, guards included), and (split) its forward x, y transforms of the
+    // first step
+    CK(P, copy_one(c, true));
+    CK(P, cudaEventRecord(P->copy_events[c], cs));
     CK(P, cudaStreamWaitEvent(st, P->copy_events[c], 0));
+    if (coupling) {
+      r = psatd_couple(coupling, PSATD_G1_TO_G2, &stage[c], &P->host_stage[c], 1, st);
+      if (r != PSATD_OK) return r;
+      launches += P->last_launches;
+    }
+    launches += mapped ? 1 : 0;
+    if (split) {
+      r = forward_xy(P, D, slot_fields(c), 1, slot_spec(c), st, &launches, false);
+      if (r != PSATD_OK) return r;
+    }
   }
+  if (split) {
+    // the steps as psatd_push runs them (the first step reads the guards
+    // the scatter filled; with the deferred exchange later steps gather
+    // them and the last one stores them), but for the first step's forward
+    // pass, done above, and the last step's inverse pass, done below
+    for (int step = 0; step < nsteps; ++step) {
+      if (step > 0) {
+        r = forward_xy(P, D, fp, 6, P->d_ws, st, &launches, P->deferred);
+        if (r != PSATD_OK) return r;
+      }
+      r = z_step(P, D, st, &launches);
+      if (r != PSATD_OK) return r;
+      if (step < nsteps - 1) {
+        r = inverse_step(P, D, fp, 6, P->d_ws, st, &launches, !P->deferred);
+        if (r != PSATD_OK) return r;
+      }
+    }
+    P->last_stream = st;
+  } else {
+    psatd_fields dev{};
+    for (int a = 0; a < 3; ++a) {
+      dev.E[a] = P->host_stage[a];
+      dev.B[a] = P->host_stage[3 + a];
+    }
+    r = psatd_push(P, &dev, s, nsteps, st);
+    if (r != PSATD_OK) return r;
+    launches += P->last_launches;
+  }
+  for (int c = 0; c < 6; ++c) {
+    // (split) the last step's inverse y, x transforms of component c, storing
+    // the guard cells; (with a coupling) its box interiors gathered back into
+    // the domain; to the host
+    if (split) {
+      r = inverse_step(P, D, slot_fields(c), 1, slot_spec(c), st, &launches, true);
+      if (r != PSATD_OK) return r;
+    }
+    if (coupling) {
+      r = psatd_couple(coupling, PSATD_G2_TO_G1, &stage[c], &P->host_stage[c], 1, st);
+      if (r != PSATD_OK) return r;
+      launches += P->last_launches;
+    }
+    launches += mapped ? 1 : 0;
+    CK(P, cudaEventRecord(P->copy_events[c], st));
+    CK(P, cudaStreamWaitEvent(cs, P->copy_events[c], 0));
+    CK(P, copy_one(c, false));
+  }
+  CK(P, cudaEventRecord(P->copy_events[6], cs));
+  CK(P, cudaStreamWaitEvent(st, P->copy_events[6], 0));
+  P->last_launches = launches;
+  P->last_stream = st;
   return PSATD_OK;
 }
 
@@ -2044,19 +2170,7 @@ psatd_status psatd_push_host(psatd_plan* P, const psatd_fields* in, const psatd_
       for (int c = 0; c < 6; ++c) CK(P, dalloc(P, bytes, &P->host_stage[c]));
     void* src[6] = {in->E[0], in->E[1], in->E[2], in->B[0], in->B[1], in->B[2]};
     void* dst[6] = {out->E[0], out->E[1], out->E[2], out->B[0], out->B[1], out->B[2]};
-    psatd_status r = host_copies(P, src, P->host_stage, bytes, true, st);
-    if (r != PSATD_OK) return r;
-    psatd_fields dev{};
-    for (int a = 0; a < 3; ++a) {
-      dev.E[a] = P->host_stage[a];
-      dev.B[a] = P->host_stage[3 + a];
-    }
-    r = psatd_push(P, &dev, s, nsteps, stream);
-    if (r != PSATD_OK) return r;
-    r = host_copies(P, dst, P->host_stage, bytes, false, st);
-    if (r != PSATD_OK) return r;
-    P->last_stream = st;
-    return PSATD_OK;
+    return host_pipeline(P, src, dst, P->host_stage, bytes, nullptr, s, nsteps, st);
   } catch (...) {
     return fail(P, PSATD_ERR_INVALID_ARG, "internal error");
   }
@@ -2091,25 +2205,7 @@ psatd_status psatd_push_host_global(psatd_plan* P, const psatd_fields* in, const
       for (int c = 0; c < 6; ++c) CK(P, dalloc(P, bytes, &P->host_stage[c]));
     void* src[6] = {in->E[0], in->E[1], in->E[2], in->B[0], in->B[1], in->B[2]};
     void* dst[6] = {out->E[0], out->E[1], out->E[2], out->B[0], out->B[1], out->B[2]};
-    // the domain to the device, then into the padded boxes (guards included)
-    psatd_status r = host_copies(P, src, P->global_stage, gbytes, true, st);
-    if (r != PSATD_OK) return r;
-    r = psatd_couple(P->global_coupling, PSATD_G1_TO_G2, P->global_stage, P->host_stage, 6, stream);
-    if (r != PSATD_OK) return r;
-    psatd_fields dev{};
-    for (int a = 0; a < 3; ++a) {
-      dev.E[a] = P->host_stage[a];
-      dev.B[a] = P->host_stage[3 + a];
-    }
-    r = psatd_push(P, &dev, s, nsteps, stream);
-    if (r != PSATD_OK) return r;
-    // the box interiors back into the domain, and to the host
-    r = psatd_couple(P->global_coupling, PSATD_G2_TO_G1, P->global_stage, P->host_stage, 6, stream);
-    if (r != PSATD_OK) return r;
-    r = host_copies(P, dst, P->global_stage, gbytes, false, st);
-    if (r != PSATD_OK) return r;
-    P->last_stream = st;
-    return PSATD_OK;
+    return host_pipeline(P, src, dst, P->global_stage, gbytes, P->global_coupling, s, nsteps, st);
   } catch (...) {
     return fail(P, PSATD_ERR_INVALID_ARG, "internal error");
   }

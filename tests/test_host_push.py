@@ -23,8 +23,11 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("prec,copy", [(32, 1), (64, 1), (32, 0)])
-def test_host_push_equals_device_push_and_oracle(torch, prec, copy):
+@pytest.mark.parametrize("prec,copy,split", [(32, 1, True), (64, 1, True), (32, 0, True), (32, 1, False)])
+def test_host_push_equals_device_push_and_oracle(torch, prec, copy, split):
+    """split: the first step's forward pass and the last step's inverse pass
+    go component by component between the copies (vacuum form); with
+    per-kernel timing on, psatd_push runs whole between the copies."""
     from paper_1812_07357_gb300 import _abi as A
     from paper_1812_07357_gb300.solver import Plan
     lay = I.local_layout((128, 64, 32), (2, 1, 2), (16, 16, 4), 16)     # register kernels in FP32
@@ -39,6 +42,8 @@ def test_host_push_equals_device_push_and_oracle(torch, prec, copy):
     host_in = {k: v.cpu().pin_memory() for k, v in dev.items()}
     keep = {k: v.clone() for k, v in host_in.items()}
     host_out = {k: torch.empty_like(v).pin_memory() for k, v in host_in.items()}
+    if not split:
+        A.psatd_plan_set_timing(plan.handle, True)
     plan.push(dev, None, 3)
     plan.push_host(host_in, host_out, None, 3)
     plan.sync()
@@ -55,11 +60,16 @@ def test_host_push_equals_device_push_and_oracle(torch, prec, copy):
     assert_fields(lay, got, ref, O.COMPS, prec)
 
 
-@pytest.mark.parametrize("prec,copy", [(32, 1), (64, 1), (32, 0)])
-def test_host_global_push_matches_device_push_and_oracle(torch, prec, copy):
+@pytest.mark.parametrize("prec,copy,nsteps,split", [(32, 1, 3, True), (64, 1, 3, True), (32, 0, 3, True),
+                                                    (32, 1, 1, True), (32, 0, 1, True), (64, 1, 1, True),
+                                                    (32, 1, 2, False), (32, 0, 1, False)])
+def test_host_global_push_matches_device_push_and_oracle(torch, prec, copy, nsteps, split):
     """Whole-domain host arrays: scattered into the boxes (guards included),
-    pushed, interiors gathered back; equal to the device push of the same
-    boxes bit for bit, and to the oracle."""
+    pushed, interiors gathered back, component by component (split: the
+    first step's forward pass and the last step's inverse pass per component
+    too; with per-kernel timing on, psatd_push runs whole between the
+    scatters and the gathers).  Two calls in place: equal to two device
+    pushes of the same boxes bit for bit, and to the oracle."""
     from paper_1812_07357_gb300 import _abi as A
     from paper_1812_07357_gb300.solver import Plan
     g = (128, 64, 32)
@@ -73,8 +83,11 @@ def test_host_global_push_matches_device_push_and_oracle(torch, prec, copy):
     host = {k: torch.from_numpy(v.ravel().copy()).to(dt_).pin_memory() for k, v in f.items()}
     boxes = {k: I.scatter_global(v, lay) for k, v in f.items()}
     dev = plan.pack_fields(boxes)
-    plan.push(dev, None, 3)
-    plan.push_host_global(host, None, None, 3)
+    if not split:
+        A.psatd_plan_set_timing(plan.handle, True)
+    for _ in range(2):
+        plan.push(dev, None, nsteps)
+        plan.push_host_global(host, None, None, nsteps)
     torch.cuda.synchronize()
     got_dev = plan.unpack_fields(dev)
     for k in O.COMPS:
@@ -83,6 +96,6 @@ def test_host_global_push_matches_device_push_and_oracle(torch, prec, copy):
             o, m = b.origin, b.interior
             assert np.array_equal(hg[o[2]:o[2] + m[2], o[1]:o[1] + m[1], o[0]:o[0] + m[0]],
                                   a[O._interior_slices(b)]), k
-    ref = O.push(lay, boxes, {}, 3, (1.0,) * 3, 0.9)
+    ref = O.push(lay, boxes, {}, 2 * nsteps, (1.0,) * 3, 0.9)
     assert_fields(lay, got_dev, ref, O.COMPS, prec)
     plan.close()
