@@ -653,7 +653,7 @@ def run_e2e(plan, fields, args, lay, world):
 
     link = host_link_rates()
     rate = lambda ms: total_units(lay.interior_cells * args.e2e_steps, world) / (ms / 1e3)
-    names = {1: "copy kernel through the host buffers' device mapping", 0: "copy engines, one stream per component"}
+    names = {1: "copy kernel through the host buffers' device mapping", 0: "copy engines"}
     mode = A.psatd_plan_tuning(plan.handle, A.PSATD_TUNE_HOST_COPY)
     ms = timed_steps(plan.push_host_global, host)          # the plan's default copy mode
     A.psatd_plan_tune(plan.handle, A.PSATD_TUNE_HOST_COPY, 1 - mode)
@@ -676,9 +676,9 @@ def run_e2e(plan, fields, args, lay, world):
                                      "value": rate(ms_boxes), "h2d_bytes_per_step": nbb, "d2h_bytes_per_step": nbb},
             "host_link": {"h2d_gbs": link["h2d_gbs"], "d2h_gbs": link["d2h_gbs"],
                           "copy_ms_per_step": nb / (link["h2d_gbs"] * 1e6) + nb / (link["d2h_gbs"] * 1e6),
-                          "what": "1 GiB cudaMemcpyAsync each way from page-locked memory; a step's input copy "
-                                  "precedes its push and the result copy follows it, so copy_ms_per_step plus "
-                                  "the device step bounds ms_per_step from below"}}
+                          "what": "1 GiB cudaMemcpyAsync each way from page-locked memory; every input copy of "
+                                  "a step precedes its z pass and every result copy follows it, so "
+                                  "copy_ms_per_step plus the z pass bounds ms_per_step from below"}}
 
 
 def run_fp64_plain(lay, w, fac, nsteps=2):
