@@ -438,7 +438,7 @@ struct psatd_plan {
   void* global_stage[6] = {};
   psatd_coupling* global_coupling = nullptr;
   void* host_stage[6] = {};
-  cudaStream_t copy_streams[6] = {};
+  cudaStream_t copy_stream = nullptr;   // host paths: the copies (highest priority)
   cudaEvent_t copy_events[7] = {};
   FieldPtrs graph_fp{};
   int graph_nf = 0;
@@ -470,8 +470,7 @@ struct psatd_plan {
       if (g) cudaGraphExecDestroy(g);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     destroy_global_coupling(global_coupling);
-    for (cudaStream_t c : copy_streams)
-      if (c) cudaStreamDestroy(c);
+    if (copy_stream) cudaStreamDestroy(copy_stream);
     for (cudaEvent_t e : copy_events)
       if (e) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
@@ -2006,9 +2005,13 @@ psatd_status psatd_push(psatd_plan* P, const psatd_fields* f, const psatd_source
   }
 }
 
-static psatd_status make_copy_streams(psatd_plan* P) {
-  if (!P->copy_streams[0]) {
-    for (int c = 0; c < 6; ++c) CK(P, cudaStreamCreateWithFlags(&P->copy_streams[c], cudaStreamNonBlocking));
+static psatd_status make_copy_stream(psatd_plan* P) {
+  if (!P->copy_stream) {
+    // highest priority: a copy kernel's blocks take the SM slots that free up
+    // before the waiting blocks of the transforms running beside it
+    int least = 0, greatest = 0;
+    CK(P, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(P, cudaStreamCreateWithPriority(&P->copy_stream, cudaStreamNonBlocking, greatest));
     for (cudaEvent_t& e : P->copy_events) CK(P, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   return PSATD_OK;
@@ -2043,7 +2046,7 @@ static bool host_mapped(const psatd_plan* P, void* const host[6], void* const de
 static psatd_status host_pipeline(psatd_plan* P, void* const src[6], void* const dst[6], void* const stage[6],
                                   size_t nbytes, psatd_coupling* coupling, const psatd_sources* s, int nsteps,
                                   cudaStream_t st) {
-  psatd_status r = make_copy_streams(P);
+  psatd_status r = make_copy_stream(P);
   if (r != PSATD_OK) return r;
   FieldPtrs hin{}, hout{}, dev_g{};
   const bool mapped = host_mapped(P, src, stage, nbytes, hin, dev_g) &&
@@ -2070,7 +2073,7 @@ static psatd_status host_pipeline(psatd_plan* P, void* const src[6], void* const
     return f1;
   };
   auto slot_spec = [&](int c) { return static_cast<void*>(static_cast<char*>(P->d_ws) + c * sbytes); };
-  cudaStream_t cs = P->copy_streams[0];
+  cudaStream_t cs = P->copy_stream;
   auto copy_one = [&](int c, bool to_dev) -> cudaError_t {
     if (mapped) {
       FieldPtrs h1{}, d1{};
