@@ -23,11 +23,14 @@ def torch():
     return t
 
 
-@pytest.mark.parametrize("prec,copy,split", [(32, 1, True), (64, 1, True), (32, 0, True), (32, 1, False)])
-def test_host_push_equals_device_push_and_oracle(torch, prec, copy, split):
+@pytest.mark.parametrize("prec,copy,split,eager", [(32, 1, True, False), (64, 1, True, False), (32, 0, True, False),
+                                                  (32, 1, False, False), (32, 1, True, True)])
+def test_host_push_equals_device_push_and_oracle(torch, prec, copy, split, eager):
     """split: the first step's forward pass and the last step's inverse pass
     go component by component between the copies (vacuum form); with
-    per-kernel timing on, psatd_push runs whole between the copies."""
+    per-kernel timing on, psatd_push runs whole between the copies.  eager:
+    the guard exchange after every step (one component at a time after the
+    split inverse pass) instead of the deferred one."""
     from paper_1812_07357_gb300 import _abi as A
     from paper_1812_07357_gb300.solver import Plan
     lay = I.local_layout((128, 64, 32), (2, 1, 2), (16, 16, 4), 16)     # register kernels in FP32
@@ -35,7 +38,7 @@ def test_host_push_equals_device_push_and_oracle(torch, prec, copy, split):
     fields = {k: I.scatter_global(v, lay) for k, v in f.items()}
     if prec == 32:
         fields = {k: I.round_to(v, np.float32) for k, v in fields.items()}
-    plan = Plan(lay, (1.0,) * 3, 0.9, precision=prec, sources="vacuum")
+    plan = Plan(lay, (1.0,) * 3, 0.9, precision=prec, sources="vacuum", eager_exchange=eager)
     A.psatd_plan_tune(plan.handle, A.PSATD_TUNE_HOST_COPY, copy)
     assert plan.tuning()["host_copy"] == copy
     dev = plan.pack_fields(fields)
